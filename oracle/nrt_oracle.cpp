@@ -1,0 +1,1275 @@
+// FP64 CPU oracle for the point-cloud radio ray tracer.
+//
+// TEST INFRASTRUCTURE ONLY.  Tests, the smoke check and the benchmark's CPU
+// baseline leg may load this library; the product path (the CUDA library and
+// its Python binding) never does.  It shares no code, header, table or
+// constant generator with the CUDA path: it is a plain, slow restatement of
+// the method, step by step, in double precision.
+//
+// What it follows (Vaara et al., "Differentiable High-Performance Ray
+// Tracing-Based Simulation of Radio Propagation with Point Clouds"):
+//   Sec. II-A   voxelisation into discretised point sets (DPS), reception points
+//   Sec. II-B   visibility from each RX to every DPS reception point; LOS casts;
+//               rays launched once and reflected specularly at every hit
+//   Sec. II-B-1 diffuse scattering only as the last interaction, validated by a
+//               cast from the scatter point to the RX
+//   Sec. II-B-2 specular refinement: path-length minimisation on infinite
+//               planes (Eq. 1), then validation casts with the angle and plane
+//               distance thresholds t_a, t_d and up to kappa retries (Table I)
+//   Sec. II-B-4 duplicate removal by (interaction types, surface labels of the
+//               closest points; voxel of a diffuse scatter point)
+//   Sec. II-C   ray/disc intersection and the weighted average of Eq. 3 with
+//               the weights of Eq. 4
+// The EM formulas (the paper delegates them to an external library) are
+// readings written from textbook physics: Fresnel coefficients with the
+// ITU-R P.2040 complex permittivity, an effective-roughness reduction and a
+// Lambertian diffuse lobe (Degli-Esposti 2007), free-space spreading and delay.
+//
+// Besides the values, the oracle reports where floating point could decide a
+// discrete outcome differently in a lower-precision implementation ("ambiguous"
+// decisions within a band delta of a threshold); tests compare only the
+// decisions the oracle marks certain.
+//
+// Parity pins: see tests/test_oracle_*.py (closed forms, brute force vs grid,
+// image-source enumeration in a shoebox room, finite differences).
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <set>
+#include <tuple>
+#include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+const double kInf = std::numeric_limits<double>::infinity();
+const double kPi = 3.14159265358979323846;
+const double kC0 = 299792458.0;         // speed of light, m/s
+const double kEps0 = 8.8541878128e-12;  // vacuum permittivity, F/m
+
+struct V3 {
+  double x, y, z;
+};
+inline V3 operator+(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+inline V3 operator-(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline V3 operator*(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline double norm(V3 a) { return std::sqrt(dot(a, a)); }
+inline V3 unit(V3 a) { return (1.0 / norm(a)) * a; }
+inline double comp(V3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+// ---------------------------------------------------------------------------
+// Scene: points, voxels (DPS), reception points, and an acceleration grid.
+// ---------------------------------------------------------------------------
+struct Scene {
+  int64_t n = 0;
+  std::vector<V3> P, N;
+  std::vector<int> surf, mat;
+  std::vector<std::array<int, 3>> vox;  // voxel of each point
+  std::vector<int> dps_of;              // DPS index of each point
+  std::vector<std::array<int, 3>> dps_vox;
+  std::vector<std::vector<int>> dps_pts;
+  std::vector<V3> recv;                 // reception point = mean of the DPS's points
+  double rho = 0, rp = 0, lambda_d = 0;
+  float bmin_f[3] = {0, 0, 0};
+  // acceleration grid (grid_cell <= 0 means brute force over all discs)
+  bool brute = true;
+  double g = 0, band_cap = 0;
+  V3 gmin{0, 0, 0};
+  int gd[3] = {0, 0, 0};
+  std::vector<std::vector<int>> cells;
+};
+
+// Voxel index of a coordinate.  The voxel decides the DPS a point belongs to
+// (Sec. II-A), an integer outcome, so it is taken in float32 -- the same
+// precision as the kernel: floor(fl32(fl32(p - bmin) / rho)).
+int voxel_f32(float p, float bmin, float rho) {
+  volatile float d = p - bmin;
+  volatile float s = d / rho;
+  return (int)std::floor((float)s);
+}
+
+Scene* build_scene(const float* pos, const float* nrm, const uint16_t* surf, const uint8_t* mat,
+                   int64_t n, double rho, double rp, double lambda_d, double grid_cell,
+                   double band_cap) {
+  Scene* S = new Scene();
+  S->n = n;
+  S->rho = rho;
+  S->rp = rp;
+  S->lambda_d = lambda_d;
+  S->band_cap = band_cap;
+  S->P.resize(n);
+  S->N.resize(n);
+  S->surf.resize(n);
+  S->mat.resize(n);
+  for (int k = 0; k < 3; ++k) S->bmin_f[k] = std::numeric_limits<float>::infinity();
+  for (int64_t i = 0; i < n; ++i) {
+    S->P[i] = {pos[3 * i], pos[3 * i + 1], pos[3 * i + 2]};
+    S->N[i] = {nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+    S->surf[i] = surf[i];
+    S->mat[i] = mat[i];
+    for (int k = 0; k < 3; ++k) S->bmin_f[k] = std::min(S->bmin_f[k], pos[3 * i + k]);
+  }
+  // voxels and DPS (ordered by voxel coordinate, lexicographic)
+  const float rho_f = (float)rho;
+  S->vox.resize(n);
+  std::map<std::array<int, 3>, int> index;
+  for (int64_t i = 0; i < n; ++i) {
+    std::array<int, 3> v;
+    for (int k = 0; k < 3; ++k) v[k] = voxel_f32(pos[3 * i + k], S->bmin_f[k], rho_f);
+    S->vox[i] = v;
+    index.emplace(v, 0);
+  }
+  int next = 0;
+  for (auto& kv : index) kv.second = next++;
+  S->dps_vox.resize(next);
+  S->dps_pts.resize(next);
+  for (auto& kv : index) S->dps_vox[kv.second] = kv.first;
+  S->dps_of.resize(n);
+  for (int64_t i = 0; i < n; ++i) {
+    int d = index[S->vox[i]];
+    S->dps_of[i] = d;
+    S->dps_pts[d].push_back((int)i);
+  }
+  S->recv.resize(next);
+  for (int d = 0; d < next; ++d) {
+    V3 s{0, 0, 0};
+    for (int i : S->dps_pts[d]) s = s + S->P[i];
+    S->recv[d] = (1.0 / (double)S->dps_pts[d].size()) * s;
+  }
+  // uniform grid: each disc listed in every cell overlapped by the cube of
+  // half-size r_p + band_cap around its centre.
+  if (grid_cell > 0 && n > 0) {
+    S->brute = false;
+    S->g = grid_cell;
+    const double R = rp + band_cap + 1e-9;
+    V3 lo{kInf, kInf, kInf}, hi{-kInf, -kInf, -kInf};
+    for (int64_t i = 0; i < n; ++i) {
+      lo = {std::min(lo.x, S->P[i].x), std::min(lo.y, S->P[i].y), std::min(lo.z, S->P[i].z)};
+      hi = {std::max(hi.x, S->P[i].x), std::max(hi.y, S->P[i].y), std::max(hi.z, S->P[i].z)};
+    }
+    S->gmin = {lo.x - R, lo.y - R, lo.z - R};
+    for (int k = 0; k < 3; ++k)
+      S->gd[k] = (int)std::floor((comp(hi, k) + R - comp(S->gmin, k)) / grid_cell) + 1;
+    S->cells.assign((size_t)S->gd[0] * S->gd[1] * S->gd[2], {});
+    for (int64_t i = 0; i < n; ++i) {
+      int a[3], b[3];
+      for (int k = 0; k < 3; ++k) {
+        a[k] = std::max(0, (int)std::floor((comp(S->P[i], k) - R - comp(S->gmin, k)) / grid_cell));
+        b[k] = std::min(S->gd[k] - 1,
+                        (int)std::floor((comp(S->P[i], k) + R - comp(S->gmin, k)) / grid_cell));
+      }
+      for (int z = a[2]; z <= b[2]; ++z)
+        for (int y = a[1]; y <= b[1]; ++y)
+          for (int x = a[0]; x <= b[0]; ++x)
+            S->cells[((size_t)z * S->gd[1] + y) * S->gd[0] + x].push_back((int)i);
+    }
+  }
+  return S;
+}
+
+// ---------------------------------------------------------------------------
+// Ray/disc intersection and the closest hit (Sec. II-C, Eq. 3, Eq. 4).
+// ---------------------------------------------------------------------------
+struct DiscEval {
+  bool ok;     // plane not parallel to the ray
+  double t;    // ray parameter of the plane hit
+  double r;    // distance of the plane hit from the disc centre
+  double den;  // d . n_i
+  V3 q;        // plane hit point q_i
+};
+
+inline DiscEval eval_disc(const Scene& S, int i, V3 o, V3 d) {
+  DiscEval e;
+  e.den = dot(d, S.N[i]);
+  if (e.den == 0.0) {
+    e.ok = false;
+    e.t = e.r = 0.0;
+    e.q = {0, 0, 0};
+    return e;
+  }
+  e.ok = true;
+  e.t = dot(S.P[i] - o, S.N[i]) / e.den;
+  e.q = o + e.t * d;
+  e.r = norm(e.q - S.P[i]);
+  return e;
+}
+
+struct Hit {
+  bool hit = false;
+  double t = kInf;
+  int idx = -1;   // point index of q_min
+  int dps = -1;   // DPS of q_min
+  V3 q{0, 0, 0};  // Eq. 3 weighted intersection
+  V3 n{0, 0, 0};  // weighted normal, facing the incoming ray
+  double cos_in = 0.0;
+  bool amb = false;
+};
+
+struct CastCfg {
+  double t_min = 1e-4;  // hits need t > t_min
+  double delta = 0.0;   // ambiguity band (position units)
+};
+
+// Visit the discs that can matter for a cast on [t_lo, t_hi].  In brute
+// force mode that is every disc; with the grid it is every disc listed in a
+// cell the ray passes through, visited in order of t until `stop(t_enter)`.
+template <class F, class Stop>
+void for_candidate_discs(const Scene& S, V3 o, V3 d, double t_lo, double t_hi, F&& f, Stop&& stop) {
+  if (S.brute) {
+    for (int64_t i = 0; i < S.n; ++i) f((int)i);
+    return;
+  }
+  // slab test against the grid box
+  double t0 = t_lo, t1 = t_hi;
+  double inv[3];
+  for (int k = 0; k < 3; ++k) {
+    double dk = comp(d, k), ok = comp(o, k);
+    double lo = comp(S.gmin, k), hi = lo + S.gd[k] * S.g;
+    if (dk == 0.0) {
+      inv[k] = kInf;
+      if (ok < lo || ok > hi) return;
+      continue;
+    }
+    inv[k] = 1.0 / dk;
+    double ta = (lo - ok) * inv[k], tb = (hi - ok) * inv[k];
+    if (ta > tb) std::swap(ta, tb);
+    t0 = std::max(t0, ta);
+    t1 = std::min(t1, tb);
+  }
+  if (t0 > t1) return;
+  V3 p = o + t0 * d;
+  int c[3], step[3];
+  double tnext[3];
+  for (int k = 0; k < 3; ++k) {
+    c[k] = (int)std::floor((comp(p, k) - comp(S.gmin, k)) / S.g);
+    c[k] = std::min(std::max(c[k], 0), S.gd[k] - 1);
+    double dk = comp(d, k);
+    step[k] = dk > 0 ? 1 : (dk < 0 ? -1 : 0);
+    if (step[k] == 0) {
+      tnext[k] = kInf;
+    } else {
+      double bnd = comp(S.gmin, k) + (c[k] + (step[k] > 0 ? 1 : 0)) * S.g;
+      tnext[k] = (bnd - comp(o, k)) * inv[k];
+    }
+  }
+  for (;;) {
+    const auto& cell = S.cells[((size_t)c[2] * S.gd[1] + c[1]) * S.gd[0] + c[0]];
+    for (int i : cell) f(i);
+    int k = 0;
+    if (tnext[1] < tnext[k]) k = 1;
+    if (tnext[2] < tnext[k]) k = 2;
+    double tenter = tnext[k];
+    if (tenter > t1 || stop(tenter)) return;
+    c[k] += step[k];
+    if (c[k] < 0 || c[k] >= S.gd[k]) return;
+    double bnd = comp(S.gmin, k) + (c[k] + (step[k] > 0 ? 1 : 0)) * S.g;
+    tnext[k] = (bnd - comp(o, k)) * inv[k];
+  }
+}
+
+// Closest disc hit along o + t d (|d| = 1) with t in (t_min, t_max), ignoring
+// the discs of DPS `skip`.  q_min is the hit with the smallest t; ties go to
+// the smaller point index.  With `weighted`, the intersection point is the
+// Eq. 3 average over the intersected discs of the DPS of q_min, with the Eq. 4
+// weights exp(-|q_i - p_i|^2 / (2 r_p^2)) * exp(-lambda_d |q_i - q_min|), and
+// the normal is the same weighted average of the disc normals, normalised and
+// turned to face the incoming ray.
+Hit cast(const Scene& S, V3 o, V3 d, int skip, double t_max, bool weighted, const CastCfg& cfg) {
+  Hit h;
+  const double rp = S.rp, cap = S.band_cap;
+  struct Seen {
+    int i;
+    DiscEval e;
+  };
+  std::vector<Seen> seen;
+  seen.reserve(256);
+  double best_t = kInf;
+  int best_i = -1;
+  auto visit = [&](int i) {
+    if (S.dps_of[i] == skip) return;
+    DiscEval e = eval_disc(S, i, o, d);
+    if (!e.ok) return;
+    seen.push_back({i, e});
+    if (e.t > cfg.t_min && e.t < t_max && e.r <= rp) {
+      if (e.t < best_t || (e.t == best_t && i < best_i)) {
+        best_t = e.t;
+        best_i = i;
+      }
+    }
+  };
+  auto stop = [&](double tenter) {
+    double lim = std::min(best_t, t_max);
+    return tenter > lim + 2.0 * cap;
+  };
+  for_candidate_discs(S, o, d, cfg.t_min - cap, t_max + cap, visit, stop);
+
+  auto band = [&](const DiscEval& e) {
+    double b = cfg.delta / std::max(std::fabs(e.den), 1e-12);
+    return std::min(b, cap);
+  };
+  const bool hit = best_i >= 0;
+  double b_best = 0.0;
+  DiscEval ebest{};
+  if (hit) {
+    for (const auto& s : seen)
+      if (s.i == best_i) {
+        ebest = s.e;
+        break;
+      }
+    b_best = band(ebest);
+  }
+  // ambiguity: decisions a lower-precision implementation could take otherwise
+  if (cfg.delta > 0) {
+    const double t_lim = hit ? best_t : t_max;
+    for (const auto& s : seen) {
+      const DiscEval& e = s.e;
+      double b = band(e);
+      if (e.t < cfg.t_min - b) continue;
+      if (e.t > t_lim + b + b_best) continue;
+      bool near_or_in = e.r < rp + b;
+      if (std::fabs(e.r - rp) < b) h.amb = true;                                  // disc edge
+      if (near_or_in && std::fabs(e.t - cfg.t_min) < b) h.amb = true;            // t_min
+      if (near_or_in && std::isfinite(t_max) && std::fabs(e.t - t_max) < b) h.amb = true;
+      if (hit && s.i != best_i && near_or_in && e.t != best_t &&
+          std::fabs(e.t - best_t) < b + b_best)
+        h.amb = true;                                                             // depth tie
+    }
+  }
+  if (!hit) return h;
+  h.hit = true;
+  h.t = best_t;
+  h.idx = best_i;
+  h.dps = S.dps_of[best_i];
+  if (!weighted) return h;
+  const V3 qmin = ebest.q;
+  double sw = 0.0;
+  V3 sq{0, 0, 0}, sn{0, 0, 0};
+  for (int i : S.dps_pts[h.dps]) {
+    DiscEval e = eval_disc(S, i, o, d);
+    if (!e.ok) continue;
+    double b = band(e);
+    if (cfg.delta > 0 && e.t > cfg.t_min - b && std::fabs(e.r - rp) < b) h.amb = true;
+    if (!(e.t > cfg.t_min && e.r <= rp)) continue;
+    double w = std::exp(-e.r * e.r / (2.0 * rp * rp)) * std::exp(-S.lambda_d * norm(e.q - qmin));
+    sw += w;
+    sq = sq + w * e.q;
+    sn = sn + w * S.N[i];
+  }
+  h.q = (1.0 / sw) * sq;
+  h.n = unit(sn);
+  if (dot(h.n, d) > 0) h.n = -1.0 * h.n;
+  h.cos_in = std::fabs(dot(d, h.n));
+  return h;
+}
+
+// ---------------------------------------------------------------------------
+// Launch directions: Fibonacci sphere with a 64-bit fixed-point golden angle.
+//   z_i = 1 - (2i+1)/N,  r_i = sqrt(1 - z_i^2),
+//   phi_i = 2 pi frac(i * G / 2^64),  G = round((2 - golden ratio) * 2^64).
+// ---------------------------------------------------------------------------
+const uint64_t kGolden64 = 0x61C8864680B583EBull;
+
+V3 fib_dir(int64_t i, int64_t n) {
+  double a = (2.0 * (double)i + 1.0) / (double)n;
+  double z = 1.0 - a;
+  double r = std::sqrt(std::max(0.0, a * (2.0 - a)));
+  uint64_t u = (uint64_t)i * kGolden64;
+  double phi = 2.0 * kPi * std::ldexp((double)u, -64);
+  return {r * std::cos(phi), r * std::sin(phi), z};
+}
+
+// ---------------------------------------------------------------------------
+// EM (readings; the paper leaves these to an external library).
+// ---------------------------------------------------------------------------
+typedef std::complex<double> cd;
+
+// ITU-R P.2040 complex relative permittivity eta = eps_r - j sigma / (2 pi f eps0)
+cd permittivity(double eps_r, double sigma, double f) {
+  return cd(eps_r, -sigma / (2.0 * kPi * f * kEps0));
+}
+
+// Fresnel reflection coefficient; pol 0 = TE (perpendicular), 1 = TM (parallel)
+cd fresnel(cd eta, double cos_t, int pol) {
+  double sin2 = 1.0 - cos_t * cos_t;
+  cd s = std::sqrt(eta - sin2);
+  if (pol == 0) return (cos_t - s) / (cos_t + s);
+  return (eta * cos_t - s) / (eta * cos_t + s);
+}
+
+cd dfresnel_deta(cd eta, double cos_t, int pol) {
+  double sin2 = 1.0 - cos_t * cos_t;
+  cd s = std::sqrt(eta - sin2);
+  if (pol == 0) {
+    cd den = cos_t + s;
+    return -cos_t / (s * den * den);
+  }
+  cd den = eta * cos_t + s;
+  return cos_t * (eta - 2.0 * sin2) / (s * den * den);
+}
+
+// ---------------------------------------------------------------------------
+// Simulation (Sec. II-B): LOS, launch, bounce loop, capture, dedup, validation,
+// refinement and field.
+// ---------------------------------------------------------------------------
+}  // namespace
+
+extern "C" {
+
+struct orc_params {
+  int32_t max_depth;   // K, maximum number of interactions
+  int32_t capture;     // 0 = RX sphere, 1 = visibility matrix
+  int32_t diffuse;     // diffuse scattering as the last interaction
+  int32_t pol;         // 0 TE, 1 TM
+  int32_t kappa;       // refinement retries
+  int32_t rep_tries;   // candidates tried per key, in ray order
+  int32_t validate;    // 0: stop after the trace (records only)
+  int32_t n_threads;   // 0: OpenMP default
+  int64_t n_rays;      // N of the Fibonacci launch
+  double r_rx;         // RX sphere radius
+  double t_min;        // minimum hit distance
+  double delta;        // ambiguity band; 0 disables ambiguity tracking
+  double t_a_deg;      // refinement angle threshold, degrees
+  double t_d;          // refinement plane-distance threshold, m
+  double freq;         // Hz
+};
+
+}  // extern "C"
+
+namespace {
+
+struct HitRec {
+  int64_t idx = -1;
+  int dps = -1;
+  double t = 0, cos_in = 0;
+  V3 q{0, 0, 0}, n{0, 0, 0};
+  V3 dout{0, 0, 0};  // direction of the specular continuation
+  bool amb = false;
+};
+
+struct Key {
+  uint64_t hi = 0, lo = 0;
+  bool operator<(const Key& o) const { return hi != o.hi ? hi < o.hi : lo < o.lo; }
+  bool operator==(const Key& o) const { return hi == o.hi && lo == o.lo; }
+};
+
+// 128-bit path key: hi = [j:8 @56][diffuse:1 @55][k:3 @52][...], lo = labels.
+// Specular: lo = l1 | l2<<16 | l3<<32 | l4<<48, hi[0:16] = l5.
+// Diffuse:  lo = prefix labels l1..l(k-1), hi[0:48] = voxel x | y<<16 | z<<32.
+Key make_key(int j, bool diffuse, int k, const int* labels, int n_labels, const int* voxel) {
+  Key K;
+  K.hi = ((uint64_t)(j & 0xFF) << 56) | ((uint64_t)(diffuse ? 1 : 0) << 55) |
+         ((uint64_t)(k & 7) << 52);
+  for (int m = 0; m < n_labels && m < 4; ++m) K.lo |= (uint64_t)(labels[m] & 0xFFFF) << (16 * m);
+  if (!diffuse && n_labels >= 5) K.hi |= (uint64_t)(labels[4] & 0xFFFF);
+  if (diffuse)
+    K.hi |= (uint64_t)(voxel[0] & 0xFFFF) | ((uint64_t)(voxel[1] & 0xFFFF) << 16) |
+            ((uint64_t)(voxel[2] & 0xFFFF) << 32);
+  return K;
+}
+
+struct Cand {
+  int64_t ray;
+  bool certain;
+};
+
+struct PathOut {
+  Key key;
+  int j = 0, type = 0, k = 0;  // type 0 specular / LOS, 1 diffuse
+  int64_t rep = -1;
+  V3 pts[5];
+  int mats[5] = {0, 0, 0, 0, 0};
+  double cosv[5] = {0, 0, 0, 0, 0};
+  double geo = 0, tau = 0, length = 0;
+  bool certain = true;
+};
+
+struct KeyOut {
+  Key key;
+  int j = 0, type = 0, k = 0;
+  int64_t n_cand = 0;
+  std::vector<int64_t> tried;
+  std::vector<int> tried_valid, tried_amb;
+  int64_t rep = -1;
+  bool valid = false, certain = true;
+  int path = -1;
+};
+
+struct Sim {
+  const Scene* S = nullptr;
+  orc_params p{};
+  V3 tx{0, 0, 0};
+  std::vector<V3> rx;
+  int n_seg = 0;
+  std::vector<int64_t> ray_ids;
+  std::vector<HitRec> rec;     // [n_ray][n_seg]
+  std::vector<int> excl;       // first ambiguous hit (1-based), n_seg+1 = none
+  std::vector<int> n_hits;
+  // visibility bits, computed for the DPS the traced rays reach
+  std::map<std::pair<int, int>, std::pair<bool, bool>> vis;  // (j, dps) -> (bit, amb)
+  std::vector<KeyOut> keys;
+  std::vector<PathOut> paths;
+  std::vector<std::pair<bool, bool>> los;  // per RX (clear, amb)
+  std::vector<double> power;
+  // potential producers of keys under ambiguity
+  std::map<std::pair<int, std::vector<int>>, int64_t> prefix_min;  // (e, labels 1..e-1)
+  std::map<Key, std::vector<int64_t>> uncertain_cand;
+  std::map<Key, std::vector<Cand>> cands;  // per key, in ray order
+  std::vector<int64_t> ray_pos;  // ray id -> row, or -1
+};
+
+struct Validation {
+  bool valid = false, amb = false;
+  PathOut path;
+};
+
+double rx_margin(const Scene& S) { return std::sqrt(3.0) / 2.0 * S.rho + S.rp; }
+
+// Visibility from RX j to the reception point of DPS D (Sec. II-B): cast from
+// the RX toward the point; visible when nothing is hit before the reception
+// point's voxel could begin (t < s - (sqrt(3)/2 rho + r_p)) or the first hit
+// belongs to D itself.
+std::pair<bool, bool> vis_cast(const Scene& S, V3 rxp, int D, const CastCfg& cfg) {
+  V3 dv = S.recv[D] - rxp;
+  double s = norm(dv);
+  double t_max = s - rx_margin(S);
+  if (t_max <= cfg.t_min) return {true, cfg.delta > 0 && t_max > cfg.t_min - cfg.delta};
+  Hit h = cast(S, rxp, (1.0 / s) * dv, -1, t_max, false, cfg);
+  bool bit = !h.hit || h.dps == D;
+  return {bit, h.amb};
+}
+
+Validation validate_diffuse(const Sim& sim, int64_t row, int k, int j, const CastCfg& cfg) {
+  const Scene& S = *sim.S;
+  Validation v;
+  const HitRec& hk = sim.rec[row * sim.n_seg + (k - 1)];
+  V3 u = sim.rx[j] - hk.q;
+  double rs = norm(u);
+  V3 w = (1.0 / rs) * u;
+  double cs = dot(hk.n, w);
+  if (cfg.delta > 0 && (std::fabs(cs) < 1e-5 || hk.cos_in < 1e-5)) v.amb = true;
+  if (cs <= 0.0) return v;
+  Hit h = cast(S, hk.q, w, hk.dps, rs, false, cfg);
+  if (h.amb) v.amb = true;
+  if (h.hit) return v;
+  v.valid = true;
+  PathOut& P = v.path;
+  P.type = 1;
+  P.k = k;
+  double ri = 0.0;
+  for (int m = 0; m < k; ++m) {
+    const HitRec& hm = sim.rec[row * sim.n_seg + m];
+    P.pts[m] = hm.q;
+    P.mats[m] = S.mat[hm.idx];
+    P.cosv[m] = hm.cos_in;
+    ri += hm.t;
+  }
+  double lam = kC0 / sim.p.freq;
+  P.geo = lam / (4.0 * kPi) * std::sqrt(S.rho * S.rho * hk.cos_in * cs / kPi) / (ri * rs);
+  P.length = ri + rs;
+  P.tau = P.length / kC0;
+  return v;
+}
+
+// Specular refinement (Sec. II-B-2).  Phase 1: the minimiser of the path
+// length of Eq. 1 over points on the infinite planes (q_m, n_m); each term is
+// the norm of an affine function, so the minimiser with every reflection on
+// the correct side is the image-method path, solved here exactly.  Phase 2:
+// cast from I_{m-1} toward I_m; the interaction is valid when the hit lies on
+// the key's surface with a normal within t_a and within t_d of the plane;
+// otherwise the plane is replaced by the hit's and the solve retried, at most
+// kappa times.  Finally the last leg I_k -> RX must be clear.
+Validation validate_specular(const Sim& sim, int64_t row, int k, int j, const int* labels,
+                             const CastCfg& cfg) {
+  const Scene& S = *sim.S;
+  Validation v;
+  V3 Pp[5], Pn[5];
+  for (int m = 0; m < k; ++m) {
+    const HitRec& hm = sim.rec[row * sim.n_seg + m];
+    Pp[m] = hm.q;
+    Pn[m] = hm.n;
+  }
+  const V3 tx = sim.tx, rxp = sim.rx[j];
+  const double cos_ta = std::cos(sim.p.t_a_deg * kPi / 180.0);
+  const double ta = sim.p.t_a_deg * kPi / 180.0;
+  for (int attempt = 0; attempt <= sim.p.kappa; ++attempt) {
+    V3 img[6];
+    img[0] = tx;
+    for (int m = 0; m < k; ++m) img[m + 1] = img[m] - 2.0 * dot(img[m] - Pp[m], Pn[m]) * Pn[m];
+    V3 I[7];
+    I[0] = tx;
+    I[k + 1] = rxp;
+    V3 tgt = rxp;
+    bool ok = true;
+    for (int m = k; m >= 1; --m) {
+      V3 dir = img[m] - tgt;
+      double den = dot(dir, Pn[m - 1]);
+      if (std::fabs(den) < 1e-300) {
+        ok = false;
+        break;
+      }
+      double u = dot(Pp[m - 1] - tgt, Pn[m - 1]) / den;
+      I[m] = tgt + u * dir;
+      tgt = I[m];
+    }
+    if (!ok) return v;
+    for (int m = 1; m <= k; ++m) {
+      double a = dot(I[m - 1] - I[m], Pn[m - 1]);
+      double b = dot(I[m + 1] - I[m], Pn[m - 1]);
+      if (cfg.delta > 0 && std::min(std::fabs(a), std::fabs(b)) < cfg.delta) v.amb = true;
+      if (!(a * b > 0.0)) return v;
+    }
+    // phase 2: validation casts
+    int prev_dps = -1;
+    int fail_m = -1;
+    Hit hv[5];
+    bool dead = false;
+    for (int m = 1; m <= k; ++m) {
+      V3 seg = I[m] - I[m - 1];
+      Hit h = cast(S, I[m - 1], unit(seg), prev_dps, kInf, true, cfg);
+      if (h.amb) v.amb = true;
+      if (!h.hit || S.surf[h.idx] != labels[m - 1]) {
+        dead = true;
+        break;
+      }
+      double c = std::min(1.0, std::fabs(dot(Pn[m - 1], h.n)));
+      double dist = std::fabs(dot(h.q - I[m], Pn[m - 1]));
+      if (cfg.delta > 0) {
+        if (std::fabs(std::acos(c) - ta) < 0.01 * ta) v.amb = true;
+        if (std::fabs(dist - sim.p.t_d) < 0.01 * sim.p.t_d) v.amb = true;
+      }
+      hv[m - 1] = h;
+      if (!(c >= cos_ta && dist <= sim.p.t_d)) {
+        fail_m = m;
+        break;
+      }
+      prev_dps = h.dps;
+    }
+    if (dead) return v;
+    if (fail_m > 0) {
+      if (attempt == sim.p.kappa) return v;
+      Pp[fail_m - 1] = hv[fail_m - 1].q;
+      Pn[fail_m - 1] = hv[fail_m - 1].n;
+      continue;
+    }
+    // final leg to the RX
+    V3 last = rxp - I[k];
+    double s = norm(last);
+    Hit hf = cast(S, I[k], (1.0 / s) * last, prev_dps, s, false, cfg);
+    if (hf.amb) v.amb = true;
+    if (hf.hit) return v;
+    v.valid = true;
+    PathOut& P = v.path;
+    P.type = 0;
+    P.k = k;
+    double len = 0.0;
+    for (int m = 0; m <= k; ++m) len += norm(I[m + 1] - I[m]);
+    for (int m = 1; m <= k; ++m) {
+      P.pts[m - 1] = I[m];
+      P.mats[m - 1] = S.mat[hv[m - 1].idx];
+      P.cosv[m - 1] = std::fabs(dot(Pn[m - 1], unit(I[m] - I[m - 1])));
+    }
+    double lam = kC0 / sim.p.freq;
+    P.length = len;
+    P.geo = lam / (4.0 * kPi * len);
+    P.tau = len / kC0;
+    return v;
+  }
+  return v;
+}
+
+void trace_ray(Sim& sim, int64_t row, const CastCfg& cfg) {
+  const Scene& S = *sim.S;
+  int64_t rid = sim.ray_ids[row];
+  V3 o = sim.tx, d = fib_dir(rid, sim.p.n_rays);
+  int skip = -1;
+  sim.excl[row] = sim.n_seg + 1;
+  sim.n_hits[row] = 0;
+  for (int k = 1; k <= sim.n_seg; ++k) {
+    Hit h = cast(S, o, d, skip, kInf, true, cfg);
+    HitRec& r = sim.rec[row * sim.n_seg + (k - 1)];
+    r.amb = h.amb;
+    if (h.amb && sim.excl[row] > k) sim.excl[row] = k;
+    if (!h.hit) break;
+    r.idx = h.idx;
+    r.dps = h.dps;
+    r.t = h.t;
+    r.q = h.q;
+    r.n = h.n;
+    r.cos_in = h.cos_in;
+    sim.n_hits[row] = k;
+    d = d - 2.0 * dot(d, h.n) * h.n;  // specular continuation
+    r.dout = d;
+    o = h.q;
+    skip = h.dps;
+  }
+}
+
+int diffuse_voxel(const Scene& S, V3 q, int* v, double delta, bool* amb) {
+  for (int k = 0; k < 3; ++k) {
+    double s = (comp(q, k) - (double)S.bmin_f[k]) / S.rho;
+    v[k] = (int)std::floor(s);
+    double frac = s - std::floor(s);
+    if (delta > 0 && std::min(frac, 1.0 - frac) * S.rho < delta) *amb = true;
+  }
+  return 0;
+}
+
+void run_sim(Sim& sim) {
+  const Scene& S = *sim.S;
+  CastCfg cfg;
+  cfg.t_min = sim.p.t_min;
+  cfg.delta = sim.p.delta;
+  const int64_t n = (int64_t)sim.ray_ids.size();
+  const int M = (int)sim.rx.size();
+  const bool sphere = sim.p.capture == 0;
+  sim.n_seg = sim.p.max_depth + (sphere ? 1 : 0);
+  sim.rec.assign(n * sim.n_seg, HitRec());
+  sim.excl.assign(n, 0);
+  sim.n_hits.assign(n, 0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t r = 0; r < n; ++r) trace_ray(sim, r, cfg);
+
+  // LOS (Sec. II-B): cast from the TX to every RX
+  sim.los.assign(M, {false, false});
+  for (int j = 0; j < M; ++j) {
+    V3 dv = sim.rx[j] - sim.tx;
+    double s = norm(dv);
+    Hit h = cast(S, sim.tx, (1.0 / s) * dv, -1, s, false, cfg);
+    sim.los[j] = {!h.hit, h.amb};
+  }
+  if (!sim.p.validate) return;
+
+  // visibility matrix entries for the DPS reached
+  if (!sphere) {
+    std::set<int> reached;
+    for (int64_t r = 0; r < n; ++r)
+      for (int k = 1; k <= std::min(sim.n_hits[r], sim.p.max_depth); ++k)
+        reached.insert(sim.rec[r * sim.n_seg + k - 1].dps);
+    std::vector<std::pair<int, int>> pairs;
+    for (int D : reached)
+      for (int j = 0; j < M; ++j) pairs.push_back({j, D});
+    std::vector<std::pair<bool, bool>> res(pairs.size());
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < (int64_t)pairs.size(); ++i)
+      res[i] = vis_cast(S, sim.rx[pairs[i].first], pairs[i].second, cfg);
+    for (size_t i = 0; i < pairs.size(); ++i) sim.vis[pairs[i]] = res[i];
+  }
+
+  // candidates, in ray order
+  std::map<Key, std::vector<Cand>>& cands = sim.cands;
+  std::map<Key, std::tuple<int, int, int>> kinfo;  // j, type, k
+  auto add_uncertain = [&](const Key& K, int64_t rid) { sim.uncertain_cand[K].push_back(rid); };
+  for (int64_t r = 0; r < n; ++r) {
+    const int64_t rid = sim.ray_ids[r];
+    const int e = sim.excl[r];
+    int labels[8];
+    for (int m = 0; m < sim.n_hits[r]; ++m) labels[m] = S.surf[sim.rec[r * sim.n_seg + m].idx];
+    if (e <= sim.n_seg) {
+      std::vector<int> pre(labels, labels + std::min(e - 1, sim.n_hits[r]));
+      auto key = std::make_pair(e, pre);
+      auto it = sim.prefix_min.find(key);
+      if (it == sim.prefix_min.end() || rid < it->second) sim.prefix_min[key] = rid;
+    }
+    if (sphere) {
+      // segment s starts at hit s (s >= 1) and ends at hit s+1 (or runs to infinity)
+      for (int s = 1; s <= std::min(sim.n_hits[r], sim.p.max_depth); ++s) {
+        const HitRec& hs = sim.rec[r * sim.n_seg + s - 1];
+        const HitRec& he = sim.rec[r * sim.n_seg + s];
+        const V3 dseg = hs.dout;
+        double t_end = (sim.n_hits[r] >= s + 1) ? he.t : kInf;
+        for (int j = 0; j < M; ++j) {
+          double ts = dot(sim.rx[j] - hs.q, dseg);
+          ts = std::min(std::max(ts, 0.0), t_end);
+          double dist = norm(hs.q + ts * dseg - sim.rx[j]);
+          bool band = cfg.delta > 0 && std::fabs(dist - sim.p.r_rx) < cfg.delta;
+          if (dist <= sim.p.r_rx || band) {
+            Key K = make_key(j, false, s, labels, s, nullptr);
+            bool certain = (s + 1 < e) && !band;
+            if (dist <= sim.p.r_rx) {
+              cands[K].push_back({rid, certain});
+              kinfo[K] = {j, 0, s};
+            }
+            if (!certain) add_uncertain(K, rid);
+          }
+        }
+      }
+    } else {
+      for (int k = 1; k <= std::min(sim.n_hits[r], sim.p.max_depth); ++k) {
+        const HitRec& hk = sim.rec[r * sim.n_seg + k - 1];
+        bool vamb = false;
+        int vx[3];
+        if (sim.p.diffuse) diffuse_voxel(S, hk.q, vx, cfg.delta, &vamb);
+        for (int j = 0; j < M; ++j) {
+          auto vb = sim.vis.at({j, hk.dps});
+          if (!vb.first && !vb.second) continue;
+          bool certain = (k < e) && !vb.second;
+          Key Ks = make_key(j, false, k, labels, k, nullptr);
+          if (vb.first) {
+            cands[Ks].push_back({rid, certain});
+            kinfo[Ks] = {j, 0, k};
+          }
+          if (!certain) add_uncertain(Ks, rid);
+          if (sim.p.diffuse) {
+            Key Kd = make_key(j, true, k, labels, k - 1, vx);
+            bool dcert = certain && !vamb;
+            if (vb.first) {
+              cands[Kd].push_back({rid, dcert});
+              kinfo[Kd] = {j, 1, k};
+            }
+            if (!dcert) {
+              // the voxel may be taken on either side of a face closer than delta
+              int alt[3][2], na[3];
+              for (int a = 0; a < 3; ++a) {
+                double s = (comp(hk.q, a) - (double)S.bmin_f[a]) / S.rho;
+                double frac = s - std::floor(s);
+                na[a] = 1;
+                alt[a][0] = vx[a];
+                if (cfg.delta > 0 && frac * S.rho < cfg.delta) alt[a][na[a]++] = vx[a] - 1;
+                else if (cfg.delta > 0 && (1.0 - frac) * S.rho < cfg.delta) alt[a][na[a]++] = vx[a] + 1;
+              }
+              for (int a0 = 0; a0 < na[0]; ++a0)
+                for (int a1 = 0; a1 < na[1]; ++a1)
+                  for (int a2 = 0; a2 < na[2]; ++a2) {
+                    int vv[3] = {alt[0][a0], alt[1][a1], alt[2][a2]};
+                    add_uncertain(make_key(j, true, k, labels, k - 1, vv), rid);
+                  }
+            }
+          }
+        }
+      }
+    }
+  }
+
+  // per key: try the first rep_tries candidates in ray order
+  std::vector<Key> klist;
+  for (auto& kv : cands) {
+    std::sort(kv.second.begin(), kv.second.end(),
+              [](const Cand& a, const Cand& b) { return a.ray < b.ray; });
+    klist.push_back(kv.first);
+  }
+  sim.keys.assign(klist.size(), KeyOut());
+  std::vector<Validation> vout(klist.size());
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t qi = 0; qi < (int64_t)klist.size(); ++qi) {
+    const Key& K = klist[qi];
+    auto& cl = cands.at(K);
+    KeyOut& ko = sim.keys[qi];
+    ko.key = K;
+    std::tie(ko.j, ko.type, ko.k) = kinfo.at(K);
+    ko.n_cand = (int64_t)cl.size();
+    int labels[5] = {0, 0, 0, 0, 0};
+    for (int m = 0; m < 4; ++m) labels[m] = (int)((K.lo >> (16 * m)) & 0xFFFF);
+    labels[4] = (int)(K.hi & 0xFFFF);
+    int ntry = std::min<int64_t>(cl.size(), sim.p.rep_tries);
+    for (int c = 0; c < ntry; ++c) {
+      int64_t rid = cl[c].ray;
+      int64_t row = sim.ray_pos[rid];
+      Validation v = ko.type == 1 ? validate_diffuse(sim, row, ko.k, ko.j, cfg)
+                                  : validate_specular(sim, row, ko.k, ko.j, labels, cfg);
+      ko.tried.push_back(rid);
+      ko.tried_valid.push_back(v.valid);
+      ko.tried_amb.push_back(v.amb || !cl[c].certain);
+      if (v.valid) {
+        ko.valid = true;
+        ko.rep = rid;
+        vout[qi] = v;
+        break;
+      }
+    }
+  }
+  // a key's outcome is "tried-certain" when every candidate tried for it is a
+  // certain candidate with an unambiguous validation
+  for (size_t qi = 0; qi < klist.size(); ++qi) {
+    KeyOut& ko = sim.keys[qi];
+    bool certain = true;
+    for (int a : ko.tried_amb)
+      if (a) certain = false;
+    ko.certain = certain;
+    if (ko.valid) {
+      PathOut P = vout[qi].path;
+      P.key = ko.key;
+      P.j = ko.j;
+      P.rep = ko.rep;
+      P.certain = certain;
+      ko.path = (int)sim.paths.size();
+      sim.paths.push_back(P);
+    }
+  }
+  // LOS paths
+  double lam = kC0 / sim.p.freq;
+  for (int j = 0; j < M; ++j) {
+    if (!sim.los[j].first) continue;
+    PathOut P;
+    P.key = make_key(j, false, 0, nullptr, 0, nullptr);
+    P.j = j;
+    P.type = 0;
+    P.k = 0;
+    P.rep = -1;
+    double d = norm(sim.rx[j] - sim.tx);
+    P.length = d;
+    P.geo = lam / (4.0 * kPi * d);
+    P.tau = d / kC0;
+    P.certain = !sim.los[j].second;
+    sim.paths.push_back(P);
+  }
+}
+
+cd path_coefficient(const PathOut& P, const double* eps, const double* sig, const double* sca,
+                    double freq, int pol) {
+  cd a(P.geo, 0.0);
+  for (int m = 0; m < P.k; ++m) {
+    int l = P.mats[m];
+    cd G = fresnel(permittivity(eps[l], sig[l], freq), P.cosv[m], pol);
+    bool last_diffuse = P.type == 1 && m == P.k - 1;
+    double f = last_diffuse ? sca[l] : std::sqrt(std::max(0.0, 1.0 - sca[l] * sca[l]));
+    a *= f * G;
+  }
+  return a;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C API (ctypes)
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void* orc_scene_create(const float* pos, const float* nrm, const uint16_t* surf,
+                       const uint8_t* mat, int64_t n, double rho, double r_p, double lambda_d,
+                       double grid_cell, double band_cap) {
+  return build_scene(pos, nrm, surf, mat, n, rho, r_p, lambda_d, grid_cell, band_cap);
+}
+
+void orc_scene_destroy(void* s) { delete (Scene*)s; }
+
+int64_t orc_scene_n_dps(void* s) { return (int64_t)((Scene*)s)->dps_pts.size(); }
+
+void orc_scene_bmin(void* s, float* out) {
+  for (int k = 0; k < 3; ++k) out[k] = ((Scene*)s)->bmin_f[k];
+}
+
+void orc_scene_dps(void* s, int32_t* vox, int32_t* count, double* recv) {
+  Scene* S = (Scene*)s;
+  for (size_t d = 0; d < S->dps_pts.size(); ++d) {
+    for (int k = 0; k < 3; ++k) vox[3 * d + k] = S->dps_vox[d][k];
+    count[d] = (int32_t)S->dps_pts[d].size();
+    recv[3 * d] = S->recv[d].x;
+    recv[3 * d + 1] = S->recv[d].y;
+    recv[3 * d + 2] = S->recv[d].z;
+  }
+}
+
+void orc_scene_point_dps(void* s, int32_t* out) {
+  Scene* S = (Scene*)s;
+  for (int64_t i = 0; i < S->n; ++i) out[i] = S->dps_of[i];
+}
+
+// One cast.  out: t, q[3], n[3], cos_in.  Returns 1 on a hit.
+int orc_cast(void* s, const double* o, const double* d, int32_t skip_dps, double t_min,
+             double t_max, double delta, int weighted, double* out, int64_t* idx, int32_t* dps,
+             int32_t* amb) {
+  Scene* S = (Scene*)s;
+  CastCfg cfg;
+  cfg.t_min = t_min;
+  cfg.delta = delta;
+  V3 dv = unit({d[0], d[1], d[2]});
+  Hit h = cast(*S, {o[0], o[1], o[2]}, dv, skip_dps, t_max, weighted != 0, cfg);
+  out[0] = h.t;
+  out[1] = h.q.x; out[2] = h.q.y; out[3] = h.q.z;
+  out[4] = h.n.x; out[5] = h.n.y; out[6] = h.n.z;
+  out[7] = h.cos_in;
+  *idx = h.idx;
+  *dps = h.dps;
+  *amb = h.amb ? 1 : 0;
+  return h.hit ? 1 : 0;
+}
+
+void orc_fib_dirs(int64_t n, const int64_t* ids, int64_t m, double* out) {
+  for (int64_t i = 0; i < m; ++i) {
+    V3 d = fib_dir(ids[i], n);
+    out[3 * i] = d.x;
+    out[3 * i + 1] = d.y;
+    out[3 * i + 2] = d.z;
+  }
+}
+
+void* orc_sim_run(void* s, const double* tx, const double* rx, int n_rx, const orc_params* p,
+                  const int64_t* ray_ids, int64_t n_ids) {
+  Sim* sim = new Sim();
+  sim->S = (Scene*)s;
+  sim->p = *p;
+#ifdef _OPENMP
+  if (p->n_threads > 0) omp_set_num_threads(p->n_threads);
+#endif
+  sim->tx = {tx[0], tx[1], tx[2]};
+  for (int j = 0; j < n_rx; ++j) sim->rx.push_back({rx[3 * j], rx[3 * j + 1], rx[3 * j + 2]});
+  sim->ray_ids.assign(ray_ids, ray_ids + n_ids);
+  sim->ray_pos.assign(p->n_rays, -1);
+  for (int64_t i = 0; i < n_ids; ++i) sim->ray_pos[ray_ids[i]] = i;
+  run_sim(*sim);
+  return sim;
+}
+
+void orc_sim_destroy(void* s) { delete (Sim*)s; }
+
+int orc_sim_n_seg(void* s) { return ((Sim*)s)->n_seg; }
+
+// per-ray hit records [n_ids][n_seg]
+void orc_sim_hits(void* s, int64_t* idx, int32_t* dps, double* t, double* q, double* nrm,
+                  double* cos_in, int32_t* amb, int32_t* excl, int32_t* n_hits) {
+  Sim* sim = (Sim*)s;
+  int64_t n = (int64_t)sim->ray_ids.size();
+  for (int64_t r = 0; r < n; ++r) {
+    excl[r] = sim->excl[r];
+    n_hits[r] = sim->n_hits[r];
+    for (int k = 0; k < sim->n_seg; ++k) {
+      const HitRec& h = sim->rec[r * sim->n_seg + k];
+      int64_t o = r * sim->n_seg + k;
+      idx[o] = h.idx;
+      dps[o] = h.dps;
+      t[o] = h.t;
+      q[3 * o] = h.q.x; q[3 * o + 1] = h.q.y; q[3 * o + 2] = h.q.z;
+      nrm[3 * o] = h.n.x; nrm[3 * o + 1] = h.n.y; nrm[3 * o + 2] = h.n.z;
+      cos_in[o] = h.cos_in;
+      amb[o] = h.amb;
+    }
+  }
+}
+
+void orc_sim_los(void* s, int32_t* clear, int32_t* amb) {
+  Sim* sim = (Sim*)s;
+  for (size_t j = 0; j < sim->los.size(); ++j) {
+    clear[j] = sim->los[j].first;
+    amb[j] = sim->los[j].second;
+  }
+}
+
+int64_t orc_sim_n_vis(void* s) { return (int64_t)((Sim*)s)->vis.size(); }
+
+void orc_sim_vis(void* s, int32_t* j, int32_t* dps, int32_t* bit, int32_t* amb) {
+  Sim* sim = (Sim*)s;
+  int64_t i = 0;
+  for (auto& kv : sim->vis) {
+    j[i] = kv.first.first;
+    dps[i] = kv.first.second;
+    bit[i] = kv.second.first;
+    amb[i] = kv.second.second;
+    ++i;
+  }
+}
+
+// Visibility bits for explicit (rx, dps) pairs, without a simulation.
+void orc_vis_pairs(void* s, const double* rx, const int32_t* j, const int32_t* dps, int64_t n,
+                   double t_min, double delta, int32_t* bit, int32_t* amb) {
+  Scene* S = (Scene*)s;
+  CastCfg cfg;
+  cfg.t_min = t_min;
+  cfg.delta = delta;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    V3 r{rx[3 * j[i]], rx[3 * j[i] + 1], rx[3 * j[i] + 2]};
+    auto v = vis_cast(*S, r, dps[i], cfg);
+    bit[i] = v.first;
+    amb[i] = v.second;
+  }
+}
+
+int64_t orc_sim_n_keys(void* s) { return (int64_t)((Sim*)s)->keys.size(); }
+
+void orc_sim_keys(void* s, uint64_t* hi, uint64_t* lo, int32_t* n_tried, int64_t* n_cand,
+                  int64_t* rep, int32_t* valid, int32_t* certain, int32_t* path) {
+  Sim* sim = (Sim*)s;
+  for (size_t i = 0; i < sim->keys.size(); ++i) {
+    const KeyOut& k = sim->keys[i];
+    hi[i] = k.key.hi;
+    lo[i] = k.key.lo;
+    n_tried[i] = (int32_t)k.tried.size();
+    n_cand[i] = k.n_cand;
+    rep[i] = k.rep;
+    valid[i] = k.valid;
+    certain[i] = k.certain;
+    path[i] = k.path;
+  }
+}
+
+int64_t orc_sim_n_paths(void* s) { return (int64_t)((Sim*)s)->paths.size(); }
+
+void orc_sim_paths(void* s, uint64_t* hi, uint64_t* lo, int32_t* j, int32_t* type, int32_t* k,
+                   int64_t* rep, double* pts, int32_t* mats, double* cosv, double* geo,
+                   double* tau, double* length, int32_t* certain) {
+  Sim* sim = (Sim*)s;
+  for (size_t i = 0; i < sim->paths.size(); ++i) {
+    const PathOut& P = sim->paths[i];
+    hi[i] = P.key.hi;
+    lo[i] = P.key.lo;
+    j[i] = P.j;
+    type[i] = P.type;
+    k[i] = P.k;
+    rep[i] = P.rep;
+    for (int m = 0; m < 5; ++m) {
+      pts[15 * i + 3 * m] = P.pts[m].x;
+      pts[15 * i + 3 * m + 1] = P.pts[m].y;
+      pts[15 * i + 3 * m + 2] = P.pts[m].z;
+      mats[5 * i + m] = P.mats[m];
+      cosv[5 * i + m] = P.cosv[m];
+    }
+    geo[i] = P.geo;
+    tau[i] = P.tau;
+    length[i] = P.length;
+    certain[i] = P.certain;
+  }
+}
+
+// Candidate status of ray `rid` for key (hi, lo):
+//   0 certainly not a candidate, 1 certainly a candidate, 2 uncertain (the ray
+//   could produce the key under a decision the oracle marks ambiguous: a
+//   visibility bit, a voxel face, a sphere boundary, or any hit from the
+//   ray's first ambiguous hit on, given a matching label prefix).
+int orc_sim_cand_status(void* s, uint64_t hi, uint64_t lo, int64_t rid) {
+  Sim* sim = (Sim*)s;
+  Key K{hi, lo};
+  auto ct = sim->cands.find(K);
+  if (ct != sim->cands.end())
+    for (const Cand& c : ct->second)
+      if (c.ray == rid) return c.certain ? 1 : 2;
+  auto it = sim->uncertain_cand.find(K);
+  if (it != sim->uncertain_cand.end())
+    for (int64_t r : it->second)
+      if (r == rid) return 2;
+  if (rid < 0 || rid >= (int64_t)sim->ray_pos.size()) return 0;
+  int64_t row = sim->ray_pos[rid];
+  if (row < 0) return 0;
+  int e = sim->excl[row];
+  int k = (int)((hi >> 52) & 7);
+  int type = (int)((hi >> 55) & 1);
+  int nlab = type == 1 ? k - 1 : k;
+  int emax = sim->p.capture == 0 ? k + 1 : k;
+  if (e > emax) return 0;
+  int labels[5];
+  for (int m = 0; m < 4; ++m) labels[m] = (int)((lo >> (16 * m)) & 0xFFFF);
+  labels[4] = (int)(hi & 0xFFFF);
+  for (int m = 0; m < std::min(e - 1, nlab); ++m) {
+    if (m >= sim->n_hits[row]) return 0;
+    if (sim->S->surf[sim->rec[row * sim->n_seg + m].idx] != labels[m]) return 0;
+  }
+  return 2;
+}
+
+int64_t orc_sim_n_tried(void* s) {
+  Sim* sim = (Sim*)s;
+  int64_t n = 0;
+  for (const KeyOut& k : sim->keys) n += (int64_t)k.tried.size();
+  return n;
+}
+
+// Flattened per-key lists of the candidates tried, in key order.
+void orc_sim_tried(void* s, int64_t* ray, int32_t* valid, int32_t* amb) {
+  Sim* sim = (Sim*)s;
+  int64_t o = 0;
+  for (const KeyOut& k : sim->keys)
+    for (size_t i = 0; i < k.tried.size(); ++i, ++o) {
+      ray[o] = k.tried[i];
+      valid[o] = k.tried_valid[i];
+      amb[o] = k.tried_amb[i];
+    }
+}
+
+// Complex path coefficients (phase split: the propagation phase exp(-j 2 pi f tau)
+// is not included) and per-RX received power P_j = sum |a|^2.
+void orc_sim_field(void* s, const double* eps, const double* sig, const double* sca, double* a_re,
+                   double* a_im, double* power, int n_rx) {
+  Sim* sim = (Sim*)s;
+  for (int j = 0; j < n_rx; ++j) power[j] = 0.0;
+  for (size_t i = 0; i < sim->paths.size(); ++i) {
+    cd a = path_coefficient(sim->paths[i], eps, sig, sca, sim->p.freq, sim->p.pol);
+    a_re[i] = a.real();
+    a_im[i] = a.imag();
+    power[sim->paths[i].j] += std::norm(a);
+  }
+}
+
+// Analytic gradient of L with respect to (eps_r, sigma, S) per label, given
+// dL/dP_j.  d|a|^2/dx = 2 Re(conj(a) da/dx); da/deta_l sums over the
+// interactions with label l; deta/deps_r = 1, deta/dsigma = -j/(2 pi f eps0),
+// dR/dS = -S/R for a specular reflection, and the diffuse factor is S itself.
+void orc_sim_backward(void* s, const double* eps, const double* sig, const double* sca,
+                      const double* dL_dP, double* g_eps, double* g_sig, double* g_sca,
+                      int n_labels) {
+  Sim* sim = (Sim*)s;
+  const double f = sim->p.freq;
+  const int pol = sim->p.pol;
+  for (int l = 0; l < n_labels; ++l) g_eps[l] = g_sig[l] = g_sca[l] = 0.0;
+  const cd deta_dsig(0.0, -1.0 / (2.0 * kPi * f * kEps0));
+  for (const PathOut& P : sim->paths) {
+    cd fac[5], dfac_deta[5];
+    double dfac_dS[5] = {0, 0, 0, 0, 0};
+    cd dfdS[5];
+    for (int m = 0; m < P.k; ++m) {
+      int l = P.mats[m];
+      cd eta = permittivity(eps[l], sig[l], f);
+      cd G = fresnel(eta, P.cosv[m], pol);
+      cd dG = dfresnel_deta(eta, P.cosv[m], pol);
+      bool last_diffuse = P.type == 1 && m == P.k - 1;
+      double R = std::sqrt(std::max(0.0, 1.0 - sca[l] * sca[l]));
+      double c = last_diffuse ? sca[l] : R;
+      fac[m] = c * G;
+      dfac_deta[m] = c * dG;
+      dfdS[m] = last_diffuse ? G : (-sca[l] / R) * G;
+      (void)dfac_dS;
+    }
+    cd a(P.geo, 0.0);
+    for (int m = 0; m < P.k; ++m) a *= fac[m];
+    for (int m = 0; m < P.k; ++m) {
+      cd others(P.geo, 0.0);
+      for (int q = 0; q < P.k; ++q)
+        if (q != m) others *= fac[q];
+      cd da_deta = others * dfac_deta[m];
+      cd da_dS = others * dfdS[m];
+      double w = dL_dP[P.j] * 2.0;
+      int l = P.mats[m];
+      g_eps[l] += w * (std::conj(a) * da_deta).real();
+      g_sig[l] += w * (std::conj(a) * da_deta * deta_dsig).real();
+      g_sca[l] += w * (std::conj(a) * da_dS).real();
+    }
+  }
+}
+
+// Standalone EM helpers for closed-form pins.
+void orc_fresnel(double eps_r, double sigma, double freq, double cos_t, int pol, double* re,
+                 double* im) {
+  cd G = fresnel(permittivity(eps_r, sigma, freq), cos_t, pol);
+  *re = G.real();
+  *im = G.imag();
+}
+
+void orc_dfresnel(double eta_re, double eta_im, double cos_t, int pol, double* re, double* im) {
+  cd G = dfresnel_deta(cd(eta_re, eta_im), cos_t, pol);
+  *re = G.real();
+  *im = G.imag();
+}
+
+void orc_fresnel_eta(double eta_re, double eta_im, double cos_t, int pol, double* re, double* im) {
+  cd G = fresnel(cd(eta_re, eta_im), cos_t, pol);
+  *re = G.real();
+  *im = G.imag();
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+}  // extern "C"

@@ -1,0 +1,322 @@
+"""Pins for the oracle's path computation (Sec. II-B): specular refinement
+against the textbook image-source enumeration of a rectangular room and
+against a library minimisation of Eq. 1, dedup invariance, visibility and
+diffuse validation, and the adjoint against FP64 finite differences.  CPU only."""
+import itertools
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+import oracle
+from paper_2507_04021_gb300 import inputs
+
+C0 = 299792458.0
+ROOM = (5.0, 4.0, 3.0)
+
+
+def dense_room(spacing=0.04):
+    """Noise-free shoebox with a square lattice of discs on each face (r_p = spacing)."""
+    pts, nrm, surf = [], [], []
+    fid = 0
+    for axis in range(3):
+        u, v = [a for a in range(3) if a != axis]
+        nu, nv = int(round(ROOM[u] / spacing)), int(round(ROOM[v] / spacing))
+        gu = (np.arange(nu) + 0.5) * spacing
+        gv = (np.arange(nv) + 0.5) * spacing
+        U, V = np.meshgrid(gu, gv, indexing="ij")
+        for off, sgn in ((0.0, 1.0), (ROOM[axis], -1.0)):
+            p = np.zeros((U.size, 3))
+            p[:, axis] = off
+            p[:, u] = U.ravel()
+            p[:, v] = V.ravel()
+            n = np.zeros_like(p)
+            n[:, axis] = sgn
+            pts.append(p); nrm.append(n); surf.append(np.full(U.size, fid))
+            fid += 1
+    pos = np.concatenate(pts).astype(np.float32)
+    return pos, np.concatenate(nrm).astype(np.float32), np.concatenate(surf).astype(np.uint16)
+
+
+def image_source_paths(tx, rx, max_order=2):
+    """Textbook image sources of a rectangular room: for a wall sequence, mirror
+    the source through each wall in turn; the path length is |image - rx|.
+    Returns {wall sequence: (length, reflection points)} for valid paths."""
+    walls = [(0, 0.0), (0, ROOM[0]), (1, 0.0), (1, ROOM[1]), (2, 0.0), (2, ROOM[2])]
+    out = {}
+    for order in range(1, max_order + 1):
+        for seq in itertools.product(range(6), repeat=order):
+            if any(seq[i] == seq[i + 1] for i in range(order - 1)):
+                continue
+            imgs = [np.array(tx, float)]
+            for w in seq:
+                a, off = walls[w]
+                im = imgs[-1].copy()
+                im[a] = 2 * off - im[a]
+                imgs.append(im)
+            # back-trace from rx
+            tgt = np.array(rx, float)
+            pts = [None] * order
+            ok = True
+            for m in range(order - 1, -1, -1):
+                a, off = walls[seq[m]]
+                src = imgs[m + 1]
+                s = (off - tgt[a]) / (src[a] - tgt[a])
+                if not (0 < s < 1):
+                    ok = False
+                    break
+                p = tgt + s * (src - tgt)
+                if np.any(p < -1e-12) or np.any(p > np.array(ROOM) + 1e-12):
+                    ok = False
+                    break
+                pts[m] = p
+                tgt = p
+            if ok:
+                out[tuple(seq)] = (float(np.linalg.norm(imgs[-1] - np.array(rx, float))), pts)
+    return out
+
+
+def _decode_labels(hi, lo, k):
+    lab = [int((int(lo) >> (16 * m)) & 0xFFFF) for m in range(4)] + [int(int(hi) & 0xFFFF)]
+    return tuple(lab[:k])
+
+
+@pytest.fixture(scope="module")
+def shoebox():
+    pos, nrm, surf = dense_room()
+    mat = np.zeros(pos.shape[0], np.uint8)
+    mat[surf == 4] = 1
+    sc = oracle.OracleScene(pos, nrm, surf, mat, r_p=0.04, grid_cell=0.25)
+    tx = np.array([1.0, 1.0, 1.5], np.float32)
+    rx = np.array([[4.0, 3.0, 1.2]], np.float32)
+    p = oracle.SimParams(max_depth=2, capture=1, diffuse=0, n_rays=20000, rep_tries=8)
+    sim = oracle.OracleSim(sc, tx, rx, p)
+    return sc, sim, tx, rx
+
+
+def _edge_distance(pt, axis):
+    d = []
+    for a in range(3):
+        if a == axis:
+            continue
+        d += [pt[a], ROOM[a] - pt[a]]
+    return min(d)
+
+
+def test_shoebox_image_sources(shoebox):
+    """Valid refined specular keys of order <= 2 = the image-source enumeration,
+    with identical delays."""
+    sc, sim, tx, rx = shoebox
+    expect = image_source_paths(tx.astype(float), rx[0].astype(float), 2)
+    walls_axis = [0, 0, 1, 1, 2, 2]
+    P = sim.paths()
+    got = {}
+    for i in range(len(P["hi"])):
+        if P["k"][i] == 0:
+            continue
+        got[_decode_labels(P["hi"][i], P["lo"][i], P["k"][i])] = i
+    # every image-source path away from face edges is found
+    for seq, (length, pts) in expect.items():
+        far = all(_edge_distance(p, walls_axis[w]) > 0.1 for p, w in zip(pts, seq))
+        if far:
+            assert seq in got, seq
+    for seq, i in got.items():
+        assert seq in expect, seq
+        length, pts = expect[seq]
+        assert P["tau"][i] * C0 == pytest.approx(length, rel=1e-12)
+        for m, p in enumerate(pts):
+            assert np.allclose(P["pts"][i, m], p, atol=1e-9)
+    assert len(got) >= 20 and len(got) <= len(expect)
+
+
+def test_refined_points_minimise_eq1(shoebox):
+    """Eq. 1 minimised with a library optimiser over points on the same planes
+    agrees with the refined interaction points."""
+    sc, sim, tx, rx = shoebox
+    walls = [(0, 0.0), (0, ROOM[0]), (1, 0.0), (1, ROOM[1]), (2, 0.0), (2, ROOM[2])]
+    P = sim.paths()
+    checked = 0
+    for i in range(len(P["hi"])):
+        k = int(P["k"][i])
+        if k == 0:
+            continue
+        seq = _decode_labels(P["hi"][i], P["lo"][i], k)
+
+        def unpack(x):
+            pts = []
+            for m, w in enumerate(seq):
+                a, off = walls[w]
+                p = np.zeros(3)
+                p[a] = off
+                others = [b for b in range(3) if b != a]
+                p[others[0]], p[others[1]] = x[2 * m], x[2 * m + 1]
+                pts.append(p)
+            return pts
+
+        def f_d(x):
+            chain = [tx.astype(float)] + unpack(x) + [rx[0].astype(float)]
+            return sum(np.linalg.norm(chain[j + 1] - chain[j]) for j in range(len(chain) - 1))
+
+        x0 = np.full(2 * k, 1.0)
+        res = minimize(f_d, x0, method="BFGS", options={"gtol": 1e-12, "maxiter": 2000})
+        opt = unpack(res.x)
+        for m in range(k):
+            assert np.allclose(opt[m], P["pts"][i, m], atol=1e-5)
+        assert res.fun == pytest.approx(P["tau"][i] * C0, rel=1e-9)
+        checked += 1
+    assert checked >= 20
+
+
+def test_dedup_independent_of_processing_order(shoebox):
+    sc, sim, tx, rx = shoebox
+    p = sim.params
+    ids = np.random.default_rng(5).permutation(p.n_rays)
+    sim2 = oracle.OracleSim(sc, tx, rx, p, ray_ids=ids)
+    k1, k2 = sim.keys(), sim2.keys()
+    assert np.array_equal(k1["hi"], k2["hi"]) and np.array_equal(k1["lo"], k2["lo"])
+    assert np.array_equal(k1["rep"], k2["rep"])
+    assert np.array_equal(k1["valid"], k2["valid"])
+
+
+def test_diffuse_in_convex_room_always_valid(shoebox):
+    """In an empty convex room every diffuse candidate sees the RX in front of
+    its wall and unobstructed, so every diffuse key validates with its first
+    (lowest ray id) candidate."""
+    sc, _, tx, rx = shoebox
+    p = oracle.SimParams(max_depth=2, capture=1, diffuse=1, n_rays=2000, rep_tries=8)
+    sim = oracle.OracleSim(sc, tx, rx, p)
+    K = sim.keys()
+    H = sim.hits()
+    ray, _, _ = sim.tried()
+    first = np.concatenate([[0], np.cumsum(K["n_tried"])])[:-1]
+    diff = ((K["hi"] >> np.uint64(55)) & np.uint64(1)).astype(bool)
+    kk = ((K["hi"] >> np.uint64(52)) & np.uint64(7)).astype(int)
+    # scatter points near a room edge sit in DPS mixing two walls; leave them out
+    q = H["q"][ray[first], kk - 1]
+    lo = np.minimum(q, np.array(ROOM) - q)
+    near_edges = (lo < 0.1).sum(axis=1) >= 2
+    sel = diff & ~near_edges
+    assert sel.sum() > 100
+    assert K["valid"][sel].all()
+    assert (K["n_tried"][sel] == 1).all()
+
+
+def _plate(center, normal, half, spacing, surf_id):
+    normal = np.asarray(normal, float)
+    a = int(np.argmax(np.abs(normal)))
+    u, v = [b for b in range(3) if b != a]
+    g = np.arange(-half, half + 1e-9, spacing)
+    U, V = np.meshgrid(g, g, indexing="ij")
+    p = np.zeros((U.size, 3))
+    p[:, a] = center[a]
+    p[:, u] = center[u] + U.ravel()
+    p[:, v] = center[v] + V.ravel()
+    n = np.tile(normal, (U.size, 1))
+    return p, n, np.full(U.size, surf_id)
+
+
+def test_visibility_and_los_occlusion():
+    """A plate between RX and a wall patch hides the patch's DPS from the RX
+    and blocks LOS; without the plate both are clear."""
+    wall = _plate([0.0, 0.0, 0.0], [1, 0, 0], 0.5, 0.02, 0)
+    plate = _plate([1.0, 0.0, 0.0], [1, 0, 0], 0.2, 0.02, 1)
+    rx = np.array([[2.0, 0.0, 0.0]])
+    for with_plate in (False, True):
+        parts = [wall] + ([plate] if with_plate else [])
+        pos = np.concatenate([p[0] for p in parts]).astype(np.float32)
+        nrm = np.concatenate([p[1] for p in parts]).astype(np.float32)
+        surf = np.concatenate([p[2] for p in parts]).astype(np.uint16)
+        sc = oracle.OracleScene(pos, nrm, surf, np.zeros(pos.shape[0], np.uint8), r_p=0.02)
+        vox, cnt, recv = sc.dps()
+        # DPS on the wall nearest to the x axis
+        wall_dps = [d for d in range(len(cnt)) if abs(recv[d, 0]) < 1e-6]
+        near = min(wall_dps, key=lambda d: np.hypot(recv[d, 1], recv[d, 2]))
+        far = max(wall_dps, key=lambda d: np.hypot(recv[d, 1], recv[d, 2]))
+        bit, amb = sc.vis_pairs(rx, [0, 0], [near, far])
+        assert bit[0] == (not with_plate)
+        assert bit[1]  # the plate does not cover the wall's corner
+        h = sc.cast(rx[0], [-1.0, 0.0, 0.0], t_max=1.5, weighted=False)
+        assert h["hit"] == with_plate
+
+
+def test_adjoint_matches_central_differences(office):
+    """Analytic dP_j / d(eps_r, sigma, S)_l (one-hot dL/dP) and the gradient of
+    the per-RX dB-gain MSE against FP64 central differences of the oracle's
+    own forward, on an office sample with diffuse paths."""
+    sc = oracle.OracleScene(office.pos, office.nrm, office.surf, office.mat, r_p=0.015,
+                            grid_cell=0.1)
+    p = oracle.SimParams(max_depth=3, capture=1, diffuse=1, n_rays=1_000_000, rep_tries=4)
+    sim = oracle.OracleSim(sc, office.tx, office.rx, p, ray_ids=np.arange(0, 1_000_000, 2000))
+    base = [office.eps_r.astype(float), office.sigma.astype(float), office.scat.astype(float)]
+    M = office.rx.shape[0]
+    _, P0 = sim.field(*base)
+    checked = 0
+    for j in (0, 5, 11):
+        dL = np.zeros(M)
+        dL[j] = 1.0
+        grads = sim.backward(*base, dL)
+        for which in range(3):
+            for l in range(len(base[0])):
+                x = base[which][l]
+                h = 1e-4 * x
+                up = [b.copy() for b in base]
+                dn = [b.copy() for b in base]
+                up[which][l] += h
+                dn[which][l] -= h
+                fd = (sim.field(*up)[1][j] - sim.field(*dn)[1][j]) / (2 * h)
+                if abs(fd) * x < 1e-7 * P0[j]:
+                    continue  # below the resolution of the difference
+                assert grads[which][l] == pytest.approx(fd, rel=1e-3)
+                checked += 1
+    assert checked >= 30
+    # the configured loss: MSE of per-RX path gain in dB
+    target = np.linspace(-75, -65, M)
+    G0 = 10 * np.log10(P0)
+    dL_dP = 2 * (G0 - target) / M * 10 / (P0 * np.log(10))
+    ge, gs, gc = sim.backward(*base, dL_dP)
+
+    def loss(b):
+        return np.mean((10 * np.log10(sim.field(*b)[1]) - target) ** 2)
+
+    for which, g in ((0, ge), (2, gc)):
+        for l in range(len(base[0])):
+            h = 1e-5 * base[which][l]
+            up = [b.copy() for b in base]
+            dn = [b.copy() for b in base]
+            up[which][l] += h
+            dn[which][l] -= h
+            fd = (loss(up) - loss(dn)) / (2 * h)
+            assert g[l] == pytest.approx(fd, rel=1e-3, abs=1e-6)
+
+
+def test_single_wall_amplitude_snell_form(shoebox):
+    """First-order path: a = lambda/(4 pi d) * R * Gamma_TE(theta), with Gamma
+    from the Snell-law form and theta from the image-source geometry (S = 0,
+    so R = 1)."""
+    import cmath
+    sc, sim, tx, rx = shoebox
+    eps = np.array([5.3, 3.0])
+    sig = np.array([0.03, 0.01])
+    a, _ = sim.field(eps, sig, np.zeros(2))
+    P = sim.paths()
+    expect = image_source_paths(tx.astype(float), rx[0].astype(float), 1)
+    walls_axis = [0, 0, 1, 1, 2, 2]
+    lam = C0 / 28e9
+    n_checked = 0
+    for i in range(len(P["hi"])):
+        if P["k"][i] != 1:
+            continue
+        w = _decode_labels(P["hi"][i], P["lo"][i], 1)
+        length, pts = expect[w]
+        ax = walls_axis[w[0]]
+        din = (pts[0] - tx.astype(float)) / np.linalg.norm(pts[0] - tx.astype(float))
+        c = abs(din[ax])
+        l = 1 if w[0] == 4 else 0
+        eta = complex(eps[l], -sig[l] / (2 * np.pi * 28e9 * 8.8541878128e-12))
+        n2 = cmath.sqrt(eta)
+        ct = cmath.sqrt(1 - (1 - c * c) / eta)
+        gam = (c - n2 * ct) / (c + n2 * ct)
+        want = lam / (4 * np.pi * length) * gam
+        assert abs(a[i] - want) < 1e-10 * abs(want)
+        n_checked += 1
+    assert n_checked == 6
