@@ -702,7 +702,7 @@ void trace_ray(Sim& sim, int64_t row, const CastCfg& cfg) {
     if (!h.hit) break;
     r.idx = h.idx;
     r.dps = h.dps;
-    r.t = h.t;
+    r.t = norm(h.q - o);  // length of the segment to the interaction point q
     r.q = h.q;
     r.n = h.n;
     r.cos_in = h.cos_in;
