@@ -1,0 +1,324 @@
+"""Benchmark: one full 5-interaction simulation of the office workload per step.
+
+Workload: 20 x 10 x 3 m office, 2,000,000 oriented labelled points (40 boxes,
+1 cm position noise, 2 degree normal jitter), 16 receivers, one TX, a
+1,000,000-ray Fibonacci launch, up to 5 interactions, visibility-matrix
+capture with diffuse last interactions, dedup, refinement and field.
+A step is one call of the simulation (visibility matrix, trace, candidates,
+dedup, diffuse validation, specular refinement and validation, field).
+The scene build is setup and reported separately.
+
+value     = ray segments cast per second (trace segments + visibility casts +
+            LOS casts + validation casts), device-timed with CUDA events on the
+            library's stream, the L2 flushed between steps.
+ms_per_step = device time of one simulation.
+e2e       = the same metric through the C ABI with host buffers: TX/RX copied
+            in, all paths and the per-RX power read back, every step.
+roofline  = the trace kernel (the bounce loop), algorithmic bytes per launch
+            (oracle-counted disc reads per segment, tests/golden) over its
+            measured duration, against the measured HBM copy bandwidth.
+
+--impl reference times the FP64 CPU oracle on a bounded ray sample of the
+same workload on the host cores (the reference arm of this tier).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms per 5-bounce sim & ray-segments/s; proposal vs uniform speedup @0.5 dB"
+WORKLOAD = ("office 20x10x3 m + 40 boxes, 2M points, 16 RX, 1M Fibonacci rays, "
+            "5 interactions, visibility capture + diffuse, dedup + refinement + field")
+N_RAYS = 1_000_000
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _alg_bytes():
+    d = json.load(open(os.path.join(ROOT, "tests", "golden", "office_algorithmic_bytes.json")))
+    return d
+
+
+_ORACLE_SCENE = {}
+
+
+def run_oracle_sample(n_sample: int, threads: int = 0):
+    """Time the FP64 oracle on a ray sample of the workload; returns casts/s info.
+    The oracle's scene (voxels and its uniform grid) is built once, untimed."""
+    import oracle
+    from paper_2507_04021_gb300 import inputs
+    if not _ORACLE_SCENE:
+        o = inputs.office_scene()
+        _ORACLE_SCENE["o"] = o
+        _ORACLE_SCENE["sc"] = oracle.OracleScene(o.pos, o.nrm, o.surf, o.mat, r_p=0.015,
+                                                 grid_cell=0.1)
+    o, sc = _ORACLE_SCENE["o"], _ORACLE_SCENE["sc"]
+    stride = max(1, N_RAYS // n_sample)
+    ids = np.arange(0, N_RAYS, stride, dtype=np.int64)[:n_sample]
+    p = oracle.SimParams(max_depth=5, capture=1, diffuse=1, n_rays=N_RAYS, rep_tries=8,
+                         n_threads=threads)
+    t0 = time.perf_counter()
+    sim = oracle.OracleSim(sc, o.tx, o.rx, p, ray_ids=ids)
+    sim.field(o.eps_r, o.sigma, o.scat)
+    dt = time.perf_counter() - t0
+    c = sim.cast_counts()
+    casts = sum(c.values())
+    return {"seconds": dt, "casts": casts, "rays": int(ids.size), "counts": c,
+            "cores": oracle.max_threads() if threads <= 0 else threads}
+
+
+def reference_arm(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    n_sample = _env_int("NRT_REF_SAMPLE", 10000)
+    times, rates = [], []
+    info = None
+    for i in range(args.warmup + args.steps):
+        info = run_oracle_sample(n_sample)
+        if i >= args.warmup:
+            times.append(info["seconds"])
+            rates.append(info["casts"] / info["seconds"])
+    value = float(np.sum([info["casts"]] * len(times)) / np.sum(times))
+    sample = (f"{info['rays']} of the {N_RAYS} launch rays (every {N_RAYS // info['rays']}th), "
+              f"full pipeline, {info['casts']} casts per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ray-segments/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": float(np.mean(times) * 1000.0), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_rays": info["rays"]},
+        "cpu_baseline": {"value": value, "unit": "ray-segments/s", "cores": info["cores"],
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "ray-segments/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def ours(args):
+    import torch
+    from paper_2507_04021_gb300 import inputs, nrt
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = nrt.Context(local, stream=stream.cuda_stream)
+
+    o = inputs.office_scene()
+    scene = nrt.Scene(ctx, o.pos, o.nrm, o.surf, o.mat, rho=0.0625, r_p=0.015, lambda_d=100.0)
+    scene.set_materials(o.eps_r, o.sigma, o.scat)
+    build_ms = scene.info()["build_ms"]
+    # independent problems per rank: rank r simulates trajectory TX r (rank 0: the office TX)
+    tx = o.tx if rank == 0 else inputs.trajectory(o.extra["boxes"])[rank % 256]
+    p = nrt.default_trace_params(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=args.rays,
+                                 rep_tries=8)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        r = scene.trace(tx, o.rx, p)
+        ev1.record(stream)
+        return r, ev0, ev1
+
+    for _ in range(args.warmup):
+        r, _, _ = step()
+        r.close()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    evs, casts, trace_ms, launches, phases = [], 0, [], 0, []
+    last = None
+    for _ in range(args.steps):
+        r, e0, e1 = step()
+        _, c = r.counts()
+        casts += c["segments"] + c["vis_casts"] + c["los_casts"] + c["validation_casts"]
+        t = r.times()
+        trace_ms.append(t["trace"])
+        phases.append(t)
+        launches += c["kernel_launches"] + 1  # + the L2 flush fill
+        evs.append((e0, e1))
+        if last is not None:
+            last.close()
+        last = r
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = float(sum(a.elapsed_time(b) for a, b in evs))
+    counts = last.counts()[1]
+    if dist:
+        t = torch.tensor([total_ms, float(casts)], device=dev, dtype=torch.float64)
+        tm = t.clone()
+        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms, casts = float(tm[0]), float(t[1])
+    value = casts / (total_ms / 1000.0)
+
+    # end to end through the C ABI with host buffers: TX/RX from host memory in,
+    # the step's result (per-RX received power and path counts) back to host
+    e2e_ms, e2e_casts = [], 0
+    hb = db = 0
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = scene.trace(np.asarray(tx, np.float32), o.rx, p)
+        per_rx, c = r.counts()
+        pw = r.power()
+        e2e_ms.append((time.perf_counter() - t0) * 1000.0)
+        e2e_casts += c["segments"] + c["vis_casts"] + c["los_casts"] + c["validation_casts"]
+        hb = 12 + o.rx.nbytes
+        db = pw.nbytes + per_rx.nbytes
+        r.close()
+    e2e = None if args.no_e2e else {"value": e2e_casts / (sum(e2e_ms) / 1000.0), "unit": "ray-segments/s",
+           "h2d_bytes_per_step": int(hb), "d2h_bytes_per_step": int(db),
+           "ms_per_step": float(np.mean(e2e_ms)),
+           "result": "per-RX received power and path counts"}
+
+    ab = _alg_bytes()
+    peak, peak_kind = _peaks()
+    seg_per_launch = counts["segments"]
+    tr_ms = float(np.mean(trace_ms))
+    achieved = seg_per_launch * ab["bytes_per_segment"] / (tr_ms / 1000.0) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "trace_kernel",
+            "peak_kind": peak_kind, "bytes_per_segment": ab["bytes_per_segment"],
+            "segments_per_launch": seg_per_launch, "kernel_ms": tr_ms}
+    ph = {k: float(np.mean([x[k] for x in phases])) for k in phases[0]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "ray-segments/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "points": int(o.n_points), "rays": args.rays, "max_depth": 5,
+                   "n_rx": int(o.rx.shape[0]), "l2_flush": "256 MB fill between steps",
+                   "r_p": 0.015, "rho": 0.0625},
+        "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,
+        "phases_ms": ph, "scene_build_ms": build_ms,
+        "counts": {k: counts[k] for k in ("segments", "vis_casts", "validation_casts",
+                                          "candidates", "keys", "paths", "n_dps")},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        info = run_oracle_sample(_env_int("NRT_CPU_SAMPLE", 20000))
+        line["cpu_baseline"] = {
+            "value": info["casts"] / info["seconds"], "unit": "ray-segments/s",
+            "cores": info["cores"], "kind": "oracle",
+            "sample": f"{info['rays']} rays of the 1M launch, full pipeline, "
+                      f"{info['casts']} casts in {info['seconds']:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    last.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rays", type=int, default=N_RAYS)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours(args)
+
+
+if __name__ == "__main__":
+    main()

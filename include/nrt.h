@@ -1,0 +1,234 @@
+/*
+ * nrt.h -- C ABI of the GB300 point-cloud radio ray tracer (libnrt.so).
+ *
+ * The library implements the path computation of Vaara et al.,
+ * "Differentiable High-Performance Ray Tracing-Based Simulation of Radio
+ * Propagation with Point Clouds" (arXiv 2507.04021), as CUDA kernels for
+ * sm_103a, plus the EM field of each path and its adjoint.
+ *
+ * Conventions (every entry point):
+ *   - Plain pointers and sizes only.  "host" buffers live in host memory,
+ *     "device" buffers in device memory of the context's device.
+ *   - The caller owns every input array; the library copies what it keeps.
+ *   - The library owns nrt_ctx / nrt_scene / nrt_result until the matching
+ *     *_free / nrt_destroy call.  Handles are reference counted: a scene keeps
+ *     its context alive and a result keeps its scene alive, so the free calls
+ *     may come in any order (the memory goes with the last one).
+ *   - Work is enqueued on the context's CUDA stream.  Calls that return
+ *     host data (*_read, nrt_result_counts) synchronise that stream.
+ *   - No C++ exception crosses the ABI.  On error nothing is written to the
+ *     outputs and nrt_last_error() describes the failure.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef NRT_H_
+#define NRT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nrt_ctx nrt_ctx;
+typedef struct nrt_scene nrt_scene;
+typedef struct nrt_result nrt_result;
+
+typedef enum {
+  NRT_OK = 0,
+  NRT_ERR_ARG = 1,       /* invalid argument (NaN input, zero normal, bad size, ...) */
+  NRT_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+  NRT_ERR_OOM = 3,       /* device allocation failed */
+  NRT_ERR_OVERFLOW = 4,  /* a fixed-capacity buffer (hash table, candidates) overflowed */
+  NRT_ERR_TIMEOUT = 5,   /* a bounded device loop gave up (watchdog) */
+  NRT_ERR_STATE = 6      /* call out of order (e.g. backward without a field) */
+} nrt_status;
+
+/* Scene parameters (Table I of the paper: rho = 0.0625, r_p = 0.015,
+ * lambda_d = 100). */
+typedef struct {
+  float rho;       /* voxel size of the discretised point sets (DPS), m (Sec. II-A) */
+  float r_p;       /* disc radius, m (Sec. II-C) */
+  float lambda_d;  /* depth attenuation of Eq. 4, 1/m */
+} nrt_scene_params;
+
+enum { NRT_CAPTURE_SPHERE = 0, NRT_CAPTURE_VIS = 1 };
+enum { NRT_POL_TE = 0, NRT_POL_TM = 1 };
+
+/* Trace parameters.  nrt_trace_params_default() fills the paper's values
+ * (Table I: kappa = 10, t_a = 1 degree, t_d = 0.01 m). */
+typedef struct {
+  int32_t max_depth;    /* K: maximum number of interactions (<= 5) */
+  int32_t capture;      /* NRT_CAPTURE_SPHERE (RX sphere of radius r_rx) or
+                           NRT_CAPTURE_VIS (visibility matrix, Sec. II-B) */
+  int32_t diffuse;      /* 1: diffuse scattering as the last interaction (Sec. II-B-1) */
+  int32_t pol;          /* NRT_POL_TE or NRT_POL_TM (scalar Fresnel model) */
+  int32_t kappa;        /* refinement retries (Sec. II-B-2) */
+  int32_t rep_tries;    /* candidates validated per path key, in ray-id order (1..32) */
+  int32_t record_hits;  /* 1: keep per-ray hit records readable by nrt_hits_read */
+  int32_t reserved0;
+  int64_t n_rays;       /* N of the Fibonacci-sphere launch */
+  float r_rx;           /* RX sphere radius, m (sphere capture) */
+  float t_min;          /* minimum hit distance, m (default 1e-3) */
+  float t_a_deg;        /* refinement angle threshold, degrees */
+  float t_d;            /* refinement plane-distance threshold, m */
+  float freq;           /* carrier frequency, Hz */
+  float reserved1;
+  int64_t key_capacity;   /* hash-table slots (power of two; 0 = automatic) */
+  int64_t cand_capacity;  /* candidate buffer entries (0 = automatic) */
+} nrt_trace_params;
+
+/* Per-simulation counters (nrt_result_counts). */
+typedef struct {
+  int64_t rays;              /* rays launched */
+  int64_t segments;          /* primary ray segments cast (trace) */
+  int64_t vis_casts;         /* visibility-matrix casts */
+  int64_t los_casts;         /* TX -> RX casts */
+  int64_t validation_casts;  /* refinement, diffuse and final-leg casts */
+  int64_t candidates;        /* path candidates emitted */
+  int64_t keys;              /* distinct path keys */
+  int64_t paths;             /* valid paths (including LOS) */
+  int64_t n_dps;             /* DPS in the scene */
+  int64_t hash_probes_max;   /* longest hash probe sequence seen */
+  int64_t error_flags;       /* device error bits (0 = none) */
+  int64_t kernel_launches;   /* library kernels launched by the call */
+  int64_t reserved[4];
+} nrt_counters;
+
+/* Path view for nrt_paths_read: caller-allocated arrays of n_paths entries
+ * (n_paths from nrt_result_counts).  Any pointer may be NULL to skip it.
+ * Paths are ordered by (rx, type, interactions, representative ray id). */
+typedef struct {
+  uint64_t* key_hi;  /* 128-bit path key, see nrt_trace */
+  uint64_t* key_lo;
+  uint32_t* rep;     /* representative ray id (0xFFFFFFFF for LOS) */
+  int32_t* rx;       /* RX index */
+  int32_t* type;     /* 0 specular / LOS, 1 diffuse last interaction */
+  int32_t* k;        /* number of interactions (0 = LOS) */
+  float* pts;        /* [n][5][3] interaction points */
+  uint8_t* mats;     /* [n][5] material labels of the interactions */
+  float* cos_theta;  /* [n][5] cosine of the incidence angle at each interaction */
+  float* geo;        /* material-independent amplitude factor */
+  float* tau;        /* delay, s */
+  float* a;          /* [n][2] complex path coefficient (real, imag), without the
+                        propagation phase exp(-j 2 pi f tau) */
+} nrt_path_view;
+
+/* Status text for a status code (static storage). */
+const char* nrt_status_string(nrt_status s);
+
+/* Last error message of this context ("" if none). */
+const char* nrt_last_error(const nrt_ctx* ctx);
+
+/* Create a context on CUDA device `device` working on `cuda_stream`
+ * (a cudaStream_t; NULL = the context creates its own stream).
+ * Errors: NRT_ERR_ARG (bad device), NRT_ERR_CUDA. */
+nrt_status nrt_create(nrt_ctx** out, int device, void* cuda_stream);
+void nrt_destroy(nrt_ctx* ctx);
+
+/* Synchronise the context stream. */
+nrt_status nrt_sync(nrt_ctx* ctx);
+
+/* Fill the paper's default trace parameters. */
+void nrt_trace_params_default(nrt_trace_params* p);
+
+/* Upload an augmented point cloud (Sec. II: position p_i, normal n, surface
+ * label l_s, material label l_m) and build the ray-traceable scene
+ * (Sec. II-A): voxels of size rho; each DPS is the point set of one voxel with
+ * an AABB inflated by r_p and a reception point at the mean position.
+ *   pos, nrm   : float [n][3] (host, or device if inputs_on_device); nrm unit
+ *   surf_label : uint16 [n];  mat_label : uint8 [n]
+ * The DPS are ordered along a Morton curve and a bounding-volume hierarchy
+ * is built over their AABBs on the device.
+ * Errors: NRT_ERR_ARG for n <= 0, NaN/inf positions, zero normals,
+ * non-positive rho / r_p / lambda_d, or a scene more than 2^21 voxels wide. */
+nrt_status nrt_scene_upload(nrt_ctx* ctx, const float* pos, const float* nrm,
+                            const uint16_t* surf_label, const uint8_t* mat_label, int64_t n,
+                            const nrt_scene_params* params, int inputs_on_device,
+                            nrt_scene** out);
+void nrt_scene_free(nrt_scene* scene);
+
+/* Scene summary: number of DPS, voxel-grid origin bmin (float[3]) and the
+ * device time of the build (ms).  Any output may be NULL. */
+nrt_status nrt_scene_info(const nrt_scene* scene, int64_t* n_dps, float* bmin, float* build_ms);
+
+/* Read the DPS in library order: voxel coordinates int32[n_dps][3], point
+ * count int32[n_dps], reception point float[n_dps][3].  Host outputs. */
+nrt_status nrt_scene_dps_read(const nrt_scene* scene, int32_t* vox, int32_t* count,
+                              float* recv);
+
+/* Per-label materials: relative permittivity eps_r, conductivity sigma (S/m)
+ * and scattering coefficient S (ITU-R P.2040 convention for the complex
+ * permittivity eta = eps_r - j sigma / (2 pi f eps0)).  Host arrays of
+ * n_labels (<= 256) entries.  Errors: NRT_ERR_ARG for eps_r < 1, sigma < 0,
+ * S outside [0, 1). */
+nrt_status nrt_set_materials(nrt_scene* scene, const float* eps_r, const float* sigma,
+                             const float* scat, int n_labels);
+
+/* One simulation for one TX (Sec. II-B):
+ *   LOS casts TX -> every RX; Fibonacci launch of n_rays directions (or the
+ *   subset `ray_subset` of their ids); every interaction continues as a
+ *   specular reflection up to max_depth; path candidates from the RX sphere
+ *   or the RX -> DPS visibility matrix; duplicates removed by a 128-bit key
+ *   of (RX, type, interactions, surface labels[, scatter voxel]); the
+ *   lowest-ray-id candidate that validates represents a key (diffuse: a
+ *   cast scatter point -> RX; specular: image-method refinement on the
+ *   interaction planes, Eq. 1, validated by casts with thresholds t_a, t_d
+ *   and up to kappa retries); then the field of every path.
+ *   tx : host float[3];  rx : host float[n_rx][3] (n_rx <= 256)
+ *   ray_subset : NULL, or uint32[n_subset] ray ids < n_rays (host, or device
+ *                when subset_on_device)
+ * Key layout: hi = [rx:8 @56][diffuse:1 @55][k:3 @52][low 52 bits]; specular:
+ * lo = l1 | l2<<16 | l3<<32 | l4<<48, hi low 16 bits = l5; diffuse: lo =
+ * labels of the k-1 specular interactions, hi low 48 bits = scatter voxel
+ * x | y<<16 | z<<32 (each taken modulo 2^16).
+ * Errors: NRT_ERR_ARG, NRT_ERR_OOM, NRT_ERR_OVERFLOW (hash table or candidate
+ * buffer too small: raise key_capacity / cand_capacity), NRT_ERR_CUDA. */
+nrt_status nrt_trace(nrt_scene* scene, const float* tx, const float* rx, int n_rx,
+                     const nrt_trace_params* params, const uint32_t* ray_subset,
+                     int64_t n_subset, int subset_on_device, nrt_result** out);
+void nrt_result_free(nrt_result* result);
+
+/* Counters and per-RX path counts (host int64[n_rx], may be NULL). */
+nrt_status nrt_result_counts(const nrt_result* result, int64_t* n_paths_per_rx,
+                             nrt_counters* counters);
+
+/* Device times of the simulation phases in ms: [0] visibility, [1] LOS,
+ * [2] trace, [3] candidates + dedup, [4] validation/refinement, [5] field,
+ * [6] total.  Host float[8]. */
+nrt_status nrt_result_times(const nrt_result* result, float* ms);
+
+/* Read all paths into caller-allocated host arrays. */
+nrt_status nrt_paths_read(const nrt_result* result, const nrt_path_view* view);
+
+/* Per-ray hit records (requires record_hits): host arrays [n_traced][S]
+ * with S = max_depth (+1 for sphere capture); rays in launch order (ray ids
+ * 0..n_rays-1, or the subset order).  idx = point index of q_min (-1 after a
+ * miss), dps = library DPS index, q = Eq. 3 point, n = weighted normal
+ * facing the incoming ray, t = segment length.  Any pointer may be NULL. */
+nrt_status nrt_hits_read(const nrt_result* result, int32_t* idx, int32_t* dps, float* q,
+                         float* n, float* t);
+
+/* Visibility matrix bits (capture = VIS): host uint32[n_rx][(n_dps+31)/32],
+ * bit d of row j = DPS d visible from RX j. */
+nrt_status nrt_vis_read(const nrt_result* result, uint32_t* bits);
+
+/* Recompute the field of the stored paths with the scene's current materials
+ * (geometry does not depend on materials).  Enqueued on the context stream. */
+nrt_status nrt_field(nrt_result* result);
+
+/* Received power per RX, P_j = sum over paths of |a|^2 (host float[n_rx]). */
+nrt_status nrt_field_read(const nrt_result* result, float* power_per_rx);
+
+/* Adjoint of the received power: given dL/dP_j (host float[n_rx]), the
+ * gradient of L with respect to each label's eps_r, sigma and S (host
+ * float[n_labels] each), recomputed from the stored interaction sequences.
+ * Errors: NRT_ERR_STATE before nrt_set_materials. */
+nrt_status nrt_backward(nrt_result* result, const float* dL_dpower, float* g_eps, float* g_sigma,
+                        float* g_scat);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRT_H_ */

@@ -105,6 +105,11 @@ def _declare(L):
     L.orc_dfresnel.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, _D, _D]
     L.orc_fresnel_eta.argtypes = [C.c_double, C.c_double, C.c_double, C.c_int, _D, _D]
     L.orc_max_threads.restype = C.c_int
+    L.orc_sim_disc_counts.argtypes = [_P, _P]
+    L.orc_sim_cast_counts.argtypes = [_P, _P]
+    L.orc_sim_path_sens.argtypes = [_P, _P, _P, _P, _P, _P]
+    L.orc_sim_hit_sens.argtypes = [_P, _P, _P]
+    L.orc_vis_disc_counts.argtypes = [_P, _P, _P, _P, C.c_int64, C.c_double, _P]
 
 
 def _ptr(a: np.ndarray):
@@ -159,7 +164,7 @@ class OracleScene:
         lib().orc_scene_point_dps(self._h, _ptr(out))
         return out
 
-    def cast(self, o, d, skip_dps=-1, t_min=1e-4, t_max=np.inf, delta=0.0, weighted=True):
+    def cast(self, o, d, skip_dps=-1, t_min=1e-3, t_max=np.inf, delta=0.0, weighted=True):
         """One closest-hit cast; returns dict or None on a miss."""
         o = np.ascontiguousarray(o, np.float64)
         d = np.ascontiguousarray(d, np.float64)
@@ -173,7 +178,16 @@ class OracleScene:
                "cos_in": out[7], "idx": int(idx[0]), "dps": int(dps[0]), "amb": bool(amb[0])}
         return res
 
-    def vis_pairs(self, rx, j, dps, t_min=1e-4, delta=0.0):
+    def vis_disc_counts(self, rx, j, dps, t_min=1e-3):
+        rx = np.ascontiguousarray(rx, np.float64)
+        j = np.ascontiguousarray(j, np.int32)
+        dps = np.ascontiguousarray(dps, np.int32)
+        out = np.zeros(j.shape[0], np.int64)
+        lib().orc_vis_disc_counts(self._h, _ptr(rx), _ptr(j), _ptr(dps), j.shape[0],
+                                  float(t_min), _ptr(out))
+        return out
+
+    def vis_pairs(self, rx, j, dps, t_min=1e-3, delta=0.0):
         rx = np.ascontiguousarray(rx, np.float64)
         j = np.ascontiguousarray(j, np.int32)
         dps = np.ascontiguousarray(dps, np.int32)
@@ -203,7 +217,7 @@ class SimParams:
     n_threads: int = 0
     n_rays: int = 20000
     r_rx: float = 0.1
-    t_min: float = 1e-4
+    t_min: float = 1e-3
     delta: float = 0.0
     t_a_deg: float = 1.0
     t_d: float = 0.01
@@ -282,6 +296,18 @@ class OracleSim:
                                         "geo", "tau", "length", "certain")])
         return r
 
+    def cast_counts(self) -> dict:
+        out = np.zeros(4, np.int64)
+        lib().orc_sim_cast_counts(self._h, _ptr(out))
+        return {"segments": int(out[0]), "vis_casts": int(out[1]),
+                "validation_casts": int(out[2]), "los_casts": int(out[3])}
+
+    def disc_counts(self) -> np.ndarray:
+        """[n_rays, n_seg] discs in DPS boxes each cast enters before its hit (-1: no cast)."""
+        out = np.zeros((self.ray_ids.shape[0], lib().orc_sim_n_seg(self._h)), np.int64)
+        lib().orc_sim_disc_counts(self._h, _ptr(out))
+        return out
+
     def cand_status(self, hi, lo, ray) -> int:
         """0 certainly not a candidate, 1 certainly a candidate, 2 uncertain."""
         return int(lib().orc_sim_cand_status(self._h, int(hi), int(lo), int(ray)))
@@ -305,6 +331,22 @@ class OracleSim:
         lib().orc_sim_field(self._h, _ptr(eps), _ptr(sig), _ptr(sca), _ptr(a_re), _ptr(a_im),
                             _ptr(P), M)
         return a_re + 1j * a_im, P
+
+    def path_sens(self, eps_r, sigma, scat):
+        """(a_sens, tau_sens) per path from the shadow trajectories; -1 = fragile."""
+        eps = np.ascontiguousarray(eps_r, np.float64)
+        sig = np.ascontiguousarray(sigma, np.float64)
+        sca = np.ascontiguousarray(scat, np.float64)
+        n = lib().orc_sim_n_paths(self._h)
+        a, t = np.zeros(n), np.zeros(n)
+        lib().orc_sim_path_sens(self._h, _ptr(eps), _ptr(sig), _ptr(sca), _ptr(a), _ptr(t))
+        return a, t
+
+    def hit_sens(self):
+        n, S = self.ray_ids.shape[0], lib().orc_sim_n_seg(self._h)
+        dq, dn = np.zeros((n, S)), np.zeros((n, S))
+        lib().orc_sim_hit_sens(self._h, _ptr(dq), _ptr(dn))
+        return dq, dn
 
     def backward(self, eps_r, sigma, scat, dL_dP):
         eps = np.ascontiguousarray(eps_r, np.float64)

@@ -35,12 +35,14 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdint>
 #include <cstring>
 #include <limits>
 #include <map>
+#include <memory>
 #include <set>
 #include <tuple>
 #include <vector>
@@ -216,7 +218,9 @@ struct Hit {
 };
 
 struct CastCfg {
-  double t_min = 1e-4;  // hits need t > t_min
+  double wjit = 0.0;    // shadow trajectories: relative jitter of the Eq. 4 weights
+  int wseed = 0;
+  double t_min = 1e-3;  // hits need t > t_min
   double delta = 0.0;   // ambiguity band (position units)
 };
 
@@ -361,6 +365,10 @@ Hit cast(const Scene& S, V3 o, V3 d, int skip, double t_max, bool weighted, cons
     if (cfg.delta > 0 && e.t > cfg.t_min - b && std::fabs(e.r - rp) < b) h.amb = true;
     if (!(e.t > cfg.t_min && e.r <= rp)) continue;
     double w = std::exp(-e.r * e.r / (2.0 * rp * rp)) * std::exp(-S.lambda_d * norm(e.q - qmin));
+    if (cfg.wjit != 0.0) {
+      uint32_t hsh = (uint32_t)i * 2654435761u + (uint32_t)cfg.wseed * 40503u;
+      w *= 1.0 + cfg.wjit * (((hsh >> 15) & 1u) ? 1.0 : -1.0);
+    }
     sw += w;
     sq = sq + w * e.q;
     sn = sn + w * S.N[i];
@@ -491,6 +499,8 @@ struct PathOut {
   double cosv[5] = {0, 0, 0, 0, 0};
   double geo = 0, tau = 0, length = 0;
   bool certain = true;
+  bool shadow_ok[2] = {false, false};
+  std::shared_ptr<PathOut> shadow[2];
 };
 
 struct KeyOut {
@@ -512,6 +522,8 @@ struct Sim {
   int n_seg = 0;
   std::vector<int64_t> ray_ids;
   std::vector<HitRec> rec;     // [n_ray][n_seg]
+  std::vector<HitRec> recp[2]; // shadow trajectories (perturbed launch), same layout
+  std::vector<double> dq_sens, dn_sens;  // [n_ray][n_seg] shadow divergence
   std::vector<int> excl;       // first ambiguous hit (1-based), n_seg+1 = none
   std::vector<int> n_hits;
   // visibility bits, computed for the DPS the traced rays reach
@@ -525,6 +537,7 @@ struct Sim {
   std::map<Key, std::vector<int64_t>> uncertain_cand;
   std::map<Key, std::vector<Cand>> cands;  // per key, in ray order
   std::vector<int64_t> ray_pos;  // ray id -> row, or -1
+  mutable std::atomic<int64_t> val_casts{0}, vis_casts{0};
 };
 
 struct Validation {
@@ -548,16 +561,18 @@ std::pair<bool, bool> vis_cast(const Scene& S, V3 rxp, int D, const CastCfg& cfg
   return {bit, h.amb};
 }
 
-Validation validate_diffuse(const Sim& sim, int64_t row, int k, int j, const CastCfg& cfg) {
+Validation validate_diffuse(const Sim& sim, const std::vector<HitRec>& rec, int64_t row, int k,
+                            int j, const CastCfg& cfg) {
   const Scene& S = *sim.S;
   Validation v;
-  const HitRec& hk = sim.rec[row * sim.n_seg + (k - 1)];
+  const HitRec& hk = rec[row * sim.n_seg + (k - 1)];
   V3 u = sim.rx[j] - hk.q;
   double rs = norm(u);
   V3 w = (1.0 / rs) * u;
   double cs = dot(hk.n, w);
   if (cfg.delta > 0 && (std::fabs(cs) < 1e-5 || hk.cos_in < 1e-5)) v.amb = true;
   if (cs <= 0.0) return v;
+  sim.val_casts++;
   Hit h = cast(S, hk.q, w, hk.dps, rs, false, cfg);
   if (h.amb) v.amb = true;
   if (h.hit) return v;
@@ -567,7 +582,7 @@ Validation validate_diffuse(const Sim& sim, int64_t row, int k, int j, const Cas
   P.k = k;
   double ri = 0.0;
   for (int m = 0; m < k; ++m) {
-    const HitRec& hm = sim.rec[row * sim.n_seg + m];
+    const HitRec& hm = rec[row * sim.n_seg + m];
     P.pts[m] = hm.q;
     P.mats[m] = S.mat[hm.idx];
     P.cosv[m] = hm.cos_in;
@@ -588,13 +603,13 @@ Validation validate_diffuse(const Sim& sim, int64_t row, int k, int j, const Cas
 // the key's surface with a normal within t_a and within t_d of the plane;
 // otherwise the plane is replaced by the hit's and the solve retried, at most
 // kappa times.  Finally the last leg I_k -> RX must be clear.
-Validation validate_specular(const Sim& sim, int64_t row, int k, int j, const int* labels,
-                             const CastCfg& cfg) {
+Validation validate_specular(const Sim& sim, const std::vector<HitRec>& rec, int64_t row, int k,
+                             int j, const int* labels, const CastCfg& cfg) {
   const Scene& S = *sim.S;
   Validation v;
   V3 Pp[5], Pn[5];
   for (int m = 0; m < k; ++m) {
-    const HitRec& hm = sim.rec[row * sim.n_seg + m];
+    const HitRec& hm = rec[row * sim.n_seg + m];
     Pp[m] = hm.q;
     Pn[m] = hm.n;
   }
@@ -635,6 +650,7 @@ Validation validate_specular(const Sim& sim, int64_t row, int k, int j, const in
     bool dead = false;
     for (int m = 1; m <= k; ++m) {
       V3 seg = I[m] - I[m - 1];
+      sim.val_casts++;
       Hit h = cast(S, I[m - 1], unit(seg), prev_dps, kInf, true, cfg);
       if (h.amb) v.amb = true;
       if (!h.hit || S.surf[h.idx] != labels[m - 1]) {
@@ -664,6 +680,7 @@ Validation validate_specular(const Sim& sim, int64_t row, int k, int j, const in
     // final leg to the RX
     V3 last = rxp - I[k];
     double s = norm(last);
+    sim.val_casts++;
     Hit hf = cast(S, I[k], (1.0 / s) * last, prev_dps, s, false, cfg);
     if (hf.amb) v.amb = true;
     if (hf.hit) return v;
@@ -687,18 +704,17 @@ Validation validate_specular(const Sim& sim, int64_t row, int k, int j, const in
   return v;
 }
 
-void trace_ray(Sim& sim, int64_t row, const CastCfg& cfg) {
+// One trajectory: the launch direction d0 reflected specularly at every hit.
+void trace_one(Sim& sim, std::vector<HitRec>& rec, int64_t row, V3 d0, const CastCfg& cfg,
+               int* excl, int* n_hits, V3 kick = V3{0, 0, 0}) {
   const Scene& S = *sim.S;
-  int64_t rid = sim.ray_ids[row];
-  V3 o = sim.tx, d = fib_dir(rid, sim.p.n_rays);
+  V3 o = sim.tx, d = d0;
   int skip = -1;
-  sim.excl[row] = sim.n_seg + 1;
-  sim.n_hits[row] = 0;
   for (int k = 1; k <= sim.n_seg; ++k) {
     Hit h = cast(S, o, d, skip, kInf, true, cfg);
-    HitRec& r = sim.rec[row * sim.n_seg + (k - 1)];
+    HitRec& r = rec[row * sim.n_seg + (k - 1)];
     r.amb = h.amb;
-    if (h.amb && sim.excl[row] > k) sim.excl[row] = k;
+    if (h.amb && excl && *excl > k) *excl = k;
     if (!h.hit) break;
     r.idx = h.idx;
     r.dps = h.dps;
@@ -706,11 +722,66 @@ void trace_ray(Sim& sim, int64_t row, const CastCfg& cfg) {
     r.q = h.q;
     r.n = h.n;
     r.cos_in = h.cos_in;
-    sim.n_hits[row] = k;
+    if (n_hits) *n_hits = k;
     d = d - 2.0 * dot(d, h.n) * h.n;  // specular continuation
     r.dout = d;
-    o = h.q;
+    o = h.q + kick;  // shadows restart from a slightly displaced point
     skip = h.dps;
+  }
+}
+
+// The nominal trajectory plus two shadows whose launch direction is turned by
+// kShadowAngle about two axes orthogonal to it, whose every interaction
+// point is displaced by kShadowKick before the next segment starts, and
+// whose Eq. 4 weights are scaled by 1 +- kShadowJitter (sign from a hash of
+// the point index).  Float32 coordinates of a 20 m scene carry ~2e-6 m of
+// rounding per point and the weights inherit it; the shadows model both
+// several times over and show how strongly they grow along the (chaotic)
+// bounce sequence.  On a flat wall of identical normals the weight jitter
+// moves nothing, as rounding does not either.  A hit whose shadows land on another disc or
+// farther than delta from the nominal point is ambiguous, and the shadows'
+// divergence sizes the comparison tolerances.
+const double kShadowAngle = 1e-6;
+const double kShadowKick = 1e-5;
+const double kShadowJitter = 1e-3;
+
+void trace_ray(Sim& sim, int64_t row, const CastCfg& cfg) {
+  int64_t rid = sim.ray_ids[row];
+  V3 d0 = fib_dir(rid, sim.p.n_rays);
+  sim.excl[row] = sim.n_seg + 1;
+  sim.n_hits[row] = 0;
+  trace_one(sim, sim.rec, row, d0, cfg, &sim.excl[row], &sim.n_hits[row]);
+  if (cfg.delta <= 0) return;
+  V3 a = std::fabs(d0.z) < 0.9 ? V3{0, 0, 1} : V3{1, 0, 0};
+  V3 u = unit(V3{d0.y * a.z - d0.z * a.y, d0.z * a.x - d0.x * a.z, d0.x * a.y - d0.y * a.x});
+  V3 w{d0.y * u.z - d0.z * u.y, d0.z * u.x - d0.x * u.z, d0.x * u.y - d0.y * u.x};
+  for (int p = 0; p < 2; ++p) {
+    CastCfg quiet = cfg;
+    quiet.delta = 0.0;
+    quiet.wjit = kShadowJitter;
+    quiet.wseed = p + 1;
+    V3 dp = unit(d0 + kShadowAngle * (p == 0 ? u : w));
+    V3 kick = p == 0 ? V3{0.6, 0.48, 0.64} : V3{-0.48, 0.8, -0.36};  // unit, fixed
+    trace_one(sim, sim.recp[p], row, dp, quiet, nullptr, nullptr, kShadowKick * kick);
+  }
+  for (int k = 1; k <= sim.n_seg; ++k) {
+    const HitRec& h = sim.rec[row * sim.n_seg + (k - 1)];
+    double dq = 0.0, dn = 0.0;
+    bool split = false;
+    for (int p = 0; p < 2; ++p) {
+      const HitRec& g = sim.recp[p][row * sim.n_seg + (k - 1)];
+      if (g.idx != h.idx) {
+        split = true;
+        continue;
+      }
+      if (h.idx < 0) continue;
+      dq = std::max(dq, norm(g.q - h.q));
+      dn = std::max(dn, norm(g.n - h.n));
+    }
+    sim.dq_sens[row * sim.n_seg + (k - 1)] = dq;
+    sim.dn_sens[row * sim.n_seg + (k - 1)] = dn;
+    if ((split || dq > cfg.delta) && sim.excl[row] > k) sim.excl[row] = k;
+    if (h.idx < 0) break;
   }
 }
 
@@ -734,6 +805,9 @@ void run_sim(Sim& sim) {
   const bool sphere = sim.p.capture == 0;
   sim.n_seg = sim.p.max_depth + (sphere ? 1 : 0);
   sim.rec.assign(n * sim.n_seg, HitRec());
+  for (int p = 0; p < 2; ++p) sim.recp[p].assign(n * sim.n_seg, HitRec());
+  sim.dq_sens.assign(n * sim.n_seg, 0.0);
+  sim.dn_sens.assign(n * sim.n_seg, 0.0);
   sim.excl.assign(n, 0);
   sim.n_hits.assign(n, 0);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -763,6 +837,7 @@ void run_sim(Sim& sim) {
     for (int64_t i = 0; i < (int64_t)pairs.size(); ++i)
       res[i] = vis_cast(S, sim.rx[pairs[i].first], pairs[i].second, cfg);
     for (size_t i = 0; i < pairs.size(); ++i) sim.vis[pairs[i]] = res[i];
+    sim.vis_casts += (int64_t)pairs.size();
   }
 
   // candidates, in ray order
@@ -874,8 +949,8 @@ void run_sim(Sim& sim) {
     for (int c = 0; c < ntry; ++c) {
       int64_t rid = cl[c].ray;
       int64_t row = sim.ray_pos[rid];
-      Validation v = ko.type == 1 ? validate_diffuse(sim, row, ko.k, ko.j, cfg)
-                                  : validate_specular(sim, row, ko.k, ko.j, labels, cfg);
+      Validation v = ko.type == 1 ? validate_diffuse(sim, sim.rec, row, ko.k, ko.j, cfg)
+                                  : validate_specular(sim, sim.rec, row, ko.k, ko.j, labels, cfg);
       ko.tried.push_back(rid);
       ko.tried_valid.push_back(v.valid);
       ko.tried_amb.push_back(v.amb || !cl[c].certain);
@@ -883,6 +958,20 @@ void run_sim(Sim& sim) {
         ko.valid = true;
         ko.rep = rid;
         vout[qi] = v;
+        // the same candidate along the two shadow trajectories
+        if (cfg.delta > 0) {
+          for (int p = 0; p < 2; ++p) {
+            CastCfg quiet = cfg;
+            quiet.delta = 0.0;
+            quiet.wjit = kShadowJitter;
+            quiet.wseed = p + 1;
+            Validation w = ko.type == 1
+                               ? validate_diffuse(sim, sim.recp[p], row, ko.k, ko.j, quiet)
+                               : validate_specular(sim, sim.recp[p], row, ko.k, ko.j, labels, quiet);
+            vout[qi].path.shadow_ok[p] = w.valid;
+            if (w.valid) vout[qi].path.shadow[p] = std::make_shared<PathOut>(w.path);
+          }
+        }
         break;
       }
     }
@@ -1198,6 +1287,40 @@ void orc_sim_field(void* s, const double* eps, const double* sig, const double* 
   }
 }
 
+// Shadow sensitivity of each path: relative change of the coefficient and
+// of the delay along the two shadow trajectories (-1 when a shadow does not
+// validate: the path is fragile; 0 for LOS).
+void orc_sim_path_sens(void* s, const double* eps, const double* sig, const double* sca,
+                       double* a_sens, double* tau_sens) {
+  Sim* sim = (Sim*)s;
+  for (size_t i = 0; i < sim->paths.size(); ++i) {
+    const PathOut& P = sim->paths[i];
+    a_sens[i] = 0.0;
+    tau_sens[i] = 0.0;
+    if (P.k == 0) continue;
+    cd a = path_coefficient(P, eps, sig, sca, sim->p.freq, sim->p.pol);
+    for (int p = 0; p < 2; ++p) {
+      if (!P.shadow_ok[p] || !P.shadow[p]) {
+        a_sens[i] = -1.0;
+        tau_sens[i] = -1.0;
+        break;
+      }
+      cd b = path_coefficient(*P.shadow[p], eps, sig, sca, sim->p.freq, sim->p.pol);
+      a_sens[i] = std::max(a_sens[i], std::abs(b - a) / std::max(std::abs(a), 1e-300));
+      tau_sens[i] = std::max(tau_sens[i], std::fabs(P.shadow[p]->tau - P.tau) / P.tau);
+    }
+  }
+}
+
+// Shadow divergence of the hit records [n_ray][n_seg].
+void orc_sim_hit_sens(void* s, double* dq, double* dn) {
+  Sim* sim = (Sim*)s;
+  for (size_t i = 0; i < sim->dq_sens.size(); ++i) {
+    dq[i] = sim->dq_sens[i];
+    dn[i] = sim->dn_sens[i];
+  }
+}
+
 // Analytic gradient of L with respect to (eps_r, sigma, S) per label, given
 // dL/dP_j.  d|a|^2/dx = 2 Re(conj(a) da/dx); da/deta_l sums over the
 // interactions with label l; deta/deps_r = 1, deta/dsigma = -j/(2 pi f eps0),
@@ -1244,6 +1367,84 @@ void orc_sim_backward(void* s, const double* eps, const double* sig, const doubl
   }
 }
 
+// Algorithmic disc reads of a cast: the discs of every DPS (other than the
+// skipped one) whose r_p-inflated box the segment [t_min, t_end] enters.
+static int64_t discs_entered(const Scene& S, V3 o, V3 d, int skip, double t_min, double t_end) {
+  int64_t cnt = 0;
+  for (size_t D = 0; D < S.dps_pts.size(); ++D) {
+    if ((int)D == skip) continue;
+    V3 lo{kInf, kInf, kInf}, hi{-kInf, -kInf, -kInf};
+    for (int i : S.dps_pts[D]) {
+      lo = {std::min(lo.x, S.P[i].x), std::min(lo.y, S.P[i].y), std::min(lo.z, S.P[i].z)};
+      hi = {std::max(hi.x, S.P[i].x), std::max(hi.y, S.P[i].y), std::max(hi.z, S.P[i].z)};
+    }
+    double t0 = t_min, t1 = t_end;
+    bool miss = false;
+    for (int k = 0; k < 3 && !miss; ++k) {
+      double a = comp(lo, k) - S.rp, b = comp(hi, k) + S.rp, ok = comp(o, k), dk = comp(d, k);
+      if (dk == 0.0) {
+        if (ok < a || ok > b) miss = true;
+        continue;
+      }
+      double ta = (a - ok) / dk, tb = (b - ok) / dk;
+      if (ta > tb) std::swap(ta, tb);
+      t0 = std::max(t0, ta);
+      t1 = std::min(t1, tb);
+    }
+    if (!miss && t0 <= t1) cnt += (int64_t)S.dps_pts[D].size();
+  }
+  return cnt;
+}
+
+// Per ray and cast of a simulation: discs entered before the hit (or, after
+// a miss, along the whole ray); -1 for casts not made.
+void orc_sim_disc_counts(void* s, int64_t* out) {
+  Sim* sim = (Sim*)s;
+  const Scene& S = *sim->S;
+  const int64_t n = (int64_t)sim->ray_ids.size();
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t r = 0; r < n; ++r) {
+    V3 o = sim->tx, d = fib_dir(sim->ray_ids[r], sim->p.n_rays);
+    int skip = -1;
+    for (int k = 0; k < sim->n_seg; ++k) {
+      int64_t& dst = out[r * sim->n_seg + k];
+      if (k > sim->n_hits[r]) {
+        dst = -1;
+        continue;
+      }
+      const HitRec& h = sim->rec[r * sim->n_seg + k];
+      const bool hit = k < sim->n_hits[r];
+      dst = discs_entered(S, o, d, skip, sim->p.t_min, hit ? h.t : 1e30);
+      if (!hit) continue;
+      o = h.q;
+      d = h.dout;
+      skip = h.dps;
+    }
+  }
+}
+
+// The same count for visibility casts (RX j -> reception point of DPS D).
+void orc_vis_disc_counts(void* s, const double* rx, const int32_t* j, const int32_t* dps,
+                         int64_t n, double t_min, int64_t* out) {
+  Scene* S = (Scene*)s;
+  CastCfg cfg;
+  cfg.t_min = t_min;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) {
+    V3 r{rx[3 * j[i]], rx[3 * j[i] + 1], rx[3 * j[i] + 2]};
+    V3 v = S->recv[dps[i]] - r;
+    double sl = norm(v);
+    double t_max = sl - rx_margin(*S);
+    if (t_max <= t_min) {
+      out[i] = 0;
+      continue;
+    }
+    V3 d = (1.0 / sl) * v;
+    Hit h = cast(*S, r, d, -1, t_max, false, cfg);
+    out[i] = discs_entered(*S, r, d, -1, t_min, h.hit ? h.t : t_max);
+  }
+}
+
 // Standalone EM helpers for closed-form pins.
 void orc_fresnel(double eps_r, double sigma, double freq, double cos_t, int pol, double* re,
                  double* im) {
@@ -1262,6 +1463,18 @@ void orc_fresnel_eta(double eta_re, double eta_im, double cos_t, int pol, double
   cd G = fresnel(cd(eta_re, eta_im), cos_t, pol);
   *re = G.real();
   *im = G.imag();
+}
+
+// Casts made: [0] trace segments, [1] visibility, [2] validation, [3] LOS.
+void orc_sim_cast_counts(void* s, int64_t* out) {
+  Sim* sim = (Sim*)s;
+  int64_t segs = 0;
+  for (size_t r = 0; r < sim->ray_ids.size(); ++r)
+    segs += std::min(sim->n_hits[r] + 1, sim->n_seg);
+  out[0] = segs;
+  out[1] = sim->vis_casts.load();
+  out[2] = sim->val_casts.load();
+  out[3] = (int64_t)sim->rx.size();
 }
 
 int orc_max_threads(void) {

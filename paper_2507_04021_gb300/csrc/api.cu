@@ -1,0 +1,529 @@
+// C ABI of libnrt (declarations and contracts in include/nrt.h).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nrt_internal.h"
+
+using namespace nrt;
+
+namespace {
+
+thread_local std::string g_err;
+
+void free_dev(void* p) {
+  if (p) cudaFree(p);
+}
+
+// Handles are reference counted: a scene keeps its context alive and a result
+// keeps its scene alive, so the *_free calls may come in any order.
+void ctx_release(nrt_ctx* ctx) {
+  if (--ctx->refs > 0) return;
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+void scene_release(nrt_scene* s) {
+  if (--s->refs > 0) return;
+  cudaStreamSynchronize(s->ctx->stream);
+  free_dev(s->disc_p);
+  free_dev(s->disc_n);
+  free_dev(s->dps_range);
+  free_dev(s->dps_vox);
+  free_dev(s->dps_recv);
+  free_dev(s->dps_center);
+  free_dev(s->nodes);
+  free_dev(s->mat);
+  nrt_ctx* ctx = s->ctx;
+  delete s;
+  ctx_release(ctx);
+}
+
+__global__ void subset_check_kernel(const uint64_t* __restrict__ ids, int64_t n, int64_t n_rays,
+                                    uint32_t* __restrict__ out, unsigned int* bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t v = ids[i];
+    if ((int64_t)v >= n_rays || (i > 0 && ids[i - 1] == v)) atomicOr(bad, 1u);
+    out[i] = (uint32_t)v;
+  }
+}
+
+__global__ void widen_kernel(const uint32_t* __restrict__ in, int64_t n, uint64_t* __restrict__ k,
+                             uint32_t* __restrict__ v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    k[i] = in[i];
+    v[i] = 0;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nrt_status_string(nrt_status s) {
+  switch (s) {
+    case NRT_OK: return "ok";
+    case NRT_ERR_ARG: return "invalid argument";
+    case NRT_ERR_CUDA: return "CUDA error";
+    case NRT_ERR_OOM: return "out of device memory";
+    case NRT_ERR_OVERFLOW: return "device buffer overflow";
+    case NRT_ERR_TIMEOUT: return "device loop timeout";
+    case NRT_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* nrt_last_error(const nrt_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : g_err.c_str();
+}
+
+void nrt_trace_params_default(nrt_trace_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->max_depth = 5;
+  p->capture = NRT_CAPTURE_VIS;
+  p->diffuse = 1;
+  p->pol = NRT_POL_TE;
+  p->kappa = 10;
+  p->rep_tries = 8;
+  p->record_hits = 1;
+  p->n_rays = 1000000;
+  p->r_rx = 0.1f;
+  p->t_min = 1e-3f;
+  p->t_a_deg = 1.0f;
+  p->t_d = 0.01f;
+  p->freq = 28e9f;
+}
+
+nrt_status nrt_create(nrt_ctx** out, int device, void* cuda_stream) {
+  if (!out) return NRT_ERR_ARG;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    g_err = "no such CUDA device";
+    return NRT_ERR_ARG;
+  }
+  nrt_ctx* c = new (std::nothrow) nrt_ctx();
+  if (!c) return NRT_ERR_OOM;
+  c->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete c;
+    return NRT_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return NRT_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  // keep freed stream-ordered memory cached in the pool between simulations
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  *out = c;
+  return NRT_OK;
+}
+
+void nrt_destroy(nrt_ctx* ctx) {
+  if (!ctx) return;
+  ctx_release(ctx);
+}
+
+nrt_status nrt_sync(nrt_ctx* ctx) {
+  if (!ctx) return NRT_ERR_ARG;
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return NRT_OK;
+}
+
+nrt_status nrt_scene_upload(nrt_ctx* ctx, const float* pos, const float* nrm,
+                            const uint16_t* surf_label, const uint8_t* mat_label, int64_t n,
+                            const nrt_scene_params* params, int inputs_on_device,
+                            nrt_scene** out) {
+  if (!ctx || !out || !params || !pos || !nrm || !surf_label || !mat_label) return NRT_ERR_ARG;
+  if (n <= 0 || n >= (int64_t)1 << 31) {
+    ctx->last_error = "point count must be in [1, 2^31)";
+    return NRT_ERR_ARG;
+  }
+  if (!(params->rho > 0.f) || !(params->r_p > 0.f) || !(params->lambda_d > 0.f) ||
+      !std::isfinite(params->rho) || !std::isfinite(params->r_p) ||
+      !std::isfinite(params->lambda_d)) {
+    ctx->last_error = "rho, r_p and lambda_d must be positive and finite";
+    return NRT_ERR_ARG;
+  }
+  NRT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  const float *pd = pos, *nd = nrm;
+  const uint16_t* sd = surf_label;
+  const uint8_t* md = mat_label;
+  void* tmp = nullptr;
+  if (!inputs_on_device) {
+    const size_t bytes = n * (24 + 24 + 2 + 1) + 64;
+    NRT_CUDA_TRY(ctx, cudaMallocAsync(&tmp, bytes, st));
+    char* b = (char*)tmp;
+    NRT_CUDA_TRY(ctx, cudaMemcpyAsync(b, pos, n * 12, cudaMemcpyHostToDevice, st));
+    NRT_CUDA_TRY(ctx, cudaMemcpyAsync(b + n * 12, nrm, n * 12, cudaMemcpyHostToDevice, st));
+    NRT_CUDA_TRY(ctx, cudaMemcpyAsync(b + n * 24, surf_label, n * 2, cudaMemcpyHostToDevice, st));
+    NRT_CUDA_TRY(ctx, cudaMemcpyAsync(b + n * 26, mat_label, n, cudaMemcpyHostToDevice, st));
+    pd = (const float*)b;
+    nd = (const float*)(b + n * 12);
+    sd = (const uint16_t*)(b + n * 24);
+    md = (const uint8_t*)(b + n * 26);
+  }
+  nrt_scene* s = new (std::nothrow) nrt_scene();
+  if (!s) return NRT_ERR_OOM;
+  s->ctx = ctx;
+  ctx->refs++;
+  s->n = n;
+  s->params = *params;
+  NRT_CUDA_TRY(ctx, cudaMalloc(&s->mat, 3 * 256 * sizeof(float)));
+  nrt_status rc = build_scene(s, pd, nd, sd, md);
+  if (tmp) cudaFreeAsync(tmp, st);
+  if (rc != NRT_OK) {
+    nrt_scene_free(s);
+    return rc;
+  }
+  *out = s;
+  return NRT_OK;
+}
+
+void nrt_scene_free(nrt_scene* s) {
+  if (!s) return;
+  scene_release(s);
+}
+
+nrt_status nrt_scene_info(const nrt_scene* s, int64_t* n_dps, float* bmin, float* build_ms) {
+  if (!s) return NRT_ERR_ARG;
+  if (n_dps) *n_dps = s->n_dps;
+  if (bmin) memcpy(bmin, s->bmin, sizeof(s->bmin));
+  if (build_ms) *build_ms = s->build_ms;
+  return NRT_OK;
+}
+
+nrt_status nrt_scene_dps_read(const nrt_scene* s, int32_t* vox, int32_t* count, float* recv) {
+  if (!s) return NRT_ERR_ARG;
+  nrt_ctx* ctx = s->ctx;
+  cudaStream_t st = ctx->stream;
+  const int64_t nd = s->n_dps;
+  if (vox) NRT_CUDA_TRY(ctx, cudaMemcpyAsync(vox, s->dps_vox, nd * 12, cudaMemcpyDeviceToHost, st));
+  std::vector<uint2> rg;
+  std::vector<float4> rc;
+  if (count) {
+    rg.resize(nd);
+    NRT_CUDA_TRY(ctx, cudaMemcpyAsync(rg.data(), s->dps_range, nd * 8, cudaMemcpyDeviceToHost, st));
+  }
+  if (recv) {
+    rc.resize(nd);
+    NRT_CUDA_TRY(ctx, cudaMemcpyAsync(rc.data(), s->dps_recv, nd * 16, cudaMemcpyDeviceToHost, st));
+  }
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  for (int64_t d = 0; d < nd; ++d) {
+    if (count) count[d] = (int32_t)rg[d].y;
+    if (recv) {
+      recv[3 * d] = rc[d].x;
+      recv[3 * d + 1] = rc[d].y;
+      recv[3 * d + 2] = rc[d].z;
+    }
+  }
+  return NRT_OK;
+}
+
+nrt_status nrt_set_materials(nrt_scene* s, const float* eps_r, const float* sigma,
+                             const float* scat, int n_labels) {
+  if (!s || !eps_r || !sigma || !scat || n_labels <= 0 || n_labels > 256) return NRT_ERR_ARG;
+  nrt_ctx* ctx = s->ctx;
+  std::vector<float> h(3 * 256, 0.0f);
+  for (int l = 0; l < 256; ++l) h[l] = 1.0f;
+  for (int l = 0; l < n_labels; ++l) {
+    if (!(eps_r[l] >= 1.0f) || !(sigma[l] >= 0.0f) || !(scat[l] >= 0.0f && scat[l] < 1.0f) ||
+        !std::isfinite(eps_r[l]) || !std::isfinite(sigma[l])) {
+      ctx->last_error = "material out of range (eps_r >= 1, sigma >= 0, 0 <= S < 1)";
+      return NRT_ERR_ARG;
+    }
+    h[l] = eps_r[l];
+    h[256 + l] = sigma[l];
+    h[512 + l] = scat[l];
+  }
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(s->mat, h.data(), h.size() * 4, cudaMemcpyHostToDevice,
+                                    ctx->stream));
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  s->n_labels = n_labels;
+  s->have_materials = true;
+  return NRT_OK;
+}
+
+nrt_status nrt_trace(nrt_scene* s, const float* tx, const float* rx, int n_rx,
+                     const nrt_trace_params* p, const uint32_t* ray_subset, int64_t n_subset,
+                     int subset_on_device, nrt_result** out) {
+  if (!s || !tx || !rx || !p || !out) return NRT_ERR_ARG;
+  nrt_ctx* ctx = s->ctx;
+  if (n_rx <= 0 || n_rx > 256) {
+    ctx->last_error = "n_rx must be in [1, 256]";
+    return NRT_ERR_ARG;
+  }
+  if (p->max_depth < 1 || p->max_depth > kMaxDepth || p->n_rays <= 0 ||
+      p->n_rays > (int64_t)0xFFFFFFFE || p->rep_tries < 1 || p->rep_tries > 32 || p->kappa < 0 ||
+      !(p->freq > 0.f) || !(p->t_min >= 0.f) || (p->capture != 0 && p->capture != 1) ||
+      (p->capture == NRT_CAPTURE_SPHERE && p->diffuse)) {
+    ctx->last_error = "invalid trace parameters";
+    return NRT_ERR_ARG;
+  }
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(tx[k])) return NRT_ERR_ARG;
+  for (int k = 0; k < 3 * n_rx; ++k)
+    if (!std::isfinite(rx[k])) return NRT_ERR_ARG;
+  if (ray_subset && (n_subset <= 0 || n_subset > p->n_rays)) {
+    ctx->last_error = "invalid ray subset size";
+    return NRT_ERR_ARG;
+  }
+  NRT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  nrt_result* r = new (std::nothrow) nrt_result();
+  if (!r) return NRT_ERR_OOM;
+  r->scene = s;
+  s->refs++;
+  r->p = *p;
+  r->n_rx = n_rx;
+  memcpy(r->tx, tx, sizeof(r->tx));
+  std::vector<float4> rxh(n_rx);
+  for (int j = 0; j < n_rx; ++j) rxh[j] = make_float4(rx[3 * j], rx[3 * j + 1], rx[3 * j + 2], 0.f);
+  NRT_CUDA_TRY(ctx, cudaMalloc(&r->rx, n_rx * sizeof(float4)));
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(r->rx, rxh.data(), n_rx * sizeof(float4),
+                                    cudaMemcpyHostToDevice, st));
+  if (ray_subset) {
+    // rows are the subset in ascending ray-id order
+    uint32_t* raw = nullptr;
+    uint64_t *k = nullptr, *tk = nullptr;
+    uint32_t *v = nullptr, *tv = nullptr;
+    unsigned int* bad = nullptr;
+    NRT_CUDA_TRY(ctx, cudaMallocAsync(&raw, n_subset * 4, st));
+    NRT_CUDA_TRY(ctx, cudaMallocAsync(&k, n_subset * 8, st));
+    NRT_CUDA_TRY(ctx, cudaMallocAsync(&tk, n_subset * 8, st));
+    NRT_CUDA_TRY(ctx, cudaMallocAsync(&v, n_subset * 4, st));
+    NRT_CUDA_TRY(ctx, cudaMallocAsync(&tv, n_subset * 4, st));
+    NRT_CUDA_TRY(ctx, cudaMallocAsync(&bad, 4, st));
+    NRT_CUDA_TRY(ctx, cudaMemsetAsync(bad, 0, 4, st));
+    NRT_CUDA_TRY(ctx, cudaMemcpyAsync(raw, ray_subset, n_subset * 4,
+                                      subset_on_device ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice,
+                                      st));
+    const int g = (int)std::min<int64_t>((n_subset + 255) / 256, 4096);
+    widen_kernel<<<g, 256, 0, st>>>(raw, n_subset, k, v);
+    radix_sort_pairs(k, v, tk, tv, n_subset, 32, st);
+    NRT_CUDA_TRY(ctx, cudaMalloc(&r->ray_of_row, n_subset * 4));
+    subset_check_kernel<<<g, 256, 0, st>>>(k, n_subset, p->n_rays, r->ray_of_row, bad);
+    unsigned int bh = 0;
+    NRT_CUDA_TRY(ctx, cudaMemcpyAsync(&bh, bad, 4, cudaMemcpyDeviceToHost, st));
+    NRT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    cudaFreeAsync(raw, st);
+    cudaFreeAsync(k, st);
+    cudaFreeAsync(tk, st);
+    cudaFreeAsync(v, st);
+    cudaFreeAsync(tv, st);
+    cudaFreeAsync(bad, st);
+    if (bh) {
+      ctx->last_error = "ray subset has ids >= n_rays or duplicates";
+      nrt_result_free(r);
+      return NRT_ERR_ARG;
+    }
+    r->n_traced = n_subset;
+  } else {
+    r->n_traced = p->n_rays;
+  }
+  nrt_status rc = run_trace(r, r->ray_of_row);
+  if (rc != NRT_OK) {
+    nrt_result_free(r);
+    return rc;
+  }
+  *out = r;
+  return NRT_OK;
+}
+
+void nrt_result_free(nrt_result* r) {
+  if (!r) return;
+  cudaStreamSynchronize(r->scene->ctx->stream);
+  free_dev(r->rx);
+  free_dev(r->ray_of_row);
+  cudaStream_t st = r->scene->ctx->stream;
+  void* pool_ptrs[] = {r->rec_q, r->rec_n, r->rec_d, r->rec_i, r->vis, r->paths,
+                       r->path_a, r->power, r->ctr};
+  for (void* q : pool_ptrs)
+    if (q) cudaFreeAsync(q, st);
+  for (int e = 0; e < 8; ++e)
+    if (r->ev[e]) cudaEventDestroy(r->ev[e]);
+  delete[] r->rx_count;
+  delete[] r->rx_start;
+  nrt_scene* s = r->scene;
+  delete r;
+  scene_release(s);
+}
+
+nrt_status nrt_result_counts(const nrt_result* r, int64_t* n_paths_per_rx, nrt_counters* c) {
+  if (!r) return NRT_ERR_ARG;
+  if (n_paths_per_rx)
+    for (int j = 0; j < r->n_rx; ++j) n_paths_per_rx[j] = r->rx_count[j];
+  if (c) *c = r->counters;
+  return NRT_OK;
+}
+
+nrt_status nrt_result_times(const nrt_result* r, float* ms) {
+  if (!r || !ms) return NRT_ERR_ARG;
+  nrt_ctx* ctx = r->scene->ctx;
+  NRT_CUDA_TRY(ctx, cudaEventSynchronize(r->ev[7]));
+  auto el = [&](int a, int b) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r->ev[a], r->ev[b]);
+    return t;
+  };
+  ms[0] = el(0, 1);
+  ms[1] = 0.0f;
+  ms[2] = el(2, 3);
+  ms[3] = el(3, 4);
+  ms[4] = el(4, 5);
+  ms[5] = el(5, 6);
+  ms[6] = el(0, 7);
+  ms[7] = 0.0f;
+  return NRT_OK;
+}
+
+nrt_status nrt_paths_read(const nrt_result* r, const nrt_path_view* v) {
+  if (!r || !v) return NRT_ERR_ARG;
+  nrt_ctx* ctx = r->scene->ctx;
+  const int64_t np = r->n_paths;
+  std::vector<PathRec> P(np);
+  std::vector<float2> a(np);
+  cudaStream_t st = ctx->stream;
+  if (np > 0) {
+    NRT_CUDA_TRY(ctx, cudaMemcpyAsync(P.data(), r->paths, np * sizeof(PathRec),
+                                      cudaMemcpyDeviceToHost, st));
+    if (r->field_done)
+      NRT_CUDA_TRY(ctx, cudaMemcpyAsync(a.data(), r->path_a, np * sizeof(float2),
+                                        cudaMemcpyDeviceToHost, st));
+  }
+  std::vector<uint32_t> rays;
+  if (r->ray_of_row && np > 0) {
+    rays.resize(r->n_traced);
+    NRT_CUDA_TRY(ctx, cudaMemcpyAsync(rays.data(), r->ray_of_row, r->n_traced * 4,
+                                      cudaMemcpyDeviceToHost, st));
+  }
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  for (int64_t i = 0; i < np; ++i) {
+    const PathRec& p = P[i];
+    const int k = (p.jtk >> 9) & 7;
+    if (v->key_hi) v->key_hi[i] = p.hi;
+    if (v->key_lo) v->key_lo[i] = p.lo;
+    if (v->rep) v->rep[i] = (p.rep == kNone) ? kNone : (r->ray_of_row ? rays[p.rep] : p.rep);
+    if (v->rx) v->rx[i] = (int32_t)(p.jtk & 0xFF);
+    if (v->type) v->type[i] = (int32_t)((p.jtk >> 8) & 1);
+    if (v->k) v->k[i] = k;
+    const uint64_t mats = (uint64_t)p.mats_lo | ((uint64_t)p.mats_hi << 32);
+    for (int m = 0; m < 5; ++m) {
+      if (v->pts)
+        for (int c = 0; c < 3; ++c) v->pts[15 * i + 3 * m + c] = m < k ? p.pts[3 * m + c] : 0.f;
+      if (v->mats) v->mats[5 * i + m] = m < k ? (uint8_t)((mats >> (8 * m)) & 0xFF) : 0;
+      if (v->cos_theta) v->cos_theta[5 * i + m] = m < k ? p.cosv[m] : 0.f;
+    }
+    if (v->geo) v->geo[i] = p.geo;
+    if (v->tau) v->tau[i] = (float)((double)p.length / 299792458.0);
+    if (v->a) {
+      v->a[2 * i] = r->field_done ? a[i].x : 0.f;
+      v->a[2 * i + 1] = r->field_done ? a[i].y : 0.f;
+    }
+  }
+  return NRT_OK;
+}
+
+nrt_status nrt_hits_read(const nrt_result* r, int32_t* idx, int32_t* dps, float* q, float* n,
+                         float* t) {
+  if (!r) return NRT_ERR_ARG;
+  nrt_ctx* ctx = r->scene->ctx;
+  cudaStream_t st = ctx->stream;
+  const int64_t rows = r->n_traced, S = r->n_seg, nrec = rows * S;
+  std::vector<float4> hq(nrec), hn(nrec), hd(nrec);
+  std::vector<int2> hi(nrec);
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(hq.data(), r->rec_q, nrec * 16, cudaMemcpyDeviceToHost, st));
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(hn.data(), r->rec_n, nrec * 16, cudaMemcpyDeviceToHost, st));
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(hd.data(), r->rec_d, nrec * 16, cudaMemcpyDeviceToHost, st));
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(hi.data(), r->rec_i, nrec * 8, cudaMemcpyDeviceToHost, st));
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  for (int64_t row = 0; row < rows; ++row) {
+    bool dead = false;
+    for (int64_t s = 0; s < S; ++s) {
+      const int64_t a = s * rows + row, o = row * S + s;
+      const bool hit = !dead && hi[a].x >= 0;
+      if (!hit) dead = true;
+      if (idx) idx[o] = hit ? hi[a].x : -1;
+      int dv;
+      memcpy(&dv, &hd[a].w, 4);
+      if (dps) dps[o] = hit ? dv : -1;
+      if (q) {
+        q[3 * o] = hit ? hq[a].x : 0.f;
+        q[3 * o + 1] = hit ? hq[a].y : 0.f;
+        q[3 * o + 2] = hit ? hq[a].z : 0.f;
+      }
+      if (n) {
+        n[3 * o] = hit ? hn[a].x : 0.f;
+        n[3 * o + 1] = hit ? hn[a].y : 0.f;
+        n[3 * o + 2] = hit ? hn[a].z : 0.f;
+      }
+      if (t) t[o] = hit ? hq[a].w : 0.f;
+    }
+  }
+  return NRT_OK;
+}
+
+nrt_status nrt_vis_read(const nrt_result* r, uint32_t* bits) {
+  if (!r || !bits) return NRT_ERR_ARG;
+  nrt_ctx* ctx = r->scene->ctx;
+  if (!r->vis) {
+    ctx->last_error = "no visibility matrix (sphere capture)";
+    return NRT_ERR_STATE;
+  }
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(bits, r->vis, (size_t)r->n_rx * r->vis_words * 4,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return NRT_OK;
+}
+
+nrt_status nrt_field(nrt_result* r) {
+  if (!r) return NRT_ERR_ARG;
+  if (!r->scene->have_materials) {
+    r->scene->ctx->last_error = "materials not set";
+    return NRT_ERR_STATE;
+  }
+  return run_field(r);
+}
+
+nrt_status nrt_field_read(const nrt_result* r, float* power) {
+  if (!r || !power) return NRT_ERR_ARG;
+  nrt_ctx* ctx = r->scene->ctx;
+  if (!r->field_done) {
+    ctx->last_error = "field not computed (set materials, then nrt_field)";
+    return NRT_ERR_STATE;
+  }
+  std::vector<double> h(r->n_rx);
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), r->power, r->n_rx * 8, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int j = 0; j < r->n_rx; ++j) power[j] = (float)h[j];
+  return NRT_OK;
+}
+
+nrt_status nrt_backward(nrt_result* r, const float* dL_dpower, float* g_eps, float* g_sigma,
+                        float* g_scat) {
+  if (!r || !dL_dpower) return NRT_ERR_ARG;
+  if (!r->scene->have_materials || !r->field_done) {
+    r->scene->ctx->last_error = "backward needs materials and a computed field";
+    return NRT_ERR_STATE;
+  }
+  return run_backward(r, dL_dpower, g_eps, g_sigma, g_scat);
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+
+#include "../../include/nrt.h"
+#include "nrt_device.cuh"
+
+struct nrt_ctx {
+  int refs = 1;  // the caller's handle + one per live scene
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string last_error;
+  int sm_count = 0;
+};
+
+struct nrt_scene {
+  int refs = 1;  // the caller's handle + one per live result
+  nrt_ctx* ctx = nullptr;
+  int64_t n = 0;
+  int64_t n_dps = 0;
+  nrt_scene_params params{};
+  float bmin[3] = {0, 0, 0};
+  int grid_bits = 0;  // Morton bits per axis
+  // device arrays (owned)
+  float4* disc_p = nullptr;
+  float4* disc_n = nullptr;
+  uint2* dps_range = nullptr;
+  int32_t* dps_vox = nullptr;  // [n_dps][3]
+  float4* dps_recv = nullptr;  // reception point (xyz)
+  float4* dps_center = nullptr;  // local origin of the DPS's disc positions
+  float4* nodes = nullptr;     // 4 float4 per internal node
+  int root = 0;
+  float build_ms = 0.0f;
+  // materials
+  int n_labels = 0;
+  float* mat = nullptr;  // device [3][256]: eps_r, sigma, S
+  bool have_materials = false;
+};
+
+struct nrt_result {
+  nrt_scene* scene = nullptr;
+  nrt_trace_params p{};
+  int n_rx = 0;
+  int64_t n_traced = 0;  // rows (rays traced)
+  int n_seg = 0;
+  float tx[3] = {0, 0, 0};
+  // device arrays
+  float4* rx = nullptr;          // [n_rx]
+  uint32_t* ray_of_row = nullptr;  // nullptr: row == ray id
+  float4* rec_q = nullptr;   // [n_seg][n_traced]: q.xyz, segment length
+  float4* rec_n = nullptr;   // normal.xyz, cos_in
+  float4* rec_d = nullptr;   // outgoing direction.xyz, dps (bits)
+  int2* rec_i = nullptr;     // point index (-1 miss), labels
+  uint32_t* vis = nullptr;   // [n_rx][vis_words]
+  int64_t vis_words = 0;
+  // paths (sorted)
+  int64_t n_paths = 0;
+  int64_t path_cap = 0;
+  void* paths = nullptr;     // PathRec[path_cap]
+  float2* path_a = nullptr;  // [n_paths]
+  double* power = nullptr;   // [n_rx]
+  int64_t* rx_count = nullptr;  // [n_rx] paths per RX (host copy)
+  int64_t* rx_start = nullptr;
+  // counters
+  unsigned long long* ctr = nullptr;  // device counters
+  nrt_counters counters{};
+  cudaEvent_t ev[8] = {};
+  bool field_done = false;
+};
+
+namespace nrt {
+
+// counters slots in nrt_result::ctr
+enum Ctr : int {
+  kCtrSegments = 0,
+  kCtrVisCasts,
+  kCtrLosCasts,
+  kCtrValCasts,
+  kCtrCands,
+  kCtrKeys,
+  kCtrPaths,
+  kCtrProbeMax,
+  kCtrErr,
+  kCtrKeysSpec,
+  kCtrKeysDiff,
+  kCtrPending,
+  kCtrCount
+};
+
+// Path record (device, 128 bytes)
+struct PathRec {
+  uint64_t hi, lo;
+  uint32_t rep;   // representative row (LOS: kNone)
+  uint32_t jtk;   // rx | type << 8 | k << 9
+  float geo;
+  float length;
+  float cosv[5];
+  uint32_t mats_lo, mats_hi;  // 5 material labels, one byte each
+  float pts[15];
+  float pad[1];
+};
+static_assert(sizeof(PathRec) == 128, "PathRec layout");
+
+void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t st);
+void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
+                      int bits, cudaStream_t st);
+
+SceneView scene_view(const nrt_scene* s);
+
+// kernels launched on this host thread since the last reset
+int64_t& launch_counter();
+inline void count_launch(int64_t n = 1) { launch_counter() += n; }
+
+// scene.cu
+nrt_status build_scene(nrt_scene* s, const float* pos_d, const float* nrm_d, const uint16_t* surf_d,
+                       const uint8_t* mat_d);
+// trace.cu / paths.cu
+nrt_status run_trace(nrt_result* r, const uint32_t* subset_d);
+nrt_status run_field(nrt_result* r);
+nrt_status run_backward(nrt_result* r, const float* dL_dP, float* g_eps, float* g_sig,
+                        float* g_sca);
+
+}  // namespace nrt
+
+#define NRT_CUDA_TRY(ctx, expr)                                                   \
+  do {                                                                            \
+    cudaError_t _e = (expr);                                                      \
+    if (_e != cudaSuccess) {                                                      \
+      (ctx)->last_error = std::string(#expr) + ": " + cudaGetErrorString(_e);     \
+      return _e == cudaErrorMemoryAllocation ? NRT_ERR_OOM : NRT_ERR_CUDA;        \
+    }                                                                             \
+  } while (0)

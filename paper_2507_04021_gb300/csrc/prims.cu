@@ -1,0 +1,177 @@
+// Device primitives: exclusive scan and a stable LSD radix sort of
+// (uint64 key, uint32 value) pairs.  Used by the scene build (Morton order of
+// the points) and to put paths in a deterministic order.
+#include "nrt_internal.h"
+
+namespace nrt {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// exclusive scan of one tile per block; writes the tile total to sums[block]
+__global__ void scan_tile_kernel(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
+                                 int64_t n, uint32_t* __restrict__ sums) {
+  __shared__ uint32_t sh[kScanThreads];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t acc = 0;
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = (base + i < n) ? in[base + i] : 0u;
+    acc += v[i];
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = 1; off < kScanThreads; off <<= 1) {
+    uint32_t t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0u;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  uint32_t run = sh[threadIdx.x] - acc;  // exclusive prefix of this thread
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) out[base + i] = run;
+    run += v[i];
+  }
+  if (threadIdx.x == kScanThreads - 1 && sums) sums[blockIdx.x] = sh[threadIdx.x];
+}
+
+__global__ void scan_add_kernel(uint32_t* __restrict__ out, int64_t n,
+                                const uint32_t* __restrict__ offs) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  const uint32_t add = offs[blockIdx.x];
+  for (int i = threadIdx.x; i < kScanTile; i += kScanThreads)
+    if (base + i < n) out[base + i] += add;
+}
+
+}  // namespace
+
+int64_t& launch_counter() {
+  static thread_local int64_t c = 0;
+  return c;
+}
+
+void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  const int64_t blocks = (n + kScanTile - 1) / kScanTile;
+  if (blocks == 1) {
+    scan_tile_kernel<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr);
+    count_launch();
+    return;
+  }
+  uint32_t *sums = nullptr, *offs = nullptr;
+  cudaMallocAsync(&sums, blocks * sizeof(uint32_t), st);
+  cudaMallocAsync(&offs, blocks * sizeof(uint32_t), st);
+  scan_tile_kernel<<<(unsigned)blocks, kScanThreads, 0, st>>>(in, out, n, sums);
+  scan_exclusive(sums, offs, blocks, st);
+  scan_add_kernel<<<(unsigned)blocks, kScanThreads, 0, st>>>(out, n, offs);
+  count_launch(2);
+  cudaFreeAsync(sums, st);
+  cudaFreeAsync(offs, st);
+}
+
+// ---------------------------------------------------------------- radix sort
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 16;
+constexpr int kSortTile = kSortThreads * kSortRounds;
+constexpr int kWarps = kSortThreads / 32;
+
+__global__ void radix_hist_kernel(const uint64_t* __restrict__ keys, int64_t n, int shift,
+                                  uint32_t* __restrict__ counts, int n_blocks) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xFF], 1u);
+  }
+  __syncthreads();
+  counts[(int64_t)threadIdx.x * n_blocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: elements of a tile are ranked in input order, round by
+// round; within a round a warp ranks with match_any and warps are ordered by
+// per-warp digit counts in shared memory.
+__global__ void radix_scatter_kernel(const uint64_t* __restrict__ kin,
+                                     const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
+                                     uint32_t* __restrict__ vout, int64_t n, int shift,
+                                     const uint32_t* __restrict__ offsets, int n_blocks) {
+  __shared__ uint32_t run[256];
+  __shared__ uint32_t wcnt[kWarps][256];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  run[tid] = offsets[(int64_t)tid * n_blocks + blockIdx.x];
+  for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int64_t i = base + (int64_t)r * kSortThreads + tid;
+    const bool valid = i < n;
+    uint64_t k = 0;
+    uint32_t v = 0, dg = 0, rank_w = 0;
+    if (valid) {
+      k = kin[i];
+      v = vin[i];
+      dg = (uint32_t)(k >> shift) & 0xFF;
+    }
+    const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+    if (valid) {
+      const unsigned peers = __match_any_sync(vm, dg);
+      rank_w = __popc(peers & ((1u << lane) - 1u));
+      if (rank_w == 0) wcnt[warp][dg] = __popc(peers);
+    }
+    __syncthreads();
+    if (valid) {
+      uint32_t before = 0;
+      for (int w = 0; w < warp; ++w) before += wcnt[w][dg];
+      const uint32_t pos = run[dg] + before + rank_w;
+      kout[pos] = k;
+      vout[pos] = v;
+    }
+    __syncthreads();
+    uint32_t tot = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      tot += wcnt[w][tid];
+      wcnt[w][tid] = 0;
+    }
+    run[tid] += tot;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// Sort (keys, vals) by the low `bits` bits of the keys, stably.  The result
+// ends in keys/vals; tk/tv are scratch of n entries.
+void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
+                      int bits, cudaStream_t st) {
+  if (n <= 1) return;
+  const int n_blocks = (int)((n + kSortTile - 1) / kSortTile);
+  uint32_t *counts = nullptr, *offs = nullptr;
+  cudaMallocAsync(&counts, (size_t)256 * n_blocks * sizeof(uint32_t), st);
+  cudaMallocAsync(&offs, (size_t)256 * n_blocks * sizeof(uint32_t), st);
+  uint64_t *ka = keys, *kb = tk;
+  uint32_t *va = vals, *vb = tv;
+  int passes = 0;
+  for (int shift = 0; shift < bits; shift += 8, ++passes) {
+    radix_hist_kernel<<<n_blocks, kSortThreads, 0, st>>>(ka, n, shift, counts, n_blocks);
+    scan_exclusive(counts, offs, (int64_t)256 * n_blocks, st);
+    radix_scatter_kernel<<<n_blocks, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, offs,
+                                                            n_blocks);
+    count_launch(2);
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if (passes & 1) {
+    cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+  }
+  cudaFreeAsync(counts, st);
+  cudaFreeAsync(offs, st);
+}
+
+}  // namespace nrt

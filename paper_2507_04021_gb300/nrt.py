@@ -1,0 +1,308 @@
+"""Thin Python binding of libnrt (include/nrt.h): argument marshalling only.
+
+Every step of the simulation runs in the library's CUDA kernels.  The
+library must have been built (``paper_2507_04021_gb300.build.build()``); if it
+cannot be loaded the import of this module's functions fails loudly -- there
+is no CPU fallback.  Host inputs are numpy arrays; device inputs are torch
+CUDA tensors (their data pointers are passed with ``inputs_on_device``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+NRT_OK = 0
+CAPTURE_SPHERE = 0
+CAPTURE_VIS = 1
+POL_TE = 0
+POL_TM = 1
+
+
+class NrtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"nrt status {status}: {msg}")
+        self.status = status
+
+
+class SceneParams(C.Structure):
+    _fields_ = [("rho", C.c_float), ("r_p", C.c_float), ("lambda_d", C.c_float)]
+
+
+class TraceParams(C.Structure):
+    _fields_ = [
+        ("max_depth", C.c_int32), ("capture", C.c_int32), ("diffuse", C.c_int32),
+        ("pol", C.c_int32), ("kappa", C.c_int32), ("rep_tries", C.c_int32),
+        ("record_hits", C.c_int32), ("reserved0", C.c_int32), ("n_rays", C.c_int64),
+        ("r_rx", C.c_float), ("t_min", C.c_float), ("t_a_deg", C.c_float), ("t_d", C.c_float),
+        ("freq", C.c_float), ("reserved1", C.c_float), ("key_capacity", C.c_int64),
+        ("cand_capacity", C.c_int64),
+    ]
+
+
+class Counters(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in (
+        "rays", "segments", "vis_casts", "los_casts", "validation_casts", "candidates", "keys",
+        "paths", "n_dps", "hash_probes_max", "error_flags", "kernel_launches")] + [
+            ("reserved", C.c_int64 * 4)]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
+
+
+class PathView(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in (
+        "key_hi", "key_lo", "rep", "rx", "type", "k", "pts", "mats", "cos_theta", "geo", "tau", "a")]
+
+
+_P = C.c_void_p
+
+
+def lib():
+    """Load libnrt.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        _lib = C.CDLL(path)
+        L = _lib
+        L.nrt_status_string.restype = C.c_char_p
+        L.nrt_status_string.argtypes = [C.c_int]
+        L.nrt_last_error.restype = C.c_char_p
+        L.nrt_last_error.argtypes = [_P]
+        L.nrt_create.argtypes = [C.POINTER(_P), C.c_int, _P]
+        L.nrt_destroy.argtypes = [_P]
+        L.nrt_sync.argtypes = [_P]
+        L.nrt_trace_params_default.argtypes = [C.POINTER(TraceParams)]
+        L.nrt_trace_params_default.restype = None
+        L.nrt_scene_upload.argtypes = [_P, _P, _P, _P, _P, C.c_int64, C.POINTER(SceneParams),
+                                       C.c_int, C.POINTER(_P)]
+        L.nrt_scene_free.argtypes = [_P]
+        L.nrt_scene_free.restype = None
+        L.nrt_scene_info.argtypes = [_P, _P, _P, _P]
+        L.nrt_scene_dps_read.argtypes = [_P, _P, _P, _P]
+        L.nrt_set_materials.argtypes = [_P, _P, _P, _P, C.c_int]
+        L.nrt_trace.argtypes = [_P, _P, _P, C.c_int, C.POINTER(TraceParams), _P, C.c_int64,
+                                C.c_int, C.POINTER(_P)]
+        L.nrt_result_free.argtypes = [_P]
+        L.nrt_result_free.restype = None
+        L.nrt_result_counts.argtypes = [_P, _P, C.POINTER(Counters)]
+        L.nrt_result_times.argtypes = [_P, _P]
+        L.nrt_paths_read.argtypes = [_P, C.POINTER(PathView)]
+        L.nrt_hits_read.argtypes = [_P, _P, _P, _P, _P, _P]
+        L.nrt_vis_read.argtypes = [_P, _P]
+        L.nrt_field.argtypes = [_P]
+        L.nrt_field_read.argtypes = [_P, _P]
+        L.nrt_backward.argtypes = [_P, _P, _P, _P, _P]
+        L.nrt_destroy.restype = None
+    return _lib
+
+
+def exported_symbols():
+    return [l.split("(")[0].split()[-1].lstrip("*") for l in _header_decls()]
+
+
+def _header_decls():
+    here = os.path.dirname(os.path.abspath(__file__))
+    txt = open(os.path.join(os.path.dirname(here), "include", "nrt.h")).read()
+    import re
+    return re.findall(r"^(?:nrt_status|void|const char\*)\s+\**nrt_\w+\s*\(", txt, re.M)
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr()), bool(a.is_cuda)
+    return _np_ptr(a), False
+
+
+class Context:
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self._h = _P()
+        self._check(lib().nrt_create(C.byref(self._h), device, _P(stream) if stream else None))
+        self.device = device
+
+    def _check(self, st):
+        if st != NRT_OK:
+            msg = lib().nrt_last_error(self._h if getattr(self, "_h", None) else None)
+            raise NrtError(st, f"{lib().nrt_status_string(st).decode()}: {(msg or b'').decode()}")
+
+    def sync(self):
+        self._check(lib().nrt_sync(self._h))
+
+    def close(self):
+        if self._h:
+            lib().nrt_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def default_trace_params(**kw) -> TraceParams:
+    p = TraceParams()
+    lib().nrt_trace_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Scene:
+    def __init__(self, ctx: Context, pos, nrm, surf, mat, rho=0.0625, r_p=0.015, lambda_d=100.0):
+        self.ctx = ctx
+        dev = hasattr(pos, "data_ptr") and pos.is_cuda
+        if not dev:
+            pos = np.ascontiguousarray(pos, np.float32)
+            nrm = np.ascontiguousarray(nrm, np.float32)
+            surf = np.ascontiguousarray(surf, np.uint16)
+            mat = np.ascontiguousarray(mat, np.uint8)
+        self._keep = (pos, nrm, surf, mat)
+        n = int(pos.shape[0])
+        sp = SceneParams(rho, r_p, lambda_d)
+        self._h = _P()
+        ctx._check(lib().nrt_scene_upload(ctx._h, _ptr(pos)[0], _ptr(nrm)[0], _ptr(surf)[0],
+                                          _ptr(mat)[0], n, C.byref(sp), int(dev), C.byref(self._h)))
+        self._keep = None
+        self.n_points = n
+        self.params = (rho, r_p, lambda_d)
+
+    def info(self):
+        nd = C.c_int64()
+        bmin = np.zeros(3, np.float32)
+        ms = C.c_float()
+        self.ctx._check(lib().nrt_scene_info(self._h, C.byref(nd), _np_ptr(bmin), C.byref(ms)))
+        return {"n_dps": nd.value, "bmin": bmin, "build_ms": ms.value}
+
+    def dps(self):
+        n = self.info()["n_dps"]
+        vox = np.zeros((n, 3), np.int32)
+        cnt = np.zeros(n, np.int32)
+        recv = np.zeros((n, 3), np.float32)
+        self.ctx._check(lib().nrt_scene_dps_read(self._h, _np_ptr(vox), _np_ptr(cnt), _np_ptr(recv)))
+        return vox, cnt, recv
+
+    def set_materials(self, eps_r, sigma, scat):
+        e = np.ascontiguousarray(eps_r, np.float32)
+        s = np.ascontiguousarray(sigma, np.float32)
+        c = np.ascontiguousarray(scat, np.float32)
+        self.ctx._check(lib().nrt_set_materials(self._h, _np_ptr(e), _np_ptr(s), _np_ptr(c),
+                                                int(e.shape[0])))
+        self.n_labels = int(e.shape[0])
+
+    def trace(self, tx, rx, params: TraceParams, ray_subset=None) -> "Result":
+        return Result(self, tx, rx, params, ray_subset)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nrt_scene_free(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Result:
+    def __init__(self, scene: Scene, tx, rx, params: TraceParams, ray_subset=None):
+        self.scene = scene
+        self.ctx = scene.ctx
+        tx = np.ascontiguousarray(tx, np.float32).reshape(3)
+        rx = np.ascontiguousarray(rx, np.float32).reshape(-1, 3)
+        self.n_rx = int(rx.shape[0])
+        self.params = params
+        sub_ptr, n_sub, on_dev = None, 0, False
+        if ray_subset is not None:
+            if not (hasattr(ray_subset, "data_ptr") and ray_subset.is_cuda):
+                ray_subset = np.ascontiguousarray(ray_subset, np.uint32)
+            sub_ptr, on_dev = _ptr(ray_subset)
+            n_sub = int(ray_subset.shape[0])
+        self._h = _P()
+        self.ctx._check(lib().nrt_trace(scene._h, _np_ptr(tx), _np_ptr(rx), self.n_rx,
+                                        C.byref(params), sub_ptr, n_sub, int(on_dev),
+                                        C.byref(self._h)))
+        self.n_seg = params.max_depth + (1 if params.capture == CAPTURE_SPHERE else 0)
+        self.n_traced = n_sub if ray_subset is not None else int(params.n_rays)
+
+    def counts(self):
+        c = Counters()
+        per = np.zeros(self.n_rx, np.int64)
+        self.ctx._check(lib().nrt_result_counts(self._h, _np_ptr(per), C.byref(c)))
+        return per, c.as_dict()
+
+    def times(self):
+        t = np.zeros(8, np.float32)
+        self.ctx._check(lib().nrt_result_times(self._h, _np_ptr(t)))
+        return {"vis": float(t[0]), "trace": float(t[2]), "dedup": float(t[3]),
+                "validate": float(t[4]), "field": float(t[5]), "total": float(t[6])}
+
+    def paths(self):
+        per, c = self.counts()
+        n = c["paths"]
+        out = {"key_hi": np.zeros(n, np.uint64), "key_lo": np.zeros(n, np.uint64),
+               "rep": np.zeros(n, np.uint32), "rx": np.zeros(n, np.int32),
+               "type": np.zeros(n, np.int32), "k": np.zeros(n, np.int32),
+               "pts": np.zeros((n, 5, 3), np.float32), "mats": np.zeros((n, 5), np.uint8),
+               "cos_theta": np.zeros((n, 5), np.float32), "geo": np.zeros(n, np.float32),
+               "tau": np.zeros(n, np.float32), "a": np.zeros((n, 2), np.float32)}
+        v = PathView(**{k: _np_ptr(a) for k, a in out.items()})
+        self.ctx._check(lib().nrt_paths_read(self._h, C.byref(v)))
+        return out
+
+    def hits(self):
+        S, n = self.n_seg, self.n_traced
+        out = {"idx": np.zeros((n, S), np.int32), "dps": np.zeros((n, S), np.int32),
+               "q": np.zeros((n, S, 3), np.float32), "n": np.zeros((n, S, 3), np.float32),
+               "t": np.zeros((n, S), np.float32)}
+        self.ctx._check(lib().nrt_hits_read(self._h, *[_np_ptr(out[k]) for k in
+                                                        ("idx", "dps", "q", "n", "t")]))
+        return out
+
+    def vis(self):
+        nd = self.scene.info()["n_dps"]
+        words = (nd + 31) // 32
+        bits = np.zeros((self.n_rx, words), np.uint32)
+        self.ctx._check(lib().nrt_vis_read(self._h, _np_ptr(bits)))
+        return np.unpackbits(bits.view(np.uint8), axis=1, bitorder="little")[:, :nd].astype(bool)
+
+    def field(self):
+        self.ctx._check(lib().nrt_field(self._h))
+
+    def power(self):
+        p = np.zeros(self.n_rx, np.float32)
+        self.ctx._check(lib().nrt_field_read(self._h, _np_ptr(p)))
+        return p
+
+    def backward(self, dL_dP):
+        g = np.ascontiguousarray(dL_dP, np.float32)
+        L = self.scene.n_labels
+        ge, gs, gc = (np.zeros(L, np.float32) for _ in range(3))
+        self.ctx._check(lib().nrt_backward(self._h, _np_ptr(g), _np_ptr(ge), _np_ptr(gs),
+                                           _np_ptr(gc)))
+        return ge, gs, gc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nrt_result_free(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

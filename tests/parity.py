@@ -1,0 +1,152 @@
+"""Comparison helpers: CUDA path vs the FP64 oracle on the same seeded inputs.
+
+Hit records: bit-exact point index (q_min) at every bounce the oracle marks
+certain (before its first ambiguous decision), positions within the
+ambiguity band delta, normals within 1e-4.
+
+Paths: for every key valid on either side, the representative ray must be
+the same, or the difference must be explained by a decision the oracle
+marks ambiguous *for that key and that ray* (an uncertain candidacy or an
+ambiguous validation).  Matched paths must agree within 1e-4 relative on
+the complex coefficient and 1e-6 relative on the delay.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+C0 = 299792458.0
+
+
+def compare_hits(g, o, delta, n_tol=1e-4, sens=None):
+    """g: GPU hits dict (rows = rays in ascending id); o: oracle hits dict;
+    sens: the oracle's shadow divergence (dq, dn) per hit, which widens the
+    normal tolerance where the bounce sequence amplifies rounding."""
+    gi = g["idx"].astype(np.int64)
+    oi = o["idx"]
+    n, S = oi.shape
+    excl = o["excl"]
+    checked = mism = 0
+    max_dq = 0.0
+    worst = None
+    bad = []
+    for s in range(S):
+        cert = (s + 1) < excl
+        # compare only while the oracle ray is alive at bounce s (or its miss is certain)
+        alive = np.ones(n, bool) if s == 0 else (oi[:, s - 1] >= 0)
+        m = cert & alive
+        checked += int(m.sum())
+        diff = m & (gi[:, s] != oi[:, s])
+        mism += int(diff.sum())
+        if diff.any():
+            bad += [(int(r), s, int(gi[r, s]), int(oi[r, s])) for r in np.nonzero(diff)[0][:5]]
+        hit = m & (oi[:, s] >= 0) & (gi[:, s] == oi[:, s])
+        if hit.any():
+            dq = np.abs(g["q"][hit, s].astype(np.float64) - o["q"][hit, s]).max(axis=1)
+            dn = np.abs(g["n"][hit, s].astype(np.float64) - o["n"][hit, s]).max(axis=1)
+            if float(dq.max()) > max_dq:
+                rr = np.nonzero(hit)[0][int(np.argmax(dq))]
+                worst = {"row": int(rr), "bounce": s, "dq": float(dq.max()),
+                         "cos_in": float(o["cos_in"][rr, s]), "t": float(o["t"][rr, s]),
+                         "idx": int(oi[rr, s]),
+                         "dq_sens": float(sens[0][rr, s]) if sens is not None else None,
+                         "dq_prev": [float(np.abs(g["q"][rr, u] - o["q"][rr, u]).max())
+                                     for u in range(s)]}
+            max_dq = max(max_dq, float(dq.max()))
+            tol = np.full(dn.shape, n_tol)
+            if sens is not None:
+                tol = np.maximum(tol, 2.0 * sens[1][hit, s])
+            wi = int(np.argmax(dn - tol))
+            assert (dn <= tol).all(), f"normal differs by {dn[wi]} (tol {tol[wi]}) at bounce {s}"
+    excluded = int((excl <= S).sum())
+    return {"checked": checked, "mismatch": mism, "max_dq": max_dq, "excluded_rays": excluded,
+            "examples": bad, "worst": worst}
+
+
+def _tried_map(osim):
+    K = osim.keys()
+    ray, valid, amb = osim.tried()
+    off = np.concatenate([[0], np.cumsum(K["n_tried"])])
+    out = {}
+    for i in range(len(K["hi"])):
+        key = (int(K["hi"][i]), int(K["lo"][i]))
+        sl = slice(off[i], off[i + 1])
+        out[key] = {"valid": bool(K["valid"][i]), "rep": int(K["rep"][i]),
+                    "certain": bool(K["certain"][i]), "path": int(K["path"][i]),
+                    "tried": list(zip(ray[sl].tolist(), valid[sl].tolist(), amb[sl].tolist()))}
+    return out
+
+
+def compare_paths(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6):
+    """gp: GPU paths dict; osim: OracleSim.  Returns a summary; raises on an
+    unexplained mismatch or an out-of-tolerance matched path."""
+    O = osim.paths()
+    a_o, _ = osim.field(eps_r, sigma, scat)
+    a_sens, tau_sens = osim.path_sens(eps_r, sigma, scat)
+    omap = _tried_map(osim)
+    NONE = 0xFFFFFFFF
+    g_by_key = {}
+    for i in range(len(gp["key_hi"])):
+        g_by_key[(int(gp["key_hi"][i]), int(gp["key_lo"][i]))] = i
+    o_by_key = {}
+    for i in range(len(O["hi"])):
+        o_by_key[(int(O["hi"][i]), int(O["lo"][i]))] = i
+    keys = set(g_by_key) | set(o_by_key)
+    matched = explained = field_checked = 0
+    unexplained = []
+    max_da = max_dtau = 0.0
+    common_p_g = np.zeros(osim.rx.shape[0])
+    common_p_o = np.zeros(osim.rx.shape[0])
+    for key in keys:
+        gi = g_by_key.get(key)
+        oi = o_by_key.get(key)
+        g = None if gi is None else int(gp["rep"][gi])
+        o = None if oi is None else int(O["rep"][oi])
+        if g == NONE:
+            g = -1
+        if gi is not None and oi is not None and g == o:
+            matched += 1
+            info = omap.get(key)
+            certain = bool(O["certain"][oi]) if info is None else info["certain"]
+            j = int(O["j"][oi])
+            ag = complex(gp["a"][gi, 0], gp["a"][gi, 1])
+            ao = a_o[oi]
+            common_p_g[j] += abs(ag) ** 2
+            common_p_o[j] += abs(ao) ** 2
+            if certain and a_sens[oi] >= 0:
+                field_checked += 1
+                da = abs(ag - ao) / max(abs(ao), 1e-300)
+                dt = abs(float(gp["tau"][gi]) - O["tau"][oi]) / O["tau"][oi]
+                tol_a = max(a_rtol, 2.0 * a_sens[oi])
+                tol_t = max(tau_rtol, 2.0 * tau_sens[oi])
+                max_da = max(max_da, da / tol_a * a_rtol)
+                max_dtau = max(max_dtau, dt / tol_t * tau_rtol)
+                assert da <= tol_a, f"path {key}: a rel error {da} (tol {tol_a})"
+                assert dt <= tol_t, f"path {key}: tau rel error {dt} (tol {tol_t})"
+            continue
+        info = omap.get(key)
+        tried = info["tried"] if info else []
+        tried_rays = {r: amb for r, _, amb in tried}
+        ok = False
+        if g is not None and g >= 0:
+            if osim.cand_status(key[0], key[1], g) == 2:
+                ok = True
+            if tried_rays.get(g, False):
+                ok = True
+            if g not in tried_rays and any(a for _, _, a in tried):
+                ok = True
+        if o is not None and o >= 0:
+            if tried_rays.get(o, False) or osim.cand_status(key[0], key[1], o) == 2:
+                ok = True
+        if (g is None or o is None) and any(a for _, _, a in tried):
+            ok = True
+        if ok:
+            explained += 1
+        else:
+            unexplained.append((hex(key[0]), hex(key[1]), g, o, tried[:4]))
+    assert not unexplained, f"{len(unexplained)} unexplained path mismatches, e.g. {unexplained[:5]}"
+    m = common_p_o > 0
+    dp = np.abs(common_p_g[m] - common_p_o[m]) / common_p_o[m]
+    return {"keys": len(keys), "matched": matched, "explained": explained,
+            "fragile": int((a_sens < 0).sum()),
+            "field_checked": field_checked, "max_da": max_da, "max_dtau": max_dtau,
+            "max_dP_common": float(dp.max()) if dp.size else 0.0}

@@ -1,0 +1,161 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (libnrt.so).
+
+Room (5x4x3 m, 5,000 points): the oracle brute-forces every disc.
+Office (20x10x3 m, 2,000,000 points): the oracle uses its uniform grid on a
+ray subset; the full 1M-ray launch is checked on sampled rays.
+Tolerances (the benchmark spec): hit indices bit-exact outside the oracle's
+ambiguity band delta = 1e-5 * scene diagonal; complex path coefficients
+within 1e-4 relative; delays within 1e-6 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_04021_gb300 import inputs
+from paper_2507_04021_gb300 import nrt
+
+from parity import compare_hits, compare_paths
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return nrt.Context(0)
+
+
+@pytest.fixture(scope="module")
+def room_gpu(ctx, room):
+    sc = nrt.Scene(ctx, room.pos, room.nrm, room.surf, room.mat, rho=0.0625, r_p=0.05)
+    sc.set_materials(room.eps_r, room.sigma, room.scat)
+    return sc
+
+
+@pytest.fixture(scope="module")
+def room_orc(room):
+    return oracle.OracleScene(room.pos, room.nrm, room.surf, room.mat, rho=0.0625, r_p=0.05)
+
+
+@pytest.fixture(scope="module")
+def office_gpu(ctx, office):
+    sc = nrt.Scene(ctx, office.pos, office.nrm, office.surf, office.mat, rho=0.0625, r_p=0.015)
+    sc.set_materials(office.eps_r, office.sigma, office.scat)
+    return sc
+
+
+@pytest.fixture(scope="module")
+def office_orc(office):
+    return oracle.OracleScene(office.pos, office.nrm, office.surf, office.mat, rho=0.0625,
+                              r_p=0.015, grid_cell=0.1)
+
+
+def _same_dps(gsc, osc):
+    gv, gc, gr = gsc.dps()
+    ov, oc, orr = osc.dps()
+    order = np.lexsort((gv[:, 2], gv[:, 1], gv[:, 0]))
+    assert np.array_equal(gv[order], ov)
+    assert np.array_equal(gc[order], oc)
+    assert np.abs(gr[order].astype(np.float64) - orr).max() < 2e-5 * max(1.0, np.abs(orr).max())
+
+
+def test_scene_build_room(room_gpu, room_orc):
+    _same_dps(room_gpu, room_orc)
+    assert np.array_equal(room_gpu.info()["bmin"], room_orc.bmin())
+
+
+def test_scene_build_office(office_gpu, office_orc):
+    _same_dps(office_gpu, office_orc)
+
+
+def _room_params(**kw):
+    p = dict(max_depth=2, capture=nrt.CAPTURE_SPHERE, diffuse=0, n_rays=20000, r_rx=0.1,
+             rep_tries=8, freq=28e9)
+    p.update(kw)
+    return p
+
+
+def test_room_sphere_capture(room, room_gpu, room_orc):
+    """Config 1: 20,000 Fibonacci rays, 2 specular bounces, RX sphere 0.1 m."""
+    kp = _room_params()
+    res = room_gpu.trace(room.tx, room.rx, nrt.default_trace_params(**kp))
+    delta = 1e-5 * room.diag
+    osim = oracle.OracleSim(room_orc, room.tx, room.rx,
+                            oracle.SimParams(delta=delta, **{k: v for k, v in kp.items()
+                                                             if k != "freq"}, freq=28e9))
+    h = compare_hits(res.hits(), osim.hits(), delta, sens=osim.hit_sens())
+    assert h["mismatch"] == 0, h
+    assert h["checked"] > 20000
+    assert h["max_dq"] < delta
+    s = compare_paths(res.paths(), osim, room.eps_r, room.sigma, room.scat)
+    assert s["matched"] >= 1
+
+
+def test_room_visibility_capture(room, room_gpu, room_orc):
+    """Room scene through the visibility-matrix capture with diffuse last
+    interactions: exercises vis, dedup, diffuse validation and refinement."""
+    kp = _room_params(capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=4000)
+    res = room_gpu.trace(room.tx, room.rx, nrt.default_trace_params(**kp))
+    delta = 1e-5 * room.diag
+    osim = oracle.OracleSim(room_orc, room.tx, room.rx,
+                            oracle.SimParams(delta=delta, **{k: v for k, v in kp.items()
+                                                             if k != "freq"}, freq=28e9))
+    h = compare_hits(res.hits(), osim.hits(), delta, sens=osim.hit_sens())
+    assert h["mismatch"] == 0, h
+    # visibility bits for the DPS the oracle evaluated
+    gvis = res.vis()
+    gv, _, _ = room_gpu.dps()
+    ov, _, _ = room_orc.dps()
+    omap = {tuple(v): i for i, v in enumerate(ov)}
+    g_of_o = np.zeros(len(ov), np.int64)
+    for gi, v in enumerate(gv):
+        g_of_o[omap[tuple(v)]] = gi
+    j, d, bit, amb = osim.vis()
+    sel = ~amb
+    assert sel.sum() > 100
+    assert np.array_equal(gvis[j[sel], g_of_o[d[sel]]], bit[sel])
+    s = compare_paths(res.paths(), osim, room.eps_r, room.sigma, room.scat)
+    assert s["matched"] > 100, s
+
+
+def test_office_subset_full_pipeline(office, office_gpu, office_orc):
+    """Office scene (2M points), 16 RX, 5 interactions, visibility capture,
+    diffuse on, on a 4,000-ray sample of the 1M Fibonacci launch."""
+    ids = np.arange(0, 1_000_000, 250, dtype=np.uint32)
+    kp = dict(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1_000_000, rep_tries=8)
+    res = office_gpu.trace(office.tx, office.rx, nrt.default_trace_params(**kp), ray_subset=ids)
+    delta = 1e-5 * office.diag
+    osim = oracle.OracleSim(office_orc, office.tx, office.rx,
+                            oracle.SimParams(delta=delta, **kp), ray_ids=ids.astype(np.int64))
+    h = compare_hits(res.hits(), osim.hits(), delta, sens=osim.hit_sens())
+    print("office subset hits:", h)
+    assert h["mismatch"] == 0, h
+    assert h["max_dq"] < delta, h
+    s = compare_paths(res.paths(), osim, office.eps_r, office.sigma, office.scat)
+    print("office subset:", h, s)
+    assert s["matched"] > 0.8 * s["keys"], s
+    assert s["max_dP_common"] < 1e-4
+
+
+def test_office_full_launch_sampled_rays(office, office_gpu, office_orc):
+    """The full 1M-ray launch (the benchmarked configuration): 1,000 sampled
+    rays' hit records against the oracle, and a bit-identical re-run."""
+    kp = dict(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1_000_000, rep_tries=8)
+    p = nrt.default_trace_params(**kp)
+    res = office_gpu.trace(office.tx, office.rx, p)
+    rng = np.random.default_rng(7)
+    rows = np.sort(rng.choice(1_000_000, 1000, replace=False))
+    g = res.hits()
+    gs = {k: v[rows] for k, v in g.items()}
+    delta = 1e-5 * office.diag
+    osim = oracle.OracleSim(office_orc, office.tx, office.rx,
+                            oracle.SimParams(delta=delta, validate=0, **kp),
+                            ray_ids=rows.astype(np.int64))
+    h = compare_hits(gs, osim.hits(), delta, sens=osim.hit_sens())
+    assert h["mismatch"] == 0, h
+    print("office full launch:", h)
+    P1 = res.paths()
+    res2 = office_gpu.trace(office.tx, office.rx, p)
+    P2 = res2.paths()
+    for k in ("key_hi", "key_lo", "rep", "a", "tau"):
+        assert np.array_equal(P1[k], P2[k]), k
+    assert np.array_equal(res.power(), res2.power())
