@@ -227,6 +227,27 @@ nrt_status nrt_field_read(const nrt_result* result, float* power_per_rx);
 nrt_status nrt_backward(nrt_result* result, const float* dL_dpower, float* g_eps, float* g_sigma,
                         float* g_scat);
 
+/* Same gradient as nrt_backward, computed without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate -- work recorded into a CUDA graph (no cudaMalloc during
+ * stream capture), real-time loops that must avoid the allocator's
+ * device-wide synchronisation, hosts whose framework owns all device memory.
+ *   dL_dpower : device float[n_rx]  (input)
+ *   grad      : device float[3 * n_labels]: d/d eps_r, then d/d sigma, then
+ *               d/d S, each n_labels long (output, caller-allocated)
+ * The reduction's partial sums use a fixed 6 MiB array inside the library
+ * (1024 blocks x 3 x 256 doubles) that every GPU loading the library keeps
+ * until the process exits.  The first call on a device resolves that array's
+ * device address (cudaGetSymbolAddress with the device current); make that
+ * first call before any stream capture.  All calls share the array: calls
+ * whose kernels overlap on the GPU (several streams or contexts at once)
+ * race on it.  Each call writes every partial it reads, so no state carries
+ * over between calls.  Work is enqueued on the context stream; the call does
+ * not synchronise.
+ * Errors: NRT_ERR_ARG for NULL pointers or more than 256 labels;
+ * NRT_ERR_STATE before nrt_set_materials; NRT_ERR_CUDA. */
+nrt_status nrt_backward_noalloc(nrt_result* result, const float* dL_dpower, float* grad);
+
 #ifdef __cplusplus
 }
 #endif

@@ -99,6 +99,7 @@ def lib():
         L.nrt_field.argtypes = [_P]
         L.nrt_field_read.argtypes = [_P, _P]
         L.nrt_backward.argtypes = [_P, _P, _P, _P, _P]
+        L.nrt_backward_noalloc.argtypes = [_P, _P, _P]
         L.nrt_destroy.restype = None
     return _lib
 
@@ -295,6 +296,13 @@ class Result:
         self.ctx._check(lib().nrt_backward(self._h, _np_ptr(g), _np_ptr(ge), _np_ptr(gs),
                                            _np_ptr(gc)))
         return ge, gs, gc
+
+    def backward_noalloc(self, dL_dP_dev, grad_dev):
+        """nrt_backward_noalloc on caller-owned device buffers (torch CUDA tensors):
+        dL_dP_dev float32[n_rx] in, grad_dev float32[3 * n_labels] out.  Enqueued on
+        the context stream; call ctx.sync() before reading grad_dev."""
+        self.ctx._check(lib().nrt_backward_noalloc(self._h, _P(dL_dP_dev.data_ptr()),
+                                                   _P(grad_dev.data_ptr())))
 
     def close(self):
         if getattr(self, "_h", None):
