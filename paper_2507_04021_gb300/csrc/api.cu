@@ -20,6 +20,10 @@ void free_dev(void* p) {
 // keeps its scene alive, so the *_free calls may come in any order.
 void ctx_release(nrt_ctx* ctx) {
   if (--ctx->refs > 0) return;
+  if (ctx->order) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->order);
+  }
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }

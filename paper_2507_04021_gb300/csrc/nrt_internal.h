@@ -17,6 +17,9 @@ struct nrt_ctx {
   bool own_stream = false;
   std::string last_error;
   int sm_count = 0;
+  // launch order of the full Fibonacci launch, cached per ray count
+  uint32_t* order = nullptr;
+  int64_t order_n = 0;
 };
 
 struct nrt_scene {
@@ -90,6 +93,8 @@ enum Ctr : int {
   kCtrKeysSpec,
   kCtrKeysDiff,
   kCtrPending,
+  kCtrLeaders,
+  kCtrCompact,
   kCtrCount
 };
 

@@ -169,12 +169,13 @@ __global__ void __launch_bounds__(kTraceThreads)
 // (Sec. II-B: the ray count stays constant).  The next cast skips the DPS
 // just hit.
 __global__ void __launch_bounds__(kTraceThreads)
-    trace_kernel(SceneView S, SimConst C, const uint32_t* __restrict__ ray_of_row, Records R,
-                 unsigned long long* ctr) {
+    trace_kernel(SceneView S, SimConst C, const uint32_t* __restrict__ ray_of_row,
+                 const uint32_t* __restrict__ order, Records R, unsigned long long* ctr) {
   NRT_STACK_DECL
   unsigned long long segs = 0;
-  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < R.n_rows;
-       row += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < R.n_rows;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = order ? order[t] : t;
     const uint32_t ray = ray_of_row ? ray_of_row[row] : (uint32_t)row;
     float3 d = fib_dir(ray, C.n_rays);
     float3 o = C.tx;
@@ -207,18 +208,16 @@ __global__ void __launch_bounds__(kTraceThreads)
 // ---------------------------------------------------------------- candidates
 struct EmitArgs {
   Table T;
-  KeyState K;
-  uint32_t* spec_list;
-  uint32_t* diff_list;
-  uint2* cand;
-  int64_t cand_cap;
-  int64_t key_cap;
+  uint2* cand;              // candidates (slot, row) at per-ray offsets
+  const uint32_t* cand_off; // [launch index] first candidate of the ray
+  uint32_t* cand_cnt;       // [launch index] candidates of the ray (count pass)
 };
 
-__device__ __forceinline__ void insert_key(const EmitArgs& A, uint64_t hi, uint64_t lo,
-                                           uint32_t row, bool diffuse, unsigned long long* ctr) {
-  uint32_t* err = (uint32_t*)(ctr + kCtrErr);
-  const uint64_t f = key_fp(hi, lo);
+// Hash insert by one lane on behalf of the lanes holding the same key (same
+// fingerprint); returns the slot.  No shared counters are touched: key ids
+// are assigned afterwards from the table's occupancy.
+__device__ __forceinline__ uint64_t insert_key(const EmitArgs& A, uint64_t hi, uint64_t lo,
+                                               uint64_t f, unsigned long long* ctr) {
   uint64_t slot = f & A.T.mask;
   int probe = 0;
   for (; probe < kMaxProbe; ++probe) {
@@ -226,64 +225,97 @@ __device__ __forceinline__ void insert_key(const EmitArgs& A, uint64_t hi, uint6
     if (prev == 0ull) {
       A.T.hi[slot] = hi;
       A.T.lo[slot] = lo;
-      const unsigned long long k = atomicAdd(ctr + kCtrKeys, 1ull);
-      if ((int64_t)k >= A.key_cap) {
-        atomicOr(err, kErrHashFull);
-        return;
-      }
-      A.T.kid[slot] = (uint32_t)k;
-      A.K.slot[k] = (uint32_t)slot;
-      if (diffuse) A.diff_list[atomicAdd(ctr + kCtrKeysDiff, 1ull)] = (uint32_t)k;
-      else A.spec_list[atomicAdd(ctr + kCtrKeysSpec, 1ull)] = (uint32_t)k;
       break;
     }
     if (prev == (unsigned long long)f) break;
     slot = (slot + 1) & A.T.mask;
   }
   if (probe == kMaxProbe) {
-    atomicOr(err, kErrHashFull);
-    return;
+    atomicOr((uint32_t*)(ctr + kCtrErr), kErrHashFull);
+    return ~0ull;
   }
   if (probe > 64) atomicMax(ctr + kCtrProbeMax, (unsigned long long)probe);
-  atomicMin(A.T.minrow + slot, row);
-  const unsigned long long c = warp_inc(ctr + kCtrCands);
-  if ((int64_t)c < A.cand_cap) A.cand[c] = make_uint2((uint32_t)slot, row);
-  else atomicOr(err, kErrCandFull);
+  return slot;
 }
 
-// kCount: only count candidates (sizes the hash table); otherwise insert.
+// One candidate per lane with pred set (all lanes of the warp call this
+// together).  Lanes with equal keys are merged first: one lane inserts the
+// key and records the group's lowest row; every lane still stores its own
+// (slot, row) candidate, at its ray's next candidate position.  kCount only
+// counts candidates per ray and per-warp distinct keys (an upper bound on
+// the table's keys).
 template <bool kCount>
-__global__ void emit_kernel(SceneView S, SimConst C, const float4* __restrict__ rx, Records R,
-                            const uint32_t* __restrict__ vis, EmitArgs A,
-                            unsigned long long* ctr) {
-  unsigned long long cnt = 0;
-  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < R.n_rows;
-       row += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void warp_emit(const EmitArgs& A, bool pred, uint64_t hi, uint64_t lo,
+                                          uint32_t row, unsigned long long* ctr, uint32_t& n_mine,
+                                          unsigned long long& n_lead) {
+  const unsigned act = __ballot_sync(0xFFFFFFFFu, pred);
+  if (!act || !pred) return;
+  const int lane = threadIdx.x & 31;
+  const uint64_t f = key_fp(hi, lo);
+  const unsigned peers = __match_any_sync(act, f);
+  const int leader = __ffs(peers) - 1;
+  if (kCount) {
+    ++n_mine;
+    if (lane == leader) ++n_lead;
+    return;
+  }
+  const uint32_t minrow = __reduce_min_sync(peers, row);
+  uint64_t slot = 0;
+  if (lane == leader) {
+    slot = insert_key(A, hi, lo, f, ctr);
+    if (slot != ~0ull) atomicMin(A.T.minrow + slot, minrow);
+  }
+  slot = __shfl_sync(peers, slot, leader);
+  if (slot == ~0ull) return;
+  A.cand[n_mine++] = make_uint2((uint32_t)slot, row);
+}
+
+// Candidates of every ray (Sec. II-B): a warp walks 32 rays in launch order
+// (neighbouring directions), bounce by bounce and RX by RX in lockstep, so
+// that rays that found the same key merge before touching the hash table.
+template <bool kCount>
+__global__ void __launch_bounds__(256)
+    emit_kernel(SceneView S, SimConst C, const float4* __restrict__ rx, Records R,
+                const uint32_t* __restrict__ vis, const uint32_t* __restrict__ order, EmitArgs A,
+                unsigned long long* ctr) {
+  unsigned long long n_lead = 0, n_total = 0;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < R.n_rows; base += n_warps * 32) {
+    const int64_t t = base + lane;
+    const bool active = t < R.n_rows;
+    const uint32_t row = active ? (order ? order[t] : (uint32_t)t) : 0u;
+    uint32_t n_mine = (!kCount && active) ? A.cand_off[t] : 0u;
     uint16_t lab[kMaxDepth];
+    bool alive = active;
     for (int s = 0; s < C.max_depth; ++s) {
-      const int64_t a = R.at(s, row);
-      const int2 ri = R.i[a];
-      if (ri.x < 0) break;
+      int2 ri = make_int2(-1, 0);
+      float4 qq = make_float4(0.f, 0.f, 0.f, 0.f), dd = qq;
+      if (alive) {
+        const int64_t a = R.at(s, row);
+        ri = R.i[a];
+        if (ri.x >= 0) {
+          qq = R.q[a];
+          dd = R.d[a];
+        }
+      }
+      alive = alive && ri.x >= 0;
+      if (!__any_sync(0xFFFFFFFFu, alive)) break;
       const int k = s + 1;
       lab[s] = (uint16_t)(ri.y & 0xFFFF);
-      const float4 qq = R.q[a];
-      const float4 dd = R.d[a];
       if (C.capture == NRT_CAPTURE_VIS) {
         const int dps = __float_as_int(dd.w);
-        int vox[3];
-        voxel_of(S, xyz(qq), vox);
+        int vox[3] = {0, 0, 0};
+        if (alive) voxel_of(S, xyz(qq), vox);
         for (int j = 0; j < C.n_rx; ++j) {
-          if (!vis_bit(vis, C.vis_words, j, dps)) continue;
-          if (kCount) {
-            cnt += 1 + (C.diffuse ? 1 : 0);
-            continue;
-          }
-          uint64_t hi, lo;
-          make_key(j, 0, k, lab, vox, &hi, &lo);
-          insert_key(A, hi, lo, (uint32_t)row, false, ctr);
+          const bool v = alive && vis_bit(vis, C.vis_words, j, dps);
+          uint64_t hi = 0, lo = 0;
+          if (v) make_key(j, 0, k, lab, vox, &hi, &lo);
+          warp_emit<kCount>(A, v, hi, lo, row, ctr, n_mine, n_lead);
           if (C.diffuse) {
-            make_key(j, 1, k, lab, vox, &hi, &lo);
-            insert_key(A, hi, lo, (uint32_t)row, true, ctr);
+            if (v) make_key(j, 1, k, lab, vox, &hi, &lo);
+            warp_emit<kCount>(A, v, hi, lo, row, ctr, n_mine, n_lead);
           }
         }
       } else {
@@ -291,27 +323,72 @@ __global__ void emit_kernel(SceneView S, SimConst C, const float4* __restrict__ 
         const float3 o = xyz(qq);
         const float3 dir = xyz(dd);
         float t_end = __int_as_float(0x7f800000);
-        if (s + 1 < C.n_seg) {
+        if (alive && s + 1 < C.n_seg) {
           const int64_t b = R.at(s + 1, row);
           if (R.i[b].x >= 0) t_end = R.q[b].w;
         }
         for (int j = 0; j < C.n_rx; ++j) {
-          const float3 r = xyz(__ldg(rx + j));
-          const float ts = fminf(fmaxf(dot3(r - o, dir), 0.0f), t_end);
-          const float3 p = o + ts * dir - r;
-          if (dot3(p, p) > C.r_rx2) continue;
-          if (kCount) {
-            ++cnt;
-            continue;
+          bool v = false;
+          if (alive) {
+            const float3 r = xyz(__ldg(rx + j));
+            const float ts = fminf(fmaxf(dot3(r - o, dir), 0.0f), t_end);
+            const float3 p = o + ts * dir - r;
+            v = dot3(p, p) <= C.r_rx2;
           }
-          uint64_t hi, lo;
-          make_key(j, 0, k, lab, nullptr, &hi, &lo);
-          insert_key(A, hi, lo, (uint32_t)row, false, ctr);
+          uint64_t hi = 0, lo = 0;
+          if (v) make_key(j, 0, k, lab, nullptr, &hi, &lo);
+          warp_emit<kCount>(A, v, hi, lo, row, ctr, n_mine, n_lead);
         }
       }
     }
+    if (kCount && active) {
+      A.cand_cnt[t] = n_mine;
+      n_total += n_mine;
+    }
   }
-  if (kCount) count_add(ctr + kCtrCands, cnt);
+  if (kCount) {
+    count_add(ctr + kCtrCands, n_total);
+    count_add(ctr + kCtrLeaders, n_lead);
+  }
+}
+
+// Key ids from the table's occupancy: specular keys first, then diffuse.
+__global__ void slot_flags_kernel(Table T, int64_t cap, uint32_t* __restrict__ fs,
+                                  uint32_t* __restrict__ fd) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const bool used = T.fp[i] != 0ull;
+    const bool diff = used && ((T.hi[i] >> 55) & 1ull);
+    fs[i] = used && !diff;
+    fd[i] = diff;
+  }
+}
+
+__global__ void slot_assign_kernel(Table T, int64_t cap, const uint32_t* __restrict__ fs,
+                                   const uint32_t* __restrict__ fd, const uint32_t* __restrict__ os,
+                                   const uint32_t* __restrict__ od, uint32_t n_spec,
+                                   uint32_t* __restrict__ key_slot, uint64_t* __restrict__ sort_key,
+                                   uint32_t* __restrict__ sort_val,
+                                   const uint32_t* __restrict__ launch_pos) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (!fs[i] && !fd[i]) continue;
+    const uint32_t kid = fs[i] ? os[i] : n_spec + od[i];
+    T.kid[i] = kid;
+    key_slot[kid] = (uint32_t)i;
+    // validation order: launch position of the key's lowest row, so that a
+    // warp validates keys found by neighbouring rays
+    const uint32_t m = T.minrow[i];
+    sort_key[kid] = launch_pos ? launch_pos[m] : m;
+    sort_val[kid] = kid;
+  }
+}
+
+__global__ void inverse_order_kernel(const uint32_t* __restrict__ order, int64_t n,
+                                     uint32_t* __restrict__ pos) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x)
+    pos[order[t]] = (uint32_t)t;
 }
 
 // Every candidate re-derives its key from the hit records and compares it
@@ -356,7 +433,7 @@ __device__ __forceinline__ void finish_key(const ValArgs& A, uint32_t kid, bool 
   uint32_t* err = (uint32_t*)(ctr + kCtrErr);
   if (valid) {
     A.K.status[kid] = 1;
-    const unsigned long long p = atomicAdd(ctr + kCtrPaths, 1ull);
+    const unsigned long long p = warp_inc(ctr + kCtrPaths);
     if ((int64_t)p >= A.path_cap) {
       atomicOr(err, kErrPathFull);
       return;
@@ -370,7 +447,7 @@ __device__ __forceinline__ void finish_key(const ValArgs& A, uint32_t kid, bool 
     A.K.status[kid] = 2;
   } else {
     A.K.status[kid] = 0;
-    A.next_list[atomicAdd(ctr + A.next_ctr, 1ull)] = kid;
+    A.next_list[warp_inc(ctr + A.next_ctr)] = kid;
   }
 }
 
@@ -578,14 +655,18 @@ __global__ void next_reset_kernel(const uint32_t* __restrict__ list, int64_t n, 
     T.next[K.slot[list[i]]] = kNone;
 }
 
+// Next candidate per pending key: the smallest row above the one just tried.
+// Candidates of keys that are settled, or not above their key's current row,
+// are never needed again, so the survivors are compacted for the next round.
 __global__ void next_scan_kernel(const uint2* __restrict__ cand, int64_t n_cand, KeyState K,
-                                 Table T) {
+                                 Table T, uint2* __restrict__ out, unsigned long long* ctr) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cand;
        c += (int64_t)gridDim.x * blockDim.x) {
     const uint2 e = cand[c];
     const uint32_t kid = T.kid[e.x];
-    if (K.status[kid] != 0) continue;
-    if (e.y > K.cur[kid]) atomicMin(T.next + e.x, e.y);
+    if (K.status[kid] != 0 || e.y <= K.cur[kid]) continue;
+    atomicMin(T.next + e.x, e.y);
+    out[warp_inc(ctr + kCtrCompact)] = e;
   }
 }
 
@@ -600,7 +681,7 @@ __global__ void next_apply_kernel(const uint32_t* __restrict__ list, int64_t n, 
       K.status[kid] = 2;
     } else {
       K.cur[kid] = nx;
-      out_list[atomicAdd(ctr + out_ctr, 1ull)] = kid;
+      out_list[warp_inc(ctr + out_ctr)] = kid;
     }
   }
 }
@@ -627,11 +708,45 @@ __global__ void path_sortkey_kernel(const PathRec* __restrict__ p, int64_t n,
   }
 }
 
-__global__ void rx_hist_kernel(const uint64_t* __restrict__ key, int64_t n,
-                               unsigned long long* __restrict__ cnt) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(cnt + (key[i] >> 36), 1ull);
+// per-RX range of the sorted paths: lower bounds of (j << 36) and ((j+1) << 36)
+__global__ void rx_range_kernel(const uint64_t* __restrict__ key, int64_t n, int n_rx,
+                                unsigned long long* __restrict__ cnt) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_rx) return;
+  auto lower = [&](uint64_t v) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (key[mid] < v) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo;
+  };
+  cnt[j] = (unsigned long long)(lower((uint64_t)(j + 1) << 36) - lower((uint64_t)j << 36));
+}
+
+// Launch order: rows (rays in ascending id) sorted along a Morton curve of
+// their Fibonacci-lattice cell (z band, azimuth), so that the 32 rays of a
+// warp leave in neighbouring directions.
+__device__ __forceinline__ uint32_t spread2(uint32_t x) {
+  x &= 0xFFFF;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+
+__global__ void order_key_kernel(const uint32_t* __restrict__ ray_of_row, int64_t n, int64_t n_rays,
+                                 uint64_t* __restrict__ key, uint32_t* __restrict__ val) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t r = ray_of_row ? ray_of_row[c] : (uint64_t)c;
+    const uint32_t zb = (uint32_t)min((2 * r + 1) * 32768ull / (uint64_t)n_rays, 65535ull);
+    const uint32_t pb = (uint32_t)((r * 0x61C8864680B583EBull) >> 48);
+    key[c] = (uint64_t)(spread2(zb) | (spread2(pb) << 1));
+    val[c] = (uint32_t)c;
+  }
 }
 
 __global__ void path_gather_kernel(const PathRec* __restrict__ src, const uint32_t* __restrict__ idx,
@@ -848,35 +963,75 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
   TRY(cudaMemsetAsync(r->rec_i, 0xFF, nrec * sizeof(int2), st));
   Records R{r->rec_q, r->rec_n, r->rec_d, r->rec_i, n};
 
+  // launch order (cached for the full launch)
+  const uint32_t* order = nullptr;
+  uint32_t* order_tmp = nullptr;
+  if (subset_d || ctx->order_n != n) {
+    uint64_t *ok, *tk;
+    uint32_t *ov, *tv;
+    TRY(cudaMallocAsync(&ok, n * 8, st));
+    TRY(cudaMallocAsync(&tk, n * 8, st));
+    TRY(cudaMallocAsync(&ov, n * 4, st));
+    TRY(cudaMallocAsync(&tv, n * 4, st));
+    order_key_kernel<<<blocks_for(n, 256, sm), 256, 0, st>>>(subset_d, n, r->p.n_rays, ok, ov); count_launch();
+    radix_sort_pairs(ok, ov, tk, tv, n, 32, st);
+    cudaFreeAsync(ok, st);
+    cudaFreeAsync(tk, st);
+    cudaFreeAsync(tv, st);
+    if (subset_d) {
+      order_tmp = ov;
+    } else {
+      if (ctx->order) cudaFreeAsync(ctx->order, st);
+      ctx->order = ov;
+      ctx->order_n = n;
+    }
+  }
+  order = subset_d ? order_tmp : ctx->order;
+
   // LOS paths are written after the candidate count fixes the path buffer;
   // the cast itself is cheap and done then.
   TRY(cudaEventRecord(r->ev[2], st));
-  trace_kernel<<<blocks_for(n, kTraceThreads, sm), kTraceThreads, 0, st>>>(S, C, subset_d, R, ctr); count_launch();
+  trace_kernel<<<blocks_for(n, kTraceThreads, sm), kTraceThreads, 0, st>>>(S, C, subset_d, order, R, ctr); count_launch();
   TRY(cudaEventRecord(r->ev[3], st));
 
-  // candidate count -> table sizes
+  // candidate count per ray -> candidate offsets and table size
   EmitArgs A{};
-  emit_kernel<true><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, A, ctr); count_launch();
-  unsigned long long n_cand_h = 0;
-  TRY(cudaMemcpyAsync(&n_cand_h, ctr + kCtrCands, 8, cudaMemcpyDeviceToHost, st));
+  uint32_t *cand_cnt, *cand_off;
+  TRY(cudaMallocAsync(&cand_cnt, n * 4, st));
+  TRY(cudaMallocAsync(&cand_off, n * 4, st));
+  A.cand_cnt = cand_cnt;
+  emit_kernel<true><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, ctr); count_launch();
+  scan_exclusive(cand_cnt, cand_off, n, st);
+  unsigned long long cnt2[2] = {0, 0};
+  TRY(cudaMemcpyAsync(&cnt2[0], ctr + kCtrCands, 8, cudaMemcpyDeviceToHost, st));
+  TRY(cudaMemcpyAsync(&cnt2[1], ctr + kCtrLeaders, 8, cudaMemcpyDeviceToHost, st));
   TRY(cudaStreamSynchronize(st));
-  TRY(cudaMemsetAsync(ctr + kCtrCands, 0, 8, st));
-  int64_t cand_cap = r->p.cand_capacity > 0 ? r->p.cand_capacity : (int64_t)n_cand_h;
-  cand_cap = std::max<int64_t>(cand_cap, 1);
+  const unsigned long long n_cand_h = cnt2[0], n_lead_h = cnt2[1];
+  if (r->p.cand_capacity > 0 && (int64_t)n_cand_h > r->p.cand_capacity) {
+    ctx->last_error = "more path candidates than cand_capacity";
+    return NRT_ERR_OVERFLOW;
+  }
+  if (n_cand_h >= 0xFFFFFFFFull) {
+    ctx->last_error = "more than 2^32 path candidates";
+    return NRT_ERR_OVERFLOW;
+  }
+  const int64_t cand_cap = std::max<int64_t>((int64_t)n_cand_h, 1);
+  // distinct keys <= per-warp distinct keys (n_lead) <= candidates
+  const int64_t key_bound = std::max<int64_t>((int64_t)n_lead_h, 1);
   int64_t cap = r->p.key_capacity;
   if (cap <= 0) {
     cap = 1 << 12;
-    while (cap < cand_cap + cand_cap / 2) cap <<= 1;
+    while (cap < key_bound + key_bound / 2) cap <<= 1;
   }
   if (cap & (cap - 1)) {
     ctx->last_error = "key_capacity must be a power of two";
     return NRT_ERR_ARG;
   }
-  const int64_t key_cap = std::min<int64_t>(cap, cand_cap);
+  const int64_t key_cap = std::min<int64_t>(cap, key_bound);
   Table T{};
   KeyState K{};
   uint32_t *spec_list, *diff_list, *list2_s, *list2_d;
-  uint2* cand;
+  uint2 *cand, *cand2;
   TRY(cudaMallocAsync(&T.fp, cap * 8, st));
   TRY(cudaMallocAsync(&T.hi, cap * 8, st));
   TRY(cudaMallocAsync(&T.lo, cap * 8, st));
@@ -895,21 +1050,66 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
   TRY(cudaMallocAsync(&list2_s, key_cap * 4, st));
   TRY(cudaMallocAsync(&list2_d, key_cap * 4, st));
   TRY(cudaMallocAsync(&cand, cand_cap * sizeof(uint2), st));
+  TRY(cudaMallocAsync(&cand2, cand_cap * sizeof(uint2), st));
   A.T = T;
-  A.K = K;
-  A.spec_list = spec_list;
-  A.diff_list = diff_list;
   A.cand = cand;
-  A.cand_cap = cand_cap;
-  A.key_cap = key_cap;
-  emit_kernel<false><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, A, ctr); count_launch();
-  unsigned long long hc[kCtrCount];
-  TRY(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  A.cand_off = cand_off;
+  emit_kernel<false><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, ctr); count_launch();
+  cudaFreeAsync(cand_cnt, st);
+  cudaFreeAsync(cand_off, st);
+
+  // key ids from the occupied slots (specular first), in launch order of
+  // each key's lowest row within each type
+  uint32_t *fs, *fd, *os, *od, *pos = nullptr, *tv;
+  uint64_t *sk0, *tk0;
+  uint32_t* sv0;
+  TRY(cudaMallocAsync(&fs, cap * 4, st));
+  TRY(cudaMallocAsync(&fd, cap * 4, st));
+  TRY(cudaMallocAsync(&os, cap * 4, st));
+  TRY(cudaMallocAsync(&od, cap * 4, st));
+  slot_flags_kernel<<<blocks_for(cap, 256, sm), 256, 0, st>>>(T, cap, fs, fd); count_launch();
+  scan_exclusive(fs, os, cap, st);
+  scan_exclusive(fd, od, cap, st);
+  uint32_t tail[4];
+  TRY(cudaMemcpyAsync(&tail[0], os + cap - 1, 4, cudaMemcpyDeviceToHost, st));
+  TRY(cudaMemcpyAsync(&tail[1], fs + cap - 1, 4, cudaMemcpyDeviceToHost, st));
+  TRY(cudaMemcpyAsync(&tail[2], od + cap - 1, 4, cudaMemcpyDeviceToHost, st));
+  TRY(cudaMemcpyAsync(&tail[3], fd + cap - 1, 4, cudaMemcpyDeviceToHost, st));
   TRY(cudaStreamSynchronize(st));
-  const int64_t n_cand = std::min<int64_t>((int64_t)hc[kCtrCands], cand_cap);
-  const int64_t n_keys = std::min<int64_t>((int64_t)hc[kCtrKeys], key_cap);
-  int64_t n_spec = std::min<int64_t>((int64_t)hc[kCtrKeysSpec], key_cap);
-  int64_t n_diff = std::min<int64_t>((int64_t)hc[kCtrKeysDiff], key_cap);
+  int64_t n_spec = (int64_t)tail[0] + tail[1];
+  int64_t n_diff = (int64_t)tail[2] + tail[3];
+  const int64_t n_keys = n_spec + n_diff;
+  if (n_keys > key_cap) {
+    ctx->last_error = "hash table holds more keys than its bound";
+    return NRT_ERR_OVERFLOW;
+  }
+  TRY(cudaMemsetAsync(ctr + kCtrKeys, 0, 8, st));
+  const unsigned long long nk_h = (unsigned long long)n_keys;
+  TRY(cudaMemcpyAsync(ctr + kCtrKeys, &nk_h, 8, cudaMemcpyHostToDevice, st));
+  TRY(cudaMallocAsync(&sk0, std::max<int64_t>(n_keys, 1) * 8, st));
+  TRY(cudaMallocAsync(&tk0, std::max<int64_t>(n_keys, 1) * 8, st));
+  TRY(cudaMallocAsync(&sv0, std::max<int64_t>(n_keys, 1) * 4, st));
+  TRY(cudaMallocAsync(&tv, std::max<int64_t>(n_keys, 1) * 4, st));
+  if (order) {
+    TRY(cudaMallocAsync(&pos, n * 4, st));
+    inverse_order_kernel<<<blocks_for(n, 256, sm), 256, 0, st>>>(order, n, pos); count_launch();
+  }
+  slot_assign_kernel<<<blocks_for(cap, 256, sm), 256, 0, st>>>(T, cap, fs, fd, os, od, (uint32_t)n_spec,
+                                                               K.slot, sk0, sv0, pos); count_launch();
+  if (n_spec > 1) radix_sort_pairs(sk0, sv0, tk0, tv, n_spec, 32, st);
+  if (n_diff > 1) radix_sort_pairs(sk0 + n_spec, sv0 + n_spec, tk0, tv, n_diff, 32, st);
+  if (n_spec) TRY(cudaMemcpyAsync(spec_list, sv0, n_spec * 4, cudaMemcpyDeviceToDevice, st));
+  if (n_diff) TRY(cudaMemcpyAsync(diff_list, sv0 + n_spec, n_diff * 4, cudaMemcpyDeviceToDevice, st));
+  cudaFreeAsync(fs, st);
+  cudaFreeAsync(fd, st);
+  cudaFreeAsync(os, st);
+  cudaFreeAsync(od, st);
+  cudaFreeAsync(sk0, st);
+  cudaFreeAsync(tk0, st);
+  cudaFreeAsync(sv0, st);
+  cudaFreeAsync(tv, st);
+  if (pos) cudaFreeAsync(pos, st);
+  int64_t n_cand = (int64_t)n_cand_h;
   verify_kernel<<<blocks_for(n_cand, 256, sm), 256, 0, st>>>(S, C, R, T, cand, n_cand, ctr); count_launch();
   key_init_kernel<<<blocks_for(n_keys, 256, sm), 256, 0, st>>>(n_keys, K, T); count_launch();
 
@@ -931,6 +1131,7 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
   V.paths = raw;
   V.path_cap = r->path_cap;
   uint32_t *cur_s = spec_list, *cur_d = diff_list, *nxt_s = list2_s, *nxt_d = list2_d;
+  uint2 *cand_cur = cand, *cand_nxt = cand2;
   for (int round = 0; round < r->p.rep_tries && (n_spec > 0 || n_diff > 0); ++round) {
     TRY(cudaMemsetAsync(ctr + kCtrKeysSpec, 0, 16, st));  // spec + diff next counters
     if (n_spec > 0) {
@@ -954,7 +1155,9 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
     // next candidate rows for the keys still pending
     if (n_spec) next_reset_kernel<<<blocks_for(n_spec, 256, sm), 256, 0, st>>>(nxt_s, n_spec, K, T); count_launch();
     if (n_diff) next_reset_kernel<<<blocks_for(n_diff, 256, sm), 256, 0, st>>>(nxt_d, n_diff, K, T); count_launch();
-    next_scan_kernel<<<blocks_for(n_cand, 256, sm), 256, 0, st>>>(cand, n_cand, K, T); count_launch();
+    TRY(cudaMemsetAsync(ctr + kCtrCompact, 0, 8, st));
+    next_scan_kernel<<<blocks_for(n_cand, 256, sm), 256, 0, st>>>(cand_cur, n_cand, K, T, cand_nxt, ctr); count_launch();
+    std::swap(cand_cur, cand_nxt);
     TRY(cudaMemsetAsync(ctr + kCtrKeysSpec, 0, 16, st));
     if (n_spec)
       next_apply_kernel<<<blocks_for(n_spec, 256, sm), 256, 0, st>>>(nxt_s, n_spec, K, T, cur_s, ctr,
@@ -962,14 +1165,18 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
     if (n_diff)
       next_apply_kernel<<<blocks_for(n_diff, 256, sm), 256, 0, st>>>(nxt_d, n_diff, K, T, cur_d, ctr,
                                                                     kCtrKeysDiff); count_launch();
+    unsigned long long ncmp = 0;
     TRY(cudaMemcpyAsync(nn, ctr + kCtrKeysSpec, 16, cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(&ncmp, ctr + kCtrCompact, 8, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
     n_spec = (int64_t)nn[0];
     n_diff = (int64_t)nn[1];
+    n_cand = (int64_t)ncmp;
   }
   TRY(cudaEventRecord(r->ev[5], st));
 
   // deterministic order of the paths, then the field
+  unsigned long long hc[kCtrCount];
   TRY(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
   TRY(cudaStreamSynchronize(st));
   r->n_paths = std::min<int64_t>((int64_t)hc[kCtrPaths], r->path_cap);
@@ -991,7 +1198,7 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
   TRY(cudaMallocAsync(&rxc, r->n_rx * 8, st));
   TRY(cudaMemsetAsync(rxc, 0, r->n_rx * 8, st));
   if (np > 0) {
-    rx_hist_kernel<<<blocks_for(np, 256, sm), 256, 0, st>>>(sk, np, rxc); count_launch();
+    rx_range_kernel<<<(r->n_rx + 63) / 64, 64, 0, st>>>(sk, np, r->n_rx, rxc); count_launch();
   }
   std::vector<unsigned long long> rxh(r->n_rx);
   TRY(cudaMemcpyAsync(rxh.data(), rxc, r->n_rx * 8, cudaMemcpyDeviceToHost, st));
@@ -1021,10 +1228,12 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
   cudaFreeAsync(list2_s, st);
   cudaFreeAsync(list2_d, st);
   cudaFreeAsync(cand, st);
+  cudaFreeAsync(cand2, st);
+  if (order_tmp) cudaFreeAsync(order_tmp, st);
   TRY(cudaMallocAsync(&r->path_a, std::max<int64_t>(np, 1) * sizeof(float2), st));
   TRY(cudaMallocAsync(&r->power, r->n_rx * sizeof(double), st));
-  nrt_status fs = run_field(r);
-  if (fs != NRT_OK) return fs;
+  nrt_status fst = run_field(r);
+  if (fst != NRT_OK) return fst;
   TRY(cudaEventRecord(r->ev[6], st));
   TRY(cudaEventRecord(r->ev[7], st));
   TRY(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
