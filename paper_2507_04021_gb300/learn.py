@@ -1,0 +1,113 @@
+"""Learning per-label materials through the hand-written adjoint (Sec. III-B).
+
+The paper learns relative permittivity, conductivity and scattering
+coefficient per material label with Adam and activations that keep them in
+their valid ranges.  Here the forward is the library's field of stored paths
+(``nrt_field``: path geometry does not depend on the materials, so nothing is
+re-traced) and the backward is ``nrt_backward``.  The loss is the mean squared
+error of the per-receiver path gain in dB over one or more simulations.
+
+Activations (a reading of "appropriate activation functions"):
+eps_r = 1 + softplus(u), sigma = exp(v), S = sigmoid(w).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+
+class PowerFn(torch.autograd.Function):
+    """P[r, j] = received power of simulation r at receiver j, as a function of
+    per-label (eps_r, sigma, S).  ``backend`` provides two callables:
+    ``forward(eps, sigma, scat) -> np.ndarray [R, M]`` and
+    ``backward(eps, sigma, scat, dL_dP [R, M]) -> (g_eps, g_sigma, g_scat)``."""
+
+    @staticmethod
+    def forward(ctx, eps, sig, sca, backend):
+        e = eps.detach().cpu().numpy().astype(np.float64)
+        s = sig.detach().cpu().numpy().astype(np.float64)
+        c = sca.detach().cpu().numpy().astype(np.float64)
+        P = backend.forward(e, s, c)
+        ctx.backend = backend
+        ctx.mats = (e, s, c)
+        ctx.dev = eps.device
+        return torch.as_tensor(np.asarray(P, np.float64), device=eps.device)
+
+    @staticmethod
+    def backward(ctx, gP):
+        e, s, c = ctx.mats
+        ge, gs, gc = ctx.backend.backward(e, s, c, gP.detach().cpu().numpy().astype(np.float64))
+        t = lambda a: torch.as_tensor(np.asarray(a, np.float64), device=ctx.dev)  # noqa: E731
+        return t(ge), t(gs), t(gc), None
+
+
+class LibnrtBackend:
+    """Field and adjoint of stored paths through libnrt (one scene, R results)."""
+
+    def __init__(self, scene, results):
+        self.scene = scene
+        self.results = list(results)
+
+    def forward(self, eps, sig, sca):
+        self.scene.set_materials(eps.astype(np.float32), sig.astype(np.float32),
+                                 sca.astype(np.float32))
+        out = []
+        for r in self.results:
+            r.field()
+            out.append(r.power().astype(np.float64))
+        return np.stack(out)
+
+    def backward(self, eps, sig, sca, dL_dP):
+        ge = np.zeros(len(eps))
+        gs = np.zeros(len(eps))
+        gc = np.zeros(len(eps))
+        for r, g in zip(self.results, dL_dP):
+            a, b, c = r.backward(g.astype(np.float32))
+            ge += a
+            gs += b
+            gc += c
+        return ge, gs, gc
+
+
+def to_params(eps, sig, sca):
+    """Unconstrained parameters (u, v, w) for given materials."""
+    eps = np.asarray(eps, np.float64)
+    return (np.log(np.expm1(eps - 1.0)), np.log(np.asarray(sig, np.float64)),
+            np.log(np.asarray(sca, np.float64) / (1.0 - np.asarray(sca, np.float64))))
+
+
+def from_params(u, v, w):
+    return 1.0 + torch.nn.functional.softplus(u), torch.exp(v), torch.sigmoid(w)
+
+
+@dataclass
+class Fit:
+    eps: np.ndarray
+    sigma: np.ndarray
+    scat: np.ndarray
+    loss: list = field(default_factory=list)
+
+
+def recover_materials(backend, target_db, init, steps=200, lr=0.05) -> Fit:
+    """Adam on the per-RX dB-gain MSE; target_db [R, M]; init = (eps, sigma, S)."""
+    u0, v0, w0 = to_params(*init)
+    u = torch.tensor(u0, requires_grad=True)
+    v = torch.tensor(v0, requires_grad=True)
+    w = torch.tensor(w0, requires_grad=True)
+    tgt = torch.as_tensor(np.asarray(target_db, np.float64))
+    opt = torch.optim.Adam([u, v, w], lr=lr)
+    hist = []
+    for _ in range(steps):
+        opt.zero_grad()
+        eps, sig, sca = from_params(u, v, w)
+        P = PowerFn.apply(eps, sig, sca, backend)
+        G = 10.0 * torch.log10(P)
+        loss = torch.mean((G - tgt) ** 2)
+        loss.backward()
+        opt.step()
+        hist.append(float(loss.detach()))
+    with torch.no_grad():
+        eps, sig, sca = from_params(u, v, w)
+    return Fit(eps.numpy(), sig.numpy(), sca.numpy(), hist)
