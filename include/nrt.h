@@ -227,6 +227,53 @@ nrt_status nrt_field_read(const nrt_result* result, float* power_per_rx);
 nrt_status nrt_backward(nrt_result* result, const float* dL_dpower, float* g_eps, float* g_sigma,
                         float* g_scat);
 
+/* ---------------------------------------------------------------- batches
+ * Many TX-RX pairs in one simulation: the robot-trajectory workload (a TX
+ * moving along a path, one fixed RX, an uneven ray budget per position).
+ * Pair j launches its own Fibonacci set of budget[j] rays from tx[j]; the
+ * path keys carry j in their RX field, so paths, counts, power, field and
+ * adjoint are per pair (pass n_rx = n_pairs-sized arrays to the readout
+ * calls).  The trace runs as ONE persistent launch whose warps pull work items
+ * of `packet` rays from a queue, so uneven budgets balance themselves; the
+ * visibility matrix of the fixed RX is computed once. */
+typedef struct {
+  int32_t packet;     /* rays per work item of the persistent trace: 32, 64 or 128 */
+  int32_t schedule;   /* 0 static grid-stride, 1 persistent work queue */
+  int32_t use_graph;  /* 1: record the whole simulation into a CUDA graph; the
+                         result then serves nrt_batch_replay */
+  int32_t reserved;
+} nrt_batch_opts;
+
+/* tx: host float[n_pairs][3]; rx: host float[3] (the fixed receiver);
+ * budget: host int64[n_pairs], each in [1, 2^31); n_pairs in [1, 256];
+ * params->capture must be NRT_CAPTURE_VIS (params->n_rays is ignored).
+ * With use_graph the call runs once to size every buffer (25% headroom),
+ * records the simulation into a CUDA graph and replays it once.
+ * Errors: NRT_ERR_ARG, NRT_ERR_OOM, NRT_ERR_OVERFLOW, NRT_ERR_CUDA. */
+nrt_status nrt_trace_batch(nrt_scene* scene, const float* tx, const float* rx,
+                           const int64_t* budget, int n_pairs, const nrt_trace_params* params,
+                           const nrt_batch_opts* opts, nrt_result** out);
+
+/* Replay the recorded graph with new TX positions (host float[n_pairs][3], or
+ * NULL to keep them); the budgets and the RX are those of the recording.
+ * The result's paths/counts/power are replaced.  Errors: NRT_ERR_STATE
+ * without use_graph; NRT_ERR_OVERFLOW when a replay needs more than the
+ * recorded capacities (rebuild the batch). */
+nrt_status nrt_batch_replay(nrt_result* result, const float* tx);
+
+/* Device timestamps of the last batch run: pair_ms[j] = time from the start
+ * of the persistent trace to the moment pair j's last work item finished
+ * (host double[n_pairs]); total_ms = device time of the whole simulation
+ * (graph replay or normal run). */
+nrt_status nrt_batch_times(const nrt_result* result, double* pair_ms, float* total_ms);
+
+/* Autotuner: time the batch trace phase for each (packet, schedule) pair
+ * (host int32[n_cfg] each; `repeats` timed runs, the minimum kept) into
+ * host float ms[n_cfg]; the fastest configuration is stored in the result
+ * (used by later replays only after a rebuild) and returned in *best. */
+nrt_status nrt_autotune_batch(nrt_result* result, const int32_t* packets, const int32_t* schedules,
+                              int n_cfg, int repeats, float* ms, int32_t* best);
+
 /* Same gradient as nrt_backward, computed without allocating device memory.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate -- work recorded into a CUDA graph (no cudaMalloc during

@@ -295,6 +295,7 @@ nrt_status nrt_trace(nrt_scene* s, const float* tx, const float* rx, int n_rx,
   s->refs++;
   r->p = *p;
   r->n_rx = n_rx;
+  r->n_rx_phys = n_rx;
   memcpy(r->tx, tx, sizeof(r->tx));
   std::vector<float4> rxh(n_rx);
   for (int j = 0; j < n_rx; ++j) rxh[j] = make_float4(rx[3 * j], rx[3 * j + 1], rx[3 * j + 2], 0.f);
@@ -353,11 +354,18 @@ nrt_status nrt_trace(nrt_scene* s, const float* tx, const float* rx, int n_rx,
 void nrt_result_free(nrt_result* r) {
   if (!r) return;
   cudaStreamSynchronize(r->scene->ctx->stream);
+  free_work(r);
   free_dev(r->rx);
   free_dev(r->ray_of_row);
+  free_dev(r->tx_pair);
+  free_dev(r->pair_start);
+  free_dev(r->pair_rays);
+  free_dev(r->chunk_start);
+  free_dev(r->stamps);
+  free_dev(r->queue);
   cudaStream_t st = r->scene->ctx->stream;
   void* pool_ptrs[] = {r->rec_q, r->rec_n, r->rec_d, r->rec_i, r->vis, r->paths,
-                       r->path_a, r->power, r->ctr};
+                       r->path_a, r->power, r->ctr, r->rx_start_d, r->rx_count_d};
   for (void* q : pool_ptrs)
     if (q) cudaFreeAsync(q, st);
   for (int e = 0; e < 8; ++e)
@@ -380,6 +388,11 @@ nrt_status nrt_result_counts(const nrt_result* r, int64_t* n_paths_per_rx, nrt_c
 nrt_status nrt_result_times(const nrt_result* r, float* ms) {
   if (!r || !ms) return NRT_ERR_ARG;
   nrt_ctx* ctx = r->scene->ctx;
+  if (!r->ev[7]) {  // graph replay: one device time for the whole simulation
+    for (int k = 0; k < 8; ++k) ms[k] = 0.0f;
+    ms[6] = r->graph_ms;
+    return NRT_OK;
+  }
   NRT_CUDA_TRY(ctx, cudaEventSynchronize(r->ev[7]));
   auto el = [&](int a, int b) {
     float t = 0.f;
@@ -411,10 +424,15 @@ nrt_status nrt_paths_read(const nrt_result* r, const nrt_path_view* v) {
       NRT_CUDA_TRY(ctx, cudaMemcpyAsync(a.data(), r->path_a, np * sizeof(float2),
                                         cudaMemcpyDeviceToHost, st));
   }
-  std::vector<uint32_t> rays;
+  std::vector<uint32_t> rays, pstart;
   if (r->ray_of_row && np > 0) {
     rays.resize(r->n_traced);
     NRT_CUDA_TRY(ctx, cudaMemcpyAsync(rays.data(), r->ray_of_row, r->n_traced * 4,
+                                      cudaMemcpyDeviceToHost, st));
+  }
+  if (r->n_pairs > 0) {
+    pstart.resize(r->n_pairs + 1);
+    NRT_CUDA_TRY(ctx, cudaMemcpyAsync(pstart.data(), r->pair_start, pstart.size() * 4,
                                       cudaMemcpyDeviceToHost, st));
   }
   NRT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
@@ -423,7 +441,10 @@ nrt_status nrt_paths_read(const nrt_result* r, const nrt_path_view* v) {
     const int k = (p.jtk >> 9) & 7;
     if (v->key_hi) v->key_hi[i] = p.hi;
     if (v->key_lo) v->key_lo[i] = p.lo;
-    if (v->rep) v->rep[i] = (p.rep == kNone) ? kNone : (r->ray_of_row ? rays[p.rep] : p.rep);
+    uint32_t rep = p.rep;
+    if (rep != kNone && r->ray_of_row) rep = rays[rep];
+    if (rep != kNone && r->n_pairs > 0) rep -= pstart[p.jtk & 0xFF];  // ray id within its pair
+    if (v->rep) v->rep[i] = rep;
     if (v->rx) v->rx[i] = (int32_t)(p.jtk & 0xFF);
     if (v->type) v->type[i] = (int32_t)((p.jtk >> 8) & 1);
     if (v->k) v->k[i] = k;
@@ -493,6 +514,188 @@ nrt_status nrt_vis_read(const nrt_result* r, uint32_t* bits) {
   NRT_CUDA_TRY(ctx, cudaMemcpyAsync(bits, r->vis, (size_t)r->n_rx * r->vis_words * 4,
                                     cudaMemcpyDeviceToHost, ctx->stream));
   NRT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return NRT_OK;
+}
+
+nrt_status nrt_trace_batch(nrt_scene* s, const float* tx, const float* rx, const int64_t* budget,
+                           int n_pairs, const nrt_trace_params* p, const nrt_batch_opts* opts,
+                           nrt_result** out) {
+  if (!s || !tx || !rx || !budget || !p || !out) return NRT_ERR_ARG;
+  nrt_ctx* ctx = s->ctx;
+  if (n_pairs < 1 || n_pairs > 256) {
+    ctx->last_error = "n_pairs must be in [1, 256]";
+    return NRT_ERR_ARG;
+  }
+  if (p->capture != NRT_CAPTURE_VIS || p->max_depth < 1 || p->max_depth > kMaxDepth ||
+      p->rep_tries < 1 || p->rep_tries > 32 || p->kappa < 0 || !(p->freq > 0.f)) {
+    ctx->last_error = "invalid batch trace parameters (visibility capture required)";
+    return NRT_ERR_ARG;
+  }
+  nrt_batch_opts o{64, 1, 0, 0};
+  if (opts) o = *opts;
+  if ((o.packet != 32 && o.packet != 64 && o.packet != 128) || (o.schedule != 0 && o.schedule != 1)) {
+    ctx->last_error = "packet must be 32, 64 or 128 and schedule 0 or 1";
+    return NRT_ERR_ARG;
+  }
+  int64_t total = 0, maxb = 0;
+  std::vector<uint32_t> start(n_pairs + 1), cstart(n_pairs + 1);
+  std::vector<float4> txp(n_pairs);
+  for (int j = 0; j < n_pairs; ++j) {
+    if (budget[j] < 1 || budget[j] >= ((int64_t)1 << 31)) {
+      ctx->last_error = "ray budgets must be in [1, 2^31)";
+      return NRT_ERR_ARG;
+    }
+    for (int k = 0; k < 3; ++k)
+      if (!std::isfinite(tx[3 * j + k])) return NRT_ERR_ARG;
+    start[j] = (uint32_t)total;
+    cstart[j] = (uint32_t)(j == 0 ? 0 : cstart[j]);
+    total += budget[j];
+    maxb = std::max(maxb, budget[j]);
+    txp[j] = make_float4(tx[3 * j], tx[3 * j + 1], tx[3 * j + 2], 0.f);
+  }
+  if (total >= ((int64_t)1 << 32) - 1) {
+    ctx->last_error = "total rays of a batch must stay below 2^32";
+    return NRT_ERR_ARG;
+  }
+  start[n_pairs] = (uint32_t)total;
+  uint64_t ch = 0;
+  for (int j = 0; j < n_pairs; ++j) {
+    cstart[j] = (uint32_t)ch;
+    ch += (uint64_t)((budget[j] + o.packet - 1) / o.packet);
+  }
+  cstart[n_pairs] = (uint32_t)ch;
+  NRT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  nrt_result* r = new (std::nothrow) nrt_result();
+  if (!r) return NRT_ERR_OOM;
+  r->scene = s;
+  s->refs++;
+  r->p = *p;
+  r->p.n_rays = maxb;
+  r->n_pairs = n_pairs;
+  r->n_rx = n_pairs;
+  r->n_rx_phys = 1;
+  r->n_traced = total;
+  r->packet = o.packet;
+  r->schedule = o.schedule;
+  memcpy(r->tx, tx, sizeof(r->tx));
+  const float4 rxh = make_float4(rx[0], rx[1], rx[2], 0.f);
+  nrt_status rc = NRT_OK;
+  auto fail = [&](nrt_status e) {
+    nrt_result_free(r);
+    return e;
+  };
+  if (cudaMalloc(&r->rx, sizeof(float4)) != cudaSuccess ||
+      cudaMalloc(&r->tx_pair, n_pairs * sizeof(float4)) != cudaSuccess ||
+      cudaMalloc(&r->pair_start, (n_pairs + 1) * 4) != cudaSuccess ||
+      cudaMalloc(&r->pair_rays, n_pairs * 8) != cudaSuccess ||
+      cudaMalloc(&r->chunk_start, (n_pairs + 1) * 4) != cudaSuccess ||
+      cudaMalloc(&r->stamps, (n_pairs + 1) * 8) != cudaSuccess ||
+      cudaMalloc(&r->queue, (n_pairs + 1) * 8) != cudaSuccess) {
+    ctx->last_error = "device allocation failed";
+    return fail(NRT_ERR_OOM);
+  }
+  cudaMemcpyAsync(r->rx, &rxh, sizeof(float4), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(r->tx_pair, txp.data(), n_pairs * sizeof(float4), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(r->pair_start, start.data(), (n_pairs + 1) * 4, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(r->pair_rays, budget, n_pairs * 8, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(r->chunk_start, cstart.data(), (n_pairs + 1) * 4, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(r->stamps, 0, (n_pairs + 1) * 8, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return fail(NRT_ERR_CUDA);
+  rc = run_trace(r, nullptr);
+  if (rc != NRT_OK) return fail(rc);
+  if (o.use_graph) {
+    r->vis_shared = true;  // the fixed RX's visibility matrix is kept, not recomputed
+    rc = batch_graph_build(r);
+    if (rc == NRT_OK) rc = batch_graph_replay(r, nullptr);
+    if (rc != NRT_OK) return fail(rc);
+  }
+  *out = r;
+  return NRT_OK;
+}
+
+nrt_status nrt_batch_replay(nrt_result* r, const float* tx) {
+  if (!r) return NRT_ERR_ARG;
+  if (!r->graph) {
+    r->scene->ctx->last_error = "batch was not recorded into a graph (use_graph = 0)";
+    return NRT_ERR_STATE;
+  }
+  return batch_graph_replay(r, tx);
+}
+
+nrt_status nrt_batch_times(const nrt_result* r, double* pair_ms, float* total_ms) {
+  if (!r || r->n_pairs <= 0) return NRT_ERR_ARG;
+  nrt_ctx* ctx = r->scene->ctx;
+  std::vector<unsigned long long> t(r->n_pairs + 1);
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(t.data(), r->stamps, t.size() * 8, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (pair_ms)
+    for (int j = 0; j < r->n_pairs; ++j)
+      pair_ms[j] = t[1 + j] >= t[0] ? (double)(t[1 + j] - t[0]) * 1e-6 : 0.0;
+  if (total_ms) {
+    float ms[8];
+    nrt_result_times(r, ms);
+    *total_ms = ms[6];
+  }
+  return NRT_OK;
+}
+
+nrt_status nrt_autotune_batch(nrt_result* r, const int32_t* packets, const int32_t* schedules,
+                              int n_cfg, int repeats, float* ms, int32_t* best) {
+  if (!r || !packets || !schedules || !ms || n_cfg < 1 || r->n_pairs <= 0) return NRT_ERR_ARG;
+  nrt_ctx* ctx = r->scene->ctx;
+  if (r->graph) {
+    ctx->last_error = "autotune a batch before recording it into a graph";
+    return NRT_ERR_STATE;
+  }
+  const int keep_p = r->packet, keep_s = r->schedule;
+  float best_ms = 1e30f;
+  int best_i = 0;
+  std::vector<uint32_t> cstart(r->n_pairs + 1);
+  std::vector<uint32_t> start(r->n_pairs + 1);
+  NRT_CUDA_TRY(ctx, cudaMemcpy(start.data(), r->pair_start, (r->n_pairs + 1) * 4,
+                               cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n_cfg; ++i) {
+    if ((packets[i] != 32 && packets[i] != 64 && packets[i] != 128) ||
+        (schedules[i] != 0 && schedules[i] != 1))
+      return NRT_ERR_ARG;
+    uint64_t ch = 0;
+    for (int j = 0; j < r->n_pairs; ++j) {
+      cstart[j] = (uint32_t)ch;
+      ch += (uint64_t)((start[j + 1] - start[j] + packets[i] - 1) / packets[i]);
+    }
+    cstart[r->n_pairs] = (uint32_t)ch;
+    NRT_CUDA_TRY(ctx, cudaMemcpy(r->chunk_start, cstart.data(), cstart.size() * 4,
+                                 cudaMemcpyHostToDevice));
+    r->packet = packets[i];
+    r->schedule = schedules[i];
+    float t_min = 1e30f;
+    for (int k = 0; k < std::max(repeats, 1); ++k) {
+      float t = 0.f;
+      nrt_status rc = run_trace_phase(r, &t);
+      if (rc != NRT_OK) return rc;
+      t_min = std::min(t_min, t);
+    }
+    ms[i] = t_min;
+    if (t_min < best_ms) {
+      best_ms = t_min;
+      best_i = i;
+    }
+  }
+  (void)keep_p;
+  (void)keep_s;
+  r->packet = packets[best_i];
+  r->schedule = schedules[best_i];
+  uint64_t ch = 0;
+  for (int j = 0; j < r->n_pairs; ++j) {
+    cstart[j] = (uint32_t)ch;
+    ch += (uint64_t)((start[j + 1] - start[j] + r->packet - 1) / r->packet);
+  }
+  cstart[r->n_pairs] = (uint32_t)ch;
+  NRT_CUDA_TRY(ctx, cudaMemcpy(r->chunk_start, cstart.data(), cstart.size() * 4,
+                               cudaMemcpyHostToDevice));
+  if (best) *best = best_i;
   return NRT_OK;
 }
 

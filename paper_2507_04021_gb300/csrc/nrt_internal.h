@@ -49,32 +49,49 @@ struct nrt_scene {
 struct nrt_result {
   nrt_scene* scene = nullptr;
   nrt_trace_params p{};
-  int n_rx = 0;
+  int n_rx = 0;        // receivers of the path keys and of the power (batch: pairs)
+  int n_rx_phys = 0;   // physical receivers
+  int n_pairs = 0;     // > 0: batch of TX-RX pairs
   int64_t n_traced = 0;  // rows (rays traced)
   int n_seg = 0;
   float tx[3] = {0, 0, 0};
   // device arrays
-  float4* rx = nullptr;          // [n_rx]
+  float4* rx = nullptr;            // physical receivers
   uint32_t* ray_of_row = nullptr;  // nullptr: row == ray id
+  float4* tx_pair = nullptr;       // batch: TX of each pair
+  uint32_t* pair_start = nullptr;  // batch: first row of each pair [n_pairs + 1]
+  int64_t* pair_rays = nullptr;    // batch: Fibonacci N of each pair
+  uint32_t* chunk_start = nullptr; // batch: first work chunk of each pair [n_pairs + 1]
+  unsigned long long* stamps = nullptr;  // batch: [0] trace start, [1 + j] pair j traced (ns)
+  unsigned long long* queue = nullptr;   // batch: work queue head + per-pair chunks left
+  int packet = 64;     // rays per work item of the persistent trace
+  int schedule = 1;    // 0 static grid-stride, 1 persistent work queue
   float4* rec_q = nullptr;   // [n_seg][n_traced]: q.xyz, segment length
   float4* rec_n = nullptr;   // normal.xyz, cos_in
   float4* rec_d = nullptr;   // outgoing direction.xyz, dps (bits)
   int2* rec_i = nullptr;     // point index (-1 miss), labels
-  uint32_t* vis = nullptr;   // [n_rx][vis_words]
+  uint32_t* vis = nullptr;   // [n_rx_phys][vis_words]
   int64_t vis_words = 0;
+  bool vis_shared = false;   // vis owned by a batch plan
   // paths (sorted)
   int64_t n_paths = 0;
   int64_t path_cap = 0;
   void* paths = nullptr;     // PathRec[path_cap]
-  float2* path_a = nullptr;  // [n_paths]
+  float2* path_a = nullptr;  // [path_cap]
   double* power = nullptr;   // [n_rx]
-  int64_t* rx_count = nullptr;  // [n_rx] paths per RX (host copy)
+  int64_t* rx_start_d = nullptr;  // [n_rx] device ranges of the sorted paths
+  int64_t* rx_count_d = nullptr;
+  int64_t* rx_count = nullptr;  // host copies
   int64_t* rx_start = nullptr;
   // counters
   unsigned long long* ctr = nullptr;  // device counters
   nrt_counters counters{};
   cudaEvent_t ev[8] = {};
   bool field_done = false;
+  // graph mode: pipeline buffers and the instantiated graph, kept for replays
+  void* work = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  float graph_ms = 0.0f;
 };
 
 namespace nrt {
@@ -120,13 +137,25 @@ SceneView scene_view(const nrt_scene* s);
 
 // kernels launched on this host thread since the last reset
 int64_t& launch_counter();
-inline void count_launch(int64_t n = 1) { launch_counter() += n; }
+inline void count_launch_n(int64_t n = 1) { launch_counter() += n; }
+#ifdef NRT_CHECK_BOUNDS
+// debug builds: synchronise after every launch and report the first failing
+// launch site on stderr
+void debug_launch_check(const char* file, int line);
+#define count_launch(...) (count_launch_n(__VA_ARGS__), debug_launch_check(__FILE__, __LINE__))
+#else
+#define count_launch(...) count_launch_n(__VA_ARGS__)
+#endif
 
 // scene.cu
 nrt_status build_scene(nrt_scene* s, const float* pos_d, const float* nrm_d, const uint16_t* surf_d,
                        const uint8_t* mat_d);
 // trace.cu / paths.cu
 nrt_status run_trace(nrt_result* r, const uint32_t* subset_d);
+nrt_status batch_graph_build(nrt_result* r);
+nrt_status run_trace_phase(nrt_result* r, float* ms);
+nrt_status batch_graph_replay(nrt_result* r, const float* tx_host);
+void free_work(nrt_result* r);
 nrt_status run_field(nrt_result* r);
 nrt_status run_backward(nrt_result* r, const float* dL_dP, float* g_eps, float* g_sig,
                         float* g_sca);

@@ -1,6 +1,8 @@
 // Device primitives: exclusive scan and a stable LSD radix sort of
 // (uint64 key, uint32 value) pairs.  Used by the scene build (Morton order of
 // the points) and to put paths in a deterministic order.
+#include <cstdio>
+
 #include "nrt_internal.h"
 
 namespace nrt {
@@ -52,6 +54,19 @@ int64_t& launch_counter() {
   static thread_local int64_t c = 0;
   return c;
 }
+
+#ifdef NRT_CHECK_BOUNDS
+void debug_launch_check(const char* file, int line) {
+  static bool reported = false;
+  const cudaError_t e = cudaDeviceSynchronize();
+  const cudaError_t l = cudaPeekAtLastError();
+  if (!reported && (e != cudaSuccess || l != cudaSuccess)) {
+    reported = true;
+    fprintf(stderr, "[nrt debug] launch at %s:%d (launch #%lld): %s / %s\n", file, line,
+            (long long)launch_counter(), cudaGetErrorString(e), cudaGetErrorString(l));
+  }
+}
+#endif
 
 void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t st) {
   if (n <= 0) return;

@@ -30,6 +30,53 @@ namespace {
 constexpr int kTraceThreads = 128;
 constexpr int kMaxProbe = 4096;
 
+}  // namespace
+
+// Debug builds (-DNRT_CHECK_BOUNDS): computed indices are range-checked; the
+// first violation is recorded (kernel code << 48 | index) and the access
+// skipped, so that an indexing fault shows up as a report, not a GPU fault.
+struct DbgCaps {
+  int64_t table, keys, cand, paths, rows, nrx;
+};
+#ifdef NRT_CHECK_BOUNDS
+__device__ DbgCaps g_dbg_caps;
+__device__ unsigned long long g_dbg_word;
+#define NRT_GUARD(cond, code, val)                                                           \
+  if (!(cond)) {                                                                             \
+    atomicCAS(&g_dbg_word, 0ull,                                                             \
+              ((unsigned long long)(code) << 48) | ((unsigned long long)(val)&0xFFFFFFFFFFFFull)); \
+    continue;                                                                                \
+  }
+// record-only variant for warp-synchronous code: evaluates to cond
+#define NRT_OK_IDX(cond, code, val)                                                            \
+  ((cond) ? true                                                                             \
+          : (atomicCAS(&g_dbg_word, 0ull,                                                    \
+                       ((unsigned long long)(code) << 48) |                                  \
+                           ((unsigned long long)(val)&0xFFFFFFFFFFFFull)),                   \
+             false))
+#else
+#define NRT_GUARD(cond, code, val)
+#define NRT_OK_IDX(cond, code, val) true
+#endif
+
+// Debug builds only: the capacities the guards compare against.
+inline cudaError_t dbg_set_caps(int64_t table, int64_t keys, int64_t cand, int64_t paths,
+                                int64_t rows, int64_t nrx, cudaStream_t st) {
+#ifdef NRT_CHECK_BOUNDS
+  DbgCaps dc{table, keys, cand, paths, rows, nrx};
+  const unsigned long long zero = 0;
+  cudaError_t e = cudaMemcpyToSymbolAsync(g_dbg_caps, &dc, sizeof(dc), 0, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && table < 0)
+    e = cudaMemcpyToSymbolAsync(g_dbg_word, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
+  return e;
+#else
+  (void)table, (void)keys, (void)cand, (void)paths, (void)rows, (void)nrx, (void)st;
+  return cudaSuccess;
+#endif
+}
+
+namespace {
+
 struct Table {
   unsigned long long* fp;  // 0 = empty
   uint64_t* hi;
@@ -76,7 +123,30 @@ struct SimConst {
   float lambda;
   int64_t n_rays;
   int64_t vis_words;
+  // batch mode: rows are grouped by pair (pair j owns rows pair_start[j] ..
+  // pair_start[j+1]-1, a Fibonacci launch of pair_rays[j] rays from
+  // tx_pair[j]); one shared physical RX; the RX field of a key holds j.
+  int batch;
+  int n_pairs;
+  const float4* tx_pair;
+  const uint32_t* pair_start;
+  const int64_t* pair_rays;
 };
+
+__device__ __forceinline__ int pair_of_row(const SimConst& C, uint32_t row) {
+  int lo = 0, hi = C.n_pairs;  // largest j with pair_start[j] <= row
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(C.pair_start + mid) <= row) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// TX of key/pair j (batch) or the simulation's TX
+__device__ __forceinline__ float3 tx_of(const SimConst& C, int j) {
+  return C.batch ? xyz(__ldg(C.tx_pair + j)) : C.tx;
+}
 
 __device__ __forceinline__ bool vis_bit(const uint32_t* vis, int64_t words, int j, int d) {
   return (__ldg(vis + (int64_t)j * words + (d >> 5)) >> (d & 31)) & 1u;
@@ -140,15 +210,16 @@ __global__ void __launch_bounds__(kTraceThreads)
                unsigned long long* ctr, int64_t path_cap) {
   NRT_STACK_DECL
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= C.n_rx) return;
-  const float3 r = xyz(rx[j]);
-  const float3 v = r - C.tx;
+  if (j >= (C.batch ? C.n_pairs : C.n_rx)) return;
+  const float3 r = xyz(rx[C.batch ? 0 : j]);
+  const float3 txp = tx_of(C, j);
+  const float3 v = r - txp;
   const float s = len3(v);
-  const Hit h = cast_ray<true>(S, C.tx, (1.0f / s) * v, -1, C.t_min, s, false, my_stk, my_tstk,
+  const Hit h = cast_ray<true>(S, txp, (1.0f / s) * v, -1, C.t_min, s, false, my_stk, my_tstk,
                                kTraceThreads, err);
   atomicAdd(ctr + kCtrLosCasts, 1ull);
   if (h.idx >= 0) return;
-  const unsigned long long p = atomicAdd(ctr + kCtrPaths, 1ull);
+  const unsigned long long p = warp_inc(ctr + kCtrPaths);
   if ((int64_t)p >= path_cap) {
     atomicOr(err, kErrPathFull);
     return;
@@ -168,6 +239,14 @@ __global__ void __launch_bounds__(kTraceThreads)
 // One ray per thread; every interaction continues as a specular reflection
 // (Sec. II-B: the ray count stays constant).  The next cast skips the DPS
 // just hit.
+__device__ __forceinline__ unsigned trace_row(const SceneView& S, const SimConst& C,
+                                              const uint32_t* __restrict__ ray_of_row,
+                                              const Records& R, int64_t row, int* stk, float* tstk,
+                                              uint32_t* err);
+
+// One ray per thread (static grid-stride schedule over the launch order);
+// every interaction continues as a specular reflection (Sec. II-B: the ray
+// count stays constant).  The next cast skips the DPS just hit.
 __global__ void __launch_bounds__(kTraceThreads)
     trace_kernel(SceneView S, SimConst C, const uint32_t* __restrict__ ray_of_row,
                  const uint32_t* __restrict__ order, Records R, unsigned long long* ctr) {
@@ -176,31 +255,8 @@ __global__ void __launch_bounds__(kTraceThreads)
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < R.n_rows;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = order ? order[t] : t;
-    const uint32_t ray = ray_of_row ? ray_of_row[row] : (uint32_t)row;
-    float3 d = fib_dir(ray, C.n_rays);
-    float3 o = C.tx;
-    int skip = -1;
-    for (int s = 0; s < C.n_seg; ++s) {
-      const Hit h = cast_ray<false>(S, o, d, skip, C.t_min, __int_as_float(0x7f800000), true,
-                                    my_stk, my_tstk, kTraceThreads, err);
-      ++segs;
-      const int64_t a = R.at(s, row);
-      if (h.idx < 0) {
-        R.i[a] = make_int2(-1, 0);
-        break;
-      }
-      const float3 q = o + h.tbar * d;
-      const float dn = dot3(d, h.n);
-      float3 dout = d - (2.0f * dn) * h.n;
-      dout = unit3(dout);
-      R.q[a] = make_float4(q.x, q.y, q.z, h.tbar);
-      R.n[a] = make_float4(h.n.x, h.n.y, h.n.z, fabsf(dn));
-      R.d[a] = make_float4(dout.x, dout.y, dout.z, __int_as_float(h.dps));
-      R.i[a] = make_int2(h.idx, (int)h.labels);
-      o = q;
-      d = dout;
-      skip = h.dps;
-    }
+    NRT_GUARD(row >= 0 && row < g_dbg_caps.rows, 25, row)
+    segs += trace_row(S, C, ray_of_row, R, row, my_stk, my_tstk, err);
   }
   count_add(ctr + kCtrSegments, segs);
 }
@@ -208,6 +264,7 @@ __global__ void __launch_bounds__(kTraceThreads)
 // ---------------------------------------------------------------- candidates
 struct EmitArgs {
   Table T;
+  uint64_t cand_cap;
   uint2* cand;              // candidates (slot, row) at per-ray offsets
   const uint32_t* cand_off; // [launch index] first candidate of the ray
   uint32_t* cand_cnt;       // [launch index] candidates of the ray (count pass)
@@ -267,7 +324,9 @@ __device__ __forceinline__ void warp_emit(const EmitArgs& A, bool pred, uint64_t
   }
   slot = __shfl_sync(peers, slot, leader);
   if (slot == ~0ull) return;
-  A.cand[n_mine++] = make_uint2((uint32_t)slot, row);
+  if (n_mine < A.cand_cap) A.cand[n_mine] = make_uint2((uint32_t)slot, row);
+  else atomicOr((uint32_t*)(ctr + kCtrErr), kErrCandFull);
+  ++n_mine;
 }
 
 // Candidates of every ray (Sec. II-B): a warp walks 32 rays in launch order
@@ -284,9 +343,14 @@ __global__ void __launch_bounds__(256)
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t base = warp * 32; base < R.n_rows; base += n_warps * 32) {
     const int64_t t = base + lane;
-    const bool active = t < R.n_rows;
-    const uint32_t row = active ? (order ? order[t] : (uint32_t)t) : 0u;
+    bool active = t < R.n_rows;
+    uint32_t row = active ? (order ? order[t] : (uint32_t)t) : 0u;
+    if (active && !NRT_OK_IDX(row < g_dbg_caps.rows, 26, row)) {
+      active = false;
+      row = 0u;
+    }
     uint32_t n_mine = (!kCount && active) ? A.cand_off[t] : 0u;
+    const int pair_j = (C.batch && active) ? pair_of_row(C, row) : 0;
     uint16_t lab[kMaxDepth];
     bool alive = active;
     for (int s = 0; s < C.max_depth; ++s) {
@@ -308,8 +372,10 @@ __global__ void __launch_bounds__(256)
         const int dps = __float_as_int(dd.w);
         int vox[3] = {0, 0, 0};
         if (alive) voxel_of(S, xyz(qq), vox);
-        for (int j = 0; j < C.n_rx; ++j) {
-          const bool v = alive && vis_bit(vis, C.vis_words, j, dps);
+        const int n_j = C.batch ? 1 : C.n_rx;
+        for (int jv = 0; jv < n_j; ++jv) {
+          const bool v = alive && vis_bit(vis, C.vis_words, jv, dps);
+          const int j = C.batch ? pair_j : jv;
           uint64_t hi = 0, lo = 0;
           if (v) make_key(j, 0, k, lab, vox, &hi, &lo);
           warp_emit<kCount>(A, v, hi, lo, row, ctr, n_mine, n_lead);
@@ -366,41 +432,76 @@ __global__ void slot_flags_kernel(Table T, int64_t cap, uint32_t* __restrict__ f
 
 __global__ void slot_assign_kernel(Table T, int64_t cap, const uint32_t* __restrict__ fs,
                                    const uint32_t* __restrict__ fd, const uint32_t* __restrict__ os,
-                                   const uint32_t* __restrict__ od, uint32_t n_spec,
+                                   const uint32_t* __restrict__ od,
+                                   const unsigned long long* __restrict__ counts,
                                    uint32_t* __restrict__ key_slot, uint64_t* __restrict__ sort_key,
                                    uint32_t* __restrict__ sort_val,
                                    const uint32_t* __restrict__ launch_pos) {
+  const uint32_t n_spec = (uint32_t)counts[0];  // diffuse ids follow the specular ones
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (!fs[i] && !fd[i]) continue;
     const uint32_t kid = fs[i] ? os[i] : n_spec + od[i];
+    NRT_GUARD(kid < g_dbg_caps.keys, 1, kid)
+    NRT_GUARD(T.minrow[i] < g_dbg_caps.rows, 2, T.minrow[i])
     T.kid[i] = kid;
     key_slot[kid] = (uint32_t)i;
     // validation order: launch position of the key's lowest row, so that a
     // warp validates keys found by neighbouring rays
     const uint32_t m = T.minrow[i];
-    sort_key[kid] = launch_pos ? launch_pos[m] : m;
+    sort_key[kid] = ((uint64_t)(fs[i] ? 0u : 1u) << 32) | (launch_pos ? launch_pos[m] : m);
     sort_val[kid] = kid;
+  }
+}
+
+// key counts from the scan tails: [0] specular, [1] diffuse, [2] all
+__global__ void key_count_kernel(const uint32_t* __restrict__ fs, const uint32_t* __restrict__ fd,
+                                 const uint32_t* __restrict__ os, const uint32_t* __restrict__ od,
+                                 int64_t cap, unsigned long long* __restrict__ out) {
+  const unsigned long long ns = (unsigned long long)os[cap - 1] + fs[cap - 1];
+  const unsigned long long nd = (unsigned long long)od[cap - 1] + fd[cap - 1];
+  out[0] = ns;
+  out[1] = nd;
+  out[2] = ns + nd;
+}
+
+// keys sorted by (type, launch position): specular ids first, then diffuse
+__global__ void split_lists_kernel(const uint32_t* __restrict__ sorted, int64_t cap,
+                                   const unsigned long long* __restrict__ counts,
+                                   uint32_t* __restrict__ spec, uint32_t* __restrict__ diff) {
+  const int64_t ns = (int64_t)counts[0], nk = (int64_t)counts[2];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < min(nk, cap);
+       i += (int64_t)gridDim.x * blockDim.x) {
+    NRT_GUARD(sorted[i] < g_dbg_caps.keys, 3, sorted[i])
+    if (i < ns) spec[i] = sorted[i];
+    else diff[i - ns] = sorted[i];
   }
 }
 
 __global__ void inverse_order_kernel(const uint32_t* __restrict__ order, int64_t n,
                                      uint32_t* __restrict__ pos) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x)
+       t += (int64_t)gridDim.x * blockDim.x) {
+    NRT_GUARD(order[t] < g_dbg_caps.rows, 4, order[t])
     pos[order[t]] = (uint32_t)t;
+  }
 }
 
 // Every candidate re-derives its key from the hit records and compares it
 // with the key stored in its slot: a 64-bit fingerprint collision between
 // distinct keys is reported, never silently merged.
 __global__ void verify_kernel(SceneView S, SimConst C, Records R, Table T, const uint2* __restrict__ cand,
-                              int64_t n_cand, unsigned long long* ctr) {
+                              const unsigned long long* __restrict__ n_cand_p, int64_t cap,
+                              unsigned long long* ctr) {
   uint32_t* err = (uint32_t*)(ctr + kCtrErr);
+  const int64_t n_cand = min((int64_t)*n_cand_p, cap);
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cand;
        c += (int64_t)gridDim.x * blockDim.x) {
     const uint2 e = cand[c];
+    NRT_GUARD(e.x < g_dbg_caps.table, 21, e.x)
+    NRT_GUARD(e.y < g_dbg_caps.rows, 22, e.y)
     const uint64_t hi = T.hi[e.x], lo = T.lo[e.x];
+    NRT_GUARD(((hi >> 52) & 7) >= 1 && ((hi >> 52) & 7) <= (uint64_t)C.max_depth, 23, hi >> 52)
     const int j = (int)(hi >> 56);
     const int diffuse = (int)((hi >> 55) & 1);
     const int k = (int)((hi >> 52) & 7);
@@ -423,8 +524,8 @@ struct ValArgs {
   const uint32_t* ray_of_row;
   PathRec* paths;
   int64_t path_cap;
-  uint32_t* next_list;  // keys still pending after this round
-  int next_ctr;         // counter slot for next_list
+  uint32_t* next_list;           // keys still pending after this round
+  unsigned long long* next_cnt;  // their count
 };
 
 __device__ __forceinline__ void finish_key(const ValArgs& A, uint32_t kid, bool valid,
@@ -447,7 +548,7 @@ __device__ __forceinline__ void finish_key(const ValArgs& A, uint32_t kid, bool 
     A.K.status[kid] = 2;
   } else {
     A.K.status[kid] = 0;
-    A.next_list[warp_inc(ctr + A.next_ctr)] = kid;
+    A.next_list[warp_inc(A.next_cnt)] = kid;
   }
 }
 
@@ -456,22 +557,27 @@ __device__ __forceinline__ void finish_key(const ValArgs& A, uint32_t kid, bool 
 // scatter point (skipping its DPS) reaches the RX unobstructed (Sec. II-B-1).
 __global__ void __launch_bounds__(kTraceThreads)
     validate_diffuse_kernel(SceneView S, SimConst C, ValArgs A, const uint32_t* __restrict__ list,
-                            int64_t n_list, unsigned long long* ctr) {
+                            const unsigned long long* __restrict__ n_list_p, unsigned long long* ctr) {
   NRT_STACK_DECL
   unsigned long long casts = 0;
+  const int64_t n_list = (int64_t)*n_list_p;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_list;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t kid = list[i];
+    NRT_GUARD(kid < g_dbg_caps.keys, 5, kid)
     const uint32_t slot = A.K.slot[kid];
+    NRT_GUARD(slot < g_dbg_caps.table, 6, slot)
     const uint32_t row = A.K.cur[kid];
+    NRT_GUARD(row < g_dbg_caps.rows, 7, row)
     const uint64_t hi = A.T.hi[slot];
     const int j = (int)(hi >> 56);
     const int k = (int)((hi >> 52) & 7);
+    NRT_GUARD(k >= 1 && k <= C.max_depth, 8, k)
     const int64_t a = A.R.at(k - 1, row);
     const float4 qq = A.R.q[a], nn = A.R.n[a];
     const float3 q = xyz(qq), n = xyz(nn);
     const int dps = __float_as_int(A.R.d[a].w);
-    const float3 u = xyz(A.rx[j]) - q;
+    const float3 u = xyz(A.rx[C.batch ? 0 : j]) - q;
     const float rs = len3(u);
     const float3 w = (1.0f / rs) * u;
     const float cs = dot3(n, w);
@@ -526,28 +632,33 @@ __global__ void __launch_bounds__(kTraceThreads)
 // Coordinates are taken relative to the RX to keep float magnitudes small.
 __global__ void __launch_bounds__(kTraceThreads)
     validate_specular_kernel(SceneView S, SimConst C, ValArgs A, const uint32_t* __restrict__ list,
-                             int64_t n_list, unsigned long long* ctr) {
+                             const unsigned long long* __restrict__ n_list_p, unsigned long long* ctr) {
   NRT_STACK_DECL
   unsigned long long casts = 0;
+  const int64_t n_list = (int64_t)*n_list_p;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_list;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t kid = list[i];
+    NRT_GUARD(kid < g_dbg_caps.keys, 9, kid)
     const uint32_t slot = A.K.slot[kid];
+    NRT_GUARD(slot < g_dbg_caps.table, 10, slot)
     const uint32_t row = A.K.cur[kid];
+    NRT_GUARD(row < g_dbg_caps.rows, 11, row)
     const uint64_t hi = A.T.hi[slot], lo = A.T.lo[slot];
+    NRT_GUARD(((hi >> 52) & 7) >= 1 && ((hi >> 52) & 7) <= (uint64_t)C.max_depth, 12, hi >> 52)
     const int j = (int)(hi >> 56);
     const int k = (int)((hi >> 52) & 7);
     uint32_t lab[kMaxDepth];
     for (int m = 0; m < 4; ++m) lab[m] = (uint32_t)((lo >> (16 * m)) & 0xFFFF);
     lab[4] = (uint32_t)(hi & 0xFFFF);
-    const float3 rxp = xyz(A.rx[j]);
+    const float3 rxp = xyz(A.rx[C.batch ? 0 : j]);
     float3 Pp[kMaxDepth], Pn[kMaxDepth];
     for (int m = 0; m < k; ++m) {
       const int64_t b = A.R.at(m, row);
       Pp[m] = xyz(A.R.q[b]) - rxp;
       Pn[m] = xyz(A.R.n[b]);
     }
-    const float3 txl = C.tx - rxp;
+    const float3 txl = tx_of(C, j) - rxp;
     bool valid = false;
     float3 I[kMaxDepth + 2];
     uint32_t vmats[kMaxDepth];
@@ -649,46 +760,62 @@ __global__ void __launch_bounds__(kTraceThreads)
 }
 
 // next candidate per pending key: the smallest row above the one just tried
-__global__ void next_reset_kernel(const uint32_t* __restrict__ list, int64_t n, KeyState K, Table T) {
+__global__ void next_reset_kernel(const uint32_t* __restrict__ list,
+                                  const unsigned long long* __restrict__ n_p, KeyState K, Table T) {
+  const int64_t n = (int64_t)*n_p;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
+       i += (int64_t)gridDim.x * blockDim.x) {
+    NRT_GUARD(list[i] < g_dbg_caps.keys, 13, list[i])
+    NRT_GUARD(K.slot[list[i]] < g_dbg_caps.table, 14, K.slot[list[i]])
     T.next[K.slot[list[i]]] = kNone;
+  }
 }
 
 // Next candidate per pending key: the smallest row above the one just tried.
 // Candidates of keys that are settled, or not above their key's current row,
 // are never needed again, so the survivors are compacted for the next round.
-__global__ void next_scan_kernel(const uint2* __restrict__ cand, int64_t n_cand, KeyState K,
-                                 Table T, uint2* __restrict__ out, unsigned long long* ctr) {
+__global__ void next_scan_kernel(const uint2* __restrict__ cand,
+                                 const unsigned long long* __restrict__ n_cand_p, int64_t cap,
+                                 KeyState K, Table T, uint2* __restrict__ out,
+                                 unsigned long long* out_cnt) {
+  const int64_t n_cand = min((int64_t)*n_cand_p, cap);
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cand;
        c += (int64_t)gridDim.x * blockDim.x) {
     const uint2 e = cand[c];
+    NRT_GUARD(e.x < g_dbg_caps.table, 15, e.x)
     const uint32_t kid = T.kid[e.x];
+    NRT_GUARD(kid < g_dbg_caps.keys, 16, kid)
     if (K.status[kid] != 0 || e.y <= K.cur[kid]) continue;
     atomicMin(T.next + e.x, e.y);
-    out[warp_inc(ctr + kCtrCompact)] = e;
+    out[warp_inc(out_cnt)] = e;
   }
 }
 
-__global__ void next_apply_kernel(const uint32_t* __restrict__ list, int64_t n, KeyState K,
-                                  Table T, uint32_t* __restrict__ out_list, unsigned long long* ctr,
-                                  int out_ctr) {
+__global__ void next_apply_kernel(const uint32_t* __restrict__ list,
+                                  const unsigned long long* __restrict__ n_p, KeyState K, Table T,
+                                  uint32_t* __restrict__ out_list, unsigned long long* out_cnt) {
+  const int64_t n = (int64_t)*n_p;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t kid = list[i];
+    NRT_GUARD(kid < g_dbg_caps.keys, 17, kid)
+    NRT_GUARD(K.slot[kid] < g_dbg_caps.table, 18, K.slot[kid])
     const uint32_t nx = T.next[K.slot[kid]];
     if (nx == kNone) {
       K.status[kid] = 2;
     } else {
       K.cur[kid] = nx;
-      out_list[warp_inc(ctr + out_ctr)] = kid;
+      out_list[warp_inc(out_cnt)] = kid;
     }
   }
 }
 
-__global__ void key_init_kernel(int64_t n_keys, KeyState K, Table T) {
+__global__ void key_init_kernel(const unsigned long long* __restrict__ n_keys_p, KeyState K,
+                                Table T) {
+  const int64_t n_keys = (int64_t)*n_keys_p;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_keys;
        i += (int64_t)gridDim.x * blockDim.x) {
+    NRT_GUARD(K.slot[i] < g_dbg_caps.table, 19, K.slot[i])
     K.cur[i] = T.minrow[K.slot[i]];
     K.tries[i] = 0;
     K.status[i] = 0;
@@ -697,22 +824,30 @@ __global__ void key_init_kernel(int64_t n_keys, KeyState K, Table T) {
 
 // ---------------------------------------------------------------- ordering
 // Paths ordered by (rx, type, k, representative row): deterministic output.
-__global__ void path_sortkey_kernel(const PathRec* __restrict__ p, int64_t n,
+__global__ void path_sortkey_kernel(const PathRec* __restrict__ p,
+                                    const unsigned long long* __restrict__ n_p, int64_t cap,
                                     uint64_t* __restrict__ key, uint32_t* __restrict__ idx) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+  const int64_t n = min((int64_t)*n_p, cap);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
        i += (int64_t)gridDim.x * blockDim.x) {
+    idx[i] = (uint32_t)i;
+    if (i >= n) {
+      key[i] = ~0ull;  // padding sorts last
+      continue;
+    }
     const uint32_t jtk = p[i].jtk;
     const uint64_t j = jtk & 0xFF, ty = (jtk >> 8) & 1, k = (jtk >> 9) & 7;
     key[i] = (j << 36) | (ty << 35) | (k << 32) | (uint64_t)p[i].rep;
-    idx[i] = (uint32_t)i;
   }
 }
 
 // per-RX range of the sorted paths: lower bounds of (j << 36) and ((j+1) << 36)
-__global__ void rx_range_kernel(const uint64_t* __restrict__ key, int64_t n, int n_rx,
-                                unsigned long long* __restrict__ cnt) {
+__global__ void rx_range_kernel(const uint64_t* __restrict__ key,
+                                const unsigned long long* __restrict__ n_p, int64_t cap, int n_rx,
+                                int64_t* __restrict__ start, int64_t* __restrict__ cnt) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_rx) return;
+  const int64_t n = min((int64_t)*n_p, cap);
   auto lower = [&](uint64_t v) {
     int64_t lo = 0, hi = n;
     while (lo < hi) {
@@ -722,7 +857,9 @@ __global__ void rx_range_kernel(const uint64_t* __restrict__ key, int64_t n, int
     }
     return lo;
   };
-  cnt[j] = (unsigned long long)(lower((uint64_t)(j + 1) << 36) - lower((uint64_t)j << 36));
+  const int64_t a = lower((uint64_t)j << 36);
+  start[j] = a;
+  cnt[j] = lower((uint64_t)(j + 1) << 36) - a;
 }
 
 // Launch order: rows (rays in ascending id) sorted along a Morton curve of
@@ -737,14 +874,22 @@ __device__ __forceinline__ uint32_t spread2(uint32_t x) {
   return x;
 }
 
-__global__ void order_key_kernel(const uint32_t* __restrict__ ray_of_row, int64_t n, int64_t n_rays,
-                                 uint64_t* __restrict__ key, uint32_t* __restrict__ val) {
+__global__ void order_key_kernel(SimConst C, const uint32_t* __restrict__ ray_of_row, int64_t n,
+                                 int64_t n_rays, uint64_t* __restrict__ key,
+                                 uint32_t* __restrict__ val) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t r = ray_of_row ? ray_of_row[c] : (uint64_t)c;
-    const uint32_t zb = (uint32_t)min((2 * r + 1) * 32768ull / (uint64_t)n_rays, 65535ull);
+    uint64_t r = ray_of_row ? ray_of_row[c] : (uint64_t)c;
+    uint64_t nr = (uint64_t)n_rays, hi = 0;
+    if (C.batch) {
+      const int pj = pair_of_row(C, (uint32_t)c);
+      r = (uint64_t)c - C.pair_start[pj];
+      nr = (uint64_t)C.pair_rays[pj];
+      hi = (uint64_t)pj << 32;
+    }
+    const uint32_t zb = (uint32_t)min((2 * r + 1) * 32768ull / nr, 65535ull);
     const uint32_t pb = (uint32_t)((r * 0x61C8864680B583EBull) >> 48);
-    key[c] = (uint64_t)(spread2(zb) | (spread2(pb) << 1));
+    key[c] = hi | (uint64_t)(spread2(zb) | (spread2(pb) << 1));
     val[c] = (uint32_t)c;
   }
 }
@@ -752,8 +897,10 @@ __global__ void order_key_kernel(const uint32_t* __restrict__ ray_of_row, int64_
 __global__ void path_gather_kernel(const PathRec* __restrict__ src, const uint32_t* __restrict__ idx,
                                    int64_t n, PathRec* __restrict__ dst) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
+       i += (int64_t)gridDim.x * blockDim.x) {
+    NRT_GUARD(idx[i] < g_dbg_caps.paths, 20, idx[i])
     dst[i] = src[idx[i]];
+  }
 }
 
 // ---------------------------------------------------------------- field
@@ -764,8 +911,10 @@ __device__ __forceinline__ int path_mat(const PathRec& P, int m) {
 
 // a = geo * prod_m f_m Gamma_m(theta_m): f = sqrt(1 - S^2) for a specular
 // reflection (effective roughness), f = S for the diffuse last interaction.
-__global__ void field_kernel(const PathRec* __restrict__ P, int64_t n, const float* __restrict__ mat,
-                             float freq, int pol, float2* __restrict__ a_out) {
+__global__ void field_kernel(const PathRec* __restrict__ P, const unsigned long long* __restrict__ n_p,
+                             int64_t cap, const float* __restrict__ mat, float freq, int pol,
+                             float2* __restrict__ a_out) {
+  const int64_t n = min((int64_t)*n_p, cap);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const PathRec p = P[i];
@@ -792,6 +941,7 @@ __global__ void power_kernel(const float2* __restrict__ a, const int64_t* __rest
   const int64_t b = start[j], n = count[j];
   double acc = 0.0;
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    NRT_GUARD(b + i < g_dbg_caps.paths, 24, b + i)
     const float2 v = a[b + i];
     acc += (double)v.x * v.x + (double)v.y * v.y;
   }
@@ -902,7 +1052,7 @@ inline int blocks_for(int64_t n, int threads, int sm, int per_sm = 16) {
 SimConst make_const(const nrt_result* r) {
   SimConst C;
   C.tx = make_float3(r->tx[0], r->tx[1], r->tx[2]);
-  C.n_rx = r->n_rx;
+  C.n_rx = r->n_rx_phys;
   C.max_depth = r->p.max_depth;
   C.n_seg = r->n_seg;
   C.capture = r->p.capture;
@@ -918,329 +1068,391 @@ SimConst make_const(const nrt_result* r) {
   C.lambda = (float)(299792458.0 / (double)r->p.freq);
   C.n_rays = r->p.n_rays;
   C.vis_words = r->vis_words;
+  C.batch = r->n_pairs > 0 ? 1 : 0;
+  C.n_pairs = r->n_pairs;
+  C.tx_pair = r->tx_pair;
+  C.pair_start = r->pair_start;
+  C.pair_rays = r->pair_rays;
   return C;
+}
+
+// One ray: launch, closest hit per bounce, specular continuation; the hit
+// records go to the ray's row.  Returns the segments cast.
+__device__ __forceinline__ unsigned trace_row(const SceneView& S, const SimConst& C,
+                                              const uint32_t* __restrict__ ray_of_row,
+                                              const Records& R, int64_t row, int* stk, float* tstk,
+                                              uint32_t* err) {
+  uint32_t ray = ray_of_row ? ray_of_row[row] : (uint32_t)row;
+  int64_t n_launch = C.n_rays;
+  float3 o = C.tx;
+  if (C.batch) {
+    const int pj = pair_of_row(C, (uint32_t)row);
+    ray = (uint32_t)row - __ldg(C.pair_start + pj);
+    n_launch = __ldg(C.pair_rays + pj);
+    o = xyz(__ldg(C.tx_pair + pj));
+  }
+  float3 d = fib_dir(ray, n_launch);
+  int skip = -1;
+  unsigned segs = 0;
+  for (int s = 0; s < C.n_seg; ++s) {
+    const Hit h = cast_ray<false>(S, o, d, skip, C.t_min, __int_as_float(0x7f800000), true, stk,
+                                  tstk, kTraceThreads, err);
+    ++segs;
+    const int64_t a = R.at(s, row);
+    if (h.idx < 0) {
+      R.i[a] = make_int2(-1, 0);
+      break;
+    }
+    const float3 q = o + h.tbar * d;
+    const float dn = dot3(d, h.n);
+    float3 dout = d - (2.0f * dn) * h.n;
+    dout = unit3(dout);
+    R.q[a] = make_float4(q.x, q.y, q.z, h.tbar);
+    R.n[a] = make_float4(h.n.x, h.n.y, h.n.z, fabsf(dn));
+    R.d[a] = make_float4(dout.x, dout.y, dout.z, __int_as_float(h.dps));
+    R.i[a] = make_int2(h.idx, (int)h.labels);
+    o = q;
+    d = dout;
+    skip = h.dps;
+  }
+  return segs;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Batch trace as one persistent launch: warps pull work items of `packet`
+// rays of one pair from a queue (uneven budgets balance themselves); the warp
+// that finishes a pair's last item stamps the pair's completion time.
+__global__ void __launch_bounds__(kTraceThreads)
+    trace_persistent_kernel(SceneView S, SimConst C, const uint32_t* __restrict__ order, Records R,
+                            const uint32_t* __restrict__ chunk_start, int packet,
+                            unsigned long long* queue, unsigned long long* stamps,
+                            unsigned long long* ctr) {
+  NRT_STACK_DECL
+  const int lane = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0) stamps[0] = global_ns();
+  const uint32_t n_chunks = __ldg(chunk_start + C.n_pairs);
+  unsigned long long segs = 0;
+  for (int guard = 0; guard < (1 << 30); ++guard) {
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(queue, 1ull);
+    c = __shfl_sync(0xFFFFFFFFu, c, 0);
+    if (c >= n_chunks) break;
+    int lo = 0, hi = C.n_pairs;  // pair of chunk c
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (__ldg(chunk_start + mid) <= c) lo = mid;
+      else hi = mid;
+    }
+    const int pj = lo;
+    const int64_t t0 = (int64_t)__ldg(C.pair_start + pj) + (int64_t)(c - __ldg(chunk_start + pj)) * packet;
+    const int64_t t1 = min(t0 + packet, (int64_t)__ldg(C.pair_start + pj + 1));
+    for (int64_t t = t0 + lane; t < t1; t += 32) {
+      const int64_t row = order ? order[t] : t;
+      segs += trace_row(S, C, nullptr, R, row, my_stk, my_tstk, err);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence();
+      if (atomicAdd(queue + 1 + pj, ~0ull) == 1ull) stamps[1 + pj] = global_ns();  // -1
+    }
+  }
+  count_add(ctr + kCtrSegments, segs);
+}
+
+__global__ void queue_init_kernel(const uint32_t* __restrict__ chunk_start, int n_pairs,
+                                  unsigned long long* __restrict__ queue) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j == 0) queue[0] = 0ull;
+  if (j < n_pairs) queue[1 + j] = chunk_start[j + 1] - chunk_start[j];
 }
 
 }  // namespace
 
 #define TRY(expr) NRT_CUDA_TRY(ctx, expr)
 
-// Allocate and run a full simulation into r (scene, params, rx, rows set).
-nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
+namespace {
+
+struct Caps {
+  int64_t cand = 1, keys = 1, table = 4096, paths = 1;
+};
+
+// Pipeline buffers.  Normal simulations allocate them for one call; a batch
+// graph keeps them for every replay.
+struct Work {
+  Caps caps;
+  Table T{};
+  KeyState K{};
+  uint32_t *spec_list = nullptr, *diff_list = nullptr, *list2_s = nullptr, *list2_d = nullptr;
+  uint2 *cand = nullptr, *cand2 = nullptr;
+  uint32_t *cand_cnt = nullptr, *cand_off = nullptr;
+  uint32_t *fs = nullptr, *fd = nullptr, *os = nullptr, *od = nullptr, *pos = nullptr;
+  uint64_t *sk0 = nullptr, *tk0 = nullptr;
+  uint32_t *sv0 = nullptr, *tv = nullptr;
+  PathRec* raw = nullptr;
+  uint64_t *psk = nullptr, *ptk = nullptr;
+  uint32_t *psi = nullptr, *pti = nullptr;
+  unsigned long long* cnt = nullptr;  // round counters
+  uint32_t* order = nullptr;          // launch order owned by this call (subset / batch)
+};
+
+// round counters in Work::cnt
+enum { kCntSpec = 0, kCntDiff, kCntKeys, kCntCurS, kCntCurD, kCntNxtS, kCntNxtD, kCntCandA,
+       kCntCandB, kCntN };
+
+template <class T>
+cudaError_t dalloc(T** p, int64_t n, cudaStream_t st) {
+  return cudaMallocAsync((void**)p, (size_t)std::max<int64_t>(n, 1) * sizeof(T), st);
+}
+
+nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cudaStream_t st) {
+  W.caps = c;
+  TRY(dalloc(&W.T.fp, c.table, st));
+  TRY(dalloc(&W.T.hi, c.table, st));
+  TRY(dalloc(&W.T.lo, c.table, st));
+  TRY(dalloc(&W.T.minrow, c.table, st));
+  TRY(dalloc(&W.T.kid, c.table, st));
+  TRY(dalloc(&W.T.next, c.table, st));
+  W.T.mask = (uint64_t)c.table - 1;
+  TRY(dalloc(&W.K.slot, c.keys, st));
+  TRY(dalloc(&W.K.cur, c.keys, st));
+  TRY(dalloc(&W.K.tries, c.keys, st));
+  TRY(dalloc(&W.K.status, c.keys, st));
+  TRY(dalloc(&W.spec_list, c.keys, st));
+  TRY(dalloc(&W.diff_list, c.keys, st));
+  TRY(dalloc(&W.list2_s, c.keys, st));
+  TRY(dalloc(&W.list2_d, c.keys, st));
+  TRY(dalloc(&W.cand, c.cand, st));
+  TRY(dalloc(&W.cand2, c.cand, st));
+  if (!W.cand_cnt) TRY(dalloc(&W.cand_cnt, n_rows, st));
+  if (!W.cand_off) TRY(dalloc(&W.cand_off, n_rows, st));
+  TRY(dalloc(&W.fs, c.table, st));
+  TRY(dalloc(&W.fd, c.table, st));
+  TRY(dalloc(&W.os, c.table, st));
+  TRY(dalloc(&W.od, c.table, st));
+  TRY(dalloc(&W.pos, n_rows, st));
+  TRY(dalloc(&W.sk0, c.keys, st));
+  TRY(dalloc(&W.tk0, c.keys, st));
+  TRY(dalloc(&W.sv0, c.keys, st));
+  TRY(dalloc(&W.tv, c.keys, st));
+  TRY(dalloc(&W.raw, c.paths, st));
+  TRY(dalloc(&W.psk, c.paths, st));
+  TRY(dalloc(&W.ptk, c.paths, st));
+  TRY(dalloc(&W.psi, c.paths, st));
+  TRY(dalloc(&W.pti, c.paths, st));
+  TRY(dalloc(&W.cnt, kCntN, st));
+  return NRT_OK;
+}
+
+void release_work(Work& W, cudaStream_t st) {
+  void* ptrs[] = {W.T.fp, W.T.hi, W.T.lo, W.T.minrow, W.T.kid, W.T.next, W.K.slot, W.K.cur,
+                  W.K.tries, W.K.status, W.spec_list, W.diff_list, W.list2_s, W.list2_d, W.cand,
+                  W.cand2, W.cand_cnt, W.cand_off, W.fs, W.fd, W.os, W.od, W.pos, W.sk0, W.tk0,
+                  W.sv0, W.tv, W.raw, W.psk, W.ptk, W.psi, W.pti, W.cnt, W.order};
+  for (void* q : ptrs)
+    if (q) cudaFreeAsync(q, st);
+  W = Work();
+}
+
+// Result-owned buffers: records, counters, visibility and per-RX arrays once;
+// the path buffers (re)sized to the caps when with_paths is set.
+nrt_status alloc_result(nrt_result* r, const Caps& c, bool with_paths) {
+  nrt_ctx* ctx = r->scene->ctx;
+  cudaStream_t st = ctx->stream;
+  const size_t nrec = (size_t)r->n_seg * r->n_traced;
+  if (!r->ctr) TRY(dalloc(&r->ctr, kCtrCount, st));
+  if (!r->rec_q) {
+    TRY(dalloc(&r->rec_q, nrec, st));
+    TRY(dalloc(&r->rec_n, nrec, st));
+    TRY(dalloc(&r->rec_d, nrec, st));
+    TRY(dalloc(&r->rec_i, nrec, st));
+  }
+  if (!r->vis && r->p.capture == NRT_CAPTURE_VIS)
+    TRY(dalloc(&r->vis, (int64_t)r->n_rx_phys * r->vis_words, st));
+  if (!r->power) TRY(dalloc(&r->power, r->n_rx, st));
+  if (!r->rx_start_d) TRY(dalloc(&r->rx_start_d, r->n_rx, st));
+  if (!r->rx_count_d) TRY(dalloc(&r->rx_count_d, r->n_rx, st));
+  if (with_paths) {
+    if (r->paths) cudaFreeAsync(r->paths, st);
+    if (r->path_a) cudaFreeAsync(r->path_a, st);
+    r->path_cap = c.paths;
+    TRY(dalloc((PathRec**)&r->paths, c.paths, st));
+    TRY(dalloc(&r->path_a, c.paths, st));
+  }
+  return NRT_OK;
+}
+
+// Launch order: rows sorted by the Morton code of their Fibonacci cell (batch:
+// within each pair).  The full single-TX launch is cached in the context.
+nrt_status make_order(nrt_result* r, const SimConst& C, const uint32_t* subset_d, Work& W,
+                      const uint32_t** order) {
+  nrt_ctx* ctx = r->scene->ctx;
+  cudaStream_t st = ctx->stream;
+  const int64_t n = r->n_traced;
+  const int sm = ctx->sm_count;
+  const bool cacheable = !subset_d && !C.batch;
+  if (cacheable && ctx->order_n == n && ctx->order) {
+    *order = ctx->order;
+    return NRT_OK;
+  }
+  uint64_t *ok, *tk;
+  uint32_t *ov, *tv;
+  TRY(dalloc(&ok, n, st));
+  TRY(dalloc(&tk, n, st));
+  TRY(dalloc(&ov, n, st));
+  TRY(dalloc(&tv, n, st));
+  order_key_kernel<<<blocks_for(n, 256, sm), 256, 0, st>>>(C, subset_d, n, r->p.n_rays, ok, ov); count_launch();
+  radix_sort_pairs(ok, ov, tk, tv, n, C.batch ? 40 : 32, st);
+  cudaFreeAsync(ok, st);
+  cudaFreeAsync(tk, st);
+  cudaFreeAsync(tv, st);
+  if (cacheable) {
+    if (ctx->order) cudaFreeAsync(ctx->order, st);
+    ctx->order = ov;
+    ctx->order_n = n;
+  } else {
+    W.order = ov;
+  }
+  *order = ov;
+  return NRT_OK;
+}
+
+// Everything after the candidate count, with counts kept on the device so
+// that the sequence can also be recorded into a CUDA graph.
+nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimConst& C,
+                        const uint32_t* order) {
   nrt_scene* sc = r->scene;
   nrt_ctx* ctx = sc->ctx;
   cudaStream_t st = ctx->stream;
   const int sm = ctx->sm_count;
-  const SceneView S = scene_view(sc);
   const int64_t n = r->n_traced;
-  r->n_seg = r->p.max_depth + (r->p.capture == NRT_CAPTURE_SPHERE ? 1 : 0);
-  r->vis_words = (sc->n_dps + 31) / 32;
-  SimConst C = make_const(r);
-  launch_counter() = 0;
-  for (int e = 0; e < 8; ++e) TRY(cudaEventCreate(&r->ev[e]));
-  TRY(cudaEventRecord(r->ev[0], st));
-
-  TRY(cudaMallocAsync(&r->ctr, kCtrCount * sizeof(unsigned long long), st));
-  TRY(cudaMemsetAsync(r->ctr, 0, kCtrCount * sizeof(unsigned long long), st));
+  const Caps& c = W.caps;
   unsigned long long* ctr = r->ctr;
-  const float margin = 0.8660254037844386f * sc->params.rho + sc->params.r_p;
-
-  // visibility matrix
-  if (r->p.capture == NRT_CAPTURE_VIS) {
-    TRY(cudaMallocAsync(&r->vis, (size_t)r->n_rx * r->vis_words * 4, st));
-    const int64_t total = (int64_t)r->n_rx * r->vis_words * 32;
-    vis_kernel<<<blocks_for(total, kTraceThreads, sm), kTraceThreads, 0, st>>>(
-        S, C, r->rx, sc->dps_recv, r->vis, ctr, margin); count_launch();
-  }
-  TRY(cudaEventRecord(r->ev[1], st));
-
-  // hit records (rows of never-reached bounces read as misses)
-  const size_t nrec = (size_t)r->n_seg * n;
-  TRY(cudaMallocAsync(&r->rec_q, nrec * sizeof(float4), st));
-  TRY(cudaMallocAsync(&r->rec_n, nrec * sizeof(float4), st));
-  TRY(cudaMallocAsync(&r->rec_d, nrec * sizeof(float4), st));
-  TRY(cudaMallocAsync(&r->rec_i, nrec * sizeof(int2), st));
-  TRY(cudaMemsetAsync(r->rec_i, 0xFF, nrec * sizeof(int2), st));
   Records R{r->rec_q, r->rec_n, r->rec_d, r->rec_i, n};
 
-  // launch order (cached for the full launch)
-  const uint32_t* order = nullptr;
-  uint32_t* order_tmp = nullptr;
-  if (subset_d || ctx->order_n != n) {
-    uint64_t *ok, *tk;
-    uint32_t *ov, *tv;
-    TRY(cudaMallocAsync(&ok, n * 8, st));
-    TRY(cudaMallocAsync(&tk, n * 8, st));
-    TRY(cudaMallocAsync(&ov, n * 4, st));
-    TRY(cudaMallocAsync(&tv, n * 4, st));
-    order_key_kernel<<<blocks_for(n, 256, sm), 256, 0, st>>>(subset_d, n, r->p.n_rays, ok, ov); count_launch();
-    radix_sort_pairs(ok, ov, tk, tv, n, 32, st);
-    cudaFreeAsync(ok, st);
-    cudaFreeAsync(tk, st);
-    cudaFreeAsync(tv, st);
-    if (subset_d) {
-      order_tmp = ov;
-    } else {
-      if (ctx->order) cudaFreeAsync(ctx->order, st);
-      ctx->order = ov;
-      ctx->order_n = n;
-    }
-  }
-  order = subset_d ? order_tmp : ctx->order;
-
-  // LOS paths are written after the candidate count fixes the path buffer;
-  // the cast itself is cheap and done then.
-  TRY(cudaEventRecord(r->ev[2], st));
-  trace_kernel<<<blocks_for(n, kTraceThreads, sm), kTraceThreads, 0, st>>>(S, C, subset_d, order, R, ctr); count_launch();
-  TRY(cudaEventRecord(r->ev[3], st));
-
-  // candidate count per ray -> candidate offsets and table size
+  TRY(cudaMemsetAsync(W.T.fp, 0, c.table * 8, st));
+  TRY(cudaMemsetAsync(W.T.minrow, 0xFF, c.table * 4, st));
+  TRY(cudaMemsetAsync(W.cnt, 0, kCntN * 8, st));
   EmitArgs A{};
-  uint32_t *cand_cnt, *cand_off;
-  TRY(cudaMallocAsync(&cand_cnt, n * 4, st));
-  TRY(cudaMallocAsync(&cand_off, n * 4, st));
-  A.cand_cnt = cand_cnt;
-  emit_kernel<true><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, ctr); count_launch();
-  scan_exclusive(cand_cnt, cand_off, n, st);
-  unsigned long long cnt2[2] = {0, 0};
-  TRY(cudaMemcpyAsync(&cnt2[0], ctr + kCtrCands, 8, cudaMemcpyDeviceToHost, st));
-  TRY(cudaMemcpyAsync(&cnt2[1], ctr + kCtrLeaders, 8, cudaMemcpyDeviceToHost, st));
-  TRY(cudaStreamSynchronize(st));
-  const unsigned long long n_cand_h = cnt2[0], n_lead_h = cnt2[1];
-  if (r->p.cand_capacity > 0 && (int64_t)n_cand_h > r->p.cand_capacity) {
-    ctx->last_error = "more path candidates than cand_capacity";
-    return NRT_ERR_OVERFLOW;
-  }
-  if (n_cand_h >= 0xFFFFFFFFull) {
-    ctx->last_error = "more than 2^32 path candidates";
-    return NRT_ERR_OVERFLOW;
-  }
-  const int64_t cand_cap = std::max<int64_t>((int64_t)n_cand_h, 1);
-  // distinct keys <= per-warp distinct keys (n_lead) <= candidates
-  const int64_t key_bound = std::max<int64_t>((int64_t)n_lead_h, 1);
-  int64_t cap = r->p.key_capacity;
-  if (cap <= 0) {
-    cap = 1 << 12;
-    while (cap < key_bound + key_bound / 2) cap <<= 1;
-  }
-  if (cap & (cap - 1)) {
-    ctx->last_error = "key_capacity must be a power of two";
-    return NRT_ERR_ARG;
-  }
-  const int64_t key_cap = std::min<int64_t>(cap, key_bound);
-  Table T{};
-  KeyState K{};
-  uint32_t *spec_list, *diff_list, *list2_s, *list2_d;
-  uint2 *cand, *cand2;
-  TRY(cudaMallocAsync(&T.fp, cap * 8, st));
-  TRY(cudaMallocAsync(&T.hi, cap * 8, st));
-  TRY(cudaMallocAsync(&T.lo, cap * 8, st));
-  TRY(cudaMallocAsync(&T.minrow, cap * 4, st));
-  TRY(cudaMallocAsync(&T.kid, cap * 4, st));
-  TRY(cudaMallocAsync(&T.next, cap * 4, st));
-  TRY(cudaMemsetAsync(T.fp, 0, cap * 8, st));
-  TRY(cudaMemsetAsync(T.minrow, 0xFF, cap * 4, st));
-  T.mask = (uint64_t)cap - 1;
-  TRY(cudaMallocAsync(&K.slot, key_cap * 4, st));
-  TRY(cudaMallocAsync(&K.cur, key_cap * 4, st));
-  TRY(cudaMallocAsync(&K.tries, key_cap * 4, st));
-  TRY(cudaMallocAsync(&K.status, key_cap * 4, st));
-  TRY(cudaMallocAsync(&spec_list, key_cap * 4, st));
-  TRY(cudaMallocAsync(&diff_list, key_cap * 4, st));
-  TRY(cudaMallocAsync(&list2_s, key_cap * 4, st));
-  TRY(cudaMallocAsync(&list2_d, key_cap * 4, st));
-  TRY(cudaMallocAsync(&cand, cand_cap * sizeof(uint2), st));
-  TRY(cudaMallocAsync(&cand2, cand_cap * sizeof(uint2), st));
-  A.T = T;
-  A.cand = cand;
-  A.cand_off = cand_off;
+  A.T = W.T;
+  A.cand_cap = (uint64_t)c.cand;
+  A.cand = W.cand;
+  A.cand_off = W.cand_off;
   emit_kernel<false><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, ctr); count_launch();
-  cudaFreeAsync(cand_cnt, st);
-  cudaFreeAsync(cand_off, st);
 
-  // key ids from the occupied slots (specular first), in launch order of
-  // each key's lowest row within each type
-  uint32_t *fs, *fd, *os, *od, *pos = nullptr, *tv;
-  uint64_t *sk0, *tk0;
-  uint32_t* sv0;
-  TRY(cudaMallocAsync(&fs, cap * 4, st));
-  TRY(cudaMallocAsync(&fd, cap * 4, st));
-  TRY(cudaMallocAsync(&os, cap * 4, st));
-  TRY(cudaMallocAsync(&od, cap * 4, st));
-  slot_flags_kernel<<<blocks_for(cap, 256, sm), 256, 0, st>>>(T, cap, fs, fd); count_launch();
-  scan_exclusive(fs, os, cap, st);
-  scan_exclusive(fd, od, cap, st);
-  uint32_t tail[4];
-  TRY(cudaMemcpyAsync(&tail[0], os + cap - 1, 4, cudaMemcpyDeviceToHost, st));
-  TRY(cudaMemcpyAsync(&tail[1], fs + cap - 1, 4, cudaMemcpyDeviceToHost, st));
-  TRY(cudaMemcpyAsync(&tail[2], od + cap - 1, 4, cudaMemcpyDeviceToHost, st));
-  TRY(cudaMemcpyAsync(&tail[3], fd + cap - 1, 4, cudaMemcpyDeviceToHost, st));
-  TRY(cudaStreamSynchronize(st));
-  int64_t n_spec = (int64_t)tail[0] + tail[1];
-  int64_t n_diff = (int64_t)tail[2] + tail[3];
-  const int64_t n_keys = n_spec + n_diff;
-  if (n_keys > key_cap) {
-    ctx->last_error = "hash table holds more keys than its bound";
-    return NRT_ERR_OVERFLOW;
-  }
-  TRY(cudaMemsetAsync(ctr + kCtrKeys, 0, 8, st));
-  const unsigned long long nk_h = (unsigned long long)n_keys;
-  TRY(cudaMemcpyAsync(ctr + kCtrKeys, &nk_h, 8, cudaMemcpyHostToDevice, st));
-  TRY(cudaMallocAsync(&sk0, std::max<int64_t>(n_keys, 1) * 8, st));
-  TRY(cudaMallocAsync(&tk0, std::max<int64_t>(n_keys, 1) * 8, st));
-  TRY(cudaMallocAsync(&sv0, std::max<int64_t>(n_keys, 1) * 4, st));
-  TRY(cudaMallocAsync(&tv, std::max<int64_t>(n_keys, 1) * 4, st));
+  // key ids from the occupied slots, specular first, each type in launch
+  // order of the key's lowest row
+  slot_flags_kernel<<<blocks_for(c.table, 256, sm), 256, 0, st>>>(W.T, c.table, W.fs, W.fd); count_launch();
+  scan_exclusive(W.fs, W.os, c.table, st);
+  scan_exclusive(W.fd, W.od, c.table, st);
+  key_count_kernel<<<1, 1, 0, st>>>(W.fs, W.fd, W.os, W.od, c.table, W.cnt); count_launch();
   if (order) {
-    TRY(cudaMallocAsync(&pos, n * 4, st));
-    inverse_order_kernel<<<blocks_for(n, 256, sm), 256, 0, st>>>(order, n, pos); count_launch();
+    inverse_order_kernel<<<blocks_for(n, 256, sm), 256, 0, st>>>(order, n, W.pos); count_launch();
   }
-  slot_assign_kernel<<<blocks_for(cap, 256, sm), 256, 0, st>>>(T, cap, fs, fd, os, od, (uint32_t)n_spec,
-                                                               K.slot, sk0, sv0, pos); count_launch();
-  if (n_spec > 1) radix_sort_pairs(sk0, sv0, tk0, tv, n_spec, 32, st);
-  if (n_diff > 1) radix_sort_pairs(sk0 + n_spec, sv0 + n_spec, tk0, tv, n_diff, 32, st);
-  if (n_spec) TRY(cudaMemcpyAsync(spec_list, sv0, n_spec * 4, cudaMemcpyDeviceToDevice, st));
-  if (n_diff) TRY(cudaMemcpyAsync(diff_list, sv0 + n_spec, n_diff * 4, cudaMemcpyDeviceToDevice, st));
-  cudaFreeAsync(fs, st);
-  cudaFreeAsync(fd, st);
-  cudaFreeAsync(os, st);
-  cudaFreeAsync(od, st);
-  cudaFreeAsync(sk0, st);
-  cudaFreeAsync(tk0, st);
-  cudaFreeAsync(sv0, st);
-  cudaFreeAsync(tv, st);
-  if (pos) cudaFreeAsync(pos, st);
-  int64_t n_cand = (int64_t)n_cand_h;
-  verify_kernel<<<blocks_for(n_cand, 256, sm), 256, 0, st>>>(S, C, R, T, cand, n_cand, ctr); count_launch();
-  key_init_kernel<<<blocks_for(n_keys, 256, sm), 256, 0, st>>>(n_keys, K, T); count_launch();
+  TRY(cudaMemsetAsync(W.sk0, 0xFF, c.keys * 8, st));
+  slot_assign_kernel<<<blocks_for(c.table, 256, sm), 256, 0, st>>>(
+      W.T, c.table, W.fs, W.fd, W.os, W.od, W.cnt, W.K.slot, W.sk0, W.sv0, order ? W.pos : nullptr); count_launch();
+  radix_sort_pairs(W.sk0, W.sv0, W.tk0, W.tv, c.keys, 33, st);
+  split_lists_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.sv0, c.keys, W.cnt, W.spec_list,
+                                                                 W.diff_list); count_launch();
+  TRY(cudaMemcpyAsync(ctr + kCtrKeys, W.cnt + kCntKeys, 8, cudaMemcpyDeviceToDevice, st));
+  verify_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(S, C, R, W.T, W.cand, ctr + kCtrCands,
+                                                            c.cand, ctr); count_launch();
+  key_init_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.cnt + kCntKeys, W.K, W.T); count_launch();
 
-  // path buffer: at most one path per key, plus LOS
-  r->path_cap = n_keys + r->n_rx;
-  PathRec* raw = nullptr;
-  TRY(cudaMallocAsync(&raw, r->path_cap * sizeof(PathRec), st));
-  los_kernel<<<(r->n_rx + kTraceThreads - 1) / kTraceThreads, kTraceThreads, 0, st>>>(
-      S, C, r->rx, raw, ctr, r->path_cap); count_launch();
-  TRY(cudaEventRecord(r->ev[4], st));
-
-  // validation rounds: candidates in row (= ray id) order until one validates
+  // LOS paths first, then candidates in ray-id order until one validates
+  const int nj = C.batch ? C.n_pairs : r->n_rx_phys;
+  los_kernel<<<(nj + kTraceThreads - 1) / kTraceThreads, kTraceThreads, 0, st>>>(
+      S, C, r->rx, W.raw, ctr, c.paths); count_launch();
+  if (r->ev[4]) TRY(cudaEventRecord(r->ev[4], st));
   ValArgs V{};
-  V.T = T;
-  V.K = K;
+  V.T = W.T;
+  V.K = W.K;
   V.R = R;
   V.rx = r->rx;
-  V.ray_of_row = subset_d;
-  V.paths = raw;
-  V.path_cap = r->path_cap;
-  uint32_t *cur_s = spec_list, *cur_d = diff_list, *nxt_s = list2_s, *nxt_d = list2_d;
-  uint2 *cand_cur = cand, *cand_nxt = cand2;
-  for (int round = 0; round < r->p.rep_tries && (n_spec > 0 || n_diff > 0); ++round) {
-    TRY(cudaMemsetAsync(ctr + kCtrKeysSpec, 0, 16, st));  // spec + diff next counters
-    if (n_spec > 0) {
-      V.next_list = nxt_s;
-      V.next_ctr = kCtrKeysSpec;
-      validate_specular_kernel<<<blocks_for(n_spec, kTraceThreads, sm), kTraceThreads, 0, st>>>(
-          S, C, V, cur_s, n_spec, ctr); count_launch();
-    }
-    if (n_diff > 0) {
-      V.next_list = nxt_d;
-      V.next_ctr = kCtrKeysDiff;
-      validate_diffuse_kernel<<<blocks_for(n_diff, kTraceThreads, sm), kTraceThreads, 0, st>>>(
-          S, C, V, cur_d, n_diff, ctr); count_launch();
-    }
-    unsigned long long nn[2];
-    TRY(cudaMemcpyAsync(nn, ctr + kCtrKeysSpec, 16, cudaMemcpyDeviceToHost, st));
-    TRY(cudaStreamSynchronize(st));
-    n_spec = (int64_t)nn[0];
-    n_diff = (int64_t)nn[1];
-    if (n_spec + n_diff == 0 || round + 1 >= r->p.rep_tries) break;
-    // next candidate rows for the keys still pending
-    if (n_spec) next_reset_kernel<<<blocks_for(n_spec, 256, sm), 256, 0, st>>>(nxt_s, n_spec, K, T); count_launch();
-    if (n_diff) next_reset_kernel<<<blocks_for(n_diff, 256, sm), 256, 0, st>>>(nxt_d, n_diff, K, T); count_launch();
-    TRY(cudaMemsetAsync(ctr + kCtrCompact, 0, 8, st));
-    next_scan_kernel<<<blocks_for(n_cand, 256, sm), 256, 0, st>>>(cand_cur, n_cand, K, T, cand_nxt, ctr); count_launch();
+  V.ray_of_row = nullptr;
+  V.paths = W.raw;
+  V.path_cap = c.paths;
+  uint32_t *cur_s = W.spec_list, *cur_d = W.diff_list, *nxt_s = W.list2_s, *nxt_d = W.list2_d;
+  uint2 *cand_cur = W.cand, *cand_nxt = W.cand2;
+  unsigned long long* cnt_cand_cur = ctr + kCtrCands;
+  TRY(cudaMemcpyAsync(W.cnt + kCntCurS, W.cnt + kCntSpec, 16, cudaMemcpyDeviceToDevice, st));
+  for (int round = 0; round < r->p.rep_tries; ++round) {
+    TRY(cudaMemsetAsync(W.cnt + kCntNxtS, 0, 16, st));
+    V.next_list = nxt_s;
+    V.next_cnt = W.cnt + kCntNxtS;
+    validate_specular_kernel<<<blocks_for(c.keys, kTraceThreads, sm), kTraceThreads, 0, st>>>(
+        S, C, V, cur_s, W.cnt + kCntCurS, ctr); count_launch();
+    V.next_list = nxt_d;
+    V.next_cnt = W.cnt + kCntNxtD;
+    validate_diffuse_kernel<<<blocks_for(c.keys, kTraceThreads, sm), kTraceThreads, 0, st>>>(
+        S, C, V, cur_d, W.cnt + kCntCurD, ctr); count_launch();
+    if (round + 1 >= r->p.rep_tries) break;
+    next_reset_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(nxt_s, W.cnt + kCntNxtS, W.K, W.T); count_launch();
+    next_reset_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(nxt_d, W.cnt + kCntNxtD, W.K, W.T); count_launch();
+    unsigned long long* cnt_cand_nxt = W.cnt + ((cnt_cand_cur == W.cnt + kCntCandA) ? kCntCandB : kCntCandA);
+    TRY(cudaMemsetAsync(cnt_cand_nxt, 0, 8, st));
+    next_scan_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(cand_cur, cnt_cand_cur, c.cand, W.K,
+                                                                 W.T, cand_nxt, cnt_cand_nxt); count_launch();
     std::swap(cand_cur, cand_nxt);
-    TRY(cudaMemsetAsync(ctr + kCtrKeysSpec, 0, 16, st));
-    if (n_spec)
-      next_apply_kernel<<<blocks_for(n_spec, 256, sm), 256, 0, st>>>(nxt_s, n_spec, K, T, cur_s, ctr,
-                                                                    kCtrKeysSpec); count_launch();
-    if (n_diff)
-      next_apply_kernel<<<blocks_for(n_diff, 256, sm), 256, 0, st>>>(nxt_d, n_diff, K, T, cur_d, ctr,
-                                                                    kCtrKeysDiff); count_launch();
-    unsigned long long ncmp = 0;
-    TRY(cudaMemcpyAsync(nn, ctr + kCtrKeysSpec, 16, cudaMemcpyDeviceToHost, st));
-    TRY(cudaMemcpyAsync(&ncmp, ctr + kCtrCompact, 8, cudaMemcpyDeviceToHost, st));
-    TRY(cudaStreamSynchronize(st));
-    n_spec = (int64_t)nn[0];
-    n_diff = (int64_t)nn[1];
-    n_cand = (int64_t)ncmp;
+    cnt_cand_cur = cnt_cand_nxt;
+    TRY(cudaMemsetAsync(W.cnt + kCntCurS, 0, 16, st));
+    next_apply_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(nxt_s, W.cnt + kCntNxtS, W.K, W.T,
+                                                                  cur_s, W.cnt + kCntCurS); count_launch();
+    next_apply_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(nxt_d, W.cnt + kCntNxtD, W.K, W.T,
+                                                                  cur_d, W.cnt + kCntCurD); count_launch();
   }
-  TRY(cudaEventRecord(r->ev[5], st));
+  if (r->ev[5]) TRY(cudaEventRecord(r->ev[5], st));
 
-  // deterministic order of the paths, then the field
+  // deterministic order of the paths (padding sorts last), ranges, field
+  path_sortkey_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>(W.raw, ctr + kCtrPaths, c.paths,
+                                                                   W.psk, W.psi); count_launch();
+  radix_sort_pairs(W.psk, W.psi, W.ptk, W.pti, c.paths, 44, st);
+  path_gather_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>(W.raw, W.psi, c.paths,
+                                                                  (PathRec*)r->paths); count_launch();
+  rx_range_kernel<<<(r->n_rx + 63) / 64, 64, 0, st>>>(W.psk, ctr + kCtrPaths, c.paths, r->n_rx,
+                                                      r->rx_start_d, r->rx_count_d); count_launch();
+  if (sc->have_materials) {
+    field_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>((const PathRec*)r->paths, ctr + kCtrPaths,
+                                                              c.paths, sc->mat, r->p.freq, r->p.pol,
+                                                              r->path_a); count_launch();
+    power_kernel<<<r->n_rx, 256, 0, st>>>(r->path_a, r->rx_start_d, r->rx_count_d, r->power); count_launch();
+  }
+  return NRT_OK;
+}
+
+// Counters back to the host after a (possibly replayed) simulation.
+nrt_status finish_result(nrt_result* r) {
+  nrt_scene* sc = r->scene;
+  nrt_ctx* ctx = sc->ctx;
+  cudaStream_t st = ctx->stream;
   unsigned long long hc[kCtrCount];
-  TRY(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
-  TRY(cudaStreamSynchronize(st));
-  r->n_paths = std::min<int64_t>((int64_t)hc[kCtrPaths], r->path_cap);
-  const int64_t np = r->n_paths;
-  uint64_t *sk, *tk;
-  uint32_t *si, *ti;
-  TRY(cudaMallocAsync(&sk, std::max<int64_t>(np, 1) * 8, st));
-  TRY(cudaMallocAsync(&tk, std::max<int64_t>(np, 1) * 8, st));
-  TRY(cudaMallocAsync(&si, std::max<int64_t>(np, 1) * 4, st));
-  TRY(cudaMallocAsync(&ti, std::max<int64_t>(np, 1) * 4, st));
-  TRY(cudaMallocAsync(&r->paths, std::max<int64_t>(np, 1) * sizeof(PathRec), st));
-  if (np > 0) {
-    path_sortkey_kernel<<<blocks_for(np, 256, sm), 256, 0, st>>>(raw, np, sk, si); count_launch();
-    radix_sort_pairs(sk, si, tk, ti, np, 44, st);
-    path_gather_kernel<<<blocks_for(np, 256, sm), 256, 0, st>>>(raw, si, np, (PathRec*)r->paths); count_launch();
-  }
-  // per-RX ranges (paths are sorted by RX first)
-  unsigned long long* rxc = nullptr;
-  TRY(cudaMallocAsync(&rxc, r->n_rx * 8, st));
-  TRY(cudaMemsetAsync(rxc, 0, r->n_rx * 8, st));
-  if (np > 0) {
-    rx_range_kernel<<<(r->n_rx + 63) / 64, 64, 0, st>>>(sk, np, r->n_rx, rxc); count_launch();
-  }
-  std::vector<unsigned long long> rxh(r->n_rx);
-  TRY(cudaMemcpyAsync(rxh.data(), rxc, r->n_rx * 8, cudaMemcpyDeviceToHost, st));
-  TRY(cudaStreamSynchronize(st));
-  cudaFreeAsync(rxc, st);
-  r->rx_count = new int64_t[r->n_rx]();
-  r->rx_start = new int64_t[r->n_rx]();
-  for (int j = 0; j < r->n_rx; ++j) r->rx_count[j] = (int64_t)rxh[j];
-  for (int j = 1; j < r->n_rx; ++j) r->rx_start[j] = r->rx_start[j - 1] + r->rx_count[j - 1];
-  cudaFreeAsync(sk, st);
-  cudaFreeAsync(tk, st);
-  cudaFreeAsync(si, st);
-  cudaFreeAsync(ti, st);
-  cudaFreeAsync(raw, st);
-  cudaFreeAsync(T.fp, st);
-  cudaFreeAsync(T.hi, st);
-  cudaFreeAsync(T.lo, st);
-  cudaFreeAsync(T.minrow, st);
-  cudaFreeAsync(T.kid, st);
-  cudaFreeAsync(T.next, st);
-  cudaFreeAsync(K.slot, st);
-  cudaFreeAsync(K.cur, st);
-  cudaFreeAsync(K.tries, st);
-  cudaFreeAsync(K.status, st);
-  cudaFreeAsync(spec_list, st);
-  cudaFreeAsync(diff_list, st);
-  cudaFreeAsync(list2_s, st);
-  cudaFreeAsync(list2_d, st);
-  cudaFreeAsync(cand, st);
-  cudaFreeAsync(cand2, st);
-  if (order_tmp) cudaFreeAsync(order_tmp, st);
-  TRY(cudaMallocAsync(&r->path_a, std::max<int64_t>(np, 1) * sizeof(float2), st));
-  TRY(cudaMallocAsync(&r->power, r->n_rx * sizeof(double), st));
-  nrt_status fst = run_field(r);
-  if (fst != NRT_OK) return fst;
-  TRY(cudaEventRecord(r->ev[6], st));
-  TRY(cudaEventRecord(r->ev[7], st));
-  TRY(cudaMemcpyAsync(hc, ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  if (!r->rx_count) r->rx_count = new int64_t[r->n_rx]();
+  if (!r->rx_start) r->rx_start = new int64_t[r->n_rx]();
+  TRY(cudaMemcpyAsync(hc, r->ctr, sizeof(hc), cudaMemcpyDeviceToHost, st));
+  TRY(cudaMemcpyAsync(r->rx_count, r->rx_count_d, r->n_rx * 8, cudaMemcpyDeviceToHost, st));
+  TRY(cudaMemcpyAsync(r->rx_start, r->rx_start_d, r->n_rx * 8, cudaMemcpyDeviceToHost, st));
   TRY(cudaStreamSynchronize(st));
   TRY(cudaGetLastError());
+  r->n_paths = std::min<int64_t>((int64_t)hc[kCtrPaths], r->path_cap);
+#ifdef NRT_CHECK_BOUNDS
+  {
+    unsigned long long w = 0;
+    TRY(cudaMemcpyFromSymbol(&w, g_dbg_word, sizeof(w)));
+    if (w) {
+      ctx->last_error = "bounds check failed: kernel code " + std::to_string(w >> 48) +
+                        " index " + std::to_string(w & 0xFFFFFFFFFFFFull);
+      return NRT_ERR_OVERFLOW;
+    }
+  }
+#endif
+  r->field_done = sc->have_materials;
   nrt_counters& c = r->counters;
-  c.rays = n;
+  c.rays = r->n_traced;
   c.segments = (int64_t)hc[kCtrSegments];
   c.vis_casts = (int64_t)hc[kCtrVisCasts];
   c.los_casts = (int64_t)hc[kCtrLosCasts];
@@ -1264,6 +1476,117 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
   return NRT_OK;
 }
 
+// Prologue shared by normal runs and graph capture: counters, visibility,
+// hit records, trace.
+nrt_status enqueue_trace(nrt_result* r, const SceneView& S, const SimConst& C,
+                         const uint32_t* subset_d, const uint32_t* order, bool do_vis) {
+  nrt_ctx* ctx = r->scene->ctx;
+  cudaStream_t st = ctx->stream;
+  const int sm = ctx->sm_count;
+  const int64_t n = r->n_traced;
+  TRY(cudaMemsetAsync(r->ctr, 0, kCtrCount * sizeof(unsigned long long), st));
+  const float margin = 0.8660254037844386f * r->scene->params.rho + r->scene->params.r_p;
+  if (do_vis && r->p.capture == NRT_CAPTURE_VIS) {
+    const int64_t total = (int64_t)r->n_rx_phys * r->vis_words * 32;
+    vis_kernel<<<blocks_for(total, kTraceThreads, sm), kTraceThreads, 0, st>>>(
+        S, C, r->rx, r->scene->dps_recv, r->vis, r->ctr, margin); count_launch();
+  }
+  if (r->ev[1]) TRY(cudaEventRecord(r->ev[1], st));
+  TRY(cudaMemsetAsync(r->rec_i, 0xFF, (size_t)r->n_seg * n * sizeof(int2), st));
+  Records R{r->rec_q, r->rec_n, r->rec_d, r->rec_i, n};
+  if (r->ev[2]) TRY(cudaEventRecord(r->ev[2], st));
+  if (C.batch && r->schedule == 1) {
+    queue_init_kernel<<<(r->n_pairs + 255) / 256, 256, 0, st>>>(r->chunk_start, r->n_pairs, r->queue); count_launch();
+    trace_persistent_kernel<<<sm * 8, kTraceThreads, 0, st>>>(S, C, order, R, r->chunk_start,
+                                                              r->packet, r->queue, r->stamps, r->ctr); count_launch();
+  } else {
+    trace_kernel<<<blocks_for(n, kTraceThreads, sm), kTraceThreads, 0, st>>>(S, C, subset_d, order, R, r->ctr); count_launch();
+  }
+  if (r->ev[3]) TRY(cudaEventRecord(r->ev[3], st));
+  return NRT_OK;
+}
+
+}  // namespace
+
+// One simulation into r (scene, params, receivers and rows set).  The only
+// host round trip sizes the candidate buffers and the hash table from an
+// exact count; everything after it is enqueued without synchronising.
+nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
+  nrt_scene* sc = r->scene;
+  nrt_ctx* ctx = sc->ctx;
+  cudaStream_t st = ctx->stream;
+  const int sm = ctx->sm_count;
+  const SceneView S = scene_view(sc);
+  const int64_t n = r->n_traced;
+  r->n_seg = r->p.max_depth + (r->p.capture == NRT_CAPTURE_SPHERE ? 1 : 0);
+  r->vis_words = (sc->n_dps + 31) / 32;
+  SimConst C = make_const(r);
+  launch_counter() = 0;
+  for (int e = 0; e < 8; ++e)
+    if (!r->ev[e]) TRY(cudaEventCreate(&r->ev[e]));
+  TRY(cudaEventRecord(r->ev[0], st));
+  Caps c0;
+  nrt_status rc = alloc_result(r, c0, false);  // records, counters, visibility
+  if (rc != NRT_OK) return rc;
+  Work W;
+  TRY(dbg_set_caps(-1, 0, 0, 0, n, r->n_rx, st));
+  const uint32_t* order = nullptr;
+  rc = make_order(r, C, subset_d, W, &order);
+  if (rc != NRT_OK) return rc;
+  rc = enqueue_trace(r, S, C, subset_d, order, !r->vis_shared);
+  if (rc != NRT_OK) return rc;
+
+  // candidate count per ray -> offsets and sizes (the one host round trip)
+  TRY(dalloc(&W.cand_cnt, n, st));
+  TRY(dalloc(&W.cand_off, n, st));
+  Records R{r->rec_q, r->rec_n, r->rec_d, r->rec_i, n};
+  EmitArgs A{};
+  A.cand_cnt = W.cand_cnt;
+  emit_kernel<true><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, r->ctr); count_launch();
+  scan_exclusive(W.cand_cnt, W.cand_off, n, st);
+  unsigned long long cnt2[2] = {0, 0};
+  TRY(cudaMemcpyAsync(&cnt2[0], r->ctr + kCtrCands, 8, cudaMemcpyDeviceToHost, st));
+  TRY(cudaMemcpyAsync(&cnt2[1], r->ctr + kCtrLeaders, 8, cudaMemcpyDeviceToHost, st));
+  TRY(cudaStreamSynchronize(st));
+  if (r->p.cand_capacity > 0 && (int64_t)cnt2[0] > r->p.cand_capacity) {
+    ctx->last_error = "more path candidates than cand_capacity";
+    release_work(W, st);
+    return NRT_ERR_OVERFLOW;
+  }
+  if (cnt2[0] >= 0xFFFFFFFFull) {
+    ctx->last_error = "more than 2^32 path candidates";
+    release_work(W, st);
+    return NRT_ERR_OVERFLOW;
+  }
+  Caps c;
+  c.cand = std::max<int64_t>((int64_t)cnt2[0], 1);
+  c.keys = std::max<int64_t>((int64_t)cnt2[1], 1);  // distinct keys <= per-warp distinct keys
+  c.table = r->p.key_capacity;
+  if (c.table <= 0) {
+    c.table = 1 << 12;
+    while (c.table < c.keys + c.keys / 2) c.table <<= 1;
+  }
+  if (c.table & (c.table - 1)) {
+    ctx->last_error = "key_capacity must be a power of two";
+    release_work(W, st);
+    return NRT_ERR_ARG;
+  }
+  c.keys = std::min<int64_t>(c.keys, c.table);
+  c.paths = c.keys + (C.batch ? r->n_pairs : r->n_rx_phys);
+  rc = alloc_result(r, c, true);
+  if (rc == NRT_OK) rc = alloc_work(ctx, W, c, n, st);
+  TRY(dbg_set_caps(c.table, c.keys, c.cand, c.paths, n, r->n_rx, st));
+  if (rc == NRT_OK) rc = enqueue_rest(r, W, S, C, order);
+  if (rc != NRT_OK) {
+    release_work(W, st);
+    return rc;
+  }
+  TRY(cudaEventRecord(r->ev[6], st));
+  TRY(cudaEventRecord(r->ev[7], st));
+  release_work(W, st);
+  return finish_result(r);
+}
+
 nrt_status run_field(nrt_result* r) {
   nrt_scene* sc = r->scene;
   nrt_ctx* ctx = sc->ctx;
@@ -1272,21 +1595,142 @@ nrt_status run_field(nrt_result* r) {
     r->field_done = false;
     return NRT_OK;  // field computed once materials are set
   }
-  const int64_t np = r->n_paths;
-  if (np > 0)
-    field_kernel<<<blocks_for(np, 256, ctx->sm_count), 256, 0, st>>>(
-        (const PathRec*)r->paths, np, sc->mat, r->p.freq, r->p.pol, r->path_a); count_launch();
-  int64_t *start_d, *count_d;
-  TRY(cudaMallocAsync(&start_d, r->n_rx * 8, st));
-  TRY(cudaMallocAsync(&count_d, r->n_rx * 8, st));
-  TRY(cudaMemcpyAsync(start_d, r->rx_start, r->n_rx * 8, cudaMemcpyHostToDevice, st));
-  TRY(cudaMemcpyAsync(count_d, r->rx_count, r->n_rx * 8, cudaMemcpyHostToDevice, st));
-  power_kernel<<<r->n_rx, 256, 0, st>>>(r->path_a, start_d, count_d, r->power); count_launch();
-  cudaFreeAsync(start_d, st);
-  cudaFreeAsync(count_d, st);
+  unsigned long long* np = r->ctr + kCtrPaths;
+  field_kernel<<<blocks_for(r->path_cap, 256, ctx->sm_count), 256, 0, st>>>(
+      (const PathRec*)r->paths, np, r->path_cap, sc->mat, r->p.freq, r->p.pol, r->path_a); count_launch();
+  power_kernel<<<r->n_rx, 256, 0, st>>>(r->path_a, r->rx_start_d, r->rx_count_d, r->power); count_launch();
   TRY(cudaGetLastError());
   r->field_done = true;
   return NRT_OK;
+}
+
+// ---------------------------------------------------------------- batch graph
+// A batch plan: run once to size every buffer (with 25% headroom), keep the
+// buffers, and record the whole simulation -- trace as one persistent launch,
+// candidates, dedup, validation, field -- into a CUDA graph.  A replay takes
+// new transmitter positions and launches the graph; the visibility matrix of
+// the fixed receiver is computed once.
+nrt_status batch_graph_build(nrt_result* r) {
+  nrt_scene* sc = r->scene;
+  nrt_ctx* ctx = sc->ctx;
+  cudaStream_t st = ctx->stream;
+  const SceneView S = scene_view(sc);
+  SimConst C = make_const(r);
+  Caps c;
+  const nrt_counters& m = r->counters;
+  c.cand = std::max<int64_t>(m.candidates + m.candidates / 4 + 1024, 1);
+  c.keys = std::max<int64_t>(m.keys + m.keys / 4 + 1024, 1);
+  c.table = 1 << 12;
+  while (c.table < 2 * c.keys) c.table <<= 1;
+  c.paths = c.keys + r->n_pairs;
+  // path buffers sized by the caps (the calibration run's paths are dropped)
+  nrt_status rc = alloc_result(r, c, true);
+  if (rc != NRT_OK) return rc;
+  Work* W = new Work();
+  r->work = W;
+  const uint32_t* order = nullptr;
+  rc = make_order(r, C, nullptr, *W, &order);
+  if (rc != NRT_OK) return rc;
+  rc = alloc_work(ctx, *W, c, r->n_traced, st);
+  if (rc != NRT_OK) return rc;
+  TRY(cudaStreamSynchronize(st));
+  for (int e = 0; e < 8; ++e) {
+    if (r->ev[e]) cudaEventDestroy(r->ev[e]);
+    r->ev[e] = nullptr;
+  }
+  cudaGraph_t g;
+  TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  rc = enqueue_trace(r, S, C, nullptr, order, false);
+  Records R{r->rec_q, r->rec_n, r->rec_d, r->rec_i, r->n_traced};
+  if (rc == NRT_OK) {
+    EmitArgs A{};
+    A.cand_cnt = W->cand_cnt;
+    emit_kernel<true><<<blocks_for(r->n_traced, 256, ctx->sm_count), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, r->ctr); count_launch();
+    scan_exclusive(W->cand_cnt, W->cand_off, r->n_traced, st);
+    rc = enqueue_rest(r, *W, S, C, order);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(st, &g);
+  if (rc != NRT_OK) return rc;
+  if (e2 != cudaSuccess) {
+    ctx->last_error = std::string("graph capture: ") + cudaGetErrorString(e2);
+    return NRT_ERR_CUDA;
+  }
+  cudaError_t e3 = cudaGraphInstantiate(&r->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e3 != cudaSuccess) {
+    ctx->last_error = std::string("graph instantiate: ") + cudaGetErrorString(e3);
+    return NRT_ERR_CUDA;
+  }
+  return NRT_OK;
+}
+
+nrt_status batch_graph_replay(nrt_result* r, const float* tx_host) {
+  nrt_ctx* ctx = r->scene->ctx;
+  cudaStream_t st = ctx->stream;
+  if (!r->graph) {
+    ctx->last_error = "no batch graph";
+    return NRT_ERR_STATE;
+  }
+  if (tx_host) {
+    std::vector<float4> t(r->n_pairs);
+    for (int j = 0; j < r->n_pairs; ++j)
+      t[j] = make_float4(tx_host[3 * j], tx_host[3 * j + 1], tx_host[3 * j + 2], 0.f);
+    TRY(cudaMemcpyAsync(r->tx_pair, t.data(), r->n_pairs * sizeof(float4), cudaMemcpyHostToDevice, st));
+  }
+  launch_counter() = 0;
+  cudaEvent_t e0, e1;
+  TRY(cudaEventCreate(&e0));
+  TRY(cudaEventCreate(&e1));
+  TRY(cudaEventRecord(e0, st));
+  TRY(cudaGraphLaunch(r->graph, st));
+  TRY(cudaEventRecord(e1, st));
+  TRY(cudaEventSynchronize(e1));
+  cudaEventElapsedTime(&r->graph_ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return finish_result(r);
+}
+
+// The trace phase alone (no visibility), timed with events on the stream;
+// used by the autotuner to compare packet sizes and schedules.
+nrt_status run_trace_phase(nrt_result* r, float* ms) {
+  nrt_ctx* ctx = r->scene->ctx;
+  cudaStream_t st = ctx->stream;
+  const SceneView S = scene_view(r->scene);
+  SimConst C = make_const(r);
+  Work W;
+  const uint32_t* order = nullptr;
+  nrt_status rc = make_order(r, C, r->ray_of_row, W, &order);
+  if (rc != NRT_OK) return rc;
+  cudaEvent_t saved[8];
+  for (int e = 0; e < 8; ++e) {
+    saved[e] = r->ev[e];
+    r->ev[e] = nullptr;
+  }
+  cudaEvent_t e0, e1;
+  TRY(cudaEventCreate(&e0));
+  TRY(cudaEventCreate(&e1));
+  TRY(cudaEventRecord(e0, st));
+  rc = enqueue_trace(r, S, C, r->ray_of_row, order, false);
+  TRY(cudaEventRecord(e1, st));
+  TRY(cudaEventSynchronize(e1));
+  cudaEventElapsedTime(ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (int e = 0; e < 8; ++e) r->ev[e] = saved[e];
+  release_work(W, st);
+  return rc;
+}
+
+void free_work(nrt_result* r) {
+  if (r->graph) cudaGraphExecDestroy(r->graph);
+  r->graph = nullptr;
+  if (r->work) {
+    Work* W = (Work*)r->work;
+    release_work(*W, r->scene->ctx->stream);
+    delete W;
+    r->work = nullptr;
+  }
 }
 
 nrt_status run_backward(nrt_result* r, const float* dL_dP_h, float* g_eps, float* g_sig,

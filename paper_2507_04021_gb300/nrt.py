@@ -56,6 +56,11 @@ class Counters(C.Structure):
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
 
 
+class BatchOpts(C.Structure):
+    _fields_ = [("packet", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 class PathView(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in (
         "key_hi", "key_lo", "rep", "rx", "type", "k", "pts", "mats", "cos_theta", "geo", "tau", "a")]
@@ -100,6 +105,11 @@ def lib():
         L.nrt_field_read.argtypes = [_P, _P]
         L.nrt_backward.argtypes = [_P, _P, _P, _P, _P]
         L.nrt_backward_noalloc.argtypes = [_P, _P, _P]
+        L.nrt_trace_batch.argtypes = [_P, _P, _P, _P, C.c_int, C.POINTER(TraceParams),
+                                      C.POINTER(BatchOpts), C.POINTER(_P)]
+        L.nrt_batch_replay.argtypes = [_P, _P]
+        L.nrt_batch_times.argtypes = [_P, _P, _P]
+        L.nrt_autotune_batch.argtypes = [_P, _P, _P, C.c_int, C.c_int, _P, _P]
         L.nrt_destroy.restype = None
     return _lib
 
@@ -206,6 +216,10 @@ class Scene:
 
     def trace(self, tx, rx, params: TraceParams, ray_subset=None) -> "Result":
         return Result(self, tx, rx, params, ray_subset)
+
+    def trace_batch(self, tx, rx, budgets, params: TraceParams, packet=64, schedule=1,
+                    use_graph=False) -> "BatchResult":
+        return BatchResult(self, tx, rx, budgets, params, packet, schedule, use_graph)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -314,3 +328,49 @@ class Result:
             self.close()
         except Exception:
             pass
+
+
+class BatchResult(Result):
+    """nrt_trace_batch: TX-RX pairs (one fixed RX) with per-pair ray budgets; the
+    per-RX outputs of Result (counts, power, paths' rx field) are per pair."""
+
+    def __init__(self, scene, tx, rx, budgets, params, packet=64, schedule=1, use_graph=False):
+        self.scene = scene
+        self.ctx = scene.ctx
+        tx = np.ascontiguousarray(tx, np.float32).reshape(-1, 3)
+        rx = np.ascontiguousarray(rx, np.float32).reshape(3)
+        b = np.ascontiguousarray(budgets, np.int64).reshape(-1)
+        self.n_rx = int(tx.shape[0])
+        self.n_pairs = self.n_rx
+        self.params = params
+        self.budgets = b
+        o = BatchOpts(int(packet), int(schedule), int(bool(use_graph)), 0)
+        self._h = _P()
+        self.ctx._check(lib().nrt_trace_batch(scene._h, _np_ptr(tx), _np_ptr(rx), _np_ptr(b),
+                                              self.n_rx, C.byref(params), C.byref(o),
+                                              C.byref(self._h)))
+        self.n_seg = params.max_depth
+        self.n_traced = int(b.sum())
+
+    def replay(self, tx=None):
+        p = None
+        if tx is not None:
+            tx = np.ascontiguousarray(tx, np.float32).reshape(self.n_pairs, 3)
+            p = _np_ptr(tx)
+        self.ctx._check(lib().nrt_batch_replay(self._h, p))
+
+    def batch_times(self):
+        pm = np.zeros(self.n_pairs, np.float64)
+        tot = C.c_float()
+        self.ctx._check(lib().nrt_batch_times(self._h, _np_ptr(pm), C.byref(tot)))
+        return pm, float(tot.value)
+
+    def autotune(self, configs, repeats=2):
+        """configs: [(packet, schedule), ...]; returns (ms per config, best index)."""
+        pk = np.ascontiguousarray([c[0] for c in configs], np.int32)
+        sc = np.ascontiguousarray([c[1] for c in configs], np.int32)
+        ms = np.zeros(len(configs), np.float32)
+        best = C.c_int32()
+        self.ctx._check(lib().nrt_autotune_batch(self._h, _np_ptr(pk), _np_ptr(sc), len(configs),
+                                                 int(repeats), _np_ptr(ms), C.byref(best)))
+        return ms, int(best.value)
