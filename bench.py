@@ -18,6 +18,11 @@ roofline  = the trace kernel (the bounce loop), algorithmic bytes per launch
             (oracle-counted disc reads per segment, tests/golden) over its
             measured duration, against the measured HBM copy bandwidth.
 
+batch     = the robot-trajectory workload: 256 TX-RX pairs with budgets
+            U[1e5, 1e6], packet/schedule autotuned, the whole batch replayed
+            from a CUDA graph; per-pair trace completion p50/p99 from device
+            timestamps and pairs/s.
+
 --impl reference times the FP64 CPU oracle on a bounded ray sample of the
 same workload on the host cores (the reference arm of this tier).
 """
@@ -173,6 +178,69 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_bench(args, scene, o, rank, stream, flush):
+    """Robot-trajectory batch: pairs along the seeded trajectory, one fixed RX,
+    per-pair budgets U[1e5, 1e6]; autotuned packet/schedule; the whole batch
+    replayed from a CUDA graph.  Each rank runs its own pairs (independent
+    problems, weak scaling)."""
+    import torch
+    from paper_2507_04021_gb300 import inputs, nrt
+
+    n = args.batch_pairs
+    traj = inputs.trajectory(o.extra["boxes"])
+    budgets = inputs.ray_budgets()[:n]
+    tx = np.roll(traj, -rank * n, axis=0)[:n] if rank else traj[:n]
+    rx = np.array([17.5, 8.0, 1.2], np.float32)
+    p = nrt.default_trace_params(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1,
+                                 rep_tries=8)
+    cfgs = [(32, 1), (64, 1), (128, 1), (64, 0)]
+    cal = scene.trace_batch(tx, rx, budgets, p, packet=64, schedule=1)
+    tune_ms, best = cal.autotune(cfgs, repeats=1)
+    cal.close()
+    packet, schedule = cfgs[best]
+    g = scene.trace_batch(tx, rx, budgets, p, packet=packet, schedule=schedule, use_graph=True)
+    for _ in range(max(1, args.warmup)):
+        g.replay()
+    torch.cuda.synchronize()
+    steps = max(1, args.batch_steps)
+    tot, pair_ms, launches, segs = [], [], 0, 0
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot.append(e0.elapsed_time(e1))
+        pm, _ = g.batch_times()
+        pair_ms.append(pm)
+        _, c = g.counts()
+        launches += c["kernel_launches"] + 1
+        segs += c["segments"] + c["vis_casts"] + c["los_casts"] + c["validation_casts"]
+    _, c = g.counts()
+    g.close()
+    pm = np.concatenate(pair_ms)
+    ms = float(np.mean(tot))
+    return {
+        "workload": (f"{n} TX-RX pairs on the robot trajectory, RX (17.5, 8, 1.2), budgets "
+                     f"U[1e5, 1e6] ({int(budgets.sum())} rays), 5 interactions, VIS + diffuse"),
+        "pairs": n, "rays": int(budgets.sum()), "steps": steps,
+        "ms_per_batch": ms, "pairs_per_s": n / (ms / 1000.0),
+        "ray_segments_per_s": segs / (sum(tot) / 1000.0),
+        "pair_trace_done_ms": {"p50": float(np.percentile(pm, 50)),
+                               "p99": float(np.percentile(pm, 99))},
+        "latency_note": "per-pair time from batch start to the pair's last traced ray "
+                        "(device timestamps); every pair's paths and field are ready at ms_per_batch",
+        "autotune": {"configs": [list(c_) for c_ in cfgs], "trace_ms": [float(x) for x in tune_ms],
+                     "chosen": {"packet": packet, "schedule": ["static", "persistent"][schedule]}},
+        "graph": True, "gpu_launches": int(launches),
+        "counts": {k: c[k] for k in ("segments", "vis_casts", "validation_casts", "candidates",
+                                     "keys", "paths")},
+    }
+
+
 def ours(args):
     import torch
     from paper_2507_04021_gb300 import inputs, nrt
@@ -290,8 +358,12 @@ def ours(args):
         "counts": {k: counts[k] for k in ("segments", "vis_casts", "validation_casts",
                                           "candidates", "keys", "paths", "n_dps")},
     }
+    if args.batch_pairs > 0:
+        line["batch"] = batch_bench(args, scene, o, rank, stream, flush)
+        launches += line["batch"]["gpu_launches"]
+        line["gpu_launches"] = int(launches)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        info = run_oracle_sample(_env_int("NRT_CPU_SAMPLE", 20000))
+        info = run_oracle_sample(_env_int("NRT_CPU_SAMPLE", 150000))
         line["cpu_baseline"] = {
             "value": info["casts"] / info["seconds"], "unit": "ray-segments/s",
             "cores": info["cores"], "kind": "oracle",
@@ -313,6 +385,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rays", type=int, default=N_RAYS)
+    ap.add_argument("--batch-pairs", type=int, default=256,
+                    help="robot-trajectory batch size (0 skips the batch measurement)")
+    ap.add_argument("--batch-steps", type=int, default=3)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

@@ -92,6 +92,7 @@ struct nrt_result {
   void* work = nullptr;
   cudaGraphExec_t graph = nullptr;
   float graph_ms = 0.0f;
+  int64_t graph_launches = 0;  // kernel nodes recorded into the graph
 };
 
 namespace nrt {

@@ -1639,6 +1639,7 @@ nrt_status batch_graph_build(nrt_result* r) {
     r->ev[e] = nullptr;
   }
   cudaGraph_t g;
+  launch_counter() = 0;
   TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   rc = enqueue_trace(r, S, C, nullptr, order, false);
   Records R{r->rec_q, r->rec_n, r->rec_d, r->rec_i, r->n_traced};
@@ -1650,6 +1651,7 @@ nrt_status batch_graph_build(nrt_result* r) {
     rc = enqueue_rest(r, *W, S, C, order);
   }
   cudaError_t e2 = cudaStreamEndCapture(st, &g);
+  r->graph_launches = launch_counter();
   if (rc != NRT_OK) return rc;
   if (e2 != cudaSuccess) {
     ctx->last_error = std::string("graph capture: ") + cudaGetErrorString(e2);
@@ -1688,6 +1690,7 @@ nrt_status batch_graph_replay(nrt_result* r, const float* tx_host) {
   cudaEventElapsedTime(&r->graph_ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  launch_counter() = r->graph_launches;
   return finish_result(r);
 }
 
