@@ -116,6 +116,26 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    once the kernel sources have changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "office_sim_top_kernels.md")
+    if not os.path.exists(path):
+        return None
+    val = sha = None
+    for ln in open(path):
+        f = ln.split()
+        if len(f) == 3 and f[0] == "traffic_bytes_per_launch" and f[1] == kernel:
+            val = float(f[2])
+        if len(f) == 2 and f[0] == "source_sha256":
+            sha = f[1]
+    h = hashlib.sha256()
+    for rel in ("csrc/sim.cu", "csrc/nrt_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2507_04021_gb300", rel), "rb").read())
+    return val if (val is not None and sha == h.hexdigest()) else None
+
+
 def _alg_bytes():
     d = json.load(open(os.path.join(ROOT, "tests", "golden", "office_algorithmic_bytes.json")))
     return d
@@ -340,7 +360,7 @@ def ours(args):
     tr_ms = float(np.mean(trace_ms))
     achieved = seg_per_launch * ab["bytes_per_segment"] / (tr_ms / 1000.0) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "trace_kernel",
+            "frac": achieved / peak, "traffic": _traffic("trace_kernel"), "kernel": "trace_kernel",
             "peak_kind": peak_kind, "bytes_per_segment": ab["bytes_per_segment"],
             "segments_per_launch": seg_per_launch, "kernel_ms": tr_ms}
     ph = {k: float(np.mean([x[k] for x in phases])) for k in phases[0]}
