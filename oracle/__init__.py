@@ -92,6 +92,8 @@ def _declare(L):
     L.orc_sim_n_paths.restype = C.c_int64
     L.orc_sim_n_paths.argtypes = [_P]
     L.orc_sim_paths.argtypes = [_P] + [_P] * 13
+    L.orc_sim_ray_labels.restype = None
+    L.orc_sim_ray_labels.argtypes = [_P, _P, _P]
     L.orc_sim_cand_status.restype = C.c_int
     L.orc_sim_cand_status.argtypes = [_P, C.c_uint64, C.c_uint64, C.c_int64]
     L.orc_sim_n_tried.restype = C.c_int64
@@ -311,6 +313,15 @@ class OracleSim:
     def cand_status(self, hi, lo, ray) -> int:
         """0 certainly not a candidate, 1 certainly a candidate, 2 uncertain."""
         return int(lib().orc_sim_cand_status(self._h, int(hi), int(lo), int(ray)))
+
+    def ray_labels(self):
+        """Per row (ray_ids order): 1 if the ray is a member of a valid
+        specular key; and whether that is ambiguous under rounding."""
+        n = self.ray_ids.shape[0]
+        lab = np.zeros(n, np.int32)
+        amb = np.zeros(n, np.int32)
+        lib().orc_sim_ray_labels(self._h, _ptr(lab), _ptr(amb))
+        return lab.astype(np.uint8), amb.astype(bool)
 
     def tried(self):
         """Flattened tried lists (ray, valid, ambiguous) in key order; see keys()['n_tried']."""

@@ -1262,6 +1262,52 @@ int64_t orc_sim_n_tried(void* s) {
 }
 
 // Flattened per-key lists of the candidates tried, in key order.
+// Training labels of the launch proposal (an addition to the paper's
+// method): a ray is labelled 1 when it is a candidate (member) of a valid
+// specular key, whichever ray represents the key.  amb[row] = 1 when that
+// could change under rounding: the ray's membership or the key's validity
+// is uncertain and the ray is not certainly labelled 1 by another key.
+void orc_sim_ray_labels(void* s, int32_t* label, int32_t* amb) {
+  Sim* sim = (Sim*)s;
+  const size_t n = sim->excl.size();
+  for (size_t i = 0; i < n; ++i) label[i] = amb[i] = 0;
+  auto row_of = [&](int64_t rid) -> int64_t {
+    if (rid < 0 || rid >= (int64_t)sim->ray_pos.size()) return -1;
+    return sim->ray_pos[rid];
+  };
+  for (const KeyOut& k : sim->keys) {
+    if (k.type != 0 || k.k < 1) continue;  // specular keys (LOS has no member rays)
+    auto ct = sim->cands.find(k.key);
+    if (ct != sim->cands.end())
+      for (const Cand& c : ct->second) {
+        const int64_t row = row_of(c.ray);
+        if (row < 0) continue;
+        if (k.valid && k.certain && c.certain) label[row] = 1;
+        else if (k.valid || !k.certain) amb[row] = 1;
+      }
+    auto ut = sim->uncertain_cand.find(k.key);
+    if (ut != sim->uncertain_cand.end() && (k.valid || !k.certain))
+      for (int64_t rid : ut->second) {
+        const int64_t row = row_of(rid);
+        if (row >= 0) amb[row] = 1;
+      }
+  }
+  // uncertain candidates of keys the oracle never formed
+  for (const auto& kv : sim->uncertain_cand) {
+    if (((kv.first.hi >> 55) & 1) != 0) continue;
+    bool known = false;
+    for (const KeyOut& k : sim->keys)
+      if (k.key.hi == kv.first.hi && k.key.lo == kv.first.lo) { known = true; break; }
+    if (known) continue;
+    for (int64_t rid : kv.second) {
+      const int64_t row = row_of(rid);
+      if (row >= 0) amb[row] = 1;
+    }
+  }
+  for (size_t i = 0; i < n; ++i)
+    if (label[i]) amb[i] = 0;
+}
+
 void orc_sim_tried(void* s, int64_t* ray, int32_t* valid, int32_t* amb) {
   Sim* sim = (Sim*)s;
   int64_t o = 0;

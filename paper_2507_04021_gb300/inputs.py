@@ -329,3 +329,44 @@ def ray_budgets(n_pairs: int = 256, lo: int = 100_000, hi: int = 1_000_000,
 def hidden_materials(n_labels: int = 8, seed: int = SEED_HIDDEN_MATERIALS):
     """Ground-truth materials for the material-learning workload."""
     return office_materials(seed, n_labels)
+
+
+# ---------------------------------------------------------------- learned proposal
+MLP_IN = 96       # Fourier features: 6 coordinates x 8 octaves x (sin, cos)
+MLP_HIDDEN = 128  # three hidden layers
+
+
+def mlp_param_count(n_in: int = MLP_IN, h: int = MLP_HIDDEN) -> int:
+    return h * n_in + h + 2 * (h * h + h) + h + 1
+
+
+def mlp_init(seed: int = SEED_MLP, n_in: int = MLP_IN, h: int = MLP_HIDDEN) -> np.ndarray:
+    """Initial parameters of the proposal network, packed float32:
+    W1[h][n_in], b1[h], W2[h][h], b2[h], W3[h][h], b3[h], w4[h], b4.
+    Weights uniform in +-sqrt(6 / fan_in) (He-uniform for ReLU layers),
+    biases zero."""
+    rng = rng_for(seed)
+    parts = []
+    for fan_in, fan_out in ((n_in, h), (h, h), (h, h), (h, 1)):
+        a = np.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-a, a, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_samples(n: int, n_tx: int, n_rays: int, pos_rate: float = 0.05, seed: int = SEED_MLP):
+    """Synthetic training samples for the proposal network's parity tests:
+    (tx index [n] int32, ray id [n] uint32, label [n] float32 in {0, 1})."""
+    rng = rng_for(seed, 1)
+    return (rng.integers(0, n_tx, n).astype(np.int32),
+            rng.integers(0, n_rays, n).astype(np.uint32),
+            (rng.random(n) < pos_rate).astype(np.float32))
+
+
+def mlp_logits(n: int, seed: int = SEED_MLP) -> np.ndarray:
+    """Synthetic logits for the launch-selection parity tests: a smooth
+    profile over the index (as a trained network gives over neighbouring
+    directions) plus noise, float32."""
+    rng = rng_for(seed, 2)
+    i = np.arange(n)
+    return (3.0 * np.sin(i * 2e-4) - 2.0 + 0.5 * rng.standard_normal(n)).astype(np.float32)

@@ -1,0 +1,54 @@
+"""Pin of the proposal's training labels (a ray is labelled 1 when it is a
+member of a valid specular key under RX-sphere capture): re-derived here in
+FP64 from the oracle's per-ray hit records by the capture rule (closest
+approach of each segment to the RX sphere, Sec. II-B) and the keys'
+validity, independently of the oracle's candidate bookkeeping."""
+import numpy as np
+
+import oracle
+from paper_2507_04021_gb300 import inputs
+
+RX = np.array([[4.0, 3.0, 1.2], [1.5, 3.2, 1.0]], np.float32)
+
+
+def test_labels_match_capture_rule_rederived():
+    room = inputs.room_scene()
+    osc = oracle.OracleScene(room.pos, room.nrm, room.surf, room.mat, rho=0.0625, r_p=0.05,
+                             grid_cell=0.25)
+    n_rays = 60000
+    p = oracle.SimParams(max_depth=2, capture=0, diffuse=0, n_rays=n_rays, rep_tries=8, r_rx=0.3)
+    sim = oracle.OracleSim(osc, room.tx, RX, p)
+    lab, amb = sim.ray_labels()
+    print('labelled', int(lab.sum()), 'ambiguous', int(amb.sum()))
+    K = sim.keys()
+    valid = {(int(h), int(l)) for h, l, v, t in zip(K["hi"], K["lo"], K["valid"], K["certain"])
+             if v and t}
+    H = sim.hits()
+    d0 = oracle.fib_dirs(n_rays, np.arange(n_rays)).astype(np.float32).astype(np.float64)
+    tx = room.tx.astype(np.float64)
+    rx = RX.astype(np.float64)
+    want = np.zeros(n_rays, np.uint8)
+    for i in range(n_rays):
+        o, d = tx, d0[i]
+        labels = []
+        for s in range(H["n_hits"][i]):
+            q, nrm = H["q"][i, s], H["n"][i, s]
+            labels.append(int(room.surf[H["idx"][i, s]]))
+            d = d - 2.0 * np.dot(d, nrm) * nrm
+            d = d / np.linalg.norm(d)
+            o = q
+            k = s + 1
+            t_end = H["t"][i, s + 1] if s + 1 < H["n_hits"][i] else np.inf
+            for j in range(rx.shape[0]):
+                ts = min(max(np.dot(rx[j] - o, d), 0.0), t_end)
+                if np.linalg.norm(o + ts * d - rx[j]) <= 0.3:
+                    hi = (j << 56) | (k << 52) | (labels[4] if k > 4 else 0)
+                    lo = 0
+                    for m in range(min(k, 4)):
+                        lo |= labels[m] << (16 * m)
+                    if (hi, lo) in valid:
+                        want[i] = 1
+    ok = ~amb
+    assert lab.sum() > 50
+    assert np.array_equal(lab[ok], want[ok]), np.nonzero(lab[ok] != want[ok])[0][:10]
+    assert amb.mean() < 0.01
