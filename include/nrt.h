@@ -66,14 +66,14 @@ typedef struct {
   int32_t kappa;        /* refinement retries (Sec. II-B-2) */
   int32_t rep_tries;    /* candidates validated per path key, in ray-id order (1..32) */
   int32_t record_hits;  /* 1: keep per-ray hit records readable by nrt_hits_read */
-  int32_t reserved0;
+  int32_t ray_labels;   /* 1: per-ray proposal labels, readable by nrt_ray_labels_read */
   int64_t n_rays;       /* N of the Fibonacci-sphere launch */
   float r_rx;           /* RX sphere radius, m (sphere capture) */
   float t_min;          /* minimum hit distance, m (default 1e-3) */
   float t_a_deg;        /* refinement angle threshold, degrees */
   float t_d;            /* refinement plane-distance threshold, m */
   float freq;           /* carrier frequency, Hz */
-  float reserved1;
+  int32_t keep_keys;    /* 1: keep per-key validation summaries, readable by nrt_keys_read */
   int64_t key_capacity;   /* hash-table slots (power of two; 0 = automatic) */
   int64_t cand_capacity;  /* candidate buffer entries (0 = automatic) */
 } nrt_trace_params;
@@ -128,6 +128,10 @@ void nrt_destroy(nrt_ctx* ctx);
 
 /* Synchronise the context stream. */
 nrt_status nrt_sync(nrt_ctx* ctx);
+
+/* The context's CUDA stream (cudaStream_t) into *stream: the stream every
+ * call enqueues its work on. */
+nrt_status nrt_get_stream(const nrt_ctx* ctx, void** stream);
 
 /* Fill the paper's default trace parameters. */
 void nrt_trace_params_default(nrt_trace_params* p);
@@ -294,6 +298,98 @@ nrt_status nrt_autotune_batch(nrt_result* result, const int32_t* packets, const 
  * Errors: NRT_ERR_ARG for NULL pointers or more than 256 labels;
  * NRT_ERR_STATE before nrt_set_materials; NRT_ERR_CUDA. */
 nrt_status nrt_backward_noalloc(nrt_result* result, const float* dL_dpower, float* grad);
+
+/* Per-key validation summary of a simulation run with keep_keys = 1 (used to
+ * merge ray-range shards into the single-run result, Sec. II-B's lowest valid
+ * ray per key): for each of the result's keys (nrt_result_counts' keys),
+ * host arrays key_hi/key_lo (uint64), tried (uint32: candidates validated,
+ * in ray-id order, the valid one included) and rep (uint32: ray id of the
+ * validated candidate, 0xFFFFFFFF when the key found no valid candidate).
+ * Errors: NRT_ERR_STATE when not requested. */
+nrt_status nrt_keys_read(const nrt_result* result, uint64_t* key_hi, uint64_t* key_lo,
+                         uint32_t* tried, uint32_t* rep);
+
+/* ------------------------------------------------------------------ learned launch proposal
+ * Not part of the paper, which traces a fixed Fibonacci launch (Sec. II-B):
+ * a small network scores launch directions by the probability that the ray
+ * is a member of a valid specular path key, and a Gumbel-top-k draw over
+ * its logits picks the rays to trace (as a ray subset of the same launch).
+ *
+ * Training labels: with trace parameter ray_labels = 1, a simulation marks
+ * each traced ray 1 when it is a candidate (member) of a valid specular key,
+ * whichever ray represents the key.  host uint8_t labels[n_rows], rows in
+ * ascending ray-id order.  Errors: NRT_ERR_STATE when not requested. */
+nrt_status nrt_ray_labels_read(const nrt_result* result, uint8_t* labels);
+
+/* The network: features = sin and cos of pi 2^k v_c for the 6 coordinates
+ * v = (float32 launch direction, (tx - box centre) / box half-size) and
+ * k = 0..7 (96 inputs, column (c * 8 + k) * 2 + {0 sin, 1 cos}); layers
+ * 96 -> 128 -> 128 -> 128 (ReLU) -> 1 logit.  Weights and activations are
+ * BF16, contractions accumulate in FP32 on the tensor cores, biases and the
+ * master parameters are FP32.  Packed parameter order (float32):
+ * W1[128][96], b1[128], W2[128][128], b2[128], W3[128][128], b3[128],
+ * w4[128], b4[1]: 45,569 values. */
+typedef struct nrt_mlp nrt_mlp;
+
+typedef struct {
+  float lr, beta1, beta2, eps; /* Adam (Kingma and Ba) with bias correction */
+  float pos_weight;            /* weight of positive labels in the cross-entropy */
+  int32_t batch;               /* samples per step, a positive multiple of 128 */
+} nrt_mlp_train_opts;
+
+/* params: host float[n_params] (n_params must be 45,569); box_min/box_max:
+ * host float[3], the scene box used to normalise the TX; n_rays: N of the
+ * Fibonacci launch whose directions are scored.  The network lives on the
+ * context's device; Adam state starts at zero. */
+nrt_status nrt_mlp_create(nrt_ctx* ctx, const float* params, int64_t n_params,
+                          const float* box_min, const float* box_max, int64_t n_rays,
+                          nrt_mlp** out);
+void nrt_mlp_free(nrt_mlp* mlp);
+/* host float[45569]: the FP32 master parameters / the gradient of the last step */
+nrt_status nrt_mlp_params_read(const nrt_mlp* mlp, float* params);
+nrt_status nrt_mlp_grads_read(const nrt_mlp* mlp, float* grads);
+
+/* BF16 input features of launch rays ray_ids (device uint32[n]; NULL: rays
+ * 0..n-1) from TX tx (host float[3]) into device uint16_t[n][96] (bfloat16
+ * bits).  Asynchronous on the context stream. */
+nrt_status nrt_mlp_features(nrt_mlp* mlp, const float* tx, const uint32_t* ray_ids, int64_t n,
+                            uint16_t* out);
+
+/* Logits of launch rays ray_ids (device uint32[n] or NULL) from TX tx (host
+ * float[3]) into device float[n].  Asynchronous on the context stream. */
+nrt_status nrt_mlp_score(nrt_mlp* mlp, const float* tx, const uint32_t* ray_ids, int64_t n,
+                         float* logits);
+
+/* n_steps Adam steps of the mean weighted binary cross-entropy on device
+ * samples: tx_table float[n_tx][3], tx_index int32[n], ray_id uint32[n],
+ * label float[n] in {0, 1}; step s uses the `batch` samples at positions
+ * start + s batch, ... (mod n) of `order` (device uint32[n] permutation, or
+ * NULL for 0..n-1).  loss: host float[n_steps] (mean loss of each step) or
+ * NULL.  Synchronises.  Errors: NRT_ERR_ARG; NRT_ERR_TIMEOUT if a tensor-core
+ * wait ran out (the step's results are then invalid). */
+nrt_status nrt_mlp_train(nrt_mlp* mlp, const float* tx_table, int32_t n_tx,
+                         const int32_t* tx_index, const uint32_t* ray_id, const float* label,
+                         int64_t n, const uint32_t* order, int64_t start, int32_t n_steps,
+                         const nrt_mlp_train_opts* opts, float* loss);
+
+/* Launch selection: the k_top largest keys fl32(logit_i + fl32(g_i)), g_i
+ * standard Gumbel noise from a SplitMix64 counter generator (stream `seed`,
+ * counter i), ties to the smaller index; plus one uniform index in each of
+ * k_uniform equal strata of [0, n) (counters n + s).  The union, unique and
+ * ascending, goes to device uint32 ids[] (capacity k_top + k_uniform);
+ * *n_ids (host) receives its size.  logits: device float[n].  Synchronises. */
+nrt_status nrt_propose(nrt_ctx* ctx, const float* logits, int64_t n, int64_t k_top,
+                       int64_t k_uniform, uint64_t seed, uint32_t* ids, int64_t* n_ids);
+
+/* The tensor-core contraction behind the network: C[M][N] (+)= A[M][K] B[N][K]^T,
+ * A and B bfloat16 bits in K-major rows (device, 16-byte aligned, lda/ldb
+ * multiples of 8), C float (device, ldc a multiple of 4).  N a multiple of
+ * 16 in [16, 256]; K a multiple of 8.  accumulate = 1 adds into C; k_split > 0
+ * splits K across thread blocks (implies adding into C).  Synchronises.
+ * Errors: NRT_ERR_ARG on shapes or alignment; NRT_ERR_TIMEOUT. */
+nrt_status nrt_gemm_bf16(nrt_ctx* ctx, const uint16_t* A, int64_t lda, const uint16_t* B,
+                         int64_t ldb, float* C, int64_t ldc, int64_t M, int32_t N, int64_t K,
+                         int32_t accumulate, int64_t k_split);
 
 #ifdef __cplusplus
 }

@@ -16,9 +16,12 @@ void free_dev(void* p) {
   if (p) cudaFree(p);
 }
 
-// Handles are reference counted: a scene keeps its context alive and a result
-// keeps its scene alive, so the *_free calls may come in any order.
-void ctx_release(nrt_ctx* ctx) {
+}  // namespace
+
+// Handles are reference counted: a scene (or a proposal network) keeps its
+// context alive and a result keeps its scene alive, so the *_free calls may
+// come in any order.
+void nrt::ctx_release(nrt_ctx* ctx) {
   if (--ctx->refs > 0) return;
   if (ctx->order) {
     cudaStreamSynchronize(ctx->stream);
@@ -27,6 +30,10 @@ void ctx_release(nrt_ctx* ctx) {
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
+
+namespace {
+
+using nrt::ctx_release;
 
 void scene_release(nrt_scene* s) {
   if (--s->refs > 0) return;
@@ -139,6 +146,12 @@ nrt_status nrt_create(nrt_ctx** out, int device, void* cuda_stream) {
 void nrt_destroy(nrt_ctx* ctx) {
   if (!ctx) return;
   ctx_release(ctx);
+}
+
+nrt_status nrt_get_stream(const nrt_ctx* ctx, void** stream) {
+  if (!ctx || !stream) return NRT_ERR_ARG;
+  *stream = (void*)ctx->stream;
+  return NRT_OK;
 }
 
 nrt_status nrt_sync(nrt_ctx* ctx) {
@@ -365,7 +378,8 @@ void nrt_result_free(nrt_result* r) {
   free_dev(r->queue);
   cudaStream_t st = r->scene->ctx->stream;
   void* pool_ptrs[] = {r->rec_q, r->rec_n, r->rec_d, r->rec_i, r->vis, r->paths,
-                       r->path_a, r->power, r->ctr, r->rx_start_d, r->rx_count_d};
+                       r->path_a, r->power, r->ctr, r->rx_start_d, r->rx_count_d, r->labels,
+                       r->key_hi, r->key_lo, r->key_tried, r->key_rep};
   for (void* q : pool_ptrs)
     if (q) cudaFreeAsync(q, st);
   for (int e = 0; e < 8; ++e)
@@ -462,6 +476,37 @@ nrt_status nrt_paths_read(const nrt_result* r, const nrt_path_view* v) {
       v->a[2 * i + 1] = r->field_done ? a[i].y : 0.f;
     }
   }
+  return NRT_OK;
+}
+
+nrt_status nrt_keys_read(const nrt_result* r, uint64_t* key_hi, uint64_t* key_lo, uint32_t* tried,
+                         uint32_t* rep) {
+  if (!r || !key_hi || !key_lo || !tried || !rep) return NRT_ERR_ARG;
+  nrt_ctx* ctx = r->scene->ctx;
+  if (!r->key_hi) {
+    ctx->last_error = "key summaries were not requested (trace parameter keep_keys)";
+    return NRT_ERR_STATE;
+  }
+  const int64_t n = std::min<int64_t>(r->counters.keys, r->key_cap);
+  cudaStream_t st = ctx->stream;
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(key_hi, r->key_hi, n * 8, cudaMemcpyDeviceToHost, st));
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(key_lo, r->key_lo, n * 8, cudaMemcpyDeviceToHost, st));
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(tried, r->key_tried, n * 4, cudaMemcpyDeviceToHost, st));
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(rep, r->key_rep, n * 4, cudaMemcpyDeviceToHost, st));
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  return NRT_OK;
+}
+
+nrt_status nrt_ray_labels_read(const nrt_result* r, uint8_t* labels) {
+  if (!r || !labels) return NRT_ERR_ARG;
+  nrt_ctx* ctx = r->scene->ctx;
+  if (!r->labels) {
+    ctx->last_error = "ray labels were not requested (trace parameter ray_labels)";
+    return NRT_ERR_STATE;
+  }
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(labels, r->labels, r->n_traced, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return NRT_OK;
 }
 

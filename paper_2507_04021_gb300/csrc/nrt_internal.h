@@ -78,6 +78,13 @@ struct nrt_result {
   int64_t path_cap = 0;
   void* paths = nullptr;     // PathRec[path_cap]
   float2* path_a = nullptr;  // [path_cap]
+  uint8_t* labels = nullptr;  // [n_traced] proposal labels (ray_labels)
+  // per-key validation summaries (keep_keys), key_cap entries
+  uint64_t* key_hi = nullptr;
+  uint64_t* key_lo = nullptr;
+  uint32_t* key_tried = nullptr;
+  uint32_t* key_rep = nullptr;
+  int64_t key_cap = 0;
   double* power = nullptr;   // [n_rx]
   int64_t* rx_start_d = nullptr;  // [n_rx] device ranges of the sorted paths
   int64_t* rx_count_d = nullptr;
@@ -135,6 +142,9 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv
                       int bits, cudaStream_t st);
 
 SceneView scene_view(const nrt_scene* s);
+
+// drop one reference to a context (frees it with the last one)
+void ctx_release(nrt_ctx* ctx);
 
 // kernels launched on this host thread since the last reset
 int64_t& launch_counter();

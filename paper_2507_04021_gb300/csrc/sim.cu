@@ -268,7 +268,24 @@ struct EmitArgs {
   uint2* cand;              // candidates (slot, row) at per-ray offsets
   const uint32_t* cand_off; // [launch index] first candidate of the ray
   uint32_t* cand_cnt;       // [launch index] candidates of the ray (count pass)
+  const uint32_t* key_status;  // label pass: validation status per key id
+  uint8_t* labels;             // label pass: [row] member of a valid specular key
 };
+
+enum { kModeEmit = 0, kModeCount = 1, kModeLabel = 2 };
+
+// Slot of an existing key, or ~0 (label pass; the table is complete).
+__device__ __forceinline__ uint64_t find_key(const EmitArgs& A, uint64_t hi, uint64_t lo,
+                                             uint64_t f) {
+  uint64_t slot = f & A.T.mask;
+  for (int probe = 0; probe < kMaxProbe; ++probe) {
+    const unsigned long long g = A.T.fp[slot];
+    if (g == 0ull) return ~0ull;
+    if (g == (unsigned long long)f && A.T.hi[slot] == hi && A.T.lo[slot] == lo) return slot;
+    slot = (slot + 1) & A.T.mask;
+  }
+  return ~0ull;
+}
 
 // Hash insert by one lane on behalf of the lanes holding the same key (same
 // fingerprint); returns the slot.  No shared counters are touched: key ids
@@ -298,10 +315,11 @@ __device__ __forceinline__ uint64_t insert_key(const EmitArgs& A, uint64_t hi, u
 // One candidate per lane with pred set (all lanes of the warp call this
 // together).  Lanes with equal keys are merged first: one lane inserts the
 // key and records the group's lowest row; every lane still stores its own
-// (slot, row) candidate, at its ray's next candidate position.  kCount only
-// counts candidates per ray and per-warp distinct keys (an upper bound on
-// the table's keys).
-template <bool kCount>
+// (slot, row) candidate, at its ray's next candidate position.  The count
+// mode only counts candidates per ray and per-warp distinct keys (an upper
+// bound on the table's keys); the label mode sets n_mine to 1 when the key
+// is a validated specular key.
+template <int kMode>
 __device__ __forceinline__ void warp_emit(const EmitArgs& A, bool pred, uint64_t hi, uint64_t lo,
                                           uint32_t row, unsigned long long* ctr, uint32_t& n_mine,
                                           unsigned long long& n_lead) {
@@ -309,9 +327,15 @@ __device__ __forceinline__ void warp_emit(const EmitArgs& A, bool pred, uint64_t
   if (!act || !pred) return;
   const int lane = threadIdx.x & 31;
   const uint64_t f = key_fp(hi, lo);
+  if (kMode == kModeLabel) {
+    if ((hi >> 55) & 1ull) return;  // specular keys only
+    const uint64_t slot = find_key(A, hi, lo, f);
+    if (slot != ~0ull && A.key_status[A.T.kid[slot]] == 1u) n_mine = 1u;
+    return;
+  }
   const unsigned peers = __match_any_sync(act, f);
   const int leader = __ffs(peers) - 1;
-  if (kCount) {
+  if (kMode == kModeCount) {
     ++n_mine;
     if (lane == leader) ++n_lead;
     return;
@@ -332,7 +356,7 @@ __device__ __forceinline__ void warp_emit(const EmitArgs& A, bool pred, uint64_t
 // Candidates of every ray (Sec. II-B): a warp walks 32 rays in launch order
 // (neighbouring directions), bounce by bounce and RX by RX in lockstep, so
 // that rays that found the same key merge before touching the hash table.
-template <bool kCount>
+template <int kMode>
 __global__ void __launch_bounds__(256)
     emit_kernel(SceneView S, SimConst C, const float4* __restrict__ rx, Records R,
                 const uint32_t* __restrict__ vis, const uint32_t* __restrict__ order, EmitArgs A,
@@ -349,7 +373,7 @@ __global__ void __launch_bounds__(256)
       active = false;
       row = 0u;
     }
-    uint32_t n_mine = (!kCount && active) ? A.cand_off[t] : 0u;
+    uint32_t n_mine = (kMode == kModeEmit && active) ? A.cand_off[t] : 0u;
     const int pair_j = (C.batch && active) ? pair_of_row(C, row) : 0;
     uint16_t lab[kMaxDepth];
     bool alive = active;
@@ -378,10 +402,10 @@ __global__ void __launch_bounds__(256)
           const int j = C.batch ? pair_j : jv;
           uint64_t hi = 0, lo = 0;
           if (v) make_key(j, 0, k, lab, vox, &hi, &lo);
-          warp_emit<kCount>(A, v, hi, lo, row, ctr, n_mine, n_lead);
+          warp_emit<kMode>(A, v, hi, lo, row, ctr, n_mine, n_lead);
           if (C.diffuse) {
             if (v) make_key(j, 1, k, lab, vox, &hi, &lo);
-            warp_emit<kCount>(A, v, hi, lo, row, ctr, n_mine, n_lead);
+            warp_emit<kMode>(A, v, hi, lo, row, ctr, n_mine, n_lead);
           }
         }
       } else {
@@ -403,16 +427,17 @@ __global__ void __launch_bounds__(256)
           }
           uint64_t hi = 0, lo = 0;
           if (v) make_key(j, 0, k, lab, nullptr, &hi, &lo);
-          warp_emit<kCount>(A, v, hi, lo, row, ctr, n_mine, n_lead);
+          warp_emit<kMode>(A, v, hi, lo, row, ctr, n_mine, n_lead);
         }
       }
     }
-    if (kCount && active) {
+    if (kMode == kModeLabel && active) A.labels[row] = (uint8_t)n_mine;
+    if (kMode == kModeCount && active) {
       A.cand_cnt[t] = n_mine;
       n_total += n_mine;
     }
   }
-  if (kCount) {
+  if (kMode == kModeCount) {
     count_add(ctr + kCtrCands, n_total);
     count_add(ctr + kCtrLeaders, n_lead);
   }
@@ -807,6 +832,25 @@ __global__ void next_apply_kernel(const uint32_t* __restrict__ list,
       K.cur[kid] = nx;
       out_list[warp_inc(out_cnt)] = kid;
     }
+  }
+}
+
+// Per-key summaries for merging ray-range shards: candidates tried (the
+// valid one included) and the ray id of the validated candidate.
+__global__ void key_summary_kernel(const unsigned long long* __restrict__ n_keys_p, KeyState K,
+                                   Table T, const uint32_t* __restrict__ ray_of_row,
+                                   uint64_t* __restrict__ hi, uint64_t* __restrict__ lo,
+                                   uint32_t* __restrict__ tried, uint32_t* __restrict__ rep) {
+  const int64_t n_keys = (int64_t)*n_keys_p;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_keys;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t slot = K.slot[i];
+    hi[i] = T.hi[slot];
+    lo[i] = T.lo[slot];
+    const bool valid = K.status[i] == 1u;
+    tried[i] = K.tries[i] + (valid ? 1u : 0u);
+    const uint32_t row = K.cur[i];
+    rep[i] = valid ? (ray_of_row ? ray_of_row[row] : row) : 0xFFFFFFFFu;
   }
 }
 
@@ -1276,6 +1320,17 @@ nrt_status alloc_result(nrt_result* r, const Caps& c, bool with_paths) {
   if (!r->power) TRY(dalloc(&r->power, r->n_rx, st));
   if (!r->rx_start_d) TRY(dalloc(&r->rx_start_d, r->n_rx, st));
   if (!r->rx_count_d) TRY(dalloc(&r->rx_count_d, r->n_rx, st));
+  if (r->p.ray_labels && !r->labels) TRY(dalloc(&r->labels, r->n_traced, st));
+  if (with_paths && r->p.keep_keys) {
+    void* old[] = {r->key_hi, r->key_lo, r->key_tried, r->key_rep};
+    for (void* q : old)
+      if (q) cudaFreeAsync(q, st);
+    r->key_cap = c.keys;
+    TRY(dalloc(&r->key_hi, c.keys, st));
+    TRY(dalloc(&r->key_lo, c.keys, st));
+    TRY(dalloc(&r->key_tried, c.keys, st));
+    TRY(dalloc(&r->key_rep, c.keys, st));
+  }
   if (with_paths) {
     if (r->paths) cudaFreeAsync(r->paths, st);
     if (r->path_a) cudaFreeAsync(r->path_a, st);
@@ -1342,7 +1397,7 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   A.cand_cap = (uint64_t)c.cand;
   A.cand = W.cand;
   A.cand_off = W.cand_off;
-  emit_kernel<false><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, ctr); count_launch();
+  emit_kernel<kModeEmit><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, ctr); count_launch();
 
   // key ids from the occupied slots, specular first, each type in launch
   // order of the key's lowest row
@@ -1407,6 +1462,20 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
                                                                   cur_d, W.cnt + kCntCurD); count_launch();
   }
   if (r->ev[5]) TRY(cudaEventRecord(r->ev[5], st));
+  if (r->p.keep_keys) {
+    key_summary_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(
+        W.cnt + kCntKeys, W.K, W.T, C.batch ? nullptr : r->ray_of_row, r->key_hi, r->key_lo,
+        r->key_tried, r->key_rep); count_launch();
+  }
+  if (r->p.ray_labels) {
+    // proposal labels: rays that are members of a validated specular key
+    EmitArgs L{};
+    L.T = W.T;
+    L.key_status = W.K.status;
+    L.labels = r->labels;
+    emit_kernel<kModeLabel><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, L,
+                                                                    ctr); count_launch();
+  }
 
   // deterministic order of the paths (padding sorts last), ranges, field
   path_sortkey_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>(W.raw, ctr + kCtrPaths, c.paths,
@@ -1542,7 +1611,7 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
   Records R{r->rec_q, r->rec_n, r->rec_d, r->rec_i, n};
   EmitArgs A{};
   A.cand_cnt = W.cand_cnt;
-  emit_kernel<true><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, r->ctr); count_launch();
+  emit_kernel<kModeCount><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, r->ctr); count_launch();
   scan_exclusive(W.cand_cnt, W.cand_off, n, st);
   unsigned long long cnt2[2] = {0, 0};
   TRY(cudaMemcpyAsync(&cnt2[0], r->ctr + kCtrCands, 8, cudaMemcpyDeviceToHost, st));
@@ -1646,7 +1715,7 @@ nrt_status batch_graph_build(nrt_result* r) {
   if (rc == NRT_OK) {
     EmitArgs A{};
     A.cand_cnt = W->cand_cnt;
-    emit_kernel<true><<<blocks_for(r->n_traced, 256, ctx->sm_count), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, r->ctr); count_launch();
+    emit_kernel<kModeCount><<<blocks_for(r->n_traced, 256, ctx->sm_count), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, r->ctr); count_launch();
     scan_exclusive(W->cand_cnt, W->cand_off, r->n_traced, st);
     rc = enqueue_rest(r, *W, S, C, order);
   }

@@ -39,9 +39,9 @@ class TraceParams(C.Structure):
     _fields_ = [
         ("max_depth", C.c_int32), ("capture", C.c_int32), ("diffuse", C.c_int32),
         ("pol", C.c_int32), ("kappa", C.c_int32), ("rep_tries", C.c_int32),
-        ("record_hits", C.c_int32), ("reserved0", C.c_int32), ("n_rays", C.c_int64),
+        ("record_hits", C.c_int32), ("ray_labels", C.c_int32), ("n_rays", C.c_int64),
         ("r_rx", C.c_float), ("t_min", C.c_float), ("t_a_deg", C.c_float), ("t_d", C.c_float),
-        ("freq", C.c_float), ("reserved1", C.c_float), ("key_capacity", C.c_int64),
+        ("freq", C.c_float), ("keep_keys", C.c_int32), ("key_capacity", C.c_int64),
         ("cand_capacity", C.c_int64),
     ]
 
@@ -59,6 +59,11 @@ class Counters(C.Structure):
 class BatchOpts(C.Structure):
     _fields_ = [("packet", C.c_int32), ("schedule", C.c_int32), ("use_graph", C.c_int32),
                 ("reserved", C.c_int32)]
+
+
+class MlpTrainOpts(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("pos_weight", C.c_float), ("batch", C.c_int32)]
 
 
 class PathView(C.Structure):
@@ -110,6 +115,22 @@ def lib():
         L.nrt_batch_replay.argtypes = [_P, _P]
         L.nrt_batch_times.argtypes = [_P, _P, _P]
         L.nrt_autotune_batch.argtypes = [_P, _P, _P, C.c_int, C.c_int, _P, _P]
+        L.nrt_ray_labels_read.argtypes = [_P, _P]
+        L.nrt_keys_read.argtypes = [_P, _P, _P, _P, _P]
+        L.nrt_get_stream.argtypes = [_P, C.POINTER(_P)]
+        L.nrt_mlp_create.argtypes = [_P, _P, C.c_int64, _P, _P, C.c_int64, C.POINTER(_P)]
+        L.nrt_mlp_free.argtypes = [_P]
+        L.nrt_mlp_free.restype = None
+        L.nrt_mlp_params_read.argtypes = [_P, _P]
+        L.nrt_mlp_grads_read.argtypes = [_P, _P]
+        L.nrt_mlp_features.argtypes = [_P, _P, _P, C.c_int64, _P]
+        L.nrt_mlp_score.argtypes = [_P, _P, _P, C.c_int64, _P]
+        L.nrt_mlp_train.argtypes = [_P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, C.c_int64,
+                                    C.c_int32, C.POINTER(MlpTrainOpts), _P]
+        L.nrt_propose.argtypes = [_P, _P, C.c_int64, C.c_int64, C.c_int64, C.c_uint64, _P,
+                                  C.POINTER(C.c_int64)]
+        L.nrt_gemm_bf16.argtypes = [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int64, C.c_int64,
+                                    C.c_int32, C.c_int64, C.c_int32, C.c_int64]
         L.nrt_destroy.restype = None
     return _lib
 
@@ -149,6 +170,12 @@ class Context:
 
     def sync(self):
         self._check(lib().nrt_sync(self._h))
+
+    def stream_handle(self) -> int:
+        """The cudaStream_t the library enqueues on (for torch.cuda.ExternalStream)."""
+        s = _P()
+        self._check(lib().nrt_get_stream(self._h, C.byref(s)))
+        return int(s.value or 0)
 
     def close(self):
         if self._h:
@@ -311,6 +338,23 @@ class Result:
                                            _np_ptr(gc)))
         return ge, gs, gc
 
+    def keys(self):
+        """Per-key validation summary (trace parameter keep_keys = 1):
+        key_hi, key_lo, tried, rep (ray id, 0xFFFFFFFF = no valid candidate)."""
+        n = self.counts()[1]["keys"]
+        out = {"key_hi": np.zeros(n, np.uint64), "key_lo": np.zeros(n, np.uint64),
+               "tried": np.zeros(n, np.uint32), "rep": np.zeros(n, np.uint32)}
+        self.ctx._check(lib().nrt_keys_read(self._h, *[_np_ptr(out[k]) for k in
+                                                        ("key_hi", "key_lo", "tried", "rep")]))
+        return out
+
+    def ray_labels(self):
+        """Per traced row (ascending ray id): 1 if the ray is a member of a valid
+        specular key (needs trace parameter ray_labels = 1)."""
+        out = np.zeros(self.n_traced, np.uint8)
+        self.ctx._check(lib().nrt_ray_labels_read(self._h, _np_ptr(out)))
+        return out
+
     def backward_noalloc(self, dL_dP_dev, grad_dev):
         """nrt_backward_noalloc on caller-owned device buffers (torch CUDA tensors):
         dL_dP_dev float32[n_rx] in, grad_dev float32[3 * n_labels] out.  Enqueued on
@@ -374,3 +418,99 @@ class BatchResult(Result):
         self.ctx._check(lib().nrt_autotune_batch(self._h, _np_ptr(pk), _np_ptr(sc), len(configs),
                                                  int(repeats), _np_ptr(ms), C.byref(best)))
         return ms, int(best.value)
+
+
+# ---------------------------------------------------------------- learned proposal
+N_MLP_PARAMS = 45569
+
+
+def _dev(t):
+    """Device pointer of a torch CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if not (hasattr(t, "data_ptr") and t.is_cuda):
+        raise TypeError("expected a torch CUDA tensor")
+    return _P(t.data_ptr())
+
+
+class Mlp:
+    """The proposal network (nrt_mlp_*): FP32 master parameters and Adam state
+    on the device, BF16 tensor-core contractions."""
+
+    def __init__(self, ctx: Context, params, box_min, box_max, n_rays: int):
+        self.ctx = ctx
+        p = np.ascontiguousarray(params, np.float32)
+        lo = np.ascontiguousarray(box_min, np.float32)
+        hi = np.ascontiguousarray(box_max, np.float32)
+        self._h = _P()
+        ctx._check(lib().nrt_mlp_create(ctx._h, _np_ptr(p), int(p.size), _np_ptr(lo), _np_ptr(hi),
+                                        int(n_rays), C.byref(self._h)))
+        self.n_rays = int(n_rays)
+
+    def params(self):
+        out = np.zeros(N_MLP_PARAMS, np.float32)
+        self.ctx._check(lib().nrt_mlp_params_read(self._h, _np_ptr(out)))
+        return out
+
+    def grads(self):
+        out = np.zeros(N_MLP_PARAMS, np.float32)
+        self.ctx._check(lib().nrt_mlp_grads_read(self._h, _np_ptr(out)))
+        return out
+
+    def features(self, tx, ray_ids_dev, n, out_dev, sync=True):
+        t = np.ascontiguousarray(tx, np.float32).reshape(3)
+        self.ctx._check(lib().nrt_mlp_features(self._h, _np_ptr(t), _dev(ray_ids_dev), int(n),
+                                               _dev(out_dev)))
+        if sync:
+            self.ctx.sync()
+
+    def score(self, tx, ray_ids_dev, n, logits_dev, sync=True):
+        """Logits into logits_dev; the work is enqueued on the context stream
+        and, with sync, waited for before returning."""
+        t = np.ascontiguousarray(tx, np.float32).reshape(3)
+        self.ctx._check(lib().nrt_mlp_score(self._h, _np_ptr(t), _dev(ray_ids_dev), int(n),
+                                            _dev(logits_dev)))
+        if sync:
+            self.ctx.sync()
+
+    def train(self, tx_table_dev, tx_index_dev, ray_id_dev, label_dev, order_dev=None, start=0,
+              steps=1, lr=1e-3, batch=4096, pos_weight=1.0, beta1=0.9, beta2=0.999, eps=1e-8):
+        """Adam steps on device samples (torch CUDA tensors); returns the per-step losses."""
+        n = int(ray_id_dev.shape[0])
+        o = MlpTrainOpts(lr, beta1, beta2, eps, pos_weight, int(batch))
+        loss = np.zeros(int(steps), np.float32)
+        self.ctx._check(lib().nrt_mlp_train(self._h, _dev(tx_table_dev), int(tx_table_dev.shape[0]),
+                                            _dev(tx_index_dev), _dev(ray_id_dev), _dev(label_dev),
+                                            n, _dev(order_dev), int(start), int(steps), C.byref(o),
+                                            _np_ptr(loss)))
+        return loss
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().nrt_mlp_free(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def propose(ctx: Context, logits_dev, k_top: int, k_uniform: int, seed: int, ids_dev) -> int:
+    """nrt_propose: selected launch indices into ids_dev (uint32 capacity
+    k_top + k_uniform); returns how many."""
+    n_out = C.c_int64()
+    ctx._check(lib().nrt_propose(ctx._h, _dev(logits_dev), int(logits_dev.shape[0]), int(k_top),
+                                 int(k_uniform), C.c_uint64(seed), _dev(ids_dev), C.byref(n_out)))
+    return int(n_out.value)
+
+
+def gemm_bf16(ctx: Context, A, B, C_out, accumulate=False, k_split=0):
+    """C_out[M][N] (+)= A[M][K] B[N][K]^T on the tensor cores; A, B torch bfloat16
+    CUDA tensors (row-major), C_out float32."""
+    M, K = A.shape
+    N = B.shape[0]
+    ctx._check(lib().nrt_gemm_bf16(ctx._h, _dev(A), int(A.stride(0)), _dev(B), int(B.stride(0)),
+                                   _dev(C_out), int(C_out.stride(0)), int(M), int(N), int(K),
+                                   int(bool(accumulate)), int(k_split)))
