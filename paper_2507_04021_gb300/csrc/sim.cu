@@ -455,13 +455,28 @@ __global__ void slot_flags_kernel(Table T, int64_t cap, uint32_t* __restrict__ f
   }
 }
 
-__global__ void slot_assign_kernel(Table T, int64_t cap, const uint32_t* __restrict__ fs,
+// 10 bits per axis interleaved (x lowest)
+__device__ __forceinline__ uint32_t spread3(uint32_t x) {
+  x &= 0x3FFu;
+  x = (x | (x << 16)) & 0x030000FFu;
+  x = (x | (x << 8)) & 0x0300F00Fu;
+  x = (x | (x << 4)) & 0x030C30C3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
+// Validation order of a key: type, RX (pair), then the Morton code of the
+// voxel of its lowest row's last interaction point -- the shadow and
+// validation casts of neighbouring keys then leave from neighbouring points
+// toward the same receiver, so a warp's casts traverse the same part of the
+// BVH.
+__global__ void slot_assign_kernel(SceneView S, Records R, Table T, int64_t cap,
+                                   const uint32_t* __restrict__ fs,
                                    const uint32_t* __restrict__ fd, const uint32_t* __restrict__ os,
                                    const uint32_t* __restrict__ od,
                                    const unsigned long long* __restrict__ counts,
                                    uint32_t* __restrict__ key_slot, uint64_t* __restrict__ sort_key,
-                                   uint32_t* __restrict__ sort_val,
-                                   const uint32_t* __restrict__ launch_pos) {
+                                   uint32_t* __restrict__ sort_val) {
   const uint32_t n_spec = (uint32_t)counts[0];  // diffuse ids follow the specular ones
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -471,10 +486,14 @@ __global__ void slot_assign_kernel(Table T, int64_t cap, const uint32_t* __restr
     NRT_GUARD(T.minrow[i] < g_dbg_caps.rows, 2, T.minrow[i])
     T.kid[i] = kid;
     key_slot[kid] = (uint32_t)i;
-    // validation order: launch position of the key's lowest row, so that a
-    // warp validates keys found by neighbouring rays
     const uint32_t m = T.minrow[i];
-    sort_key[kid] = ((uint64_t)(fs[i] ? 0u : 1u) << 32) | (launch_pos ? launch_pos[m] : m);
+    const uint64_t hi = T.hi[i];
+    const int k = (int)((hi >> 52) & 7);
+    int vox[3] = {0, 0, 0};
+    if (k >= 1) voxel_of(S, xyz(R.q[R.at(k - 1, m)]), vox);
+    const uint32_t mort = spread3((uint32_t)max(vox[0], 0)) | (spread3((uint32_t)max(vox[1], 0)) << 1) |
+                          (spread3((uint32_t)max(vox[2], 0)) << 2);
+    sort_key[kid] = ((uint64_t)(fs[i] ? 0u : 1u) << 38) | ((hi >> 56) << 30) | (uint64_t)mort;
     sort_val[kid] = kid;
   }
 }
@@ -500,15 +519,6 @@ __global__ void split_lists_kernel(const uint32_t* __restrict__ sorted, int64_t 
     NRT_GUARD(sorted[i] < g_dbg_caps.keys, 3, sorted[i])
     if (i < ns) spec[i] = sorted[i];
     else diff[i - ns] = sorted[i];
-  }
-}
-
-__global__ void inverse_order_kernel(const uint32_t* __restrict__ order, int64_t n,
-                                     uint32_t* __restrict__ pos) {
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    NRT_GUARD(order[t] < g_dbg_caps.rows, 4, order[t])
-    pos[order[t]] = (uint32_t)t;
   }
 }
 
@@ -938,8 +948,11 @@ __global__ void order_key_kernel(SimConst C, const uint32_t* __restrict__ ray_of
   }
 }
 
+// sorted paths: only the first n entries hold paths (padding sorts last)
 __global__ void path_gather_kernel(const PathRec* __restrict__ src, const uint32_t* __restrict__ idx,
-                                   int64_t n, PathRec* __restrict__ dst) {
+                                   const unsigned long long* __restrict__ n_p, int64_t cap,
+                                   PathRec* __restrict__ dst) {
+  const int64_t n = min((int64_t)*n_p, cap);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     NRT_GUARD(idx[i] < g_dbg_caps.paths, 20, idx[i])
@@ -1234,7 +1247,7 @@ struct Work {
   uint32_t *spec_list = nullptr, *diff_list = nullptr, *list2_s = nullptr, *list2_d = nullptr;
   uint2 *cand = nullptr, *cand2 = nullptr;
   uint32_t *cand_cnt = nullptr, *cand_off = nullptr;
-  uint32_t *fs = nullptr, *fd = nullptr, *os = nullptr, *od = nullptr, *pos = nullptr;
+  uint32_t *fs = nullptr, *fd = nullptr, *os = nullptr, *od = nullptr;
   uint64_t *sk0 = nullptr, *tk0 = nullptr;
   uint32_t *sv0 = nullptr, *tv = nullptr;
   PathRec* raw = nullptr;
@@ -1278,7 +1291,6 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
   TRY(dalloc(&W.fd, c.table, st));
   TRY(dalloc(&W.os, c.table, st));
   TRY(dalloc(&W.od, c.table, st));
-  TRY(dalloc(&W.pos, n_rows, st));
   TRY(dalloc(&W.sk0, c.keys, st));
   TRY(dalloc(&W.tk0, c.keys, st));
   TRY(dalloc(&W.sv0, c.keys, st));
@@ -1295,7 +1307,7 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
 void release_work(Work& W, cudaStream_t st) {
   void* ptrs[] = {W.T.fp, W.T.hi, W.T.lo, W.T.minrow, W.T.kid, W.T.next, W.K.slot, W.K.cur,
                   W.K.tries, W.K.status, W.spec_list, W.diff_list, W.list2_s, W.list2_d, W.cand,
-                  W.cand2, W.cand_cnt, W.cand_off, W.fs, W.fd, W.os, W.od, W.pos, W.sk0, W.tk0,
+                  W.cand2, W.cand_cnt, W.cand_off, W.fs, W.fd, W.os, W.od, W.sk0, W.tk0,
                   W.sv0, W.tv, W.raw, W.psk, W.ptk, W.psi, W.pti, W.cnt, W.order};
   for (void* q : ptrs)
     if (q) cudaFreeAsync(q, st);
@@ -1405,13 +1417,10 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   scan_exclusive(W.fs, W.os, c.table, st);
   scan_exclusive(W.fd, W.od, c.table, st);
   key_count_kernel<<<1, 1, 0, st>>>(W.fs, W.fd, W.os, W.od, c.table, W.cnt); count_launch();
-  if (order) {
-    inverse_order_kernel<<<blocks_for(n, 256, sm), 256, 0, st>>>(order, n, W.pos); count_launch();
-  }
   TRY(cudaMemsetAsync(W.sk0, 0xFF, c.keys * 8, st));
   slot_assign_kernel<<<blocks_for(c.table, 256, sm), 256, 0, st>>>(
-      W.T, c.table, W.fs, W.fd, W.os, W.od, W.cnt, W.K.slot, W.sk0, W.sv0, order ? W.pos : nullptr); count_launch();
-  radix_sort_pairs(W.sk0, W.sv0, W.tk0, W.tv, c.keys, 33, st);
+      S, R, W.T, c.table, W.fs, W.fd, W.os, W.od, W.cnt, W.K.slot, W.sk0, W.sv0); count_launch();
+  radix_sort_pairs(W.sk0, W.sv0, W.tk0, W.tv, c.keys, 40, st);
   split_lists_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.sv0, c.keys, W.cnt, W.spec_list,
                                                                  W.diff_list); count_launch();
   TRY(cudaMemcpyAsync(ctr + kCtrKeys, W.cnt + kCntKeys, 8, cudaMemcpyDeviceToDevice, st));
@@ -1481,8 +1490,8 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   path_sortkey_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>(W.raw, ctr + kCtrPaths, c.paths,
                                                                    W.psk, W.psi); count_launch();
   radix_sort_pairs(W.psk, W.psi, W.ptk, W.pti, c.paths, 44, st);
-  path_gather_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>(W.raw, W.psi, c.paths,
-                                                                  (PathRec*)r->paths); count_launch();
+  path_gather_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>(W.raw, W.psi, ctr + kCtrPaths,
+                                                                  c.paths, (PathRec*)r->paths); count_launch();
   rx_range_kernel<<<(r->n_rx + 63) / 64, 64, 0, st>>>(W.psk, ctr + kCtrPaths, c.paths, r->n_rx,
                                                       r->rx_start_d, r->rx_count_d); count_launch();
   if (sc->have_materials) {
