@@ -168,7 +168,7 @@ __device__ __forceinline__ void count_add(unsigned long long* c, unsigned long l
 // One thread per (RX, DPS); a warp covers 32 consecutive DPS of one RX and
 // writes one bit word.  Visible when nothing is hit before the reception
 // point's voxel could begin, or the first hit lies in the DPS itself.
-__global__ void __launch_bounds__(kTraceThreads)
+__global__ void __launch_bounds__(kTraceThreads, 8)
     vis_kernel(SceneView S, SimConst C, const float4* __restrict__ rx,
                const float4* __restrict__ recv, uint32_t* __restrict__ vis,
                unsigned long long* ctr, float margin) {
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kTraceThreads)
 }
 
 // ---------------------------------------------------------------- LOS
-__global__ void __launch_bounds__(kTraceThreads)
+__global__ void __launch_bounds__(kTraceThreads, 8)
     los_kernel(SceneView S, SimConst C, const float4* __restrict__ rx, PathRec* __restrict__ paths,
                unsigned long long* ctr, int64_t path_cap) {
   NRT_STACK_DECL
@@ -247,7 +247,7 @@ __device__ __forceinline__ unsigned trace_row(const SceneView& S, const SimConst
 // One ray per thread (static grid-stride schedule over the launch order);
 // every interaction continues as a specular reflection (Sec. II-B: the ray
 // count stays constant).  The next cast skips the DPS just hit.
-__global__ void __launch_bounds__(kTraceThreads)
+__global__ void __launch_bounds__(kTraceThreads, 8)
     trace_kernel(SceneView S, SimConst C, const uint32_t* __restrict__ ray_of_row,
                  const uint32_t* __restrict__ order, Records R, unsigned long long* ctr) {
   NRT_STACK_DECL
@@ -590,7 +590,7 @@ __device__ __forceinline__ void finish_key(const ValArgs& A, uint32_t kid, bool 
 // Diffuse: the candidate's own interaction points; the last one scatters
 // toward the RX if the RX is in front of the surface and a cast from the
 // scatter point (skipping its DPS) reaches the RX unobstructed (Sec. II-B-1).
-__global__ void __launch_bounds__(kTraceThreads)
+__global__ void __launch_bounds__(kTraceThreads, 8)
     validate_diffuse_kernel(SceneView S, SimConst C, ValArgs A, const uint32_t* __restrict__ list,
                             const unsigned long long* __restrict__ n_list_p, unsigned long long* ctr) {
   NRT_STACK_DECL
@@ -665,7 +665,7 @@ __global__ void __launch_bounds__(kTraceThreads)
 // most kappa times).  A hit on another surface, a miss or a failed side
 // check ends the candidate.  Finally I_k -> RX must be clear.
 // Coordinates are taken relative to the RX to keep float magnitudes small.
-__global__ void __launch_bounds__(kTraceThreads)
+__global__ void __launch_bounds__(kTraceThreads, 8)
     validate_specular_kernel(SceneView S, SimConst C, ValArgs A, const uint32_t* __restrict__ list,
                              const unsigned long long* __restrict__ n_list_p, unsigned long long* ctr) {
   NRT_STACK_DECL
@@ -1184,7 +1184,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Batch trace as one persistent launch: warps pull work items of `packet`
 // rays of one pair from a queue (uneven budgets balance themselves); the warp
 // that finishes a pair's last item stamps the pair's completion time.
-__global__ void __launch_bounds__(kTraceThreads)
+__global__ void __launch_bounds__(kTraceThreads, 8)
     trace_persistent_kernel(SceneView S, SimConst C, const uint32_t* __restrict__ order, Records R,
                             const uint32_t* __restrict__ chunk_start, int packet,
                             unsigned long long* queue, unsigned long long* stamps,
