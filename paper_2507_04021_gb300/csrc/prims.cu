@@ -130,7 +130,7 @@ __global__ void radix_scatter_kernel(const uint64_t* __restrict__ kin,
     uint32_t v = 0, dg = 0, rank_w = 0;
     if (valid) {
       k = kin[i];
-      v = vin[i];
+      if (vin) v = vin[i];
       dg = (uint32_t)(k >> shift) & 0xFF;
     }
     const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
@@ -145,7 +145,7 @@ __global__ void radix_scatter_kernel(const uint64_t* __restrict__ kin,
       for (int w = 0; w < warp; ++w) before += wcnt[w][dg];
       const uint32_t pos = run[dg] + before + rank_w;
       kout[pos] = k;
-      vout[pos] = v;
+      if (vout) vout[pos] = v;
     }
     __syncthreads();
     uint32_t tot = 0;
@@ -183,7 +183,7 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv
   }
   if (passes & 1) {
     cudaMemcpyAsync(keys, ka, n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
-    cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+    if (vals) cudaMemcpyAsync(vals, va, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
   }
   cudaFreeAsync(counts, st);
   cudaFreeAsync(offs, st);

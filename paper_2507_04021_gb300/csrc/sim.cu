@@ -90,8 +90,18 @@ struct Table {
 struct KeyState {
   uint32_t* slot;    // [key] -> table slot
   uint32_t* cur;     // candidate row being validated
+  uint32_t* pos;     // its position in the sorted candidate array
   uint32_t* tries;
   uint32_t* status;  // 0 pending, 1 valid, 2 invalid
+};
+
+// Candidates sorted once by (table slot, row): a key's candidates form one
+// run in ray order, so its next candidate is the next element of the run.
+struct SortedCand {
+  const uint64_t* key;  // (slot << row_bits) | row; padding ~0 sorts last
+  const unsigned long long* n_p;
+  int64_t cap;
+  int row_bits;
 };
 
 struct Records {
@@ -794,52 +804,53 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
   count_add(ctr + kCtrValCasts, casts);
 }
 
-// next candidate per pending key: the smallest row above the one just tried
-__global__ void next_reset_kernel(const uint32_t* __restrict__ list,
-                                  const unsigned long long* __restrict__ n_p, KeyState K, Table T) {
-  const int64_t n = (int64_t)*n_p;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    NRT_GUARD(list[i] < g_dbg_caps.keys, 13, list[i])
-    NRT_GUARD(K.slot[list[i]] < g_dbg_caps.table, 14, K.slot[list[i]])
-    T.next[K.slot[list[i]]] = kNone;
-  }
-}
-
-// Next candidate per pending key: the smallest row above the one just tried.
-// Candidates of keys that are settled, or not above their key's current row,
-// are never needed again, so the survivors are compacted for the next round.
-__global__ void next_scan_kernel(const uint2* __restrict__ cand,
-                                 const unsigned long long* __restrict__ n_cand_p, int64_t cap,
-                                 KeyState K, Table T, uint2* __restrict__ out,
-                                 unsigned long long* out_cnt) {
-  const int64_t n_cand = min((int64_t)*n_cand_p, cap);
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cand;
+// (slot, row) candidates -> sort keys, in place; entries past the count are
+// padding that sorts last
+__global__ void cand_key_kernel(uint2* __restrict__ cand, const unsigned long long* __restrict__ n_p,
+                                int64_t cap, int row_bits) {
+  const int64_t n = min((int64_t)*n_p, cap);
+  uint64_t* key = reinterpret_cast<uint64_t*>(cand);
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cap;
        c += (int64_t)gridDim.x * blockDim.x) {
+    if (c >= n) {
+      key[c] = ~0ull;
+      continue;
+    }
     const uint2 e = cand[c];
-    NRT_GUARD(e.x < g_dbg_caps.table, 15, e.x)
-    const uint32_t kid = T.kid[e.x];
-    NRT_GUARD(kid < g_dbg_caps.keys, 16, kid)
-    if (K.status[kid] != 0 || e.y <= K.cur[kid]) continue;
-    atomicMin(T.next + e.x, e.y);
-    out[warp_inc(out_cnt)] = e;
+    key[c] = ((uint64_t)e.x << row_bits) | (uint64_t)e.y;
   }
 }
 
+// first position of every slot's run
+__global__ void run_start_kernel(SortedCand SC, uint32_t* __restrict__ start) {
+  const int64_t n = min((int64_t)*SC.n_p, SC.cap);
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t s = SC.key[c] >> SC.row_bits;
+    if (c == 0 || (SC.key[c - 1] >> SC.row_bits) != s) start[s] = (uint32_t)c;
+  }
+}
+
+// Next candidate of each key that failed this round: the next element of its
+// run in the sorted candidates (the smallest row above the one just tried).
 __global__ void next_apply_kernel(const uint32_t* __restrict__ list,
-                                  const unsigned long long* __restrict__ n_p, KeyState K, Table T,
-                                  uint32_t* __restrict__ out_list, unsigned long long* out_cnt) {
+                                  const unsigned long long* __restrict__ n_p, KeyState K,
+                                  SortedCand SC, uint32_t* __restrict__ out_list,
+                                  unsigned long long* out_cnt) {
   const int64_t n = (int64_t)*n_p;
+  const int64_t n_cand = min((int64_t)*SC.n_p, SC.cap);
+  const uint64_t row_mask = (1ull << SC.row_bits) - 1ull;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t kid = list[i];
     NRT_GUARD(kid < g_dbg_caps.keys, 17, kid)
-    NRT_GUARD(K.slot[kid] < g_dbg_caps.table, 18, K.slot[kid])
-    const uint32_t nx = T.next[K.slot[kid]];
-    if (nx == kNone) {
+    const int64_t q = (int64_t)K.pos[kid] + 1;
+    const uint64_t e = q < n_cand ? SC.key[q] : ~0ull;
+    if (q >= n_cand || (e >> SC.row_bits) != (uint64_t)K.slot[kid]) {
       K.status[kid] = 2;
     } else {
-      K.cur[kid] = nx;
+      K.cur[kid] = (uint32_t)(e & row_mask);
+      K.pos[kid] = (uint32_t)q;
       out_list[warp_inc(out_cnt)] = kid;
     }
   }
@@ -864,13 +875,17 @@ __global__ void key_summary_kernel(const unsigned long long* __restrict__ n_keys
   }
 }
 
+// every key starts at the first (lowest-row) candidate of its run
 __global__ void key_init_kernel(const unsigned long long* __restrict__ n_keys_p, KeyState K,
-                                Table T) {
+                                const uint32_t* __restrict__ run_start, SortedCand SC) {
   const int64_t n_keys = (int64_t)*n_keys_p;
+  const uint64_t row_mask = (1ull << SC.row_bits) - 1ull;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_keys;
        i += (int64_t)gridDim.x * blockDim.x) {
     NRT_GUARD(K.slot[i] < g_dbg_caps.table, 19, K.slot[i])
-    K.cur[i] = T.minrow[K.slot[i]];
+    const uint32_t p = run_start[K.slot[i]];
+    K.pos[i] = p;
+    K.cur[i] = (uint32_t)(SC.key[p] & row_mask);
     K.tries[i] = 0;
     K.status[i] = 0;
   }
@@ -1258,8 +1273,7 @@ struct Work {
 };
 
 // round counters in Work::cnt
-enum { kCntSpec = 0, kCntDiff, kCntKeys, kCntCurS, kCntCurD, kCntNxtS, kCntNxtD, kCntCandA,
-       kCntCandB, kCntN };
+enum { kCntSpec = 0, kCntDiff, kCntKeys, kCntCurS, kCntCurD, kCntNxtS, kCntNxtD, kCntN };
 
 template <class T>
 cudaError_t dalloc(T** p, int64_t n, cudaStream_t st) {
@@ -1277,6 +1291,7 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
   W.T.mask = (uint64_t)c.table - 1;
   TRY(dalloc(&W.K.slot, c.keys, st));
   TRY(dalloc(&W.K.cur, c.keys, st));
+  TRY(dalloc(&W.K.pos, c.keys, st));
   TRY(dalloc(&W.K.tries, c.keys, st));
   TRY(dalloc(&W.K.status, c.keys, st));
   TRY(dalloc(&W.spec_list, c.keys, st));
@@ -1305,7 +1320,7 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
 }
 
 void release_work(Work& W, cudaStream_t st) {
-  void* ptrs[] = {W.T.fp, W.T.hi, W.T.lo, W.T.minrow, W.T.kid, W.T.next, W.K.slot, W.K.cur,
+  void* ptrs[] = {W.T.fp, W.T.hi, W.T.lo, W.T.minrow, W.T.kid, W.T.next, W.K.slot, W.K.cur, W.K.pos,
                   W.K.tries, W.K.status, W.spec_list, W.diff_list, W.list2_s, W.list2_d, W.cand,
                   W.cand2, W.cand_cnt, W.cand_off, W.fs, W.fd, W.os, W.od, W.sk0, W.tk0,
                   W.sv0, W.tv, W.raw, W.psk, W.ptk, W.psi, W.pti, W.cnt, W.order};
@@ -1426,7 +1441,17 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   TRY(cudaMemcpyAsync(ctr + kCtrKeys, W.cnt + kCntKeys, 8, cudaMemcpyDeviceToDevice, st));
   verify_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(S, C, R, W.T, W.cand, ctr + kCtrCands,
                                                             c.cand, ctr); count_launch();
-  key_init_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.cnt + kCntKeys, W.K, W.T); count_launch();
+  // candidates sorted by (slot, row) once; T.next holds each slot's run start
+  int row_bits = 1, table_bits = 0;
+  while ((1ll << row_bits) < n) ++row_bits;
+  while ((1ll << table_bits) < c.table) ++table_bits;
+  cand_key_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(W.cand, ctr + kCtrCands, c.cand,
+                                                              row_bits); count_launch();
+  radix_sort_pairs(reinterpret_cast<uint64_t*>(W.cand), nullptr, reinterpret_cast<uint64_t*>(W.cand2),
+                   nullptr, c.cand, row_bits + table_bits, st);
+  const SortedCand SC{reinterpret_cast<const uint64_t*>(W.cand), ctr + kCtrCands, c.cand, row_bits};
+  run_start_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(SC, W.T.next); count_launch();
+  key_init_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.cnt + kCntKeys, W.K, W.T.next, SC); count_launch();
 
   // LOS paths first, then candidates in ray-id order until one validates
   const int nj = C.batch ? C.n_pairs : r->n_rx_phys;
@@ -1442,8 +1467,6 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   V.paths = W.raw;
   V.path_cap = c.paths;
   uint32_t *cur_s = W.spec_list, *cur_d = W.diff_list, *nxt_s = W.list2_s, *nxt_d = W.list2_d;
-  uint2 *cand_cur = W.cand, *cand_nxt = W.cand2;
-  unsigned long long* cnt_cand_cur = ctr + kCtrCands;
   TRY(cudaMemcpyAsync(W.cnt + kCntCurS, W.cnt + kCntSpec, 16, cudaMemcpyDeviceToDevice, st));
   for (int round = 0; round < r->p.rep_tries; ++round) {
     TRY(cudaMemsetAsync(W.cnt + kCntNxtS, 0, 16, st));
@@ -1456,18 +1479,10 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
     validate_diffuse_kernel<<<blocks_for(c.keys, kTraceThreads, sm), kTraceThreads, 0, st>>>(
         S, C, V, cur_d, W.cnt + kCntCurD, ctr); count_launch();
     if (round + 1 >= r->p.rep_tries) break;
-    next_reset_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(nxt_s, W.cnt + kCntNxtS, W.K, W.T); count_launch();
-    next_reset_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(nxt_d, W.cnt + kCntNxtD, W.K, W.T); count_launch();
-    unsigned long long* cnt_cand_nxt = W.cnt + ((cnt_cand_cur == W.cnt + kCntCandA) ? kCntCandB : kCntCandA);
-    TRY(cudaMemsetAsync(cnt_cand_nxt, 0, 8, st));
-    next_scan_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(cand_cur, cnt_cand_cur, c.cand, W.K,
-                                                                 W.T, cand_nxt, cnt_cand_nxt); count_launch();
-    std::swap(cand_cur, cand_nxt);
-    cnt_cand_cur = cnt_cand_nxt;
     TRY(cudaMemsetAsync(W.cnt + kCntCurS, 0, 16, st));
-    next_apply_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(nxt_s, W.cnt + kCntNxtS, W.K, W.T,
+    next_apply_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(nxt_s, W.cnt + kCntNxtS, W.K, SC,
                                                                   cur_s, W.cnt + kCntCurS); count_launch();
-    next_apply_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(nxt_d, W.cnt + kCntNxtD, W.K, W.T,
+    next_apply_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(nxt_d, W.cnt + kCntNxtD, W.K, SC,
                                                                   cur_d, W.cnt + kCntCurD); count_launch();
   }
   if (r->ev[5]) TRY(cudaEventRecord(r->ev[5], st));
