@@ -17,6 +17,8 @@ constexpr int kMaxDepth = 5;     // maximum interactions per path
 // block, 8 blocks (32 warps) per SM.  A deeper tree than the stack sets
 // kErrStack and fails the call (the office scene's radix tree is 23 deep).
 constexpr int kStackDepth = 27;
+// unused child slot of a 4-wide BVH node (leaves are ~DPS >= -n_dps)
+constexpr int kEmptyChild = (int)0x80000000;
 constexpr float kC0 = 299792458.0f;
 constexpr double kEps0 = 8.8541878128e-12;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
@@ -157,44 +159,66 @@ __device__ __forceinline__ Hit cast_ray(const SceneView& S, float3 o, float3 d, 
   int sp = 0;
   for (;;) {
     if (node >= 0) {
-      const float4* nd = S.nodes + 4 * (size_t)node;
-      const float4 a = __ldg(nd + 0), b = __ldg(nd + 1), c = __ldg(nd + 2), e = __ldg(nd + 3);
-      // left box (a.x a.y a.z) - (a.w b.x b.y); right box (b.z b.w c.x) - (c.y c.z c.w)
-      float l0 = fmaf(a.x, inv.x, -oi.x), l1 = fmaf(a.w, inv.x, -oi.x);
-      float l2 = fmaf(a.y, inv.y, -oi.y), l3 = fmaf(b.x, inv.y, -oi.y);
-      float l4 = fmaf(a.z, inv.z, -oi.z), l5 = fmaf(b.y, inv.z, -oi.z);
-      float lin = fmaxf(fmaxf(fminf(l0, l1), fminf(l2, l3)), fmaxf(fminf(l4, l5), tmin));
-      float lout = fminf(fminf(fmaxf(l0, l1), fmaxf(l2, l3)), fminf(fmaxf(l4, l5), best_t));
-      float r0 = fmaf(b.z, inv.x, -oi.x), r1 = fmaf(c.y, inv.x, -oi.x);
-      float r2 = fmaf(b.w, inv.y, -oi.y), r3 = fmaf(c.z, inv.y, -oi.y);
-      float r4 = fmaf(c.x, inv.z, -oi.z), r5 = fmaf(c.w, inv.z, -oi.z);
-      float rin = fmaxf(fmaxf(fminf(r0, r1), fminf(r2, r3)), fmaxf(fminf(r4, r5), tmin));
-      float rout = fminf(fminf(fmaxf(r0, r1), fmaxf(r2, r3)), fminf(fmaxf(r4, r5), best_t));
-      // conservative comparison: widen by a relative 1e-6 so that float error
-      // in the slab test never drops a box the ray grazes
-      const bool hl = lin <= lout * 1.000001f + 1e-6f;
-      const bool hr = rin <= rout * 1.000001f + 1e-6f;
-      const int cl = __float_as_int(e.x), cr = __float_as_int(e.y);
-      if (hl && hr) {
-        int nearc = lin <= rin ? cl : cr;
-        int farc = lin <= rin ? cr : cl;
-        float fart = lin <= rin ? rin : lin;
-        if (sp >= kStackDepth) {
+      // 4-wide node: slab tests of the four child boxes, then the nearest hit
+      // child next and the others pushed farthest first
+      const float4* nd = S.nodes + 8 * (size_t)node;
+      const float4 lx = __ldg(nd + 0), ly = __ldg(nd + 1), lz = __ldg(nd + 2);
+      const float4 hx = __ldg(nd + 3), hy = __ldg(nd + 4), hz = __ldg(nd + 5);
+      const float4 cf = __ldg(nd + 6);
+      const float blx[4] = {lx.x, lx.y, lx.z, lx.w}, bly[4] = {ly.x, ly.y, ly.z, ly.w};
+      const float blz[4] = {lz.x, lz.y, lz.z, lz.w}, bhx[4] = {hx.x, hx.y, hx.z, hx.w};
+      const float bhy[4] = {hy.x, hy.y, hy.z, hy.w}, bhz[4] = {hz.x, hz.y, hz.z, hz.w};
+      const int cid[4] = {__float_as_int(cf.x), __float_as_int(cf.y), __float_as_int(cf.z),
+                          __float_as_int(cf.w)};
+      float te[4];
+      int ce[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float x0 = fmaf(blx[c], inv.x, -oi.x), x1 = fmaf(bhx[c], inv.x, -oi.x);
+        const float y0 = fmaf(bly[c], inv.y, -oi.y), y1 = fmaf(bhy[c], inv.y, -oi.y);
+        const float z0 = fmaf(blz[c], inv.z, -oi.z), z1 = fmaf(bhz[c], inv.z, -oi.z);
+        const float tin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), tmin));
+        const float tout = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fminf(fmaxf(z0, z1), best_t));
+        // conservative comparison: widen by a relative 1e-6 so that float error
+        // in the slab test never drops a box the ray grazes
+        const bool hit = cid[c] != kEmptyChild && tin <= tout * 1.000001f + 1e-6f;
+        te[c] = hit ? tin : __int_as_float(0x7f800000);
+        ce[c] = hit ? cid[c] : kEmptyChild;
+      }
+      // sort the four (entry t, child) pairs by t: misses (+inf) go last
+#define NRT_CSWAP(i, j)                                  \
+  if (te[j] < te[i]) {                                   \
+    const float tt = te[i];                              \
+    te[i] = te[j];                                       \
+    te[j] = tt;                                          \
+    const int cc = ce[i];                                \
+    ce[i] = ce[j];                                       \
+    ce[j] = cc;                                          \
+  }
+      NRT_CSWAP(0, 1)
+      NRT_CSWAP(2, 3)
+      NRT_CSWAP(0, 2)
+      NRT_CSWAP(1, 3)
+      NRT_CSWAP(1, 2)
+#undef NRT_CSWAP
+      if (ce[0] != kEmptyChild) {
+        bool over = false;
+#pragma unroll
+        for (int c = 3; c >= 1; --c) {
+          if (ce[c] == kEmptyChild) continue;
+          if (sp >= kStackDepth) {
+            over = true;
+            break;
+          }
+          stack[sp * stride] = ce[c];
+          tstack[sp * stride] = te[c];
+          ++sp;
+        }
+        if (over) {
           atomicOr(err, kErrStack);
           break;
         }
-        stack[sp * stride] = farc;
-        tstack[sp * stride] = fart;
-        ++sp;
-        node = nearc;
-        continue;
-      }
-      if (hl) {
-        node = cl;
-        continue;
-      }
-      if (hr) {
-        node = cr;
+        node = ce[0];
         continue;
       }
     } else {

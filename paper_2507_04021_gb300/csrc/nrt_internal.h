@@ -37,7 +37,8 @@ struct nrt_scene {
   int32_t* dps_vox = nullptr;  // [n_dps][3]
   float4* dps_recv = nullptr;  // reception point (xyz)
   float4* dps_center = nullptr;  // local origin of the DPS's disc positions
-  float4* nodes = nullptr;     // 4 float4 per internal node
+  float4* nodes = nullptr;     // 4-wide BVH: 8 float4 (128 B) per node
+  int64_t n_nodes4 = 0;
   int root = 0;
   float build_ms = 0.0f;
   // materials
@@ -159,6 +160,7 @@ void debug_launch_check(const char* file, int line);
 #endif
 
 // scene.cu
+nrt_status collapse_bvh4(nrt_scene* s, int64_t n_int, cudaStream_t st);
 nrt_status build_scene(nrt_scene* s, const float* pos_d, const float* nrm_d, const uint16_t* surf_d,
                        const uint8_t* mat_d);
 // trace.cu / paths.cu

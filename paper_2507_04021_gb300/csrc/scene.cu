@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "nrt_internal.h"
 
@@ -378,6 +379,8 @@ nrt_status build_scene(nrt_scene* s, const float* pos, const float* nrm, const u
     cudaFreeAsync(leaf_parent, st);
     cudaFreeAsync(node_box, st);
     cudaFreeAsync(visits, st);
+    const nrt_status rc4 = collapse_bvh4(s, n_int, st);
+    if (rc4 != NRT_OK) return rc4;
   }
   cudaFreeAsync(key, st);
   cudaFreeAsync(tkey, st);
@@ -394,6 +397,101 @@ nrt_status build_scene(nrt_scene* s, const float* pos, const float* nrm, const u
   cudaEventElapsedTime(&s->build_ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  return NRT_OK;
+}
+
+// 4-wide BVH collapsed (on the host) from the binary radix tree: a node takes
+// its binary node's two children and opens the internal child with the
+// largest box surface area until it holds four children or only leaves.
+// Node layout, 8 float4: lo.x[4], lo.y[4], lo.z[4], hi.x[4], hi.y[4], hi.z[4],
+// child[4] (>= 0 node, < 0 ~DPS, kEmptyChild unused), spare.  Replaces the
+// binary nodes in s->nodes; the root is node 0.
+nrt_status collapse_bvh4(nrt_scene* s, int64_t n_int, cudaStream_t st) {
+  nrt_ctx* ctx = s->ctx;
+  std::vector<float4> bin((size_t)n_int * 4);
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(bin.data(), s->nodes, bin.size() * sizeof(float4),
+                                    cudaMemcpyDeviceToHost, st));
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  struct Child {
+    int id;
+    float lo[3], hi[3];
+  };
+  auto kids = [&](int node, Child* c) {
+    const float4 a = bin[4 * node], b = bin[4 * node + 1], cc = bin[4 * node + 2], e = bin[4 * node + 3];
+    int l, r;
+    memcpy(&l, &e.x, 4);
+    memcpy(&r, &e.y, 4);
+    c[0] = Child{l, {a.x, a.y, a.z}, {a.w, b.x, b.y}};
+    c[1] = Child{r, {b.z, b.w, cc.x}, {cc.y, cc.z, cc.w}};
+  };
+  auto area = [](const Child& c) {
+    const float dx = c.hi[0] - c.lo[0], dy = c.hi[1] - c.lo[1], dz = c.hi[2] - c.lo[2];
+    return dx * dy + dy * dz + dz * dx;
+  };
+  std::vector<float4> out;
+  out.reserve((size_t)n_int * 4);
+  std::vector<std::pair<int, int64_t>> queue;  // (binary node, BVH4 node)
+  queue.push_back({0, 0});
+  out.resize(8);
+  for (size_t qi = 0; qi < queue.size(); ++qi) {
+    const int bn = queue[qi].first;
+    const int64_t slot = queue[qi].second;
+    Child ch[4];
+    int nc = 2;
+    kids(bn, ch);
+    while (nc < 4) {
+      int best = -1;
+      float ba = -1.0f;
+      for (int i = 0; i < nc; ++i)
+        if (ch[i].id >= 0 && area(ch[i]) > ba) {
+          ba = area(ch[i]);
+          best = i;
+        }
+      if (best < 0) break;
+      Child two[2];
+      kids(ch[best].id, two);
+      ch[best] = two[0];
+      ch[nc++] = two[1];
+    }
+    float lo[3][4], hi[3][4];
+    int cid[4];
+    for (int i = 0; i < 4; ++i) {
+      if (i >= nc) {
+        for (int k = 0; k < 3; ++k) lo[k][i] = hi[k][i] = 0.0f;
+        cid[i] = kEmptyChild;
+        continue;
+      }
+      for (int k = 0; k < 3; ++k) {
+        lo[k][i] = ch[i].lo[k];
+        hi[k][i] = ch[i].hi[k];
+      }
+      if (ch[i].id >= 0) {
+        const int64_t ns = (int64_t)(out.size() / 8);
+        out.resize(out.size() + 8);
+        queue.push_back({ch[i].id, ns});
+        cid[i] = (int)ns;
+      } else {
+        cid[i] = ch[i].id;
+      }
+    }
+    float4* nd = out.data() + 8 * slot;
+    for (int k = 0; k < 3; ++k) {
+      nd[k] = make_float4(lo[k][0], lo[k][1], lo[k][2], lo[k][3]);
+      nd[3 + k] = make_float4(hi[k][0], hi[k][1], hi[k][2], hi[k][3]);
+    }
+    float f[4];
+    memcpy(f, cid, 16);
+    nd[6] = make_float4(f[0], f[1], f[2], f[3]);
+    nd[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  float4* n4 = nullptr;
+  NRT_CUDA_TRY(ctx, cudaMalloc(&n4, out.size() * sizeof(float4)));
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(n4, out.data(), out.size() * sizeof(float4),
+                                    cudaMemcpyHostToDevice, st));
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  cudaFree(s->nodes);
+  s->nodes = n4;
+  s->n_nodes4 = (int64_t)(out.size() / 8);
   return NRT_OK;
 }
 
