@@ -378,7 +378,7 @@ void nrt_result_free(nrt_result* r) {
   free_dev(r->queue);
   cudaStream_t st = r->scene->ctx->stream;
   void* pool_ptrs[] = {r->rec_q, r->rec_n, r->rec_d, r->rec_i, r->vis, r->paths,
-                       r->path_a, r->power, r->ctr, r->rx_start_d, r->rx_count_d, r->labels,
+                       r->path_a, r->power, r->power_part, r->ctr, r->rx_start_d, r->rx_count_d, r->labels,
                        r->key_hi, r->key_lo, r->key_tried, r->key_rep};
   for (void* q : pool_ptrs)
     if (q) cudaFreeAsync(q, st);

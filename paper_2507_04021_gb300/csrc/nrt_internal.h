@@ -87,6 +87,7 @@ struct nrt_result {
   uint32_t* key_rep = nullptr;
   int64_t key_cap = 0;
   double* power = nullptr;   // [n_rx]
+  double* power_part = nullptr;  // [n_rx][64] partial sums of the power reduction
   int64_t* rx_start_d = nullptr;  // [n_rx] device ranges of the sorted paths
   int64_t* rx_count_d = nullptr;
   int64_t* rx_count = nullptr;  // host copies

@@ -1005,14 +1005,18 @@ __global__ void field_kernel(const PathRec* __restrict__ P, const unsigned long 
   }
 }
 
-// per-RX power: one block per RX over its contiguous range, fixed-order tree
-__global__ void power_kernel(const float2* __restrict__ a, const int64_t* __restrict__ start,
-                             const int64_t* __restrict__ count, double* __restrict__ power) {
+// P_j = sum |a|^2 over RX j's paths in two fixed-order levels (the same
+// result on every run): kPowerChunks blocks per RX write partial sums, then
+// one pass adds each RX's partials in order.
+constexpr int kPowerChunks = 64;
+__global__ void power_partial_kernel(const float2* __restrict__ a, const int64_t* __restrict__ start,
+                                     const int64_t* __restrict__ count, double* __restrict__ partial) {
   __shared__ double sh[256];
-  const int j = blockIdx.x;
+  const int j = blockIdx.y;
   const int64_t b = start[j], n = count[j];
   double acc = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
     NRT_GUARD(b + i < g_dbg_caps.paths, 24, b + i)
     const float2 v = a[b + i];
     acc += (double)v.x * v.x + (double)v.y * v.y;
@@ -1023,7 +1027,16 @@ __global__ void power_kernel(const float2* __restrict__ a, const int64_t* __rest
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) power[j] = sh[0];
+  if (threadIdx.x == 0) partial[(int64_t)j * kPowerChunks + blockIdx.x] = sh[0];
+}
+
+__global__ void power_sum_kernel(const double* __restrict__ partial, int n_rx,
+                                 double* __restrict__ power) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_rx) return;
+  double s = 0.0;
+  for (int c = 0; c < kPowerChunks; ++c) s += partial[(int64_t)j * kPowerChunks + c];
+  power[j] = s;
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -1345,6 +1358,7 @@ nrt_status alloc_result(nrt_result* r, const Caps& c, bool with_paths) {
   if (!r->vis && r->p.capture == NRT_CAPTURE_VIS)
     TRY(dalloc(&r->vis, (int64_t)r->n_rx_phys * r->vis_words, st));
   if (!r->power) TRY(dalloc(&r->power, r->n_rx, st));
+  if (!r->power_part) TRY(dalloc(&r->power_part, (int64_t)r->n_rx * kPowerChunks, st));
   if (!r->rx_start_d) TRY(dalloc(&r->rx_start_d, r->n_rx, st));
   if (!r->rx_count_d) TRY(dalloc(&r->rx_count_d, r->n_rx, st));
   if (r->p.ray_labels && !r->labels) TRY(dalloc(&r->labels, r->n_traced, st));
@@ -1513,7 +1527,9 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
     field_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>((const PathRec*)r->paths, ctr + kCtrPaths,
                                                               c.paths, sc->mat, r->p.freq, r->p.pol,
                                                               r->path_a); count_launch();
-    power_kernel<<<r->n_rx, 256, 0, st>>>(r->path_a, r->rx_start_d, r->rx_count_d, r->power); count_launch();
+    power_partial_kernel<<<dim3(kPowerChunks, r->n_rx), 256, 0, st>>>(r->path_a, r->rx_start_d,
+                                                                     r->rx_count_d, r->power_part); count_launch();
+    power_sum_kernel<<<(r->n_rx + 127) / 128, 128, 0, st>>>(r->power_part, r->n_rx, r->power); count_launch();
   }
   return NRT_OK;
 }
@@ -1691,7 +1707,9 @@ nrt_status run_field(nrt_result* r) {
   unsigned long long* np = r->ctr + kCtrPaths;
   field_kernel<<<blocks_for(r->path_cap, 256, ctx->sm_count), 256, 0, st>>>(
       (const PathRec*)r->paths, np, r->path_cap, sc->mat, r->p.freq, r->p.pol, r->path_a); count_launch();
-  power_kernel<<<r->n_rx, 256, 0, st>>>(r->path_a, r->rx_start_d, r->rx_count_d, r->power); count_launch();
+  power_partial_kernel<<<dim3(kPowerChunks, r->n_rx), 256, 0, st>>>(r->path_a, r->rx_start_d,
+                                                                   r->rx_count_d, r->power_part); count_launch();
+  power_sum_kernel<<<(r->n_rx + 127) / 128, 128, 0, st>>>(r->power_part, r->n_rx, r->power); count_launch();
   TRY(cudaGetLastError());
   r->field_done = true;
   return NRT_OK;
