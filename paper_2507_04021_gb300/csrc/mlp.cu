@@ -335,6 +335,191 @@ __global__ void features_kernel(SampleSrc S, int64_t B, int64_t n_rays, bf16* __
   }
 }
 
+// ---------------------------------------------------------------- fused scoring
+// One persistent CTA per SM scores 128-row tiles end to end on the tensor
+// cores: the tile's Fourier features are written straight into the MMA
+// operand layout in shared memory, the three hidden layers run as chained
+// tcgen05.mma into one tensor-memory accumulator (bias, ReLU and the BF16
+// rounding applied by the epilogue, which writes the next layer's operand
+// back to shared memory), and the output layer is folded into the last
+// epilogue: each thread owns one row, so the logit is a per-thread dot product.
+// W1, W2, W3 stay in shared memory for the whole launch.
+constexpr int kScoreThreads = 128;
+constexpr int kSW1 = 0;                          // W1: 128 x 96 bf16
+constexpr int kSW2 = kSW1 + kH * kIn * 2;        // W2: 128 x 128 bf16
+constexpr int kSW3 = kSW2 + kH * kH * 2;         // W3
+constexpr int kSAct = kSW3 + kH * kH * 2;        // activations: 128 x 128 bf16
+constexpr int kSVec = kSAct + 128 * kH * 2;      // b1, b2, b3, w4 (fp32)
+constexpr int kSBar = kSVec + 4 * kH * 4;        // mbarrier + tensor-memory address
+constexpr size_t kScoreSmem = (size_t)kSBar + 16;
+
+// byte offset of element (r, k) in the no-swizzle K-major core-matrix layout
+// of a tile with kdim columns: core (r / 8, k / 8) at ((r/8)(kdim/8) + k/8) 128 B
+__device__ __forceinline__ uint32_t cm_off(int r, int k, int kdim) {
+  return (uint32_t)((((r >> 3) * (kdim >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ void stage_weights(uint8_t* dst, const bf16* __restrict__ src, int kdim) {
+  const int per_row = kdim / 8;
+  for (int v = threadIdx.x; v < kH * per_row; v += blockDim.x) {
+    const int r = v / per_row, c = v - r * per_row;
+    *reinterpret_cast<uint4*>(dst + cm_off(r, 8 * c, kdim)) =
+        *reinterpret_cast<const uint4*>(src + (int64_t)r * kdim + 8 * c);
+  }
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// bounded wait for the tile's MMAs, agreed by the whole block
+__device__ __forceinline__ bool block_wait(uint32_t bar, uint32_t phase) {
+  const bool got = mbar_wait(bar, phase);
+  return __syncthreads_and(got) != 0;
+}
+
+__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a0, uint32_t b0, int kdim,
+                                            uint32_t bar) {
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    const uint32_t sbo = (uint32_t)(kdim / 8) * 128u;
+    for (int kk = 0; kk < kdim / 16; ++kk)
+      tc_mma(tmem, smem_desc(a0 + kk * 256, 128, sbo), smem_desc(b0 + kk * 256, 128, sbo),
+             idesc_bf16(128, kH), kk > 0 ? 1u : 0u);
+    tc_commit(bar);
+  }
+}
+
+// hidden-layer epilogue: row threadIdx.x of the accumulator + bias, ReLU,
+// BF16, into the activation tile (K = 128 layout)
+__device__ __forceinline__ void hidden_epilogue(uint32_t tmem, const float* bias, uint8_t* act) {
+  const int warp = threadIdx.x >> 5, r = threadIdx.x;
+  for (int c0 = 0; c0 < kH; c0 += 16) {
+    float v[16];
+    tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      w[i] = pack_bf16x2(fmaxf(v[2 * i] + bias[c0 + 2 * i], 0.0f),
+                         fmaxf(v[2 * i + 1] + bias[c0 + 2 * i + 1], 0.0f));
+    *reinterpret_cast<uint4*>(act + cm_off(r, c0, kH)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(act + cm_off(r, c0 + 8, kH)) = make_uint4(w[4], w[5], w[6], w[7]);
+  }
+}
+
+__global__ void __launch_bounds__(kScoreThreads, 1)
+    mlp_score_fused_kernel(SampleSrc S, int64_t n, int64_t n_rays, const bf16* __restrict__ W1,
+                           const bf16* __restrict__ W2, const bf16* __restrict__ W3,
+                           const float* __restrict__ theta, float* __restrict__ logits,
+                           uint32_t* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  float* vec = reinterpret_cast<float*>(smem + kSVec);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSBar);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSBar + 8);
+  const int warp = threadIdx.x >> 5;
+  stage_weights(smem + kSW1, W1, kIn);
+  stage_weights(smem + kSW2, W2, kH);
+  stage_weights(smem + kSW3, W3, kH);
+  for (int f = threadIdx.x; f < kH; f += blockDim.x) {
+    vec[f] = theta[kOffB1 + f];
+    vec[kH + f] = theta[kOffB2 + f];
+    vec[2 * kH + f] = theta[kOffB3 + f];
+    vec[3 * kH + f] = __bfloat162float(__float2bfloat16_rn(theta[kOffW4 + f]));
+  }
+  const float b4 = theta[kOffB4];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) mbar_init(smem_u32(bar), 1);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sact = smem_u32(smem + kSAct), bar_a = smem_u32(bar);
+  uint8_t* act = smem + kSAct;
+  uint32_t phase = 0;
+  bool ok = true, issued = false;
+  const int64_t n_tiles = (n + 127) / 128;
+  for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+    // features of row threadIdx.x, eight columns per 16-byte store (K = 96 layout)
+    const int64_t row = tile * 128 + threadIdx.x;
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (row < n) {
+      const uint32_t ray = S.ray_id ? S.ray_id[row] : (uint32_t)row;
+      const float3 d = fib_dir(ray, n_rays);
+      v[0] = d.x;
+      v[1] = d.y;
+      v[2] = d.z;
+      for (int c = 0; c < 3; ++c) v[3 + c] = __fdiv_rn(__fsub_rn(S.tx0[c], S.cen[c]), S.inv_half_num[c]);
+    }
+    for (int c = 0; c < 6; ++c) {
+      uint32_t w[8];
+#pragma unroll
+      for (int k = 0; k < kOct; ++k) {
+        float sn, cs;
+        sincospif(ldexpf(v[c], k), &sn, &cs);
+        w[k] = row < n ? pack_bf16x2(sn, cs) : 0u;
+      }
+      // columns (c * 8 + k) * 2 + {0, 1}: 16 columns per coordinate
+      *reinterpret_cast<uint4*>(act + cm_off(threadIdx.x, 16 * c, kIn)) = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(act + cm_off(threadIdx.x, 16 * c + 8, kIn)) = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    // layer 1 (K = 96)
+    issue_layer(tmem, sact, smem_u32(smem + kSW1), kIn, bar_a);
+    issued = true;
+    if (!(ok = block_wait(bar_a, phase))) break;
+    phase ^= 1u;
+    tc_fence_after();
+    hidden_epilogue(tmem, vec, act);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    // layer 2
+    issue_layer(tmem, sact, smem_u32(smem + kSW2), kH, bar_a);
+    if (!(ok = block_wait(bar_a, phase))) break;
+    phase ^= 1u;
+    tc_fence_after();
+    hidden_epilogue(tmem, vec + kH, act);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    // layer 3 and the output layer
+    issue_layer(tmem, sact, smem_u32(smem + kSW3), kH, bar_a);
+    if (!(ok = block_wait(bar_a, phase))) break;
+    phase ^= 1u;
+    tc_fence_after();
+    float z = 0.0f;
+    for (int c0 = 0; c0 < kH; c0 += 16) {
+      float a[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, a);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(a[i] + vec[2 * kH + c0 + i], 0.0f)));
+        z = fmaf(h, vec[3 * kH + c0 + i], z);
+      }
+    }
+    if (row < n) logits[row] = z + b4;
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(err, kErrMmaTimeout);
+    if (issued) mbar_wait(bar_a, phase);  // bounded: let our MMAs drain
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+}
+
 // H = bf16(relu(Z + bias)) [B x 128], optionally also transposed [128 x ldt].
 // Block: 128 threads = the 128 features, 64 samples per block.
 __global__ void act_kernel(const float* __restrict__ Z, const float* __restrict__ bias, int64_t B,
@@ -739,18 +924,22 @@ nrt_status nrt_mlp_score(nrt_mlp* m, const float* tx, const uint32_t* ray_ids, i
   nrt_ctx* ctx = m->ctx;
   NRT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   launch_counter() = 0;
-  MTRY(ensure_ws(m, n));
   SampleSrc S = norm_src(m);
   for (int c = 0; c < 3; ++c) S.tx0[c] = tx[c];
   S.ray_id = ray_ids;
   S.n = n;
   cudaStream_t st = ctx->stream;
-  features_kernel<<<blocks_for_n(n), 256, 0, st>>>(S, n, m->n_rays, m->X, nullptr, 0, nullptr);
-  count_launch();
-  MTRY(forward_layers(m, n, false));
-  head_kernel<<<(unsigned)((n + 63) / 64), kH, 0, st>>>(m->H3, m->w4, m->theta + kOffB4, n, nullptr,
-                                                        nullptr, 0.f, 0.f, logits, nullptr, nullptr,
-                                                        0, nullptr, nullptr);
+  static bool attr_set = false;
+  if (!attr_set) {
+    NRT_CUDA_TRY(ctx, cudaFuncSetAttribute(mlp_score_fused_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)kScoreSmem));
+    attr_set = true;
+  }
+  const int64_t tiles = (n + 127) / 128;
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, ctx->sm_count);
+  mlp_score_fused_kernel<<<grid, kScoreThreads, kScoreSmem, st>>>(S, n, m->n_rays, m->W1, m->W2, m->W3,
+                                                                 m->theta, logits, m->err);
   count_launch();
   NRT_CUDA_TRY(ctx, cudaGetLastError());
   return NRT_OK;
