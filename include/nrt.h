@@ -92,7 +92,8 @@ typedef struct {
   int64_t hash_probes_max;   /* longest hash probe sequence seen */
   int64_t error_flags;       /* device error bits (0 = none) */
   int64_t kernel_launches;   /* library kernels launched by the call */
-  int64_t reserved[4];
+  int64_t diffuse_casts;     /* of validation_casts: diffuse shadow casts (Sec. II-B-1) */
+  int64_t reserved[3];
 } nrt_counters;
 
 /* Path view for nrt_paths_read: caller-allocated arrays of n_paths entries

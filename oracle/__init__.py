@@ -92,6 +92,8 @@ def _declare(L):
     L.orc_sim_n_paths.restype = C.c_int64
     L.orc_sim_n_paths.argtypes = [_P]
     L.orc_sim_paths.argtypes = [_P] + [_P] * 13
+    L.orc_sim_shadow_disc_counts.restype = None
+    L.orc_sim_shadow_disc_counts.argtypes = [_P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.orc_sim_ray_labels.restype = None
     L.orc_sim_ray_labels.argtypes = [_P, _P, _P]
     L.orc_sim_cand_status.restype = C.c_int
@@ -309,6 +311,14 @@ class OracleSim:
         out = np.zeros((self.ray_ids.shape[0], lib().orc_sim_n_seg(self._h)), np.int64)
         lib().orc_sim_disc_counts(self._h, _ptr(out))
         return out
+
+    def shadow_disc_counts(self, stride: int = 1):
+        """(discs entered, casts) of the diffuse validation shadow casts of every
+        `stride`-th tried diffuse candidate."""
+        s = C.c_int64()
+        n = C.c_int64()
+        lib().orc_sim_shadow_disc_counts(self._h, int(stride), C.byref(s), C.byref(n))
+        return int(s.value), int(n.value)
 
     def cand_status(self, hi, lo, ray) -> int:
         """0 certainly not a candidate, 1 certainly a candidate, 2 uncertain."""

@@ -1469,6 +1469,43 @@ void orc_sim_disc_counts(void* s, int64_t* out) {
   }
 }
 
+// The same count for the diffuse validation shadow casts (scatter point of a
+// tried candidate -> RX, skipping the scatter DPS, Sec. II-B-1): every
+// `stride`-th tried candidate of the diffuse keys, in key order.  *n_casts
+// receives the number of casts counted, *sum their discs.
+void orc_sim_shadow_disc_counts(void* s, int64_t stride, int64_t* sum, int64_t* n_casts) {
+  Sim* sim = (Sim*)s;
+  const Scene& S = *sim->S;
+  CastCfg cfg;
+  cfg.t_min = sim->p.t_min;
+  std::vector<std::pair<int64_t, int>> items;  // (row, key index)
+  int64_t idx = 0;
+  for (size_t ki = 0; ki < sim->keys.size(); ++ki) {
+    const KeyOut& k = sim->keys[ki];
+    if (k.type != 1) continue;
+    for (int64_t rid : k.tried) {
+      if (idx++ % stride) continue;
+      const int64_t row = (rid >= 0 && rid < (int64_t)sim->ray_pos.size()) ? sim->ray_pos[rid] : -1;
+      if (row >= 0) items.push_back({row, (int)ki});
+    }
+  }
+  int64_t tot = 0, cnt = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : tot, cnt)
+  for (int64_t i = 0; i < (int64_t)items.size(); ++i) {
+    const KeyOut& k = sim->keys[items[i].second];
+    const HitRec& hk = sim->rec[items[i].first * sim->n_seg + (k.k - 1)];
+    const V3 u = sim->rx[k.j] - hk.q;
+    const double rs = norm(u);
+    const V3 w = (1.0 / rs) * u;
+    if (dot(hk.n, w) <= 0.0) continue;  // no cast
+    const Hit h = cast(S, hk.q, w, hk.dps, rs, false, cfg);
+    tot += discs_entered(S, hk.q, w, hk.dps, sim->p.t_min, h.hit ? h.t : rs);
+    ++cnt;
+  }
+  *sum = tot;
+  *n_casts = cnt;
+}
+
 // The same count for visibility casts (RX j -> reception point of DPS D).
 void orc_vis_disc_counts(void* s, const double* rx, const int32_t* j, const int32_t* dps,
                          int64_t n, double t_min, int64_t* out) {

@@ -112,6 +112,7 @@ enum Ctr : int {
   kCtrVisCasts,
   kCtrLosCasts,
   kCtrValCasts,
+  kCtrDiffCasts,  // diffuse validation shadow casts (also in kCtrValCasts)
   kCtrCands,
   kCtrKeys,
   kCtrPaths,

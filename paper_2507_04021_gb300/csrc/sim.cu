@@ -663,6 +663,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
     finish_key(A, kid, valid, ctr, C, &P);
   }
   count_add(ctr + kCtrValCasts, casts);
+  count_add(ctr + kCtrDiffCasts, casts);
 }
 
 // Specular: phase 1 solves Eq. 1 on the infinite planes (q_m, n_m) of the
@@ -1573,6 +1574,7 @@ nrt_status finish_result(nrt_result* r) {
   c.hash_probes_max = (int64_t)hc[kCtrProbeMax];
   c.error_flags = (int64_t)(hc[kCtrErr] & 0xFFFFFFFFull);
   c.kernel_launches = launch_counter();
+  c.diffuse_casts = (int64_t)hc[kCtrDiffCasts];
   if (c.error_flags & (kErrHashFull | kErrCandFull | kErrPathFull | kErrKeyMismatch)) {
     ctx->last_error = "device buffer overflow or key fingerprint collision (flags " +
                       std::to_string(c.error_flags) + ")";

@@ -49,8 +49,8 @@ class TraceParams(C.Structure):
 class Counters(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "rays", "segments", "vis_casts", "los_casts", "validation_casts", "candidates", "keys",
-        "paths", "n_dps", "hash_probes_max", "error_flags", "kernel_launches")] + [
-            ("reserved", C.c_int64 * 4)]
+        "paths", "n_dps", "hash_probes_max", "error_flags", "kernel_launches", "diffuse_casts")] + [
+            ("reserved", C.c_int64 * 3)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
