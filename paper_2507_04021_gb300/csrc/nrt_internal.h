@@ -142,7 +142,7 @@ static_assert(sizeof(PathRec) == 128, "PathRec layout");
 
 void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t st);
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
-                      int bits, cudaStream_t st);
+                      int bits, cudaStream_t st, int lo_bit = 0);
 
 SceneView scene_view(const nrt_scene* s);
 

@@ -160,10 +160,11 @@ __global__ void radix_scatter_kernel(const uint64_t* __restrict__ kin,
 
 }  // namespace
 
-// Sort (keys, vals) by the low `bits` bits of the keys, stably.  The result
-// ends in keys/vals; tk/tv are scratch of n entries.
+// Sort (keys, vals) stably by key bits [lo_bit, bits) (lower bits keep their
+// input order).  The result ends in keys/vals; tk/tv are scratch of n
+// entries; vals (and tv) may be null for a keys-only sort.
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
-                      int bits, cudaStream_t st) {
+                      int bits, cudaStream_t st, int lo_bit) {
   if (n <= 1) return;
   const int n_blocks = (int)((n + kSortTile - 1) / kSortTile);
   uint32_t *counts = nullptr, *offs = nullptr;
@@ -172,7 +173,7 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv
   uint64_t *ka = keys, *kb = tk;
   uint32_t *va = vals, *vb = tv;
   int passes = 0;
-  for (int shift = 0; shift < bits; shift += 8, ++passes) {
+  for (int shift = lo_bit; shift < bits; shift += 8, ++passes) {
     radix_hist_kernel<<<n_blocks, kSortThreads, 0, st>>>(ka, n, shift, counts, n_blocks);
     scan_exclusive(counts, offs, (int64_t)256 * n_blocks, st);
     radix_scatter_kernel<<<n_blocks, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, offs,

@@ -275,9 +275,9 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
 struct EmitArgs {
   Table T;
   uint64_t cand_cap;
-  uint2* cand;              // candidates (slot, row) at per-ray offsets
-  const uint32_t* cand_off; // [launch index] first candidate of the ray
-  uint32_t* cand_cnt;       // [launch index] candidates of the ray (count pass)
+  uint2* cand;              // candidates (slot, row) at per-ray offsets, rows ascending
+  const uint32_t* cand_off; // [row] first candidate of the ray
+  uint32_t* cand_cnt;       // [row] candidates of the ray (count pass)
   const uint32_t* key_status;  // label pass: validation status per key id
   uint8_t* labels;             // label pass: [row] member of a valid specular key
 };
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(256)
       active = false;
       row = 0u;
     }
-    uint32_t n_mine = (kMode == kModeEmit && active) ? A.cand_off[t] : 0u;
+    uint32_t n_mine = (kMode == kModeEmit && active) ? A.cand_off[row] : 0u;
     const int pair_j = (C.batch && active) ? pair_of_row(C, row) : 0;
     uint16_t lab[kMaxDepth];
     bool alive = active;
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(256)
     }
     if (kMode == kModeLabel && active) A.labels[row] = (uint8_t)n_mine;
     if (kMode == kModeCount && active) {
-      A.cand_cnt[t] = n_mine;
+      A.cand_cnt[row] = n_mine;
       n_total += n_mine;
     }
   }
@@ -894,9 +894,12 @@ __global__ void key_init_kernel(const unsigned long long* __restrict__ n_keys_p,
 
 // ---------------------------------------------------------------- ordering
 // Paths ordered by (rx, type, k, representative row): deterministic output.
+// key = [rx][type][k][representative row in row_bits bits] (LOS, the only
+// k = 0 path of an RX, keeps its masked kNone); bits row_bits + 12
 __global__ void path_sortkey_kernel(const PathRec* __restrict__ p,
                                     const unsigned long long* __restrict__ n_p, int64_t cap,
-                                    uint64_t* __restrict__ key, uint32_t* __restrict__ idx) {
+                                    int row_bits, uint64_t* __restrict__ key,
+                                    uint32_t* __restrict__ idx) {
   const int64_t n = min((int64_t)*n_p, cap);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -907,14 +910,15 @@ __global__ void path_sortkey_kernel(const PathRec* __restrict__ p,
     }
     const uint32_t jtk = p[i].jtk;
     const uint64_t j = jtk & 0xFF, ty = (jtk >> 8) & 1, k = (jtk >> 9) & 7;
-    key[i] = (j << 36) | (ty << 35) | (k << 32) | (uint64_t)p[i].rep;
+    key[i] = (j << (row_bits + 4)) | (ty << (row_bits + 3)) | (k << row_bits) |
+             ((uint64_t)p[i].rep & ((1ull << row_bits) - 1ull));
   }
 }
 
 // per-RX range of the sorted paths: lower bounds of (j << 36) and ((j+1) << 36)
 __global__ void rx_range_kernel(const uint64_t* __restrict__ key,
                                 const unsigned long long* __restrict__ n_p, int64_t cap, int n_rx,
-                                int64_t* __restrict__ start, int64_t* __restrict__ cnt) {
+                                int rx_shift, int64_t* __restrict__ start, int64_t* __restrict__ cnt) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n_rx) return;
   const int64_t n = min((int64_t)*n_p, cap);
@@ -927,9 +931,9 @@ __global__ void rx_range_kernel(const uint64_t* __restrict__ key,
     }
     return lo;
   };
-  const int64_t a = lower((uint64_t)j << 36);
+  const int64_t a = lower((uint64_t)j << rx_shift);
   start[j] = a;
-  cnt[j] = lower((uint64_t)(j + 1) << 36) - a;
+  cnt[j] = lower((uint64_t)(j + 1) << rx_shift) - a;
 }
 
 // Launch order: rows (rays in ascending id) sorted along a Morton curve of
@@ -1462,8 +1466,10 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   while ((1ll << table_bits) < c.table) ++table_bits;
   cand_key_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(W.cand, ctr + kCtrCands, c.cand,
                                                               row_bits); count_launch();
+  // the candidates are in ascending row order (offsets per row), so a stable
+  // sort on the slot bits alone leaves each run in ray order
   radix_sort_pairs(reinterpret_cast<uint64_t*>(W.cand), nullptr, reinterpret_cast<uint64_t*>(W.cand2),
-                   nullptr, c.cand, row_bits + table_bits, st);
+                   nullptr, c.cand, row_bits + table_bits, st, row_bits);
   const SortedCand SC{reinterpret_cast<const uint64_t*>(W.cand), ctr + kCtrCands, c.cand, row_bits};
   run_start_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(SC, W.T.next); count_launch();
   key_init_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.cnt + kCntKeys, W.K, W.T.next, SC); count_launch();
@@ -1518,12 +1524,12 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
 
   // deterministic order of the paths (padding sorts last), ranges, field
   path_sortkey_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>(W.raw, ctr + kCtrPaths, c.paths,
-                                                                   W.psk, W.psi); count_launch();
-  radix_sort_pairs(W.psk, W.psi, W.ptk, W.pti, c.paths, 44, st);
+                                                                   row_bits, W.psk, W.psi); count_launch();
+  radix_sort_pairs(W.psk, W.psi, W.ptk, W.pti, c.paths, row_bits + 12, st);
   path_gather_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>(W.raw, W.psi, ctr + kCtrPaths,
                                                                   c.paths, (PathRec*)r->paths); count_launch();
   rx_range_kernel<<<(r->n_rx + 63) / 64, 64, 0, st>>>(W.psk, ctr + kCtrPaths, c.paths, r->n_rx,
-                                                      r->rx_start_d, r->rx_count_d); count_launch();
+                                                      row_bits + 4, r->rx_start_d, r->rx_count_d); count_launch();
   if (sc->have_materials) {
     field_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>((const PathRec*)r->paths, ctr + kCtrPaths,
                                                               c.paths, sc->mat, r->p.freq, r->p.pol,
