@@ -92,6 +92,8 @@ def _declare(L):
     L.orc_sim_n_paths.restype = C.c_int64
     L.orc_sim_n_paths.argtypes = [_P]
     L.orc_sim_paths.argtypes = [_P] + [_P] * 13
+    L.orc_sim_path_grads.restype = None
+    L.orc_sim_path_grads.argtypes = [_P, _P, _P, _P, C.c_int, _P]
     L.orc_sim_shadow_disc_counts.restype = None
     L.orc_sim_shadow_disc_counts.argtypes = [_P, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
     L.orc_sim_ray_labels.restype = None
@@ -311,6 +313,17 @@ class OracleSim:
         out = np.zeros((self.ray_ids.shape[0], lib().orc_sim_n_seg(self._h)), np.int64)
         lib().orc_sim_disc_counts(self._h, _ptr(out))
         return out
+
+    def path_grads(self, eps_r, sigma, scat) -> np.ndarray:
+        """[n_paths, 3, n_labels] complex d a_p / d(eps_r, sigma, S)_l."""
+        eps = np.ascontiguousarray(eps_r, np.float64)
+        sig = np.ascontiguousarray(sigma, np.float64)
+        sca = np.ascontiguousarray(scat, np.float64)
+        L = eps.shape[0]
+        n = lib().orc_sim_n_paths(self._h)
+        out = np.zeros((n, 3, L, 2))
+        lib().orc_sim_path_grads(self._h, _ptr(eps), _ptr(sig), _ptr(sca), L, _ptr(out))
+        return out[..., 0] + 1j * out[..., 1]
 
     def shadow_disc_counts(self, stride: int = 1):
         """(discs entered, casts) of the diffuse validation shadow casts of every

@@ -1370,6 +1370,50 @@ void orc_sim_hit_sens(void* s, double* dq, double* dn) {
 // Analytic gradient of L with respect to (eps_r, sigma, S) per label, given
 // dL/dP_j.  d|a|^2/dx = 2 Re(conj(a) da/dx); da/deta_l sums over the
 // interactions with label l; deta/deps_r = 1, deta/dsigma = -j/(2 pi f eps0),
+// Complex derivatives of every path coefficient (phase split, Sec. II-B
+// readings) with respect to the per-label (eps_r, sigma, S): out[p][t][l] for
+// t = 0 eps_r, 1 sigma, 2 S, as (re, im) pairs; the same product rule as
+// orc_sim_backward, before it is contracted with a loss.
+void orc_sim_path_grads(void* s, const double* eps, const double* sig, const double* sca,
+                        int n_labels, double* out) {
+  Sim* sim = (Sim*)s;
+  const double f = sim->p.freq;
+  const int pol = sim->p.pol;
+  const cd deta_dsig(0.0, -1.0 / (2.0 * kPi * f * kEps0));
+  const size_t per = (size_t)3 * n_labels * 2;
+  for (size_t i = 0; i < sim->paths.size(); ++i) {
+    double* o = out + i * per;
+    for (size_t q = 0; q < per; ++q) o[q] = 0.0;
+    const PathOut& P = sim->paths[i];
+    cd fac[5], dfac_deta[5], dfdS[5];
+    for (int m = 0; m < P.k; ++m) {
+      const int l = P.mats[m];
+      const cd eta = permittivity(eps[l], sig[l], f);
+      const cd G = fresnel(eta, P.cosv[m], pol);
+      const bool last_diffuse = P.type == 1 && m == P.k - 1;
+      const double R = std::sqrt(std::max(0.0, 1.0 - sca[l] * sca[l]));
+      const double c = last_diffuse ? sca[l] : R;
+      fac[m] = c * G;
+      dfac_deta[m] = c * dfresnel_deta(eta, P.cosv[m], pol);
+      dfdS[m] = last_diffuse ? G : (-sca[l] / R) * G;
+    }
+    for (int m = 0; m < P.k; ++m) {
+      cd others(P.geo, 0.0);
+      for (int q = 0; q < P.k; ++q)
+        if (q != m) others *= fac[q];
+      const int l = P.mats[m];
+      const cd de = others * dfac_deta[m];
+      const cd ds = de * deta_dsig;
+      const cd dc = others * dfdS[m];
+      const cd v[3] = {de, ds, dc};
+      for (int t = 0; t < 3; ++t) {
+        o[(t * n_labels + l) * 2] += v[t].real();
+        o[(t * n_labels + l) * 2 + 1] += v[t].imag();
+      }
+    }
+  }
+}
+
 // dR/dS = -S/R for a specular reflection, and the diffuse factor is S itself.
 void orc_sim_backward(void* s, const double* eps, const double* sig, const double* sca,
                       const double* dL_dP, double* g_eps, double* g_sig, double* g_sca,
