@@ -300,6 +300,28 @@ nrt_status nrt_autotune_batch(nrt_result* result, const int32_t* packets, const 
  * NRT_ERR_STATE before nrt_set_materials; NRT_ERR_CUDA. */
 nrt_status nrt_backward_noalloc(nrt_result* result, const float* dL_dpower, float* grad);
 
+/* Channel frequency response (Sec. III-B): for every receiver j and
+ * f_n = f_c + (n - (N-1)/2) B/(N-1), n = 0..N-1, with f_c the simulation's
+ * frequency (the path coefficients are taken there),
+ *   H_j(f_n) = sum over RX j's paths of a_p exp(-j 2 pi f_n tau_p),
+ * summed in FP64 (phase from the FP64 cycle count).  The CIR is its inverse
+ * DFT.  H: host double[n_rx][n_freq][2] (re, im).  Needs the field
+ * (materials set).  Synchronises.  Errors: NRT_ERR_ARG (n_freq < 2,
+ * bandwidth <= 0), NRT_ERR_STATE (no materials). */
+nrt_status nrt_cfr(nrt_result* result, double bandwidth, int32_t n_freq, double* H);
+
+/* Eq. 5 loss per receiver, L_j = |h_j - h^_j|^2 / |h^_j|^2 on the CIR (equal
+ * to the same ratio on the CFR by Parseval), and the gradient of
+ * sum_j w_j L_j with respect to the per-label eps_r, sigma, S.
+ *   H_target : host double[n_rx][n_freq][2], the target CFR (same grid)
+ *   rx_weight: host float[n_rx] (0 leaves a receiver out)
+ *   loss     : host double[n_rx] or NULL
+ *   g_*      : host float[n_labels] each, or NULL
+ * Synchronises.  Errors as nrt_cfr. */
+nrt_status nrt_cfr_backward(nrt_result* result, double bandwidth, int32_t n_freq,
+                            const double* H_target, const float* rx_weight, double* loss,
+                            float* g_eps, float* g_sig, float* g_sca);
+
 /* Per-key validation summary of a simulation run with keep_keys = 1 (used to
  * merge ray-range shards into the single-run result, Sec. II-B's lowest valid
  * ray per key): for each of the result's keys (nrt_result_counts' keys),

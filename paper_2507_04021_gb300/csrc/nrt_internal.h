@@ -174,6 +174,8 @@ void free_work(nrt_result* r);
 nrt_status run_field(nrt_result* r);
 nrt_status run_backward(nrt_result* r, const float* dL_dP, float* g_eps, float* g_sig,
                         float* g_sca);
+nrt_status adjoint_to_host(nrt_result* r, const float* dL_dP_h, const double2* wpath_d,
+                           float* g_eps, float* g_sig, float* g_sca);
 
 }  // namespace nrt
 

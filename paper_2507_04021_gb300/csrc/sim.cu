@@ -1062,10 +1062,12 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+// wpath (optional): per-path complex weights W_p of a loss whose gradient is
+// sum_p Re(W_p da_p/dtheta); without it W_p = 2 dL/dP_j conj(a_p) (power loss).
 __global__ void __launch_bounds__(kAdjThreads)
     adjoint_kernel(const PathRec* __restrict__ P, int64_t n, const float* __restrict__ mat,
-                   float freq, int pol, const float* __restrict__ dLdP, int n_labels,
-                   double* __restrict__ partial) {
+                   float freq, int pol, const float* __restrict__ dLdP,
+                   const double2* __restrict__ wpath, int n_labels, double* __restrict__ partial) {
   __shared__ double sh[kAdjThreads / 32];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int k = 0, labs[kMaxDepth];
@@ -1092,18 +1094,23 @@ __global__ void __launch_bounds__(kAdjThreads)
     }
     float2 a = make_float2(p.geo, 0.0f);
     for (int m = 0; m < k; ++m) a = cmul(a, fac[m]);
-    const float w = 2.0f * dLdP[j];
+    float2 W;
+    if (wpath) {
+      const double2 wd = wpath[i];
+      W = make_float2((float)wd.x, (float)wd.y);
+    } else {
+      W = cscale(2.0f * dLdP[j], cconj(a));
+    }
     const float ks = (float)(1.0 / (2.0 * 3.14159265358979323846 * kEps0)) / freq;
     for (int m = 0; m < k; ++m) {
       float2 oth = make_float2(p.geo, 0.0f);
       for (int q = 0; q < k; ++q)
         if (q != m) oth = cmul(oth, fac[q]);
-      const float2 ca = cconj(a);
-      const float2 de = cmul(ca, cmul(oth, dfe[m]));
-      const float2 ds = cmul(ca, cmul(oth, dfs[m]));
-      ge[m] = w * de.x;
-      gs[m] = w * (de.y * ks);  // Re(z * (-j ks)) = ks * Im(z)
-      gc[m] = w * ds.x;
+      const float2 de = cmul(W, cmul(oth, dfe[m]));
+      const float2 ds = cmul(W, cmul(oth, dfs[m]));
+      ge[m] = de.x;
+      gs[m] = de.y * ks;  // Re(z * (-j ks)) = ks * Im(z)
+      gc[m] = ds.x;
     }
   }
   for (int l = 0; l < n_labels; ++l) {
@@ -1857,6 +1864,13 @@ void free_work(nrt_result* r) {
 
 nrt_status run_backward(nrt_result* r, const float* dL_dP_h, float* g_eps, float* g_sig,
                         float* g_sca) {
+  return adjoint_to_host(r, dL_dP_h, nullptr, g_eps, g_sig, g_sca);
+}
+
+// Material gradient sum_p Re(W_p da_p/dtheta) into host arrays: W_p from the
+// per-RX dL/dP (host) or from per-path weights already on the device.
+nrt_status adjoint_to_host(nrt_result* r, const float* dL_dP_h, const double2* wpath_d,
+                           float* g_eps, float* g_sig, float* g_sca) {
   nrt_scene* sc = r->scene;
   nrt_ctx* ctx = sc->ctx;
   cudaStream_t st = ctx->stream;
@@ -1868,11 +1882,13 @@ nrt_status run_backward(nrt_result* r, const float* dL_dP_h, float* g_eps, float
   TRY(cudaMallocAsync(&dldp, r->n_rx * 4, st));
   TRY(cudaMallocAsync(&out, 3 * L * 4, st));
   TRY(cudaMallocAsync(&partial, nb * 3 * L * 8, st));
-  TRY(cudaMemcpyAsync(dldp, dL_dP_h, r->n_rx * 4, cudaMemcpyHostToDevice, st));
+  if (dL_dP_h) TRY(cudaMemcpyAsync(dldp, dL_dP_h, r->n_rx * 4, cudaMemcpyHostToDevice, st));
+  else TRY(cudaMemsetAsync(dldp, 0, r->n_rx * 4, st));
   TRY(cudaMemsetAsync(partial, 0, nb * 3 * L * 8, st));
   if (np > 0)
     adjoint_kernel<<<(unsigned)nb, kAdjThreads, 0, st>>>((const PathRec*)r->paths, np, sc->mat,
-                                                         r->p.freq, r->p.pol, dldp, L, partial); count_launch();
+                                                         r->p.freq, r->p.pol, dldp, wpath_d, L,
+                                                         partial); count_launch();
   adjoint_reduce_kernel<<<(3 * L + 127) / 128, 128, 0, st>>>(partial, nb, L, out); count_launch();
   std::vector<float> h(3 * L);
   TRY(cudaMemcpyAsync(h.data(), out, 3 * L * 4, cudaMemcpyDeviceToHost, st));

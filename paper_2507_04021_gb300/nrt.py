@@ -116,6 +116,8 @@ def lib():
         L.nrt_batch_times.argtypes = [_P, _P, _P]
         L.nrt_autotune_batch.argtypes = [_P, _P, _P, C.c_int, C.c_int, _P, _P]
         L.nrt_ray_labels_read.argtypes = [_P, _P]
+        L.nrt_cfr.argtypes = [_P, C.c_double, C.c_int32, _P]
+        L.nrt_cfr_backward.argtypes = [_P, C.c_double, C.c_int32, _P, _P, _P, _P, _P, _P]
         L.nrt_keys_read.argtypes = [_P, _P, _P, _P, _P]
         L.nrt_get_stream.argtypes = [_P, C.POINTER(_P)]
         L.nrt_mlp_create.argtypes = [_P, _P, C.c_int64, _P, _P, C.c_int64, C.POINTER(_P)]
@@ -347,6 +349,27 @@ class Result:
         self.ctx._check(lib().nrt_keys_read(self._h, *[_np_ptr(out[k]) for k in
                                                         ("key_hi", "key_lo", "tried", "rep")]))
         return out
+
+    def cfr(self, bandwidth=1.5e9, n_freq=129):
+        """[n_rx, n_freq] complex channel frequency response around the
+        simulation frequency (nrt_cfr)."""
+        H = np.zeros((self.n_rx, n_freq, 2), np.float64)
+        self.ctx._check(lib().nrt_cfr(self._h, float(bandwidth), int(n_freq), _np_ptr(H)))
+        return H[..., 0] + 1j * H[..., 1]
+
+    def cfr_backward(self, H_target, rx_weight=None, bandwidth=1.5e9):
+        """Eq. 5 losses per RX and the gradient of sum_j w_j L_j (nrt_cfr_backward)."""
+        T = np.asarray(H_target)
+        n_freq = T.shape[1]
+        Tr = np.ascontiguousarray(np.stack([T.real, T.imag], -1), np.float64)
+        w = np.ascontiguousarray(np.ones(self.n_rx) if rx_weight is None else rx_weight, np.float32)
+        L = self.scene.n_labels
+        loss = np.zeros(self.n_rx, np.float64)
+        ge, gs, gc = (np.zeros(L, np.float32) for _ in range(3))
+        self.ctx._check(lib().nrt_cfr_backward(self._h, float(bandwidth), int(n_freq), _np_ptr(Tr),
+                                               _np_ptr(w), _np_ptr(loss), _np_ptr(ge), _np_ptr(gs),
+                                               _np_ptr(gc)))
+        return loss, (ge, gs, gc)
 
     def ray_labels(self):
         """Per traced row (ascending ray id): 1 if the ray is a member of a valid
