@@ -111,3 +111,80 @@ def recover_materials(backend, target_db, init, steps=200, lr=0.05) -> Fit:
     with torch.no_grad():
         eps, sig, sca = from_params(u, v, w)
     return Fit(eps.numpy(), sig.numpy(), sca.numpy(), hist)
+
+
+# ---------------------------------------------------------------- Eq. 5 (CIR) loss
+class CfrLossFn(torch.autograd.Function):
+    """Eq. 5 loss |h - h^|^2 / |h^|^2 on the CIR (equal on the CFR), weighted
+    over receivers and summed over simulations, as a function of per-label
+    (eps_r, sigma, S).  ``backend.loss_and_grads(eps, sigma, scat)`` returns
+    (loss, (g_eps, g_sigma, g_scat)) from nrt_cfr_backward."""
+
+    @staticmethod
+    def forward(ctx, eps, sig, sca, backend):
+        e = eps.detach().cpu().numpy().astype(np.float64)
+        s = sig.detach().cpu().numpy().astype(np.float64)
+        c = sca.detach().cpu().numpy().astype(np.float64)
+        loss, g = backend.loss_and_grads(e, s, c)
+        ctx.g = [torch.as_tensor(np.asarray(x, np.float64), device=eps.device) for x in g]
+        return torch.as_tensor(loss, dtype=torch.float64, device=eps.device)
+
+    @staticmethod
+    def backward(ctx, gL):
+        return gL * ctx.g[0], gL * ctx.g[1], gL * ctx.g[2], None
+
+
+class LibnrtCfrBackend:
+    """CFR targets of R simulations (stored paths re-weighted by the field;
+    nothing is re-traced) and the Eq. 5 loss with receivers weighted 1/M."""
+
+    def __init__(self, scene, results, targets, bandwidth=1.5e9):
+        self.scene = scene
+        self.results = list(results)
+        self.targets = [np.asarray(t) for t in targets]
+        self.bandwidth = bandwidth
+
+    def loss_and_grads(self, eps, sig, sca):
+        self.scene.set_materials(eps.astype(np.float32), sig.astype(np.float32),
+                                 sca.astype(np.float32))
+        total = 0.0
+        g = [np.zeros(len(eps)) for _ in range(3)]
+        for r, T in zip(self.results, self.targets):
+            r.field()
+            w = np.full(r.n_rx, 1.0 / r.n_rx)
+            loss, gr = r.cfr_backward(T, w, self.bandwidth)
+            total += float(np.sum(w * loss))
+            for i in range(3):
+                g[i] += gr[i]
+        return total, g
+
+
+def cfr_targets(scene, results, eps, sig, sca, bandwidth=1.5e9, n_freq=129):
+    """Target CFRs of the results at given materials (the ground truth)."""
+    scene.set_materials(np.asarray(eps, np.float32), np.asarray(sig, np.float32),
+                        np.asarray(sca, np.float32))
+    out = []
+    for r in results:
+        r.field()
+        out.append(r.cfr(bandwidth, n_freq))
+    return out
+
+
+def recover_materials_cfr(backend, init, steps=200, lr=0.05) -> Fit:
+    """Adam on the Eq. 5 loss; init = (eps, sigma, S)."""
+    u0, v0, w0 = to_params(*init)
+    u = torch.tensor(u0, requires_grad=True)
+    v = torch.tensor(v0, requires_grad=True)
+    w = torch.tensor(w0, requires_grad=True)
+    opt = torch.optim.Adam([u, v, w], lr=lr)
+    hist = []
+    for _ in range(steps):
+        opt.zero_grad()
+        eps, sig, sca = from_params(u, v, w)
+        loss = CfrLossFn.apply(eps, sig, sca, backend)
+        loss.backward()
+        opt.step()
+        hist.append(float(loss.detach()))
+    with torch.no_grad():
+        eps, sig, sca = from_params(u, v, w)
+    return Fit(eps.numpy(), sig.numpy(), sca.numpy(), hist)
