@@ -448,6 +448,20 @@ def ours(args):
                                           "diffuse_casts", "candidates", "keys", "paths",
                                           "n_dps")},
     }
+    # channel frequency response of the last simulation (129 frequencies over
+    # 1.5 GHz, all receivers) and its Eq. 5 gradient, device-timed
+    import torch as _t
+    cf_ev = [_t.cuda.Event(enable_timing=True) for _ in range(3)]
+    cf_ev[0].record(stream)
+    H = last.cfr(1.5e9, 129)
+    cf_ev[1].record(stream)
+    last.cfr_backward(H * 0.9, None, 1.5e9)
+    cf_ev[2].record(stream)
+    _t.cuda.synchronize()
+    line["cfr"] = {"n_freq": 129, "bandwidth_hz": 1.5e9, "paths": counts["paths"],
+                   "ms": cf_ev[0].elapsed_time(cf_ev[1]),
+                   "backward_ms": cf_ev[1].elapsed_time(cf_ev[2]),
+                   "note": "FP64 sums; includes the host copy of H (and of the target)"}
     if args.proposal and rank == 0:
         line["proposal"] = proposal_bench(scene, o)
     if args.batch_pairs > 0:

@@ -54,6 +54,7 @@ typedef struct {
 
 enum { NRT_CAPTURE_SPHERE = 0, NRT_CAPTURE_VIS = 1 };
 enum { NRT_POL_TE = 0, NRT_POL_TM = 1 };
+enum { NRT_LAUNCH_FIB = 0, NRT_LAUNCH_DPS = 1 };
 
 /* Trace parameters.  nrt_trace_params_default() fills the paper's values
  * (Table I: kappa = 10, t_a = 1 degree, t_d = 0.01 m). */
@@ -76,6 +77,11 @@ typedef struct {
   int32_t keep_keys;    /* 1: keep per-key validation summaries, readable by nrt_keys_read */
   int64_t key_capacity;   /* hash-table slots (power of two; 0 = automatic) */
   int64_t cand_capacity;  /* candidate buffer entries (0 = automatic) */
+  int32_t launch;       /* NRT_LAUNCH_FIB: Fibonacci sphere of n_rays rays;
+                           NRT_LAUNCH_DPS: one ray per DPS toward its reception
+                           point (Sec. II-B), ray i = the i-th DPS in voxel Morton
+                           order, n_rays taken as the scene's DPS count */
+  int32_t reserved2;
 } nrt_trace_params;
 
 /* Per-simulation counters (nrt_result_counts). */

@@ -54,6 +54,7 @@ class OrcParams(C.Structure):
         ("validate", C.c_int32), ("n_threads", C.c_int32), ("n_rays", C.c_int64),
         ("r_rx", C.c_double), ("t_min", C.c_double), ("delta", C.c_double),
         ("t_a_deg", C.c_double), ("t_d", C.c_double), ("freq", C.c_double),
+        ("launch", C.c_int32), ("pad0", C.c_int32),
     ]
 
 
@@ -228,9 +229,10 @@ class SimParams:
     t_a_deg: float = 1.0
     t_d: float = 0.01
     freq: float = 28e9
+    launch: int = 0           # 0 Fibonacci sphere, 1 one ray per DPS (Morton order)
 
     def to_c(self) -> OrcParams:
-        return OrcParams(**{k: getattr(self, k) for k, _ in OrcParams._fields_})
+        return OrcParams(**{k: getattr(self, k) for k, _ in OrcParams._fields_ if k != "pad0"})
 
 
 class OracleSim:
@@ -242,9 +244,11 @@ class OracleSim:
         self.tx = np.ascontiguousarray(tx, np.float64).reshape(3)
         self.rx = np.ascontiguousarray(rx, np.float64).reshape(-1, 3)
         if ray_ids is None:
-            ray_ids = np.arange(params.n_rays, dtype=np.int64)
+            ray_ids = np.arange(scene.n_dps if params.launch == 1 else params.n_rays, dtype=np.int64)
         self.ray_ids = np.ascontiguousarray(ray_ids, np.int64)
         cp = params.to_c()
+        if params.launch == 1:  # one ray per DPS: the launch has n_dps rays
+            cp.n_rays = scene.n_dps
         self._h = lib().orc_sim_run(scene._h, _ptr(self.tx), _ptr(self.rx), self.rx.shape[0],
                                     C.byref(cp), _ptr(self.ray_ids), self.ray_ids.shape[0])
 

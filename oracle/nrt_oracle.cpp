@@ -81,6 +81,7 @@ struct Scene {
   std::vector<std::array<int, 3>> dps_vox;
   std::vector<std::vector<int>> dps_pts;
   std::vector<V3> recv;                 // reception point = mean of the DPS's points
+  std::vector<int> dps_morton;          // DPS of each rank in voxel Morton order
   double rho = 0, rp = 0, lambda_d = 0;
   float bmin_f[3] = {0, 0, 0};
   // acceleration grid (grid_cell <= 0 means brute force over all discs)
@@ -147,6 +148,22 @@ Scene* build_scene(const float* pos, const float* nrm, const uint16_t* surf, con
     V3 s{0, 0, 0};
     for (int i : S->dps_pts[d]) s = s + S->P[i];
     S->recv[d] = (1.0 / (double)S->dps_pts[d].size()) * s;
+  }
+  // DPS-directed launch order: voxel Morton code, x in the lowest bit
+  {
+    auto spread = [](uint64_t x) {
+      uint64_t r = 0;
+      for (int b = 0; b < 21; ++b) r |= ((x >> b) & 1ull) << (3 * b);
+      return r;
+    };
+    std::vector<std::pair<uint64_t, int>> mk(next);
+    for (int d = 0; d < next; ++d) {
+      const auto& v = S->dps_vox[d];
+      mk[d] = {spread((uint64_t)v[0]) | (spread((uint64_t)v[1]) << 1) | (spread((uint64_t)v[2]) << 2), d};
+    }
+    std::sort(mk.begin(), mk.end());
+    S->dps_morton.resize(next);
+    for (int d = 0; d < next; ++d) S->dps_morton[d] = mk[d].second;
   }
   // uniform grid: each disc listed in every cell overlapped by the cube of
   // half-size r_p + band_cap around its centre.
@@ -449,6 +466,8 @@ struct orc_params {
   double t_a_deg;      // refinement angle threshold, degrees
   double t_d;          // refinement plane-distance threshold, m
   double freq;         // Hz
+  int32_t launch;      // 0 Fibonacci sphere of n_rays, 1 one ray per DPS (Sec. II-B)
+  int32_t pad0;
 };
 
 }  // extern "C"
@@ -745,9 +764,16 @@ const double kShadowAngle = 1e-6;
 const double kShadowKick = 1e-5;
 const double kShadowJitter = 1e-3;
 
+// Launch direction of ray rid: Fibonacci sphere, or (Sec. II-B) toward the
+// reception point of the rid-th DPS in voxel Morton order.
+V3 launch_dir(const Sim& sim, int64_t rid) {
+  if (sim.p.launch == 1) return unit(sim.S->recv[sim.S->dps_morton[rid]] - sim.tx);
+  return fib_dir(rid, sim.p.n_rays);
+}
+
 void trace_ray(Sim& sim, int64_t row, const CastCfg& cfg) {
   int64_t rid = sim.ray_ids[row];
-  V3 d0 = fib_dir(rid, sim.p.n_rays);
+  V3 d0 = launch_dir(sim, rid);
   sim.excl[row] = sim.n_seg + 1;
   sim.n_hits[row] = 0;
   trace_one(sim, sim.rec, row, d0, cfg, &sim.excl[row], &sim.n_hits[row]);
@@ -1494,7 +1520,7 @@ void orc_sim_disc_counts(void* s, int64_t* out) {
   const int64_t n = (int64_t)sim->ray_ids.size();
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t r = 0; r < n; ++r) {
-    V3 o = sim->tx, d = fib_dir(sim->ray_ids[r], sim->p.n_rays);
+    V3 o = sim->tx, d = launch_dir(*sim, sim->ray_ids[r]);
     int skip = -1;
     for (int k = 0; k < sim->n_seg; ++k) {
       int64_t& dst = out[r * sim->n_seg + k];

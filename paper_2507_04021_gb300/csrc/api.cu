@@ -277,10 +277,18 @@ nrt_status nrt_set_materials(nrt_scene* s, const float* eps_r, const float* sigm
 }
 
 nrt_status nrt_trace(nrt_scene* s, const float* tx, const float* rx, int n_rx,
-                     const nrt_trace_params* p, const uint32_t* ray_subset, int64_t n_subset,
+                     const nrt_trace_params* p_in, const uint32_t* ray_subset, int64_t n_subset,
                      int subset_on_device, nrt_result** out) {
-  if (!s || !tx || !rx || !p || !out) return NRT_ERR_ARG;
+  if (!s || !tx || !rx || !p_in || !out) return NRT_ERR_ARG;
   nrt_ctx* ctx = s->ctx;
+  nrt_trace_params pl = *p_in;
+  if (pl.launch == NRT_LAUNCH_DPS) {
+    pl.n_rays = s->n_dps;  // one ray per DPS
+  } else if (pl.launch != NRT_LAUNCH_FIB) {
+    ctx->last_error = "unknown launch mode";
+    return NRT_ERR_ARG;
+  }
+  const nrt_trace_params* p = &pl;
   if (n_rx <= 0 || n_rx > 256) {
     ctx->last_error = "n_rx must be in [1, 256]";
     return NRT_ERR_ARG;
@@ -615,6 +623,12 @@ nrt_status nrt_trace_batch(nrt_scene* s, const float* tx, const float* rx, const
   if (!r) return NRT_ERR_OOM;
   r->scene = s;
   s->refs++;
+  if (p->launch != NRT_LAUNCH_FIB) {
+    ctx->last_error = "batches use the Fibonacci launch";
+    delete r;
+    s->refs--;
+    return NRT_ERR_ARG;
+  }
   r->p = *p;
   r->p.n_rays = maxb;
   r->n_pairs = n_pairs;

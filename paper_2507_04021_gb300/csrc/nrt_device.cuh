@@ -110,6 +110,7 @@ struct SceneView {
   const float4* __restrict__ disc_n;
   const uint2* __restrict__ dps_range;  // (first disc, count)
   const float4* __restrict__ dps_center;
+  const float4* __restrict__ recv;      // reception point per DPS (DPS-directed launch)
   const float4* __restrict__ nodes;     // 4 float4 per internal node
   int n_dps;
   int root;        // >= 0 internal node, < 0 leaf ~dps

@@ -501,6 +501,7 @@ SceneView scene_view(const nrt_scene* s) {
   v.disc_n = s->disc_n;
   v.dps_range = s->dps_range;
   v.dps_center = s->dps_center;
+  v.recv = s->dps_recv;
   v.nodes = s->nodes;
   v.n_dps = (int)s->n_dps;
   v.root = s->root;

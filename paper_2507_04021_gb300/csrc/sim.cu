@@ -133,6 +133,7 @@ struct SimConst {
   float lambda;
   int64_t n_rays;
   int64_t vis_words;
+  int launch;  // NRT_LAUNCH_FIB or NRT_LAUNCH_DPS
   // batch mode: rows are grouped by pair (pair j owns rows pair_start[j] ..
   // pair_start[j+1]-1, a Fibonacci launch of pair_rays[j] rays from
   // tx_pair[j]); one shared physical RX; the RX field of a key holds j.
@@ -1164,6 +1165,7 @@ SimConst make_const(const nrt_result* r) {
   C.freq = r->p.freq;
   C.lambda = (float)(299792458.0 / (double)r->p.freq);
   C.n_rays = r->p.n_rays;
+  C.launch = r->p.launch;
   C.vis_words = r->vis_words;
   C.batch = r->n_pairs > 0 ? 1 : 0;
   C.n_pairs = r->n_pairs;
@@ -1188,7 +1190,9 @@ __device__ __forceinline__ unsigned trace_row(const SceneView& S, const SimConst
     n_launch = __ldg(C.pair_rays + pj);
     o = xyz(__ldg(C.tx_pair + pj));
   }
-  float3 d = fib_dir(ray, n_launch);
+  // Fibonacci sphere, or (Sec. II-B) toward the reception point of DPS `ray`
+  // (the DPS are stored in voxel Morton order)
+  float3 d = C.launch == NRT_LAUNCH_DPS ? unit3(xyz(__ldg(S.recv + ray)) - o) : fib_dir(ray, n_launch);
   int skip = -1;
   unsigned segs = 0;
   for (int s = 0; s < C.n_seg; ++s) {
@@ -1402,6 +1406,10 @@ nrt_status make_order(nrt_result* r, const SimConst& C, const uint32_t* subset_d
   cudaStream_t st = ctx->stream;
   const int64_t n = r->n_traced;
   const int sm = ctx->sm_count;
+  if (C.launch == NRT_LAUNCH_DPS) {  // DPS order is already Morton order
+    *order = nullptr;
+    return NRT_OK;
+  }
   const bool cacheable = !subset_d && !C.batch;
   if (cacheable && ctx->order_n == n && ctx->order) {
     *order = ctx->order;

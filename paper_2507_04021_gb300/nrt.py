@@ -21,6 +21,8 @@ _lib = None
 NRT_OK = 0
 CAPTURE_SPHERE = 0
 CAPTURE_VIS = 1
+LAUNCH_FIB = 0
+LAUNCH_DPS = 1
 POL_TE = 0
 POL_TM = 1
 
@@ -42,7 +44,7 @@ class TraceParams(C.Structure):
         ("record_hits", C.c_int32), ("ray_labels", C.c_int32), ("n_rays", C.c_int64),
         ("r_rx", C.c_float), ("t_min", C.c_float), ("t_a_deg", C.c_float), ("t_d", C.c_float),
         ("freq", C.c_float), ("keep_keys", C.c_int32), ("key_capacity", C.c_int64),
-        ("cand_capacity", C.c_int64),
+        ("cand_capacity", C.c_int64), ("launch", C.c_int32), ("reserved2", C.c_int32),
     ]
 
 
@@ -281,7 +283,12 @@ class Result:
                                         C.byref(params), sub_ptr, n_sub, int(on_dev),
                                         C.byref(self._h)))
         self.n_seg = params.max_depth + (1 if params.capture == CAPTURE_SPHERE else 0)
-        self.n_traced = n_sub if ray_subset is not None else int(params.n_rays)
+        if ray_subset is not None:
+            self.n_traced = n_sub
+        elif params.launch == LAUNCH_DPS:
+            self.n_traced = int(scene.info()["n_dps"])
+        else:
+            self.n_traced = int(params.n_rays)
 
     def counts(self):
         c = Counters()

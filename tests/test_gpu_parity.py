@@ -159,3 +159,43 @@ def test_office_full_launch_sampled_rays(office, office_gpu, office_orc):
     for k in ("key_hi", "key_lo", "rep", "a", "tau"):
         assert np.array_equal(P1[k], P2[k]), k
     assert np.array_equal(res.power(), res2.power())
+
+
+def test_room_dps_directed_launch(room, room_gpu, room_orc):
+    """The paper's launch (Sec. II-B): one ray per DPS toward its reception
+    point, visibility capture with diffuse paths, room scene."""
+    kp = _room_params(capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1)
+    p = nrt.default_trace_params(**kp)
+    p.launch = nrt.LAUNCH_DPS
+    res = room_gpu.trace(room.tx, room.rx, p)
+    delta = 1e-5 * room.diag
+    osim = oracle.OracleSim(room_orc, room.tx, room.rx,
+                            oracle.SimParams(delta=delta, launch=1, **{k: v for k, v in kp.items()
+                                                                       if k != "freq"}, freq=28e9))
+    assert res.n_traced == room_orc.n_dps
+    h = compare_hits(res.hits(), osim.hits(), delta, sens=osim.hit_sens())
+    print("room DPS launch hits:", h)
+    assert h["mismatch"] == 0, h
+    s = compare_paths(res.paths(), osim, room.eps_r, room.sigma, room.scat)
+    print("room DPS launch paths:", s)
+    assert s["matched"] > 100, s
+
+
+def test_office_dps_directed_launch_subset(office, office_gpu, office_orc):
+    """Office, one ray per DPS (every 60th DPS in Morton order), 5
+    interactions, visibility capture and diffuse paths."""
+    n_dps = office_orc.n_dps
+    ids = np.arange(0, n_dps, 60, dtype=np.uint32)
+    kp = dict(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1, rep_tries=8)
+    p = nrt.default_trace_params(**kp)
+    p.launch = nrt.LAUNCH_DPS
+    res = office_gpu.trace(office.tx, office.rx, p, ray_subset=ids)
+    delta = 1e-5 * office.diag
+    osim = oracle.OracleSim(office_orc, office.tx, office.rx,
+                            oracle.SimParams(delta=delta, launch=1, **kp), ray_ids=ids.astype(np.int64))
+    h = compare_hits(res.hits(), osim.hits(), delta, sens=osim.hit_sens())
+    print("office DPS launch hits:", h)
+    assert h["mismatch"] == 0, h
+    s = compare_paths(res.paths(), osim, office.eps_r, office.sigma, office.scat)
+    print("office DPS launch paths:", s)
+    assert s["matched"] > 0.8 * s["keys"], s

@@ -190,3 +190,30 @@ def test_grid_equals_brute_force_office_subset(office):
         d = rng.normal(size=3)
         rays.append((o, d / np.linalg.norm(d)))
     _compare_casts(bf, gr, rays, delta=1e-5 * office.diag)
+
+
+def test_dps_directed_launch_hits_its_target_dps():
+    """One ray per DPS (Sec. II-B), ray i toward the reception point of the
+    i-th DPS in voxel Morton order: in the convex room a ray aimed at a
+    reception point either hits that DPS or a neighbour sharing its wall
+    (the reception point lies between discs) or leaves through a gap."""
+    room = inputs.room_scene()
+    osc = oracle.OracleScene(room.pos, room.nrm, room.surf, room.mat, rho=0.0625, r_p=0.05)
+    sim = oracle.OracleSim(osc, room.tx, np.array([[4.0, 3.0, 1.2]]), oracle.SimParams(
+        max_depth=1, capture=0, diffuse=0, n_rays=0, launch=1, validate=0))
+    H = sim.hits()
+    vox, cnt, recv = osc.dps()
+    def spread(x):
+        r = np.zeros_like(x)
+        for b in range(21):
+            r |= ((x >> b) & 1) << (3 * b)
+        return r
+    v = vox.astype(np.int64)
+    order = np.argsort(spread(v[:, 0]) | (spread(v[:, 1]) << 1) | (spread(v[:, 2]) << 2), kind="stable")
+    target = order[np.arange(osc.n_dps)]
+    first = H["dps"][:, 0]
+    hit = first >= 0
+    assert hit.mean() > 0.3
+    same = first[hit] == target[hit]
+    near = np.abs(v[first[hit]] - v[target[hit]]).max(axis=1) <= 1
+    assert same.mean() > 0.5 and near.all()
