@@ -267,6 +267,39 @@ def batch_bench(args, scene, o, rank, stream, flush):
     }
 
 
+def launch_bench(scene, o, tx, stream):
+    """The paper's launch (one ray per DPS toward its reception point) against
+    the Fibonacci sphere with the same number of rays: device time, paths
+    and received power per receiver (office, 16 RX, 5 interactions, VIS +
+    diffuse)."""
+    import torch
+    from paper_2507_04021_gb300 import nrt
+
+    n_dps = int(scene.info()["n_dps"])
+    out = {}
+    for name, launch in (("dps", nrt.LAUNCH_DPS), ("fibonacci", nrt.LAUNCH_FIB)):
+        p = nrt.default_trace_params(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1,
+                                     n_rays=n_dps, rep_tries=8)
+        p.launch = launch
+        scene.trace(tx, o.rx, p).close()  # warm-up
+        ms = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = scene.trace(tx, o.rx, p)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            _, c = r.counts()
+            pw = r.power().astype(np.float64)
+            r.close()
+        out[name] = {"rays": n_dps, "ms": float(np.median(ms)), "paths": c["paths"],
+                     "keys": c["keys"],
+                     "power_db": [round(float(10 * np.log10(x)), 3) if x > 0 else None for x in pw]}
+    return out
+
+
 def proposal_bench(scene, o):
     """Learned launch proposal (RX-sphere capture, 16 RX, 5 specular
     interactions): 5M labelled rays from 250 trajectory positions, training
@@ -462,6 +495,8 @@ def ours(args):
                    "ms": cf_ev[0].elapsed_time(cf_ev[1]),
                    "backward_ms": cf_ev[1].elapsed_time(cf_ev[2]),
                    "note": "FP64 sums; includes the host copy of H (and of the target)"}
+    if rank == 0:
+        line["launch_comparison"] = launch_bench(scene, o, tx, stream)
     if args.proposal and rank == 0:
         line["proposal"] = proposal_bench(scene, o)
     if args.batch_pairs > 0:

@@ -5,8 +5,10 @@
 // frequency f_c at which the coefficients a_p are computed.  At 28 GHz a path
 // accumulates ~1e3 cycles, so the phase is formed from the cycle count
 // f_n tau_p in FP64, reduced to its fractional part exactly, and only then
-// turned into a phasor (FP32 sincospi of a value in [-1, 1]); the sums are
-// FP64, in a fixed two-level order (the same result on every run).
+// turned into a phasor (FP32 sincospi of a value in [-1, 1]); within a run of
+// 16 frequencies the phasor advances by FP32 products with the per-path step,
+// re-anchored from FP64 at every run.  The sums are FP64, in a fixed
+// two-level order (the same result on every run).
 //
 // Eq. 5, L_j = |h_j - h^_j|^2 / |h^_j|^2 on the CIR h = IDFT(H), equals the
 // same ratio on the CFR (Parseval), so it is evaluated on H; its material
@@ -34,6 +36,13 @@ __device__ __forceinline__ float2 phasor(double cyc) {
   return make_float2(c, -s);
 }
 
+// Within a run of kCfrGroup frequencies the phasor advances by a fixed step
+// e^{-j 2 pi df tau}; FP32 products drift by ~1e-6 rad over a run, and every
+// run starts again from the exact FP64 cycle count.
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
 __global__ void tau_kernel(const PathRec* __restrict__ P, int64_t n, double* __restrict__ tau) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -55,13 +64,15 @@ __global__ void __launch_bounds__(kCfrThreads)
        i += (int64_t)gridDim.x * blockDim.x) {
     const float2 av = a[b + i];
     const double t = tau[b + i];
-    const double c0 = (f0 + n0 * df) * t, dc = df * t;
+    float2 e = phasor((f0 + n0 * df) * t);
+    const float2 step = phasor(df * t);
 #pragma unroll
     for (int q = 0; q < kCfrGroup; ++q) {
       if (q >= nf) break;
-      const float2 e = phasor(fma((double)q, dc, c0));
-      re[q] += (double)(av.x * e.x - av.y * e.y);
-      im[q] += (double)(av.x * e.y + av.y * e.x);
+      const float2 v = cmulf(av, e);
+      re[q] += (double)v.x;
+      im[q] += (double)v.y;
+      e = cmulf(e, step);
     }
   }
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -109,13 +120,19 @@ __global__ void cfr_weight_kernel(const PathRec* __restrict__ P, const double* _
        i += (int64_t)gridDim.x * blockDim.x) {
     const int j = P[i].jtk & 0xFF;
     const double t = tau[i];
-    const double c0 = f0 * t, dc = df * t;
+    const float2 step = phasor(df * t);
     double gx = 0.0, gy = 0.0;
-    for (int q = 0; q < n_freq; ++q) {
-      const float2 e = phasor(fma((double)q, dc, c0));  // exp(-j ...); use its conjugate
-      const double2 d = dH[(int64_t)j * n_freq + q];
-      gx += d.x * e.x + d.y * e.y;
-      gy += d.y * e.x - d.x * e.y;
+    for (int q0 = 0; q0 < n_freq; q0 += kCfrGroup) {
+      float2 e = phasor((f0 + q0 * df) * t);  // exp(-j ...); its conjugate is used
+      float sx = 0.f, sy = 0.f;
+      for (int q = q0; q < min(n_freq, q0 + kCfrGroup); ++q) {
+        const double2 d = dH[(int64_t)j * n_freq + q];
+        sx += (float)d.x * e.x + (float)d.y * e.y;
+        sy += (float)d.y * e.x - (float)d.x * e.y;
+        e = cmulf(e, step);
+      }
+      gx += (double)sx;
+      gy += (double)sy;
     }
     W[i] = make_double2(coef[j] * gx, -coef[j] * gy);
   }
