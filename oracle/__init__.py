@@ -93,6 +93,9 @@ def _declare(L):
     L.orc_sim_n_paths.restype = C.c_int64
     L.orc_sim_n_paths.argtypes = [_P]
     L.orc_sim_paths.argtypes = [_P] + [_P] * 13
+    L.orc_jones_amplitude.restype = None
+    L.orc_jones_amplitude.argtypes = [_P, _P, _P, C.c_int, C.c_int, _P, _P, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double)]
     L.orc_sim_path_grads.restype = None
     L.orc_sim_path_grads.argtypes = [_P, _P, _P, _P, C.c_int, _P]
     L.orc_sim_shadow_disc_counts.restype = None
@@ -413,6 +416,21 @@ def fresnel_eta(eta: complex, cos_t, pol=0) -> complex:
 def dfresnel_deta(eta: complex, cos_t, pol=0) -> complex:
     re, im = C.c_double(), C.c_double()
     lib().orc_dfresnel(eta.real, eta.imag, cos_t, pol, C.byref(re), C.byref(im))
+    return complex(re.value, im.value)
+
+
+def jones_amplitude(tx, rx, pts, D, diffuse=False, nd=(0.0, 0.0, 1.0)) -> complex:
+    """Vector-polarisation a / geo of an explicit path (pol = 2 reading):
+    pts [k,3] interaction points, D [k,2] complex (c Gamma_TE, c Gamma_TM)."""
+    tx = np.ascontiguousarray(tx, np.float64)
+    rx = np.ascontiguousarray(rx, np.float64)
+    pts = np.ascontiguousarray(np.asarray(pts, np.float64).reshape(-1, 3))
+    D = np.asarray(D, np.complex128).reshape(-1, 2)
+    Dr = np.ascontiguousarray(np.stack([D.real, D.imag], -1))
+    nd = np.ascontiguousarray(nd, np.float64)
+    re, im = C.c_double(), C.c_double()
+    lib().orc_jones_amplitude(_ptr(tx), _ptr(rx), _ptr(pts), pts.shape[0], int(diffuse), _ptr(nd),
+                              _ptr(Dr), C.byref(re), C.byref(im))
     return complex(re.value, im.value)
 
 

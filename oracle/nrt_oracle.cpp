@@ -514,6 +514,7 @@ struct PathOut {
   int j = 0, type = 0, k = 0;  // type 0 specular / LOS, 1 diffuse
   int64_t rep = -1;
   V3 pts[5];
+  V3 nd{0, 0, 0};  // diffuse paths: surface normal at the scatter point
   int mats[5] = {0, 0, 0, 0, 0};
   double cosv[5] = {0, 0, 0, 0, 0};
   double geo = 0, tau = 0, length = 0;
@@ -599,6 +600,7 @@ Validation validate_diffuse(const Sim& sim, const std::vector<HitRec>& rec, int6
   PathOut& P = v.path;
   P.type = 1;
   P.k = k;
+  P.nd = hk.n;
   double ri = 0.0;
   for (int m = 0; m < k; ++m) {
     const HitRec& hm = rec[row * sim.n_seg + m];
@@ -1039,8 +1041,139 @@ void run_sim(Sim& sim) {
   }
 }
 
-cd path_coefficient(const PathOut& P, const double* eps, const double* sig, const double* sca,
-                    double freq, int pol) {
+// ---------------------------------------------------------------------------
+// Vector polarisation (pol = 2; a reading, the paper leaves the field model to
+// an external library).  TX and RX are isotropic with vertical polarisation:
+// the field leaves along d with unit vector theta^(d) of the spherical basis
+// about +z, and is received with theta^(u), u the direction from the RX back
+// along the arriving ray.  At an interaction with normal n, incoming d_i and
+// outgoing d_o: s^ = unit(d_i x n), p^_in = s^ x d_i, p^_out = s^ x d_o; the
+// s component is multiplied by c Gamma_TE and the p component by c Gamma_TM
+// (c = R, or S at a diffuse last interaction, whose d_o points to the RX).
+// A specular interaction's normal is unit(d_o - d_i).  In these bases a path
+// is a = geo r^T D_k B_{k-1} ... B_1 D_1 e0: e0 the TX polarisation in the
+// first incoming basis, B_m the real 2x2 change from the outgoing basis of
+// interaction m to the incoming basis of m+1, D_m = diag(c Gamma_TE, c Gamma_TM),
+// r the RX polarisation in the last outgoing basis.
+// ---------------------------------------------------------------------------
+inline V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+V3 theta_hat(V3 d) {
+  const double st = std::sqrt(d.x * d.x + d.y * d.y);
+  if (st < 1e-12) return {1.0, 0.0, 0.0};  // along the z axis: x^ by convention
+  return {d.z * d.x / st, d.z * d.y / st, -st};
+}
+
+struct Jones {
+  int k = 0;
+  double los = 0.0;       // k = 0: theta^(d) . theta^(-d)
+  double e0[2] = {0, 0};
+  double B[5][2][2] = {};
+  double r[2] = {0, 0};
+};
+
+Jones make_jones(V3 tx, V3 rx, const V3* pts, int k, bool diffuse, V3 nd) {
+  Jones J;
+  J.k = k;
+  V3 d[6];
+  if (k == 0) {
+    const V3 u = unit(rx - tx);
+    J.los = dot(theta_hat(u), theta_hat((-1.0) * u));
+    return J;
+  }
+  d[0] = unit(pts[0] - tx);
+  for (int m = 1; m < k; ++m) d[m] = unit(pts[m] - pts[m - 1]);
+  d[k] = unit(rx - pts[k - 1]);
+  V3 sv[5], pin[5], pout[5];
+  for (int m = 0; m < k; ++m) {
+    const V3 n = (diffuse && m == k - 1) ? nd : unit(d[m + 1] - d[m]);
+    V3 sx = cross(d[m], n);
+    if (norm(sx) < 1e-12) sx = cross(d[m], std::fabs(d[m].z) < 0.9 ? V3{0, 0, 1} : V3{1, 0, 0});
+    sv[m] = unit(sx);
+    pin[m] = cross(sv[m], d[m]);
+    pout[m] = cross(sv[m], d[m + 1]);
+  }
+  const V3 t0 = theta_hat(d[0]);
+  J.e0[0] = dot(t0, sv[0]);
+  J.e0[1] = dot(t0, pin[0]);
+  for (int m = 0; m + 1 < k; ++m) {
+    J.B[m][0][0] = dot(sv[m + 1], sv[m]);
+    J.B[m][0][1] = dot(sv[m + 1], pout[m]);
+    J.B[m][1][0] = dot(pin[m + 1], sv[m]);
+    J.B[m][1][1] = dot(pin[m + 1], pout[m]);
+  }
+  const V3 tr = theta_hat((-1.0) * d[k]);
+  J.r[0] = dot(tr, sv[k - 1]);
+  J.r[1] = dot(tr, pout[k - 1]);
+  return J;
+}
+
+// a / geo for diagonal factors D[m] = (c Gamma_TE, c Gamma_TM)
+cd jones_amplitude(const Jones& J, const cd (*D)[2]) {
+  if (J.k == 0) return cd(J.los, 0.0);
+  cd v[2] = {J.e0[0], J.e0[1]};
+  for (int m = 0; m < J.k; ++m) {
+    v[0] *= D[m][0];
+    v[1] *= D[m][1];
+    if (m + 1 < J.k) {
+      const cd a0 = J.B[m][0][0] * v[0] + J.B[m][0][1] * v[1];
+      const cd a1 = J.B[m][1][0] * v[0] + J.B[m][1][1] * v[1];
+      v[0] = a0;
+      v[1] = a1;
+    }
+  }
+  return J.r[0] * v[0] + J.r[1] * v[1];
+}
+
+// d(a/geo)/d(D[m][c]) for every interaction m and component c
+void jones_partials(const Jones& J, const cd (*D)[2], cd (*dA)[2]) {
+  cd fwd[5][2];  // field entering interaction m (its incoming basis)
+  cd v[2] = {J.e0[0], J.e0[1]};
+  for (int m = 0; m < J.k; ++m) {
+    fwd[m][0] = v[0];
+    fwd[m][1] = v[1];
+    v[0] *= D[m][0];
+    v[1] *= D[m][1];
+    if (m + 1 < J.k) {
+      const cd a0 = J.B[m][0][0] * v[0] + J.B[m][0][1] * v[1];
+      const cd a1 = J.B[m][1][0] * v[0] + J.B[m][1][1] * v[1];
+      v[0] = a0;
+      v[1] = a1;
+    }
+  }
+  cd w[2] = {J.r[0], J.r[1]};  // row vector after interaction m, in its outgoing basis
+  for (int m = J.k - 1; m >= 0; --m) {
+    dA[m][0] = w[0] * fwd[m][0];
+    dA[m][1] = w[1] * fwd[m][1];
+    // w <- w D_m B_{m-1}
+    const cd u0 = w[0] * D[m][0], u1 = w[1] * D[m][1];
+    if (m > 0) {
+      w[0] = u0 * J.B[m - 1][0][0] + u1 * J.B[m - 1][1][0];
+      w[1] = u0 * J.B[m - 1][0][1] + u1 * J.B[m - 1][1][1];
+    }
+  }
+}
+
+Jones path_jones(const Sim& sim, const PathOut& P) {
+  return make_jones(sim.tx, sim.rx[P.j], P.pts, P.k, P.type == 1, P.nd);
+}
+
+cd path_coefficient(const Sim& sim, const PathOut& P, const double* eps, const double* sig,
+                    const double* sca, double freq, int pol) {
+  if (pol == 2) {
+    cd D[5][2];
+    for (int m = 0; m < P.k; ++m) {
+      const int l = P.mats[m];
+      const cd eta = permittivity(eps[l], sig[l], freq);
+      const bool last_diffuse = P.type == 1 && m == P.k - 1;
+      const double c = last_diffuse ? sca[l] : std::sqrt(std::max(0.0, 1.0 - sca[l] * sca[l]));
+      D[m][0] = c * fresnel(eta, P.cosv[m], 0);
+      D[m][1] = c * fresnel(eta, P.cosv[m], 1);
+    }
+    return P.geo * jones_amplitude(path_jones(sim, P), D);
+  }
   cd a(P.geo, 0.0);
   for (int m = 0; m < P.k; ++m) {
     int l = P.mats[m];
@@ -1352,7 +1485,7 @@ void orc_sim_field(void* s, const double* eps, const double* sig, const double* 
   Sim* sim = (Sim*)s;
   for (int j = 0; j < n_rx; ++j) power[j] = 0.0;
   for (size_t i = 0; i < sim->paths.size(); ++i) {
-    cd a = path_coefficient(sim->paths[i], eps, sig, sca, sim->p.freq, sim->p.pol);
+    cd a = path_coefficient(*sim, sim->paths[i], eps, sig, sca, sim->p.freq, sim->p.pol);
     a_re[i] = a.real();
     a_im[i] = a.imag();
     power[sim->paths[i].j] += std::norm(a);
@@ -1370,14 +1503,14 @@ void orc_sim_path_sens(void* s, const double* eps, const double* sig, const doub
     a_sens[i] = 0.0;
     tau_sens[i] = 0.0;
     if (P.k == 0) continue;
-    cd a = path_coefficient(P, eps, sig, sca, sim->p.freq, sim->p.pol);
+    cd a = path_coefficient(*sim, P, eps, sig, sca, sim->p.freq, sim->p.pol);
     for (int p = 0; p < 2; ++p) {
       if (!P.shadow_ok[p] || !P.shadow[p]) {
         a_sens[i] = -1.0;
         tau_sens[i] = -1.0;
         break;
       }
-      cd b = path_coefficient(*P.shadow[p], eps, sig, sca, sim->p.freq, sim->p.pol);
+      cd b = path_coefficient(*sim, *P.shadow[p], eps, sig, sca, sim->p.freq, sim->p.pol);
       a_sens[i] = std::max(a_sens[i], std::abs(b - a) / std::max(std::abs(a), 1e-300));
       tau_sens[i] = std::max(tau_sens[i], std::fabs(P.shadow[p]->tau - P.tau) / P.tau);
     }
@@ -1396,42 +1529,80 @@ void orc_sim_hit_sens(void* s, double* dq, double* dn) {
 // Analytic gradient of L with respect to (eps_r, sigma, S) per label, given
 // dL/dP_j.  d|a|^2/dx = 2 Re(conj(a) da/dx); da/deta_l sums over the
 // interactions with label l; deta/deps_r = 1, deta/dsigma = -j/(2 pi f eps0),
+}  // extern "C"
+
+namespace {
+
+// a and, per interaction m, da/deta_m and da/dS_m (the label's S) for the
+// scalar model (pol 0 TE, 1 TM: product rule) and the vector model (pol 2:
+// partials of the Jones product).  dR/dS = -S/R; the diffuse factor is S.
+void path_derivs(const Sim& sim, const PathOut& P, const double* eps, const double* sig,
+                 const double* sca, double f, int pol, cd* a_out, cd* da_deta, cd* da_dS) {
+  cd G[5][2], dG[5][2];
+  double c[5], dc[5];
+  for (int m = 0; m < P.k; ++m) {
+    const int l = P.mats[m];
+    const cd eta = permittivity(eps[l], sig[l], f);
+    for (int t = 0; t < 2; ++t) {
+      const int pp = pol == 2 ? t : pol;
+      G[m][t] = fresnel(eta, P.cosv[m], pp);
+      dG[m][t] = dfresnel_deta(eta, P.cosv[m], pp);
+    }
+    const bool last_diffuse = P.type == 1 && m == P.k - 1;
+    const double R = std::sqrt(std::max(0.0, 1.0 - sca[l] * sca[l]));
+    c[m] = last_diffuse ? sca[l] : R;
+    dc[m] = last_diffuse ? 1.0 : (R > 0.0 ? -sca[l] / R : 0.0);
+  }
+  if (pol == 2) {
+    cd D[5][2], dA[5][2];
+    for (int m = 0; m < P.k; ++m)
+      for (int t = 0; t < 2; ++t) D[m][t] = c[m] * G[m][t];
+    const Jones J = path_jones(sim, P);
+    *a_out = P.geo * jones_amplitude(J, D);
+    jones_partials(J, D, dA);
+    for (int m = 0; m < P.k; ++m) {
+      da_deta[m] = P.geo * (dA[m][0] * (c[m] * dG[m][0]) + dA[m][1] * (c[m] * dG[m][1]));
+      da_dS[m] = P.geo * (dA[m][0] * (dc[m] * G[m][0]) + dA[m][1] * (dc[m] * G[m][1]));
+    }
+    return;
+  }
+  cd fac[5];
+  for (int m = 0; m < P.k; ++m) fac[m] = c[m] * G[m][0];
+  cd a(P.geo, 0.0);
+  for (int m = 0; m < P.k; ++m) a *= fac[m];
+  *a_out = a;
+  for (int m = 0; m < P.k; ++m) {
+    cd others(P.geo, 0.0);
+    for (int q = 0; q < P.k; ++q)
+      if (q != m) others *= fac[q];
+    da_deta[m] = others * (c[m] * dG[m][0]);
+    da_dS[m] = others * (dc[m] * G[m][0]);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
 // Complex derivatives of every path coefficient (phase split, Sec. II-B
 // readings) with respect to the per-label (eps_r, sigma, S): out[p][t][l] for
-// t = 0 eps_r, 1 sigma, 2 S, as (re, im) pairs; the same product rule as
-// orc_sim_backward, before it is contracted with a loss.
+// t = 0 eps_r, 1 sigma, 2 S, as (re, im) pairs, before they are contracted
+// with a loss.
 void orc_sim_path_grads(void* s, const double* eps, const double* sig, const double* sca,
                         int n_labels, double* out) {
   Sim* sim = (Sim*)s;
   const double f = sim->p.freq;
-  const int pol = sim->p.pol;
   const cd deta_dsig(0.0, -1.0 / (2.0 * kPi * f * kEps0));
   const size_t per = (size_t)3 * n_labels * 2;
   for (size_t i = 0; i < sim->paths.size(); ++i) {
     double* o = out + i * per;
     for (size_t q = 0; q < per; ++q) o[q] = 0.0;
     const PathOut& P = sim->paths[i];
-    cd fac[5], dfac_deta[5], dfdS[5];
+    cd a, de[5], dS[5];
+    path_derivs(*sim, P, eps, sig, sca, f, sim->p.pol, &a, de, dS);
     for (int m = 0; m < P.k; ++m) {
       const int l = P.mats[m];
-      const cd eta = permittivity(eps[l], sig[l], f);
-      const cd G = fresnel(eta, P.cosv[m], pol);
-      const bool last_diffuse = P.type == 1 && m == P.k - 1;
-      const double R = std::sqrt(std::max(0.0, 1.0 - sca[l] * sca[l]));
-      const double c = last_diffuse ? sca[l] : R;
-      fac[m] = c * G;
-      dfac_deta[m] = c * dfresnel_deta(eta, P.cosv[m], pol);
-      dfdS[m] = last_diffuse ? G : (-sca[l] / R) * G;
-    }
-    for (int m = 0; m < P.k; ++m) {
-      cd others(P.geo, 0.0);
-      for (int q = 0; q < P.k; ++q)
-        if (q != m) others *= fac[q];
-      const int l = P.mats[m];
-      const cd de = others * dfac_deta[m];
-      const cd ds = de * deta_dsig;
-      const cd dc = others * dfdS[m];
-      const cd v[3] = {de, ds, dc};
+      const cd v[3] = {de[m], de[m] * deta_dsig, dS[m]};
       for (int t = 0; t < 3; ++t) {
         o[(t * n_labels + l) * 2] += v[t].real();
         o[(t * n_labels + l) * 2 + 1] += v[t].imag();
@@ -1440,45 +1611,24 @@ void orc_sim_path_grads(void* s, const double* eps, const double* sig, const dou
   }
 }
 
-// dR/dS = -S/R for a specular reflection, and the diffuse factor is S itself.
+// Gradient of a loss of the received powers: d|a|^2/dx = 2 Re(conj(a) da/dx),
+// weighted by dL/dP_j of the path's receiver.
 void orc_sim_backward(void* s, const double* eps, const double* sig, const double* sca,
                       const double* dL_dP, double* g_eps, double* g_sig, double* g_sca,
                       int n_labels) {
   Sim* sim = (Sim*)s;
   const double f = sim->p.freq;
-  const int pol = sim->p.pol;
   for (int l = 0; l < n_labels; ++l) g_eps[l] = g_sig[l] = g_sca[l] = 0.0;
   const cd deta_dsig(0.0, -1.0 / (2.0 * kPi * f * kEps0));
   for (const PathOut& P : sim->paths) {
-    cd fac[5], dfac_deta[5];
-    double dfac_dS[5] = {0, 0, 0, 0, 0};
-    cd dfdS[5];
+    cd a, de[5], dS[5];
+    path_derivs(*sim, P, eps, sig, sca, f, sim->p.pol, &a, de, dS);
+    const double w = dL_dP[P.j] * 2.0;
     for (int m = 0; m < P.k; ++m) {
-      int l = P.mats[m];
-      cd eta = permittivity(eps[l], sig[l], f);
-      cd G = fresnel(eta, P.cosv[m], pol);
-      cd dG = dfresnel_deta(eta, P.cosv[m], pol);
-      bool last_diffuse = P.type == 1 && m == P.k - 1;
-      double R = std::sqrt(std::max(0.0, 1.0 - sca[l] * sca[l]));
-      double c = last_diffuse ? sca[l] : R;
-      fac[m] = c * G;
-      dfac_deta[m] = c * dG;
-      dfdS[m] = last_diffuse ? G : (-sca[l] / R) * G;
-      (void)dfac_dS;
-    }
-    cd a(P.geo, 0.0);
-    for (int m = 0; m < P.k; ++m) a *= fac[m];
-    for (int m = 0; m < P.k; ++m) {
-      cd others(P.geo, 0.0);
-      for (int q = 0; q < P.k; ++q)
-        if (q != m) others *= fac[q];
-      cd da_deta = others * dfac_deta[m];
-      cd da_dS = others * dfdS[m];
-      double w = dL_dP[P.j] * 2.0;
-      int l = P.mats[m];
-      g_eps[l] += w * (std::conj(a) * da_deta).real();
-      g_sig[l] += w * (std::conj(a) * da_deta * deta_dsig).real();
-      g_sca[l] += w * (std::conj(a) * da_dS).real();
+      const int l = P.mats[m];
+      g_eps[l] += w * (std::conj(a) * de[m]).real();
+      g_sig[l] += w * (std::conj(a) * de[m] * deta_dsig).real();
+      g_sca[l] += w * (std::conj(a) * dS[m]).real();
     }
   }
 }
@@ -1596,6 +1746,24 @@ void orc_vis_disc_counts(void* s, const double* rx, const int32_t* j, const int3
     Hit h = cast(*S, r, d, -1, t_max, false, cfg);
     out[i] = discs_entered(*S, r, d, -1, t_min, h.hit ? h.t : t_max);
   }
+}
+
+// Vector-polarisation coefficient / geo of a path given explicitly: TX, RX,
+// k interaction points (pts[3k]), diffuse flag with the scatter normal nd,
+// and the diagonal factors D (c Gamma_TE, c Gamma_TM per interaction, as
+// re/im pairs [k][2][2]).  For closed-form pins of the vector model.
+void orc_jones_amplitude(const double* tx, const double* rx, const double* pts, int k, int diffuse,
+                         const double* nd, const double* D, double* re, double* im) {
+  V3 p[5];
+  for (int m = 0; m < k; ++m) p[m] = {pts[3 * m], pts[3 * m + 1], pts[3 * m + 2]};
+  const Jones J = make_jones({tx[0], tx[1], tx[2]}, {rx[0], rx[1], rx[2]}, p, k, diffuse != 0,
+                             {nd[0], nd[1], nd[2]});
+  cd DD[5][2];
+  for (int m = 0; m < k; ++m)
+    for (int t = 0; t < 2; ++t) DD[m][t] = cd(D[(m * 2 + t) * 2], D[(m * 2 + t) * 2 + 1]);
+  const cd a = jones_amplitude(J, DD);
+  *re = a.real();
+  *im = a.imag();
 }
 
 // Standalone EM helpers for closed-form pins.
