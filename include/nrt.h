@@ -53,7 +53,7 @@ typedef struct {
 } nrt_scene_params;
 
 enum { NRT_CAPTURE_SPHERE = 0, NRT_CAPTURE_VIS = 1 };
-enum { NRT_POL_TE = 0, NRT_POL_TM = 1 };
+enum { NRT_POL_TE = 0, NRT_POL_TM = 1, NRT_POL_VECTOR = 2 };
 enum { NRT_LAUNCH_FIB = 0, NRT_LAUNCH_DPS = 1 };
 
 /* Trace parameters.  nrt_trace_params_default() fills the paper's values
@@ -63,7 +63,15 @@ typedef struct {
   int32_t capture;      /* NRT_CAPTURE_SPHERE (RX sphere of radius r_rx) or
                            NRT_CAPTURE_VIS (visibility matrix, Sec. II-B) */
   int32_t diffuse;      /* 1: diffuse scattering as the last interaction (Sec. II-B-1) */
-  int32_t pol;          /* NRT_POL_TE or NRT_POL_TM (scalar Fresnel model) */
+  int32_t pol;          /* NRT_POL_TE or NRT_POL_TM: scalar Fresnel model, every
+                           interaction reflects with that coefficient.
+                           NRT_POL_VECTOR: vertically polarised isotropic TX and RX
+                           (theta^ of the spherical basis about +z); at each
+                           interaction the component across the plane of
+                           incidence takes Gamma_TE and the one in it Gamma_TM,
+                           with the basis rotations between interactions (the
+                           paper delegates the field model to an EM library,
+                           Sec. II-B; this is the vector reading of it) */
   int32_t kappa;        /* refinement retries (Sec. II-B-2) */
   int32_t rep_tries;    /* candidates validated per path key, in ray-id order (1..32) */
   int32_t record_hits;  /* 1: keep per-ray hit records readable by nrt_hits_read */
@@ -119,6 +127,8 @@ typedef struct {
   float* tau;        /* delay, s */
   float* a;          /* [n][2] complex path coefficient (real, imag), without the
                         propagation phase exp(-j 2 pi f tau) */
+  float* normal;     /* [n][3] surface normal at the scatter point of a diffuse
+                        path, facing the incoming ray (0 for specular / LOS) */
 } nrt_path_view;
 
 /* Status text for a status code (static storage). */
@@ -302,8 +312,9 @@ nrt_status nrt_autotune_batch(nrt_result* result, const int32_t* packets, const 
  * race on it.  Each call writes every partial it reads, so no state carries
  * over between calls.  Work is enqueued on the context stream; the call does
  * not synchronise.
- * Errors: NRT_ERR_ARG for NULL pointers or more than 256 labels;
- * NRT_ERR_STATE before nrt_set_materials; NRT_ERR_CUDA. */
+ * Errors: NRT_ERR_ARG for NULL pointers, more than 256 labels or a result
+ * traced with NRT_POL_VECTOR (scalar models only); NRT_ERR_STATE before
+ * nrt_set_materials; NRT_ERR_CUDA. */
 nrt_status nrt_backward_noalloc(nrt_result* result, const float* dL_dpower, float* grad);
 
 /* Channel frequency response (Sec. III-B): for every receiver j and

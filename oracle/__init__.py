@@ -93,6 +93,8 @@ def _declare(L):
     L.orc_sim_n_paths.restype = C.c_int64
     L.orc_sim_n_paths.argtypes = [_P]
     L.orc_sim_paths.argtypes = [_P] + [_P] * 13
+    L.orc_sim_path_normals.restype = None
+    L.orc_sim_path_normals.argtypes = [_P, _P]
     L.orc_jones_amplitude.restype = None
     L.orc_jones_amplitude.argtypes = [_P, _P, _P, C.c_int, C.c_int, _P, _P, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double)]
@@ -220,7 +222,7 @@ class SimParams:
     max_depth: int = 2
     capture: int = 0          # 0 RX sphere, 1 visibility matrix
     diffuse: int = 0
-    pol: int = 0              # 0 TE, 1 TM
+    pol: int = 0              # 0 TE, 1 TM, 2 vector (Jones chain)
     kappa: int = 10
     rep_tries: int = 8
     validate: int = 1
@@ -308,6 +310,12 @@ class OracleSim:
                                        ("hi", "lo", "j", "type", "k", "rep", "pts", "mats", "cos",
                                         "geo", "tau", "length", "certain")])
         return r
+
+    def path_normals(self) -> np.ndarray:
+        """[n_paths, 3] scatter-point normal of each diffuse path (0 otherwise)."""
+        out = np.zeros((lib().orc_sim_n_paths(self._h), 3))
+        lib().orc_sim_path_normals(self._h, _ptr(out))
+        return out
 
     def cast_counts(self) -> dict:
         out = np.zeros(4, np.int64)

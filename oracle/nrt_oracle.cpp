@@ -1378,6 +1378,18 @@ void orc_sim_paths(void* s, uint64_t* hi, uint64_t* lo, int32_t* j, int32_t* typ
   }
 }
 
+// [n_paths][3] surface normal at the scatter point of each diffuse path,
+// facing the incoming ray (0 for specular and LOS paths)
+void orc_sim_path_normals(void* s, double* nd) {
+  Sim* sim = (Sim*)s;
+  for (size_t i = 0; i < sim->paths.size(); ++i) {
+    const PathOut& P = sim->paths[i];
+    nd[3 * i] = P.nd.x;
+    nd[3 * i + 1] = P.nd.y;
+    nd[3 * i + 2] = P.nd.z;
+  }
+}
+
 // Candidate status of ray `rid` for key (hi, lo):
 //   0 certainly not a candidate, 1 certainly a candidate, 2 uncertain (the ray
 //   could produce the key under a decision the oracle marks ambiguous: a

@@ -296,6 +296,7 @@ nrt_status nrt_trace(nrt_scene* s, const float* tx, const float* rx, int n_rx,
   if (p->max_depth < 1 || p->max_depth > kMaxDepth || p->n_rays <= 0 ||
       p->n_rays > (int64_t)0xFFFFFFFE || p->rep_tries < 1 || p->rep_tries > 32 || p->kappa < 0 ||
       !(p->freq > 0.f) || !(p->t_min >= 0.f) || (p->capture != 0 && p->capture != 1) ||
+      p->pol < NRT_POL_TE || p->pol > NRT_POL_VECTOR ||
       (p->capture == NRT_CAPTURE_SPHERE && p->diffuse)) {
     ctx->last_error = "invalid trace parameters";
     return NRT_ERR_ARG;
@@ -479,6 +480,8 @@ nrt_status nrt_paths_read(const nrt_result* r, const nrt_path_view* v) {
     }
     if (v->geo) v->geo[i] = p.geo;
     if (v->tau) v->tau[i] = (float)((double)p.length / 299792458.0);
+    if (v->normal)
+      for (int c = 0; c < 3; ++c) v->normal[3 * i + c] = p.nd[c];
     if (v->a) {
       v->a[2 * i] = r->field_done ? a[i].x : 0.f;
       v->a[2 * i + 1] = r->field_done ? a[i].y : 0.f;
@@ -580,7 +583,8 @@ nrt_status nrt_trace_batch(nrt_scene* s, const float* tx, const float* rx, const
     return NRT_ERR_ARG;
   }
   if (p->capture != NRT_CAPTURE_VIS || p->max_depth < 1 || p->max_depth > kMaxDepth ||
-      p->rep_tries < 1 || p->rep_tries > 32 || p->kappa < 0 || !(p->freq > 0.f)) {
+      p->rep_tries < 1 || p->rep_tries > 32 || p->kappa < 0 || !(p->freq > 0.f) ||
+      p->pol < NRT_POL_TE || p->pol > NRT_POL_VECTOR) {
     ctx->last_error = "invalid batch trace parameters (visibility capture required)";
     return NRT_ERR_ARG;
   }

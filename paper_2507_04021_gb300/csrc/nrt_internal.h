@@ -126,8 +126,8 @@ enum Ctr : int {
   kCtrCount
 };
 
-// Path record (device, 128 bytes)
-struct PathRec {
+// Path record (device, 144 bytes)
+struct alignas(16) PathRec {
   uint64_t hi, lo;
   uint32_t rep;   // representative row (LOS: kNone)
   uint32_t jtk;   // rx | type << 8 | k << 9
@@ -136,9 +136,10 @@ struct PathRec {
   float cosv[5];
   uint32_t mats_lo, mats_hi;  // 5 material labels, one byte each
   float pts[15];
-  float pad[1];
+  float nd[3];    // diffuse: surface normal at the scatter point (facing the incoming ray)
+  float pad[3];
 };
-static_assert(sizeof(PathRec) == 128, "PathRec layout");
+static_assert(sizeof(PathRec) == 144, "PathRec layout");
 
 void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t st);
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,

@@ -655,6 +655,9 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
       }
       P.mats_lo = (uint32_t)mats;
       P.mats_hi = (uint32_t)(mats >> 32);
+      P.nd[0] = n.x;
+      P.nd[1] = n.y;
+      P.nd[2] = n.z;
       const float ci = nn.w;
       const float rho = S.rho;
       P.geo = C.lambda / (4.0f * 3.14159265358979f) *
@@ -987,11 +990,122 @@ __device__ __forceinline__ int path_mat(const PathRec& P, int m) {
   return (int)((mats >> (8 * m)) & 0xFF);
 }
 
+// ---------------------------------------------------------------- vector polarisation
+// pol = NRT_POL_VECTOR.  TX and RX radiate / receive along theta^ (spherical
+// basis about +z).  Each interaction m has an incoming direction d_m, an
+// outgoing d_{m+1} and a normal n_m (specular: along d_{m+1} - d_m; diffuse
+// last interaction: the scatter point's surface normal).  Its field basis is
+// s = unit(d_m x n_m) across the plane of incidence and p = s x d (in: d_m,
+// out: d_{m+1}); the s component is scaled by c Gamma_TE, the p component by
+// c Gamma_TM (c = R, or S at a diffuse last interaction).  Between two
+// interactions the outgoing basis of m is re-expressed in the incoming basis
+// of m+1 by a real 2x2 matrix, both bases spanning the plane normal to
+// d_{m+1}.  a = geo r^T D_k B_{k-1} ... B_1 D_1 e0 (e0, r: the TX and RX
+// polarisation in the first and last basis).  LOS: theta^(u) . theta^(-u) = 1.
+struct PathFrame {
+  float3 tx;              // the simulation's TX
+  const float4* tx_pair;  // batch: TX of pair j
+  const float4* rx;       // physical receivers (batch: one)
+  int batch;
+};
+
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// theta^ along the unit direction d; x^ on the z axis
+__device__ __forceinline__ float3 theta_unit(float3 d) {
+  const float h = sqrtf(d.x * d.x + d.y * d.y);
+  if (h < 1e-12f) return f3(1.0f, 0.0f, 0.0f);
+  const float c = d.z / h;
+  return f3(c * d.x, c * d.y, -h);
+}
+
+// s^ across the plane of incidence; at (near) normal incidence, where the
+// plane is undefined and Gamma_TM = -Gamma_TE, any unit vector across d_in
+__device__ __forceinline__ float3 across_unit(float3 din, float3 n) {
+  const float3 s = cross3(din, n);
+  const float l = len3(s);
+  if (l < 1e-4f)
+    return unit3(cross3(din, fabsf(din.z) < 0.9f ? f3(0.0f, 0.0f, 1.0f) : f3(1.0f, 0.0f, 0.0f)));
+  return (1.0f / l) * s;
+}
+
+struct JonesGeom {
+  float e0[2];                 // TX polarisation in the first incoming basis
+  float B[kMaxDepth - 1][4];   // outgoing basis of m -> incoming basis of m+1 (row-major)
+  float r[2];                  // RX polarisation in the last outgoing basis
+};
+
+__device__ __forceinline__ void jones_geom(const PathRec& p, int k, int diffuse, float3 tx,
+                                           float3 rx, JonesGeom& J) {
+  float3 q = f3(p.pts[0], p.pts[1], p.pts[2]);
+  float3 din = unit3(q - tx);
+  float3 s_prev = f3(0.f, 0.f, 0.f), po_prev = s_prev;
+#pragma unroll
+  for (int m = 0; m < kMaxDepth; ++m) {
+    if (m < k) {
+      const float3 nxt = m + 1 < k ? f3(p.pts[3 * m + 3], p.pts[3 * m + 4], p.pts[3 * m + 5]) : rx;
+      const float3 dout = unit3(nxt - q);
+      const float3 n = (diffuse && m == k - 1) ? f3(p.nd[0], p.nd[1], p.nd[2]) : unit3(dout - din);
+      const float3 s = across_unit(din, n);
+      const float3 pin = cross3(s, din);
+      if (m == 0) {
+        const float3 t = theta_unit(din);
+        J.e0[0] = dot3(t, s);
+        J.e0[1] = dot3(t, pin);
+      } else {
+        J.B[m - 1][0] = dot3(s, s_prev);
+        J.B[m - 1][1] = dot3(s, po_prev);
+        J.B[m - 1][2] = dot3(pin, s_prev);
+        J.B[m - 1][3] = dot3(pin, po_prev);
+      }
+      s_prev = s;
+      po_prev = cross3(s, dout);
+      din = dout;
+      q = nxt;
+    }
+  }
+  const float3 t = theta_unit(-1.0f * din);
+  J.r[0] = dot3(t, s_prev);
+  J.r[1] = dot3(t, po_prev);
+}
+
+__device__ __forceinline__ float3 frame_tx(const PathFrame& F, int j) {
+  return F.batch ? xyz(__ldg(F.tx_pair + j)) : F.tx;
+}
+__device__ __forceinline__ float3 frame_rx(const PathFrame& F, int j) {
+  return xyz(__ldg(F.rx + (F.batch ? 0 : j)));
+}
+
+// per-interaction factors c Gamma (scalar: pol's coefficient; vector: TE, TM)
+// and, for the adjoint, c dGamma/deta and dc/dS Gamma
+__device__ __forceinline__ void interaction_factors(const PathRec& p, int m, int k, int diffuse,
+                                                    const float* __restrict__ mat, float freq,
+                                                    int pol, float2* D, float2* dDe, float2* dDs) {
+  const int l = path_mat(p, m);
+  const float2 eta = permittivity(mat[l], mat[256 + l], freq);
+  const float Sl = mat[512 + l];
+  const bool last_d = diffuse && m == k - 1;
+  const float R = sqrtf(fmaxf(0.0f, 1.0f - Sl * Sl));
+  const float c = last_d ? Sl : R;
+  const float dc = last_d ? 1.0f : (R > 0.0f ? -Sl / R : 0.0f);
+  const int n = pol == 2 ? 2 : 1;
+  for (int t = 0; t < n; ++t) {
+    const int pp = pol == 2 ? t : pol;
+    const float2 G = fresnel(eta, p.cosv[m], pp);
+    D[t] = cscale(c, G);
+    if (dDe) dDe[t] = cscale(c, dfresnel(eta, p.cosv[m], pp));
+    if (dDs) dDs[t] = cscale(dc, G);
+  }
+}
+
 // a = geo * prod_m f_m Gamma_m(theta_m): f = sqrt(1 - S^2) for a specular
-// reflection (effective roughness), f = S for the diffuse last interaction.
+// reflection (effective roughness), f = S for the diffuse last interaction;
+// the vector model replaces the product by the 2x2 chain above.
 __global__ void field_kernel(const PathRec* __restrict__ P, const unsigned long long* __restrict__ n_p,
                              int64_t cap, const float* __restrict__ mat, float freq, int pol,
-                             float2* __restrict__ a_out) {
+                             PathFrame F, float2* __restrict__ a_out) {
   const int64_t n = min((int64_t)*n_p, cap);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -999,13 +1113,35 @@ __global__ void field_kernel(const PathRec* __restrict__ P, const unsigned long 
     const int k = (p.jtk >> 9) & 7;
     const int diffuse = (p.jtk >> 8) & 1;
     float2 a = make_float2(p.geo, 0.0f);
-    for (int m = 0; m < k; ++m) {
-      const int l = path_mat(p, m);
-      const float2 eta = permittivity(mat[l], mat[256 + l], freq);
-      const float2 G = fresnel(eta, p.cosv[m], pol);
-      const float Sl = mat[512 + l];
-      const float f = (diffuse && m == k - 1) ? Sl : sqrtf(fmaxf(0.0f, 1.0f - Sl * Sl));
-      a = cmul(a, cscale(f, G));
+    if (pol == 2) {
+      if (k > 0) {
+        const int j = p.jtk & 0xFF;
+        JonesGeom J;
+        jones_geom(p, k, diffuse, frame_tx(F, j), frame_rx(F, j), J);
+        float2 v0 = make_float2(J.e0[0], 0.0f), v1 = make_float2(J.e0[1], 0.0f);
+#pragma unroll
+        for (int m = 0; m < kMaxDepth; ++m) {
+          if (m < k) {
+            float2 D[2];
+            interaction_factors(p, m, k, diffuse, mat, freq, pol, D, nullptr, nullptr);
+            v0 = cmul(v0, D[0]);
+            v1 = cmul(v1, D[1]);
+            if (m + 1 < k) {
+              const float2 u0 = cadd(cscale(J.B[m][0], v0), cscale(J.B[m][1], v1));
+              const float2 u1 = cadd(cscale(J.B[m][2], v0), cscale(J.B[m][3], v1));
+              v0 = u0;
+              v1 = u1;
+            }
+          }
+        }
+        a = cscale(p.geo, cadd(cscale(J.r[0], v0), cscale(J.r[1], v1)));
+      }
+    } else {
+      for (int m = 0; m < k; ++m) {
+        float2 D[1];
+        interaction_factors(p, m, k, diffuse, mat, freq, pol, D, nullptr, nullptr);
+        a = cmul(a, D[0]);
+      }
     }
     a_out[i] = a;
   }
@@ -1065,9 +1201,13 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // wpath (optional): per-path complex weights W_p of a loss whose gradient is
 // sum_p Re(W_p da_p/dtheta); without it W_p = 2 dL/dP_j conj(a_p) (power loss).
+//
+// Vector model: a / geo is linear in each interaction's (D_TE, D_TM); its
+// partials are (row vector after m) x (field entering m), component-wise,
+// from one forward and one backward sweep over the 2x2 chain.
 __global__ void __launch_bounds__(kAdjThreads)
     adjoint_kernel(const PathRec* __restrict__ P, int64_t n, const float* __restrict__ mat,
-                   float freq, int pol, const float* __restrict__ dLdP,
+                   float freq, int pol, PathFrame F, const float* __restrict__ dLdP,
                    const double2* __restrict__ wpath, int n_labels, double* __restrict__ partial) {
   __shared__ double sh[kAdjThreads / 32];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1078,23 +1218,63 @@ __global__ void __launch_bounds__(kAdjThreads)
     k = (p.jtk >> 9) & 7;
     const int diffuse = (p.jtk >> 8) & 1;
     const int j = p.jtk & 0xFF;
-    float2 fac[kMaxDepth], dfe[kMaxDepth], dfs[kMaxDepth];
-    for (int m = 0; m < k; ++m) {
-      const int l = path_mat(p, m);
-      labs[m] = l;
-      const float2 eta = permittivity(mat[l], mat[256 + l], freq);
-      const float2 G = fresnel(eta, p.cosv[m], pol);
-      const float2 dG = dfresnel(eta, p.cosv[m], pol);
-      const float Sl = mat[512 + l];
-      const bool last_d = diffuse && m == k - 1;
-      const float R = sqrtf(fmaxf(0.0f, 1.0f - Sl * Sl));
-      const float c = last_d ? Sl : R;
-      fac[m] = cscale(c, G);
-      dfe[m] = cscale(c, dG);
-      dfs[m] = last_d ? G : cscale(R > 0.0f ? -Sl / R : 0.0f, G);
-    }
+    // da/deta_m and da/dS_m (before the loss weight)
+    float2 dae[kMaxDepth], das[kMaxDepth];
     float2 a = make_float2(p.geo, 0.0f);
-    for (int m = 0; m < k; ++m) a = cmul(a, fac[m]);
+    if (pol == 2) {
+      if (k > 0) {
+        JonesGeom J;
+        jones_geom(p, k, diffuse, frame_tx(F, j), frame_rx(F, j), J);
+        float2 D[kMaxDepth][2], De[kMaxDepth][2], Ds[kMaxDepth][2], fw[kMaxDepth][2];
+        float2 v0 = make_float2(J.e0[0], 0.0f), v1 = make_float2(J.e0[1], 0.0f);
+#pragma unroll
+        for (int m = 0; m < kMaxDepth; ++m) {
+          if (m < k) {
+            labs[m] = path_mat(p, m);
+            interaction_factors(p, m, k, diffuse, mat, freq, pol, D[m], De[m], Ds[m]);
+            fw[m][0] = v0;
+            fw[m][1] = v1;
+            v0 = cmul(v0, D[m][0]);
+            v1 = cmul(v1, D[m][1]);
+            if (m + 1 < k) {
+              const float2 u0 = cadd(cscale(J.B[m][0], v0), cscale(J.B[m][1], v1));
+              const float2 u1 = cadd(cscale(J.B[m][2], v0), cscale(J.B[m][3], v1));
+              v0 = u0;
+              v1 = u1;
+            }
+          }
+        }
+        a = cscale(p.geo, cadd(cscale(J.r[0], v0), cscale(J.r[1], v1)));
+        float2 w0 = make_float2(p.geo * J.r[0], 0.0f), w1 = make_float2(p.geo * J.r[1], 0.0f);
+#pragma unroll
+        for (int m = kMaxDepth - 1; m >= 0; --m) {
+          if (m < k) {
+            const float2 x0 = cmul(w0, fw[m][0]), x1 = cmul(w1, fw[m][1]);
+            dae[m] = cadd(cmul(x0, De[m][0]), cmul(x1, De[m][1]));
+            das[m] = cadd(cmul(x0, Ds[m][0]), cmul(x1, Ds[m][1]));
+            if (m > 0) {  // w <- w D_m B_{m-1}
+              const float2 y0 = cmul(w0, D[m][0]), y1 = cmul(w1, D[m][1]);
+              w0 = cadd(cscale(J.B[m - 1][0], y0), cscale(J.B[m - 1][2], y1));
+              w1 = cadd(cscale(J.B[m - 1][1], y0), cscale(J.B[m - 1][3], y1));
+            }
+          }
+        }
+      }
+    } else {
+      float2 fac[kMaxDepth], dfe[kMaxDepth], dfs[kMaxDepth];
+      for (int m = 0; m < k; ++m) {
+        labs[m] = path_mat(p, m);
+        interaction_factors(p, m, k, diffuse, mat, freq, pol, &fac[m], &dfe[m], &dfs[m]);
+      }
+      for (int m = 0; m < k; ++m) a = cmul(a, fac[m]);
+      for (int m = 0; m < k; ++m) {
+        float2 oth = make_float2(p.geo, 0.0f);
+        for (int q = 0; q < k; ++q)
+          if (q != m) oth = cmul(oth, fac[q]);
+        dae[m] = cmul(oth, dfe[m]);
+        das[m] = cmul(oth, dfs[m]);
+      }
+    }
     float2 W;
     if (wpath) {
       const double2 wd = wpath[i];
@@ -1104,11 +1284,8 @@ __global__ void __launch_bounds__(kAdjThreads)
     }
     const float ks = (float)(1.0 / (2.0 * 3.14159265358979323846 * kEps0)) / freq;
     for (int m = 0; m < k; ++m) {
-      float2 oth = make_float2(p.geo, 0.0f);
-      for (int q = 0; q < k; ++q)
-        if (q != m) oth = cmul(oth, fac[q]);
-      const float2 de = cmul(W, cmul(oth, dfe[m]));
-      const float2 ds = cmul(W, cmul(oth, dfs[m]));
+      const float2 de = cmul(W, dae[m]);
+      const float2 ds = cmul(W, das[m]);
       ge[m] = de.x;
       gs[m] = de.y * ks;  // Re(z * (-j ks)) = ks * Im(z)
       gc[m] = ds.x;
@@ -1140,6 +1317,15 @@ __global__ void adjoint_reduce_kernel(const double* __restrict__ partial, int64_
   double s = 0.0;
   for (int64_t b = 0; b < n_blocks; ++b) s += partial[b * 3 * n_labels + t];
   out[t] = (float)s;
+}
+
+PathFrame path_frame(const nrt_result* r) {
+  PathFrame F;
+  F.tx = make_float3(r->tx[0], r->tx[1], r->tx[2]);
+  F.tx_pair = r->tx_pair;
+  F.rx = r->rx;
+  F.batch = r->n_pairs > 0 ? 1 : 0;
+  return F;
 }
 
 inline int blocks_for(int64_t n, int threads, int sm, int per_sm = 16) {
@@ -1548,7 +1734,7 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   if (sc->have_materials) {
     field_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>((const PathRec*)r->paths, ctr + kCtrPaths,
                                                               c.paths, sc->mat, r->p.freq, r->p.pol,
-                                                              r->path_a); count_launch();
+                                                              path_frame(r), r->path_a); count_launch();
     power_partial_kernel<<<dim3(kPowerChunks, r->n_rx), 256, 0, st>>>(r->path_a, r->rx_start_d,
                                                                      r->rx_count_d, r->power_part); count_launch();
     power_sum_kernel<<<(r->n_rx + 127) / 128, 128, 0, st>>>(r->power_part, r->n_rx, r->power); count_launch();
@@ -1729,7 +1915,8 @@ nrt_status run_field(nrt_result* r) {
   }
   unsigned long long* np = r->ctr + kCtrPaths;
   field_kernel<<<blocks_for(r->path_cap, 256, ctx->sm_count), 256, 0, st>>>(
-      (const PathRec*)r->paths, np, r->path_cap, sc->mat, r->p.freq, r->p.pol, r->path_a); count_launch();
+      (const PathRec*)r->paths, np, r->path_cap, sc->mat, r->p.freq, r->p.pol, path_frame(r),
+      r->path_a); count_launch();
   power_partial_kernel<<<dim3(kPowerChunks, r->n_rx), 256, 0, st>>>(r->path_a, r->rx_start_d,
                                                                    r->rx_count_d, r->power_part); count_launch();
   power_sum_kernel<<<(r->n_rx + 127) / 128, 128, 0, st>>>(r->power_part, r->n_rx, r->power); count_launch();
@@ -1895,8 +2082,8 @@ nrt_status adjoint_to_host(nrt_result* r, const float* dL_dP_h, const double2* w
   TRY(cudaMemsetAsync(partial, 0, nb * 3 * L * 8, st));
   if (np > 0)
     adjoint_kernel<<<(unsigned)nb, kAdjThreads, 0, st>>>((const PathRec*)r->paths, np, sc->mat,
-                                                         r->p.freq, r->p.pol, dldp, wpath_d, L,
-                                                         partial); count_launch();
+                                                         r->p.freq, r->p.pol, path_frame(r), dldp,
+                                                         wpath_d, L, partial); count_launch();
   adjoint_reduce_kernel<<<(3 * L + 127) / 128, 128, 0, st>>>(partial, nb, L, out); count_launch();
   std::vector<float> h(3 * L);
   TRY(cudaMemcpyAsync(h.data(), out, 3 * L * 4, cudaMemcpyDeviceToHost, st));

@@ -25,6 +25,7 @@ LAUNCH_FIB = 0
 LAUNCH_DPS = 1
 POL_TE = 0
 POL_TM = 1
+POL_VECTOR = 2
 
 
 class NrtError(RuntimeError):
@@ -70,7 +71,8 @@ class MlpTrainOpts(C.Structure):
 
 class PathView(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in (
-        "key_hi", "key_lo", "rep", "rx", "type", "k", "pts", "mats", "cos_theta", "geo", "tau", "a")]
+        "key_hi", "key_lo", "rep", "rx", "type", "k", "pts", "mats", "cos_theta", "geo", "tau", "a",
+        "normal")]
 
 
 _P = C.c_void_p
@@ -310,7 +312,8 @@ class Result:
                "type": np.zeros(n, np.int32), "k": np.zeros(n, np.int32),
                "pts": np.zeros((n, 5, 3), np.float32), "mats": np.zeros((n, 5), np.uint8),
                "cos_theta": np.zeros((n, 5), np.float32), "geo": np.zeros(n, np.float32),
-               "tau": np.zeros(n, np.float32), "a": np.zeros((n, 2), np.float32)}
+               "tau": np.zeros(n, np.float32), "a": np.zeros((n, 2), np.float32),
+               "normal": np.zeros((n, 3), np.float32)}
         v = PathView(**{k: _np_ptr(a) for k, a in out.items()})
         self.ctx._check(lib().nrt_paths_read(self._h, C.byref(v)))
         return out

@@ -35,16 +35,17 @@ def _by_key(P, mask_rx):
     return {(int(h), int(l)): i for i, (h, l) in enumerate(zip(hi, P["key_lo"]))}
 
 
-def test_batch_equals_single_pair_runs(setup):
+@pytest.mark.parametrize("pol", [nrt.POL_TE, nrt.POL_VECTOR])
+def test_batch_equals_single_pair_runs(setup, pol):
     ctx, sc, traj = setup
     budgets = np.array([3000, 12000, 700, 5000], np.int64)
     tx = traj[[0, 40, 80, 120]]
-    p = _params(n_rays=1)
+    p = _params(n_rays=1, pol=pol)
     b = sc.trace_batch(tx, RXF, budgets, p, packet=64, schedule=1)
     B = b.paths()
     Pb = b.power()
     for j in range(len(budgets)):
-        r = sc.trace(tx[j], RXF[None], _params(n_rays=int(budgets[j])))
+        r = sc.trace(tx[j], RXF[None], _params(n_rays=int(budgets[j]), pol=pol))
         S = r.paths()
         mine = B["rx"] == j
         sub = {k: v[mine] for k, v in B.items()}
