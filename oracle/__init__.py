@@ -54,7 +54,7 @@ class OrcParams(C.Structure):
         ("validate", C.c_int32), ("n_threads", C.c_int32), ("n_rays", C.c_int64),
         ("r_rx", C.c_double), ("t_min", C.c_double), ("delta", C.c_double),
         ("t_a_deg", C.c_double), ("t_d", C.c_double), ("freq", C.c_double),
-        ("launch", C.c_int32), ("pad0", C.c_int32),
+        ("launch", C.c_int32), ("diffraction", C.c_int32),
     ]
 
 
@@ -93,6 +93,15 @@ def _declare(L):
     L.orc_sim_n_paths.restype = C.c_int64
     L.orc_sim_n_paths.argtypes = [_P]
     L.orc_sim_paths.argtypes = [_P] + [_P] * 13
+    L.orc_sim_diffraction.restype = None
+    L.orc_sim_diffraction.argtypes = [_P, C.c_int64, _P, _P, _P, _P, _P, _P]
+    L.orc_utd_F.restype = None
+    L.orc_utd_F.argtypes = [C.c_double, _D, _D]
+    L.orc_diffraction_amplitude.restype = C.c_int
+    L.orc_diffraction_amplitude.argtypes = [_P, _P, _P, _P, _P, _P, _P, _P, C.c_double, C.c_int,
+                                            _D, _D]
+    L.orc_diffraction_geometry.restype = C.c_int
+    L.orc_diffraction_geometry.argtypes = [_P, _P, _P, _P, _P, _P, _P]
     L.orc_sim_path_normals.restype = None
     L.orc_sim_path_normals.argtypes = [_P, _P]
     L.orc_jones_amplitude.restype = None
@@ -235,15 +244,16 @@ class SimParams:
     t_d: float = 0.01
     freq: float = 28e9
     launch: int = 0           # 0 Fibonacci sphere, 1 one ray per DPS (Morton order)
+    diffraction: int = 0      # 1: single-bounce edge diffraction over the given edges
 
     def to_c(self) -> OrcParams:
-        return OrcParams(**{k: getattr(self, k) for k, _ in OrcParams._fields_ if k != "pad0"})
+        return OrcParams(**{k: getattr(self, k) for k, _ in OrcParams._fields_})
 
 
 class OracleSim:
     """One full simulation for one TX (Sec. II-B), run on construction."""
 
-    def __init__(self, scene: OracleScene, tx, rx, params: SimParams, ray_ids=None):
+    def __init__(self, scene: OracleScene, tx, rx, params: SimParams, ray_ids=None, edges=None):
         self.scene = scene
         self.params = params
         self.tx = np.ascontiguousarray(tx, np.float64).reshape(3)
@@ -256,6 +266,11 @@ class OracleSim:
             cp.n_rays = scene.n_dps
         self._h = lib().orc_sim_run(scene._h, _ptr(self.tx), _ptr(self.rx), self.rx.shape[0],
                                     C.byref(cp), _ptr(self.ray_ids), self.ray_ids.shape[0])
+        if params.diffraction and edges is not None and len(edges.m0) > 0:
+            f = lambda x: np.ascontiguousarray(x, np.float32)  # noqa: E731
+            u = lambda x: np.ascontiguousarray(x, np.uint8)  # noqa: E731
+            self._edges = (f(edges.a), f(edges.b), f(edges.n0), f(edges.n1), u(edges.m0), u(edges.m1))
+            lib().orc_sim_diffraction(self._h, len(edges.m0), *[_ptr(x) for x in self._edges])
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -440,6 +455,37 @@ def jones_amplitude(tx, rx, pts, D, diffuse=False, nd=(0.0, 0.0, 1.0)) -> comple
     lib().orc_jones_amplitude(_ptr(tx), _ptr(rx), _ptr(pts), pts.shape[0], int(diffuse), _ptr(nd),
                               _ptr(Dr), C.byref(re), C.byref(im))
     return complex(re.value, im.value)
+
+
+def utd_F(x: float) -> complex:
+    """UTD transition function F(x) = 2j sqrt(x) e^{jx} int_{sqrt x}^inf e^{-j t^2} dt."""
+    re, im = C.c_double(), C.c_double()
+    lib().orc_utd_F(float(x), C.byref(re), C.byref(im))
+    return complex(re.value, im.value)
+
+
+def _d3(x):
+    return np.ascontiguousarray(x, np.float64).reshape(3)
+
+
+def diffraction_amplitude(tx, rx, a, b, n0, n1, eta0, eta1, freq=28e9, pol=0):
+    """a of the single-bounce diffracted path TX -> edge (a, b; face normals
+    n0, n1; face permittivities eta0, eta1) -> RX, or None without a path."""
+    e0 = np.array([complex(eta0).real, complex(eta0).imag])
+    e1 = np.array([complex(eta1).real, complex(eta1).imag])
+    re, im = C.c_double(), C.c_double()
+    args = [_d3(v) for v in (tx, rx, a, b, n0, n1)] + [e0, e1]
+    ok = lib().orc_diffraction_amplitude(*[_ptr(v) for v in args], float(freq), int(pol),
+                                         C.byref(re), C.byref(im))
+    return complex(re.value, im.value) if ok else None
+
+
+def diffraction_geometry(tx, rx, a, b, n0, n1):
+    """(ok, D, s', s, phi', phi, n, sin b0) of the diffracted path."""
+    out = np.zeros(9)
+    args = [_d3(v) for v in (tx, rx, a, b, n0, n1)]
+    ok = lib().orc_diffraction_geometry(*[_ptr(v) for v in args], _ptr(out))
+    return bool(ok), out[:3].copy(), *[float(v) for v in out[3:]]
 
 
 def max_threads() -> int:

@@ -467,7 +467,7 @@ struct orc_params {
   double t_d;          // refinement plane-distance threshold, m
   double freq;         // Hz
   int32_t launch;      // 0 Fibonacci sphere of n_rays, 1 one ray per DPS (Sec. II-B)
-  int32_t pad0;
+  int32_t diffraction; // 1: single-bounce edge diffraction (orc_sim_diffraction)
 };
 
 }  // extern "C"
@@ -511,10 +511,11 @@ struct Cand {
 
 struct PathOut {
   Key key;
-  int j = 0, type = 0, k = 0;  // type 0 specular / LOS, 1 diffuse
-  int64_t rep = -1;
+  int j = 0, type = 0, k = 0;  // type 0 specular / LOS, 1 diffuse, 2 edge diffraction
+  int64_t rep = -1;            // representative ray id (diffraction: edge index)
   V3 pts[5];
   V3 nd{0, 0, 0};  // diffuse paths: surface normal at the scatter point
+  V3 e0{0, 0, 0}, e1{0, 0, 0}, en0{0, 0, 0}, en1{0, 0, 0};  // diffraction: the edge
   int mats[5] = {0, 0, 0, 0, 0};
   double cosv[5] = {0, 0, 0, 0, 0};
   double geo = 0, tau = 0, length = 0;
@@ -1156,12 +1157,222 @@ void jones_partials(const Jones& J, const cd (*D)[2], cd (*dA)[2]) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Single-bounce edge diffraction (Sec. II-B-3).  An edge is a segment e0 -> e1
+// with the outward normals n0, n1 of its two faces and their materials; the
+// solid is the convex wedge {x : (x - D).n0 < 0 and (x - D).n1 < 0}.
+//   Path: the point D of the edge line minimising |TX - D| + |D - RX| (the
+//     path-length minimisation of the specular refinement, here in closed
+//     form: unfold the two half-planes through the edge into one plane and
+//     cross the edge with the straight line); kept when D lies strictly inside
+//     the segment and TX and RX are both outside the wedge.
+//   Visibility: from the TX and from the RX, a cast toward D with no hit
+//     closer than rho (the voxel size) before D: the faces meeting at the
+//     edge are crossed only at D itself.
+//   Field (the paper leaves it to its EM library; a reading): the UTD wedge
+//     coefficient of Kouyoumjian and Pathak (1974) with the face reflection
+//     coefficients of Luebbers (1984) weighting the reflection-boundary terms,
+//     for a spherical wave: a = lambda/(4 pi) D / sqrt(s s' (s + s')),
+//     D = K [T1 + T2 + R0 T3 + Rn T4], K = -exp(-j pi/4) / (2 n sqrt(2 pi k) sin b0),
+//     distance parameter L = s s' sin^2 b0 / (s + s').  R0 (Rn) is the
+//     Fresnel coefficient of face 0 (n) at its true incidence cosine
+//     sin b0 sin(phi') (sin b0 sin(n pi - phi)); soft coefficients (TE) for
+//     pol 0, hard (TM) for pol 1, and for the vector model the edge-fixed
+//     basis: a = geo (v_s D_s + v_h D_h), v_s = -(theta^_rx . b^)(theta^_tx . b^'),
+//     v_h = -(theta^_rx . f^)(theta^_tx . f^'), with f^' = -unit(e x s'),
+//     b^' = f^' x s', f^ = unit(e x s), b^ = f^ x s.
+// ---------------------------------------------------------------------------
+struct WedgeFrame {
+  V3 e;          // unit edge direction
+  double len;
+  V3 n0, n1;     // face normals
+  V3 t0;         // in face 0, normal to the edge, pointing away from it
+  double nw;     // exterior angle / pi
+};
+
+WedgeFrame wedge_frame(V3 a, V3 b, V3 n0, V3 n1) {
+  WedgeFrame W;
+  const V3 ev = b - a;
+  W.len = norm(ev);
+  W.e = (1.0 / W.len) * ev;
+  W.n0 = n0;
+  W.n1 = n1;
+  V3 t0 = unit(cross(n0, W.e));
+  if (dot(t0, n1) > 0.0) t0 = (-1.0) * t0;
+  V3 t1 = unit(cross(n1, W.e));
+  if (dot(t1, n0) > 0.0) t1 = (-1.0) * t1;
+  W.t0 = t0;
+  W.nw = 2.0 - std::acos(std::max(-1.0, std::min(1.0, dot(t0, t1)))) / kPi;
+  return W;
+}
+
+// angle of x about the edge through D, from face 0 through the exterior, in [0, 2 pi)
+double wedge_angle(const WedgeFrame& W, V3 D, V3 x) {
+  const V3 v = x - D;
+  const V3 vp = v - dot(v, W.e) * W.e;
+  double phi = std::atan2(dot(vp, W.n0), dot(vp, W.t0));
+  if (phi < 0.0) phi += 2.0 * kPi;
+  return phi;
+}
+
+// UTD transition function F(x) = 2j sqrt(x) exp(jx) int_{sqrt x}^inf exp(-j t^2) dt,
+// x >= 0: the integral as (sqrt(pi)/2) exp(-j pi/4) minus int_0^{sqrt x} by
+// composite 10-point Gauss-Legendre (panels of at most 0.05); for x > 60 the
+// asymptotic series sum_n (-1)^n (2n-1)!! / (2jx)^n.
+cd utd_F(double x) {
+  if (x <= 0.0) return cd(0.0, 0.0);
+  if (x > 60.0) {
+    cd sum(1.0, 0.0), term(1.0, 0.0);
+    for (int n = 1; n < 40; ++n) {
+      term *= -(2.0 * n - 1.0) / (cd(0.0, 2.0 * x));
+      sum += term;
+      if (std::abs(term) < 1e-18) break;
+    }
+    return sum;
+  }
+  static double gx[10], gw[10];
+  static bool init = false;
+  if (!init) {  // Legendre nodes by Newton iteration on P_10
+    for (int i = 0; i < 10; ++i) {
+      double z = std::cos(kPi * (i + 0.75) / 10.5), pp = 0.0;
+      for (int it = 0; it < 100; ++it) {
+        double p1 = 1.0, p2 = 0.0;
+        for (int j = 1; j <= 10; ++j) {
+          const double p3 = p2;
+          p2 = p1;
+          p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+        }
+        pp = 10.0 * (z * p1 - p2) / (z * z - 1.0);
+        const double dz = p1 / pp;
+        z -= dz;
+        if (std::fabs(dz) < 1e-16) break;
+      }
+      gx[i] = z;
+      gw[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+    init = true;
+  }
+  const double u = std::sqrt(x);
+  const int np = std::max(1, (int)std::ceil(u / 0.05));
+  const double h = u / np;
+  cd acc(0.0, 0.0);
+  for (int p = 0; p < np; ++p) {
+    const double c = (p + 0.5) * h;
+    for (int i = 0; i < 10; ++i) {
+      const double t = c + 0.5 * h * gx[i];
+      acc += (0.5 * h * gw[i]) * std::exp(cd(0.0, -t * t));
+    }
+  }
+  const cd tail = 0.5 * std::sqrt(kPi) * std::exp(cd(0.0, -kPi / 4.0)) - acc;
+  return cd(0.0, 2.0) * u * std::exp(cd(0.0, x)) * tail;
+}
+
+struct UtdTerms {
+  cd t12, t3, t4;  // K (T1 + T2), K T3, K T4
+};
+
+UtdTerms utd_terms(double phi_in, double phi_out, double nw, double sinb, double L, double k) {
+  const cd K = -std::exp(cd(0.0, -kPi / 4.0)) / (2.0 * nw * std::sqrt(2.0 * kPi * k) * sinb);
+  auto a_pm = [&](double beta, int sgn) {
+    const double N = std::round((beta + sgn * kPi) / (2.0 * kPi * nw));
+    const double c = std::cos((2.0 * kPi * nw * N - beta) / 2.0);
+    return 2.0 * c * c;
+  };
+  auto cot = [](double v) { return std::cos(v) / std::sin(v); };
+  const double bm = phi_out - phi_in, bp = phi_out + phi_in;
+  const cd T1 = cot((kPi + bm) / (2.0 * nw)) * utd_F(k * L * a_pm(bm, +1));
+  const cd T2 = cot((kPi - bm) / (2.0 * nw)) * utd_F(k * L * a_pm(bm, -1));
+  const cd T3 = cot((kPi - bp) / (2.0 * nw)) * utd_F(k * L * a_pm(bp, -1));
+  const cd T4 = cot((kPi + bp) / (2.0 * nw)) * utd_F(k * L * a_pm(bp, +1));
+  return {K * (T1 + T2), K * T3, K * T4};
+}
+
+// Geometry of the diffracted path TX -> D -> RX of one edge
+struct DiffGeom {
+  bool ok = false;
+  V3 D{0, 0, 0};
+  double tpar = 0;          // position of D along the edge
+  double s_in = 0, s_out = 0, phi_in = 0, phi_out = 0, sinb = 0;
+  double side_tx = 0, side_rx = 0;  // max signed distance to the two face planes
+  double vs = 0, vh = 0;    // vector-model projections
+};
+
+DiffGeom diffraction_geometry(const WedgeFrame& W, V3 a, V3 tx, V3 rx) {
+  DiffGeom G;
+  const V3 wt = tx - a, wr = rx - a;
+  const double at = dot(wt, W.e), ar = dot(wr, W.e);
+  const double bt = norm(wt - at * W.e), br = norm(wr - ar * W.e);
+  if (!(bt + br > 0.0)) return G;
+  G.tpar = (at * br + ar * bt) / (bt + br);
+  G.D = a + G.tpar * W.e;
+  G.side_tx = std::max(dot(tx - G.D, W.n0), dot(tx - G.D, W.n1));
+  G.side_rx = std::max(dot(rx - G.D, W.n0), dot(rx - G.D, W.n1));
+  G.s_in = norm(G.D - tx);
+  G.s_out = norm(rx - G.D);
+  const V3 si = (1.0 / G.s_in) * (G.D - tx), so = (1.0 / G.s_out) * (rx - G.D);
+  const double cb = dot(si, W.e);
+  G.sinb = std::sqrt(std::max(0.0, 1.0 - cb * cb));
+  G.phi_in = wedge_angle(W, G.D, tx);
+  G.phi_out = wedge_angle(W, G.D, rx);
+  const V3 fi = (-1.0) * unit(cross(W.e, si)), bi = cross(fi, si);
+  const V3 fo = unit(cross(W.e, so)), bo = cross(fo, so);
+  const V3 tht = theta_hat(si), thr = theta_hat((-1.0) * so);
+  G.vs = -dot(thr, bo) * dot(tht, bi);
+  G.vh = -dot(thr, fo) * dot(tht, fi);
+  G.ok = G.tpar > 0.0 && G.tpar < W.len && G.side_tx > 0.0 && G.side_rx > 0.0 && G.sinb > 0.0;
+  return G;
+}
+
+// a of a diffracted path and its derivatives w.r.t. the two face
+// permittivities (d_eta[0] face 0, d_eta[1] face n)
+cd diffraction_coefficient(const WedgeFrame& W, const DiffGeom& G, cd eta0, cd eta1, double freq,
+                           int pol, cd* d_eta) {
+  const double k = 2.0 * kPi * freq / kC0, lam = kC0 / freq;
+  const double L = G.s_in * G.s_out * G.sinb * G.sinb / (G.s_in + G.s_out);
+  const UtdTerms T = utd_terms(G.phi_in, G.phi_out, W.nw, G.sinb, L, k);
+  const double geo = lam / (4.0 * kPi * std::sqrt(G.s_in * G.s_out * (G.s_in + G.s_out)));
+  const double c0 = G.sinb * std::sin(G.phi_in), c1 = G.sinb * std::sin(W.nw * kPi - G.phi_out);
+  cd a(0.0, 0.0), g0(0.0, 0.0), g1(0.0, 0.0);
+  for (int t = 0; t < 2; ++t) {
+    const double v = pol == 2 ? (t == 0 ? G.vs : G.vh) : (t == pol ? 1.0 : 0.0);
+    if (v == 0.0) continue;
+    const cd Dc = T.t12 + fresnel(eta0, c0, t) * T.t3 + fresnel(eta1, c1, t) * T.t4;
+    a += v * Dc;
+    g0 += v * dfresnel_deta(eta0, c0, t) * T.t3;
+    g1 += v * dfresnel_deta(eta1, c1, t) * T.t4;
+  }
+  if (d_eta) {
+    d_eta[0] = geo * g0;
+    d_eta[1] = geo * g1;
+  }
+  return geo * a;
+}
+
+WedgeFrame path_wedge(const PathOut& P) { return wedge_frame(P.e0, P.e1, P.en0, P.en1); }
+
+// a of a stored diffracted path for given TX and RX positions (ok = false
+// when the edge gives no path there); its delay in *tau
+cd diffracted_path_coefficient(const PathOut& P, V3 tx, V3 rx, const double* eps,
+                               const double* sig, double freq, int pol, bool* ok, double* tau,
+                               cd* d_eta) {
+  const WedgeFrame W = path_wedge(P);
+  const DiffGeom G = diffraction_geometry(W, P.e0, tx, rx);
+  if (ok) *ok = G.ok;
+  if (tau) *tau = (G.s_in + G.s_out) / kC0;
+  return diffraction_coefficient(W, G, permittivity(eps[P.mats[0]], sig[P.mats[0]], freq),
+                                 permittivity(eps[P.mats[1]], sig[P.mats[1]], freq), freq, pol,
+                                 d_eta);
+}
+
 Jones path_jones(const Sim& sim, const PathOut& P) {
   return make_jones(sim.tx, sim.rx[P.j], P.pts, P.k, P.type == 1, P.nd);
 }
 
 cd path_coefficient(const Sim& sim, const PathOut& P, const double* eps, const double* sig,
                     const double* sca, double freq, int pol) {
+  if (P.type == 2)
+    return diffracted_path_coefficient(P, sim.tx, sim.rx[P.j], eps, sig, freq, pol, nullptr,
+                                       nullptr, nullptr);
   if (pol == 2) {
     cd D[5][2];
     for (int m = 0; m < P.k; ++m) {
@@ -1378,6 +1589,125 @@ void orc_sim_paths(void* s, uint64_t* hi, uint64_t* lo, int32_t* j, int32_t* typ
   }
 }
 
+// Single-bounce diffraction paths of every (edge, RX) pair, appended to the
+// paths after the ray-traced ones (type 2, key hi = j << 56 | 1 << 52 |
+// 1 << 51, lo = edge index, rep = edge index).  Edges as float32 arrays
+// [n][3] (ends a, b; face normals n0, n1) and uint8 face materials.
+// Ambiguous (not certain): D within delta of an edge end, TX or RX within
+// delta of a face plane, or a visibility cast with an ambiguous decision.
+void orc_sim_diffraction(void* s, int64_t n_edges, const float* ea, const float* eb,
+                         const float* n0, const float* n1, const uint8_t* m0, const uint8_t* m1) {
+  Sim* sim = (Sim*)s;
+  const Scene& S = *sim->S;
+  CastCfg cfg;
+  cfg.t_min = sim->p.t_min;
+  cfg.delta = sim->p.delta;
+  const double lam = kC0 / sim->p.freq, dl = sim->p.delta;
+  const int M = (int)sim->rx.size();
+  auto v3 = [](const float* p, int64_t e) {
+    return V3{(double)p[3 * e], (double)p[3 * e + 1], (double)p[3 * e + 2]};
+  };
+  std::vector<PathOut> out((size_t)n_edges * M);
+  std::vector<char> keep((size_t)n_edges * M, 0), amb_q((size_t)n_edges * M, 0);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t q = 0; q < n_edges * M; ++q) {
+    const int64_t e = q / M;
+    const int j = (int)(q % M);
+    const V3 a = v3(ea, e), b = v3(eb, e);
+    const WedgeFrame W = wedge_frame(a, b, v3(n0, e), v3(n1, e));
+    const DiffGeom G = diffraction_geometry(W, a, sim->tx, sim->rx[j]);
+    bool amb = dl > 0 && (std::fabs(G.tpar) < dl || std::fabs(G.tpar - W.len) < dl ||
+                          std::fabs(G.side_tx) < dl || std::fabs(G.side_rx) < dl);
+    amb_q[q] = amb;
+    if (!G.ok) continue;
+    bool vis = true;
+    const V3 ends[2] = {sim->tx, sim->rx[j]};
+    const double dist[2] = {G.s_in, G.s_out};
+    for (int t = 0; t < 2 && vis; ++t) {
+      const double tmax = dist[t] - S.rho;
+      if (!(tmax > cfg.t_min)) continue;
+      const Hit h = cast(S, ends[t], (1.0 / dist[t]) * (G.D - ends[t]), -1, tmax, false, cfg);
+      sim->val_casts++;
+      if (h.amb) amb = true;
+      if (h.hit) vis = false;
+    }
+    amb_q[q] = amb;
+    if (!vis) continue;
+    PathOut& P = out[q];
+    P.key.hi = ((uint64_t)(j & 0xFF) << 56) | (1ull << 52) | (1ull << 51);
+    P.key.lo = (uint64_t)e;
+    P.j = j;
+    P.type = 2;
+    P.k = 1;
+    P.rep = e;
+    P.pts[0] = G.D;
+    P.mats[0] = m0[e];
+    P.mats[1] = m1[e];
+    P.cosv[0] = G.sinb * std::sin(G.phi_in);
+    P.cosv[1] = G.sinb * std::sin(W.nw * kPi - G.phi_out);
+    P.e0 = a;
+    P.e1 = b;
+    P.en0 = v3(n0, e);
+    P.en1 = v3(n1, e);
+    P.length = G.s_in + G.s_out;
+    P.tau = P.length / kC0;
+    P.geo = lam / (4.0 * kPi * std::sqrt(G.s_in * G.s_out * (G.s_in + G.s_out)));
+    P.certain = !amb;
+    keep[q] = 1;
+  }
+  for (size_t q = 0; q < out.size(); ++q) {
+    if (keep[q]) sim->paths.push_back(out[q]);
+    if (amb_q[q]) {  // either outcome possible under float rounding
+      const int64_t e = (int64_t)q / M;
+      const Key K{((uint64_t)((q % M) & 0xFF) << 56) | (1ull << 52) | (1ull << 51), (uint64_t)e};
+      sim->uncertain_cand[K].push_back(e);
+    }
+  }
+}
+
+// UTD transition function F(x) (pins)
+void orc_utd_F(double x, double* re, double* im) {
+  const cd F = utd_F(x);
+  *re = F.real();
+  *im = F.imag();
+}
+
+// a of the diffracted path TX -> edge -> RX on explicit geometry (pins):
+// edge ends a, b, face normals n0, n1, face permittivities eta0, eta1
+// (re, im); returns 0 and leaves a untouched when the edge yields no path
+int orc_diffraction_amplitude(const double* tx, const double* rx, const double* a,
+                              const double* b, const double* n0, const double* n1,
+                              const double* eta0, const double* eta1, double freq, int pol,
+                              double* re, double* im) {
+  auto v3 = [](const double* p) { return V3{p[0], p[1], p[2]}; };
+  const WedgeFrame W = wedge_frame(v3(a), v3(b), v3(n0), v3(n1));
+  const DiffGeom G = diffraction_geometry(W, v3(a), v3(tx), v3(rx));
+  if (!G.ok) return 0;
+  const cd A = diffraction_coefficient(W, G, cd(eta0[0], eta0[1]), cd(eta1[0], eta1[1]), freq,
+                                       pol, nullptr);
+  *re = A.real();
+  *im = A.imag();
+  return 1;
+}
+
+// Geometry of the diffracted path (pins): D, then s', s, phi', phi, n, sin b0
+int orc_diffraction_geometry(const double* tx, const double* rx, const double* a, const double* b,
+                             const double* n0, const double* n1, double* out) {
+  auto v3 = [](const double* p) { return V3{p[0], p[1], p[2]}; };
+  const WedgeFrame W = wedge_frame(v3(a), v3(b), v3(n0), v3(n1));
+  const DiffGeom G = diffraction_geometry(W, v3(a), v3(tx), v3(rx));
+  out[0] = G.D.x;
+  out[1] = G.D.y;
+  out[2] = G.D.z;
+  out[3] = G.s_in;
+  out[4] = G.s_out;
+  out[5] = G.phi_in;
+  out[6] = G.phi_out;
+  out[7] = W.nw;
+  out[8] = G.sinb;
+  return G.ok ? 1 : 0;
+}
+
 // [n_paths][3] surface normal at the scatter point of each diffuse path,
 // facing the incoming ray (0 for specular and LOS paths)
 void orc_sim_path_normals(void* s, double* nd) {
@@ -1406,6 +1736,7 @@ int orc_sim_cand_status(void* s, uint64_t hi, uint64_t lo, int64_t rid) {
   if (it != sim->uncertain_cand.end())
     for (int64_t r : it->second)
       if (r == rid) return 2;
+  if ((hi >> 51) & 1) return 0;  // a diffraction key: no ray candidates
   if (rid < 0 || rid >= (int64_t)sim->ray_pos.size()) return 0;
   int64_t row = sim->ray_pos[rid];
   if (row < 0) return 0;
@@ -1516,6 +1847,37 @@ void orc_sim_path_sens(void* s, const double* eps, const double* sig, const doub
     tau_sens[i] = 0.0;
     if (P.k == 0) continue;
     cd a = path_coefficient(*sim, P, eps, sig, sca, sim->p.freq, sim->p.pol);
+    if (P.type == 2) {
+      // closed-form geometry: sensitivity to float32-sized moves of TX, RX
+      // and the edge ends (-1 across a discontinuity: a shadow boundary)
+      const double h = 4.0 * std::ldexp(1.0, -24);
+      for (int q = 0; q < 12; ++q) {
+        const V3 dir{q % 3 == 0 ? 1.0 : 0.0, q % 3 == 1 ? 1.0 : 0.0, q % 3 == 2 ? 1.0 : 0.0};
+        const double sg = (q / 3) % 2 ? -1.0 : 1.0;
+        V3 tx = sim->tx, rx = sim->rx[P.j];
+        PathOut Q = P;
+        if (q < 6) {
+          tx = tx + (sg * h * std::max(1.0, norm(tx))) * dir;
+        } else {
+          rx = rx + (sg * h * std::max(1.0, norm(rx))) * dir;
+          Q.e0 = Q.e0 + (sg * h * std::max(1.0, norm(Q.e0))) * dir;
+          Q.e1 = Q.e1 - (sg * h * std::max(1.0, norm(Q.e1))) * dir;
+        }
+        bool ok = false;
+        double tb = 0.0;
+        const cd b = diffracted_path_coefficient(Q, tx, rx, eps, sig, sim->p.freq, sim->p.pol,
+                                                 &ok, &tb, nullptr);
+        const double rel = std::abs(b - a) / std::max(std::abs(a), 1e-300);
+        if (!ok || rel > 0.25) {
+          a_sens[i] = -1.0;
+          tau_sens[i] = -1.0;
+          break;
+        }
+        a_sens[i] = std::max(a_sens[i], rel);
+        tau_sens[i] = std::max(tau_sens[i], std::fabs(tb - P.tau) / P.tau);
+      }
+      continue;
+    }
     for (int p = 0; p < 2; ++p) {
       if (!P.shadow_ok[p] || !P.shadow[p]) {
         a_sens[i] = -1.0;
@@ -1545,11 +1907,21 @@ void orc_sim_hit_sens(void* s, double* dq, double* dn) {
 
 namespace {
 
+// material factors of a path: one per interaction, two (the faces) for a
+// diffracted path
+int n_factors(const PathOut& P) { return P.type == 2 ? 2 : P.k; }
+
 // a and, per interaction m, da/deta_m and da/dS_m (the label's S) for the
 // scalar model (pol 0 TE, 1 TM: product rule) and the vector model (pol 2:
 // partials of the Jones product).  dR/dS = -S/R; the diffuse factor is S.
 void path_derivs(const Sim& sim, const PathOut& P, const double* eps, const double* sig,
                  const double* sca, double f, int pol, cd* a_out, cd* da_deta, cd* da_dS) {
+  if (P.type == 2) {  // diffraction: the two faces' reflection coefficients; no S
+    *a_out = diffracted_path_coefficient(P, sim.tx, sim.rx[P.j], eps, sig, f, pol, nullptr,
+                                         nullptr, da_deta);
+    da_dS[0] = da_dS[1] = cd(0.0, 0.0);
+    return;
+  }
   cd G[5][2], dG[5][2];
   double c[5], dc[5];
   for (int m = 0; m < P.k; ++m) {
@@ -1612,7 +1984,7 @@ void orc_sim_path_grads(void* s, const double* eps, const double* sig, const dou
     const PathOut& P = sim->paths[i];
     cd a, de[5], dS[5];
     path_derivs(*sim, P, eps, sig, sca, f, sim->p.pol, &a, de, dS);
-    for (int m = 0; m < P.k; ++m) {
+    for (int m = 0; m < n_factors(P); ++m) {
       const int l = P.mats[m];
       const cd v[3] = {de[m], de[m] * deta_dsig, dS[m]};
       for (int t = 0; t < 3; ++t) {
@@ -1636,7 +2008,7 @@ void orc_sim_backward(void* s, const double* eps, const double* sig, const doubl
     cd a, de[5], dS[5];
     path_derivs(*sim, P, eps, sig, sca, f, sim->p.pol, &a, de, dS);
     const double w = dL_dP[P.j] * 2.0;
-    for (int m = 0; m < P.k; ++m) {
+    for (int m = 0; m < n_factors(P); ++m) {
       const int l = P.mats[m];
       g_eps[l] += w * (std::conj(a) * de[m]).real();
       g_sig[l] += w * (std::conj(a) * de[m] * deta_dsig).real();

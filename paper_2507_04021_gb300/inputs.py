@@ -34,6 +34,9 @@ __all__ = [
     "trajectory",
     "ray_budgets",
     "rng_for",
+    "Edges",
+    "office_edges",
+    "room_edges",
 ]
 
 # Seeds: one per input family.
@@ -43,6 +46,7 @@ SEED_HIDDEN_MATERIALS = 3
 SEED_TRAJECTORY = 4
 SEED_BUDGETS = 5
 SEED_MLP = 6
+SEED_EDGES = 7
 
 
 def rng_for(seed: int, stream: int = 0) -> np.random.Generator:
@@ -283,6 +287,72 @@ def office_scene(n_points: int = 2_000_000, seed: int = SEED_OFFICE, n_boxes: in
         extra={"room": Lr, "boxes": boxes, "r_p": 0.015, "rho": 0.0625,
                "lambda_d": 100.0, "n_rays": 1_000_000, "max_depth": 5},
     )
+
+
+@dataclass
+class Edges:
+    """Edges of the augmented point cloud (Sec. II): segment ends a -> b, the
+    outward normals n0, n1 of the two faces that meet there and their
+    material labels.  The faces bound a convex wedge."""
+    a: np.ndarray   # [n, 3] float32
+    b: np.ndarray   # [n, 3] float32
+    n0: np.ndarray  # [n, 3] float32
+    n1: np.ndarray  # [n, 3] float32
+    m0: np.ndarray  # [n] uint8
+    m1: np.ndarray  # [n] uint8
+
+    def __len__(self) -> int:
+        return int(self.m0.shape[0])
+
+
+def _edges(rows) -> Edges:
+    a, b, n0, n1, m0, m1 = zip(*rows)
+    f = lambda x: np.asarray(x, np.float32).reshape(-1, 3)  # noqa: E731
+    return Edges(f(a), f(b), f(n0), f(n1), np.asarray(m0, np.uint8), np.asarray(m1, np.uint8))
+
+
+def office_edges(boxes: np.ndarray) -> Edges:
+    """The convex edges of the office boxes: 4 vertical edges (floor to top)
+    and the 4 edges of the top face, 8 per box; both faces carry the box's
+    material (4 + b % 4)."""
+    rows = []
+    for b, (x0, x1, y0, y1, h) in enumerate(boxes):
+        m = 4 + b % 4
+        for x, nx in ((x0, -1.0), (x1, 1.0)):
+            for y, ny in ((y0, -1.0), (y1, 1.0)):
+                rows.append(((x, y, 0.0), (x, y, h), (nx, 0, 0), (0, ny, 0), m, m))
+        for y, ny in ((y0, -1.0), (y1, 1.0)):
+            rows.append(((x0, y, h), (x1, y, h), (0, 0, 1.0), (0, ny, 0), m, m))
+        for x, nx in ((x0, -1.0), (x1, 1.0)):
+            rows.append(((x, y0, h), (x, y1, h), (0, 0, 1.0), (nx, 0, 0), m, m))
+    return _edges(rows)
+
+
+def room_edges(n_edges: int = 24, seed: int = SEED_EDGES) -> Edges:
+    """Free-standing wedges inside the 5 x 4 x 3 m room (no points of their
+    own): random centre in [1, 4] x [0.8, 3.2] x [0.5, 2.5], random direction,
+    length U[0.5, 1.5], interior angle U[30, 150] degrees, random face
+    orientation about the edge and face materials in {0, 1}."""
+    rng = rng_for(seed)
+    rows = []
+    for _ in range(n_edges):
+        c = rng.uniform((1.0, 0.8, 0.5), (4.0, 3.2, 2.5))
+        e = rng.normal(size=3)
+        e /= np.linalg.norm(e)
+        L = rng.uniform(0.5, 1.5)
+        u = np.cross(e, rng.normal(size=3))
+        u /= np.linalg.norm(u)
+        w = np.cross(e, u)
+        alpha = np.deg2rad(rng.uniform(30.0, 150.0))
+        t0, t1 = u, np.cos(alpha) * u + np.sin(alpha) * w
+        n0 = np.cross(e, t0)
+        n0 = -n0 if n0 @ t1 > 0 else n0
+        n1 = np.cross(e, t1)
+        n1 = -n1 if n1 @ t0 > 0 else n1
+        m = rng.integers(0, 2, 2)
+        rows.append((c - 0.5 * L * e, c + 0.5 * L * e, n0 / np.linalg.norm(n0),
+                     n1 / np.linalg.norm(n1), m[0], m[1]))
+    return _edges(rows)
 
 
 def trajectory(boxes: np.ndarray, n_steps: int = 256, step: float = 0.2,
