@@ -89,7 +89,10 @@ typedef struct {
                            NRT_LAUNCH_DPS: one ray per DPS toward its reception
                            point (Sec. II-B), ray i = the i-th DPS in voxel Morton
                            order, n_rays taken as the scene's DPS count */
-  int32_t reserved2;
+  int32_t diffraction;  /* 1: single-bounce diffraction on the scene's edges
+                           (Sec. II-B-3, nrt_scene_set_edges): one candidate per
+                           (edge, RX), kept when its point lies inside the edge,
+                           TX and RX lie outside the wedge and both see it */
 } nrt_trace_params;
 
 /* Per-simulation counters (nrt_result_counts). */
@@ -107,18 +110,24 @@ typedef struct {
   int64_t error_flags;       /* device error bits (0 = none) */
   int64_t kernel_launches;   /* library kernels launched by the call */
   int64_t diffuse_casts;     /* of validation_casts: diffuse shadow casts (Sec. II-B-1) */
-  int64_t reserved[3];
+  int64_t diffraction_casts; /* edge visibility casts (Sec. II-B-3) */
+  int64_t reserved[2];
 } nrt_counters;
 
 /* Path view for nrt_paths_read: caller-allocated arrays of n_paths entries
  * (n_paths from nrt_result_counts).  Any pointer may be NULL to skip it.
- * Paths are ordered by (rx, type, interactions, representative ray id). */
+ * Paths are ordered by (rx, type, interactions, representative ray id);
+ * diffracted paths (type 2) come last for their RX, by edge index.
+ * A diffracted path has k = 1, pts[0] = the diffraction point, rep = the
+ * edge index, mats[0..1] = the materials of faces 0 and n, cos_theta[0..1]
+ * = the incidence cosines on those faces; its key is
+ * hi = rx << 56 | 1 << 52 | 1 << 51, lo = edge index. */
 typedef struct {
   uint64_t* key_hi;  /* 128-bit path key, see nrt_trace */
   uint64_t* key_lo;
   uint32_t* rep;     /* representative ray id (0xFFFFFFFF for LOS) */
   int32_t* rx;       /* RX index */
-  int32_t* type;     /* 0 specular / LOS, 1 diffuse last interaction */
+  int32_t* type;     /* 0 specular / LOS, 1 diffuse last interaction, 2 edge diffraction */
   int32_t* k;        /* number of interactions (0 = LOS) */
   float* pts;        /* [n][5][3] interaction points */
   uint8_t* mats;     /* [n][5] material labels of the interactions */
@@ -185,6 +194,22 @@ nrt_status nrt_scene_dps_read(const nrt_scene* scene, int32_t* vox, int32_t* cou
  * S outside [0, 1). */
 nrt_status nrt_set_materials(nrt_scene* scene, const float* eps_r, const float* sigma,
                              const float* scat, int n_labels);
+
+/* Edges of the augmented point cloud (Sec. II, used by the diffraction of
+ * Sec. II-B-3): host arrays of n_edges entries -- segment ends a, b
+ * (float[3] each), the outward unit normals n0, n1 of the two faces meeting
+ * there (float[3] each; the solid is the convex wedge behind both faces) and
+ * their material labels m0, m1.  Copied to the device; replaces any earlier
+ * set (n_edges = 0 clears it).  The diffraction coefficient (the paper leaves
+ * it to its EM library) is the UTD wedge coefficient of Kouyoumjian and
+ * Pathak with Luebbers' face reflection coefficients; see nrt_trace.
+ * Errors: NRT_ERR_ARG for non-finite values, a segment shorter than 1e-6 m,
+ * normals not unit (1e-3) or not normal to the edge (1e-3), faces that do not
+ * form a wedge (|n0 . n1| > 1 - 1e-6), n_edges > 2^24; NRT_ERR_STATE while a
+ * result of this scene is alive (its batch plan may read the edges). */
+nrt_status nrt_scene_set_edges(nrt_scene* scene, int64_t n_edges, const float* a, const float* b,
+                               const float* n0, const float* n1, const uint8_t* m0,
+                               const uint8_t* m1);
 
 /* One simulation for one TX (Sec. II-B):
  *   LOS casts TX -> every RX; Fibonacci launch of n_rays directions (or the
@@ -313,7 +338,8 @@ nrt_status nrt_autotune_batch(nrt_result* result, const int32_t* packets, const 
  * over between calls.  Work is enqueued on the context stream; the call does
  * not synchronise.
  * Errors: NRT_ERR_ARG for NULL pointers, more than 256 labels or a result
- * traced with NRT_POL_VECTOR (scalar models only); NRT_ERR_STATE before
+ * traced with NRT_POL_VECTOR or with diffraction (scalar reflection and
+ * scattering models only); NRT_ERR_STATE before
  * nrt_set_materials; NRT_ERR_CUDA. */
 nrt_status nrt_backward_noalloc(nrt_result* result, const float* dL_dpower, float* grad);
 

@@ -46,6 +46,7 @@ void scene_release(nrt_scene* s) {
   free_dev(s->dps_center);
   free_dev(s->nodes);
   free_dev(s->mat);
+  free_dev(s->edges);
   nrt_ctx* ctx = s->ctx;
   delete s;
   ctx_release(ctx);
@@ -276,6 +277,68 @@ nrt_status nrt_set_materials(nrt_scene* s, const float* eps_r, const float* sigm
   return NRT_OK;
 }
 
+nrt_status nrt_scene_set_edges(nrt_scene* s, int64_t n_edges, const float* a, const float* b,
+                               const float* n0, const float* n1, const uint8_t* m0,
+                               const uint8_t* m1) {
+  if (!s || n_edges < 0) return NRT_ERR_ARG;
+  nrt_ctx* ctx = s->ctx;
+  if (n_edges > 0 && (!a || !b || !n0 || !n1 || !m0 || !m1)) return NRT_ERR_ARG;
+  if (n_edges > ((int64_t)1 << 24)) {
+    ctx->last_error = "at most 2^24 edges";
+    return NRT_ERR_ARG;
+  }
+  if (s->refs > 1) {
+    ctx->last_error = "set the edges before tracing (results of this scene are alive)";
+    return NRT_ERR_STATE;
+  }
+  std::vector<float4> h((size_t)4 * n_edges);
+  for (int64_t e = 0; e < n_edges; ++e) {
+    double v[4][3];
+    const float* src[4] = {a + 3 * e, b + 3 * e, n0 + 3 * e, n1 + 3 * e};
+    for (int q = 0; q < 4; ++q)
+      for (int c = 0; c < 3; ++c) {
+        if (!std::isfinite(src[q][c])) {
+          ctx->last_error = "non-finite edge data";
+          return NRT_ERR_ARG;
+        }
+        v[q][c] = src[q][c];
+      }
+    double ev[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+    const double len = std::sqrt(ev[0] * ev[0] + ev[1] * ev[1] + ev[2] * ev[2]);
+    auto dot = [](const double* x, const double* y) { return x[0] * y[0] + x[1] * y[1] + x[2] * y[2]; };
+    bool ok = len >= 1e-6;
+    for (int q = 2; q < 4 && ok; ++q)
+      ok = std::fabs(std::sqrt(dot(v[q], v[q])) - 1.0) <= 1e-3 &&
+           std::fabs(dot(v[q], ev)) <= 1e-3 * len;
+    if (ok) ok = std::fabs(dot(v[2], v[3])) <= 1.0 - 1e-6;
+    if (!ok) {
+      ctx->last_error = "edge " + std::to_string(e) +
+                        ": short segment, or face normals not unit, not normal to the edge, or "
+                        "not forming a wedge";
+      return NRT_ERR_ARG;
+    }
+    float mb[2];  // material labels as raw bits in .w
+    const int32_t mi[2] = {(int32_t)m0[e], (int32_t)m1[e]};
+    memcpy(mb, mi, sizeof(mb));
+    h[4 * e + 0] = make_float4(src[0][0], src[0][1], src[0][2], mb[0]);
+    h[4 * e + 1] = make_float4(src[1][0], src[1][1], src[1][2], mb[1]);
+    h[4 * e + 2] = make_float4(src[2][0], src[2][1], src[2][2], 0.0f);
+    h[4 * e + 3] = make_float4(src[3][0], src[3][1], src[3][2], 0.0f);
+  }
+  NRT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  free_dev(s->edges);
+  s->edges = nullptr;
+  s->n_edges = 0;
+  if (n_edges > 0) {
+    NRT_CUDA_TRY(ctx, cudaMalloc(&s->edges, h.size() * sizeof(float4)));
+    NRT_CUDA_TRY(ctx, cudaMemcpyAsync(s->edges, h.data(), h.size() * sizeof(float4),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    NRT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  s->n_edges = n_edges;
+  return NRT_OK;
+}
+
 nrt_status nrt_trace(nrt_scene* s, const float* tx, const float* rx, int n_rx,
                      const nrt_trace_params* p_in, const uint32_t* ray_subset, int64_t n_subset,
                      int subset_on_device, nrt_result** out) {
@@ -296,7 +359,7 @@ nrt_status nrt_trace(nrt_scene* s, const float* tx, const float* rx, int n_rx,
   if (p->max_depth < 1 || p->max_depth > kMaxDepth || p->n_rays <= 0 ||
       p->n_rays > (int64_t)0xFFFFFFFE || p->rep_tries < 1 || p->rep_tries > 32 || p->kappa < 0 ||
       !(p->freq > 0.f) || !(p->t_min >= 0.f) || (p->capture != 0 && p->capture != 1) ||
-      p->pol < NRT_POL_TE || p->pol > NRT_POL_VECTOR ||
+      p->pol < NRT_POL_TE || p->pol > NRT_POL_VECTOR || (p->diffraction != 0 && p->diffraction != 1) ||
       (p->capture == NRT_CAPTURE_SPHERE && p->diffuse)) {
     ctx->last_error = "invalid trace parameters";
     return NRT_ERR_ARG;
@@ -464,19 +527,21 @@ nrt_status nrt_paths_read(const nrt_result* r, const nrt_path_view* v) {
     const int k = (p.jtk >> 9) & 7;
     if (v->key_hi) v->key_hi[i] = p.hi;
     if (v->key_lo) v->key_lo[i] = p.lo;
+    const bool dfr = (p.jtk >> 12) & 1;  // diffracted: rep is the edge index
     uint32_t rep = p.rep;
-    if (rep != kNone && r->ray_of_row) rep = rays[rep];
-    if (rep != kNone && r->n_pairs > 0) rep -= pstart[p.jtk & 0xFF];  // ray id within its pair
+    if (!dfr && rep != kNone && r->ray_of_row) rep = rays[rep];
+    if (!dfr && rep != kNone && r->n_pairs > 0) rep -= pstart[p.jtk & 0xFF];  // ray id within its pair
     if (v->rep) v->rep[i] = rep;
     if (v->rx) v->rx[i] = (int32_t)(p.jtk & 0xFF);
-    if (v->type) v->type[i] = (int32_t)((p.jtk >> 8) & 1);
+    if (v->type) v->type[i] = dfr ? 2 : (int32_t)((p.jtk >> 8) & 1);
     if (v->k) v->k[i] = k;
     const uint64_t mats = (uint64_t)p.mats_lo | ((uint64_t)p.mats_hi << 32);
+    const int nm = dfr ? 2 : k;  // material / cosine entries
     for (int m = 0; m < 5; ++m) {
       if (v->pts)
         for (int c = 0; c < 3; ++c) v->pts[15 * i + 3 * m + c] = m < k ? p.pts[3 * m + c] : 0.f;
-      if (v->mats) v->mats[5 * i + m] = m < k ? (uint8_t)((mats >> (8 * m)) & 0xFF) : 0;
-      if (v->cos_theta) v->cos_theta[5 * i + m] = m < k ? p.cosv[m] : 0.f;
+      if (v->mats) v->mats[5 * i + m] = m < nm ? (uint8_t)((mats >> (8 * m)) & 0xFF) : 0;
+      if (v->cos_theta) v->cos_theta[5 * i + m] = m < nm ? p.cosv[m] : 0.f;
     }
     if (v->geo) v->geo[i] = p.geo;
     if (v->tau) v->tau[i] = (float)((double)p.length / 299792458.0);
@@ -584,7 +649,8 @@ nrt_status nrt_trace_batch(nrt_scene* s, const float* tx, const float* rx, const
   }
   if (p->capture != NRT_CAPTURE_VIS || p->max_depth < 1 || p->max_depth > kMaxDepth ||
       p->rep_tries < 1 || p->rep_tries > 32 || p->kappa < 0 || !(p->freq > 0.f) ||
-      p->pol < NRT_POL_TE || p->pol > NRT_POL_VECTOR) {
+      p->pol < NRT_POL_TE || p->pol > NRT_POL_VECTOR ||
+      (p->diffraction != 0 && p->diffraction != 1)) {
     ctx->last_error = "invalid batch trace parameters (visibility capture required)";
     return NRT_ERR_ARG;
   }

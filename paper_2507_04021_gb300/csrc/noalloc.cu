@@ -109,8 +109,9 @@ extern "C" nrt_status nrt_backward_noalloc(nrt_result* r, const float* dL_dpower
     ctx->last_error = "backward needs materials (nrt_set_materials)";
     return NRT_ERR_STATE;
   }
-  if (r->p.pol == NRT_POL_VECTOR) {
-    ctx->last_error = "nrt_backward_noalloc supports the scalar polarisation models only";
+  if (r->p.pol == NRT_POL_VECTOR || r->p.diffraction) {
+    ctx->last_error =
+        "nrt_backward_noalloc supports the scalar polarisation models without diffraction only";
     return NRT_ERR_ARG;
   }
   const int L = sc->n_labels;

@@ -45,6 +45,9 @@ struct nrt_scene {
   int n_labels = 0;
   float* mat = nullptr;  // device [3][256]: eps_r, sigma, S
   bool have_materials = false;
+  // edges (diffraction): 4 float4 per edge -- (a, m0 bits), (b, m1 bits), (n0, 0), (n1, 0)
+  float4* edges = nullptr;
+  int64_t n_edges = 0;
 };
 
 struct nrt_result {
@@ -123,6 +126,7 @@ enum Ctr : int {
   kCtrPending,
   kCtrLeaders,
   kCtrCompact,
+  kCtrDfrCasts,  // edge visibility casts (diffraction)
   kCtrCount
 };
 

@@ -246,6 +246,196 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
   paths[p] = R;
 }
 
+// ---------------------------------------------------------------- diffraction
+// Single-bounce edge diffraction (Sec. II-B-3): one thread per (edge, RX)
+// (batch: per (edge, pair)).  The diffraction point is the exact minimiser
+// of |TX - D| + |D - RX| on the edge line (unfold the half-planes through the
+// edge into one plane; the straight line crosses the edge at
+// t = (a_t b_r + a_r b_t) / (b_t + b_r), a the position along the edge, b the
+// distance from it), kept strictly inside the segment with TX and RX
+// outside the wedge; each end then casts toward D and must not hit anything
+// closer than rho before it.  The geometry and the UTD wedge terms
+// (Kouyoumjian-Pathak, Luebbers' weighting of the reflection-boundary terms)
+// are evaluated in FP64: they are material independent, so they are stored
+// once per path and the field kernel only applies the face reflection
+// coefficients.  Record layout of a diffracted path: pts[0..2] = D,
+// pts[3..8] = K (T1 + T2), K T3, K T4 (complex), pts[9..10] = the vector-model
+// projections (v_s, v_h), cosv[0..1] = the face incidence cosines,
+// mats = face 0 | face n << 8, rep = the edge index.
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 zsc(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 zexpj(double t) {
+  double sn, cs;
+  sincos(t, &sn, &cs);
+  return make_double2(cs, sn);
+}
+
+// F(x) = j sqrt(pi x) e^{j(x - pi/4)} erfc(e^{j pi/4} sqrt x) (the UTD transition
+// function): the power series of erf for x <= 20, the asymptotic series
+// sum_n t_n, t_n = t_{n-1} j (2n - 1) / (2x), beyond (both ~1e-8 relative at
+// the switch)
+__device__ double2 utd_transition(double x) {
+  if (!(x > 0.0)) return make_double2(0.0, 0.0);
+  if (x > 20.0) {
+    double2 sum = make_double2(1.0, 0.0), t = sum;
+    for (int n = 1; n < 64; ++n) {
+      const double2 nt = zmul(t, make_double2(0.0, (2.0 * n - 1.0) / (2.0 * x)));
+      if (hypot(nt.x, nt.y) > hypot(t.x, t.y)) break;
+      t = nt;
+      sum = zadd(sum, t);
+      if (hypot(t.x, t.y) < 1e-17) break;
+    }
+    return sum;
+  }
+  // erf(z) = 2/sqrt(pi) z sum_n (-z^2)^n / (n! (2n + 1)), z^2 = j x
+  double2 c = make_double2(1.0, 0.0), acc = c;
+  for (int n = 1; n < 200; ++n) {
+    c = zsc(1.0 / n, zmul(c, make_double2(0.0, -x)));
+    const double2 term = zsc(1.0 / (2.0 * n + 1.0), c);
+    acc = zadd(acc, term);
+    if (n > x && hypot(term.x, term.y) < 1e-17 * hypot(acc.x, acc.y)) break;
+  }
+  const double u = sqrt(x);
+  const double2 z = zsc(u, make_double2(0.70710678118654752440, 0.70710678118654752440));
+  const double2 erf_z = zsc(1.12837916709551257390, zmul(z, acc));  // 2 / sqrt(pi)
+  const double2 erfc_z = make_double2(1.0 - erf_z.x, -erf_z.y);
+  const double2 pre = zmul(make_double2(0.0, sqrt(3.14159265358979323846 * x)),
+                           zexpj(x - 0.25 * 3.14159265358979323846));
+  return zmul(pre, erfc_z);
+}
+
+struct D3 {
+  double x, y, z;
+};
+__device__ __forceinline__ D3 d3(float3 v) { return {v.x, v.y, v.z}; }
+__device__ __forceinline__ D3 d3(float4 v) { return {v.x, v.y, v.z}; }
+__device__ __forceinline__ D3 dsub(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ D3 dadd(D3 a, D3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ D3 dmul(double s, D3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double ddot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ double dlen(D3 a) { return sqrt(ddot(a, a)); }
+__device__ __forceinline__ D3 dunit(D3 a) { return dmul(1.0 / dlen(a), a); }
+__device__ __forceinline__ D3 dcross(D3 a, D3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ D3 dtheta(D3 d) {  // theta^ about +z (x^ on the axis)
+  const double h = sqrt(d.x * d.x + d.y * d.y);
+  if (h < 1e-12) return {1.0, 0.0, 0.0};
+  return {d.z * d.x / h, d.z * d.y / h, -h};
+}
+
+__global__ void __launch_bounds__(kTraceThreads)
+    diffraction_kernel(SceneView S, SimConst C, const float4* __restrict__ rx,
+                       const float4* __restrict__ edges, int64_t n_edges, PathRec* __restrict__ paths,
+                       unsigned long long* ctr, int64_t path_cap) {
+  NRT_STACK_DECL
+  const double kPiD = 3.14159265358979323846;
+  const int nj = C.batch ? C.n_pairs : C.n_rx;
+  unsigned long long casts = 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_edges * nj;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = q / nj;
+    const int j = (int)(q - e * nj);
+    const float4 ea = __ldg(edges + 4 * e), eb = __ldg(edges + 4 * e + 1);
+    const D3 A = d3(ea), n0 = d3(__ldg(edges + 4 * e + 2)), n1 = d3(__ldg(edges + 4 * e + 3));
+    const float3 txf = tx_of(C, j), rxf = xyz(__ldg(rx + (C.batch ? 0 : j)));
+    const D3 T = d3(txf), R = d3(rxf);
+    const D3 ev = dsub(d3(eb), A);
+    const double len = dlen(ev);
+    const D3 eu = dmul(1.0 / len, ev);
+    const double at = ddot(dsub(T, A), eu), ar = ddot(dsub(R, A), eu);
+    const double bt = dlen(dsub(dsub(T, A), dmul(at, eu))), br = dlen(dsub(dsub(R, A), dmul(ar, eu)));
+    if (!(bt + br > 0.0)) continue;
+    const double tp = (at * br + ar * bt) / (bt + br);
+    if (!(tp > 0.0 && tp < len)) continue;
+    const D3 D = dadd(A, dmul(tp, eu));
+    if (!(fmax(ddot(dsub(T, D), n0), ddot(dsub(T, D), n1)) > 0.0)) continue;
+    if (!(fmax(ddot(dsub(R, D), n0), ddot(dsub(R, D), n1)) > 0.0)) continue;
+    const double s_in = dlen(dsub(D, T)), s_out = dlen(dsub(R, D));
+    const D3 si = dmul(1.0 / s_in, dsub(D, T)), so = dmul(1.0 / s_out, dsub(R, D));
+    const double cb = ddot(si, eu);
+    const double sinb = sqrt(fmax(0.0, 1.0 - cb * cb));
+    if (!(sinb > 0.0)) continue;
+    // visibility of the edge point from the TX, then from the RX
+    bool vis = true;
+    const float3 Df = make_float3((float)D.x, (float)D.y, (float)D.z);
+    const float3 ends[2] = {txf, rxf};
+    const double dist[2] = {s_in, s_out};
+    for (int t = 0; t < 2 && vis; ++t) {
+      const float tmax = (float)(dist[t] - (double)S.rho);
+      if (!(tmax > C.t_min)) continue;
+      const Hit h = cast_ray<true>(S, ends[t], unit3(Df - ends[t]), -1, C.t_min, tmax, false, my_stk,
+                                   my_tstk, kTraceThreads, err);
+      ++casts;
+      vis = h.idx < 0;
+    }
+    if (!vis) continue;
+    // wedge frame: t0 in face 0 pointing away from the edge; exterior angle n pi
+    D3 t0 = dunit(dcross(n0, eu));
+    if (ddot(t0, n1) > 0.0) t0 = dmul(-1.0, t0);
+    D3 t1 = dunit(dcross(n1, eu));
+    if (ddot(t1, n0) > 0.0) t1 = dmul(-1.0, t1);
+    const double nw = 2.0 - acos(fmin(1.0, fmax(-1.0, ddot(t0, t1)))) / kPiD;
+    auto angle = [&](D3 x) {
+      const D3 v = dsub(x, D);
+      const D3 vp = dsub(v, dmul(ddot(v, eu), eu));
+      double ph = atan2(ddot(vp, n0), ddot(vp, t0));
+      return ph < 0.0 ? ph + 2.0 * kPiD : ph;
+    };
+    const double phi_in = angle(T), phi_out = angle(R);
+    const double k = 2.0 * kPiD * (double)C.freq / 299792458.0;
+    const double L = s_in * s_out * sinb * sinb / (s_in + s_out);
+    auto term = [&](double beta, int sgn) {  // cot((pi + sgn beta) / 2n) F(kL a^{sgn}(beta))
+      const double N = rint((beta + sgn * kPiD) / (2.0 * kPiD * nw));
+      const double c = cos((2.0 * kPiD * nw * N - beta) / 2.0);
+      const double v = (kPiD + sgn * beta) / (2.0 * nw);
+      return zsc(cos(v) / sin(v), utd_transition(k * L * 2.0 * c * c));
+    };
+    const double bm = phi_out - phi_in, bp = phi_out + phi_in;
+    const double2 Kc = zsc(-1.0 / (2.0 * nw * sqrt(2.0 * kPiD * k) * sinb),
+                           zexpj(-0.25 * kPiD));
+    const double2 t12 = zmul(Kc, zadd(term(bm, +1), term(bm, -1)));
+    const double2 t3 = zmul(Kc, term(bp, -1));
+    const double2 t4 = zmul(Kc, term(bp, +1));
+    // vector model: edge-fixed bases of the incident and diffracted rays
+    const D3 fi = dmul(-1.0, dunit(dcross(eu, si))), bi = dcross(fi, si);
+    const D3 fo = dunit(dcross(eu, so)), bo = dcross(fo, so);
+    const D3 tht = dtheta(si), thr = dtheta(dmul(-1.0, so));
+    const unsigned long long p = warp_inc(ctr + kCtrPaths);
+    if ((int64_t)p >= path_cap) {
+      atomicOr(err, kErrPathFull);
+      continue;
+    }
+    PathRec P;
+    memset(&P, 0, sizeof(P));
+    P.hi = ((uint64_t)(j & 0xFF) << 56) | (1ull << 52) | (1ull << 51);
+    P.lo = (uint64_t)e;
+    P.rep = (uint32_t)e;
+    P.jtk = (uint32_t)j | (1u << 9) | (1u << 12);
+    P.length = (float)(s_in + s_out);
+    P.geo = (float)(((double)C.lambda) / (4.0 * kPiD * sqrt(s_in * s_out * (s_in + s_out))));
+    P.cosv[0] = (float)(sinb * sin(phi_in));
+    P.cosv[1] = (float)(sinb * sin(nw * kPiD - phi_out));
+    P.mats_lo = (uint32_t)(__float_as_int(ea.w) & 0xFF) | ((uint32_t)(__float_as_int(eb.w) & 0xFF) << 8);
+    P.pts[0] = Df.x;
+    P.pts[1] = Df.y;
+    P.pts[2] = Df.z;
+    P.pts[3] = (float)t12.x;
+    P.pts[4] = (float)t12.y;
+    P.pts[5] = (float)t3.x;
+    P.pts[6] = (float)t3.y;
+    P.pts[7] = (float)t4.x;
+    P.pts[8] = (float)t4.y;
+    P.pts[9] = (float)(-ddot(thr, bo) * ddot(tht, bi));
+    P.pts[10] = (float)(-ddot(thr, fo) * ddot(tht, fi));
+    paths[p] = P;
+  }
+  count_add(ctr + kCtrDfrCasts, casts);
+}
+
 // ---------------------------------------------------------------- trace
 // One ray per thread; every interaction continues as a specular reflection
 // (Sec. II-B: the ray count stays constant).  The next cast skips the DPS
@@ -913,7 +1103,8 @@ __global__ void path_sortkey_kernel(const PathRec* __restrict__ p,
       continue;
     }
     const uint32_t jtk = p[i].jtk;
-    const uint64_t j = jtk & 0xFF, ty = (jtk >> 8) & 1, k = (jtk >> 9) & 7;
+    const bool dfr = (jtk >> 12) & 1;  // diffracted paths last: class (1, 6)
+    const uint64_t j = jtk & 0xFF, ty = dfr ? 1 : (jtk >> 8) & 1, k = dfr ? 6 : (jtk >> 9) & 7;
     key[i] = (j << (row_bits + 4)) | (ty << (row_bits + 3)) | (k << row_bits) |
              ((uint64_t)p[i].rep & ((1ull << row_bits) - 1ull));
   }
@@ -1100,6 +1291,36 @@ __device__ __forceinline__ void interaction_factors(const PathRec& p, int m, int
   }
 }
 
+// Diffracted path: D = K(T1 + T2) + R0 K T3 + Rn K T4 with the stored
+// material-independent terms (soft / TE coefficients for pol 0, hard / TM
+// for pol 1, v_s D_s + v_h D_h for the vector model); a = geo D.  dD
+// (optional): dD/deta of face 0 and face n.
+__device__ __forceinline__ float2 diffraction_factor(const PathRec& p, const float* __restrict__ mat,
+                                                     float freq, int pol, float2* dD) {
+  const float2 t12 = make_float2(p.pts[3], p.pts[4]), t3 = make_float2(p.pts[5], p.pts[6]);
+  const float2 t4 = make_float2(p.pts[7], p.pts[8]);
+  const int l0 = path_mat(p, 0), l1 = path_mat(p, 1);
+  const float2 eta0 = permittivity(mat[l0], mat[256 + l0], freq);
+  const float2 eta1 = permittivity(mat[l1], mat[256 + l1], freq);
+  float2 Dsum = make_float2(0.f, 0.f), g0 = Dsum, g1 = Dsum;
+  for (int t = 0; t < 2; ++t) {
+    const float v = pol == 2 ? p.pts[9 + t] : (t == pol ? 1.0f : 0.0f);
+    if (v == 0.0f) continue;
+    const float2 Dt = cadd(t12, cadd(cmul(fresnel(eta0, p.cosv[0], t), t3),
+                                     cmul(fresnel(eta1, p.cosv[1], t), t4)));
+    Dsum = cadd(Dsum, cscale(v, Dt));
+    if (dD) {
+      g0 = cadd(g0, cscale(v, cmul(dfresnel(eta0, p.cosv[0], t), t3)));
+      g1 = cadd(g1, cscale(v, cmul(dfresnel(eta1, p.cosv[1], t), t4)));
+    }
+  }
+  if (dD) {
+    dD[0] = g0;
+    dD[1] = g1;
+  }
+  return Dsum;
+}
+
 // a = geo * prod_m f_m Gamma_m(theta_m): f = sqrt(1 - S^2) for a specular
 // reflection (effective roughness), f = S for the diffuse last interaction;
 // the vector model replaces the product by the 2x2 chain above.
@@ -1113,7 +1334,9 @@ __global__ void field_kernel(const PathRec* __restrict__ P, const unsigned long 
     const int k = (p.jtk >> 9) & 7;
     const int diffuse = (p.jtk >> 8) & 1;
     float2 a = make_float2(p.geo, 0.0f);
-    if (pol == 2) {
+    if ((p.jtk >> 12) & 1) {
+      a = cscale(p.geo, diffraction_factor(p, mat, freq, pol, nullptr));
+    } else if (pol == 2) {
       if (k > 0) {
         const int j = p.jtk & 0xFF;
         JonesGeom J;
@@ -1221,7 +1444,16 @@ __global__ void __launch_bounds__(kAdjThreads)
     // da/deta_m and da/dS_m (before the loss weight)
     float2 dae[kMaxDepth], das[kMaxDepth];
     float2 a = make_float2(p.geo, 0.0f);
-    if (pol == 2) {
+    if ((p.jtk >> 12) & 1) {  // diffracted: the two faces' coefficients, no S
+      float2 dD[2];
+      a = cscale(p.geo, diffraction_factor(p, mat, freq, pol, dD));
+      k = 2;
+      labs[0] = path_mat(p, 0);
+      labs[1] = path_mat(p, 1);
+      dae[0] = cscale(p.geo, dD[0]);
+      dae[1] = cscale(p.geo, dD[1]);
+      das[0] = das[1] = make_float2(0.f, 0.f);
+    } else if (pol == 2) {
       if (k > 0) {
         JonesGeom J;
         jones_geom(p, k, diffuse, frame_tx(F, j), frame_rx(F, j), J);
@@ -1317,6 +1549,12 @@ __global__ void adjoint_reduce_kernel(const double* __restrict__ partial, int64_
   double s = 0.0;
   for (int64_t b = 0; b < n_blocks; ++b) s += partial[b * 3 * n_labels + t];
   out[t] = (float)s;
+}
+
+// path records reserved for diffracted paths: one per (edge, RX or pair)
+int64_t diffraction_slots(const nrt_result* r) {
+  if (!r->p.diffraction) return 0;
+  return r->scene->n_edges * (r->n_pairs > 0 ? r->n_pairs : r->n_rx_phys);
 }
 
 PathFrame path_frame(const nrt_result* r) {
@@ -1679,6 +1917,10 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   const int nj = C.batch ? C.n_pairs : r->n_rx_phys;
   los_kernel<<<(nj + kTraceThreads - 1) / kTraceThreads, kTraceThreads, 0, st>>>(
       S, C, r->rx, W.raw, ctr, c.paths); count_launch();
+  if (r->p.diffraction && sc->n_edges > 0) {
+    diffraction_kernel<<<blocks_for(sc->n_edges * nj, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
+        S, C, r->rx, sc->edges, sc->n_edges, W.raw, ctr, c.paths); count_launch();
+  }
   if (r->ev[4]) TRY(cudaEventRecord(r->ev[4], st));
   ValArgs V{};
   V.T = W.T;
@@ -1723,14 +1965,18 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
                                                                     ctr); count_launch();
   }
 
-  // deterministic order of the paths (padding sorts last), ranges, field
+  // deterministic order of the paths (padding sorts last), ranges, field;
+  // the representative field also holds edge indices of diffracted paths
+  int path_bits = row_bits;
+  if (r->p.diffraction)
+    while ((1ll << path_bits) < sc->n_edges) ++path_bits;
   path_sortkey_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>(W.raw, ctr + kCtrPaths, c.paths,
-                                                                   row_bits, W.psk, W.psi); count_launch();
-  radix_sort_pairs(W.psk, W.psi, W.ptk, W.pti, c.paths, row_bits + 12, st);
+                                                                   path_bits, W.psk, W.psi); count_launch();
+  radix_sort_pairs(W.psk, W.psi, W.ptk, W.pti, c.paths, path_bits + 12, st);
   path_gather_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>(W.raw, W.psi, ctr + kCtrPaths,
                                                                   c.paths, (PathRec*)r->paths); count_launch();
   rx_range_kernel<<<(r->n_rx + 63) / 64, 64, 0, st>>>(W.psk, ctr + kCtrPaths, c.paths, r->n_rx,
-                                                      row_bits + 4, r->rx_start_d, r->rx_count_d); count_launch();
+                                                      path_bits + 4, r->rx_start_d, r->rx_count_d); count_launch();
   if (sc->have_materials) {
     field_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>((const PathRec*)r->paths, ctr + kCtrPaths,
                                                               c.paths, sc->mat, r->p.freq, r->p.pol,
@@ -1782,6 +2028,7 @@ nrt_status finish_result(nrt_result* r) {
   c.error_flags = (int64_t)(hc[kCtrErr] & 0xFFFFFFFFull);
   c.kernel_launches = launch_counter();
   c.diffuse_casts = (int64_t)hc[kCtrDiffCasts];
+  c.diffraction_casts = (int64_t)hc[kCtrDfrCasts];
   if (c.error_flags & (kErrHashFull | kErrCandFull | kErrPathFull | kErrKeyMismatch)) {
     ctx->last_error = "device buffer overflow or key fingerprint collision (flags " +
                       std::to_string(c.error_flags) + ")";
@@ -1890,7 +2137,7 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
     return NRT_ERR_ARG;
   }
   c.keys = std::min<int64_t>(c.keys, c.table);
-  c.paths = c.keys + (C.batch ? r->n_pairs : r->n_rx_phys);
+  c.paths = c.keys + (C.batch ? r->n_pairs : r->n_rx_phys) + diffraction_slots(r);
   rc = alloc_result(r, c, true);
   if (rc == NRT_OK) rc = alloc_work(ctx, W, c, n, st);
   TRY(dbg_set_caps(c.table, c.keys, c.cand, c.paths, n, r->n_rx, st));
@@ -1943,7 +2190,7 @@ nrt_status batch_graph_build(nrt_result* r) {
   c.keys = std::max<int64_t>(m.keys + m.keys / 4 + 1024, 1);
   c.table = 1 << 12;
   while (c.table < 2 * c.keys) c.table <<= 1;
-  c.paths = c.keys + r->n_pairs;
+  c.paths = c.keys + r->n_pairs + diffraction_slots(r);
   // path buffers sized by the caps (the calibration run's paths are dropped)
   nrt_status rc = alloc_result(r, c, true);
   if (rc != NRT_OK) return rc;

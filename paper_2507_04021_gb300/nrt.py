@@ -45,15 +45,15 @@ class TraceParams(C.Structure):
         ("record_hits", C.c_int32), ("ray_labels", C.c_int32), ("n_rays", C.c_int64),
         ("r_rx", C.c_float), ("t_min", C.c_float), ("t_a_deg", C.c_float), ("t_d", C.c_float),
         ("freq", C.c_float), ("keep_keys", C.c_int32), ("key_capacity", C.c_int64),
-        ("cand_capacity", C.c_int64), ("launch", C.c_int32), ("reserved2", C.c_int32),
+        ("cand_capacity", C.c_int64), ("launch", C.c_int32), ("diffraction", C.c_int32),
     ]
 
 
 class Counters(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "rays", "segments", "vis_casts", "los_casts", "validation_casts", "candidates", "keys",
-        "paths", "n_dps", "hash_probes_max", "error_flags", "kernel_launches", "diffuse_casts")] + [
-            ("reserved", C.c_int64 * 3)]
+        "paths", "n_dps", "hash_probes_max", "error_flags", "kernel_launches", "diffuse_casts",
+        "diffraction_casts")] + [("reserved", C.c_int64 * 2)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
@@ -101,6 +101,7 @@ def lib():
         L.nrt_scene_info.argtypes = [_P, _P, _P, _P]
         L.nrt_scene_dps_read.argtypes = [_P, _P, _P, _P]
         L.nrt_set_materials.argtypes = [_P, _P, _P, _P, C.c_int]
+        L.nrt_scene_set_edges.argtypes = [_P, C.c_int64, _P, _P, _P, _P, _P, _P]
         L.nrt_trace.argtypes = [_P, _P, _P, C.c_int, C.POINTER(TraceParams), _P, C.c_int64,
                                 C.c_int, C.POINTER(_P)]
         L.nrt_result_free.argtypes = [_P]
@@ -246,6 +247,19 @@ class Scene:
         self.ctx._check(lib().nrt_set_materials(self._h, _np_ptr(e), _np_ptr(s), _np_ptr(c),
                                                 int(e.shape[0])))
         self.n_labels = int(e.shape[0])
+
+    def set_edges(self, edges):
+        """Edges for the diffraction of Sec. II-B-3 (an object with arrays a, b,
+        n0, n1 [n, 3] and m0, m1 [n], e.g. inputs.Edges); None clears them."""
+        if edges is None:
+            self.ctx._check(lib().nrt_scene_set_edges(self._h, 0, None, None, None, None, None,
+                                                      None))
+            return
+        f = lambda x: np.ascontiguousarray(x, np.float32).reshape(-1, 3)  # noqa: E731
+        u = lambda x: np.ascontiguousarray(x, np.uint8).reshape(-1)  # noqa: E731
+        arrs = (f(edges.a), f(edges.b), f(edges.n0), f(edges.n1), u(edges.m0), u(edges.m1))
+        self.ctx._check(lib().nrt_scene_set_edges(self._h, int(arrs[4].shape[0]),
+                                                  *[_np_ptr(x) for x in arrs]))
 
     def trace(self, tx, rx, params: TraceParams, ray_subset=None) -> "Result":
         return Result(self, tx, rx, params, ray_subset)
