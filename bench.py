@@ -300,6 +300,40 @@ def launch_bench(scene, o, tx, stream):
     return out
 
 
+def diffraction_bench(ctx, o, tx, stream, rays):
+    """Single-bounce edge diffraction (Sec. II-B-3) on the 320 convex box edges
+    of the office: the full simulation (1M rays, 16 RX, 5 interactions, VIS +
+    diffuse) with and without diffraction, device-timed (median of 3), and the
+    diffracted paths and edge visibility casts it adds."""
+    import torch
+    from paper_2507_04021_gb300 import inputs, nrt
+
+    sc = nrt.Scene(ctx, o.pos, o.nrm, o.surf, o.mat, rho=0.0625, r_p=0.015, lambda_d=100.0)
+    sc.set_materials(o.eps_r, o.sigma, o.scat)
+    edges = inputs.office_edges(o.extra["boxes"])
+    sc.set_edges(edges)
+    out = {"edges": len(edges)}
+    for name, flag in (("off", 0), ("on", 1)):
+        p = nrt.default_trace_params(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=rays,
+                                     rep_tries=8, diffraction=flag)
+        sc.trace(tx, o.rx, p).close()  # warm-up
+        ms = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = sc.trace(tx, o.rx, p)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            _, c = r.counts()
+            r.close()
+        out[name] = {"ms": float(np.median(ms)), "paths": c["paths"],
+                     "diffraction_casts": c["diffraction_casts"]}
+    out["diffracted_paths"] = out["on"]["paths"] - out["off"]["paths"]
+    return out
+
+
 def proposal_bench(scene, o):
     """Learned launch proposal (RX-sphere capture, 16 RX, 5 specular
     interactions): 5M labelled rays from 250 trajectory positions, training
@@ -497,6 +531,7 @@ def ours(args):
                    "note": "FP64 sums; includes the host copy of H (and of the target)"}
     if rank == 0:
         line["launch_comparison"] = launch_bench(scene, o, tx, stream)
+        line["diffraction"] = diffraction_bench(ctx, o, tx, stream, args.rays)
     if args.proposal and rank == 0:
         line["proposal"] = proposal_bench(scene, o)
     if args.batch_pairs > 0:
