@@ -93,6 +93,9 @@ def _declare(L):
     L.orc_sim_n_paths.restype = C.c_int64
     L.orc_sim_n_paths.argtypes = [_P]
     L.orc_sim_paths.argtypes = [_P] + [_P] * 13
+    L.orc_cast_sdf.restype = C.c_int
+    L.orc_cast_sdf.argtypes = [_P, _P, _P, C.c_double, C.c_double, C.c_double, C.c_double, _P,
+                               C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.orc_sim_diffraction.restype = None
     L.orc_sim_diffraction.argtypes = [_P, C.c_int64, _P, _P, _P, _P, _P, _P]
     L.orc_utd_F.restype = None
@@ -198,6 +201,18 @@ class OracleScene:
         res = {"hit": bool(hit), "t": out[0], "q": out[1:4].copy(), "n": out[4:7].copy(),
                "cos_in": out[7], "idx": int(idx[0]), "dps": int(dps[0]), "amb": bool(amb[0])}
         return res
+
+    def cast_sdf(self, o, d, sigma, t_min=1e-3, t_max=np.inf, delta=0.0):
+        """Closest hit under the SDF model of Eq. 2 (the ablation); dict or None."""
+        o = np.ascontiguousarray(o, np.float64)
+        d = np.ascontiguousarray(d, np.float64)
+        out = np.zeros(7, np.float64)
+        dps, lab, amb = C.c_int32(), C.c_int32(), C.c_int32()
+        hit = lib().orc_cast_sdf(self._h, _ptr(o), _ptr(d), float(t_min), float(t_max),
+                                 float(sigma), float(delta), _ptr(out), C.byref(dps), C.byref(lab),
+                                 C.byref(amb))
+        return {"hit": bool(hit), "t": out[0], "q": out[1:4].copy(), "n": out[4:7].copy(),
+                "dps": int(dps.value), "labels": int(lab.value), "amb": bool(amb.value)}
 
     def vis_disc_counts(self, rx, j, dps, t_min=1e-3):
         rx = np.ascontiguousarray(rx, np.float64)
