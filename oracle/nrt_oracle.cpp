@@ -1461,8 +1461,10 @@ int orc_cast(void* s, const double* o, const double* d, int32_t skip_dps, double
 // ray crosses the bounding box of its points grown by 2 sigma (clipped to
 // (t_min, t_max)): samples t_k = t_in + k sigma / 2; the first k with both
 // samples defined and f(t_k) > 0 >= f(t_k+1) brackets the surface (outside
-// to inside), 20 bisection steps refine it and the hit is the midpoint.  The
-// hit is the smallest t over all DPS (ties: smaller DPS index); its normal
+// to inside), 20 bisection steps refine it and the hit is the midpoint.  Each
+// DPS is marched over its whole interval (the grid and the bracket do not
+// depend on other DPS).  The hit is the smallest t over all DPS (ties:
+// smaller DPS index); its normal
 // the normalised sum_i w_i n_i, turned to face the ray; its label the label of
 // D's point nearest to the hit.  Ambiguous: a bracketing sample with |f| <
 // delta, a weight sum within 1e-4 (relative) of the threshold, or two DPS hits
@@ -1500,7 +1502,7 @@ int orc_cast_sdf(void* s, const double* o_in, const double* d_in, double t_min, 
       }
     }
     const double oc[3] = {o.x, o.y, o.z}, dc[3] = {d.x, d.y, d.z};
-    double t0 = t_min, t1 = std::min(t_max, best + delta);
+    double t0 = t_min, t1 = t_max;
     for (int a = 0; a < 3; ++a) {
       const double l = lo[a] - 2.0 * sigma, u = hi[a] + 2.0 * sigma;
       if (dc[a] == 0.0) {
@@ -1517,7 +1519,8 @@ int orc_cast_sdf(void* s, const double* o_in, const double* d_in, double t_min, 
     eval(pts, o + t0 * d, &fa, &Wa);
     for (int k = 0;; ++k) {
       const double ta = t0 + k * h, tb = t0 + (k + 1) * h;
-      if (tb > t1) break;
+      // a bracket starting beyond the best hit (plus the tie band) cannot win
+      if (tb > t1 || ta > best + delta) break;
       double fb, Wb;
       eval(pts, o + tb * d, &fb, &Wb);
       if (std::fabs(Wa - wmin) < 1e-4 * wmin || std::fabs(Wb - wmin) < 1e-4 * wmin) amb = true;
