@@ -211,6 +211,38 @@ nrt_status nrt_scene_set_edges(nrt_scene* scene, int64_t n_edges, const float* a
                                const float* n0, const float* n1, const uint8_t* m0,
                                const uint8_t* m1);
 
+/* Intersection models for nrt_cast. */
+enum { NRT_ISECT_DISC = 0, NRT_ISECT_SDF = 1 };
+
+typedef struct {
+  int32_t model;  /* NRT_ISECT_DISC: the paper's model (Sec. II-C) -- ray/disc
+                     intersections of the DPS of the closest disc, the Eq. 3
+                     point with the Eq. 4 weights, the weighted normal;
+                     NRT_ISECT_SDF: the SDF of the prior work (Eq. 2), kept for
+                     the ablation: per DPS the Eq. 2-weighted mean of the points'
+                     tangent-plane distances (defined where the weight sum is
+                     >= e^-2), marched in steps of sigma/2 over the ray's crossing
+                     of the points' box grown by 2 sigma, the first
+                     outside-to-inside sign change refined by 20 bisections */
+  float sigma;    /* SDF: Gaussian width of Eq. 2, m, in (0, 1) */
+  float t_min;    /* hits need t > t_min (>= 0) */
+  float t_max;    /* and t < t_max (INFINITY for no bound) */
+} nrt_cast_params;
+
+/* Closest hits of n arbitrary rays against the scene.  o, d: device
+ * float[n][3] (d need not be unit; it is normalised).  Outputs, device,
+ * caller-allocated, any may be NULL: t float[n] (ray parameter of the hit
+ * point along unit d; +inf on a miss), normal float[n][3] (facing the ray; 0
+ * on a miss), dps int32[n] (-1 on a miss), labels uint32[n] (surface |
+ * material << 16 of the closest disc, or of the hit DPS's point nearest to
+ * the SDF hit).  Enqueued on the context stream; synchronises to read the
+ * traversal status.  Errors: NRT_ERR_ARG (NULL rays, n > 2^31, unknown
+ * model, sigma outside (0, 1) for the SDF, not 0 <= t_min < t_max),
+ * NRT_ERR_OVERFLOW (traversal stack overflow), NRT_ERR_CUDA. */
+nrt_status nrt_cast(nrt_scene* scene, const float* o, const float* d, int64_t n,
+                    const nrt_cast_params* params, float* t, float* normal, int32_t* dps,
+                    uint32_t* labels);
+
 /* One simulation for one TX (Sec. II-B):
  *   LOS casts TX -> every RX; Fibonacci launch of n_rays directions (or the
  *   subset `ray_subset` of their ids); every interaction continues as a

@@ -26,6 +26,8 @@ LAUNCH_DPS = 1
 POL_TE = 0
 POL_TM = 1
 POL_VECTOR = 2
+ISECT_DISC = 0
+ISECT_SDF = 1
 
 
 class NrtError(RuntimeError):
@@ -47,6 +49,11 @@ class TraceParams(C.Structure):
         ("freq", C.c_float), ("keep_keys", C.c_int32), ("key_capacity", C.c_int64),
         ("cand_capacity", C.c_int64), ("launch", C.c_int32), ("diffraction", C.c_int32),
     ]
+
+
+class CastParams(C.Structure):
+    _fields_ = [("model", C.c_int32), ("sigma", C.c_float), ("t_min", C.c_float),
+                ("t_max", C.c_float)]
 
 
 class Counters(C.Structure):
@@ -102,6 +109,7 @@ def lib():
         L.nrt_scene_dps_read.argtypes = [_P, _P, _P, _P]
         L.nrt_set_materials.argtypes = [_P, _P, _P, _P, C.c_int]
         L.nrt_scene_set_edges.argtypes = [_P, C.c_int64, _P, _P, _P, _P, _P, _P]
+        L.nrt_cast.argtypes = [_P, _P, _P, C.c_int64, C.POINTER(CastParams), _P, _P, _P, _P]
         L.nrt_trace.argtypes = [_P, _P, _P, C.c_int, C.POINTER(TraceParams), _P, C.c_int64,
                                 C.c_int, C.POINTER(_P)]
         L.nrt_result_free.argtypes = [_P]
@@ -260,6 +268,26 @@ class Scene:
         arrs = (f(edges.a), f(edges.b), f(edges.n0), f(edges.n1), u(edges.m0), u(edges.m1))
         self.ctx._check(lib().nrt_scene_set_edges(self._h, int(arrs[4].shape[0]),
                                                   *[_np_ptr(x) for x in arrs]))
+
+    def cast(self, o, d, model=ISECT_DISC, sigma=0.0, t_min=1e-3, t_max=float("inf")):
+        """Closest hits of rays o + t d (CUDA float32 tensors [n, 3]) under the
+        disc model or the SDF model (nrt_cast); returns CUDA tensors t [n],
+        normal [n, 3], dps [n], labels [n]."""
+        import torch
+
+        o = o.contiguous()
+        d = d.contiguous()
+        n = int(o.shape[0])
+        dev = o.device
+        out = {"t": torch.empty(n, dtype=torch.float32, device=dev),
+               "normal": torch.empty((n, 3), dtype=torch.float32, device=dev),
+               "dps": torch.empty(n, dtype=torch.int32, device=dev),
+               "labels": torch.empty(n, dtype=torch.int32, device=dev)}
+        prm = CastParams(int(model), float(sigma), float(t_min), float(t_max))
+        self.ctx._check(lib().nrt_cast(self._h, _P(o.data_ptr()), _P(d.data_ptr()), n,
+                                       C.byref(prm), *[_P(out[k].data_ptr()) for k in
+                                                       ("t", "normal", "dps", "labels")]))
+        return out
 
     def trace(self, tx, rx, params: TraceParams, ray_subset=None) -> "Result":
         return Result(self, tx, rx, params, ray_subset)
