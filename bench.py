@@ -334,6 +334,58 @@ def diffraction_bench(ctx, o, tx, stream, rays):
     return out
 
 
+def _face_plane(surf, boxes, room=(20.0, 10.0, 3.0)):
+    """(axis, offset) of the office's planar face with surface label surf."""
+    if surf < 6:
+        return surf // 2, 0.0 if surf % 2 == 0 else room[surf // 2]
+    b, f = divmod(surf - 6, 5)
+    x0, x1, y0, y1, h = boxes[b]
+    return [(0, x0), (0, x1), (1, y0), (1, y1), (2, h)][f]
+
+
+def isect_bench(scene, o, stream, n=1_000_000):
+    """Intersection-model ablation (Sec. II-C against the prior work's SDF,
+    Eq. 2): the first hit of n seeded random directions from the office TX
+    under each model (nrt_cast), device-timed (median of 3 after a warm-up),
+    the share of rays that hit, and the distance of each hit from the true
+    face plane of its surface label (the points carry 1 cm noise)."""
+    import torch
+    from paper_2507_04021_gb300 import inputs, nrt
+
+    rng = inputs.rng_for(inputs.SEED_EDGES, 9)
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    dd = torch.from_numpy(d.astype(np.float32)).cuda()
+    oo = torch.from_numpy(np.tile(np.asarray(o.tx, np.float32), (n, 1))).cuda()
+    torch.cuda.synchronize()  # the casts run on the library's stream
+    boxes = o.extra["boxes"]
+    out = {"rays": n}
+    for name, model, sigma in (("disc", nrt.ISECT_DISC, 0.0), ("sdf", nrt.ISECT_SDF, 0.015)):
+        scene.cast(oo, dd, model=model, sigma=sigma)
+        ms = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = scene.cast(oo, dd, model=model, sigma=sigma)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = r["t"].cpu().numpy().astype(np.float64)
+        lab = r["labels"].cpu().numpy().astype(np.int64) & 0xFFFF
+        hit = np.isfinite(t)
+        q = np.asarray(o.tx, np.float64)[None] + t[hit, None] * d[hit]
+        err = np.array([abs(q[i, a] - off) for i, (a, off) in
+                        enumerate(_face_plane(int(s_), boxes) for s_ in lab[hit])])
+        out[name] = {"sigma": sigma if model == nrt.ISECT_SDF else None,
+                     "ms": float(np.median(ms)), "casts_per_s": n / (float(np.median(ms)) / 1e3),
+                     "hit_fraction": float(hit.mean()),
+                     "plane_error_m": {"mean": float(err.mean()), "p50": float(np.median(err)),
+                                       "p99": float(np.quantile(err, 0.99))}}
+    out["sdf_over_disc_time"] = out["sdf"]["ms"] / out["disc"]["ms"]
+    return out
+
+
 def proposal_bench(scene, o):
     """Learned launch proposal (RX-sphere capture, 16 RX, 5 specular
     interactions): 5M labelled rays from 250 trajectory positions, training
@@ -532,6 +584,7 @@ def ours(args):
     if rank == 0:
         line["launch_comparison"] = launch_bench(scene, o, tx, stream)
         line["diffraction"] = diffraction_bench(ctx, o, tx, stream, args.rays)
+        line["intersection_ablation"] = isect_bench(scene, o, stream)
     if args.proposal and rank == 0:
         line["proposal"] = proposal_bench(scene, o)
     if args.batch_pairs > 0:
