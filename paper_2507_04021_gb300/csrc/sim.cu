@@ -870,39 +870,64 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
 // most kappa times).  A hit on another surface, a miss or a failed side
 // check ends the candidate.  Finally I_k -> RX must be clear.
 // Coordinates are taken relative to the RX to keep float magnitudes small.
+// Scheduling: one loop step is one refinement attempt of the lane's current
+// key; a lane whose key is finished takes the next key of the list from a
+// per-round counter (one warp-aggregated atomic per fetch).  Keys with many
+// retries then no longer hold the other 31 lanes of their warp idle until
+// the slowest key of each batch is done.  Every key's arithmetic is that of
+// a key-at-a-time loop, so the outcome does not depend on the order.
 __global__ void __launch_bounds__(kTraceThreads, 8)
     validate_specular_kernel(SceneView S, SimConst C, ValArgs A, const uint32_t* __restrict__ list,
-                             const unsigned long long* __restrict__ n_list_p, unsigned long long* ctr) {
+                             const unsigned long long* __restrict__ n_list_p,
+                             unsigned long long* __restrict__ fetch, unsigned long long* ctr) {
   NRT_STACK_DECL
   unsigned long long casts = 0;
   const int64_t n_list = (int64_t)*n_list_p;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_list;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t kid = list[i];
-    NRT_GUARD(kid < g_dbg_caps.keys, 9, kid)
-    const uint32_t slot = A.K.slot[kid];
-    NRT_GUARD(slot < g_dbg_caps.table, 10, slot)
-    const uint32_t row = A.K.cur[kid];
-    NRT_GUARD(row < g_dbg_caps.rows, 11, row)
-    const uint64_t hi = A.T.hi[slot], lo = A.T.lo[slot];
-    NRT_GUARD(((hi >> 52) & 7) >= 1 && ((hi >> 52) & 7) <= (uint64_t)C.max_depth, 12, hi >> 52)
-    const int j = (int)(hi >> 56);
-    const int k = (int)((hi >> 52) & 7);
+  const int lane = threadIdx.x & 31;
+  bool have = false;
+  uint32_t kid = 0, row = 0;
+  uint64_t hi = 0, lo = 0;
+  int j = 0, k = 0, attempt = 0;
+  float3 rxp = f3(0.f, 0.f, 0.f), txl = rxp;
+  float3 Pp[kMaxDepth], Pn[kMaxDepth];
+  for (;;) {
+    if (!have) {
+      const unsigned mask = __activemask();
+      const int leader = __ffs(mask) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(fetch, (unsigned long long)__popc(mask));
+      base = __shfl_sync(mask, base, leader);
+      const int64_t i = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+      if (i >= n_list) break;
+      kid = list[i];
+      NRT_GUARD(kid < g_dbg_caps.keys, 9, kid)
+      const uint32_t slot = A.K.slot[kid];
+      NRT_GUARD(slot < g_dbg_caps.table, 10, slot)
+      row = A.K.cur[kid];
+      NRT_GUARD(row < g_dbg_caps.rows, 11, row)
+      hi = A.T.hi[slot];
+      lo = A.T.lo[slot];
+      NRT_GUARD(((hi >> 52) & 7) >= 1 && ((hi >> 52) & 7) <= (uint64_t)C.max_depth, 12, hi >> 52)
+      j = (int)(hi >> 56);
+      k = (int)((hi >> 52) & 7);
+      rxp = xyz(A.rx[C.batch ? 0 : j]);
+      for (int m = 0; m < k; ++m) {
+        const int64_t b = A.R.at(m, row);
+        Pp[m] = xyz(A.R.q[b]) - rxp;
+        Pn[m] = xyz(A.R.n[b]);
+      }
+      txl = tx_of(C, j) - rxp;
+      attempt = 0;
+      have = true;
+    }
     uint32_t lab[kMaxDepth];
     for (int m = 0; m < 4; ++m) lab[m] = (uint32_t)((lo >> (16 * m)) & 0xFFFF);
     lab[4] = (uint32_t)(hi & 0xFFFF);
-    const float3 rxp = xyz(A.rx[C.batch ? 0 : j]);
-    float3 Pp[kMaxDepth], Pn[kMaxDepth];
-    for (int m = 0; m < k; ++m) {
-      const int64_t b = A.R.at(m, row);
-      Pp[m] = xyz(A.R.q[b]) - rxp;
-      Pn[m] = xyz(A.R.n[b]);
-    }
-    const float3 txl = tx_of(C, j) - rxp;
-    bool valid = false;
+    // one attempt: image solve, side checks, leg casts
+    bool finished = true, valid = false;
     float3 I[kMaxDepth + 2];
     uint32_t vmats[kMaxDepth];
-    for (int attempt = 0; attempt <= C.kappa; ++attempt) {
+    do {
       float3 img[kMaxDepth + 1];
       img[0] = txl;
       for (int m = 0; m < k; ++m)
@@ -960,7 +985,9 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
         if (attempt == C.kappa) break;
         Pp[fail_m - 1] = fq;
         Pn[fail_m - 1] = fn;
-        continue;
+        ++attempt;
+        finished = false;  // retry with the hit's plane in the next step
+        break;
       }
       // last leg to the RX
       const float3 last = f3(0.f, 0.f, 0.f) - I[k];
@@ -969,8 +996,8 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
                                     my_stk, my_tstk, kTraceThreads, err);
       ++casts;
       valid = hf.idx < 0;
-      break;
-    }
+    } while (false);
+    if (!finished) continue;
     PathRec P;
     if (valid) {
       memset(&P, 0, sizeof(P));
@@ -995,6 +1022,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
       P.geo = C.lambda / (4.0f * 3.14159265358979f * len);
     }
     finish_key(A, kid, valid, ctr, C, &P);
+    have = false;
   }
   count_add(ctr + kCtrValCasts, casts);
 }
@@ -1726,7 +1754,7 @@ struct Work {
 };
 
 // round counters in Work::cnt
-enum { kCntSpec = 0, kCntDiff, kCntKeys, kCntCurS, kCntCurD, kCntNxtS, kCntNxtD, kCntN };
+enum { kCntSpec = 0, kCntDiff, kCntKeys, kCntCurS, kCntCurD, kCntNxtS, kCntNxtD, kCntFetch, kCntN };
 
 template <class T>
 cudaError_t dalloc(T** p, int64_t n, cudaStream_t st) {
@@ -1933,11 +1961,11 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   uint32_t *cur_s = W.spec_list, *cur_d = W.diff_list, *nxt_s = W.list2_s, *nxt_d = W.list2_d;
   TRY(cudaMemcpyAsync(W.cnt + kCntCurS, W.cnt + kCntSpec, 16, cudaMemcpyDeviceToDevice, st));
   for (int round = 0; round < r->p.rep_tries; ++round) {
-    TRY(cudaMemsetAsync(W.cnt + kCntNxtS, 0, 16, st));
+    TRY(cudaMemsetAsync(W.cnt + kCntNxtS, 0, 24, st));  // next lists and the fetch counter
     V.next_list = nxt_s;
     V.next_cnt = W.cnt + kCntNxtS;
-    validate_specular_kernel<<<blocks_for(c.keys, kTraceThreads, sm), kTraceThreads, 0, st>>>(
-        S, C, V, cur_s, W.cnt + kCntCurS, ctr); count_launch();
+    validate_specular_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
+        S, C, V, cur_s, W.cnt + kCntCurS, W.cnt + kCntFetch, ctr); count_launch();
     V.next_list = nxt_d;
     V.next_cnt = W.cnt + kCntNxtD;
     validate_diffuse_kernel<<<blocks_for(c.keys, kTraceThreads, sm), kTraceThreads, 0, st>>>(
