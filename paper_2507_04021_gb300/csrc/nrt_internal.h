@@ -127,6 +127,7 @@ enum Ctr : int {
   kCtrLeaders,
   kCtrCompact,
   kCtrDfrCasts,  // edge visibility casts (diffraction)
+  kCtrRayFetch,  // trace: rays handed out to lanes
   kCtrCount
 };
 

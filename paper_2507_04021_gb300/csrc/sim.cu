@@ -445,19 +445,65 @@ __device__ __forceinline__ unsigned trace_row(const SceneView& S, const SimConst
                                               const Records& R, int64_t row, int* stk, float* tstk,
                                               uint32_t* err);
 
-// One ray per thread (static grid-stride schedule over the launch order);
-// every interaction continues as a specular reflection (Sec. II-B: the ray
-// count stays constant).  The next cast skips the DPS just hit.
+__device__ __forceinline__ void ray_start(const SceneView& S, const SimConst& C,
+                                          const uint32_t* __restrict__ ray_of_row, int64_t row,
+                                          float3* o, float3* d);
+
+// Every interaction continues as a specular reflection (Sec. II-B: the ray
+// count stays constant); the next cast skips the DPS just hit.  Scheduling:
+// one loop step is one bounce of the lane's current ray; a lane whose ray
+// has ended (a miss or the last segment) takes the next ray of the launch
+// order from a counter (one warp-aggregated atomic per fetch), so rays that
+// escape early do not leave their lanes idle while the warp's longest ray
+// finishes.  Each ray's casts are those of a ray-at-a-time loop.
 __global__ void __launch_bounds__(kTraceThreads, 8)
     trace_kernel(SceneView S, SimConst C, const uint32_t* __restrict__ ray_of_row,
-                 const uint32_t* __restrict__ order, Records R, unsigned long long* ctr) {
+                 const uint32_t* __restrict__ order, Records R, unsigned long long* __restrict__ fetch,
+                 unsigned long long* ctr) {
   NRT_STACK_DECL
   unsigned long long segs = 0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < R.n_rows;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = order ? order[t] : t;
-    NRT_GUARD(row >= 0 && row < g_dbg_caps.rows, 25, row)
-    segs += trace_row(S, C, ray_of_row, R, row, my_stk, my_tstk, err);
+  const int lane = threadIdx.x & 31;
+  bool have = false;
+  int64_t row = 0;
+  float3 o = C.tx, d = C.tx;
+  int skip = -1, seg = 0;
+  for (;;) {
+    if (!have) {
+      const unsigned mask = __activemask();
+      const int leader = __ffs(mask) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(fetch, (unsigned long long)__popc(mask));
+      base = __shfl_sync(mask, base, leader);
+      const int64_t t = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+      if (t >= R.n_rows) break;
+      row = order ? order[t] : t;
+      NRT_GUARD(row >= 0 && row < g_dbg_caps.rows, 25, row)
+      ray_start(S, C, ray_of_row, row, &o, &d);
+      skip = -1;
+      seg = 0;
+      have = true;
+    }
+    const Hit h = cast_ray<false>(S, o, d, skip, C.t_min, __int_as_float(0x7f800000), true, my_stk,
+                                  my_tstk, kTraceThreads, err);
+    ++segs;
+    const int64_t a = R.at(seg, row);
+    if (h.idx < 0) {
+      R.i[a] = make_int2(-1, 0);
+      have = false;
+      continue;
+    }
+    const float3 q = o + h.tbar * d;
+    const float dn = dot3(d, h.n);
+    float3 dout = d - (2.0f * dn) * h.n;
+    dout = unit3(dout);
+    R.q[a] = make_float4(q.x, q.y, q.z, h.tbar);
+    R.n[a] = make_float4(h.n.x, h.n.y, h.n.z, fabsf(dn));
+    R.d[a] = make_float4(dout.x, dout.y, dout.z, __int_as_float(h.dps));
+    R.i[a] = make_int2(h.idx, (int)h.labels);
+    o = q;
+    d = dout;
+    skip = h.dps;
+    if (++seg >= C.n_seg) have = false;
   }
   count_add(ctr + kCtrSegments, segs);
 }
@@ -1627,12 +1673,12 @@ SimConst make_const(const nrt_result* r) {
   return C;
 }
 
-// One ray: launch, closest hit per bounce, specular continuation; the hit
-// records go to the ray's row.  Returns the segments cast.
-__device__ __forceinline__ unsigned trace_row(const SceneView& S, const SimConst& C,
-                                              const uint32_t* __restrict__ ray_of_row,
-                                              const Records& R, int64_t row, int* stk, float* tstk,
-                                              uint32_t* err) {
+// Origin and direction of the ray of `row`: the Fibonacci sphere, or
+// (Sec. II-B) toward the reception point of DPS `ray` (the DPS are stored in
+// voxel Morton order); batch rows take their pair's TX and launch size.
+__device__ __forceinline__ void ray_start(const SceneView& S, const SimConst& C,
+                                          const uint32_t* __restrict__ ray_of_row, int64_t row,
+                                          float3* o_out, float3* d_out) {
   uint32_t ray = ray_of_row ? ray_of_row[row] : (uint32_t)row;
   int64_t n_launch = C.n_rays;
   float3 o = C.tx;
@@ -1642,9 +1688,18 @@ __device__ __forceinline__ unsigned trace_row(const SceneView& S, const SimConst
     n_launch = __ldg(C.pair_rays + pj);
     o = xyz(__ldg(C.tx_pair + pj));
   }
-  // Fibonacci sphere, or (Sec. II-B) toward the reception point of DPS `ray`
-  // (the DPS are stored in voxel Morton order)
-  float3 d = C.launch == NRT_LAUNCH_DPS ? unit3(xyz(__ldg(S.recv + ray)) - o) : fib_dir(ray, n_launch);
+  *o_out = o;
+  *d_out = C.launch == NRT_LAUNCH_DPS ? unit3(xyz(__ldg(S.recv + ray)) - o) : fib_dir(ray, n_launch);
+}
+
+// One ray: launch, closest hit per bounce, specular continuation; the hit
+// records go to the ray's row.  Returns the segments cast.
+__device__ __forceinline__ unsigned trace_row(const SceneView& S, const SimConst& C,
+                                              const uint32_t* __restrict__ ray_of_row,
+                                              const Records& R, int64_t row, int* stk, float* tstk,
+                                              uint32_t* err) {
+  float3 o, d;
+  ray_start(S, C, ray_of_row, row, &o, &d);
   int skip = -1;
   unsigned segs = 0;
   for (int s = 0; s < C.n_seg; ++s) {
@@ -2093,7 +2148,8 @@ nrt_status enqueue_trace(nrt_result* r, const SceneView& S, const SimConst& C,
     trace_persistent_kernel<<<sm * 8, kTraceThreads, 0, st>>>(S, C, order, R, r->chunk_start,
                                                               r->packet, r->queue, r->stamps, r->ctr); count_launch();
   } else {
-    trace_kernel<<<blocks_for(n, kTraceThreads, sm), kTraceThreads, 0, st>>>(S, C, subset_d, order, R, r->ctr); count_launch();
+    trace_kernel<<<blocks_for(n, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
+        S, C, subset_d, order, R, r->ctr + kCtrRayFetch, r->ctr); count_launch();
   }
   if (r->ev[3]) TRY(cudaEventRecord(r->ev[3], st));
   return NRT_OK;
