@@ -807,50 +807,88 @@ struct ValArgs {
   const uint32_t* ray_of_row;
   PathRec* paths;
   int64_t path_cap;
-  uint32_t* next_list;           // keys still pending after this round
-  unsigned long long* next_cnt;  // their count
+  SortedCand SC;  // each key's candidates, one run per slot in ray order
 };
 
-__device__ __forceinline__ void finish_key(const ValArgs& A, uint32_t kid, bool valid,
-                                           unsigned long long* ctr, const SimConst& C,
-                                           const PathRec* rec) {
+// Outcome of one try of key kid (candidate row *row at position *pos of the
+// sorted candidates): a valid path is recorded; otherwise the key moves to
+// its next candidate -- the next element of its slot's run, i.e. the next
+// larger ray id -- unless it has used rep_tries tries or has no candidate
+// left.  Returns true when the key is finished.
+__device__ __forceinline__ bool key_try(const ValArgs& A, uint32_t kid, uint32_t slot, bool valid,
+                                        const PathRec* rec, uint32_t* row, uint32_t* pos,
+                                        unsigned long long* ctr, const SimConst& C) {
   uint32_t* err = (uint32_t*)(ctr + kCtrErr);
   if (valid) {
     A.K.status[kid] = 1;
     const unsigned long long p = warp_inc(ctr + kCtrPaths);
     if ((int64_t)p >= A.path_cap) {
       atomicOr(err, kErrPathFull);
-      return;
+      return true;
     }
     A.paths[p] = *rec;
-    return;
+    return true;
   }
   const uint32_t tr = A.K.tries[kid] + 1;
   A.K.tries[kid] = tr;
   if ((int)tr >= C.rep_tries) {
     A.K.status[kid] = 2;
-  } else {
-    A.K.status[kid] = 0;
-    A.next_list[warp_inc(A.next_cnt)] = kid;
+    return true;
   }
+  const int64_t n_cand = min((int64_t)*A.SC.n_p, A.SC.cap);
+  const int64_t q = (int64_t)*pos + 1;
+  const uint64_t e = q < n_cand ? A.SC.key[q] : ~0ull;
+  if (q >= n_cand || (e >> A.SC.row_bits) != (uint64_t)slot) {
+    A.K.status[kid] = 2;
+    return true;
+  }
+  *row = (uint32_t)(e & ((1ull << A.SC.row_bits) - 1ull));
+  *pos = (uint32_t)q;
+  A.K.cur[kid] = *row;
+  A.K.pos[kid] = *pos;
+  return false;
+}
+
+// next key of a list for the calling lane (one warp-aggregated atomic per
+// fetch); returns its position or -1 when the list is exhausted
+__device__ __forceinline__ int64_t fetch_next(unsigned long long* fetch, int64_t n) {
+  const int lane = threadIdx.x & 31;
+  const unsigned mask = __activemask();
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(fetch, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  const int64_t i = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+  return i < n ? i : -1;
 }
 
 // Diffuse: the candidate's own interaction points; the last one scatters
 // toward the RX if the RX is in front of the surface and a cast from the
 // scatter point (skipping its DPS) reaches the RX unobstructed (Sec. II-B-1).
+// One loop step is one try (one shadow cast); a lane walks its key's
+// candidates in ray order and takes the next key of the list when the key is
+// finished.
 __global__ void __launch_bounds__(kTraceThreads, 8)
     validate_diffuse_kernel(SceneView S, SimConst C, ValArgs A, const uint32_t* __restrict__ list,
-                            const unsigned long long* __restrict__ n_list_p, unsigned long long* ctr) {
+                            const unsigned long long* __restrict__ n_list_p,
+                            unsigned long long* __restrict__ fetch, unsigned long long* ctr) {
   NRT_STACK_DECL
   unsigned long long casts = 0;
   const int64_t n_list = (int64_t)*n_list_p;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_list;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t kid = list[i];
-    NRT_GUARD(kid < g_dbg_caps.keys, 5, kid)
-    const uint32_t slot = A.K.slot[kid];
-    NRT_GUARD(slot < g_dbg_caps.table, 6, slot)
-    const uint32_t row = A.K.cur[kid];
+  bool have = false;
+  uint32_t kid = 0, slot = 0, row = 0, pos = 0;
+  for (;;) {
+    if (!have) {
+      const int64_t i = fetch_next(fetch, n_list);
+      if (i < 0) break;
+      kid = list[i];
+      NRT_GUARD(kid < g_dbg_caps.keys, 5, kid)
+      slot = A.K.slot[kid];
+      NRT_GUARD(slot < g_dbg_caps.table, 6, slot)
+      row = A.K.cur[kid];
+      pos = A.K.pos[kid];
+      have = true;
+    }
     NRT_GUARD(row < g_dbg_caps.rows, 7, row)
     const uint64_t hi = A.T.hi[slot];
     const int j = (int)(hi >> 56);
@@ -901,7 +939,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
               sqrtf(rho * rho * ci * cs / 3.14159265358979f) / (ri * rs);
       P.length = ri + rs;
     }
-    finish_key(A, kid, valid, ctr, C, &P);
+    if (key_try(A, kid, slot, valid, &P, &row, &pos, ctr, C)) have = false;
   }
   count_add(ctr + kCtrValCasts, casts);
   count_add(ctr + kCtrDiffCasts, casts);
@@ -918,11 +956,12 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
 // check ends the candidate.  Finally I_k -> RX must be clear.
 // Coordinates are taken relative to the RX to keep float magnitudes small.
 // Scheduling: one loop step is one refinement attempt of the lane's current
-// key; a lane whose key is finished takes the next key of the list from a
-// per-round counter (one warp-aggregated atomic per fetch).  Keys with many
-// retries then no longer hold the other 31 lanes of their warp idle until
-// the slowest key of each batch is done.  Every key's arithmetic is that of
-// a key-at-a-time loop, so the outcome does not depend on the order.
+// candidate; a failed candidate moves the lane to its key's next candidate
+// (ray order), and a finished key to the next key of the list (one
+// warp-aggregated atomic per fetch).  Keys with many retries or tries then
+// no longer hold the other 31 lanes of their warp idle, and one launch
+// covers all of a key's tries.  Every key's arithmetic is that of a
+// key-at-a-time loop, so the outcome does not depend on the order.
 __global__ void __launch_bounds__(kTraceThreads, 8)
     validate_specular_kernel(SceneView S, SimConst C, ValArgs A, const uint32_t* __restrict__ list,
                              const unsigned long long* __restrict__ n_list_p,
@@ -930,42 +969,41 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
   NRT_STACK_DECL
   unsigned long long casts = 0;
   const int64_t n_list = (int64_t)*n_list_p;
-  const int lane = threadIdx.x & 31;
-  bool have = false;
-  uint32_t kid = 0, row = 0;
+  bool have = false, fresh = false;
+  uint32_t kid = 0, slot = 0, row = 0, pos = 0;
   uint64_t hi = 0, lo = 0;
   int j = 0, k = 0, attempt = 0;
   float3 rxp = f3(0.f, 0.f, 0.f), txl = rxp;
   float3 Pp[kMaxDepth], Pn[kMaxDepth];
   for (;;) {
     if (!have) {
-      const unsigned mask = __activemask();
-      const int leader = __ffs(mask) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(fetch, (unsigned long long)__popc(mask));
-      base = __shfl_sync(mask, base, leader);
-      const int64_t i = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
-      if (i >= n_list) break;
+      const int64_t i = fetch_next(fetch, n_list);
+      if (i < 0) break;
       kid = list[i];
       NRT_GUARD(kid < g_dbg_caps.keys, 9, kid)
-      const uint32_t slot = A.K.slot[kid];
+      slot = A.K.slot[kid];
       NRT_GUARD(slot < g_dbg_caps.table, 10, slot)
       row = A.K.cur[kid];
-      NRT_GUARD(row < g_dbg_caps.rows, 11, row)
+      pos = A.K.pos[kid];
       hi = A.T.hi[slot];
       lo = A.T.lo[slot];
       NRT_GUARD(((hi >> 52) & 7) >= 1 && ((hi >> 52) & 7) <= (uint64_t)C.max_depth, 12, hi >> 52)
       j = (int)(hi >> 56);
       k = (int)((hi >> 52) & 7);
       rxp = xyz(A.rx[C.batch ? 0 : j]);
+      txl = tx_of(C, j) - rxp;
+      have = true;
+      fresh = true;
+    }
+    if (fresh) {  // a new candidate: its recorded planes, attempt 0
+      NRT_GUARD(row < g_dbg_caps.rows, 11, row)
       for (int m = 0; m < k; ++m) {
         const int64_t b = A.R.at(m, row);
         Pp[m] = xyz(A.R.q[b]) - rxp;
         Pn[m] = xyz(A.R.n[b]);
       }
-      txl = tx_of(C, j) - rxp;
       attempt = 0;
-      have = true;
+      fresh = false;
     }
     uint32_t lab[kMaxDepth];
     for (int m = 0; m < 4; ++m) lab[m] = (uint32_t)((lo >> (16 * m)) & 0xFFFF);
@@ -1068,8 +1106,8 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
       P.length = len;
       P.geo = C.lambda / (4.0f * 3.14159265358979f * len);
     }
-    finish_key(A, kid, valid, ctr, C, &P);
-    have = false;
+    if (key_try(A, kid, slot, valid, &P, &row, &pos, ctr, C)) have = false;
+    else fresh = true;
   }
   count_add(ctr + kCtrValCasts, casts);
 }
@@ -1101,30 +1139,6 @@ __global__ void run_start_kernel(SortedCand SC, uint32_t* __restrict__ start) {
   }
 }
 
-// Next candidate of each key that failed this round: the next element of its
-// run in the sorted candidates (the smallest row above the one just tried).
-__global__ void next_apply_kernel(const uint32_t* __restrict__ list,
-                                  const unsigned long long* __restrict__ n_p, KeyState K,
-                                  SortedCand SC, uint32_t* __restrict__ out_list,
-                                  unsigned long long* out_cnt) {
-  const int64_t n = (int64_t)*n_p;
-  const int64_t n_cand = min((int64_t)*SC.n_p, SC.cap);
-  const uint64_t row_mask = (1ull << SC.row_bits) - 1ull;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t kid = list[i];
-    NRT_GUARD(kid < g_dbg_caps.keys, 17, kid)
-    const int64_t q = (int64_t)K.pos[kid] + 1;
-    const uint64_t e = q < n_cand ? SC.key[q] : ~0ull;
-    if (q >= n_cand || (e >> SC.row_bits) != (uint64_t)K.slot[kid]) {
-      K.status[kid] = 2;
-    } else {
-      K.cur[kid] = (uint32_t)(e & row_mask);
-      K.pos[kid] = (uint32_t)q;
-      out_list[warp_inc(out_cnt)] = kid;
-    }
-  }
-}
 
 // Per-key summaries for merging ray-range shards: candidates tried (the
 // valid one included) and the ray id of the validated candidate.
@@ -1796,7 +1810,7 @@ struct Work {
   Caps caps;
   Table T{};
   KeyState K{};
-  uint32_t *spec_list = nullptr, *diff_list = nullptr, *list2_s = nullptr, *list2_d = nullptr;
+  uint32_t *spec_list = nullptr, *diff_list = nullptr;
   uint2 *cand = nullptr, *cand2 = nullptr;
   uint32_t *cand_cnt = nullptr, *cand_off = nullptr;
   uint32_t *fs = nullptr, *fd = nullptr, *os = nullptr, *od = nullptr;
@@ -1810,7 +1824,7 @@ struct Work {
 };
 
 // round counters in Work::cnt
-enum { kCntSpec = 0, kCntDiff, kCntKeys, kCntCurS, kCntCurD, kCntNxtS, kCntNxtD, kCntFetch, kCntN };
+enum { kCntSpec = 0, kCntDiff, kCntKeys, kCntFetchS, kCntFetchD, kCntN };
 
 template <class T>
 cudaError_t dalloc(T** p, int64_t n, cudaStream_t st) {
@@ -1833,8 +1847,6 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
   TRY(dalloc(&W.K.status, c.keys, st));
   TRY(dalloc(&W.spec_list, c.keys, st));
   TRY(dalloc(&W.diff_list, c.keys, st));
-  TRY(dalloc(&W.list2_s, c.keys, st));
-  TRY(dalloc(&W.list2_d, c.keys, st));
   TRY(dalloc(&W.cand, c.cand, st));
   TRY(dalloc(&W.cand2, c.cand, st));
   if (!W.cand_cnt) TRY(dalloc(&W.cand_cnt, n_rows, st));
@@ -1858,7 +1870,7 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
 
 void release_work(Work& W, cudaStream_t st) {
   void* ptrs[] = {W.T.fp, W.T.hi, W.T.lo, W.T.minrow, W.T.kid, W.T.next, W.K.slot, W.K.cur, W.K.pos,
-                  W.K.tries, W.K.status, W.spec_list, W.diff_list, W.list2_s, W.list2_d, W.cand,
+                  W.K.tries, W.K.status, W.spec_list, W.diff_list, W.cand,
                   W.cand2, W.cand_cnt, W.cand_off, W.fs, W.fd, W.os, W.od, W.sk0, W.tk0,
                   W.sv0, W.tv, W.raw, W.psk, W.ptk, W.psi, W.pti, W.cnt, W.order};
   for (void* q : ptrs)
@@ -2014,25 +2026,13 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   V.ray_of_row = nullptr;
   V.paths = W.raw;
   V.path_cap = c.paths;
-  uint32_t *cur_s = W.spec_list, *cur_d = W.diff_list, *nxt_s = W.list2_s, *nxt_d = W.list2_d;
-  TRY(cudaMemcpyAsync(W.cnt + kCntCurS, W.cnt + kCntSpec, 16, cudaMemcpyDeviceToDevice, st));
-  for (int round = 0; round < r->p.rep_tries; ++round) {
-    TRY(cudaMemsetAsync(W.cnt + kCntNxtS, 0, 24, st));  // next lists and the fetch counter
-    V.next_list = nxt_s;
-    V.next_cnt = W.cnt + kCntNxtS;
-    validate_specular_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
-        S, C, V, cur_s, W.cnt + kCntCurS, W.cnt + kCntFetch, ctr); count_launch();
-    V.next_list = nxt_d;
-    V.next_cnt = W.cnt + kCntNxtD;
-    validate_diffuse_kernel<<<blocks_for(c.keys, kTraceThreads, sm), kTraceThreads, 0, st>>>(
-        S, C, V, cur_d, W.cnt + kCntCurD, ctr); count_launch();
-    if (round + 1 >= r->p.rep_tries) break;
-    TRY(cudaMemsetAsync(W.cnt + kCntCurS, 0, 16, st));
-    next_apply_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(nxt_s, W.cnt + kCntNxtS, W.K, SC,
-                                                                  cur_s, W.cnt + kCntCurS); count_launch();
-    next_apply_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(nxt_d, W.cnt + kCntNxtD, W.K, SC,
-                                                                  cur_d, W.cnt + kCntCurD); count_launch();
-  }
+  V.SC = SC;
+  // every key walks its candidates in ray order inside one launch per type
+  TRY(cudaMemsetAsync(W.cnt + kCntFetchS, 0, 16, st));
+  validate_specular_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
+      S, C, V, W.spec_list, W.cnt + kCntSpec, W.cnt + kCntFetchS, ctr); count_launch();
+  validate_diffuse_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
+      S, C, V, W.diff_list, W.cnt + kCntDiff, W.cnt + kCntFetchD, ctr); count_launch();
   if (r->ev[5]) TRY(cudaEventRecord(r->ev[5], st));
   if (r->p.keep_keys) {
     key_summary_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(
