@@ -341,7 +341,7 @@ __device__ __forceinline__ void make_key(int j, int diffuse, int k, const uint16
 }
 
 // 64-bit fingerprint of a key: the splitmix64 finaliser applied to a
-// combination of both words; 0 is reserved for "empty".
+// combination of both words; all-ones is reserved for "empty".
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   x ^= x >> 30;
   x *= 0xbf58476d1ce4e5b9ull;
@@ -352,7 +352,7 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
 }
 __device__ __forceinline__ uint64_t key_fp(uint64_t hi, uint64_t lo) {
   uint64_t f = mix64(hi ^ mix64(lo + 0x9E3779B97F4A7C15ull));
-  return f ? f : 1ull;
+  return f != ~0ull ? f : 1ull;
 }
 
 // voxel of a point, floor((q - bmin) / rho), as in the scene build

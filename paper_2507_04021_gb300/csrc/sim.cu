@@ -77,13 +77,20 @@ inline cudaError_t dbg_set_caps(int64_t table, int64_t keys, int64_t cand, int64
 
 namespace {
 
+// One hash slot in one 32-byte sector: an insert or a lookup touches one
+// sector.  All-ones is the empty fingerprint and the initial minrow, so one
+// 0xFF fill initialises the table.
+struct alignas(32) Bucket {
+  unsigned long long fp;  // ~0 = empty
+  uint64_t hi, lo;
+  uint32_t minrow;        // lowest row among the key's candidates
+  uint32_t kid;           // key id
+};
+static_assert(sizeof(Bucket) == 32, "Bucket layout");
+
 struct Table {
-  unsigned long long* fp;  // 0 = empty
-  uint64_t* hi;
-  uint64_t* lo;
-  uint32_t* minrow;
-  uint32_t* kid;
-  uint32_t* next;
+  Bucket* b;
+  uint32_t* next;  // [slot] first position of the slot's run in the sorted candidates
   uint64_t mask;
 };
 
@@ -526,9 +533,10 @@ __device__ __forceinline__ uint64_t find_key(const EmitArgs& A, uint64_t hi, uin
                                              uint64_t f) {
   uint64_t slot = f & A.T.mask;
   for (int probe = 0; probe < kMaxProbe; ++probe) {
-    const unsigned long long g = A.T.fp[slot];
-    if (g == 0ull) return ~0ull;
-    if (g == (unsigned long long)f && A.T.hi[slot] == hi && A.T.lo[slot] == lo) return slot;
+    const Bucket& bk = A.T.b[slot];
+    const unsigned long long g = bk.fp;
+    if (g == ~0ull) return ~0ull;
+    if (g == (unsigned long long)f && bk.hi == hi && bk.lo == lo) return slot;
     slot = (slot + 1) & A.T.mask;
   }
   return ~0ull;
@@ -542,10 +550,10 @@ __device__ __forceinline__ uint64_t insert_key(const EmitArgs& A, uint64_t hi, u
   uint64_t slot = f & A.T.mask;
   int probe = 0;
   for (; probe < kMaxProbe; ++probe) {
-    const unsigned long long prev = atomicCAS(A.T.fp + slot, 0ull, (unsigned long long)f);
-    if (prev == 0ull) {
-      A.T.hi[slot] = hi;
-      A.T.lo[slot] = lo;
+    const unsigned long long prev = atomicCAS(&A.T.b[slot].fp, ~0ull, (unsigned long long)f);
+    if (prev == ~0ull) {
+      A.T.b[slot].hi = hi;
+      A.T.b[slot].lo = lo;
       break;
     }
     if (prev == (unsigned long long)f) break;
@@ -577,7 +585,7 @@ __device__ __forceinline__ void warp_emit(const EmitArgs& A, bool pred, uint64_t
   if (kMode == kModeLabel) {
     if ((hi >> 55) & 1ull) return;  // specular keys only
     const uint64_t slot = find_key(A, hi, lo, f);
-    if (slot != ~0ull && A.key_status[A.T.kid[slot]] == 1u) n_mine = 1u;
+    if (slot != ~0ull && A.key_status[A.T.b[slot].kid] == 1u) n_mine = 1u;
     return;
   }
   const unsigned peers = __match_any_sync(act, f);
@@ -591,7 +599,7 @@ __device__ __forceinline__ void warp_emit(const EmitArgs& A, bool pred, uint64_t
   uint64_t slot = 0;
   if (lane == leader) {
     slot = insert_key(A, hi, lo, f, ctr);
-    if (slot != ~0ull) atomicMin(A.T.minrow + slot, minrow);
+    if (slot != ~0ull) atomicMin(&A.T.b[slot].minrow, minrow);
   }
   slot = __shfl_sync(peers, slot, leader);
   if (slot == ~0ull) return;
@@ -695,8 +703,8 @@ __global__ void slot_flags_kernel(Table T, int64_t cap, uint32_t* __restrict__ f
                                   uint32_t* __restrict__ fd) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const bool used = T.fp[i] != 0ull;
-    const bool diff = used && ((T.hi[i] >> 55) & 1ull);
+    const bool used = T.b[i].fp != ~0ull;
+    const bool diff = used && ((T.b[i].hi >> 55) & 1ull);
     fs[i] = used && !diff;
     fd[i] = diff;
   }
@@ -731,11 +739,11 @@ __global__ void slot_assign_kernel(SceneView S, Records R, Table T, int64_t cap,
     if (!fs[i] && !fd[i]) continue;
     const uint32_t kid = fs[i] ? os[i] : n_spec + od[i];
     NRT_GUARD(kid < g_dbg_caps.keys, 1, kid)
-    NRT_GUARD(T.minrow[i] < g_dbg_caps.rows, 2, T.minrow[i])
-    T.kid[i] = kid;
+    NRT_GUARD(T.b[i].minrow < g_dbg_caps.rows, 2, T.b[i].minrow)
+    T.b[i].kid = kid;
     key_slot[kid] = (uint32_t)i;
-    const uint32_t m = T.minrow[i];
-    const uint64_t hi = T.hi[i];
+    const uint32_t m = T.b[i].minrow;
+    const uint64_t hi = T.b[i].hi;
     const int k = (int)((hi >> 52) & 7);
     int vox[3] = {0, 0, 0};
     if (k >= 1) voxel_of(S, xyz(R.q[R.at(k - 1, m)]), vox);
@@ -783,7 +791,7 @@ __global__ void verify_kernel(SceneView S, SimConst C, Records R, Table T, const
     const uint2 e = cand[c];
     NRT_GUARD(e.x < g_dbg_caps.table, 21, e.x)
     NRT_GUARD(e.y < g_dbg_caps.rows, 22, e.y)
-    const uint64_t hi = T.hi[e.x], lo = T.lo[e.x];
+    const uint64_t hi = T.b[e.x].hi, lo = T.b[e.x].lo;
     NRT_GUARD(((hi >> 52) & 7) >= 1 && ((hi >> 52) & 7) <= (uint64_t)C.max_depth, 23, hi >> 52)
     const int j = (int)(hi >> 56);
     const int diffuse = (int)((hi >> 55) & 1);
@@ -890,7 +898,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
       have = true;
     }
     NRT_GUARD(row < g_dbg_caps.rows, 7, row)
-    const uint64_t hi = A.T.hi[slot];
+    const uint64_t hi = A.T.b[slot].hi;
     const int j = (int)(hi >> 56);
     const int k = (int)((hi >> 52) & 7);
     NRT_GUARD(k >= 1 && k <= C.max_depth, 8, k)
@@ -913,7 +921,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
     if (valid) {
       memset(&P, 0, sizeof(P));
       P.hi = hi;
-      P.lo = A.T.lo[slot];
+      P.lo = A.T.b[slot].lo;
       P.rep = row;
       P.jtk = (uint32_t)j | (1u << 8) | ((uint32_t)k << 9);
       float ri = 0.0f;
@@ -985,8 +993,8 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
       NRT_GUARD(slot < g_dbg_caps.table, 10, slot)
       row = A.K.cur[kid];
       pos = A.K.pos[kid];
-      hi = A.T.hi[slot];
-      lo = A.T.lo[slot];
+      hi = A.T.b[slot].hi;
+      lo = A.T.b[slot].lo;
       NRT_GUARD(((hi >> 52) & 7) >= 1 && ((hi >> 52) & 7) <= (uint64_t)C.max_depth, 12, hi >> 52)
       j = (int)(hi >> 56);
       k = (int)((hi >> 52) & 7);
@@ -1150,8 +1158,8 @@ __global__ void key_summary_kernel(const unsigned long long* __restrict__ n_keys
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_keys;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t slot = K.slot[i];
-    hi[i] = T.hi[slot];
-    lo[i] = T.lo[slot];
+    hi[i] = T.b[slot].hi;
+    lo[i] = T.b[slot].lo;
     const bool valid = K.status[i] == 1u;
     tried[i] = K.tries[i] + (valid ? 1u : 0u);
     const uint32_t row = K.cur[i];
@@ -1833,11 +1841,7 @@ cudaError_t dalloc(T** p, int64_t n, cudaStream_t st) {
 
 nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cudaStream_t st) {
   W.caps = c;
-  TRY(dalloc(&W.T.fp, c.table, st));
-  TRY(dalloc(&W.T.hi, c.table, st));
-  TRY(dalloc(&W.T.lo, c.table, st));
-  TRY(dalloc(&W.T.minrow, c.table, st));
-  TRY(dalloc(&W.T.kid, c.table, st));
+  TRY(dalloc(&W.T.b, c.table, st));
   TRY(dalloc(&W.T.next, c.table, st));
   W.T.mask = (uint64_t)c.table - 1;
   TRY(dalloc(&W.K.slot, c.keys, st));
@@ -1869,7 +1873,7 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
 }
 
 void release_work(Work& W, cudaStream_t st) {
-  void* ptrs[] = {W.T.fp, W.T.hi, W.T.lo, W.T.minrow, W.T.kid, W.T.next, W.K.slot, W.K.cur, W.K.pos,
+  void* ptrs[] = {W.T.b, W.T.next, W.K.slot, W.K.cur, W.K.pos,
                   W.K.tries, W.K.status, W.spec_list, W.diff_list, W.cand,
                   W.cand2, W.cand_cnt, W.cand_off, W.fs, W.fd, W.os, W.od, W.sk0, W.tk0,
                   W.sv0, W.tv, W.raw, W.psk, W.ptk, W.psi, W.pti, W.cnt, W.order};
@@ -1970,8 +1974,7 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   unsigned long long* ctr = r->ctr;
   Records R{r->rec_q, r->rec_n, r->rec_d, r->rec_i, n};
 
-  TRY(cudaMemsetAsync(W.T.fp, 0, c.table * 8, st));
-  TRY(cudaMemsetAsync(W.T.minrow, 0xFF, c.table * 4, st));
+  TRY(cudaMemsetAsync(W.T.b, 0xFF, c.table * sizeof(Bucket), st));
   TRY(cudaMemsetAsync(W.cnt, 0, kCntN * 8, st));
   EmitArgs A{};
   A.T = W.T;
