@@ -542,7 +542,7 @@ def ours(args):
     per_val = ((n_diff * ab["bytes_per_shadow_cast"] + n_spec * ab["bytes_per_segment"])
                / max(counts["validation_casts"], 1))
     roof = roof_entry("validation phase: validate_specular_kernel + validate_diffuse_kernel "
-                      "(8 rounds)", counts["validation_casts"], per_val, ph["validate"],
+                      "(one launch each)", counts["validation_casts"], per_val, ph["validate"],
                       "validation cast", "validation")
     tr_ms = float(np.mean(trace_ms))
     roof_more = [
