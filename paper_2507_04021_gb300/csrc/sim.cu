@@ -2034,9 +2034,9 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   V.SC = SC;
   // every key walks its candidates in ray order inside one launch per type
   TRY(cudaMemsetAsync(W.cnt + kCntFetchS, 0, 16, st));
-  validate_specular_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
+  validate_specular_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 6), kTraceThreads, 0, st>>>(
       S, C, V, W.spec_list, W.cnt + kCntSpec, W.cnt + kCntFetchS, ctr); count_launch();
-  validate_diffuse_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
+  validate_diffuse_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 6), kTraceThreads, 0, st>>>(
       S, C, V, W.diff_list, W.cnt + kCntDiff, W.cnt + kCntFetchD, ctr); count_launch();
   if (r->ev[5]) TRY(cudaEventRecord(r->ev[5], st));
   if (r->p.keep_keys) {
