@@ -252,14 +252,19 @@ nrt_status nrt_cast(nrt_scene* scene, const float* o, const float* d, int64_t n,
  *   lowest-ray-id candidate that validates represents a key (diffuse: a
  *   cast scatter point -> RX; specular: image-method refinement on the
  *   interaction planes, Eq. 1, validated by casts with thresholds t_a, t_d
- *   and up to kappa retries); then the field of every path.
+ *   and up to kappa retries); with `diffraction`, one single-bounce
+ *   diffracted path per (edge, RX) that passes its checks (Sec. II-B-3);
+ *   then the field of every path (`pol`).
  *   tx : host float[3];  rx : host float[n_rx][3] (n_rx <= 256)
  *   ray_subset : NULL, or uint32[n_subset] ray ids < n_rays (host, or device
  *                when subset_on_device)
  * Key layout: hi = [rx:8 @56][diffuse:1 @55][k:3 @52][low 52 bits]; specular:
  * lo = l1 | l2<<16 | l3<<32 | l4<<48, hi low 16 bits = l5; diffuse: lo =
  * labels of the k-1 specular interactions, hi low 48 bits = scatter voxel
- * x | y<<16 | z<<32 (each taken modulo 2^16).
+ * x | y<<16 | z<<32 (each taken modulo 2^16); diffracted: hi = rx << 56 |
+ * 1 << 52 | 1 << 51, lo = edge index.  The outputs do not depend on the order
+ * in which the GPU hands rays and keys to its lanes: the same inputs give
+ * bit-identical paths.
  * Errors: NRT_ERR_ARG, NRT_ERR_OOM, NRT_ERR_OVERFLOW (hash table or candidate
  * buffer too small: raise key_capacity / cand_capacity), NRT_ERR_CUDA. */
 nrt_status nrt_trace(nrt_scene* scene, const float* tx, const float* rx, int n_rx,

@@ -1829,11 +1829,11 @@ struct Work {
   PathRec* raw = nullptr;
   uint64_t *psk = nullptr, *ptk = nullptr;
   uint32_t *psi = nullptr, *pti = nullptr;
-  unsigned long long* cnt = nullptr;  // round counters
+  unsigned long long* cnt = nullptr;  // key counts and work counters
   uint32_t* order = nullptr;          // launch order owned by this call (subset / batch)
 };
 
-// round counters in Work::cnt
+// key counts and work-fetch counters in Work::cnt
 enum { kCntSpec = 0, kCntDiff, kCntKeys, kCntFetchS, kCntFetchD, kCntN };
 
 template <class T>
