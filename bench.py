@@ -334,6 +334,36 @@ def diffraction_bench(ctx, o, tx, stream, rays):
     return out
 
 
+def rp_variant_bench(ctx, o, tx, stream, rays, r_p=0.025):
+    """The office simulation with the larger disc radius r_p = 0.025 m (the
+    second radius of the office configuration): device time (median of 3
+    after a warm-up), counts and ray segments per second."""
+    import torch
+    from paper_2507_04021_gb300 import nrt
+
+    sc = nrt.Scene(ctx, o.pos, o.nrm, o.surf, o.mat, rho=0.0625, r_p=r_p, lambda_d=100.0)
+    sc.set_materials(o.eps_r, o.sigma, o.scat)
+    p = nrt.default_trace_params(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=rays,
+                                 rep_tries=8)
+    sc.trace(tx, o.rx, p).close()
+    ms = []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = sc.trace(tx, o.rx, p)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        _, c = r.counts()
+        r.close()
+    t = float(np.median(ms))
+    casts = c["segments"] + c["vis_casts"] + c["los_casts"] + c["validation_casts"]
+    return {"r_p": r_p, "ms": t, "ray_segments_per_s": casts / (t / 1e3),
+            "counts": {k: c[k] for k in ("segments", "vis_casts", "validation_casts", "keys",
+                                         "paths")}}
+
+
 def _face_plane(surf, boxes, room=(20.0, 10.0, 3.0)):
     """(axis, offset) of the office's planar face with surface label surf."""
     if surf < 6:
@@ -585,6 +615,7 @@ def ours(args):
         line["launch_comparison"] = launch_bench(scene, o, tx, stream)
         line["diffraction"] = diffraction_bench(ctx, o, tx, stream, args.rays)
         line["intersection_ablation"] = isect_bench(scene, o, stream)
+        line["r_p_variant"] = rp_variant_bench(ctx, o, tx, stream, args.rays)
     if args.proposal and rank == 0:
         line["proposal"] = proposal_bench(scene, o)
     if args.batch_pairs > 0:
