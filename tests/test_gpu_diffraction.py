@@ -187,3 +187,40 @@ def test_edge_input_checks(ctx, room):
         res.backward_noalloc(dldp, grad)
     res.close()
     sc.set_edges(None)
+
+
+def test_cfr_and_eq5_gradient_with_diffraction(ctx, room, room_orc, room_edges):
+    """The CFR and the Eq. 5 gradient include the diffracted paths (room
+    wedges, vector model) and match the oracle's under the same bound as the
+    other path types: per frequency |dH| <= sum_p |a_p| (1e-4 + 2 pi f tau_p
+    1e-6)."""
+    from oracle import cfr
+
+    sc = _room_scene(ctx, room, room_edges, tuple(m.astype(np.float32) for m in MATS))
+    kp = dict(max_depth=2, capture=nrt.CAPTURE_VIS, diffuse=0, n_rays=4000, rep_tries=8,
+              pol=nrt.POL_VECTOR, diffraction=1)
+    res = sc.trace(room.tx, RX4, nrt.default_trace_params(**kp))
+    osim = oracle.OracleSim(room_orc, room.tx, RX4, oracle.SimParams(**kp), edges=room_edges)
+    BW, NF = 1.5e9, 129
+    f = cfr.freqs(28e9, BW, NF)
+    P = osim.paths()
+    assert (P["type"] == 2).sum() > 10
+    a, _ = osim.field(*MATS)
+    Ho = cfr.cfr(a, P["tau"], P["j"], RX4.shape[0], f)
+    H = res.cfr(BW, NF)
+    amp = np.abs(a)
+    bound = np.stack([(amp[P["j"] == j, None] * (1e-4 + 2 * np.pi * f[None, :] *
+                                                  P["tau"][P["j"] == j, None] * 1e-6)).sum(0)
+                      for j in range(RX4.shape[0])])
+    assert np.all(np.abs(H - Ho) <= bound)
+    hidden = (np.array([4.1, 2.4]), np.array([0.05, 0.002]), np.array([0.45, 0.1]))
+    a_h, _ = osim.field(*hidden)
+    T = cfr.cfr(a_h, P["tau"], P["j"], RX4.shape[0], f)
+    w = np.array([1.0, 0.5, 0.25, 2.0])
+    loss, g = res.cfr_backward(T, w, BW)
+    go = cfr.eq5_grad(osim.path_grads(*MATS), P["tau"], P["j"], f, Ho, T, w)
+    assert np.allclose(loss, cfr.eq5_loss(Ho, T), rtol=1e-2, atol=1e-4)
+    for t in range(2):  # eps_r, sigma (S does not enter diffraction; it does the reflections)
+        rel = np.abs(g[t] - go[t]) / np.maximum(np.abs(go[t]), 1e-2 * np.abs(go).max())
+        assert rel.max() < 2e-2, t
+    res.close()
