@@ -88,3 +88,34 @@ def test_vector_path_grads_match_central_differences():
     sim_te = oracle.OracleSim(osc, room.tx, RX, oracle.SimParams(max_depth=2, capture=1, diffuse=1,
                                                                  n_rays=4000, rep_tries=8, pol=0))
     assert not np.allclose(np.abs(sim.field(*MATS)[0]), np.abs(sim_te.field(*MATS)[0]))
+
+
+def _theta(d):
+    h = np.hypot(d[0], d[1])
+    if h < 1e-12:
+        return np.array([1.0, 0.0, 0.0])
+    return np.array([d[2] * d[0] / h, d[2] * d[1] / h, -h])
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_perfect_conductor_chain_equals_vector_image_maps(k):
+    """With Gamma_TE = -1 and Gamma_TM = +1 (a perfect conductor) every
+    reflection maps the field vector by the image rule E -> -E + 2 (E.n) n
+    (tangential part reversed, normal part kept); the 2x2 basis chain must
+    equal that plain 3D computation on random multi-bounce geometry."""
+    rng = np.random.default_rng(10 + k)
+    for _ in range(20):
+        tx = rng.uniform(-2, 2, 3)
+        rx = rng.uniform(-2, 2, 3)
+        pts = rng.uniform(-3, 3, (k, 3))
+        chain = [tx] + list(pts) + [rx]
+        d = [(chain[m + 1] - chain[m]) / np.linalg.norm(chain[m + 1] - chain[m])
+             for m in range(k + 1)]
+        E = _theta(d[0])
+        for m in range(k):
+            n = d[m + 1] - d[m]
+            n /= np.linalg.norm(n)
+            E = -E + 2.0 * (E @ n) * n
+        want = E @ _theta(-d[k])
+        got = oracle.jones_amplitude(tx, rx, pts, [[-1.0, 1.0]] * k)
+        assert got == pytest.approx(want, abs=1e-10)
