@@ -204,3 +204,29 @@ def test_diffracted_path_derivatives_match_central_differences(pol):
             scale = np.abs(fd[dif]).max() + 1e-30
             assert np.allclose(G[dif, t, l], fd[dif], atol=1e-6 * scale, rtol=1e-5), (t, l)
     assert np.all(G[dif, 2, :] == 0)  # no roughness dependence
+
+
+@pytest.mark.parametrize("pol", [0, 1])
+def test_perfect_conductor_wedge_is_reciprocal(pol):
+    """For a perfect conductor (R0 = Rn = -/+1) the wedge coefficient is
+    symmetric in (phi, phi') and the spreading in (s, s'): exchanging TX and
+    RX gives the same diffracted field, on random wedges and positions."""
+    rng = np.random.default_rng(21 + pol)
+    E = inputs.room_edges(16, seed=99)
+    checked = 0
+    for i in range(len(E)):
+        for _ in range(6):
+            tx = rng.uniform((0.3, 0.3, 0.3), (4.7, 3.7, 2.7))
+            rx = rng.uniform((0.3, 0.3, 0.3), (4.7, 3.7, 2.7))
+            # |eta| = 1e30: Gamma_TM departs from +1 by ~2 / (cos sqrt|eta|), so the
+            # perfect-conductor limit holds to 1e-12 even at grazing incidence
+            pec = complex(1e30, -1e30)
+            args = (E.a[i], E.b[i], E.n0[i], E.n1[i], pec, pec, F0, pol)
+            ab = oracle.diffraction_amplitude(tx, rx, *args)
+            ba = oracle.diffraction_amplitude(rx, tx, *args)
+            assert (ab is None) == (ba is None)
+            if ab is None:
+                continue
+            assert ab == pytest.approx(ba, rel=1e-9)
+            checked += 1
+    assert checked > 10
