@@ -147,8 +147,12 @@ struct alignas(16) PathRec {
 static_assert(sizeof(PathRec) == 144, "PathRec layout");
 
 void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t st);
+// n = capacity of the buffers (sets the grid); n_dev, if given, is the live
+// count on the device (at most n): only the first *n_dev entries are sorted
+// and the rest of keys/vals is left undefined
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
-                      int bits, cudaStream_t st, int lo_bit = 0);
+                      int bits, cudaStream_t st, int lo_bit = 0,
+                      const unsigned long long* n_dev = nullptr);
 
 SceneView scene_view(const nrt_scene* s);
 

@@ -95,9 +95,17 @@ constexpr int kSortRounds = 16;
 constexpr int kSortTile = kSortThreads * kSortRounds;
 constexpr int kWarps = kSortThreads / 32;
 
-__global__ void radix_hist_kernel(const uint64_t* __restrict__ keys, int64_t n, int shift,
+// n_dev (optional): the live element count on the device; entries past it
+// are neither counted nor moved
+__device__ __forceinline__ int64_t live_count(int64_t cap, const unsigned long long* n_dev) {
+  return n_dev ? min((int64_t)*n_dev, cap) : cap;
+}
+
+__global__ void radix_hist_kernel(const uint64_t* __restrict__ keys, int64_t cap,
+                                  const unsigned long long* __restrict__ n_dev, int shift,
                                   uint32_t* __restrict__ counts, int n_blocks) {
   __shared__ uint32_t h[256];
+  const int64_t n = live_count(cap, n_dev);
   h[threadIdx.x] = 0;
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
@@ -114,10 +122,13 @@ __global__ void radix_hist_kernel(const uint64_t* __restrict__ keys, int64_t n, 
 // per-warp digit counts in shared memory.
 __global__ void radix_scatter_kernel(const uint64_t* __restrict__ kin,
                                      const uint32_t* __restrict__ vin, uint64_t* __restrict__ kout,
-                                     uint32_t* __restrict__ vout, int64_t n, int shift,
+                                     uint32_t* __restrict__ vout, int64_t cap,
+                                     const unsigned long long* __restrict__ n_dev, int shift,
                                      const uint32_t* __restrict__ offsets, int n_blocks) {
   __shared__ uint32_t run[256];
   __shared__ uint32_t wcnt[kWarps][256];
+  const int64_t n = live_count(cap, n_dev);
+  if ((int64_t)blockIdx.x * kSortTile >= n) return;  // a tile past the live count moves nothing
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   run[tid] = offsets[(int64_t)tid * n_blocks + blockIdx.x];
   for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
@@ -164,7 +175,7 @@ __global__ void radix_scatter_kernel(const uint64_t* __restrict__ kin,
 // input order).  The result ends in keys/vals; tk/tv are scratch of n
 // entries; vals (and tv) may be null for a keys-only sort.
 void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv, int64_t n,
-                      int bits, cudaStream_t st, int lo_bit) {
+                      int bits, cudaStream_t st, int lo_bit, const unsigned long long* n_dev) {
   if (n <= 1) return;
   const int n_blocks = (int)((n + kSortTile - 1) / kSortTile);
   uint32_t *counts = nullptr, *offs = nullptr;
@@ -174,10 +185,10 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv
   uint32_t *va = vals, *vb = tv;
   int passes = 0;
   for (int shift = lo_bit; shift < bits; shift += 8, ++passes) {
-    radix_hist_kernel<<<n_blocks, kSortThreads, 0, st>>>(ka, n, shift, counts, n_blocks);
+    radix_hist_kernel<<<n_blocks, kSortThreads, 0, st>>>(ka, n, n_dev, shift, counts, n_blocks);
     scan_exclusive(counts, offs, (int64_t)256 * n_blocks, st);
-    radix_scatter_kernel<<<n_blocks, kSortThreads, 0, st>>>(ka, va, kb, vb, n, shift, offs,
-                                                            n_blocks);
+    radix_scatter_kernel<<<n_blocks, kSortThreads, 0, st>>>(ka, va, kb, vb, n, n_dev, shift,
+                                                            offs, n_blocks);
     count_launch(2);
     std::swap(ka, kb);
     std::swap(va, vb);

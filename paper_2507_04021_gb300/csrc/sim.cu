@@ -90,7 +90,6 @@ static_assert(sizeof(Bucket) == 32, "Bucket layout");
 
 struct Table {
   Bucket* b;
-  uint32_t* next;  // [slot] first position of the slot's run in the sorted candidates
   uint64_t mask;
 };
 
@@ -102,10 +101,10 @@ struct KeyState {
   uint32_t* status;  // 0 pending, 1 valid, 2 invalid
 };
 
-// Candidates sorted once by (table slot, row): a key's candidates form one
-// run in ray order, so its next candidate is the next element of the run.
+// Candidates sorted once by (key id, row): a key's candidates form one run in
+// ray order, so its next candidate is the next element of the run.
 struct SortedCand {
-  const uint64_t* key;  // (slot << row_bits) | row; padding ~0 sorts last
+  const uint64_t* key;  // (key id << row_bits) | row
   const unsigned long long* n_p;
   int64_t cap;
   int row_bits;
@@ -725,14 +724,16 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x) {
 // leave from one region toward the receivers, so the region's BVH nodes and
 // discs are read once for all receivers and the receivers' neighbourhoods
 // stay in L2 (measured against RX-first order: 1.6 ms less validation time
-// per office simulation).
+// per office simulation).  The fields are packed tight (jb bits of RX, mb =
+// 3 x grid bits of Morton code, one type bit) so that the sort takes as few
+// 8-bit passes as the scene needs.
 __global__ void slot_assign_kernel(SceneView S, Records R, Table T, int64_t cap,
                                    const uint32_t* __restrict__ fs,
                                    const uint32_t* __restrict__ fd, const uint32_t* __restrict__ os,
                                    const uint32_t* __restrict__ od,
                                    const unsigned long long* __restrict__ counts,
                                    uint32_t* __restrict__ key_slot, uint64_t* __restrict__ sort_key,
-                                   uint32_t* __restrict__ sort_val) {
+                                   uint32_t* __restrict__ sort_val, int jb, int mb) {
   const uint32_t n_spec = (uint32_t)counts[0];  // diffuse ids follow the specular ones
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -747,9 +748,11 @@ __global__ void slot_assign_kernel(SceneView S, Records R, Table T, int64_t cap,
     const int k = (int)((hi >> 52) & 7);
     int vox[3] = {0, 0, 0};
     if (k >= 1) voxel_of(S, xyz(R.q[R.at(k - 1, m)]), vox);
-    const uint32_t mort = spread3((uint32_t)max(vox[0], 0)) | (spread3((uint32_t)max(vox[1], 0)) << 1) |
-                          (spread3((uint32_t)max(vox[2], 0)) << 2);
-    sort_key[kid] = ((uint64_t)(fs[i] ? 0u : 1u) << 38) | ((uint64_t)mort << 8) | (hi >> 56);
+    const int vmax = (1 << (mb / 3)) - 1;  // Morton fields stay inside their mb bits
+    const uint32_t mort = spread3((uint32_t)min(max(vox[0], 0), vmax)) |
+                          (spread3((uint32_t)min(max(vox[1], 0), vmax)) << 1) |
+                          (spread3((uint32_t)min(max(vox[2], 0), vmax)) << 2);
+    sort_key[kid] = ((uint64_t)(fs[i] ? 0u : 1u) << (jb + mb)) | ((uint64_t)mort << jb) | (hi >> 56);
     sort_val[kid] = kid;
   }
 }
@@ -780,10 +783,13 @@ __global__ void split_lists_kernel(const uint32_t* __restrict__ sorted, int64_t 
 
 // Every candidate re-derives its key from the hit records and compares it
 // with the key stored in its slot: a 64-bit fingerprint collision between
-// distinct keys is reported, never silently merged.
-__global__ void verify_kernel(SceneView S, SimConst C, Records R, Table T, const uint2* __restrict__ cand,
+// distinct keys is reported, never silently merged.  The candidate (slot,
+// row) is then replaced, in place, by its sort key (key id << row_bits) |
+// row: the key id sits in the bucket just read, and sorting on it takes
+// ceil(log2(keys)) bits instead of the table's.
+__global__ void verify_kernel(SceneView S, SimConst C, Records R, Table T, uint2* cand,
                               const unsigned long long* __restrict__ n_cand_p, int64_t cap,
-                              unsigned long long* ctr) {
+                              int row_bits, unsigned long long* ctr) {
   uint32_t* err = (uint32_t*)(ctr + kCtrErr);
   const int64_t n_cand = min((int64_t)*n_cand_p, cap);
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cand;
@@ -803,6 +809,9 @@ __global__ void verify_kernel(SceneView S, SimConst C, Records R, Table T, const
     uint64_t h2, l2;
     make_key(j, diffuse, k, lab, vox, &h2, &l2);
     if (h2 != hi || l2 != lo) atomicOr(err, kErrKeyMismatch);
+    const uint32_t kid = T.b[e.x].kid;
+    NRT_GUARD(kid < g_dbg_caps.keys, 4, kid)
+    reinterpret_cast<uint64_t*>(cand)[c] = ((uint64_t)kid << row_bits) | (uint64_t)e.y;
   }
 }
 
@@ -820,10 +829,10 @@ struct ValArgs {
 
 // Outcome of one try of key kid (candidate row *row at position *pos of the
 // sorted candidates): a valid path is recorded; otherwise the key moves to
-// its next candidate -- the next element of its slot's run, i.e. the next
-// larger ray id -- unless it has used rep_tries tries or has no candidate
-// left.  Returns true when the key is finished.
-__device__ __forceinline__ bool key_try(const ValArgs& A, uint32_t kid, uint32_t slot, bool valid,
+// its next candidate -- the next element of its run, i.e. the next larger
+// ray id -- unless it has used rep_tries tries or has no candidate left.
+// Returns true when the key is finished.
+__device__ __forceinline__ bool key_try(const ValArgs& A, uint32_t kid, bool valid,
                                         const PathRec* rec, uint32_t* row, uint32_t* pos,
                                         unsigned long long* ctr, const SimConst& C) {
   uint32_t* err = (uint32_t*)(ctr + kCtrErr);
@@ -846,7 +855,7 @@ __device__ __forceinline__ bool key_try(const ValArgs& A, uint32_t kid, uint32_t
   const int64_t n_cand = min((int64_t)*A.SC.n_p, A.SC.cap);
   const int64_t q = (int64_t)*pos + 1;
   const uint64_t e = q < n_cand ? A.SC.key[q] : ~0ull;
-  if (q >= n_cand || (e >> A.SC.row_bits) != (uint64_t)slot) {
+  if (q >= n_cand || (e >> A.SC.row_bits) != (uint64_t)kid) {
     A.K.status[kid] = 2;
     return true;
   }
@@ -947,7 +956,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6)
               sqrtf(rho * rho * ci * cs / 3.14159265358979f) / (ri * rs);
       P.length = ri + rs;
     }
-    if (key_try(A, kid, slot, valid, &P, &row, &pos, ctr, C)) have = false;
+    if (key_try(A, kid, valid, &P, &row, &pos, ctr, C)) have = false;
   }
   count_add(ctr + kCtrValCasts, casts);
   count_add(ctr + kCtrDiffCasts, casts);
@@ -1116,36 +1125,28 @@ __global__ void __launch_bounds__(kTraceThreads, 6)
       P.length = len;
       P.geo = C.lambda / (4.0f * 3.14159265358979f * len);
     }
-    if (key_try(A, kid, slot, valid, &P, &row, &pos, ctr, C)) have = false;
+    if (key_try(A, kid, valid, &P, &row, &pos, ctr, C)) have = false;
     else fresh = true;
   }
   count_add(ctr + kCtrValCasts, casts);
 }
 
-// (slot, row) candidates -> sort keys, in place; entries past the count are
-// padding that sorts last
-__global__ void cand_key_kernel(uint2* __restrict__ cand, const unsigned long long* __restrict__ n_p,
-                                int64_t cap, int row_bits) {
-  const int64_t n = min((int64_t)*n_p, cap);
-  uint64_t* key = reinterpret_cast<uint64_t*>(cand);
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < cap;
-       c += (int64_t)gridDim.x * blockDim.x) {
-    if (c >= n) {
-      key[c] = ~0ull;
-      continue;
-    }
-    const uint2 e = cand[c];
-    key[c] = ((uint64_t)e.x << row_bits) | (uint64_t)e.y;
-  }
-}
-
-// first position of every slot's run
-__global__ void run_start_kernel(SortedCand SC, uint32_t* __restrict__ start) {
+// Every key starts at the first (lowest-row) candidate of its run.  cur, pos,
+// tries and status are zeroed beforehand, so a key left without a run (a
+// result that overflowed its candidate capacity reports an error) still
+// points at a candidate inside the arrays.
+__global__ void run_start_kernel(SortedCand SC, KeyState K) {
   const int64_t n = min((int64_t)*SC.n_p, SC.cap);
+  const uint64_t row_mask = (1ull << SC.row_bits) - 1ull;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t s = SC.key[c] >> SC.row_bits;
-    if (c == 0 || (SC.key[c - 1] >> SC.row_bits) != s) start[s] = (uint32_t)c;
+    const uint64_t e = SC.key[c];
+    const uint64_t kid = e >> SC.row_bits;
+    if (c == 0 || (SC.key[c - 1] >> SC.row_bits) != kid) {
+      NRT_GUARD(kid < g_dbg_caps.keys, 19, kid)
+      K.pos[kid] = (uint32_t)c;
+      K.cur[kid] = (uint32_t)(e & row_mask);
+    }
   }
 }
 
@@ -1169,21 +1170,6 @@ __global__ void key_summary_kernel(const unsigned long long* __restrict__ n_keys
   }
 }
 
-// every key starts at the first (lowest-row) candidate of its run
-__global__ void key_init_kernel(const unsigned long long* __restrict__ n_keys_p, KeyState K,
-                                const uint32_t* __restrict__ run_start, SortedCand SC) {
-  const int64_t n_keys = (int64_t)*n_keys_p;
-  const uint64_t row_mask = (1ull << SC.row_bits) - 1ull;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_keys;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    NRT_GUARD(K.slot[i] < g_dbg_caps.table, 19, K.slot[i])
-    const uint32_t p = run_start[K.slot[i]];
-    K.pos[i] = p;
-    K.cur[i] = (uint32_t)(SC.key[p] & row_mask);
-    K.tries[i] = 0;
-    K.status[i] = 0;
-  }
-}
 
 // ---------------------------------------------------------------- ordering
 // Paths ordered by (rx, type, k, representative row): deterministic output.
@@ -1194,13 +1180,9 @@ __global__ void path_sortkey_kernel(const PathRec* __restrict__ p,
                                     int row_bits, uint64_t* __restrict__ key,
                                     uint32_t* __restrict__ idx) {
   const int64_t n = min((int64_t)*n_p, cap);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     idx[i] = (uint32_t)i;
-    if (i >= n) {
-      key[i] = ~0ull;  // padding sorts last
-      continue;
-    }
     const uint32_t jtk = p[i].jtk;
     const bool dfr = (jtk >> 12) & 1;  // diffracted paths last: class (1, 6)
     const uint64_t j = jtk & 0xFF, ty = dfr ? 1 : (jtk >> 8) & 1, k = dfr ? 6 : (jtk >> 9) & 7;
@@ -1844,7 +1826,6 @@ cudaError_t dalloc(T** p, int64_t n, cudaStream_t st) {
 nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cudaStream_t st) {
   W.caps = c;
   TRY(dalloc(&W.T.b, c.table, st));
-  TRY(dalloc(&W.T.next, c.table, st));
   W.T.mask = (uint64_t)c.table - 1;
   TRY(dalloc(&W.K.slot, c.keys, st));
   TRY(dalloc(&W.K.cur, c.keys, st));
@@ -1875,7 +1856,7 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
 }
 
 void release_work(Work& W, cudaStream_t st) {
-  void* ptrs[] = {W.T.b, W.T.next, W.K.slot, W.K.cur, W.K.pos,
+  void* ptrs[] = {W.T.b, W.K.slot, W.K.cur, W.K.pos,
                   W.K.tries, W.K.status, W.spec_list, W.diff_list, W.cand,
                   W.cand2, W.cand_cnt, W.cand_off, W.fs, W.fd, W.os, W.od, W.sk0, W.tk0,
                   W.sv0, W.tv, W.raw, W.psk, W.ptk, W.psi, W.pti, W.cnt, W.order};
@@ -1991,31 +1972,36 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   scan_exclusive(W.fs, W.os, c.table, st);
   scan_exclusive(W.fd, W.od, c.table, st);
   key_count_kernel<<<1, 1, 0, st>>>(W.fs, W.fd, W.os, W.od, c.table, W.cnt); count_launch();
-  TRY(cudaMemsetAsync(W.sk0, 0xFF, c.keys * 8, st));
+  // key ids are dense in [0, keys): the sort takes the live count from the
+  // device and leaves the rest of the capacity alone
+  const int nj = C.batch ? C.n_pairs : r->n_rx_phys;
+  int jb = 0;
+  while ((1 << jb) < nj) ++jb;
+  const int mb = 3 * std::min(sc->grid_bits, 10);  // spread3 keeps 10 bits per axis
   slot_assign_kernel<<<blocks_for(c.table, 256, sm), 256, 0, st>>>(
-      S, R, W.T, c.table, W.fs, W.fd, W.os, W.od, W.cnt, W.K.slot, W.sk0, W.sv0); count_launch();
-  radix_sort_pairs(W.sk0, W.sv0, W.tk0, W.tv, c.keys, 40, st);
+      S, R, W.T, c.table, W.fs, W.fd, W.os, W.od, W.cnt, W.K.slot, W.sk0, W.sv0, jb, mb); count_launch();
+  radix_sort_pairs(W.sk0, W.sv0, W.tk0, W.tv, c.keys, 1 + jb + mb, st, 0, W.cnt + kCntKeys);
   split_lists_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.sv0, c.keys, W.cnt, W.spec_list,
                                                                  W.diff_list); count_launch();
   TRY(cudaMemcpyAsync(ctr + kCtrKeys, W.cnt + kCntKeys, 8, cudaMemcpyDeviceToDevice, st));
-  verify_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(S, C, R, W.T, W.cand, ctr + kCtrCands,
-                                                            c.cand, ctr); count_launch();
-  // candidates sorted by (slot, row) once; T.next holds each slot's run start
-  int row_bits = 1, table_bits = 0;
+  // candidates sorted by (key id, row) once: verify writes the sort keys
+  int row_bits = 1, kid_bits = 1;
   while ((1ll << row_bits) < n) ++row_bits;
-  while ((1ll << table_bits) < c.table) ++table_bits;
-  cand_key_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(W.cand, ctr + kCtrCands, c.cand,
-                                                              row_bits); count_launch();
+  while ((1ll << kid_bits) < c.keys) ++kid_bits;
+  verify_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(S, C, R, W.T, W.cand, ctr + kCtrCands,
+                                                            c.cand, row_bits, ctr); count_launch();
   // the candidates are in ascending row order (offsets per row), so a stable
-  // sort on the slot bits alone leaves each run in ray order
+  // sort on the key-id bits alone leaves each run in ray order
   radix_sort_pairs(reinterpret_cast<uint64_t*>(W.cand), nullptr, reinterpret_cast<uint64_t*>(W.cand2),
-                   nullptr, c.cand, row_bits + table_bits, st, row_bits);
+                   nullptr, c.cand, row_bits + kid_bits, st, row_bits, ctr + kCtrCands);
   const SortedCand SC{reinterpret_cast<const uint64_t*>(W.cand), ctr + kCtrCands, c.cand, row_bits};
-  run_start_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(SC, W.T.next); count_launch();
-  key_init_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.cnt + kCntKeys, W.K, W.T.next, SC); count_launch();
+  TRY(cudaMemsetAsync(W.K.cur, 0, c.keys * sizeof(uint32_t), st));
+  TRY(cudaMemsetAsync(W.K.pos, 0, c.keys * sizeof(uint32_t), st));
+  TRY(cudaMemsetAsync(W.K.tries, 0, c.keys * sizeof(uint32_t), st));
+  TRY(cudaMemsetAsync(W.K.status, 0, c.keys * sizeof(uint32_t), st));
+  run_start_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(SC, W.K); count_launch();
 
   // LOS paths first, then candidates in ray-id order until one validates
-  const int nj = C.batch ? C.n_pairs : r->n_rx_phys;
   los_kernel<<<(nj + kTraceThreads - 1) / kTraceThreads, kTraceThreads, 0, st>>>(
       S, C, r->rx, W.raw, ctr, c.paths); count_launch();
   if (r->p.diffraction && sc->n_edges > 0) {
@@ -2061,7 +2047,7 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
     while ((1ll << path_bits) < sc->n_edges) ++path_bits;
   path_sortkey_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>(W.raw, ctr + kCtrPaths, c.paths,
                                                                    path_bits, W.psk, W.psi); count_launch();
-  radix_sort_pairs(W.psk, W.psi, W.ptk, W.pti, c.paths, path_bits + 12, st);
+  radix_sort_pairs(W.psk, W.psi, W.ptk, W.pti, c.paths, path_bits + 12, st, 0, ctr + kCtrPaths);
   path_gather_kernel<<<blocks_for(c.paths, 256, sm), 256, 0, st>>>(W.raw, W.psi, ctr + kCtrPaths,
                                                                   c.paths, (PathRec*)r->paths); count_launch();
   rx_range_kernel<<<(r->n_rx + 63) / 64, 64, 0, st>>>(W.psk, ctr + kCtrPaths, c.paths, r->n_rx,
