@@ -28,7 +28,7 @@ enum : uint32_t {
   kErrStack = 1u << 0,       // traversal stack would overflow
   kErrHashFull = 1u << 1,    // hash probe limit reached
   kErrCandFull = 1u << 2,    // candidate buffer full
-  kErrKeyMismatch = 1u << 3, // 64-bit fingerprint collision between distinct keys
+  // 1u << 3 is unused
   kErrPathFull = 1u << 4,    // path buffer full
   kErrTimeout = 1u << 5,     // bounded loop gave up
 };
@@ -340,8 +340,8 @@ __device__ __forceinline__ void make_key(int j, int diffuse, int k, const uint16
   *lo = l;
 }
 
-// 64-bit fingerprint of a key: the splitmix64 finaliser applied to a
-// combination of both words; all-ones is reserved for "empty".
+// 64-bit hash of a key (the start of its probe sequence): the splitmix64
+// finaliser applied to a combination of both words.
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   x ^= x >> 30;
   x *= 0xbf58476d1ce4e5b9ull;
@@ -350,9 +350,8 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x) {
   x ^= x >> 31;
   return x;
 }
-__device__ __forceinline__ uint64_t key_fp(uint64_t hi, uint64_t lo) {
-  uint64_t f = mix64(hi ^ mix64(lo + 0x9E3779B97F4A7C15ull));
-  return f != ~0ull ? f : 1ull;
+__device__ __forceinline__ uint64_t key_hash(uint64_t hi, uint64_t lo) {
+  return mix64(hi ^ mix64(lo + 0x9E3779B97F4A7C15ull));
 }
 
 // voxel of a point, floor((q - bmin) / rho), as in the scene build

@@ -78,15 +78,23 @@ inline cudaError_t dbg_set_caps(int64_t table, int64_t keys, int64_t cand, int64
 namespace {
 
 // One hash slot in one 32-byte sector: an insert or a lookup touches one
-// sector.  All-ones is the empty fingerprint and the initial minrow, so one
-// 0xFF fill initialises the table.
+// sector.  The slot holds the whole 128-bit key, claimed by one 128-bit
+// compare-and-swap, so two distinct keys never share a slot.  All-ones is
+// the empty key (no key has all three bits of its k field set) and the
+// initial minrow, so one 0xFF fill initialises the table.
+struct alignas(16) Key128 {
+  unsigned long long hi, lo;
+};
 struct alignas(32) Bucket {
-  unsigned long long fp;  // ~0 = empty
-  uint64_t hi, lo;
-  uint32_t minrow;        // lowest row among the key's candidates
-  uint32_t kid;           // key id
+  uint64_t hi, lo;  // the key (the first 16 bytes, a Key128); all-ones = empty
+  uint32_t minrow;  // lowest row among the key's candidates
+  uint32_t kid;     // key id
+  uint64_t spare;
 };
 static_assert(sizeof(Bucket) == 32, "Bucket layout");
+__device__ __forceinline__ bool key_empty(uint64_t hi, uint64_t lo) {
+  return hi == ~0ull && lo == ~0ull;
+}
 
 struct Table {
   Bucket* b;
@@ -532,30 +540,27 @@ __device__ __forceinline__ uint64_t find_key(const EmitArgs& A, uint64_t hi, uin
                                              uint64_t f) {
   uint64_t slot = f & A.T.mask;
   for (int probe = 0; probe < kMaxProbe; ++probe) {
-    const Bucket& bk = A.T.b[slot];
-    const unsigned long long g = bk.fp;
-    if (g == ~0ull) return ~0ull;
-    if (g == (unsigned long long)f && bk.hi == hi && bk.lo == lo) return slot;
+    const Key128 g = *reinterpret_cast<const Key128*>(&A.T.b[slot]);
+    if (key_empty(g.hi, g.lo)) return ~0ull;
+    if (g.hi == hi && g.lo == lo) return slot;
     slot = (slot + 1) & A.T.mask;
   }
   return ~0ull;
 }
 
-// Hash insert by one lane on behalf of the lanes holding the same key (same
-// fingerprint); returns the slot.  No shared counters are touched: key ids
-// are assigned afterwards from the table's occupancy.
+// Hash insert by one lane on behalf of the lanes holding the same key;
+// returns the slot.  The probe sequence starts at the key's hash f; a slot
+// is claimed, or found to hold the key already, by one 128-bit
+// compare-and-swap.  No shared counters are touched: key ids are assigned
+// afterwards from the table's occupancy.
 __device__ __forceinline__ uint64_t insert_key(const EmitArgs& A, uint64_t hi, uint64_t lo,
                                                uint64_t f, unsigned long long* ctr) {
   uint64_t slot = f & A.T.mask;
+  const Key128 empty{~0ull, ~0ull}, mine{hi, lo};
   int probe = 0;
   for (; probe < kMaxProbe; ++probe) {
-    const unsigned long long prev = atomicCAS(&A.T.b[slot].fp, ~0ull, (unsigned long long)f);
-    if (prev == ~0ull) {
-      A.T.b[slot].hi = hi;
-      A.T.b[slot].lo = lo;
-      break;
-    }
-    if (prev == (unsigned long long)f) break;
+    const Key128 prev = atomicCAS(reinterpret_cast<Key128*>(&A.T.b[slot]), empty, mine);
+    if (key_empty(prev.hi, prev.lo) || (prev.hi == hi && prev.lo == lo)) break;
     slot = (slot + 1) & A.T.mask;
   }
   if (probe == kMaxProbe) {
@@ -580,14 +585,14 @@ __device__ __forceinline__ void warp_emit(const EmitArgs& A, bool pred, uint64_t
   const unsigned act = __ballot_sync(0xFFFFFFFFu, pred);
   if (!act || !pred) return;
   const int lane = threadIdx.x & 31;
-  const uint64_t f = key_fp(hi, lo);
+  const uint64_t f = key_hash(hi, lo);
   if (kMode == kModeLabel) {
     if ((hi >> 55) & 1ull) return;  // specular keys only
     const uint64_t slot = find_key(A, hi, lo, f);
     if (slot != ~0ull && A.key_status[A.T.b[slot].kid] == 1u) n_mine = 1u;
     return;
   }
-  const unsigned peers = __match_any_sync(act, f);
+  const unsigned peers = __match_any_sync(act, hi) & __match_any_sync(act, lo);  // equal keys
   const int leader = __ffs(peers) - 1;
   if (kMode == kModeCount) {
     ++n_mine;
@@ -702,7 +707,7 @@ __global__ void slot_flags_kernel(Table T, int64_t cap, uint32_t* __restrict__ f
                                   uint32_t* __restrict__ fd) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const bool used = T.b[i].fp != ~0ull;
+    const bool used = !key_empty(T.b[i].hi, T.b[i].lo);
     const bool diff = used && ((T.b[i].hi >> 55) & 1ull);
     fs[i] = used && !diff;
     fd[i] = diff;
@@ -788,34 +793,17 @@ __global__ void split_lists_kernel(const uint32_t* __restrict__ sorted, int64_t 
   }
 }
 
-// Every candidate re-derives its key from the hit records and compares it
-// with the key stored in its slot: a 64-bit fingerprint collision between
-// distinct keys is reported, never silently merged.  The candidate (slot,
-// row) is then replaced, in place, by its sort key (key id << row_bits) |
-// row: the key id sits in the bucket just read, and sorting on it takes
+// Candidates (slot, row) -> sort keys (key id << row_bits) | row, in place:
+// the key id sits in the slot's bucket, and sorting on it takes
 // ceil(log2(keys)) bits instead of the table's.
-__global__ void verify_kernel(SceneView S, SimConst C, Records R, Table T, uint2* cand,
-                              const unsigned long long* __restrict__ n_cand_p, int64_t cap,
-                              int row_bits, unsigned long long* ctr) {
-  uint32_t* err = (uint32_t*)(ctr + kCtrErr);
+__global__ void cand_key_kernel(Table T, uint2* cand, const unsigned long long* __restrict__ n_cand_p,
+                                int64_t cap, int row_bits) {
   const int64_t n_cand = min((int64_t)*n_cand_p, cap);
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cand;
        c += (int64_t)gridDim.x * blockDim.x) {
     const uint2 e = cand[c];
     NRT_GUARD(e.x < g_dbg_caps.table, 21, e.x)
     NRT_GUARD(e.y < g_dbg_caps.rows, 22, e.y)
-    const uint64_t hi = T.b[e.x].hi, lo = T.b[e.x].lo;
-    NRT_GUARD(((hi >> 52) & 7) >= 1 && ((hi >> 52) & 7) <= (uint64_t)C.max_depth, 23, hi >> 52)
-    const int j = (int)(hi >> 56);
-    const int diffuse = (int)((hi >> 55) & 1);
-    const int k = (int)((hi >> 52) & 7);
-    uint16_t lab[kMaxDepth];
-    for (int s = 0; s < k; ++s) lab[s] = (uint16_t)(R.i[R.at(s, e.y)].y & 0xFFFF);
-    int vox[3] = {0, 0, 0};
-    if (diffuse) voxel_of(S, xyz(R.q[R.at(k - 1, e.y)]), vox);
-    uint64_t h2, l2;
-    make_key(j, diffuse, k, lab, vox, &h2, &l2);
-    if (h2 != hi || l2 != lo) atomicOr(err, kErrKeyMismatch);
     const uint32_t kid = T.b[e.x].kid;
     NRT_GUARD(kid < g_dbg_caps.keys, 4, kid)
     reinterpret_cast<uint64_t*>(cand)[c] = ((uint64_t)kid << row_bits) | (uint64_t)e.y;
@@ -1992,12 +1980,12 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   split_lists_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.sv0, c.keys, W.cnt, W.spec_list,
                                                                  W.diff_list); count_launch();
   TRY(cudaMemcpyAsync(ctr + kCtrKeys, W.cnt + kCntKeys, 8, cudaMemcpyDeviceToDevice, st));
-  // candidates sorted by (key id, row) once: verify writes the sort keys
+  // candidates sorted by (key id, row) once
   int row_bits = 1, kid_bits = 1;
   while ((1ll << row_bits) < n) ++row_bits;
   while ((1ll << kid_bits) < c.keys) ++kid_bits;
-  verify_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(S, C, R, W.T, W.cand, ctr + kCtrCands,
-                                                            c.cand, row_bits, ctr); count_launch();
+  cand_key_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(W.T, W.cand, ctr + kCtrCands, c.cand,
+                                                              row_bits); count_launch();
   // the candidates are in ascending row order (offsets per row), so a stable
   // sort on the key-id bits alone leaves each run in ray order
   radix_sort_pairs(reinterpret_cast<uint64_t*>(W.cand), nullptr, reinterpret_cast<uint64_t*>(W.cand2),
@@ -2112,8 +2100,8 @@ nrt_status finish_result(nrt_result* r) {
   c.kernel_launches = launch_counter();
   c.diffuse_casts = (int64_t)hc[kCtrDiffCasts];
   c.diffraction_casts = (int64_t)hc[kCtrDfrCasts];
-  if (c.error_flags & (kErrHashFull | kErrCandFull | kErrPathFull | kErrKeyMismatch)) {
-    ctx->last_error = "device buffer overflow or key fingerprint collision (flags " +
+  if (c.error_flags & (kErrHashFull | kErrCandFull | kErrPathFull)) {
+    ctx->last_error = "device buffer overflow (flags " +
                       std::to_string(c.error_flags) + ")";
     return NRT_ERR_OVERFLOW;
   }
