@@ -80,15 +80,15 @@ namespace {
 // One hash slot in one 32-byte sector: an insert or a lookup touches one
 // sector.  The slot holds the whole 128-bit key, claimed by one 128-bit
 // compare-and-swap, so two distinct keys never share a slot.  All-ones is
-// the empty key (no key has all three bits of its k field set) and the
-// initial minrow, so one 0xFF fill initialises the table.
+// the empty key (no key has all three bits of its k field set), so one 0xFF
+// fill initialises the table.
 struct alignas(16) Key128 {
   unsigned long long hi, lo;
 };
 struct alignas(32) Bucket {
   uint64_t hi, lo;  // the key (the first 16 bytes, a Key128); all-ones = empty
-  uint32_t minrow;  // lowest row among the key's candidates
   uint32_t kid;     // key id
+  uint32_t spare32;
   uint64_t spare;
 };
 static_assert(sizeof(Bucket) == 32, "Bucket layout");
@@ -573,8 +573,8 @@ __device__ __forceinline__ uint64_t insert_key(const EmitArgs& A, uint64_t hi, u
 
 // One candidate per lane with pred set (all lanes of the warp call this
 // together).  Lanes with equal keys are merged first: one lane inserts the
-// key and records the group's lowest row; every lane still stores its own
-// (slot, row) candidate, at its ray's next candidate position.  The count
+// key; every lane still stores its own (slot, row) candidate, at its ray's
+// next candidate position.  The count
 // mode only counts candidates per ray and per-warp distinct keys (an upper
 // bound on the table's keys); the label mode sets n_mine to 1 when the key
 // is a validated specular key.
@@ -599,12 +599,8 @@ __device__ __forceinline__ void warp_emit(const EmitArgs& A, bool pred, uint64_t
     if (lane == leader) ++n_lead;
     return;
   }
-  const uint32_t minrow = __reduce_min_sync(peers, row);
   uint64_t slot = 0;
-  if (lane == leader) {
-    slot = insert_key(A, hi, lo, f, ctr);
-    if (slot != ~0ull) atomicMin(&A.T.b[slot].minrow, minrow);
-  }
+  if (lane == leader) slot = insert_key(A, hi, lo, f, ctr);
   slot = __shfl_sync(peers, slot, leader);
   if (slot == ~0ull) return;
   if (n_mine < A.cand_cap) A.cand[n_mine] = make_uint2((uint32_t)slot, row);
@@ -702,15 +698,65 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Key ids from the table's occupancy: specular keys first, then diffuse.
-__global__ void slot_flags_kernel(Table T, int64_t cap, uint32_t* __restrict__ fs,
-                                  uint32_t* __restrict__ fd) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const bool used = !key_empty(T.b[i].hi, T.b[i].lo);
-    const bool diff = used && ((T.b[i].hi >> 55) & 1ull);
-    fs[i] = used && !diff;
-    fd[i] = diff;
+// Key ids from the table's occupancy: specular keys first, then diffuse,
+// each in slot order.  The table is cut into tiles of kSlotTile slots, one
+// block each; thread t of a block owns the kSlotPer consecutive slots from
+// t * kSlotPer.  A first pass counts each tile's keys of both types, the
+// tile counts are scanned, and the assigning pass ranks the slots inside
+// its tile with a block-wide scan -- no per-slot flag or offset arrays.
+constexpr int kSlotThreads = 256;
+constexpr int kSlotPer = 16;
+constexpr int kSlotTile = kSlotThreads * kSlotPer;
+
+// occupancy masks of the calling thread's slots (bit r: slot first + r)
+__device__ __forceinline__ void slot_masks(const Table& T, int64_t cap, int64_t first,
+                                           uint32_t* ms, uint32_t* md) {
+  uint32_t s = 0, d = 0;
+  for (int r = 0; r < kSlotPer; ++r) {
+    const int64_t i = first + r;
+    if (i >= cap) break;
+    const Key128 g = *reinterpret_cast<const Key128*>(&T.b[i]);
+    if (key_empty(g.hi, g.lo)) continue;
+    if ((g.hi >> 55) & 1ull) d |= 1u << r;
+    else s |= 1u << r;
+  }
+  *ms = s;
+  *md = d;
+}
+
+// Exclusive block-wide prefix of v (two 16-bit counts packed in one word:
+// a tile holds at most kSlotTile = 4096 keys of each type) and the block
+// total.  All kSlotThreads threads call it.
+__device__ __forceinline__ uint32_t block_prefix(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_sum[kSlotThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, off);
+    if (lane >= off) x += y;
+  }
+  if (lane == 31) warp_sum[w] = x;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+  for (int k = 0; k < kSlotThreads / 32; ++k) {
+    if (k < w) before += warp_sum[k];
+    all += warp_sum[k];
+  }
+  __syncthreads();  // warp_sum may be reused by a later call
+  *total = all;
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kSlotThreads)
+    slot_count_kernel(Table T, int64_t cap, uint32_t* __restrict__ tile_s,
+                      uint32_t* __restrict__ tile_d) {
+  const int64_t first = (int64_t)blockIdx.x * kSlotTile + (int64_t)threadIdx.x * kSlotPer;
+  uint32_t ms, md, total;
+  slot_masks(T, cap, first, &ms, &md);
+  block_prefix((uint32_t)__popc(ms) | ((uint32_t)__popc(md) << 16), &total);
+  if (threadIdx.x == 0) {
+    tile_s[blockIdx.x] = total & 0xFFFFu;
+    tile_d[blockIdx.x] = total >> 16;
   }
 }
 
@@ -724,9 +770,34 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x) {
   return x;
 }
 
+__global__ void __launch_bounds__(kSlotThreads)
+    slot_assign_kernel(Table T, int64_t cap, const uint32_t* __restrict__ tile_os,
+                       const uint32_t* __restrict__ tile_od,
+                       const unsigned long long* __restrict__ counts,
+                       uint32_t* __restrict__ key_slot) {
+  const uint32_t n_spec = (uint32_t)counts[0];  // diffuse ids follow the specular ones
+  const int64_t first = (int64_t)blockIdx.x * kSlotTile + (int64_t)threadIdx.x * kSlotPer;
+  uint32_t ms, md, total;
+  slot_masks(T, cap, first, &ms, &md);
+  const uint32_t pre =
+      block_prefix((uint32_t)__popc(ms) | ((uint32_t)__popc(md) << 16), &total);
+  uint32_t next_s = tile_os[blockIdx.x] + (pre & 0xFFFFu);
+  uint32_t next_d = n_spec + tile_od[blockIdx.x] + (pre >> 16);
+  for (int r = 0; r < kSlotPer; ++r) {
+    const bool spec = (ms >> r) & 1u, diff = (md >> r) & 1u;
+    if (!spec && !diff) continue;
+    const int64_t i = first + r;
+    const uint32_t kid = spec ? next_s++ : next_d++;
+    NRT_GUARD(kid < g_dbg_caps.keys, 1, kid)
+    T.b[i].kid = kid;
+    key_slot[kid] = (uint32_t)i;
+  }
+}
+
 // Validation order of a key: type, the coarse Morton code of the voxel of its
-// lowest row's last interaction point, the RX (pair), then the fine Morton
-// code (the low fb bits).  Diffuse keys take fb = 0 (voxel, then RX): a
+// lowest row's last interaction point (the lowest row is the first
+// candidate of the key's run), the RX (pair), then the fine Morton code (the
+// low fb bits).  Diffuse keys take fb = 0 (voxel, then RX): a
 // warp's shadow casts leave one voxel toward the receivers, so the region's
 // BVH nodes and discs are read once for all receivers.  Specular keys take
 // cells of 16 voxels per axis (fb = 12), then the RX: a warp's image-method
@@ -736,24 +807,19 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x) {
 // flat from 9 to 15; RX-first order, fb = mb, 15.4 ms).  The fields are
 // packed tight (jb bits of RX, mb = 3 x grid bits of Morton code, one type
 // bit) so that the sort takes as few 8-bit passes as the scene needs.
-__global__ void slot_assign_kernel(SceneView S, Records R, Table T, int64_t cap,
-                                   const uint32_t* __restrict__ fs,
-                                   const uint32_t* __restrict__ fd, const uint32_t* __restrict__ os,
-                                   const uint32_t* __restrict__ od,
-                                   const unsigned long long* __restrict__ counts,
-                                   uint32_t* __restrict__ key_slot, uint64_t* __restrict__ sort_key,
-                                   uint32_t* __restrict__ sort_val, int jb, int mb, int fb_spec) {
-  const uint32_t n_spec = (uint32_t)counts[0];  // diffuse ids follow the specular ones
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    if (!fs[i] && !fd[i]) continue;
-    const uint32_t kid = fs[i] ? os[i] : n_spec + od[i];
-    NRT_GUARD(kid < g_dbg_caps.keys, 1, kid)
-    NRT_GUARD(T.b[i].minrow < g_dbg_caps.rows, 2, T.b[i].minrow)
-    T.b[i].kid = kid;
-    key_slot[kid] = (uint32_t)i;
-    const uint32_t m = T.b[i].minrow;
-    const uint64_t hi = T.b[i].hi;
+__global__ void val_order_kernel(SceneView S, Records R, Table T, KeyState K,
+                                 const unsigned long long* __restrict__ counts,
+                                 uint64_t* __restrict__ sort_key, uint32_t* __restrict__ sort_val,
+                                 int jb, int mb, int fb_spec) {
+  const int64_t n_keys = (int64_t)counts[2];
+  for (int64_t kid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; kid < n_keys;
+       kid += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t slot = K.slot[kid];
+    NRT_GUARD(slot < g_dbg_caps.table, 2, slot)
+    const uint32_t m = K.cur[kid];  // lowest row: the first candidate of the key's run
+    NRT_GUARD(m < g_dbg_caps.rows, 27, m)
+    const uint64_t hi = T.b[slot].hi;
+    const bool spec = !((hi >> 55) & 1ull);
     const int k = (int)((hi >> 52) & 7);
     int vox[3] = {0, 0, 0};
     if (k >= 1) voxel_of(S, xyz(R.q[R.at(k - 1, m)]), vox);
@@ -761,20 +827,20 @@ __global__ void slot_assign_kernel(SceneView S, Records R, Table T, int64_t cap,
     const uint32_t mort = spread3((uint32_t)min(max(vox[0], 0), vmax)) |
                           (spread3((uint32_t)min(max(vox[1], 0), vmax)) << 1) |
                           (spread3((uint32_t)min(max(vox[2], 0), vmax)) << 2);
-    const int fb = fs[i] ? fb_spec : 0;
+    const int fb = spec ? fb_spec : 0;
     const uint64_t fine = (uint64_t)mort & ((1ull << fb) - 1ull);
-    sort_key[kid] = ((uint64_t)(fs[i] ? 0u : 1u) << (jb + mb)) | ((uint64_t)(mort >> fb) << (jb + fb)) |
+    sort_key[kid] = ((uint64_t)(spec ? 0u : 1u) << (jb + mb)) | ((uint64_t)(mort >> fb) << (jb + fb)) |
                     ((hi >> 56) << fb) | fine;
-    sort_val[kid] = kid;
+    sort_val[kid] = (uint32_t)kid;
   }
 }
 
-// key counts from the scan tails: [0] specular, [1] diffuse, [2] all
+// key counts from the tile-count scan tails: [0] specular, [1] diffuse, [2] all
 __global__ void key_count_kernel(const uint32_t* __restrict__ fs, const uint32_t* __restrict__ fd,
                                  const uint32_t* __restrict__ os, const uint32_t* __restrict__ od,
-                                 int64_t cap, unsigned long long* __restrict__ out) {
-  const unsigned long long ns = (unsigned long long)os[cap - 1] + fs[cap - 1];
-  const unsigned long long nd = (unsigned long long)od[cap - 1] + fd[cap - 1];
+                                 int64_t n, unsigned long long* __restrict__ out) {
+  const unsigned long long ns = (unsigned long long)os[n - 1] + fs[n - 1];
+  const unsigned long long nd = (unsigned long long)od[n - 1] + fd[n - 1];
   out[0] = ns;
   out[1] = nd;
   out[2] = ns + nd;
@@ -1800,7 +1866,7 @@ struct Work {
   uint32_t *spec_list = nullptr, *diff_list = nullptr;
   uint2 *cand = nullptr, *cand2 = nullptr;
   uint32_t *cand_cnt = nullptr, *cand_off = nullptr;
-  uint32_t *fs = nullptr, *fd = nullptr, *os = nullptr, *od = nullptr;
+  uint32_t *fs = nullptr, *fd = nullptr, *os = nullptr, *od = nullptr;  // per-tile key counts, scans
   uint64_t *sk0 = nullptr, *tk0 = nullptr;
   uint32_t *sv0 = nullptr, *tv = nullptr;
   PathRec* raw = nullptr;
@@ -1833,10 +1899,11 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
   TRY(dalloc(&W.cand2, c.cand, st));
   if (!W.cand_cnt) TRY(dalloc(&W.cand_cnt, n_rows, st));
   if (!W.cand_off) TRY(dalloc(&W.cand_off, n_rows, st));
-  TRY(dalloc(&W.fs, c.table, st));
-  TRY(dalloc(&W.fd, c.table, st));
-  TRY(dalloc(&W.os, c.table, st));
-  TRY(dalloc(&W.od, c.table, st));
+  const int64_t n_tiles = (c.table + kSlotTile - 1) / kSlotTile;  // per-tile key counts
+  TRY(dalloc(&W.fs, n_tiles, st));
+  TRY(dalloc(&W.fd, n_tiles, st));
+  TRY(dalloc(&W.os, n_tiles, st));
+  TRY(dalloc(&W.od, n_tiles, st));
   TRY(dalloc(&W.sk0, c.keys, st));
   TRY(dalloc(&W.tk0, c.keys, st));
   TRY(dalloc(&W.sv0, c.keys, st));
@@ -1963,22 +2030,13 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
 
   // key ids from the occupied slots, specular first, each type in launch
   // order of the key's lowest row
-  slot_flags_kernel<<<blocks_for(c.table, 256, sm), 256, 0, st>>>(W.T, c.table, W.fs, W.fd); count_launch();
-  scan_exclusive(W.fs, W.os, c.table, st);
-  scan_exclusive(W.fd, W.od, c.table, st);
-  key_count_kernel<<<1, 1, 0, st>>>(W.fs, W.fd, W.os, W.od, c.table, W.cnt); count_launch();
-  // key ids are dense in [0, keys): the sort takes the live count from the
-  // device and leaves the rest of the capacity alone
-  const int nj = C.batch ? C.n_pairs : r->n_rx_phys;
-  int jb = 0;
-  while ((1 << jb) < nj) ++jb;
-  const int mb = 3 * std::min(sc->grid_bits, 10);  // spread3 keeps 10 bits per axis
-  const int fb_spec = std::min(12, mb);  // specular: cells of 16 voxels per axis
-  slot_assign_kernel<<<blocks_for(c.table, 256, sm), 256, 0, st>>>(
-      S, R, W.T, c.table, W.fs, W.fd, W.os, W.od, W.cnt, W.K.slot, W.sk0, W.sv0, jb, mb, fb_spec); count_launch();
-  radix_sort_pairs(W.sk0, W.sv0, W.tk0, W.tv, c.keys, 1 + jb + mb, st, 0, W.cnt + kCntKeys);
-  split_lists_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.sv0, c.keys, W.cnt, W.spec_list,
-                                                                 W.diff_list); count_launch();
+  const int64_t n_tiles = (c.table + kSlotTile - 1) / kSlotTile;
+  slot_count_kernel<<<(unsigned)n_tiles, kSlotThreads, 0, st>>>(W.T, c.table, W.fs, W.fd); count_launch();
+  scan_exclusive(W.fs, W.os, n_tiles, st);
+  scan_exclusive(W.fd, W.od, n_tiles, st);
+  key_count_kernel<<<1, 1, 0, st>>>(W.fs, W.fd, W.os, W.od, n_tiles, W.cnt); count_launch();
+  slot_assign_kernel<<<(unsigned)n_tiles, kSlotThreads, 0, st>>>(W.T, c.table, W.os, W.od, W.cnt,
+                                                                W.K.slot); count_launch();
   TRY(cudaMemcpyAsync(ctr + kCtrKeys, W.cnt + kCntKeys, 8, cudaMemcpyDeviceToDevice, st));
   // candidates sorted by (key id, row) once
   int row_bits = 1, kid_bits = 1;
@@ -1996,6 +2054,19 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   TRY(cudaMemsetAsync(W.K.tries, 0, c.keys * sizeof(uint32_t), st));
   TRY(cudaMemsetAsync(W.K.status, 0, c.keys * sizeof(uint32_t), st));
   run_start_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(SC, W.K); count_launch();
+
+  // validation order of the keys; key ids are dense in [0, keys): the sort
+  // takes the live count from the device and leaves the rest alone
+  const int nj = C.batch ? C.n_pairs : r->n_rx_phys;
+  int jb = 0;
+  while ((1 << jb) < nj) ++jb;
+  const int mb = 3 * std::min(sc->grid_bits, 10);  // spread3 keeps 10 bits per axis
+  const int fb_spec = std::min(12, mb);  // specular: cells of 16 voxels per axis
+  val_order_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(S, R, W.T, W.K, W.cnt, W.sk0, W.sv0,
+                                                               jb, mb, fb_spec); count_launch();
+  radix_sort_pairs(W.sk0, W.sv0, W.tk0, W.tv, c.keys, 1 + jb + mb, st, 0, W.cnt + kCntKeys);
+  split_lists_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.sv0, c.keys, W.cnt, W.spec_list,
+                                                                 W.diff_list); count_launch();
 
   // LOS paths first, then candidates in ray-id order until one validates
   los_kernel<<<(nj + kTraceThreads - 1) / kTraceThreads, kTraceThreads, 0, st>>>(
