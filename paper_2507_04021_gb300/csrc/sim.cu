@@ -77,27 +77,23 @@ inline cudaError_t dbg_set_caps(int64_t table, int64_t keys, int64_t cand, int64
 
 namespace {
 
-// One hash slot in one 32-byte sector: an insert or a lookup touches one
-// sector.  The slot holds the whole 128-bit key, claimed by one 128-bit
-// compare-and-swap, so two distinct keys never share a slot.  All-ones is
-// the empty key (no key has all three bits of its k field set), so one 0xFF
-// fill initialises the table.
+// One hash slot is the whole 128-bit key (16 bytes, two slots per 32-byte
+// sector), claimed by one 128-bit compare-and-swap, so two distinct keys
+// never share a slot.  All-ones is the empty key (no key has all three bits
+// of its k field set), so one 0xFF fill initialises the table.  Key ids live
+// in a separate array, kid[slot], written once the table is complete: the
+// candidate pass reads 4 bytes per candidate from it instead of a bucket.
 struct alignas(16) Key128 {
   unsigned long long hi, lo;
 };
-struct alignas(32) Bucket {
-  uint64_t hi, lo;  // the key (the first 16 bytes, a Key128); all-ones = empty
-  uint32_t kid;     // key id
-  uint32_t spare32;
-  uint64_t spare;
-};
-static_assert(sizeof(Bucket) == 32, "Bucket layout");
+static_assert(sizeof(Key128) == 16, "Key128 layout");
 __device__ __forceinline__ bool key_empty(uint64_t hi, uint64_t lo) {
   return hi == ~0ull && lo == ~0ull;
 }
 
 struct Table {
-  Bucket* b;
+  Key128* b;      // [slot] key; all-ones = empty
+  uint32_t* kid;  // [slot] key id of an occupied slot
   uint64_t mask;
 };
 
@@ -540,7 +536,7 @@ __device__ __forceinline__ uint64_t find_key(const EmitArgs& A, uint64_t hi, uin
                                              uint64_t f) {
   uint64_t slot = f & A.T.mask;
   for (int probe = 0; probe < kMaxProbe; ++probe) {
-    const Key128 g = *reinterpret_cast<const Key128*>(&A.T.b[slot]);
+    const Key128 g = A.T.b[slot];
     if (key_empty(g.hi, g.lo)) return ~0ull;
     if (g.hi == hi && g.lo == lo) return slot;
     slot = (slot + 1) & A.T.mask;
@@ -559,7 +555,7 @@ __device__ __forceinline__ uint64_t insert_key(const EmitArgs& A, uint64_t hi, u
   const Key128 empty{~0ull, ~0ull}, mine{hi, lo};
   int probe = 0;
   for (; probe < kMaxProbe; ++probe) {
-    const Key128 prev = atomicCAS(reinterpret_cast<Key128*>(&A.T.b[slot]), empty, mine);
+    const Key128 prev = atomicCAS(&A.T.b[slot], empty, mine);
     if (key_empty(prev.hi, prev.lo) || (prev.hi == hi && prev.lo == lo)) break;
     slot = (slot + 1) & A.T.mask;
   }
@@ -589,7 +585,7 @@ __device__ __forceinline__ void warp_emit(const EmitArgs& A, bool pred, uint64_t
   if (kMode == kModeLabel) {
     if ((hi >> 55) & 1ull) return;  // specular keys only
     const uint64_t slot = find_key(A, hi, lo, f);
-    if (slot != ~0ull && A.key_status[A.T.b[slot].kid] == 1u) n_mine = 1u;
+    if (slot != ~0ull && A.key_status[A.T.kid[slot]] == 1u) n_mine = 1u;
     return;
   }
   const unsigned peers = __match_any_sync(act, hi) & __match_any_sync(act, lo);  // equal keys
@@ -715,7 +711,7 @@ __device__ __forceinline__ void slot_masks(const Table& T, int64_t cap, int64_t 
   for (int r = 0; r < kSlotPer; ++r) {
     const int64_t i = first + r;
     if (i >= cap) break;
-    const Key128 g = *reinterpret_cast<const Key128*>(&T.b[i]);
+    const Key128 g = T.b[i];
     if (key_empty(g.hi, g.lo)) continue;
     if ((g.hi >> 55) & 1ull) d |= 1u << r;
     else s |= 1u << r;
@@ -789,7 +785,7 @@ __global__ void __launch_bounds__(kSlotThreads)
     const int64_t i = first + r;
     const uint32_t kid = spec ? next_s++ : next_d++;
     NRT_GUARD(kid < g_dbg_caps.keys, 1, kid)
-    T.b[i].kid = kid;
+    T.kid[i] = kid;
     key_slot[kid] = (uint32_t)i;
   }
 }
@@ -860,8 +856,7 @@ __global__ void split_lists_kernel(const uint32_t* __restrict__ sorted, int64_t 
 }
 
 // Candidates (slot, row) -> sort keys (key id << row_bits) | row, in place:
-// the key id sits in the slot's bucket, and sorting on it takes
-// ceil(log2(keys)) bits instead of the table's.
+// sorting on the key id takes ceil(log2(keys)) bits instead of the table's.
 __global__ void cand_key_kernel(Table T, uint2* cand, const unsigned long long* __restrict__ n_cand_p,
                                 int64_t cap, int row_bits) {
   const int64_t n_cand = min((int64_t)*n_cand_p, cap);
@@ -870,7 +865,7 @@ __global__ void cand_key_kernel(Table T, uint2* cand, const unsigned long long* 
     const uint2 e = cand[c];
     NRT_GUARD(e.x < g_dbg_caps.table, 21, e.x)
     NRT_GUARD(e.y < g_dbg_caps.rows, 22, e.y)
-    const uint32_t kid = T.b[e.x].kid;
+    const uint32_t kid = T.kid[e.x];
     NRT_GUARD(kid < g_dbg_caps.keys, 4, kid)
     reinterpret_cast<uint64_t*>(cand)[c] = ((uint64_t)kid << row_bits) | (uint64_t)e.y;
   }
@@ -1887,6 +1882,7 @@ cudaError_t dalloc(T** p, int64_t n, cudaStream_t st) {
 nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cudaStream_t st) {
   W.caps = c;
   TRY(dalloc(&W.T.b, c.table, st));
+  TRY(dalloc(&W.T.kid, c.table, st));
   W.T.mask = (uint64_t)c.table - 1;
   TRY(dalloc(&W.K.slot, c.keys, st));
   TRY(dalloc(&W.K.cur, c.keys, st));
@@ -1918,7 +1914,7 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
 }
 
 void release_work(Work& W, cudaStream_t st) {
-  void* ptrs[] = {W.T.b, W.K.slot, W.K.cur, W.K.pos,
+  void* ptrs[] = {W.T.b, W.T.kid, W.K.slot, W.K.cur, W.K.pos,
                   W.K.tries, W.K.status, W.spec_list, W.diff_list, W.cand,
                   W.cand2, W.cand_cnt, W.cand_off, W.fs, W.fd, W.os, W.od, W.sk0, W.tk0,
                   W.sv0, W.tv, W.raw, W.psk, W.ptk, W.psi, W.pti, W.cnt, W.order};
@@ -2019,7 +2015,7 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   unsigned long long* ctr = r->ctr;
   Records R{r->rec_q, r->rec_n, r->rec_d, r->rec_i, n};
 
-  TRY(cudaMemsetAsync(W.T.b, 0xFF, c.table * sizeof(Bucket), st));
+  TRY(cudaMemsetAsync(W.T.b, 0xFF, c.table * sizeof(Key128), st));
   TRY(cudaMemsetAsync(W.cnt, 0, kCntN * 8, st));
   EmitArgs A{};
   A.T = W.T;
