@@ -28,7 +28,7 @@ enum : uint32_t {
   kErrStack = 1u << 0,       // traversal stack would overflow
   kErrHashFull = 1u << 1,    // hash probe limit reached
   kErrCandFull = 1u << 2,    // candidate buffer full
-  // 1u << 3 is unused
+  kErrKeyFull = 1u << 3,     // more distinct keys than the key capacity
   kErrPathFull = 1u << 4,    // path buffer full
   kErrTimeout = 1u << 5,     // bounded loop gave up
 };

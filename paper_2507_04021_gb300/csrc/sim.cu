@@ -770,7 +770,7 @@ __global__ void __launch_bounds__(kSlotThreads)
     slot_assign_kernel(Table T, int64_t cap, const uint32_t* __restrict__ tile_os,
                        const uint32_t* __restrict__ tile_od,
                        const unsigned long long* __restrict__ counts,
-                       uint32_t* __restrict__ key_slot) {
+                       uint32_t* __restrict__ key_slot, int64_t key_cap) {
   const uint32_t n_spec = (uint32_t)counts[0];  // diffuse ids follow the specular ones
   const int64_t first = (int64_t)blockIdx.x * kSlotTile + (int64_t)threadIdx.x * kSlotPer;
   uint32_t ms, md, total;
@@ -784,9 +784,8 @@ __global__ void __launch_bounds__(kSlotThreads)
     if (!spec && !diff) continue;
     const int64_t i = first + r;
     const uint32_t kid = spec ? next_s++ : next_d++;
-    NRT_GUARD(kid < g_dbg_caps.keys, 1, kid)
-    T.kid[i] = kid;
-    key_slot[kid] = (uint32_t)i;
+    T.kid[i] = kid;  // ids at or past key_cap: keys over capacity, reported by key_count
+    if ((int64_t)kid < key_cap) key_slot[kid] = (uint32_t)i;
   }
 }
 
@@ -831,15 +830,23 @@ __global__ void val_order_kernel(SceneView S, Records R, Table T, KeyState K,
   }
 }
 
-// key counts from the tile-count scan tails: [0] specular, [1] diffuse, [2] all
+// key counts from the tile-count scan tails: [0] specular, [1] diffuse, [2]
+// all, clamped to the key capacity.  More keys than that (possible only
+// when the capacity was fixed ahead of the trace, as for a recorded graph)
+// raise kErrKeyFull; keys with ids at or past the capacity are left out.
 __global__ void key_count_kernel(const uint32_t* __restrict__ fs, const uint32_t* __restrict__ fd,
                                  const uint32_t* __restrict__ os, const uint32_t* __restrict__ od,
-                                 int64_t n, unsigned long long* __restrict__ out) {
+                                 int64_t n, int64_t key_cap, unsigned long long* __restrict__ out,
+                                 unsigned long long* __restrict__ ctr) {
   const unsigned long long ns = (unsigned long long)os[n - 1] + fs[n - 1];
   const unsigned long long nd = (unsigned long long)od[n - 1] + fd[n - 1];
-  out[0] = ns;
-  out[1] = nd;
-  out[2] = ns + nd;
+  const unsigned long long cap = (unsigned long long)key_cap;
+  if (ns + nd > cap) atomicOr((uint32_t*)(ctr + kCtrErr), kErrKeyFull);
+  const unsigned long long ns_c = ns < cap ? ns : cap;
+  const unsigned long long all = ns + nd < cap ? ns + nd : cap;
+  out[0] = ns_c;
+  out[1] = all - ns_c;
+  out[2] = all;
 }
 
 // keys sorted by (type, launch position): specular ids first, then diffuse
@@ -858,7 +865,7 @@ __global__ void split_lists_kernel(const uint32_t* __restrict__ sorted, int64_t 
 // Candidates (slot, row) -> sort keys (key id << row_bits) | row, in place:
 // sorting on the key id takes ceil(log2(keys)) bits instead of the table's.
 __global__ void cand_key_kernel(Table T, uint2* cand, const unsigned long long* __restrict__ n_cand_p,
-                                int64_t cap, int row_bits) {
+                                int64_t cap, int row_bits, int64_t key_cap) {
   const int64_t n_cand = min((int64_t)*n_cand_p, cap);
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cand;
        c += (int64_t)gridDim.x * blockDim.x) {
@@ -866,8 +873,10 @@ __global__ void cand_key_kernel(Table T, uint2* cand, const unsigned long long* 
     NRT_GUARD(e.x < g_dbg_caps.table, 21, e.x)
     NRT_GUARD(e.y < g_dbg_caps.rows, 22, e.y)
     const uint32_t kid = T.kid[e.x];
-    NRT_GUARD(kid < g_dbg_caps.keys, 4, kid)
-    reinterpret_cast<uint64_t*>(cand)[c] = ((uint64_t)kid << row_bits) | (uint64_t)e.y;
+    // a key over capacity gets all ones: its id field sorts after every id
+    // below key_cap (2^kid_bits > key_cap) and matches none of them
+    reinterpret_cast<uint64_t*>(cand)[c] =
+        (int64_t)kid < key_cap ? ((uint64_t)kid << row_bits) | (uint64_t)e.y : ~0ull;
   }
 }
 
@@ -1191,15 +1200,15 @@ __global__ void __launch_bounds__(kTraceThreads, 6)
 // tries and status are zeroed beforehand, so a key left without a run (a
 // result that overflowed its candidate capacity reports an error) still
 // points at a candidate inside the arrays.
-__global__ void run_start_kernel(SortedCand SC, KeyState K) {
+__global__ void run_start_kernel(SortedCand SC, KeyState K, int64_t key_cap) {
   const int64_t n = min((int64_t)*SC.n_p, SC.cap);
   const uint64_t row_mask = (1ull << SC.row_bits) - 1ull;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
        c += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t e = SC.key[c];
     const uint64_t kid = e >> SC.row_bits;
+    if (kid >= (uint64_t)key_cap) continue;  // candidates of keys over capacity
     if (c == 0 || (SC.key[c - 1] >> SC.row_bits) != kid) {
-      NRT_GUARD(kid < g_dbg_caps.keys, 19, kid)
       K.pos[kid] = (uint32_t)c;
       K.cur[kid] = (uint32_t)(e & row_mask);
     }
@@ -2030,16 +2039,16 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   slot_count_kernel<<<(unsigned)n_tiles, kSlotThreads, 0, st>>>(W.T, c.table, W.fs, W.fd); count_launch();
   scan_exclusive(W.fs, W.os, n_tiles, st);
   scan_exclusive(W.fd, W.od, n_tiles, st);
-  key_count_kernel<<<1, 1, 0, st>>>(W.fs, W.fd, W.os, W.od, n_tiles, W.cnt); count_launch();
+  key_count_kernel<<<1, 1, 0, st>>>(W.fs, W.fd, W.os, W.od, n_tiles, c.keys, W.cnt, ctr); count_launch();
   slot_assign_kernel<<<(unsigned)n_tiles, kSlotThreads, 0, st>>>(W.T, c.table, W.os, W.od, W.cnt,
-                                                                W.K.slot); count_launch();
+                                                                W.K.slot, c.keys); count_launch();
   TRY(cudaMemcpyAsync(ctr + kCtrKeys, W.cnt + kCntKeys, 8, cudaMemcpyDeviceToDevice, st));
   // candidates sorted by (key id, row) once
   int row_bits = 1, kid_bits = 1;
   while ((1ll << row_bits) < n) ++row_bits;
-  while ((1ll << kid_bits) < c.keys) ++kid_bits;
+  while ((1ll << kid_bits) <= c.keys) ++kid_bits;  // all-ones id field >= c.keys
   cand_key_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(W.T, W.cand, ctr + kCtrCands, c.cand,
-                                                              row_bits); count_launch();
+                                                              row_bits, c.keys); count_launch();
   // the candidates are in ascending row order (offsets per row), so a stable
   // sort on the key-id bits alone leaves each run in ray order
   radix_sort_pairs(reinterpret_cast<uint64_t*>(W.cand), nullptr, reinterpret_cast<uint64_t*>(W.cand2),
@@ -2049,7 +2058,7 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   TRY(cudaMemsetAsync(W.K.pos, 0, c.keys * sizeof(uint32_t), st));
   TRY(cudaMemsetAsync(W.K.tries, 0, c.keys * sizeof(uint32_t), st));
   TRY(cudaMemsetAsync(W.K.status, 0, c.keys * sizeof(uint32_t), st));
-  run_start_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(SC, W.K); count_launch();
+  run_start_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(SC, W.K, c.keys); count_launch();
 
   // validation order of the keys; key ids are dense in [0, keys): the sort
   // takes the live count from the device and leaves the rest alone
@@ -2167,7 +2176,7 @@ nrt_status finish_result(nrt_result* r) {
   c.kernel_launches = launch_counter();
   c.diffuse_casts = (int64_t)hc[kCtrDiffCasts];
   c.diffraction_casts = (int64_t)hc[kCtrDfrCasts];
-  if (c.error_flags & (kErrHashFull | kErrCandFull | kErrPathFull)) {
+  if (c.error_flags & (kErrHashFull | kErrCandFull | kErrPathFull | kErrKeyFull)) {
     ctx->last_error = "device buffer overflow (flags " +
                       std::to_string(c.error_flags) + ")";
     return NRT_ERR_OVERFLOW;

@@ -110,3 +110,22 @@ def test_autotune_picks_a_configuration(setup):
     ms, best = b.autotune(cfgs, repeats=2)
     assert np.all(ms > 0) and 0 <= best < len(cfgs)
     assert ms[best] == ms.min()
+
+
+def test_graph_replay_over_capacity_reports_overflow(setup):
+    """A recorded graph keeps the buffer capacities of its first run.  Recorded
+    with the TX pairs far above the office (almost every ray escapes, so the
+    capacities stay near their floors), a replay inside the office finds far
+    more candidates and keys than that: every write stays bounded, the replay
+    reports an overflow, and the context keeps working."""
+    ctx, sc, traj = setup
+    budgets = np.full(4, 4000, np.int64)
+    far = np.tile(np.array([10.0, 5.0, 200.0], np.float32), (4, 1))
+    g = sc.trace_batch(far, RXF, budgets, _params(n_rays=1), use_graph=True)
+    assert g.counts()[1]["keys"] < 1024
+    with pytest.raises(nrt.NrtError):
+        g.replay(traj[[0, 40, 80, 120]])
+    g.close()
+    r = sc.trace(traj[0], RXF[None], _params(n_rays=4000))
+    assert r.counts()[1]["paths"] >= 1
+    r.close()
