@@ -40,9 +40,12 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The oracle library: built from nrt_oracle.cpp, or, when the environment
+    names one in NRT_ORACLE_LIB, that prebuilt file instead (the
+    planted-mistake tests load deliberately broken copies this way)."""
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        _lib = C.CDLL(os.environ.get("NRT_ORACLE_LIB") or build())
         _declare(_lib)
     return _lib
 

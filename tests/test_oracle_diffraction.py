@@ -207,6 +207,41 @@ def test_diffracted_path_derivatives_match_central_differences(pol):
 
 
 @pytest.mark.parametrize("pol", [0, 1])
+def test_grazing_face_material_drops_out(pol):
+    """Each face's reflection factor takes that face's own incidence cosine:
+    sin(beta0) sin(phi') on face 0, sin(beta0) sin(n pi - phi) on face n.  A
+    wave grazing a face (cosine -> 0) reflects with -1 from any material
+    (TE and TM alike), so with the RX grazing face n the coefficient stops
+    depending on face n's material, and with the TX grazing face 0 on face
+    0's; away from grazing both materials matter."""
+    g = _box_edge()
+    t0, n0 = (-1.0, 0.0, 0.0), (0.0, 0.0, 1.0)
+    A, B = ETA, complex(2.0, -0.5)
+    eps = 1e-7
+    edge = (g["a"], g["b"], g["n0"], g["n1"])
+
+    def amp(tx, rx, e0, e1):
+        a = oracle.diffraction_amplitude(tx, rx, *edge, e0, e1, F0, pol)
+        assert a is not None
+        return a
+
+    for phi_in, y_tx, phi_out, y_rx in [(0.7, 0.2, 1.2 * math.pi, -0.1),
+                                        (1.1, -0.3, 0.9 * math.pi, 0.4)]:
+        tx = _rx_at(phi_in, 2.0, t0, n0, y_tx)
+        rx = _rx_at(phi_out, 1.5, t0, n0, y_rx)
+        rx_g = _rx_at(1.5 * math.pi - eps, 1.5, t0, n0, y_rx)  # grazing face n
+        tx_g = _rx_at(eps, 2.0, t0, n0, y_tx)                  # grazing face 0
+        a, b = amp(tx, rx_g, ETA, A), amp(tx, rx_g, ETA, B)
+        assert abs(a - b) < 1e-5 * abs(a)
+        a, b = amp(tx_g, rx, A, ETA), amp(tx_g, rx, B, ETA)
+        assert abs(a - b) < 1e-5 * abs(a)
+        a, b = amp(tx, rx, ETA, A), amp(tx, rx, ETA, B)
+        assert abs(a - b) > 1e-3 * abs(a)
+        a, b = amp(tx, rx, A, ETA), amp(tx, rx, B, ETA)
+        assert abs(a - b) > 1e-3 * abs(a)
+
+
+@pytest.mark.parametrize("pol", [0, 1])
 def test_perfect_conductor_wedge_is_reciprocal(pol):
     """For a perfect conductor (R0 = Rn = -/+1) the wedge coefficient is
     symmetric in (phi, phi') and the spreading in (s, s'): exchanging TX and

@@ -118,6 +118,39 @@ def test_gaussian_weight_symmetry_and_limit():
     assert np.allclose(R @ h1b["n"], h2["n"], atol=2e-6)
 
 
+def test_gaussian_weight_closed_form():
+    """Two discs whose planes both pass through the hit point X of a ray along
+    -z: disc 1 tilted by alpha with its centre a from X, disc 2 level with its
+    centre b from X.  Both meet the ray at X (q_i = q_min, so the Eq. 4 depth
+    factors are 1) and the Eq. 3 normal leans from +z toward n_1 by theta with
+    tan(theta) = w1 sin(alpha) / (w1 cos(alpha) + w2), where
+    w1 / w2 = exp(-(a^2 - b^2) / (2 r_p^2)): the Gaussian's width in closed form."""
+    rp = 0.05
+    for alpha_deg, a, b in [(20.0, 0.03, 0.01), (35.0, 0.045, 0.02), (10.0, 0.0, 0.04)]:
+        al = np.deg2rad(alpha_deg)
+        n1 = np.array([np.sin(al), 0.0, np.cos(al)])
+        p1 = a * np.array([np.cos(al), 0.0, -np.sin(al)])  # in plane 1, a from X = 0
+        p2 = np.array([0.0, b, 0.0])
+        # lambda_d near 0: the float32 rounding of disc 1 moves its plane hit by
+        # ~1e-9 m, which must not enter through the depth factor
+        sc = _scene([p1, p2], [n1, [0, 0, 1]], r_p=rp, rho=10.0, lambda_d=1e-9)
+        assert sc.n_dps == 1
+        h = sc.cast([0.0, 0.0, 1.0], [0, 0, -1])
+        assert h["hit"]
+        # the scene keeps float32 positions and normals, as given
+        P = np.array([p1, p2], np.float32).astype(np.float64)
+        N = np.array([n1, [0, 0, 1]], np.float32).astype(np.float64)
+        X = [np.array([0.0, 0.0, np.dot(P[i], N[i]) / N[i, 2]]) for i in range(2)]
+        ra = np.linalg.norm(X[0] - P[0])
+        rb = np.linalg.norm(X[1] - P[1])
+        w_ratio = np.exp(-(ra * ra - rb * rb) / (2.0 * rp * rp))
+        v = w_ratio * N[0] + N[1]  # the weighted normal sum, up to the factor w2
+        theta = np.arctan2(v[0], v[2])
+        n_got = np.asarray(h["n"])
+        assert abs(n_got[1]) < 1e-12
+        assert np.arctan2(n_got[0], n_got[2]) == pytest.approx(theta, abs=1e-9)
+
+
 def test_tie_rule_smaller_index():
     """Coplanar discs covering the hit point tie exactly in t: q_min is the
     smaller point index."""

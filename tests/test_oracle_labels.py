@@ -52,3 +52,69 @@ def test_labels_match_capture_rule_rederived():
     assert lab.sum() > 50
     assert np.array_equal(lab[ok], want[ok]), np.nonzero(lab[ok] != want[ok])[0][:10]
     assert amb.mean() < 0.01
+
+
+def test_dedup_tries_lowest_ray_ids_first():
+    """Sec. II-B-4 keeps, per key, the lowest ray id whose candidate validates,
+    trying candidates in ascending ray id and at most rep_tries of them.  The
+    candidate set of every key is re-derived here from the hit records by the
+    sphere capture rule (as above); each key's tried list must be the first
+    n_tried ids of that set in ascending order, invalid up to its last entry,
+    which is the representative when the key is valid, and n_tried must be
+    min(candidates, rep_tries) when no candidate validated."""
+    room = inputs.room_scene()
+    osc = oracle.OracleScene(room.pos, room.nrm, room.surf, room.mat, rho=0.0625, r_p=0.05,
+                             grid_cell=0.25)
+    n_rays, r_rx, tries = 60000, 0.3, 3
+    p = oracle.SimParams(max_depth=4, capture=0, diffuse=0, n_rays=n_rays, rep_tries=tries,
+                         r_rx=r_rx)
+    sim = oracle.OracleSim(osc, room.tx, RX, p)
+    H = sim.hits()
+    d0 = oracle.fib_dirs(n_rays, np.arange(n_rays)).astype(np.float32).astype(np.float64)
+    tx = room.tx.astype(np.float64)
+    rx = RX.astype(np.float64)
+    cands, near = {}, set()
+    for i in range(n_rays):
+        o, d = tx, d0[i]
+        labels = []
+        for s in range(H["n_hits"][i]):
+            q, nrm = H["q"][i, s], H["n"][i, s]
+            labels.append(int(room.surf[H["idx"][i, s]]))
+            d = d - 2.0 * np.dot(d, nrm) * nrm
+            d = d / np.linalg.norm(d)
+            o = q
+            k = s + 1
+            t_end = H["t"][i, s + 1] if s + 1 < H["n_hits"][i] else np.inf
+            for j in range(rx.shape[0]):
+                ts = min(max(np.dot(rx[j] - o, d), 0.0), t_end)
+                dist = np.linalg.norm(o + ts * d - rx[j])
+                lo = 0
+                for m in range(min(k, 4)):
+                    lo |= labels[m] << (16 * m)
+                key = ((j << 56) | (k << 52) | (labels[4] if k > 4 else 0), lo)
+                if abs(dist - r_rx) < 1e-9:
+                    near.add(key)  # the capture decision is within rounding
+                if dist <= r_rx:
+                    cands.setdefault(key, []).append(i)
+    K = sim.keys()
+    ray, valid, _ = sim.tried()
+    start = np.concatenate([[0], np.cumsum(K["n_tried"])])
+    checked = capped = 0
+    for q in range(K["hi"].shape[0]):
+        key = (int(K["hi"][q]), int(K["lo"][q]))
+        if key in near or not K["certain"][q]:
+            continue
+        want = sorted(cands[key])
+        assert K["n_cand"][q] == len(want)
+        t = ray[start[q]:start[q + 1]]
+        v = valid[start[q]:start[q + 1]]
+        assert list(t) == want[:len(t)]
+        assert not v[:-1].any()
+        if K["valid"][q]:
+            assert v[-1] and K["rep"][q] == t[-1]
+        else:
+            assert len(t) == min(len(want), tries)
+            capped += len(want) > tries
+        checked += 1
+    print("keys checked", checked, "capped", capped)
+    assert checked > 60 and capped > 10

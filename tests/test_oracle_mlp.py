@@ -33,6 +33,11 @@ def test_counter_uniform_and_gumbel_moments():
     assert abs(g.var() - math.pi ** 2 / 6.0) < 2e-2
     # counter-based: element i does not depend on how many are drawn
     assert np.array_equal(M.counter_uniform(99, [5, 7]), u[[5, 7]])
+    # counter i is output i + 1 of the SplitMix64 stream of the same seed
+    # (pinned above to the published outputs), top 53 bits, half-ulp offset
+    z = M.splitmix64_stream(1234567, 5)
+    want = ((z >> np.uint64(11)).astype(np.float64) + 0.5) * 2.0 ** -53
+    assert np.array_equal(M.counter_uniform(1234567, np.arange(5)), want)
 
 
 def test_bf16_matches_torch_cast():
@@ -179,6 +184,31 @@ def test_select_structure():
     big = (np.arange(n) % 977).astype(np.float32) * 1000.0
     want = np.sort(np.argsort(-big.astype(np.float64), kind="stable")[:50])
     assert np.array_equal(M.select(big, 50, 0, seed=2), want)
+    # every key tied (logit = -its float32 Gumbel noise, so logit + noise is
+    # exactly 0): ties go to the smaller index, so top-k is 0 .. k-1
+    g32 = M.gumbel(3, np.arange(n)).astype(np.float32)
+    assert np.array_equal(M.select(-g32, 40, 0, seed=3), np.arange(40))
+
+
+def test_strata_draws_are_independent_of_the_gumbel_noise():
+    """The uniform stratum picks use their own counters: across seeds, the
+    position of the pick inside stratum 0 is uncorrelated with the Gumbel
+    noise of index 0 (had they shared a counter, the two would be the same
+    monotone function of one uniform, rank correlation 1)."""
+    n, k_u, seeds = 1000, 10, 400
+    pos, g0 = np.zeros(seeds), np.zeros(seeds)
+    z = np.full(n, -1e4, np.float32)  # no top-k pick lands in stratum 0 by accident
+    z[-1] = 0.0
+    for s in range(seeds):
+        ids = M.select(z, 1, k_u, seed=500 + s)
+        in0 = ids[ids < n // k_u]
+        assert in0.size == 1
+        pos[s] = in0[0]
+        g0[s] = M.gumbel(500 + s, [0])[0]
+    rp = np.argsort(np.argsort(pos)).astype(np.float64)
+    rg = np.argsort(np.argsort(g0)).astype(np.float64)
+    rho = np.corrcoef(rp, rg)[0, 1]
+    assert abs(rho) < 4.0 / np.sqrt(seeds)
 
 
 def test_gumbel_max_samples_the_softmax():

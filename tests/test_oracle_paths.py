@@ -239,6 +239,25 @@ def test_visibility_and_los_occlusion():
         assert h["hit"] == with_plate
 
 
+def test_rough_wall_fully_visible_from_the_front():
+    """Nothing stands between a receiver and a single wall in front of it, so
+    every DPS of the wall is visible (the visibility matrix of Sec. II-B-1),
+    also when the wall is rough: the test cast toward a DPS ends short of
+    its reception point by the DPS's own extent (half a voxel diagonal plus
+    r_p), so the bumps of its neighbours around that point do not count."""
+    rng = np.random.default_rng(11)
+    pos, nrm, surf = _plate([0.0, 0.0, 0.0], [1, 0, 0], 0.5, 0.02, 0)
+    pos[:, 0] += rng.uniform(-0.005, 0.005, pos.shape[0])  # +-5 mm of roughness
+    sc = oracle.OracleScene(pos.astype(np.float32), nrm.astype(np.float32),
+                            surf.astype(np.uint16), np.zeros(pos.shape[0], np.uint8), r_p=0.05)
+    _, cnt, _ = sc.dps()
+    rx = np.array([[1.5, 0.2, -0.1]])
+    n = len(cnt)
+    bit, amb = sc.vis_pairs(rx, np.zeros(n, np.int32), np.arange(n, dtype=np.int32), delta=1e-7)
+    assert n > 200
+    assert bit[~amb].all() and amb.mean() < 0.02
+
+
 def test_adjoint_matches_central_differences(office):
     """Analytic dP_j / d(eps_r, sigma, S)_l (one-hot dL/dP) and the gradient of
     the per-RX dB-gain MSE against FP64 central differences of the oracle's

@@ -66,6 +66,19 @@ def test_single_point_gives_its_tangent_plane():
     # a ray whose plane crossing lies beyond 2 sigma of the point misses
     o2 = np.array([0.30 + 3 * SIG_POINT, 0.5, 0.5])
     assert not osc.cast_sdf(o2, d, SIG_POINT)["hit"]
+    # one point's weight is exp(-r^2 / (2 sigma^2)), so the field is defined
+    # (W >= e^-2) only within r <= 2 sigma of it: a ray along -n crossing the
+    # plane at lateral offset 1.6 sigma hits, one at 2.4 sigma misses.  The
+    # offset runs diagonally in the plane, so that every coordinate of the
+    # crossing stays within 2 sigma of the point (inside the marched box).
+    nu = nd / np.linalg.norm(nd)
+    t1 = np.array([1.0, 0.0, 0.0])
+    u = t1 + np.cross(nu, t1)
+    u /= np.linalg.norm(u)
+    for r, hit in [(1.6, True), (2.4, False)]:
+        o3 = pd + r * SIG_POINT * u + 0.4 * nu
+        assert np.all(np.abs(r * SIG_POINT * u) < 2 * SIG_POINT)
+        assert osc.cast_sdf(o3, -nu, SIG_POINT)["hit"] == hit, r
 
 
 def test_first_crossing_matches_a_dense_scan():
