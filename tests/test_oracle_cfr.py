@@ -32,6 +32,20 @@ def test_one_and_two_path_closed_forms():
     assert np.allclose(np.abs(H2) ** 2, want, rtol=1e-10)
 
 
+def test_cir_of_one_path_is_a_delayed_impulse():
+    """One path whose delay is m0 / (N df) (df the grid step): its CFR is
+    C exp(-j 2 pi n m0 / N) over the grid index n, so the inverse DFT is the
+    impulse C delta[m - m0]: |h| = |a| at tap m0 and 0 elsewhere."""
+    df = F[1] - F[0]
+    a = 2e-4 * np.exp(0.3j)
+    for m0 in (1, 5, 40):
+        tau = m0 / (F.size * df)
+        h = cfr.cir(cfr.cfr([a], [tau], [0], 1, F))[0]
+        assert int(np.argmax(np.abs(h))) == m0
+        assert abs(h[m0]) == pytest.approx(abs(a), rel=1e-9)
+        assert np.abs(np.delete(h, m0)).max() < 1e-9 * abs(a)
+
+
 def test_eq5_on_cfr_equals_eq5_on_cir():
     rng = np.random.default_rng(1)
     H = rng.standard_normal((3, 129)) + 1j * rng.standard_normal((3, 129))

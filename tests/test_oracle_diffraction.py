@@ -55,6 +55,23 @@ def _box_edge():
     return dict(a=(0.0, -1.0, 0.0), b=(0.0, 1.0, 0.0), n0=(0.0, 0.0, 1.0), n1=(1.0, 0.0, 0.0))
 
 
+def test_exterior_angle_closed_forms():
+    """n pi is the exterior angle of the wedge, 2 pi minus the angle between
+    its faces: a right-angled box edge gives n = 3/2, a thin half-plane
+    n -> 2, a 60-degree wedge n = 5/3 and a 120-degree one n = 4/3."""
+    tx, rx = (1.0, 0.3, 1.0), (0.8, -0.2, -1.2)
+    a, b = (0.0, -1.0, 0.0), (0.0, 1.0, 0.0)
+    for interior, want in [(90.0, 1.5), (1e-6, 2.0), (60.0, 5.0 / 3.0), (120.0, 4.0 / 3.0)]:
+        g = math.radians(interior)
+        # face 0 extends along -x with normal +z; face n is face 0 turned by the
+        # interior angle about the edge (y axis), its normal pointing outwards
+        n0 = (0.0, 0.0, 1.0)
+        n1 = (math.sin(g), 0.0, -math.cos(g))
+        ok, D, s_in, s_out, phi_in, phi_out, nw, sinb = oracle.diffraction_geometry(
+            tx, rx, a, b, n0, n1)
+        assert nw == pytest.approx(want, abs=1e-6), interior
+
+
 def test_keller_point_minimises_the_path_length():
     rng = np.random.default_rng(11)
     E = inputs.room_edges(12)

@@ -118,3 +118,27 @@ def test_dedup_tries_lowest_ray_ids_first():
         checked += 1
     print("keys checked", checked, "capped", capped)
     assert checked > 60 and capped > 10
+
+
+def test_capture_stops_at_the_segment_ends():
+    """Sphere capture tests each segment between two interactions (Sec. II-B):
+    the closest approach is clamped to the segment, so a receiver beyond a
+    wall (above the ceiling, below the floor of a floor-and-ceiling slab) is
+    never captured, while one inside the slab is."""
+    g = np.arange(-3.0, 3.0 + 1e-9, 0.05)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    flat = np.column_stack([X.ravel(), Y.ravel()])
+    floor = np.column_stack([flat, np.zeros(len(flat))])
+    ceil = np.column_stack([flat, np.full(len(flat), 2.0)])
+    pos = np.vstack([floor, ceil]).astype(np.float32)
+    nrm = np.vstack([np.tile([0, 0, 1.0], (len(flat), 1)),
+                     np.tile([0, 0, -1.0], (len(flat), 1))]).astype(np.float32)
+    surf = np.repeat([0, 1], len(flat)).astype(np.uint16)
+    osc = oracle.OracleScene(pos, nrm, surf, np.zeros(len(pos), np.uint8), rho=0.0625, r_p=0.05,
+                             grid_cell=0.25)
+    rx = np.array([[0.5, 0.3, 2.25], [0.4, -0.2, -0.25], [0.6, 0.1, 1.0]])
+    p = oracle.SimParams(max_depth=3, capture=0, diffuse=0, n_rays=20000, r_rx=0.2)
+    sim = oracle.OracleSim(osc, np.array([0.0, 0.0, 1.0]), rx, p)
+    j = (sim.keys()["hi"] >> np.uint64(56)).astype(int)
+    assert np.sum(j == 0) == 0 and np.sum(j == 1) == 0
+    assert np.sum(j == 2) > 3

@@ -74,6 +74,29 @@ MUTANTS = [
      "img[m + 1] = img[m] - 2.0 * dot(img[m] - Pp[m], Pn[m]) * Pn[m];",
      "img[m + 1] = img[m] - dot(img[m] - Pp[m], Pn[m]) * Pn[m];",
      [f"{T_PATHS}::test_shoebox_image_sources"]),
+    ("refinement_accepts_either_criterion", CPP, "if (!(c >= cos_ta && dist <= sim.p.t_d)) {",
+     "if (!(c >= cos_ta || dist <= sim.p.t_d)) {",
+     [f"{T_PATHS}::test_refinement_converges_on_a_cylinder"]),
+    ("refinement_never_retries", CPP, "if (attempt == sim.p.kappa) return v;",
+     "if (attempt == 0) return v;", [f"{T_PATHS}::test_refinement_converges_on_a_cylinder"]),
+    ("side_check_dropped", CPP, "if (!(a * b > 0.0)) return v;", "if (false) return v;",
+     [f"{T_PATHS}::test_valid_paths_are_physical"]),
+    ("last_leg_unchecked", CPP, "if (hf.hit) return v;", "if (false) return v;",
+     [f"{T_PATHS}::test_valid_paths_are_physical"]),
+    ("surface_label_unchecked", CPP, "if (!h.hit || S.surf[h.idx] != labels[m - 1]) {",
+     "if (!h.hit) {", [f"{T_PATHS}::test_valid_paths_are_physical"]),
+    ("diffuse_shadow_unchecked", CPP,
+     "  Hit h = cast(S, hk.q, w, hk.dps, rs, false, cfg);\n  if (h.amb) v.amb = true;\n  if (h.hit) return v;",
+     "  Hit h = cast(S, hk.q, w, hk.dps, rs, false, cfg);\n  if (h.amb) v.amb = true;",
+     [f"{T_PATHS}::test_valid_paths_are_physical"]),
+    ("diffuse_length_last_segment", CPP, "ri += hm.t;", "ri = hm.t;",
+     [f"{T_PATHS}::test_valid_paths_are_physical"]),
+    ("capture_before_segment_start", CPP, "ts = std::min(std::max(ts, 0.0), t_end);",
+     "ts = std::min(ts, t_end);", [f"{T_LAB}::test_capture_stops_at_the_segment_ends"]),
+    ("capture_past_segment_end", CPP, "ts = std::min(std::max(ts, 0.0), t_end);",
+     "ts = std::max(ts, 0.0);", [f"{T_LAB}::test_capture_stops_at_the_segment_ends"]),
+    ("hits_below_t_min", CPP, "if (e.t > cfg.t_min && e.t < t_max && e.r <= rp) {",
+     "if (e.t > 0.0 && e.t < t_max && e.r <= rp) {", [f"{T_GEO}::test_single_disc_hit_and_miss"]),
     # EM readings
     ("fresnel_te_sign", CPP, "if (pol == 0) return (cos_t - s) / (cos_t + s);",
      "if (pol == 0) return (s - cos_t) / (cos_t + s);", [T_EM]),
@@ -83,6 +106,10 @@ MUTANTS = [
      "return cd(eps_r, sigma / (2.0 * kPi * f * kEps0));", [T_EM]),
     ("fresnel_derivative_sign", CPP, "return -cos_t / (s * den * den);",
      "return cos_t / (s * den * den);", [f"{T_EM}::test_fresnel_derivative_complex_step"]),
+    ("los_delay_doubled", CPP, "P.tau = d / kC0;", "P.tau = 2.0 * d / kC0;",
+     [f"{T_EM}::test_los_amplitude_and_delay"]),
+    ("specular_delay_halved", CPP, "P.tau = len / kC0;", "P.tau = 0.5 * len / kC0;",
+     [f"{T_PATHS}::test_shoebox_image_sources"]),
     ("los_two_pi", CPP, "P.geo = lam / (4.0 * kPi * d);", "P.geo = lam / (2.0 * kPi * d);",
      [f"{T_EM}::test_los_amplitude_and_delay"]),
     ("specular_spreading_squared", CPP, "P.geo = lam / (4.0 * kPi * len);",
@@ -105,6 +132,10 @@ MUTANTS = [
      "return {d.z * d.x / st, d.z * d.y / st, st};", [f"{T_POL}::test_floor_reflection_is_tm"]),
     ("p_basis_handedness", CPP, "pout[m] = cross(sv[m], d[m + 1]);",
      "pout[m] = cross(d[m + 1], sv[m]);", [f"{T_POL}::test_floor_reflection_is_tm"]),
+    ("jones_e0_basis", CPP, "J.e0[1] = dot(t0, pin[0]);", "J.e0[1] = dot(t0, pout[0]);", [T_POL]),
+    ("jones_basis_change_transposed", CPP, "J.B[m][0][1] = dot(sv[m + 1], pout[m]);",
+     "J.B[m][0][1] = dot(pin[m + 1], sv[m]);", [T_POL]),
+    ("jones_rx_basis", CPP, "J.r[1] = dot(tr, pout[k - 1]);", "J.r[1] = dot(tr, pin[k - 1]);", [T_POL]),
     # Sec. II-B-3 edge diffraction
     ("utd_constant_sign", CPP, "const cd K = -std::exp(cd(0.0, -kPi / 4.0)) / (2.0 * nw",
      "const cd K = std::exp(cd(0.0, -kPi / 4.0)) / (2.0 * nw",
@@ -132,6 +163,13 @@ MUTANTS = [
     ("face_0_incidence_angle", CPP, "const double c0 = G.sinb * std::sin(G.phi_in),",
      "const double c0 = G.sinb * std::sin(G.phi_out),",
      [f"{T_DIF}::test_grazing_face_material_drops_out"]),
+    ("transition_asymptote_sign", CPP, "term *= -(2.0 * n - 1.0) / (cd(0.0, 2.0 * x));",
+     "term *= (2.0 * n - 1.0) / (cd(0.0, 2.0 * x));", [T_DIF]),
+    ("exterior_angle_sign", CPP, "W.nw = 2.0 - std::acos", "W.nw = 2.0 + std::acos",
+     [f"{T_DIF}::test_exterior_angle_closed_forms"]),
+    ("transition_index_floored", CPP,
+     "const double N = std::round((beta + sgn * kPi) / (2.0 * kPi * nw));",
+     "const double N = std::floor((beta + sgn * kPi) / (2.0 * kPi * nw));", [T_DIF]),
     # Eq. 2 SDF (ablation)
     ("sdf_sign", CPP, "sf += w * dot(S->N[i], v);", "sf -= w * dot(S->N[i], v);",
      [f"{T_SDF}::test_single_point_gives_its_tangent_plane"]),
@@ -150,6 +188,9 @@ MUTANTS = [
      "w = 1.0 * np.asarray(rx_weight, np.float64)[rx] / D[rx]", [T_CFR]),
     ("eq5_gradient_phase", "cfr.py", "np.exp(2j * np.pi * tau[:, None] * np.asarray(f)[None, :])",
      "np.exp(-2j * np.pi * tau[:, None] * np.asarray(f)[None, :])", [T_CFR]),
+    ("cir_forward_transform", "cfr.py", "return np.fft.ifft(np.asarray(H), axis=-1)",
+     "return np.fft.fft(np.asarray(H), axis=-1)",
+     [f"{T_CFR}::test_cir_of_one_path_is_a_delayed_impulse"]),
     # proposal network (Python)
     ("splitmix_shift", "mlp.py", "z = (z ^ (z >> np.uint64(30))) * _M1",
      "z = (z ^ (z >> np.uint64(31))) * _M1", [f"{T_MLP}::test_splitmix64_published_outputs"]),
@@ -170,6 +211,9 @@ MUTANTS = [
      [f"{T_MLP}::test_forward_and_gradients_match_torch_autograd"]),
     ("adam_bias_correction_dropped", "mlp.py", "mh = m / (1.0 - b1 ** t)", "mh = m",
      [f"{T_MLP}::test_adam_matches_torch_optim"]),
+    ("adam_epsilon_inside_the_root", "mlp.py",
+     "return theta - lr * mh / (np.sqrt(vh) + eps), m, v",
+     "return theta - lr * mh / np.sqrt(vh + eps), m, v", [f"{T_MLP}::test_adam_matches_torch_optim"]),
     ("selection_ties_larger_index", "mlp.py",
      "order = np.lexsort((np.arange(n), -key.astype(np.float64)))",
      "order = np.lexsort((-np.arange(n), -key.astype(np.float64)))",

@@ -258,6 +258,160 @@ def test_rough_wall_fully_visible_from_the_front():
     assert bit[~amb].all() and amb.mean() < 0.02
 
 
+# axis-aligned rectangles: (axis of the normal, plane coordinate, outward
+# normal sign, (lo, hi) of the other two coordinates in axis order)
+# (gaps of at least 30 cm between them keep every DPS on one surface)
+_RECTS = {
+    0: (2, 0.0, +1, ((-2.0, 1.8), (-2.0, 2.0))),   # floor z = 0
+    1: (0, 2.0, -1, ((-2.0, 2.0), (0.3, 2.5))),    # wall x = 2
+    2: (1, 0.5, -1, ((-0.8, 0.4), (0.3, 1.6))),    # occluder y = 0.5
+    3: (0, 1.0, -1, ((-1.2, 0.4), (0.4, 2.0))),    # screen x = 1, parallel to the wall
+}
+
+
+def _rect_points(label, spacing=0.04):
+    ax, c, sgn, ((a0, a1), (b0, b1)) = _RECTS[label]
+    u, v = [b for b in range(3) if b != ax]
+    A, B = np.meshgrid(np.arange(a0, a1 + 1e-9, spacing), np.arange(b0, b1 + 1e-9, spacing),
+                       indexing="ij")
+    p = np.zeros((A.size, 3))
+    p[:, ax], p[:, u], p[:, v] = c, A.ravel(), B.ravel()
+    n = np.zeros((A.size, 3))
+    n[:, ax] = sgn
+    return p, n
+
+
+def _crosses(p0, p1, label, margin, end_eps):
+    """Whether the open segment p0 -> p1 passes through rectangle `label`
+    (grown by `margin`, the disc radius) away from its end points."""
+    ax, c, _, ((a0, a1), (b0, b1)) = _RECTS[label]
+    u, v = [b for b in range(3) if b != ax]
+    d = p1[ax] - p0[ax]
+    if d == 0.0:
+        return False
+    t = (c - p0[ax]) / d
+    L = np.linalg.norm(p1 - p0)
+    if not (end_eps / L < t < 1.0 - end_eps / L):
+        return False
+    x = p0 + t * (p1 - p0)
+    return a0 - margin <= x[u] <= a1 + margin and b0 - margin <= x[v] <= b1 + margin
+
+
+def test_valid_paths_are_physical():
+    """Every valid path of a scene with an occluder obeys the geometry that
+    Sec. II-B-1 / II-B-2 validate, checked here analytically against the
+    scene's rectangles: each interaction point lies on the surface its key
+    names (within t_d), each specular interaction reflects (both legs on the
+    same side of its surface), no leg passes through a surface, and the
+    delay is the polyline's length over the speed of light.  The
+    occluder blocks the floor's specular image path to the RX, and a screen
+    in front of the wall blocks the wall's image path on its TX side, so
+    those keys are rejected while the screen's own reflection is valid."""
+    parts = [_rect_points(l) for l in _RECTS]
+    pos = np.vstack([p for p, _ in parts]).astype(np.float32)
+    nrm = np.vstack([n for _, n in parts]).astype(np.float32)
+    surf = np.concatenate([np.full(len(p), l) for l, (p, _) in enumerate(parts)]).astype(np.uint16)
+    osc = oracle.OracleScene(pos, nrm, surf, np.zeros(len(pos), np.uint8), rho=0.25, r_p=0.05,
+                             grid_cell=0.25)
+    tx = np.array([-1.0, -1.0, 1.2])
+    rx = np.array([[-0.5, 1.2, 1.0]])
+    t_d = 0.01
+    p = oracle.SimParams(max_depth=2, capture=1, diffuse=1, n_rays=100000, t_d=t_d)
+    sim = oracle.OracleSim(osc, tx, rx, p)
+    P = sim.paths()
+    K = sim.keys()
+    n_checked = 0
+    for i in range(len(P["type"])):
+        k, ty = int(P["k"][i]), int(P["type"][i])
+        if k == 0:
+            continue
+        pts = [tx] + [P["pts"][i, m] for m in range(k)] + [rx[0]]
+        lo = int(P["lo"][i])
+        labels = [(lo >> (16 * m)) & 0xFFFF for m in range(min(k, 4))]
+        for m in range(1, k + 1):
+            q = pts[m]
+            if ty == 1 and m == k:  # the scatter point: on some surface
+                on = [l for l in _RECTS if abs(q[_RECTS[l][0]] - _RECTS[l][1]) <= t_d]
+                assert on, (i, q)
+                continue
+            ax, c, _, _ = _RECTS[labels[m - 1]]
+            assert abs(q[ax] - c) <= t_d + 1e-9, (i, m, q)
+            a = pts[m - 1][ax] - c
+            b = pts[m + 1][ax] - c
+            assert a * b > 0, (i, m)  # reflection, not transmission
+        # the delay is the polyline's length over c (specular and diffuse)
+        length = sum(np.linalg.norm(pts[m + 1] - pts[m]) for m in range(k + 1))
+        assert P["length"][i] == pytest.approx(length, rel=1e-9)
+        assert P["tau"][i] == pytest.approx(length / 299792458.0, rel=1e-9)
+        # inside a rectangle of points 4 cm apart every spot is within 3 cm of
+        # a disc centre (r_p = 5 cm): a leg through it is certainly blocked
+        for m in range(k + 1):
+            for l in _RECTS:
+                assert not _crosses(pts[m], pts[m + 1], l, 0.0, 0.02), (i, m, l)
+        n_checked += 1
+    assert n_checked > 20
+    # the floor's one-bounce specular image path is blocked by the occluder
+    img = tx * np.array([1, 1, -1.0])
+    t = img[2] / (img[2] - rx[0, 2])
+    fp = img + t * (rx[0] - img)
+    assert _crosses(fp, rx[0], 2, 0.0, 0.02)
+    spec1 = (((K["hi"] >> np.uint64(52)) & np.uint64(7)) == 1) & \
+        (((K["hi"] >> np.uint64(55)) & np.uint64(1)) == 0)
+    for label, valid in ((0, False), (1, False), (3, True)):
+        sel = spec1 & (K["lo"] == label)
+        assert sel.sum() == 1 and bool(K["valid"][sel][0]) == valid, label
+
+
+def test_refinement_converges_on_a_cylinder():
+    """Sec. II-B-2 on a curved surface: a convex cylinder (R = 3 m) of points
+    with radial normals.  A candidate's own hit gives only an approximate
+    tangent plane, so the image-method point must be refined (the hit's plane
+    replaces the solve's until the normal is within t_a and the hit within
+    t_d).  At the valid single-bounce path's point the law of reflection
+    must hold to within t_a (plus half a degree for the discs' normals): the
+    two legs' unit vectors sum to a vector within 1.5 degrees of the radial
+    normal there.  The point must also lie within 5 cm of the true specular
+    point, found here by root finding on the cylinder angle.  Several TX/RX
+    placements, and a wide capture sphere whose candidates start several
+    degrees off."""
+    R = 3.0
+    na = int(round(2 * np.pi * R / 0.02))
+    th = np.arange(na) * (2 * np.pi / na)
+    z = np.arange(0.0, 2.0 + 1e-9, 0.02)
+    TH, Z = np.meshgrid(th, z, indexing="ij")
+    pos = np.column_stack([R * np.cos(TH.ravel()), R * np.sin(TH.ravel()), Z.ravel()])
+    nrm = np.column_stack([np.cos(TH.ravel()), np.sin(TH.ravel()), np.zeros(TH.size)])
+    n = len(pos)
+    osc = oracle.OracleScene(pos.astype(np.float32), nrm.astype(np.float32),
+                             np.zeros(n, np.uint16), np.zeros(n, np.uint8), rho=0.0625,
+                             r_p=0.05, grid_cell=0.25)
+    brentq = pytest.importorskip("scipy.optimize").brentq
+
+    def at(a, d):
+        return np.array([(R + d) * np.cos(a), (R + d) * np.sin(a), 1.0])
+
+    for a_tx, d_tx, a_rx, d_rx in [(0.2, 1.2, 1.3, 1.6), (3.5, 2.5, 4.3, 1.0), (2.0, 1.0, 2.5, 2.5)]:
+        tx, rx = at(a_tx, d_tx), at(a_rx, d_rx)
+        p = oracle.SimParams(max_depth=1, capture=0, diffuse=0, n_rays=200000, r_rx=0.4)
+        P = oracle.OracleSim(osc, tx, rx[None], p).paths()
+        spec = (P["type"] == 0) & (P["k"] == 1)
+        assert spec.sum() == 1, (a_tx, a_rx)
+        q = P["pts"][spec][0, 0]
+
+        def tangential(a):
+            pt = np.array([R * np.cos(a), R * np.sin(a), 1.0])
+            u = (tx - pt) / np.linalg.norm(tx - pt) + (rx - pt) / np.linalg.norm(rx - pt)
+            return u @ np.array([-np.sin(a), np.cos(a), 0.0])
+        a_star = brentq(tangential, a_tx, a_rx)
+        want = np.array([R * np.cos(a_star), R * np.sin(a_star), 1.0])
+        b = (tx - q) / np.linalg.norm(tx - q) + (rx - q) / np.linalg.norm(rx - q)
+        nr = np.array([q[0], q[1], 0.0])
+        ang = np.degrees(np.arccos(np.clip(b @ nr / (np.linalg.norm(b) * np.linalg.norm(nr)),
+                                           -1.0, 1.0)))
+        assert ang < 1.5, (a_tx, a_rx, ang)
+        assert np.linalg.norm(q - want) < 0.05, (a_tx, a_rx, q, want)
+
+
 def test_adjoint_matches_central_differences(office):
     """Analytic dP_j / d(eps_r, sigma, S)_l (one-hot dL/dP) and the gradient of
     the per-RX dB-gain MSE against FP64 central differences of the oracle's
