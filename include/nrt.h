@@ -107,7 +107,12 @@ typedef struct {
   int64_t paths;             /* valid paths (including LOS) */
   int64_t n_dps;             /* DPS in the scene */
   int64_t hash_probes_max;   /* longest hash probe sequence seen */
-  int64_t error_flags;       /* device error bits (0 = none) */
+  int64_t error_flags;       /* device error bits, 0 = none: 1 traversal stack
+                                would overflow (tree deeper than the stack);
+                                2 hash probe limit reached; 4 candidate buffer
+                                full; 8 more distinct keys than the key
+                                capacity; 16 path buffer full.  Any of them
+                                makes the call return NRT_ERR_OVERFLOW. */
   int64_t kernel_launches;   /* library kernels launched by the call */
   int64_t diffuse_casts;     /* of validation_casts: diffuse shadow casts (Sec. II-B-1) */
   int64_t diffraction_casts; /* edge visibility casts (Sec. II-B-3) */
