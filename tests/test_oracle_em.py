@@ -101,9 +101,10 @@ def test_los_amplitude_and_delay(room):
 def test_diffuse_power_off_a_plane_is_the_lambertian_integral():
     """The diffuse reading gives a scatter cell of area rho^2 the amplitude
     lambda/(4 pi) sqrt(rho^2 cos_i cos_s / pi) / (r_i r_s), i.e. a Lambertian
-    lobe.  Summed over a flat plane (z = 0), the powers |a|^2 / (lambda/4 pi)^2
+    lobe.  Summed over a flat plane, the powers |a|^2 / (lambda/4 pi)^2
     are then a midpoint Riemann sum of the radiometric integral
-    int z_t z_r / (pi r_i^3 r_s^3) dA.  One ray per DPS (the DPS-directed
+    int x_t x_r / (pi r_i^3 r_s^3) dA over a wall x = 0 (a vertical plane, so
+    that the incidence cosine is not a z component).  One ray per DPS (the DPS-directed
     launch) scatters at each DPS's reception point: with four points per
     voxel axis these are the centres of rho-sized cells, so the sum must meet
     a fine quadrature of the integral over those cells to the midpoint
@@ -111,13 +112,13 @@ def test_diffuse_power_off_a_plane_is_the_lambertian_integral():
     rho = 0.0625
     g = -1.5 + np.arange(48 * 4) * (rho / 4)  # 48 voxels, 4 points per axis in each
     X, Y = np.meshgrid(g, g, indexing="ij")
-    pos = np.column_stack([X.ravel(), Y.ravel(), np.zeros(X.size)]).astype(np.float32)
-    nrm = np.tile(np.array([0, 0, 1], np.float32), (pos.shape[0], 1))
+    pos = np.column_stack([np.zeros(X.size), X.ravel(), Y.ravel()]).astype(np.float32)
+    nrm = np.tile(np.array([1, 0, 0], np.float32), (pos.shape[0], 1))
     n = pos.shape[0]
     osc = oracle.OracleScene(pos, nrm, np.zeros(n, np.uint16), np.zeros(n, np.uint8), rho=rho,
                              r_p=0.05, grid_cell=0.25)
-    tx = np.array([0.3, -0.2, 1.0])
-    rx = np.array([[-0.4, 0.5, 0.8]])
+    tx = np.array([1.0, 0.3, -0.2])
+    rx = np.array([[0.8, -0.4, 0.5]])
     sim = oracle.OracleSim(osc, tx, rx, oracle.SimParams(max_depth=1, capture=1, diffuse=1,
                                                          n_rays=0, launch=1))
     P = sim.paths()
@@ -132,7 +133,7 @@ def test_diffuse_power_off_a_plane_is_the_lambertian_integral():
     M = 4000
     xs = x0 + (np.arange(M) + 0.5) * (48 * rho / M)
     XX, YY = np.meshgrid(xs, xs, indexing="ij")
-    ri2 = (XX - tx[0]) ** 2 + (YY - tx[1]) ** 2 + tx[2] ** 2
-    rs2 = (XX - rx[0, 0]) ** 2 + (YY - rx[0, 1]) ** 2 + rx[0, 2] ** 2
-    want = np.sum(tx[2] * rx[0, 2] / (np.pi * ri2 ** 1.5 * rs2 ** 1.5)) * (48 * rho / M) ** 2
+    ri2 = tx[0] ** 2 + (XX - tx[1]) ** 2 + (YY - tx[2]) ** 2
+    rs2 = rx[0, 0] ** 2 + (XX - rx[0, 1]) ** 2 + (YY - rx[0, 2]) ** 2
+    want = np.sum(tx[0] * rx[0, 0] / (np.pi * ri2 ** 1.5 * rs2 ** 1.5)) * (48 * rho / M) ** 2
     assert got == pytest.approx(want, rel=1e-3)

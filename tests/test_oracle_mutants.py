@@ -49,6 +49,14 @@ MUTANTS = [
     ("disc_radius_doubled", CPP, "if (e.t > cfg.t_min && e.t < t_max && e.r <= rp) {",
      "if (e.t > cfg.t_min && e.t < t_max && e.r <= 2.0 * rp) {",
      [f"{T_GEO}::test_single_disc_hit_and_miss"]),
+    ("eq3_point_unweighted", CPP, "    sq = sq + w * e.q;", "    sq = sq + e.q;",
+     [f"{T_GEO}::test_depth_attenuation_closed_form"]),
+    ("eq3_normal_unweighted", CPP, "    sn = sn + w * S.N[i];\n  }\n  h.q = (1.0 / sw) * sq;",
+     "    sn = sn + S.N[i];\n  }\n  h.q = (1.0 / sw) * sq;",
+     [f"{T_GEO}::test_gaussian_weight_closed_form"]),
+    ("incidence_cosine_from_z", CPP, "  h.cos_in = std::fabs(dot(d, h.n));",
+     "  h.cos_in = std::fabs(d.z);",
+     [f"{T_EM}::test_diffuse_power_off_a_plane_is_the_lambertian_integral"]),
     # Sec. II-A voxelisation, Sec. II-B launch
     ("voxel_rounded_not_floored", CPP, "return (int)std::floor((float)s);",
      "return (int)std::lround((float)s);", [f"{T_GEO}::test_voxelisation_matches_float32_floor"]),
@@ -106,6 +114,9 @@ MUTANTS = [
      "return cd(eps_r, sigma / (2.0 * kPi * f * kEps0));", [T_EM]),
     ("fresnel_derivative_sign", CPP, "return -cos_t / (s * den * den);",
      "return cos_t / (s * den * den);", [f"{T_EM}::test_fresnel_derivative_complex_step"]),
+    ("fresnel_tm_derivative", CPP, "return cos_t * (eta - 2.0 * sin2) / (s * den * den);",
+     "return cos_t * (eta - sin2) / (s * den * den);",
+     [f"{T_EM}::test_fresnel_derivative_complex_step"]),
     ("los_delay_doubled", CPP, "P.tau = d / kC0;", "P.tau = 2.0 * d / kC0;",
      [f"{T_EM}::test_los_amplitude_and_delay"]),
     ("specular_delay_halved", CPP, "P.tau = len / kC0;", "P.tau = 0.5 * len / kC0;",
@@ -136,6 +147,11 @@ MUTANTS = [
     ("jones_basis_change_transposed", CPP, "J.B[m][0][1] = dot(sv[m + 1], pout[m]);",
      "J.B[m][0][1] = dot(pin[m + 1], sv[m]);", [T_POL]),
     ("jones_rx_basis", CPP, "J.r[1] = dot(tr, pout[k - 1]);", "J.r[1] = dot(tr, pin[k - 1]);", [T_POL]),
+    ("jones_partial_forward_index", CPP, "    dA[m][0] = w[0] * fwd[m][0];",
+     "    dA[m][0] = w[1] * fwd[m][0];", [T_POL]),
+    ("jones_partial_backward_transpose", CPP,
+     "      w[0] = u0 * J.B[m - 1][0][0] + u1 * J.B[m - 1][1][0];",
+     "      w[0] = u0 * J.B[m - 1][0][0] + u1 * J.B[m - 1][0][1];", [T_POL]),
     # Sec. II-B-3 edge diffraction
     ("utd_constant_sign", CPP, "const cd K = -std::exp(cd(0.0, -kPi / 4.0)) / (2.0 * nw",
      "const cd K = std::exp(cd(0.0, -kPi / 4.0)) / (2.0 * nw",
@@ -173,6 +189,8 @@ MUTANTS = [
     # Eq. 2 SDF (ablation)
     ("sdf_sign", CPP, "sf += w * dot(S->N[i], v);", "sf -= w * dot(S->N[i], v);",
      [f"{T_SDF}::test_single_point_gives_its_tangent_plane"]),
+    ("sdf_label_of_the_farthest_point", CPP, "if (dd < dmin || (dd == dmin && i < lab)) {",
+     "if (dd > dmin || dmin == kInf) {", [f"{T_SDF}::test_label_is_the_nearest_points"]),
     ("sdf_kernel_width", CPP, "inv2s2 = 1.0 / (2.0 * sigma * sigma);", "inv2s2 = 1.0 / (sigma * sigma);",
      [f"{T_SDF}::test_planar_faces_are_hit_exactly"]),
     ("sdf_defined_region", CPP, "const double wmin = std::exp(-2.0),",
@@ -211,6 +229,8 @@ MUTANTS = [
      [f"{T_MLP}::test_forward_and_gradients_match_torch_autograd"]),
     ("adam_bias_correction_dropped", "mlp.py", "mh = m / (1.0 - b1 ** t)", "mh = m",
      [f"{T_MLP}::test_adam_matches_torch_optim"]),
+    ("top_k_one_short", "mlp.py", "    k_top = min(k_top, n)", "    k_top = min(k_top, n - 1)",
+     [f"{T_MLP}::test_select_structure"]),
     ("adam_epsilon_inside_the_root", "mlp.py",
      "return theta - lr * mh / (np.sqrt(vh) + eps), m, v",
      "return theta - lr * mh / np.sqrt(vh + eps), m, v", [f"{T_MLP}::test_adam_matches_torch_optim"]),

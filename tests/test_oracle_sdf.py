@@ -79,6 +79,22 @@ def test_single_point_gives_its_tangent_plane():
         o3 = pd + r * SIG_POINT * u + 0.4 * nu
         assert np.all(np.abs(r * SIG_POINT * u) < 2 * SIG_POINT)
         assert osc.cast_sdf(o3, -nu, SIG_POINT)["hit"] == hit, r
+    # a surface is entered from outside only: from behind, the field rises
+    # through zero (- to +), which is no hit
+    assert not osc.cast_sdf(pd - 0.4 * nu, nu, SIG_POINT)["hit"]
+
+
+def test_label_is_the_nearest_points():
+    """Two points of different labels in one DPS: the SDF hit takes the label
+    of the point nearest to it."""
+    p = np.array([[0.10, 0.10, 0.0], [0.14, 0.10, 0.0]], np.float32)
+    n = np.array([[0, 0, 1.0], [0, 0, 1.0]], np.float32)
+    surf = np.array([3, 7], np.uint16)
+    osc = oracle.OracleScene(p, n, surf, np.zeros(2, np.uint8), rho=0.0625, r_p=0.05)
+    assert osc.n_dps == 1
+    for x, want in [(0.105, 3), (0.135, 7)]:
+        h = osc.cast_sdf(np.array([x, 0.10, 0.3]), np.array([0, 0, -1.0]), SIG_POINT)
+        assert h["hit"] and (h["labels"] & 0xFFFF) == want, x
 
 
 def test_first_crossing_matches_a_dense_scan():
