@@ -1442,7 +1442,11 @@ int orc_cast(void* s, const double* o, const double* d, int32_t skip_dps, double
   cfg.t_min = t_min;
   cfg.delta = delta;
   V3 dv = unit({d[0], d[1], d[2]});
-  Hit h = cast(*S, {o[0], o[1], o[2]}, dv, skip_dps, t_max, weighted != 0, cfg);
+  Hit h;  // a ray that is not finite hits nothing (and must not reach the grid walk)
+  const double in[6] = {o[0], o[1], o[2], dv.x, dv.y, dv.z};
+  bool finite = true;
+  for (double v : in) finite = finite && std::isfinite(v);
+  if (finite) h = cast(*S, {o[0], o[1], o[2]}, dv, skip_dps, t_max, weighted != 0, cfg);
   out[0] = h.t;
   out[1] = h.q.x; out[2] = h.q.y; out[3] = h.q.z;
   out[4] = h.n.x; out[5] = h.n.y; out[6] = h.n.z;
@@ -1475,6 +1479,11 @@ int orc_cast_sdf(void* s, const double* o_in, const double* d_in, double t_min, 
   Scene* S = (Scene*)s;
   const V3 o{o_in[0], o_in[1], o_in[2]};
   const V3 d = unit({d_in[0], d_in[1], d_in[2]});
+  if (!(std::isfinite(o.x) && std::isfinite(o.y) && std::isfinite(o.z) && std::isfinite(d.x) &&
+        std::isfinite(d.y) && std::isfinite(d.z))) {
+    *amb_out = 0;
+    return 0;  // a ray that is not finite hits nothing
+  }
   const double wmin = std::exp(-2.0), h = 0.5 * sigma, inv2s2 = 1.0 / (2.0 * sigma * sigma);
   double best = kInf;
   int best_D = -1;

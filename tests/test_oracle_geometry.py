@@ -151,6 +151,16 @@ def test_gaussian_weight_closed_form():
         assert np.arctan2(n_got[0], n_got[2]) == pytest.approx(theta, abs=1e-9)
 
 
+def test_non_finite_rays_hit_nothing():
+    """Test-API guard: a ray with a NaN or infinite component is a miss for
+    both intersection models (it must not reach the grid walk)."""
+    sc = _scene([[0, 0, 0]], [[0, 0, 1]], r_p=0.05, grid_cell=0.25)
+    for o, d in [([np.nan, 0, 1.0], [0, 0, -1]), ([0, 0, 1.0], [0, np.nan, -1]),
+                 ([0, 0, np.inf], [0, 0, -1]), ([0, 0, 1.0], [0, 0, 0])]:
+        assert not sc.cast(o, d)["hit"]
+        assert not sc.cast_sdf(np.array(o, float), np.array(d, float), 0.02)["hit"]
+
+
 def test_tie_rule_smaller_index():
     """Coplanar discs covering the hit point tie exactly in t: q_min is the
     smaller point index."""
