@@ -223,6 +223,44 @@ def test_diffracted_path_derivatives_match_central_differences(pol):
     assert np.all(G[dif, 2, :] == 0)  # no roughness dependence
 
 
+def test_diffraction_point_must_see_tx_and_rx():
+    """Sec. II-B-3: a diffracted path exists only when its diffraction point
+    sees both the TX and the RX.  One free-standing box edge, and a plate of
+    points placed across the TX -> D segment: without the plate the edge
+    gives its path, with it (or with the plate across D -> RX) none."""
+    g = _box_edge()
+    E = inputs.Edges(a=np.array([g["a"]], np.float32), b=np.array([g["b"]], np.float32),
+                     n0=np.array([g["n0"]], np.float32), n1=np.array([g["n1"]], np.float32),
+                     m0=np.zeros(1, np.uint8), m1=np.ones(1, np.uint8))
+    tx = np.array([-1.5, 0.2, 1.2])
+    rx = np.array([[1.2, -0.1, -1.0]])
+    ok, D, *_ = oracle.diffraction_geometry(tx, rx[0], g["a"], g["b"], g["n0"], g["n1"])
+    assert ok
+
+    def plate_across(p0, p1):
+        """A 0.6 m square of points, 3 cm apart, across the segment's middle."""
+        c = 0.5 * (p0 + p1)
+        u = (p1 - p0) / np.linalg.norm(p1 - p0)
+        e1 = np.cross(u, [0.0, 1.0, 0.0])
+        e1 /= np.linalg.norm(e1)
+        e2 = np.cross(u, e1)
+        s = np.arange(-0.3, 0.3 + 1e-9, 0.03)
+        A, B = np.meshgrid(s, s, indexing="ij")
+        pts = c + A.reshape(-1, 1) * e1 + B.reshape(-1, 1) * e2
+        return pts, np.tile(u, (len(pts), 1))
+
+    far = (np.array([[10.0, 10.0, 10.0]]), np.array([[0.0, 0.0, 1.0]]))  # nothing in the way
+    counts = []
+    for pts, nrm in (far, plate_across(tx, D), plate_across(D, rx[0])):
+        n = len(pts)
+        osc = oracle.OracleScene(pts.astype(np.float32), nrm.astype(np.float32),
+                                 np.zeros(n, np.uint16), np.zeros(n, np.uint8), r_p=0.05)
+        sim = oracle.OracleSim(osc, tx, rx, oracle.SimParams(max_depth=1, capture=1, diffuse=0,
+                                                             n_rays=100, diffraction=1), edges=E)
+        counts.append(int(np.sum(sim.paths()["type"] == 2)))
+    assert counts == [1, 0, 0]
+
+
 @pytest.mark.parametrize("pol", [0, 1])
 def test_grazing_face_material_drops_out(pol):
     """Each face's reflection factor takes that face's own incidence cosine:

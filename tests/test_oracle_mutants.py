@@ -179,6 +179,8 @@ MUTANTS = [
     ("face_0_incidence_angle", CPP, "const double c0 = G.sinb * std::sin(G.phi_in),",
      "const double c0 = G.sinb * std::sin(G.phi_out),",
      [f"{T_DIF}::test_grazing_face_material_drops_out"]),
+    ("diffraction_visibility_unchecked", CPP, "      if (h.hit) vis = false;", "      (void)h;",
+     [f"{T_DIF}::test_diffraction_point_must_see_tx_and_rx"]),
     ("transition_asymptote_sign", CPP, "term *= -(2.0 * n - 1.0) / (cd(0.0, 2.0 * x));",
      "term *= (2.0 * n - 1.0) / (cd(0.0, 2.0 * x));", [T_DIF]),
     ("exterior_angle_sign", CPP, "W.nw = 2.0 - std::acos", "W.nw = 2.0 + std::acos",
