@@ -65,11 +65,18 @@ MUTANTS = [
     ("fibonacci_half_turn", CPP, "double phi = 2.0 * kPi * std::ldexp((double)u, -64);",
      "double phi = kPi * std::ldexp((double)u, -64);", [f"{T_GEO}::test_fibonacci_directions"]),
     # Sec. II-B: continuation, visibility, capture, dedup
+    ("dps_launch_not_in_morton_order", CPP,
+     "  if (sim.p.launch == 1) return unit(sim.S->recv[sim.S->dps_morton[rid]] - sim.tx);",
+     "  if (sim.p.launch == 1) return unit(sim.S->recv[rid] - sim.tx);",
+     [f"{T_GEO}::test_dps_directed_launch_hits_its_target_dps"]),
     ("continuation_projects_not_mirrors", CPP,
      "d = d - 2.0 * dot(d, h.n) * h.n;  // specular continuation",
      "d = d - dot(d, h.n) * h.n;  // specular continuation",
      [f"{T_PATHS}::test_shoebox_image_sources"]),
     ("visibility_cast_to_the_centre", CPP, "double t_max = s - rx_margin(S);", "double t_max = s;",
+     [f"{T_PATHS}::test_rough_wall_fully_visible_from_the_front"]),
+    ("receiver_inside_a_dps_sees_nothing", CPP, "  if (t_max <= cfg.t_min) return {true,",
+     "  if (t_max <= cfg.t_min) return {false,",
      [f"{T_PATHS}::test_rough_wall_fully_visible_from_the_front"]),
     ("dedup_highest_ray_first", CPP, "return a.ray < b.ray;", "return a.ray > b.ray;",
      [f"{T_LAB}::test_dedup_tries_lowest_ray_ids_first"]),

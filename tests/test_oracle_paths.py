@@ -256,6 +256,15 @@ def test_rough_wall_fully_visible_from_the_front():
     bit, amb = sc.vis_pairs(rx, np.zeros(n, np.int32), np.arange(n, dtype=np.int32), delta=1e-7)
     assert n > 200
     assert bit[~amb].all() and amb.mean() < 0.02
+    # a receiver closer to a reception point than the DPS's extent sees it by
+    # definition (the test cast would start inside the DPS)
+    _, _, recv = sc.dps()
+    rx2 = np.array([[0.05, 0.0, 0.0]])
+    margin = np.sqrt(3.0) / 2.0 * 0.0625 + 0.05
+    near = np.nonzero(np.linalg.norm(recv - rx2[0], axis=1) - margin <= 1e-3)[0]
+    assert near.size >= 2
+    bit2, _ = sc.vis_pairs(rx2, np.zeros(near.size, np.int32), near.astype(np.int32))
+    assert bit2.all()
 
 
 # axis-aligned rectangles: (axis of the normal, plane coordinate, outward
