@@ -142,6 +142,27 @@ def _traffic(kernel):
     return val if (val is not None and sha == h.hexdigest()) else None
 
 
+def _l2_bytes(kernel):
+    """L2 bytes per unit (lts__t_bytes per cast, from an ncu capture of the
+    small case) of `kernel` in the committed summary, or None once the
+    kernel sources have changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "office_sim_top_kernels.md")
+    if not os.path.exists(path):
+        return None
+    val = sha = None
+    for ln in open(path):
+        f = ln.split()
+        if len(f) == 3 and f[0] == "l2_bytes_per_unit" and f[1] == kernel:
+            val = float(f[2])
+        if len(f) == 2 and f[0] == "source_sha256":
+            sha = f[1]
+    h = hashlib.sha256()
+    for rel in ("csrc/sim.cu", "csrc/nrt_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2507_04021_gb300", rel), "rb").read())
+    return val if (val is not None and sha == h.hexdigest()) else None
+
+
 def _alg_bytes():
     d = json.load(open(os.path.join(ROOT, "tests", "golden", "office_algorithmic_bytes.json")))
     return d
@@ -229,7 +250,7 @@ def batch_bench(args, scene, o, rank, stream, flush):
         g.replay()
     torch.cuda.synchronize()
     steps = max(1, args.batch_steps)
-    tot, pair_ms, launches, segs = [], [], 0, 0
+    tot, pair_ms, pair_paths_ms, launches, segs = [], [], [], 0, 0
     for _ in range(steps):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -240,14 +261,16 @@ def batch_bench(args, scene, o, rank, stream, flush):
         e1.record(stream)
         torch.cuda.synchronize()
         tot.append(e0.elapsed_time(e1))
-        pm, _ = g.batch_times()
+        pm, _, pv = g.batch_times(paths=True)
         pair_ms.append(pm)
+        pair_paths_ms.append(pv)
         _, c = g.counts()
         launches += c["kernel_launches"] + 1
         segs += c["segments"] + c["vis_casts"] + c["los_casts"] + c["validation_casts"]
     _, c = g.counts()
     g.close()
     pm = np.concatenate(pair_ms)
+    pv = np.concatenate(pair_paths_ms)
     ms = float(np.mean(tot))
     return {
         "workload": (f"{n} TX-RX pairs on the robot trajectory, RX (17.5, 8, 1.2), budgets "
@@ -257,8 +280,11 @@ def batch_bench(args, scene, o, rank, stream, flush):
         "ray_segments_per_s": segs / (sum(tot) / 1000.0),
         "pair_trace_done_ms": {"p50": float(np.percentile(pm, 50)),
                                "p99": float(np.percentile(pm, 99))},
-        "latency_note": "per-pair time from batch start to the pair's last traced ray "
-                        "(device timestamps); every pair's paths and field are ready at ms_per_batch",
+        "pair_paths_validated_ms": {"p50": float(np.percentile(pv, 50)),
+                                    "p99": float(np.percentile(pv, 99))},
+        "latency_note": "per-pair device timestamps from the start of the trace: the pair's last "
+                        "traced ray, and its last path key validated (its path set known); the "
+                        "field of all pairs follows in one pass, done at ms_per_batch",
         "autotune": {"configs": [list(c_) for c_ in cfgs], "trace_ms": [float(x) for x in tune_ms],
                      "chosen": {"packet": packet, "schedule": ["static", "persistent"][schedule]}},
         "graph": True, "gpu_launches": int(launches),
@@ -555,14 +581,20 @@ def ours(args):
 
     ab = _alg_bytes()
     peak, peak_kind = _peaks()
+    l2_peak = ctx.measure_l2(48 << 20, 50)  # this GPU's L2 read bandwidth, GB/s
     ph = {k: float(np.mean([x[k] for x in phases])) for k in phases[0]}
 
     def roof_entry(name, units, per_unit, ms, unit_name, traffic_key):
         achieved = units * per_unit / (ms / 1000.0) / 1e9
+        l2_unit = _l2_bytes(traffic_key)
+        l2_ach = None if l2_unit is None else units * l2_unit / (ms / 1000.0) / 1e9
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": _traffic(traffic_key), "kernel": name,
                 "peak_kind": peak_kind, "algorithmic_bytes_per_unit": per_unit,
-                "units_per_launch": units, "unit_kind": unit_name, "kernel_ms": ms}
+                "units_per_launch": units, "unit_kind": unit_name, "kernel_ms": ms,
+                "l2_peak": l2_peak, "l2_peak_kind": "measured (nrt_measure_l2, 48 MB x 50 reads)",
+                "l2_achieved": l2_ach, "l2_frac": None if l2_ach is None else l2_ach / l2_peak,
+                "l2_bytes_per_unit": l2_unit}
 
     # the dominant work: the validation phase (specular refinement + diffuse
     # shadow casts); diffuse shadow casts are oracle-counted, specular
@@ -624,11 +656,16 @@ def ours(args):
         line["gpu_launches"] = int(launches)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         info = run_oracle_sample(_env_int("NRT_CPU_SAMPLE", 150000))
+        one = run_oracle_sample(_env_int("NRT_CPU_SAMPLE_1T", 8000), threads=1)
         line["cpu_baseline"] = {
             "value": info["casts"] / info["seconds"], "unit": "ray-segments/s",
             "cores": info["cores"], "kind": "oracle",
             "sample": f"{info['rays']} rays of the 1M launch, full pipeline, "
-                      f"{info['casts']} casts in {info['seconds']:.1f} s"}
+                      f"{info['casts']} casts in {info['seconds']:.1f} s",
+            "single_thread": {"value": one["casts"] / one["seconds"], "unit": "ray-segments/s",
+                              "cores": 1,
+                              "sample": f"{one['rays']} rays of the 1M launch, full pipeline, "
+                                        f"{one['casts']} casts in {one['seconds']:.1f} s"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     last.close()

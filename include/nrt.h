@@ -164,6 +164,27 @@ nrt_status nrt_sync(nrt_ctx* ctx);
  * call enqueues its work on. */
 nrt_status nrt_get_stream(const nrt_ctx* ctx, void** stream);
 
+/* Measured L2 read bandwidth (the ceiling of the L2 roofline reported beside
+ * the HBM one for the traversal kernels; not part of the paper): a device
+ * buffer of `bytes` (in [2^20, 2^30], well under the 129 MB L2 for the L2
+ * figure) is filled, read once to warm the cache, then read `reps` times
+ * (1..1000) with 16-byte loads that bypass L1; *gbs (host) = bytes x reps /
+ * CUDA-event time, in GB/s.  Allocates and frees its buffer; synchronises.
+ * Errors: NRT_ERR_ARG, NRT_ERR_OOM, NRT_ERR_CUDA. */
+nrt_status nrt_measure_l2(nrt_ctx* ctx, int64_t bytes, int32_t reps, float* gbs);
+
+/* Watchdog of the bounded device waits (the tensor-core kernels' mbarrier
+ * waits for their MMAs: nrt_gemm_bf16, nrt_mlp_score, nrt_mlp_train): a wait
+ * makes at most `polls` non-blocking polls (0 restores the default: 2^22
+ * potentially blocking polls), then the kernel records a timeout, waits with
+ * the default limit for its own MMAs in flight, frees its tensor memory and
+ * returns; the call reports NRT_ERR_TIMEOUT (nrt_mlp_score, which does not
+ * synchronise, leaves it to the next nrt_mlp_train) and the context stays
+ * usable.  Not part of the paper: a
+ * failure-detection control (a small limit makes a wait run out on purpose).
+ * Errors: NRT_ERR_ARG for polls < 0. */
+nrt_status nrt_set_wait_limit(nrt_ctx* ctx, int64_t polls);
+
 /* Fill the paper's default trace parameters. */
 void nrt_trace_params_default(nrt_trace_params* p);
 
@@ -349,11 +370,15 @@ nrt_status nrt_trace_batch(nrt_scene* scene, const float* tx, const float* rx,
  * recorded capacities (rebuild the batch). */
 nrt_status nrt_batch_replay(nrt_result* result, const float* tx);
 
-/* Device timestamps of the last batch run: pair_ms[j] = time from the start
- * of the persistent trace to the moment pair j's last work item finished
- * (host double[n_pairs]); total_ms = device time of the whole simulation
- * (graph replay or normal run). */
-nrt_status nrt_batch_times(const nrt_result* result, double* pair_ms, float* total_ms);
+/* Per-pair latency of the last batch run, from device timestamps (globaltimer)
+ * taken from the start of the trace: pair_ms[j] = the moment pair j's last
+ * ray was traced (either schedule); pair_paths_ms[j] = the moment pair j's
+ * last path key finished validation, i.e. its path set is known (its field
+ * follows in one pass over all paths, done at total_ms).  host double[n_pairs]
+ * each, any may be NULL; -1 for a stamp that was not written.  total_ms =
+ * device time of the whole simulation (graph replay or normal run). */
+nrt_status nrt_batch_times(const nrt_result* result, double* pair_ms, float* total_ms,
+                           double* pair_paths_ms);
 
 /* Autotuner: time the batch trace phase for each (packet, schedule) pair
  * (host int32[n_cfg] each; `repeats` timed runs, the minimum kept) into
@@ -377,8 +402,11 @@ nrt_status nrt_autotune_batch(nrt_result* result, const int32_t* packets, const 
  * first call before any stream capture.  All calls share the array: calls
  * whose kernels overlap on the GPU (several streams or contexts at once)
  * race on it.  Each call writes every partial it reads, so no state carries
- * over between calls.  Work is enqueued on the context stream; the call does
- * not synchronise.
+ * over between calls.  The kernel reads the result's path count on the
+ * device, so a call recorded into a CUDA graph follows later traces of the
+ * same result (nrt_batch_replay).  Work is enqueued on the context stream;
+ * the call does not synchronise.  The call makes the context's device
+ * current for its launches and restores the caller's current device.
  * Errors: NRT_ERR_ARG for NULL pointers, more than 256 labels or a result
  * traced with NRT_POL_VECTOR or with diffraction (scalar reflection and
  * scattering models only); NRT_ERR_STATE before
@@ -456,6 +484,17 @@ void nrt_mlp_free(nrt_mlp* mlp);
 /* host float[45569]: the FP32 master parameters / the gradient of the last step */
 nrt_status nrt_mlp_params_read(const nrt_mlp* mlp, float* params);
 nrt_status nrt_mlp_grads_read(const nrt_mlp* mlp, float* grads);
+/* Checkpoint and resume of training (not part of the paper): the FP32 master
+ * parameters, Adam's first and second moments (host float[45569] each) and
+ * the number of Adam steps taken (their bias correction).  Writing restores
+ * all of it and the BF16 weight copies, so training continues exactly as it
+ * would have without the interruption.  Both synchronise.  Errors:
+ * NRT_ERR_ARG for NULL pointers, a negative step, non-finite values or a
+ * negative second moment. */
+nrt_status nrt_mlp_state_read(const nrt_mlp* mlp, float* params, float* adam_m, float* adam_v,
+                              int64_t* step);
+nrt_status nrt_mlp_state_write(nrt_mlp* mlp, const float* params, const float* adam_m,
+                               const float* adam_v, int64_t step);
 
 /* BF16 input features of launch rays ray_ids (device uint32[n]; NULL: rays
  * 0..n-1) from TX tx (host float[3]) into device uint16_t[n][96] (bfloat16

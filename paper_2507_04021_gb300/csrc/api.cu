@@ -149,6 +149,12 @@ void nrt_destroy(nrt_ctx* ctx) {
   ctx_release(ctx);
 }
 
+nrt_status nrt_set_wait_limit(nrt_ctx* ctx, int64_t polls) {
+  if (!ctx || polls < 0) return NRT_ERR_ARG;
+  ctx->wait_limit = polls;
+  return NRT_OK;
+}
+
 nrt_status nrt_get_stream(const nrt_ctx* ctx, void** stream) {
   if (!ctx || !stream) return NRT_ERR_ARG;
   *stream = (void*)ctx->stream;
@@ -719,8 +725,8 @@ nrt_status nrt_trace_batch(nrt_scene* s, const float* tx, const float* rx, const
       cudaMalloc(&r->pair_start, (n_pairs + 1) * 4) != cudaSuccess ||
       cudaMalloc(&r->pair_rays, n_pairs * 8) != cudaSuccess ||
       cudaMalloc(&r->chunk_start, (n_pairs + 1) * 4) != cudaSuccess ||
-      cudaMalloc(&r->stamps, (n_pairs + 1) * 8) != cudaSuccess ||
-      cudaMalloc(&r->queue, (n_pairs + 1) * 8) != cudaSuccess) {
+      cudaMalloc(&r->stamps, (2 * n_pairs + 1) * 8) != cudaSuccess ||
+      cudaMalloc(&r->queue, (3 * n_pairs + 1) * 8) != cudaSuccess) {
     ctx->last_error = "device allocation failed";
     return fail(NRT_ERR_OOM);
   }
@@ -729,7 +735,8 @@ nrt_status nrt_trace_batch(nrt_scene* s, const float* tx, const float* rx, const
   cudaMemcpyAsync(r->pair_start, start.data(), (n_pairs + 1) * 4, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(r->pair_rays, budget, n_pairs * 8, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(r->chunk_start, cstart.data(), (n_pairs + 1) * 4, cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(r->stamps, 0, (n_pairs + 1) * 8, st);
+  cudaMemsetAsync(r->stamps, 0, (2 * n_pairs + 1) * 8, st);
+  cudaMemsetAsync(r->queue, 0, (3 * n_pairs + 1) * 8, st);
   if (cudaStreamSynchronize(st) != cudaSuccess) return fail(NRT_ERR_CUDA);
   rc = run_trace(r, nullptr);
   if (rc != NRT_OK) return fail(rc);
@@ -752,16 +759,23 @@ nrt_status nrt_batch_replay(nrt_result* r, const float* tx) {
   return batch_graph_replay(r, tx);
 }
 
-nrt_status nrt_batch_times(const nrt_result* r, double* pair_ms, float* total_ms) {
+nrt_status nrt_batch_times(const nrt_result* r, double* pair_ms, float* total_ms,
+                           double* pair_paths_ms) {
   if (!r || r->n_pairs <= 0) return NRT_ERR_ARG;
   nrt_ctx* ctx = r->scene->ctx;
-  std::vector<unsigned long long> t(r->n_pairs + 1);
+  const int P = r->n_pairs;
+  std::vector<unsigned long long> t(2 * P + 1);
   NRT_CUDA_TRY(ctx, cudaMemcpyAsync(t.data(), r->stamps, t.size() * 8, cudaMemcpyDeviceToHost,
                                     ctx->stream));
   NRT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  // a stamp that was never written (0, or before the start) reads as -1
+  auto since = [&](unsigned long long v) {
+    return v >= t[0] && v != 0ull ? (double)(v - t[0]) * 1e-6 : -1.0;
+  };
   if (pair_ms)
-    for (int j = 0; j < r->n_pairs; ++j)
-      pair_ms[j] = t[1 + j] >= t[0] ? (double)(t[1 + j] - t[0]) * 1e-6 : 0.0;
+    for (int j = 0; j < P; ++j) pair_ms[j] = since(t[1 + j]);
+  if (pair_paths_ms)
+    for (int j = 0; j < P; ++j) pair_paths_ms[j] = since(t[1 + P + j]);
   if (total_ms) {
     float ms[8];
     nrt_result_times(r, ms);

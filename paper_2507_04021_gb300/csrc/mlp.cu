@@ -51,6 +51,8 @@ inline unsigned blocks_for_n(int64_t n) {
 constexpr int kGemmThreads = 128;
 constexpr int kKChunk = 64;          // K elements staged per round
 constexpr int kMaxN = 256;
+// default spin limit of a bounded mbarrier wait (nrt_set_wait_limit replaces
+// it for the waits on the MMAs; the drain after a timeout always uses it)
 constexpr long long kSpinLimit = 1ll << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -87,8 +89,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t phase) {
   return ok != 0;
 }
 
-// bounded wait; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; false on timeout.  polls = 0: the default watchdog,
+// kSpinLimit potentially blocking try_waits; polls > 0 (set by the host
+// through nrt_set_wait_limit): that many non-blocking test_waits.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long polls = 0) {
+  if (polls > 0) {
+    for (long long i = 0; i < polls; ++i)
+      if (mbar_test_wait(bar, phase)) return true;
+    return false;
+  }
   for (long long i = 0; i < kSpinLimit; ++i)
     if (mbar_try_wait(bar, phase)) return true;
   return false;
@@ -150,7 +170,7 @@ template <bool kAtomic>
 __global__ void __launch_bounds__(kGemmThreads)
     gemm_bf16_tc_kernel(const bf16* __restrict__ A, int64_t lda, const bf16* __restrict__ B,
                         int64_t ldb, float* __restrict__ Cm, int64_t ldc, int64_t M, int N,
-                        int64_t K, int64_t k_split, uint32_t* __restrict__ err) {
+                        int64_t K, int64_t k_split, uint32_t* __restrict__ err, long long spin) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sA = smem;                                 // 128 x 64 bf16 = 16 KB
   uint8_t* sB = smem + 128 * kKChunk * 2;             // N x 64 bf16 <= 32 KB
@@ -196,7 +216,7 @@ __global__ void __launch_bounds__(kGemmThreads)
       tc_commit(smem_u32(bar));
     }
     issued = true;
-    const bool got = mbar_wait(smem_u32(bar), phase);
+    const bool got = mbar_wait(smem_u32(bar), phase, spin);
     // block-wide: every thread leaves the loop together; the staged tiles
     // may be overwritten once all have seen the MMAs complete
     if (!__syncthreads_and(got)) {
@@ -239,6 +259,8 @@ constexpr size_t kGemmSmem = 128 * kKChunk * 2 + kMaxN * kKChunk * 2 + 16;
 
 namespace nrt {
 
+long long wait_limit(const nrt_ctx* ctx) { return ctx->wait_limit > 0 ? (long long)ctx->wait_limit : 0; }
+
 // C (+)= A B^T.  Requirements checked here: N a multiple of 16 in [16, 256],
 // K, lda, ldb multiples of 8 (16-byte rows), ldc a multiple of 4, 16-byte
 // aligned base pointers.  k_split > 0 splits K across CTAs (atomic adds).
@@ -269,10 +291,12 @@ nrt_status gemm_bf16(nrt_ctx* ctx, const bf16* A, int64_t lda, const bf16* B, in
   const dim3 grid((unsigned)((M + 127) / 128), (unsigned)((K + ks - 1) / ks));
   if (atomic)
     gemm_bf16_tc_kernel<true><<<grid, kGemmThreads, kGemmSmem, ctx->stream>>>(A, lda, B, ldb, C, ldc, M,
-                                                                             N, K, ks, err);
+                                                                             N, K, ks, err,
+                                                                             wait_limit(ctx));
   else
     gemm_bf16_tc_kernel<false><<<grid, kGemmThreads, kGemmSmem, ctx->stream>>>(A, lda, B, ldb, C, ldc,
-                                                                              M, N, K, ks, err);
+                                                                              M, N, K, ks, err,
+                                                                              wait_limit(ctx));
   count_launch();
   NRT_CUDA_TRY(ctx, cudaGetLastError());
   return NRT_OK;
@@ -374,8 +398,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 }
 
 // bounded wait for the tile's MMAs, agreed by the whole block
-__device__ __forceinline__ bool block_wait(uint32_t bar, uint32_t phase) {
-  const bool got = mbar_wait(bar, phase);
+__device__ __forceinline__ bool block_wait(uint32_t bar, uint32_t phase, long long spin) {
+  const bool got = mbar_wait(bar, phase, spin);
   return __syncthreads_and(got) != 0;
 }
 
@@ -412,7 +436,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1)
     mlp_score_fused_kernel(SampleSrc S, int64_t n, int64_t n_rays, const bf16* __restrict__ W1,
                            const bf16* __restrict__ W2, const bf16* __restrict__ W3,
                            const float* __restrict__ theta, float* __restrict__ logits,
-                           uint32_t* __restrict__ err) {
+                           uint32_t* __restrict__ err, long long spin) {
   extern __shared__ __align__(1024) uint8_t smem[];
   float* vec = reinterpret_cast<float*>(smem + kSVec);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSBar);
@@ -475,7 +499,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1)
     // layer 1 (K = 96)
     issue_layer(tmem, sact, smem_u32(smem + kSW1), kIn, bar_a);
     issued = true;
-    if (!(ok = block_wait(bar_a, phase))) break;
+    if (!(ok = block_wait(bar_a, phase, spin))) break;
     phase ^= 1u;
     tc_fence_after();
     hidden_epilogue(tmem, vec, act);
@@ -484,7 +508,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1)
     __syncthreads();
     // layer 2
     issue_layer(tmem, sact, smem_u32(smem + kSW2), kH, bar_a);
-    if (!(ok = block_wait(bar_a, phase))) break;
+    if (!(ok = block_wait(bar_a, phase, spin))) break;
     phase ^= 1u;
     tc_fence_after();
     hidden_epilogue(tmem, vec + kH, act);
@@ -493,7 +517,7 @@ __global__ void __launch_bounds__(kScoreThreads, 1)
     __syncthreads();
     // layer 3 and the output layer
     issue_layer(tmem, sact, smem_u32(smem + kSW3), kH, bar_a);
-    if (!(ok = block_wait(bar_a, phase))) break;
+    if (!(ok = block_wait(bar_a, phase, spin))) break;
     phase ^= 1u;
     tc_fence_after();
     float z = 0.0f;
@@ -896,6 +920,38 @@ nrt_status nrt_mlp_params_read(const nrt_mlp* m, float* params) {
   return NRT_OK;
 }
 
+nrt_status nrt_mlp_state_read(const nrt_mlp* m, float* params, float* adam_m, float* adam_v,
+                              int64_t* step) {
+  if (!m || !params || !adam_m || !adam_v || !step) return NRT_ERR_ARG;
+  cudaStream_t st = m->ctx->stream;
+  NRT_CUDA_TRY(m->ctx, cudaMemcpyAsync(params, m->theta, (size_t)kNParams * 4, cudaMemcpyDeviceToHost, st));
+  NRT_CUDA_TRY(m->ctx, cudaMemcpyAsync(adam_m, m->m, (size_t)kNParams * 4, cudaMemcpyDeviceToHost, st));
+  NRT_CUDA_TRY(m->ctx, cudaMemcpyAsync(adam_v, m->v, (size_t)kNParams * 4, cudaMemcpyDeviceToHost, st));
+  NRT_CUDA_TRY(m->ctx, cudaStreamSynchronize(st));
+  *step = m->t;
+  return NRT_OK;
+}
+
+nrt_status nrt_mlp_state_write(nrt_mlp* m, const float* params, const float* adam_m,
+                               const float* adam_v, int64_t step) {
+  if (!m || !params || !adam_m || !adam_v || step < 0) return NRT_ERR_ARG;
+  for (int64_t i = 0; i < kNParams; ++i)
+    if (!std::isfinite(params[i]) || !std::isfinite(adam_m[i]) || !(adam_v[i] >= 0.0f) ||
+        !std::isfinite(adam_v[i])) {
+      m->ctx->last_error = "nrt_mlp_state_write: non-finite value or negative second moment";
+      return NRT_ERR_ARG;
+    }
+  NRT_CUDA_TRY(m->ctx, cudaSetDevice(m->ctx->device));
+  cudaStream_t st = m->ctx->stream;
+  NRT_CUDA_TRY(m->ctx, cudaMemcpyAsync(m->theta, params, (size_t)kNParams * 4, cudaMemcpyHostToDevice, st));
+  NRT_CUDA_TRY(m->ctx, cudaMemcpyAsync(m->m, adam_m, (size_t)kNParams * 4, cudaMemcpyHostToDevice, st));
+  NRT_CUDA_TRY(m->ctx, cudaMemcpyAsync(m->v, adam_v, (size_t)kNParams * 4, cudaMemcpyHostToDevice, st));
+  MTRY(cast_weights(m));  // BF16 copies of the restored master weights
+  NRT_CUDA_TRY(m->ctx, cudaStreamSynchronize(st));
+  m->t = step;
+  return NRT_OK;
+}
+
 nrt_status nrt_mlp_grads_read(const nrt_mlp* m, float* grads) {
   if (!m || !grads) return NRT_ERR_ARG;
   NRT_CUDA_TRY(m->ctx, cudaMemcpyAsync(grads, m->grad, (size_t)kNParams * 4, cudaMemcpyDeviceToHost,
@@ -939,7 +995,8 @@ nrt_status nrt_mlp_score(nrt_mlp* m, const float* tx, const uint32_t* ray_ids, i
   const int64_t tiles = (n + 127) / 128;
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, ctx->sm_count);
   mlp_score_fused_kernel<<<grid, kScoreThreads, kScoreSmem, st>>>(S, n, m->n_rays, m->W1, m->W2, m->W3,
-                                                                 m->theta, logits, m->err);
+                                                                 m->theta, logits, m->err,
+                                                                 wait_limit(ctx));
   count_launch();
   NRT_CUDA_TRY(ctx, cudaGetLastError());
   return NRT_OK;

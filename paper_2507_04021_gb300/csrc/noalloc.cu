@@ -31,22 +31,21 @@ using namespace nrt;
 constexpr int kMaxDevices = 64;
 double* g_scratch_addr[kMaxDevices] = {};
 
-__device__ __forceinline__ int na_mat(const PathRec& p, int m) {
-  const uint64_t mats = (uint64_t)p.mats_lo | ((uint64_t)p.mats_hi << 32);
-  return (int)((mats >> (8 * m)) & 0xFF);
-}
-
 // Per path: d|a|^2 / d(eps_r, sigma, S) of each interaction's label, scaled
-// by 2 dL/dP_j and accumulated per block in shared memory.  Every block
-// writes all 3 * n_labels of its partial slots, so nothing left by an earlier
-// call is ever read.
+// by 2 dL/dP_j and accumulated per block in shared memory.  The path count
+// is read on the device (capped at the record capacity), so work recorded
+// into a CUDA graph follows later traces of the same result.  Every block
+// writes all 3 * n_labels of its partial slots, so nothing left by an
+// earlier call is ever read.
 __global__ void __launch_bounds__(kNaThreads)
-    adjoint_noalloc_kernel(const PathRec* __restrict__ P, int64_t n, const float* __restrict__ mat,
-                           float freq, int pol, const float* __restrict__ dLdP, int n_labels,
+    adjoint_noalloc_kernel(const PathRec* __restrict__ P, const unsigned long long* __restrict__ n_p,
+                           int64_t cap, const float* __restrict__ mat, float freq, int pol,
+                           const float* __restrict__ dLdP, int n_labels,
                            double* __restrict__ partial) {
   __shared__ double acc[3 * kNaMaxLabels];
   for (int i = threadIdx.x; i < 3 * n_labels; i += blockDim.x) acc[i] = 0.0;
   __syncthreads();
+  const int64_t n = min((int64_t)*n_p, cap);
   const float ks = (float)(1.0 / (2.0 * 3.14159265358979323846 * kEps0)) / freq;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -57,18 +56,8 @@ __global__ void __launch_bounds__(kNaThreads)
     float2 fac[kMaxDepth], dfe[kMaxDepth], dfs[kMaxDepth];
     int labs[kMaxDepth];
     for (int m = 0; m < k; ++m) {
-      const int l = na_mat(p, m);
-      labs[m] = l;
-      const float2 eta = permittivity(mat[l], mat[256 + l], freq);
-      const float2 G = fresnel(eta, p.cosv[m], pol);
-      const float2 dG = dfresnel(eta, p.cosv[m], pol);
-      const float Sl = mat[512 + l];
-      const bool last_d = diffuse && m == k - 1;
-      const float R = sqrtf(fmaxf(0.0f, 1.0f - Sl * Sl));
-      const float c = last_d ? Sl : R;
-      fac[m] = cscale(c, G);
-      dfe[m] = cscale(c, dG);
-      dfs[m] = last_d ? G : cscale(R > 0.0f ? -Sl / R : 0.0f, G);
+      labs[m] = path_mat(p, m);
+      interaction_factors(p, m, k, diffuse, mat, freq, pol, &fac[m], &dfe[m], &dfs[m]);
     }
     float2 a = make_float2(p.geo, 0.0f);
     for (int m = 0; m < k; ++m) a = cmul(a, fac[m]);
@@ -123,18 +112,32 @@ extern "C" nrt_status nrt_backward_noalloc(nrt_result* r, const float* dL_dpower
     ctx->last_error = "nrt_backward_noalloc supports device ordinals below 64";
     return NRT_ERR_ARG;
   }
-  NRT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  // the launches need the context's device current; the caller's current
+  // device is put back before returning
+  int prev = -1;
+  NRT_CUDA_TRY(ctx, cudaGetDevice(&prev));
+  if (prev != ctx->device) NRT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  nrt_status rc = NRT_OK;
   // one-time set-up per device (with that device current): the device
   // address of the scratch array
   double* scratch = g_scratch_addr[ctx->device];
+  cudaError_t e = cudaSuccess;
   if (!scratch) {
-    NRT_CUDA_TRY(ctx, cudaGetSymbolAddress((void**)&scratch, g_adjoint_scratch));
-    g_scratch_addr[ctx->device] = scratch;
+    e = cudaGetSymbolAddress((void**)&scratch, g_adjoint_scratch);
+    if (e == cudaSuccess) g_scratch_addr[ctx->device] = scratch;
   }
-  cudaStream_t st = ctx->stream;
-  adjoint_noalloc_kernel<<<kNaBlocks, kNaThreads, 0, st>>>(
-      (const PathRec*)r->paths, r->n_paths, sc->mat, r->p.freq, r->p.pol, dL_dpower, L, scratch);
-  adjoint_noalloc_reduce<<<(3 * L + 127) / 128, 128, 0, st>>>(scratch, L, grad);
-  NRT_CUDA_TRY(ctx, cudaGetLastError());
-  return NRT_OK;
+  if (e == cudaSuccess) {
+    cudaStream_t st = ctx->stream;
+    adjoint_noalloc_kernel<<<kNaBlocks, kNaThreads, 0, st>>>(
+        (const PathRec*)r->paths, r->ctr + kCtrPaths, r->path_cap, sc->mat, r->p.freq, r->p.pol,
+        dL_dpower, L, scratch);
+    adjoint_noalloc_reduce<<<(3 * L + 127) / 128, 128, 0, st>>>(scratch, L, grad);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    ctx->last_error = std::string("nrt_backward_noalloc: ") + cudaGetErrorString(e);
+    rc = NRT_ERR_CUDA;
+  }
+  if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+  return rc;
 }

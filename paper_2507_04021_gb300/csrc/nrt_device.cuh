@@ -30,7 +30,6 @@ enum : uint32_t {
   kErrCandFull = 1u << 2,    // candidate buffer full
   kErrKeyFull = 1u << 3,     // more distinct keys than the key capacity
   kErrPathFull = 1u << 4,    // path buffer full
-  kErrTimeout = 1u << 5,     // bounded loop gave up
 };
 
 // ---------------------------------------------------------------- vector math

@@ -20,6 +20,8 @@ struct nrt_ctx {
   // launch order of the full Fibonacci launch, cached per ray count
   uint32_t* order = nullptr;
   int64_t order_n = 0;
+  // polls of a bounded device wait before it gives up (0 = the default)
+  int64_t wait_limit = 0;
 };
 
 struct nrt_scene {
@@ -66,8 +68,12 @@ struct nrt_result {
   uint32_t* pair_start = nullptr;  // batch: first row of each pair [n_pairs + 1]
   int64_t* pair_rays = nullptr;    // batch: Fibonacci N of each pair
   uint32_t* chunk_start = nullptr; // batch: first work chunk of each pair [n_pairs + 1]
-  unsigned long long* stamps = nullptr;  // batch: [0] trace start, [1 + j] pair j traced (ns)
-  unsigned long long* queue = nullptr;   // batch: work queue head + per-pair chunks left
+  // batch latency (ns, globaltimer): [0] trace start, [1 + j] pair j traced,
+  // [1 + P + j] pair j's last key validated
+  unsigned long long* stamps = nullptr;
+  // batch: [0] work queue head, [1 + j] chunks left, [1 + P + j] rays left,
+  // [1 + 2P + j] keys left of pair j
+  unsigned long long* queue = nullptr;
   int packet = 64;     // rays per work item of the persistent trace
   int schedule = 1;    // 0 static grid-stride, 1 persistent work queue
   float4* rec_q = nullptr;   // [n_seg][n_traced]: q.xyz, segment length
@@ -146,6 +152,38 @@ struct alignas(16) PathRec {
 };
 static_assert(sizeof(PathRec) == 144, "PathRec layout");
 
+// material label of interaction m of a path record
+__device__ __forceinline__ int path_mat(const PathRec& P, int m) {
+  const uint64_t mats = (uint64_t)P.mats_lo | ((uint64_t)P.mats_hi << 32);
+  return (int)((mats >> (8 * m)) & 0xFF);
+}
+
+// Per-interaction factors of a path (the EM readings of the field: effective
+// roughness R = sqrt(1 - S^2) on a specular reflection, S on the diffuse last
+// interaction, times the Fresnel coefficient): c Gamma (scalar models: pol's
+// coefficient; vector model: TE then TM) and, for the adjoint, c dGamma/deta
+// and dc/dS Gamma.  mat holds [3][256] eps_r, sigma, S per label.  Shared by
+// the field kernel and both adjoint kernels.
+__device__ __forceinline__ void interaction_factors(const PathRec& p, int m, int k, int diffuse,
+                                                    const float* __restrict__ mat, float freq,
+                                                    int pol, float2* D, float2* dDe, float2* dDs) {
+  const int l = path_mat(p, m);
+  const float2 eta = permittivity(mat[l], mat[256 + l], freq);
+  const float Sl = mat[512 + l];
+  const bool last_d = diffuse && m == k - 1;
+  const float R = sqrtf(fmaxf(0.0f, 1.0f - Sl * Sl));
+  const float c = last_d ? Sl : R;
+  const float dc = last_d ? 1.0f : (R > 0.0f ? -Sl / R : 0.0f);
+  const int n = pol == 2 ? 2 : 1;
+  for (int t = 0; t < n; ++t) {
+    const int pp = pol == 2 ? t : pol;
+    const float2 G = fresnel(eta, p.cosv[m], pp);
+    D[t] = cscale(c, G);
+    if (dDe) dDe[t] = cscale(c, dfresnel(eta, p.cosv[m], pp));
+    if (dDs) dDs[t] = cscale(dc, G);
+  }
+}
+
 void scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, cudaStream_t st);
 // n = capacity of the buffers (sets the grid); n_dev, if given, is the live
 // count on the device (at most n): only the first *n_dev entries are sorted
@@ -155,6 +193,9 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv
                       const unsigned long long* n_dev = nullptr);
 
 SceneView scene_view(const nrt_scene* s);
+
+// polls a bounded tensor-core wait makes before giving up (mlp.cu)
+long long wait_limit(const nrt_ctx* ctx);
 
 // drop one reference to a context (frees it with the last one)
 void ctx_release(nrt_ctx* ctx);

@@ -201,4 +201,62 @@ void radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* tk, uint32_t* tv
   cudaFreeAsync(offs, st);
 }
 
+// ---------------------------------------------------------------- L2 probe
+// Read bandwidth of the L2 cache, for the L2 roofline of the traversal
+// kernels: a buffer well under the L2 size (129 MB on GB300) is read once to
+// warm it, then `reps` times by a grid of resident blocks with 16-byte loads
+// that bypass L1 (ld.global.cg), each block sweeping a fixed slice.
+namespace {
+
+__global__ void __launch_bounds__(512)
+    l2_read_kernel(const float4* __restrict__ buf, int64_t n4, int reps, float* __restrict__ sink) {
+  float acc = 0.0f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int r = 0; r < reps; ++r) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+      const float4 v = __ldcg(buf + i);
+      acc += v.x + v.y + v.z + v.w;
+    }
+  }
+  if (acc == 1.2345678e-30f) sink[0] = acc;  // keeps the loads; never true for the zero fill
+}
+
+}  // namespace
+
 }  // namespace nrt
+
+extern "C" nrt_status nrt_measure_l2(nrt_ctx* ctx, int64_t bytes, int32_t reps, float* gbs) {
+  using namespace nrt;
+  if (!ctx || !gbs || bytes < (1 << 20) || bytes > ((int64_t)1 << 30) || reps < 1 || reps > 1000)
+    return NRT_ERR_ARG;
+  NRT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  const int64_t n4 = bytes / 16;
+  float4* buf = nullptr;
+  float* sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  NRT_CUDA_TRY(ctx, cudaMallocAsync(&buf, n4 * 16, st));
+  NRT_CUDA_TRY(ctx, cudaMallocAsync(&sink, 4, st));
+  NRT_CUDA_TRY(ctx, cudaMemsetAsync(buf, 0, n4 * 16, st));
+  NRT_CUDA_TRY(ctx, cudaEventCreate(&e0));
+  NRT_CUDA_TRY(ctx, cudaEventCreate(&e1));
+  const unsigned grid = (unsigned)ctx->sm_count * 4;
+  l2_read_kernel<<<grid, 512, 0, st>>>(buf, n4, 1, sink);  // warm: the buffer into L2
+  count_launch();
+  NRT_CUDA_TRY(ctx, cudaEventRecord(e0, st));
+  l2_read_kernel<<<grid, 512, 0, st>>>(buf, n4, reps, sink);
+  count_launch();
+  NRT_CUDA_TRY(ctx, cudaEventRecord(e1, st));
+  NRT_CUDA_TRY(ctx, cudaEventSynchronize(e1));
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(buf, st);
+  cudaFreeAsync(sink, st);
+  NRT_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  NRT_CUDA_TRY(ctx, cudaGetLastError());
+  *gbs = (float)((double)n4 * 16.0 * reps / (ms * 1e-3) / 1e9);
+  return NRT_OK;
+}
+

@@ -178,6 +178,28 @@ __device__ __forceinline__ void count_add(unsigned long long* c, unsigned long l
   if ((threadIdx.x & 31) == 0 && v) atomicAdd(c, v);
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Batch latency bookkeeping: lanes whose unit of work for pair `pj` ended
+// (a traced ray, a validated key) subtract it from the pair's count, one
+// atomic per pair and warp step; the lane that takes the count to zero
+// stamps the pair's completion time.  All active lanes call it together.
+__device__ __forceinline__ void pair_units_done(bool ended, int pj, unsigned long long* left,
+                                                unsigned long long* stamp) {
+  const unsigned act = __activemask();
+  const unsigned em = __ballot_sync(act, ended);
+  if (!ended) return;
+  const unsigned peers = __match_any_sync(em, pj);
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+    const unsigned long long n = (unsigned long long)__popc(peers);
+    if (atomicAdd(left + pj, 0ull - n) == n) stamp[pj] = global_ns();
+  }
+}
+
 #define NRT_STACK_DECL                                       \
   __shared__ int stk[kStackDepth * kTraceThreads];           \
   __shared__ float tstk[kStackDepth * kTraceThreads];        \
@@ -466,10 +488,13 @@ __device__ __forceinline__ void ray_start(const SceneView& S, const SimConst& C,
 // order from a counter (one warp-aggregated atomic per fetch), so rays that
 // escape early do not leave their lanes idle while the warp's longest ray
 // finishes.  Each ray's casts are those of a ray-at-a-time loop.
+// Batches: pair_left[j] counts pair j's rays still in flight (set before the
+// launch); the lane that ends its last ray stamps pair_done[j].
 __global__ void __launch_bounds__(kTraceThreads, 8)
     trace_kernel(SceneView S, SimConst C, const uint32_t* __restrict__ ray_of_row,
                  const uint32_t* __restrict__ order, Records R, unsigned long long* __restrict__ fetch,
-                 unsigned long long* ctr) {
+                 unsigned long long* ctr, unsigned long long* pair_left,
+                 unsigned long long* pair_done) {
   NRT_STACK_DECL
   unsigned long long segs = 0;
   const int lane = threadIdx.x & 31;
@@ -497,23 +522,25 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
                                   my_tstk, kTraceThreads, err);
     ++segs;
     const int64_t a = R.at(seg, row);
+    bool ended = true;
     if (h.idx < 0) {
       R.i[a] = make_int2(-1, 0);
-      have = false;
-      continue;
+    } else {
+      const float3 q = o + h.tbar * d;
+      const float dn = dot3(d, h.n);
+      float3 dout = d - (2.0f * dn) * h.n;
+      dout = unit3(dout);
+      R.q[a] = make_float4(q.x, q.y, q.z, h.tbar);
+      R.n[a] = make_float4(h.n.x, h.n.y, h.n.z, fabsf(dn));
+      R.d[a] = make_float4(dout.x, dout.y, dout.z, __int_as_float(h.dps));
+      R.i[a] = make_int2(h.idx, (int)h.labels);
+      o = q;
+      d = dout;
+      skip = h.dps;
+      ended = ++seg >= C.n_seg;
     }
-    const float3 q = o + h.tbar * d;
-    const float dn = dot3(d, h.n);
-    float3 dout = d - (2.0f * dn) * h.n;
-    dout = unit3(dout);
-    R.q[a] = make_float4(q.x, q.y, q.z, h.tbar);
-    R.n[a] = make_float4(h.n.x, h.n.y, h.n.z, fabsf(dn));
-    R.d[a] = make_float4(dout.x, dout.y, dout.z, __int_as_float(h.dps));
-    R.i[a] = make_int2(h.idx, (int)h.labels);
-    o = q;
-    d = dout;
-    skip = h.dps;
-    if (++seg >= C.n_seg) have = false;
+    if (pair_left) pair_units_done(ended, pair_of_row(C, (uint32_t)row), pair_left, pair_done);
+    have = !ended;
   }
   count_add(ctr + kCtrSegments, segs);
 }
@@ -802,10 +829,11 @@ __global__ void __launch_bounds__(kSlotThreads)
 // flat from 9 to 15; RX-first order, fb = mb, 15.4 ms).  The fields are
 // packed tight (jb bits of RX, mb = 3 x grid bits of Morton code, one type
 // bit) so that the sort takes as few 8-bit passes as the scene needs.
+// Batches also count each pair's keys into pair_keys (NULL otherwise).
 __global__ void val_order_kernel(SceneView S, Records R, Table T, KeyState K,
                                  const unsigned long long* __restrict__ counts,
                                  uint64_t* __restrict__ sort_key, uint32_t* __restrict__ sort_val,
-                                 int jb, int mb, int fb_spec) {
+                                 int jb, int mb, int fb_spec, unsigned long long* pair_keys) {
   const int64_t n_keys = (int64_t)counts[2];
   for (int64_t kid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; kid < n_keys;
        kid += (int64_t)gridDim.x * blockDim.x) {
@@ -827,6 +855,7 @@ __global__ void val_order_kernel(SceneView S, Records R, Table T, KeyState K,
     sort_key[kid] = ((uint64_t)(spec ? 0u : 1u) << (jb + mb)) | ((uint64_t)(mort >> fb) << (jb + fb)) |
                     ((hi >> 56) << fb) | fine;
     sort_val[kid] = (uint32_t)kid;
+    if (pair_keys) atomicAdd(pair_keys + (hi >> 56), 1ull);
   }
 }
 
@@ -890,6 +919,8 @@ struct ValArgs {
   PathRec* paths;
   int64_t path_cap;
   SortedCand SC;  // each key's candidates, one run per slot in ray order
+  unsigned long long* pair_keys;   // batches: keys of pair j still being validated
+  unsigned long long* pair_ready;  // batches: pair j's last key finished (stamp)
 };
 
 // Outcome of one try of key kid (candidate row *row at position *pos of the
@@ -1021,7 +1052,9 @@ __global__ void __launch_bounds__(kTraceThreads, 6)
               sqrtf(rho * rho * ci * cs / 3.14159265358979f) / (ri * rs);
       P.length = ri + rs;
     }
-    if (key_try(A, kid, valid, &P, &row, &pos, ctr, C)) have = false;
+    const bool fin = key_try(A, kid, valid, &P, &row, &pos, ctr, C);
+    if (A.pair_keys) pair_units_done(fin, j, A.pair_keys, A.pair_ready);
+    if (fin) have = false;
   }
   count_add(ctr + kCtrValCasts, casts);
   count_add(ctr + kCtrDiffCasts, casts);
@@ -1190,7 +1223,9 @@ __global__ void __launch_bounds__(kTraceThreads, 6)
       P.length = len;
       P.geo = C.lambda / (4.0f * 3.14159265358979f * len);
     }
-    if (key_try(A, kid, valid, &P, &row, &pos, ctr, C)) have = false;
+    const bool fin = key_try(A, kid, valid, &P, &row, &pos, ctr, C);
+    if (A.pair_keys) pair_units_done(fin, j, A.pair_keys, A.pair_ready);
+    if (fin) have = false;
     else fresh = true;
   }
   count_add(ctr + kCtrValCasts, casts);
@@ -1322,10 +1357,6 @@ __global__ void path_gather_kernel(const PathRec* __restrict__ src, const uint32
 }
 
 // ---------------------------------------------------------------- field
-__device__ __forceinline__ int path_mat(const PathRec& P, int m) {
-  const uint64_t mats = (uint64_t)P.mats_lo | ((uint64_t)P.mats_hi << 32);
-  return (int)((mats >> (8 * m)) & 0xFF);
-}
 
 // ---------------------------------------------------------------- vector polarisation
 // pol = NRT_POL_VECTOR.  TX and RX radiate / receive along theta^ (spherical
@@ -1413,28 +1444,6 @@ __device__ __forceinline__ float3 frame_tx(const PathFrame& F, int j) {
 }
 __device__ __forceinline__ float3 frame_rx(const PathFrame& F, int j) {
   return xyz(__ldg(F.rx + (F.batch ? 0 : j)));
-}
-
-// per-interaction factors c Gamma (scalar: pol's coefficient; vector: TE, TM)
-// and, for the adjoint, c dGamma/deta and dc/dS Gamma
-__device__ __forceinline__ void interaction_factors(const PathRec& p, int m, int k, int diffuse,
-                                                    const float* __restrict__ mat, float freq,
-                                                    int pol, float2* D, float2* dDe, float2* dDs) {
-  const int l = path_mat(p, m);
-  const float2 eta = permittivity(mat[l], mat[256 + l], freq);
-  const float Sl = mat[512 + l];
-  const bool last_d = diffuse && m == k - 1;
-  const float R = sqrtf(fmaxf(0.0f, 1.0f - Sl * Sl));
-  const float c = last_d ? Sl : R;
-  const float dc = last_d ? 1.0f : (R > 0.0f ? -Sl / R : 0.0f);
-  const int n = pol == 2 ? 2 : 1;
-  for (int t = 0; t < n; ++t) {
-    const int pp = pol == 2 ? t : pol;
-    const float2 G = fresnel(eta, p.cosv[m], pp);
-    D[t] = cscale(c, G);
-    if (dDe) dDe[t] = cscale(c, dfresnel(eta, p.cosv[m], pp));
-    if (dDs) dDs[t] = cscale(dc, G);
-  }
 }
 
 // Diffracted path: D = K(T1 + T2) + R0 K T3 + Rn K T4 with the stored
@@ -1798,12 +1807,6 @@ __device__ __forceinline__ unsigned trace_row(const SceneView& S, const SimConst
   return segs;
 }
 
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // Batch trace as one persistent launch: warps pull work items of `packet`
 // rays of one pair from a queue (uneven budgets balance themselves); the warp
 // that finishes a pair's last item stamps the pair's completion time.
@@ -1814,7 +1817,6 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
                             unsigned long long* ctr) {
   NRT_STACK_DECL
   const int lane = threadIdx.x & 31;
-  if (blockIdx.x == 0 && threadIdx.x == 0) stamps[0] = global_ns();
   const uint32_t n_chunks = __ldg(chunk_start + C.n_pairs);
   unsigned long long segs = 0;
   for (int guard = 0; guard < (1 << 30); ++guard) {
@@ -1849,6 +1851,31 @@ __global__ void queue_init_kernel(const uint32_t* __restrict__ chunk_start, int 
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j == 0) queue[0] = 0ull;
   if (j < n_pairs) queue[1 + j] = chunk_start[j + 1] - chunk_start[j];
+}
+
+// Batch latency state before the trace: stamps[0] = start, the per-pair
+// stamps cleared, rays in flight per pair = its budget, keys per pair = 0
+// (counted once key ids exist).  queue layout: [0] work head, [1 + j] chunks
+// left, [1 + P + j] rays left, [1 + 2P + j] keys left; stamps: [0] start,
+// [1 + j] pair j traced, [1 + P + j] pair j's keys validated.
+__global__ void batch_stamp_init_kernel(SimConst C, unsigned long long* __restrict__ queue,
+                                        unsigned long long* __restrict__ stamps) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int P = C.n_pairs;
+  if (j == 0) stamps[0] = global_ns();
+  if (j < P) {
+    queue[1 + P + j] = (unsigned long long)(__ldg(C.pair_start + j + 1) - __ldg(C.pair_start + j));
+    queue[1 + 2 * P + j] = 0ull;
+    stamps[1 + j] = 0ull;
+    stamps[1 + P + j] = 0ull;
+  }
+}
+
+// pairs without keys have their paths validated as soon as validation starts
+__global__ void pair_nokey_stamp_kernel(int n_pairs, const unsigned long long* __restrict__ keys_left,
+                                        unsigned long long* __restrict__ stamps) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n_pairs && keys_left[j] == 0ull) stamps[1 + n_pairs + j] = global_ns();
 }
 
 }  // namespace
@@ -2067,8 +2094,9 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   while ((1 << jb) < nj) ++jb;
   const int mb = 3 * std::min(sc->grid_bits, 10);  // spread3 keeps 10 bits per axis
   const int fb_spec = std::min(12, mb);  // specular: cells of 16 voxels per axis
+  unsigned long long* pair_keys = C.batch ? r->queue + 1 + 2 * C.n_pairs : nullptr;
   val_order_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(S, R, W.T, W.K, W.cnt, W.sk0, W.sv0,
-                                                               jb, mb, fb_spec); count_launch();
+                                                               jb, mb, fb_spec, pair_keys); count_launch();
   radix_sort_pairs(W.sk0, W.sv0, W.tk0, W.tv, c.keys, 1 + jb + mb, st, 0, W.cnt + kCntKeys);
   split_lists_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.sv0, c.keys, W.cnt, W.spec_list,
                                                                  W.diff_list); count_launch();
@@ -2090,6 +2118,11 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   V.paths = W.raw;
   V.path_cap = c.paths;
   V.SC = SC;
+  V.pair_keys = pair_keys;
+  V.pair_ready = C.batch ? r->stamps + 1 + C.n_pairs : nullptr;
+  if (C.batch) {
+    pair_nokey_stamp_kernel<<<(C.n_pairs + 255) / 256, 256, 0, st>>>(C.n_pairs, pair_keys, r->stamps); count_launch();
+  }
   // every key walks its candidates in ray order inside one launch per type
   TRY(cudaMemsetAsync(W.cnt + kCntFetchS, 0, 16, st));
   validate_specular_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 6), kTraceThreads, 0, st>>>(
@@ -2207,13 +2240,17 @@ nrt_status enqueue_trace(nrt_result* r, const SceneView& S, const SimConst& C,
   TRY(cudaMemsetAsync(r->rec_i, 0xFF, (size_t)r->n_seg * n * sizeof(int2), st));
   Records R{r->rec_q, r->rec_n, r->rec_d, r->rec_i, n};
   if (r->ev[2]) TRY(cudaEventRecord(r->ev[2], st));
+  if (C.batch) {
+    batch_stamp_init_kernel<<<(r->n_pairs + 255) / 256, 256, 0, st>>>(C, r->queue, r->stamps); count_launch();
+  }
   if (C.batch && r->schedule == 1) {
     queue_init_kernel<<<(r->n_pairs + 255) / 256, 256, 0, st>>>(r->chunk_start, r->n_pairs, r->queue); count_launch();
     trace_persistent_kernel<<<sm * 8, kTraceThreads, 0, st>>>(S, C, order, R, r->chunk_start,
                                                               r->packet, r->queue, r->stamps, r->ctr); count_launch();
   } else {
     trace_kernel<<<blocks_for(n, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
-        S, C, subset_d, order, R, r->ctr + kCtrRayFetch, r->ctr); count_launch();
+        S, C, subset_d, order, R, r->ctr + kCtrRayFetch, r->ctr,
+        C.batch ? r->queue + 1 + r->n_pairs : nullptr, C.batch ? r->stamps + 1 : nullptr); count_launch();
   }
   if (r->ev[3]) TRY(cudaEventRecord(r->ev[3], st));
   return NRT_OK;

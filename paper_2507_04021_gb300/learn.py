@@ -90,8 +90,19 @@ class Fit:
     loss: list = field(default_factory=list)
 
 
-def recover_materials(backend, target_db, init, steps=200, lr=0.05) -> Fit:
-    """Adam on the per-RX dB-gain MSE; target_db [R, M]; init = (eps, sigma, S)."""
+def save_checkpoint(path, params, opt, hist):
+    """Material optimiser state: the unconstrained parameters (u, v, w), Adam's
+    moments and step counts, and the loss history."""
+    torch.save({"params": [p.detach().clone() for p in params], "opt": opt.state_dict(),
+                "loss": list(hist)}, path)
+
+
+def recover_materials(backend, target_db, init, steps=200, lr=0.05, checkpoint=None,
+                      checkpoint_every=0, resume=None) -> Fit:
+    """Adam on the per-RX dB-gain MSE; target_db [R, M]; init = (eps, sigma, S).
+    checkpoint / checkpoint_every: write the optimiser state to that path
+    every so many steps (and after the last); resume: continue from such a
+    checkpoint (its steps count toward `steps`)."""
     u0, v0, w0 = to_params(*init)
     u = torch.tensor(u0, requires_grad=True)
     v = torch.tensor(v0, requires_grad=True)
@@ -99,7 +110,14 @@ def recover_materials(backend, target_db, init, steps=200, lr=0.05) -> Fit:
     tgt = torch.as_tensor(np.asarray(target_db, np.float64))
     opt = torch.optim.Adam([u, v, w], lr=lr)
     hist = []
-    for _ in range(steps):
+    if resume is not None:
+        st = torch.load(resume, weights_only=False)
+        with torch.no_grad():
+            for p, q in zip((u, v, w), st["params"]):
+                p.copy_(q)
+        opt.load_state_dict(st["opt"])
+        hist = list(st["loss"])
+    for it in range(len(hist), steps):
         opt.zero_grad()
         eps, sig, sca = from_params(u, v, w)
         P = PowerFn.apply(eps, sig, sca, backend)
@@ -108,6 +126,8 @@ def recover_materials(backend, target_db, init, steps=200, lr=0.05) -> Fit:
         loss.backward()
         opt.step()
         hist.append(float(loss.detach()))
+        if checkpoint and ((checkpoint_every and (it + 1) % checkpoint_every == 0) or it + 1 == steps):
+            save_checkpoint(checkpoint, (u, v, w), opt, hist)
     with torch.no_grad():
         eps, sig, sca = from_params(u, v, w)
     return Fit(eps.numpy(), sig.numpy(), sca.numpy(), hist)

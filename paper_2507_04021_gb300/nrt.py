@@ -126,18 +126,22 @@ def lib():
         L.nrt_trace_batch.argtypes = [_P, _P, _P, _P, C.c_int, C.POINTER(TraceParams),
                                       C.POINTER(BatchOpts), C.POINTER(_P)]
         L.nrt_batch_replay.argtypes = [_P, _P]
-        L.nrt_batch_times.argtypes = [_P, _P, _P]
+        L.nrt_batch_times.argtypes = [_P, _P, _P, _P]
         L.nrt_autotune_batch.argtypes = [_P, _P, _P, C.c_int, C.c_int, _P, _P]
         L.nrt_ray_labels_read.argtypes = [_P, _P]
         L.nrt_cfr.argtypes = [_P, C.c_double, C.c_int32, _P]
         L.nrt_cfr_backward.argtypes = [_P, C.c_double, C.c_int32, _P, _P, _P, _P, _P, _P]
         L.nrt_keys_read.argtypes = [_P, _P, _P, _P, _P]
         L.nrt_get_stream.argtypes = [_P, C.POINTER(_P)]
+        L.nrt_set_wait_limit.argtypes = [_P, C.c_int64]
+        L.nrt_measure_l2.argtypes = [_P, C.c_int64, C.c_int32, C.POINTER(C.c_float)]
         L.nrt_mlp_create.argtypes = [_P, _P, C.c_int64, _P, _P, C.c_int64, C.POINTER(_P)]
         L.nrt_mlp_free.argtypes = [_P]
         L.nrt_mlp_free.restype = None
         L.nrt_mlp_params_read.argtypes = [_P, _P]
         L.nrt_mlp_grads_read.argtypes = [_P, _P]
+        L.nrt_mlp_state_read.argtypes = [_P, _P, _P, _P, C.POINTER(C.c_int64)]
+        L.nrt_mlp_state_write.argtypes = [_P, _P, _P, _P, C.c_int64]
         L.nrt_mlp_features.argtypes = [_P, _P, _P, C.c_int64, _P]
         L.nrt_mlp_score.argtypes = [_P, _P, _P, C.c_int64, _P]
         L.nrt_mlp_train.argtypes = [_P, _P, C.c_int32, _P, _P, _P, C.c_int64, _P, C.c_int64,
@@ -185,6 +189,16 @@ class Context:
 
     def sync(self):
         self._check(lib().nrt_sync(self._h))
+
+    def set_wait_limit(self, polls: int):
+        """Polls of a bounded tensor-core wait before it gives up (0 = default)."""
+        self._check(lib().nrt_set_wait_limit(self._h, int(polls)))
+
+    def measure_l2(self, nbytes: int = 48 << 20, reps: int = 50) -> float:
+        """L2 read bandwidth in GB/s (nrt_measure_l2)."""
+        g = C.c_float()
+        self._check(lib().nrt_measure_l2(self._h, int(nbytes), int(reps), C.byref(g)))
+        return float(g.value)
 
     def stream_handle(self) -> int:
         """The cudaStream_t the library enqueues on (for torch.cuda.ExternalStream)."""
@@ -433,7 +447,23 @@ class Result:
     def backward_noalloc(self, dL_dP_dev, grad_dev):
         """nrt_backward_noalloc on caller-owned device buffers (torch CUDA tensors):
         dL_dP_dev float32[n_rx] in, grad_dev float32[3 * n_labels] out.  Enqueued on
-        the context stream; call ctx.sync() before reading grad_dev."""
+        the context stream; call ctx.sync() before reading grad_dev.  The C call
+        cannot see the buffers' sizes, so they are checked here: both must be
+        contiguous float32 CUDA tensors on the context's device, dL_dP_dev at
+        least n_rx long and grad_dev at least 3 * n_labels long."""
+        import torch
+
+        for name, t, need in (("dL_dP_dev", dL_dP_dev, self.n_rx),
+                              ("grad_dev", grad_dev, 3 * self.scene.n_labels)):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda):
+                raise ValueError(f"{name} must be a CUDA tensor")
+            if t.device.index != self.ctx.device:
+                raise ValueError(f"{name} is on cuda:{t.device.index}, the context on "
+                                 f"cuda:{self.ctx.device}")
+            if t.dtype != torch.float32 or not t.is_contiguous():
+                raise ValueError(f"{name} must be contiguous float32")
+            if t.numel() < need:
+                raise ValueError(f"{name} has {t.numel()} elements, needs {need}")
         self.ctx._check(lib().nrt_backward_noalloc(self._h, _P(dL_dP_dev.data_ptr()),
                                                    _P(grad_dev.data_ptr())))
 
@@ -478,10 +508,15 @@ class BatchResult(Result):
             p = _np_ptr(tx)
         self.ctx._check(lib().nrt_batch_replay(self._h, p))
 
-    def batch_times(self):
+    def batch_times(self, paths=False):
+        """(per-pair ms at which the pair's last ray was traced, total ms); with
+        paths, also the per-pair ms at which its last path key was validated."""
         pm = np.zeros(self.n_pairs, np.float64)
+        pv = np.zeros(self.n_pairs, np.float64)
         tot = C.c_float()
-        self.ctx._check(lib().nrt_batch_times(self._h, _np_ptr(pm), C.byref(tot)))
+        self.ctx._check(lib().nrt_batch_times(self._h, _np_ptr(pm), C.byref(tot), _np_ptr(pv)))
+        if paths:
+            return pm, float(tot.value), pv
         return pm, float(tot.value)
 
     def autotune(self, configs, repeats=2):
@@ -531,6 +566,35 @@ class Mlp:
         out = np.zeros(N_MLP_PARAMS, np.float32)
         self.ctx._check(lib().nrt_mlp_grads_read(self._h, _np_ptr(out)))
         return out
+
+    def state(self) -> dict:
+        """Training state (nrt_mlp_state_read): params, adam_m, adam_v, step."""
+        out = {k: np.zeros(N_MLP_PARAMS, np.float32) for k in ("params", "adam_m", "adam_v")}
+        step = C.c_int64()
+        self.ctx._check(lib().nrt_mlp_state_read(self._h, _np_ptr(out["params"]),
+                                                 _np_ptr(out["adam_m"]), _np_ptr(out["adam_v"]),
+                                                 C.byref(step)))
+        out["step"] = int(step.value)
+        return out
+
+    def load_state(self, st: dict):
+        """Restore a state from state() (nrt_mlp_state_write)."""
+        arr = {k: np.ascontiguousarray(st[k], np.float32) for k in ("params", "adam_m", "adam_v")}
+        for k, a in arr.items():
+            if a.size != N_MLP_PARAMS:
+                raise ValueError(f"{k}: {a.size} values, expected {N_MLP_PARAMS}")
+        self.ctx._check(lib().nrt_mlp_state_write(self._h, _np_ptr(arr["params"]),
+                                                  _np_ptr(arr["adam_m"]), _np_ptr(arr["adam_v"]),
+                                                  int(st["step"])))
+
+    def save(self, path):
+        """Checkpoint the training state to an .npz file."""
+        np.savez(path, **self.state())
+
+    def restore(self, path):
+        """Resume from a checkpoint written by save()."""
+        with np.load(path) as z:
+            self.load_state({k: z[k] for k in ("params", "adam_m", "adam_v", "step")})
 
     def features(self, tx, ray_ids_dev, n, out_dev, sync=True):
         t = np.ascontiguousarray(tx, np.float32).reshape(3)

@@ -30,10 +30,26 @@ def room_pair(room):
     return sc, res, osim
 
 
+def _same_path_rx(gp, O, n_rx):
+    """Receivers whose (key, representative) sets are identical on both
+    sides: a loss restricted to them sums over the same paths."""
+    NONE = 0xFFFFFFFF
+    same = []
+    for j in range(n_rx):
+        g = set(zip(gp["key_hi"][gp["rx"] == j].tolist(), gp["key_lo"][gp["rx"] == j].tolist(),
+                    gp["rep"][gp["rx"] == j].tolist()))
+        m = O["j"] == j
+        o = set(zip(O["hi"][m].tolist(), O["lo"][m].tolist(),
+                    [NONE if r < 0 else r for r in O["rep"][m].tolist()]))
+        same.append(g == o and len(g) > 0)
+    return np.array(same)
+
+
 def test_backward_matches_oracle_gradient(room_pair):
     """eps_r, sigma and S (through the roughness factor sqrt(1 - S^2)) against
-    the oracle's analytic gradient; the path sets may differ by a few keys at
-    the room's corner voxels, hence 2e-3 relative."""
+    the oracle's analytic gradient within 1e-3 relative (the adjoint bar); the
+    loss weights only receivers whose path sets agree exactly, so both sides
+    differentiate the same sum."""
     sc, res, osim = room_pair
     gp = res.paths()
     O = osim.paths()
@@ -43,25 +59,32 @@ def test_backward_matches_oracle_gradient(room_pair):
     print("room specular keys: gpu", len(gk), "oracle", len(ok), "common", len(gk & ok))
     assert len(gk & ok) >= 0.98 * max(len(gk), len(ok)) and len(gk) >= 15
     _, Po = osim.field(*MATS)
-    dLdP = (1.0 / Po) * np.array([1.0, -0.5, 0.25, 2.0])
+    same = _same_path_rx(gp, O, len(RX4))
+    print("receivers with identical path sets:", same)
+    assert same.sum() >= 3
+    dLdP = (1.0 / Po) * np.array([1.0, -0.5, 0.25, 2.0]) * same
     g = res.backward(dLdP.astype(np.float32))
     want = osim.backward(*MATS, dLdP)
     for name, gi, wi in zip(("eps", "sigma", "S"), g, want):
         rel = np.abs(gi - wi) / np.maximum(np.abs(wi), 1e-3 * np.abs(wi).max())
         print(name, "max rel diff", float(rel.max()))
-        assert rel.max() < 2e-3, (name, gi, wi)
+        assert rel.max() < 1e-3, (name, gi, wi)
 
 
-def test_backward_diffuse_office_subset(office):
+@pytest.mark.parametrize("depth", [3, 5])
+def test_backward_diffuse_office_subset(office, depth):
     """Office sample with diffuse paths (the S Gamma factor of the last
-    interaction): against the oracle's gradient.  The two path sets differ by
-    the keys the oracle flags ambiguous (~0.1% of keys), so the bound is 5e-3
-    relative on the per-label gradient."""
+    interaction), up to 3 and to 5 interactions (the office workload's K):
+    against the oracle's gradient within 1e-3 relative per label.  The two
+    path sets differ by the keys the oracle flags ambiguous (~0.1% of keys),
+    so the loss weights only receivers whose path sets agree exactly when
+    at least half of them do."""
     ctx = nrt.Context(0)
     sc = nrt.Scene(ctx, office.pos, office.nrm, office.surf, office.mat, r_p=0.015)
     sc.set_materials(office.eps_r, office.sigma, office.scat)
     ids = np.arange(0, 1_000_000, 250, dtype=np.uint32)
-    kp = dict(max_depth=3, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1_000_000, rep_tries=8)
+    kp = dict(max_depth=depth, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1_000_000,
+              rep_tries=8)
     res = sc.trace(office.tx, office.rx, nrt.default_trace_params(**kp), ray_subset=ids)
     osc = oracle.OracleScene(office.pos, office.nrm, office.surf, office.mat, r_p=0.015,
                              grid_cell=0.1)
@@ -70,13 +93,18 @@ def test_backward_diffuse_office_subset(office):
                             ray_ids=ids.astype(np.int64))
     mats = tuple(m.astype(np.float64) for m in (office.eps_r, office.sigma, office.scat))
     _, Po = osim.field(*mats)
-    dLdP = 1.0 / Po
+    same = _same_path_rx(res.paths(), osim.paths(), len(office.rx))
+    print("receivers with identical path sets:", int(same.sum()), "of", len(same))
+    # with too few such receivers, every receiver is weighted: the ambiguous
+    # keys then differ on the two sides (about 0.1% of keys at K = 5)
+    w = same if same.sum() >= len(same) // 2 else np.ones(len(same), bool)
+    dLdP = (1.0 / Po) * w
     g = res.backward(dLdP.astype(np.float32))
     want = osim.backward(*mats, dLdP)
     for name, gi, wi in zip(("eps", "sigma", "S"), g, want):
         rel = np.abs(gi - wi) / np.maximum(np.abs(wi), 1e-3 * np.abs(wi).max())
         print(name, "max rel diff", float(rel.max()))
-        assert rel.max() < 5e-3, (name, gi, wi)
+        assert rel.max() < 1e-3, (name, gi, wi)
 
 
 def test_recover_hidden_materials_on_gpu(office):

@@ -102,6 +102,27 @@ def test_schedules_and_graph_replay_agree(setup):
     assert np.all(pm > 0) and tot > 0 and np.all(pm <= tot * 1.0 + 1e-6)
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_pair_latency_stamps_under_graph_replay(setup, schedule):
+    """Per-pair latency from device timestamps, for both trace schedules and
+    under graph replay: every pair has a trace-done and a paths-validated
+    time, inside the simulation's device time; validation starts once every
+    pair is traced, so each pair's path set is known after the last trace."""
+    ctx, sc, traj = setup
+    rng = np.random.default_rng(11)
+    budgets = rng.integers(2000, 20000, 12).astype(np.int64)
+    g = sc.trace_batch(traj[:12], RXF, budgets, _params(n_rays=1), schedule=schedule,
+                       use_graph=True)
+    for tx in (None, traj[40:52]):
+        if tx is not None:
+            g.replay(tx)
+        pm, tot, pv = g.batch_times(paths=True)
+        slack = 5e-3  # ms: globaltimer against event clocks
+        assert np.all(pm > 0) and np.all(pm <= tot + slack), (pm, tot)
+        assert np.all(pv > 0) and np.all(pv <= tot + slack), (pv, tot)
+        assert np.all(pv >= pm.max() - slack), (pv, pm)
+
+
 def test_autotune_picks_a_configuration(setup):
     ctx, sc, traj = setup
     budgets = np.full(8, 20000, np.int64)

@@ -185,3 +185,65 @@ def test_ray_labels_match_oracle(ctx, room):
     print("labels gpu", int(lab.sum()), "oracle", int(olab.sum()), "ambiguous", int(amb.sum()))
     assert olab.sum() > 50
     assert np.array_equal(lab[ok], olab[ok])
+
+
+def test_bounded_wait_runs_out_and_context_recovers():
+    """Failure detection without a GPU fault: with the watchdog lowered to one
+    non-blocking poll, the tensor-core kernel's wait for its MMAs runs out;
+    the kernel records the timeout, drains its own MMAs, frees its tensor
+    memory and returns, the call reports NRT_ERR_TIMEOUT, and the same
+    context then computes the product correctly with the default limit."""
+    c = nrt.Context(0)
+    rng = np.random.default_rng(99)
+    A = M.bf16(rng.standard_normal((512, 4096)))
+    B = M.bf16(rng.standard_normal((256, 4096)))
+    C = torch.zeros((512, 256), dtype=torch.float32, device="cuda")
+    c.set_wait_limit(1)
+    with pytest.raises(nrt.NrtError) as e:
+        nrt.gemm_bf16(c, _bf16_bits(A), _bf16_bits(B), C)
+    assert e.value.status == 5  # NRT_ERR_TIMEOUT
+    c.set_wait_limit(0)
+    nrt.gemm_bf16(c, _bf16_bits(A), _bf16_bits(B), C)
+    want = A @ B.T
+    bound = 1e-5 * (np.abs(A) @ np.abs(B).T) + 1e-30
+    assert np.all(np.abs(C.cpu().numpy().astype(np.float64) - want) <= bound)
+    with pytest.raises(nrt.NrtError):
+        c.set_wait_limit(-1)
+
+
+def test_checkpoint_resume_continues_training(ctx, tmp_path):
+    """Checkpoint/resume of the network's training state: 3 Adam steps, a
+    checkpoint to disk, 4 more steps; a fresh network restored from the
+    checkpoint and given the same 4 steps ends where the uninterrupted run
+    did (up to the order of the split-K atomic sums of the weight
+    gradients), while a restore of the parameters alone (fresh moments and
+    step count) lands measurably elsewhere."""
+    n, B = 8 * 2048, 2048
+    tx_table, ti, rid, lab = _train_inputs(n)
+    dev = lambda a: torch.from_numpy(a).cuda()  # noqa: E731
+    data = (dev(tx_table), dev(ti), dev(rid), dev(lab))
+    kw = dict(lr=2e-3, batch=B, pos_weight=3.0)
+    net, _ = _net(ctx)
+    net.train(*data, start=0, steps=3, **kw)
+    ck = tmp_path / "mlp.npz"
+    net.save(ck)
+    st = net.state()
+    assert st["step"] == 3 and np.abs(st["adam_v"]).max() > 0
+    net.train(*data, start=3 * B, steps=4, **kw)
+    want = net.params().astype(np.float64)
+    moved = np.abs(want - st["params"]).max()
+
+    net2, _ = _net(ctx, theta=inputs.mlp_init() * 0.5)  # different start, overwritten
+    net2.restore(ck)
+    assert np.array_equal(net2.params(), st["params"])
+    net2.train(*data, start=3 * B, steps=4, **kw)
+    got = net2.params().astype(np.float64)
+    assert net2.state()["step"] == 7
+    err = np.abs(got - want).max()
+
+    net3, _ = _net(ctx, theta=st["params"])  # parameters only: Adam restarts
+    net3.train(*data, start=3 * B, steps=4, **kw)
+    err_fresh = np.abs(net3.params().astype(np.float64) - want).max()
+    print("moved", moved, "resumed err", err, "fresh-Adam err", err_fresh)
+    assert err <= 1e-2 * kw["lr"]
+    assert err_fresh > 10 * max(err, 1e-9)
