@@ -251,7 +251,7 @@ class SimParams:
     diffuse: int = 0
     pol: int = 0              # 0 TE, 1 TM, 2 vector (Jones chain)
     kappa: int = 10
-    rep_tries: int = 8
+    rep_tries: int = 0        # candidates tried per key in ray order; 0 = all (the paper's rule)
     validate: int = 1
     n_threads: int = 0
     n_rays: int = 20000

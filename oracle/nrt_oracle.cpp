@@ -456,7 +456,7 @@ struct orc_params {
   int32_t diffuse;     // diffuse scattering as the last interaction
   int32_t pol;         // 0 TE, 1 TM
   int32_t kappa;       // refinement retries
-  int32_t rep_tries;   // candidates tried per key, in ray order
+  int32_t rep_tries;   // candidates tried per key, in ray order (0: all of them)
   int32_t validate;    // 0: stop after the trace (records only)
   int32_t n_threads;   // 0: OpenMP default
   int64_t n_rays;      // N of the Fibonacci launch
@@ -954,7 +954,9 @@ void run_sim(Sim& sim) {
     }
   }
 
-  // per key: try the first rep_tries candidates in ray order
+  // per key: try the candidates in ray order until one validates -- all of
+  // them (rep_tries = 0: every candidate is refined, Sec. II-B-2, and the
+  // duplicates of a key are removed, Sec. II-B-4), or at most rep_tries
   std::vector<Key> klist;
   for (auto& kv : cands) {
     std::sort(kv.second.begin(), kv.second.end(),
@@ -974,8 +976,9 @@ void run_sim(Sim& sim) {
     int labels[5] = {0, 0, 0, 0, 0};
     for (int m = 0; m < 4; ++m) labels[m] = (int)((K.lo >> (16 * m)) & 0xFFFF);
     labels[4] = (int)(K.hi & 0xFFFF);
-    int ntry = std::min<int64_t>(cl.size(), sim.p.rep_tries);
-    for (int c = 0; c < ntry; ++c) {
+    const int64_t ntry =
+        sim.p.rep_tries > 0 ? std::min<int64_t>(cl.size(), sim.p.rep_tries) : (int64_t)cl.size();
+    for (int64_t c = 0; c < ntry; ++c) {
       int64_t rid = cl[c].ray;
       int64_t row = sim.ray_pos[rid];
       Validation v = ko.type == 1 ? validate_diffuse(sim, sim.rec, row, ko.k, ko.j, cfg)

@@ -1,0 +1,59 @@
+"""The benchmarked configuration in full against the FP64 oracle: the
+office (2M points, 16 RX), the whole 1M-ray Fibonacci launch, 5
+interactions, visibility capture with diffuse last interactions, rep_tries
+8 -- every step compared: hit records of every ray (bit-exact outside the
+oracle's ambiguity), the path set and each key's representative (the
+lowest valid ray id of Sec. II-B-4), every matched path's coefficient and
+delay, and the per-RX received power.  The oracle traces all 1M rays with
+its shadow trajectories (a few minutes on the host's cores)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2507_04021_gb300 import nrt
+
+from parity import compare_hits, compare_paths
+
+pytestmark = pytest.mark.gpu
+
+
+def test_office_full_launch_against_oracle(office):
+    ctx = nrt.Context(0)
+    sc = nrt.Scene(ctx, office.pos, office.nrm, office.surf, office.mat, rho=0.0625, r_p=0.015)
+    sc.set_materials(office.eps_r, office.sigma, office.scat)
+    kp = dict(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1_000_000, rep_tries=8)
+    res = sc.trace(office.tx, office.rx, nrt.default_trace_params(**kp))
+    _, cg = res.counts()
+    delta = 1e-5 * office.diag
+    osc = oracle.OracleScene(office.pos, office.nrm, office.surf, office.mat, rho=0.0625,
+                             r_p=0.015, grid_cell=0.1)
+    osim = oracle.OracleSim(osc, office.tx, office.rx, oracle.SimParams(delta=delta, **kp))
+    h = compare_hits(res.hits(), osim.hits(), delta, sens=osim.hit_sens())
+    h.pop("examples")
+    print("full launch hits:", h)
+    assert h["mismatch"] == 0, h
+    assert h["checked"] > 3_000_000
+    gp = res.paths()
+    s = compare_paths(gp, osim, office.eps_r, office.sigma, office.scat)
+    print("full launch paths:", json.dumps(s))
+    K = osim.keys()
+    n_keys_o = len(K["hi"])
+    print("keys: gpu", cg["keys"], "oracle", n_keys_o, "paths: gpu", cg["paths"], "oracle",
+          len(osim.paths()["hi"]))
+    assert s["matched"] >= 0.995 * s["keys"], s
+    assert abs(cg["keys"] - n_keys_o) <= 1e-3 * n_keys_o
+    assert s["max_dP_common"] < 1e-4, s
+    # received power over all paths (common and explained-different alike)
+    Pg = res.power().astype(np.float64)
+    _, Po = osim.field(office.eps_r, office.sigma, office.scat)
+    dP = np.abs(Pg - Po) / Po
+    print("per-RX power, relative difference over all paths:", np.array2string(dP, precision=2))
+    assert np.all(dP < 1e-2)
+    out = os.environ.get("NRT_PARITY_OUT")
+    if out:
+        with open(out, "w") as f:
+            json.dump({"hits": h, "paths": s, "keys_gpu": cg["keys"], "keys_oracle": n_keys_o,
+                       "power_rel_diff_all_paths": dP.tolist()}, f, indent=1)

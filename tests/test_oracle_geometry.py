@@ -44,6 +44,32 @@ def test_voxelisation_matches_float32_floor(room):
     assert np.array_equal(sc.point_dps(), inv.ravel())
 
 
+def test_voxel_membership_is_the_exact_floor_up_to_float32_rounding(office):
+    """Sec. II-A's voxel of a point is floor((p - bmin) / rho).  The oracle
+    takes that integer decision in float32, the kernel's precision (a
+    reading); here it is pinned to the exact quotient evaluated in FP64:
+    every point farther from a voxel face than the float32 rounding of the
+    quotient gets exactly floor of the exact value, and the few that are
+    nearer get it or a neighbour (counted: the points whose DPS depends on
+    the precision)."""
+    sc = oracle.OracleScene(office.pos, office.nrm, office.surf, office.mat, r_p=0.015,
+                            grid_cell=0.1)
+    vox, _, _ = sc.dps()
+    v = vox[sc.point_dps()].astype(np.int64)
+    bmin = sc.bmin().astype(np.float64)
+    q = (office.pos.astype(np.float64) - bmin) / 0.0625  # rho = 0.0625 is exact in binary
+    fl = np.floor(q)
+    # float32 rounding of the difference and of the quotient: a few ulp of q
+    band = 4.0 * np.spacing(np.abs(q).astype(np.float32)).astype(np.float64) + 1e-12
+    near = (q - fl < band) | (fl + 1.0 - q < band)
+    far = ~near
+    assert np.array_equal(v[far], fl[far].astype(np.int64))
+    assert np.all(np.abs(v[near] - fl[near]) <= 1)
+    n_near = int(near.any(axis=1).sum())
+    print("points within float32 rounding of a voxel face:", n_near, "of", len(v))
+    assert n_near < 1e-3 * len(v)
+
+
 def test_single_disc_hit_and_miss():
     sc = _scene([[0, 0, 0]], [[0, 0, 1]], r_p=0.05)
     h = sc.cast([0.01, 0.02, 1.0], [0, 0, -1])

@@ -80,8 +80,16 @@ MUTANTS = [
      [f"{T_PATHS}::test_rough_wall_fully_visible_from_the_front"]),
     ("dedup_highest_ray_first", CPP, "return a.ray < b.ray;", "return a.ray > b.ray;",
      [f"{T_LAB}::test_dedup_tries_lowest_ray_ids_first"]),
-    ("dedup_one_try", CPP, "int ntry = std::min<int64_t>(cl.size(), sim.p.rep_tries);",
-     "int ntry = std::min<int64_t>(cl.size(), 1);", [f"{T_LAB}::test_dedup_tries_lowest_ray_ids_first"]),
+    ("dedup_one_try", CPP,
+     "sim.p.rep_tries > 0 ? std::min<int64_t>(cl.size(), sim.p.rep_tries) : (int64_t)cl.size();",
+     "std::min<int64_t>(cl.size(), 1);", [f"{T_LAB}::test_dedup_tries_lowest_ray_ids_first"]),
+    ("dedup_cap_ignored", CPP,
+     "sim.p.rep_tries > 0 ? std::min<int64_t>(cl.size(), sim.p.rep_tries) : (int64_t)cl.size();",
+     "(int64_t)cl.size();", [f"{T_LAB}::test_dedup_tries_lowest_ray_ids_first"]),
+    ("dedup_uncapped_stops_at_8", CPP,
+     "sim.p.rep_tries > 0 ? std::min<int64_t>(cl.size(), sim.p.rep_tries) : (int64_t)cl.size();",
+     "std::min<int64_t>(cl.size(), sim.p.rep_tries > 0 ? sim.p.rep_tries : 8);",
+     [f"{T_LAB}::test_dedup_tries_lowest_ray_ids_first"]),
     # Sec. II-B-1 diffuse, Sec. II-B-2 specular refinement (Eq. 1)
     ("diffuse_accepts_rx_behind", CPP, "if (cs <= 0.0) return v;", "if (cs < -1.0) return v;",
      [f"{T_PATHS}::test_adjoint_matches_central_differences"]),
