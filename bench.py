@@ -184,7 +184,7 @@ def run_oracle_sample(n_sample: int, threads: int = 0):
     o, sc = _ORACLE_SCENE["o"], _ORACLE_SCENE["sc"]
     stride = max(1, N_RAYS // n_sample)
     ids = np.arange(0, N_RAYS, stride, dtype=np.int64)[:n_sample]
-    p = oracle.SimParams(max_depth=5, capture=1, diffuse=1, n_rays=N_RAYS, rep_tries=8,
+    p = oracle.SimParams(max_depth=5, capture=1, diffuse=1, n_rays=N_RAYS, rep_tries=0,
                          n_threads=threads)
     t0 = time.perf_counter()
     sim = oracle.OracleSim(sc, o.tx, o.rx, p, ray_ids=ids)
@@ -239,7 +239,7 @@ def batch_bench(args, scene, o, rank, stream, flush):
     tx = np.roll(traj, -rank * n, axis=0)[:n] if rank else traj[:n]
     rx = np.array([17.5, 8.0, 1.2], np.float32)
     p = nrt.default_trace_params(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1,
-                                 rep_tries=8)
+                                 rep_tries=0)
     cfgs = [(32, 1), (64, 1), (128, 1), (64, 0)]
     cal = scene.trace_batch(tx, rx, budgets, p, packet=64, schedule=1)
     tune_ms, best = cal.autotune(cfgs, repeats=1)
@@ -305,7 +305,7 @@ def launch_bench(scene, o, tx, stream):
     out = {}
     for name, launch in (("dps", nrt.LAUNCH_DPS), ("fibonacci", nrt.LAUNCH_FIB)):
         p = nrt.default_trace_params(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1,
-                                     n_rays=n_dps, rep_tries=8)
+                                     n_rays=n_dps, rep_tries=0)
         p.launch = launch
         scene.trace(tx, o.rx, p).close()  # warm-up
         ms = []
@@ -341,7 +341,7 @@ def diffraction_bench(ctx, o, tx, stream, rays):
     out = {"edges": len(edges)}
     for name, flag in (("off", 0), ("on", 1)):
         p = nrt.default_trace_params(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=rays,
-                                     rep_tries=8, diffraction=flag)
+                                     rep_tries=0, diffraction=flag)
         sc.trace(tx, o.rx, p).close()  # warm-up
         ms = []
         for _ in range(3):
@@ -370,7 +370,7 @@ def rp_variant_bench(ctx, o, tx, stream, rays, r_p=0.025):
     sc = nrt.Scene(ctx, o.pos, o.nrm, o.surf, o.mat, rho=0.0625, r_p=r_p, lambda_d=100.0)
     sc.set_materials(o.eps_r, o.sigma, o.scat)
     p = nrt.default_trace_params(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=rays,
-                                 rep_tries=8)
+                                 rep_tries=0)
     sc.trace(tx, o.rx, p).close()
     ms = []
     for _ in range(3):
@@ -506,11 +506,40 @@ def ours(args):
     scene = nrt.Scene(ctx, o.pos, o.nrm, o.surf, o.mat, rho=0.0625, r_p=0.015, lambda_d=100.0)
     scene.set_materials(o.eps_r, o.sigma, o.scat)
     build_ms = scene.info()["build_ms"]
-    # independent problems per rank: rank r simulates trajectory TX r (rank 0: the office TX)
-    tx = o.tx if rank == 0 else inputs.trajectory(o.extra["boxes"])[rank % 256]
+    # one office simulation; with N ranks, each traces its contiguous ray range
+    # of the launch and the ranks' paths are merged on the device (strong
+    # scaling: the total work is the same simulation at every N)
+    tx = o.tx
     p = nrt.default_trace_params(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=args.rays,
-                                 rep_tries=8)
+                                 rep_tries=0)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    subset = None
+    if world > 1:
+        from paper_2507_04021_gb300 import shard as _shard
+        lo, hi = _shard.shard_ranges(args.rays, world)[rank]
+        subset = torch.arange(lo, hi, dtype=torch.int32, device=dev)
+    merged_power = [None]
+
+    def exchange(r):
+        """All-gather every rank's exported paths and merge them on the device."""
+        e = r.export_paths()
+        n = torch.tensor([e["key_hi"].shape[0]], dtype=torch.int64, device=dev)
+        sizes = [torch.zeros_like(n) for _ in range(world)]
+        dist.all_gather(sizes, n)
+        m = int(max(int(x) for x in sizes))
+        pad = lambda t, v: torch.cat([t, t.new_full((m - t.shape[0],), v)])  # noqa: E731
+        fields = {"key_hi": (e["key_hi"], -1), "key_lo": (e["key_lo"], -1),
+                  "rep": (e["rep"], -1), "power": (e["power"], 0.0)}
+        out = {}
+        for f, (t, v) in fields.items():
+            parts = [torch.empty(m, dtype=t.dtype, device=dev) for _ in range(world)]
+            dist.all_gather(parts, pad(t, v))
+            out[f] = torch.cat([q[:int(sizes[i])] for i, q in enumerate(parts)])
+        sid = torch.cat([torch.full((int(sizes[i]),), i, dtype=torch.int32, device=dev)
+                         for i in range(world)])
+        _, pw = nrt.shard_merge(ctx, out["key_hi"], out["key_lo"], sid, out["rep"],
+                                power=out["power"], n_rx=int(o.rx.shape[0]))
+        return pw
 
     def step():
         with torch.cuda.stream(stream):
@@ -518,7 +547,10 @@ def ours(args):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        r = scene.trace(tx, o.rx, p)
+        r = scene.trace(tx, o.rx, p, ray_subset=subset)
+        if world > 1:
+            with torch.cuda.stream(stream):
+                merged_power[0] = exchange(r)
         ev1.record(stream)
         return r, ev0, ev1
 
@@ -565,15 +597,27 @@ def ours(args):
     hb = db = 0
     for _ in range(0 if args.no_e2e else max(1, min(args.steps, 5))):
         torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
-        r = scene.trace(np.asarray(tx, np.float32), o.rx, p)
+        r = scene.trace(np.asarray(tx, np.float32), o.rx, p, ray_subset=subset)
         per_rx, c = r.counts()
-        pw = r.power()
+        if world > 1:  # the merged per-RX power of all ranks' paths
+            with torch.cuda.stream(stream):
+                pw = exchange(r).cpu().numpy()
+        else:
+            pw = r.power()
         e2e_ms.append((time.perf_counter() - t0) * 1000.0)
         e2e_casts += c["segments"] + c["vis_casts"] + c["los_casts"] + c["validation_casts"]
         hb = 12 + o.rx.nbytes
         db = pw.nbytes + per_rx.nbytes
         r.close()
+    if dist and e2e_ms:
+        t = torch.tensor([sum(e2e_ms), float(e2e_casts)], device=dev, dtype=torch.float64)
+        tm = t.clone()
+        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        e2e_ms, e2e_casts = [float(tm[0]) / len(e2e_ms)] * len(e2e_ms), float(t[1])
     e2e = None if args.no_e2e else {"value": e2e_casts / (sum(e2e_ms) / 1000.0), "unit": "ray-segments/s",
            "h2d_bytes_per_step": int(hb), "d2h_bytes_per_step": int(db),
            "ms_per_step": float(np.mean(e2e_ms)),
@@ -617,9 +661,11 @@ def ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "ray-segments/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "points": int(o.n_points), "rays": args.rays, "max_depth": 5,
+                   "parallelism": f"ray-range shards x{world}, device merge" if world > 1 else "1 GPU",
+                   "rep_tries": "all candidates (the paper's rule)",
                    "n_rx": int(o.rx.shape[0]), "l2_flush": "256 MB fill between steps",
                    "r_p": 0.015, "rho": 0.0625},
         "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks, "roofline": roof,

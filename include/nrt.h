@@ -73,7 +73,12 @@ typedef struct {
                            paper delegates the field model to an EM library,
                            Sec. II-B; this is the vector reading of it) */
   int32_t kappa;        /* refinement retries (Sec. II-B-2) */
-  int32_t rep_tries;    /* candidates validated per path key, in ray-id order (1..32) */
+  int32_t rep_tries;    /* 0 (default): every candidate of a path key is refined and
+                           validated and the lowest valid ray id represents the key
+                           (the paper refines all candidates, Sec. II-B-2, then
+                           removes duplicates, Sec. II-B-4); > 0: at most that many
+                           candidates per key, in ray-id order (a cap that changes
+                           the result) */
   int32_t record_hits;  /* 1: keep per-ray hit records readable by nrt_hits_read */
   int32_t ray_labels;   /* 1: per-ray proposal labels, readable by nrt_ray_labels_read */
   int64_t n_rays;       /* N of the Fibonacci-sphere launch */
@@ -111,12 +116,18 @@ typedef struct {
                                 would overflow (tree deeper than the stack);
                                 2 hash probe limit reached; 4 candidate buffer
                                 full; 8 more distinct keys than the key
-                                capacity; 16 path buffer full.  Any of them
-                                makes the call return NRT_ERR_OVERFLOW. */
+                                capacity; 16 path buffer full (any of these
+                                makes the call return NRT_ERR_OVERFLOW); 32 an
+                                internal consistency check failed (a path
+                                refined twice came out differently:
+                                NRT_ERR_STATE). */
   int64_t kernel_launches;   /* library kernels launched by the call */
   int64_t diffuse_casts;     /* of validation_casts: diffuse shadow casts (Sec. II-B-1) */
   int64_t diffraction_casts; /* edge visibility casts (Sec. II-B-3) */
-  int64_t reserved[2];
+  int64_t pruned_legs;       /* specular refinement legs ended without a cast: the
+                                leg's ray cannot enter the box of the key's surface
+                                label there, so its closest hit is another surface */
+  int64_t reserved[1];
 } nrt_counters;
 
 /* Path view for nrt_paths_read: caller-allocated arrays of n_paths entries
@@ -326,13 +337,20 @@ nrt_status nrt_vis_read(const nrt_result* result, uint32_t* bits);
  * (geometry does not depend on materials).  Enqueued on the context stream. */
 nrt_status nrt_field(nrt_result* result);
 
-/* Received power per RX, P_j = sum over paths of |a|^2 (host float[n_rx]). */
+/* Received power per RX, P_j = sum over paths of |a|^2 (host float[n_rx]):
+ * the incoherent sum of the path coefficients (the paper hands its paths to
+ * an EM library for the field, Sec. II; its learning experiment, Sec. III-B,
+ * reads the channel from the same per-path coefficients -- see nrt_cfr for
+ * the coherent CFR).  Errors: NRT_ERR_STATE before the field was computed. */
 nrt_status nrt_field_read(const nrt_result* result, float* power_per_rx);
 
-/* Adjoint of the received power: given dL/dP_j (host float[n_rx]), the
+/* Adjoint of the received power (the differentiable electromagnetic
+ * computation used to learn per-label relative permittivity, conductivity and
+ * scattering coefficient, Sec. III-B): given dL/dP_j (host float[n_rx]), the
  * gradient of L with respect to each label's eps_r, sigma and S (host
- * float[n_labels] each), recomputed from the stored interaction sequences.
- * Errors: NRT_ERR_STATE before nrt_set_materials. */
+ * float[n_labels] each), recomputed from the stored interaction sequences
+ * (material labels and incidence cosines) rather than from stored
+ * intermediates.  Errors: NRT_ERR_STATE before nrt_set_materials. */
 nrt_status nrt_backward(nrt_result* result, const float* dL_dpower, float* g_eps, float* g_sigma,
                         float* g_scat);
 
@@ -444,6 +462,37 @@ nrt_status nrt_cfr_backward(nrt_result* result, double bandwidth, int32_t n_freq
  * Errors: NRT_ERR_STATE when not requested. */
 nrt_status nrt_keys_read(const nrt_result* result, uint64_t* key_hi, uint64_t* key_lo,
                          uint32_t* tried, uint32_t* rep);
+
+/* ------------------------------------------------------------------ ray-range shards
+ * One simulation split across GPUs by ray range (rays are independent until
+ * duplicate paths are removed, Sec. II-B-4): every rank traces its range
+ * (ray_subset), exports its paths to device buffers, the ranks all-gather
+ * them, and nrt_shard_merge keeps per key the entry of the lowest shard in
+ * ray-range order -- the key's lowest valid ray id, so the merged paths and
+ * per-RX power equal one simulation of the whole launch.
+ *
+ * nrt_paths_export: the result's paths (nrt_result_counts' paths, in
+ * nrt_paths_read order) into caller-allocated DEVICE arrays, any may be NULL:
+ * key words, the representative ray id (0 for LOS and diffracted paths, which
+ * have none and are the same on every shard) and |a|^2 (double; needs the
+ * field).  Enqueued on the context stream.  Errors: NRT_ERR_STATE for power
+ * without a field. */
+nrt_status nrt_paths_export(const nrt_result* result, uint64_t* key_hi, uint64_t* key_lo,
+                            uint32_t* rep, double* power);
+
+/* Merge of n shard entries (DEVICE arrays): key_hi/key_lo, shard index
+ * (ray-range order), rep (0xFFFFFFFF = the shard found no valid candidate),
+ * tried (candidates the shard tried for the key, the valid one included; NULL
+ * = exported valid paths, no try budget) and rep_tries (0 = no cap; > 0 =
+ * the budget carried from shard to shard in ray order, with tried given).
+ * win[i] (device uint8) = 1 when entry i represents its key; with power
+ * (device double per entry, |a|^2) and power_out (device double[n_rx]), the
+ * per-RX received power of the merged paths (RX = key_hi >> 56).  Allocates
+ * scratch on the context stream; does not synchronise.  Errors: NRT_ERR_ARG. */
+nrt_status nrt_shard_merge(nrt_ctx* ctx, int64_t n, const uint64_t* key_hi, const uint64_t* key_lo,
+                           const uint32_t* shard, const uint32_t* tried, const uint32_t* rep,
+                           int32_t rep_tries, const double* power, int32_t n_rx, uint8_t* win,
+                           double* power_out);
 
 /* ------------------------------------------------------------------ learned launch proposal
  * Not part of the paper, which traces a fixed Fibonacci launch (Sec. II-B):

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libnrt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "prims.cu", "scene.cu", "sim.cu", "noalloc.cu", "mlp.cu", "cfr.cu", "isect.cu"]
+SOURCES = ["api.cu", "prims.cu", "scene.cu", "sim.cu", "noalloc.cu", "mlp.cu", "cfr.cu", "isect.cu",
+           "shard.cu"]
 
 
 def nvcc() -> str:

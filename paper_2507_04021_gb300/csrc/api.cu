@@ -44,6 +44,7 @@ void scene_release(nrt_scene* s) {
   free_dev(s->dps_vox);
   free_dev(s->dps_recv);
   free_dev(s->dps_center);
+  free_dev(s->label_box);
   free_dev(s->nodes);
   free_dev(s->mat);
   free_dev(s->edges);
@@ -100,7 +101,7 @@ void nrt_trace_params_default(nrt_trace_params* p) {
   p->diffuse = 1;
   p->pol = NRT_POL_TE;
   p->kappa = 10;
-  p->rep_tries = 8;
+  p->rep_tries = 0;
   p->record_hits = 1;
   p->n_rays = 1000000;
   p->r_rx = 0.1f;
@@ -363,7 +364,7 @@ nrt_status nrt_trace(nrt_scene* s, const float* tx, const float* rx, int n_rx,
     return NRT_ERR_ARG;
   }
   if (p->max_depth < 1 || p->max_depth > kMaxDepth || p->n_rays <= 0 ||
-      p->n_rays > (int64_t)0xFFFFFFFE || p->rep_tries < 1 || p->rep_tries > 32 || p->kappa < 0 ||
+      p->n_rays > (int64_t)0xFFFFFFFE || p->rep_tries < 0 || p->kappa < 0 ||
       !(p->freq > 0.f) || !(p->t_min >= 0.f) || (p->capture != 0 && p->capture != 1) ||
       p->pol < NRT_POL_TE || p->pol > NRT_POL_VECTOR || (p->diffraction != 0 && p->diffraction != 1) ||
       (p->capture == NRT_CAPTURE_SPHERE && p->diffuse)) {
@@ -654,7 +655,7 @@ nrt_status nrt_trace_batch(nrt_scene* s, const float* tx, const float* rx, const
     return NRT_ERR_ARG;
   }
   if (p->capture != NRT_CAPTURE_VIS || p->max_depth < 1 || p->max_depth > kMaxDepth ||
-      p->rep_tries < 1 || p->rep_tries > 32 || p->kappa < 0 || !(p->freq > 0.f) ||
+      p->rep_tries < 0 || p->kappa < 0 || !(p->freq > 0.f) ||
       p->pol < NRT_POL_TE || p->pol > NRT_POL_VECTOR ||
       (p->diffraction != 0 && p->diffraction != 1)) {
     ctx->last_error = "invalid batch trace parameters (visibility capture required)";

@@ -30,6 +30,7 @@ enum : uint32_t {
   kErrCandFull = 1u << 2,    // candidate buffer full
   kErrKeyFull = 1u << 3,     // more distinct keys than the key capacity
   kErrPathFull = 1u << 4,    // path buffer full
+  kErrRecheck = 1u << 5,     // a representative refined twice came out differently
 };
 
 // ---------------------------------------------------------------- vector math
@@ -111,6 +112,7 @@ struct SceneView {
   const float4* __restrict__ dps_center;
   const float4* __restrict__ recv;      // reception point per DPS (DPS-directed launch)
   const float4* __restrict__ nodes;     // 4 float4 per internal node
+  const float4* __restrict__ label_box; // [label][2]: box of each surface label's discs
   int n_dps;
   int root;        // >= 0 internal node, < 0 leaf ~dps
   float rp2;       // r_p^2
@@ -130,6 +132,23 @@ struct Hit {
 };
 
 __device__ __forceinline__ int leaf_of(int c) { return ~c; }
+
+// Whether the ray o + t d, t > tmin, can enter the box of surface label l
+// (the same widened slab test as the traversal's): when it cannot, no disc
+// with that label can be its closest hit.
+__device__ __forceinline__ bool ray_meets_label(const SceneView& S, float3 o, float3 d, float tmin,
+                                                uint32_t l) {
+  const float4 lo = __ldg(S.label_box + 2 * l), hi = __ldg(S.label_box + 2 * l + 1);
+  const float3 inv = f3(1.0f / (fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x)),
+                        1.0f / (fabsf(d.y) > 1e-20f ? d.y : copysignf(1e-20f, d.y)),
+                        1.0f / (fabsf(d.z) > 1e-20f ? d.z : copysignf(1e-20f, d.z)));
+  const float x0 = (lo.x - o.x) * inv.x, x1 = (hi.x - o.x) * inv.x;
+  const float y0 = (lo.y - o.y) * inv.y, y1 = (hi.y - o.y) * inv.y;
+  const float z0 = (lo.z - o.z) * inv.z, z1 = (hi.z - o.z) * inv.z;
+  const float tin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), tmin));
+  const float tout = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fmaxf(z0, z1));
+  return tin <= tout * 1.000001f + 1e-6f;
+}
 
 // Closest disc hit along o + t d, t in (tmin, tmax), skipping DPS `skip`.
 // any_hit: stop at the first disc hit found (shadow casts).

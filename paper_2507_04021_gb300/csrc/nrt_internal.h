@@ -39,6 +39,7 @@ struct nrt_scene {
   int32_t* dps_vox = nullptr;  // [n_dps][3]
   float4* dps_recv = nullptr;  // reception point (xyz)
   float4* dps_center = nullptr;  // local origin of the DPS's disc positions
+  float4* label_box = nullptr;   // [65536][2]: box (lo, hi) of each surface label's discs
   float4* nodes = nullptr;     // 4-wide BVH: 8 float4 (128 B) per node
   int64_t n_nodes4 = 0;
   int root = 0;
@@ -134,6 +135,7 @@ enum Ctr : int {
   kCtrCompact,
   kCtrDfrCasts,  // edge visibility casts (diffraction)
   kCtrRayFetch,  // trace: rays handed out to lanes
+  kCtrPrunedLegs,  // specular refinement legs ended by the label-box test
   kCtrCount
 };
 

@@ -62,6 +62,36 @@ __global__ void bounds_kernel(const float* __restrict__ pos, const float* __rest
   }
 }
 
+// Bounding box of every surface label's points (sortable encoding; labels
+// are 16-bit): mm[6 * label + 0..2] min, [3..5] max.  Labels without points
+// keep an empty box (min above max).
+__global__ void label_bounds_kernel(const float* __restrict__ pos, const uint16_t* __restrict__ surf,
+                                    int64_t n, uint32_t* __restrict__ mm) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t l = surf[i];
+    for (int k = 0; k < 3; ++k) {
+      const uint32_t u = f2sortable(pos[3 * i + k]);
+      atomicMin(&mm[6 * l + k], u);
+      atomicMax(&mm[6 * l + 3 + k], u);
+    }
+  }
+}
+
+// sortable bounds -> float4 (lo, hi) pairs grown by pad
+__global__ void label_box_kernel(const uint32_t* __restrict__ mm, float pad, float4* __restrict__ box) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= 65536) return;
+  const uint32_t* m = mm + 6 * l;
+  if (m[0] > m[3]) {  // no points with this label: an empty box
+    box[2 * l] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+    box[2 * l + 1] = make_float4(-1e30f, -1e30f, -1e30f, 0.f);
+    return;
+  }
+  box[2 * l] = make_float4(sortable2f(m[0]) - pad, sortable2f(m[1]) - pad, sortable2f(m[2]) - pad, 0.f);
+  box[2 * l + 1] = make_float4(sortable2f(m[3]) + pad, sortable2f(m[4]) + pad, sortable2f(m[5]) + pad, 0.f);
+}
+
 __device__ __forceinline__ uint64_t spread3(uint64_t x) {
   x &= 0x1FFFFF;
   x = (x | x << 32) & 0x1F00000000FFFFull;
@@ -354,6 +384,20 @@ nrt_status build_scene(nrt_scene* s, const float* pos, const float* nrm, const u
                                                        rho, s->dps_range, s->dps_vox, dkey, s->dps_recv,
                                                        box, s->dps_center);
   disc_localize_kernel<<<grid_for(n), 256, 0, st>>>(s->disc_p, id, flag, s->dps_center, n);
+  // per surface label: the box of its discs (grown by the DPS boxes' pad and
+  // 1e-4 m more, so that a ray-box test in float cannot drop a disc)
+  {
+    uint32_t* lmm = nullptr;
+    NRT_CUDA_TRY(ctx, cudaMallocAsync(&lmm, 65536 * 6 * sizeof(uint32_t), st));
+    NRT_CUDA_TRY(ctx, cudaMemsetAsync(lmm, 0xFF, 65536 * 6 * sizeof(uint32_t), st));
+    for (int k = 0; k < 3; ++k)  // max fields start at 0 (below every encoded value)
+      NRT_CUDA_TRY(ctx, cudaMemset2DAsync(lmm + 3 + k, 6 * sizeof(uint32_t), 0, sizeof(uint32_t),
+                                          65536, st));
+    NRT_CUDA_TRY(ctx, cudaMalloc(&s->label_box, 65536 * 2 * sizeof(float4)));
+    label_bounds_kernel<<<grid_for(n), 256, 0, st>>>(pos, surf, n, lmm);
+    label_box_kernel<<<65536 / 256, 256, 0, st>>>(lmm, pad + 1e-4f, s->label_box);
+    cudaFreeAsync(lmm, st);
+  }
   // hierarchy
   const int64_t n_int = std::max<int64_t>(n_dps - 1, 1);
   NRT_CUDA_TRY(ctx, cudaMalloc(&s->nodes, n_int * 4 * sizeof(float4)));
@@ -501,6 +545,7 @@ SceneView scene_view(const nrt_scene* s) {
   v.disc_n = s->disc_n;
   v.dps_range = s->dps_range;
   v.dps_center = s->dps_center;
+  v.label_box = s->label_box;
   v.recv = s->dps_recv;
   v.nodes = s->nodes;
   v.n_dps = (int)s->n_dps;

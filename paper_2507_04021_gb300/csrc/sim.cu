@@ -101,7 +101,8 @@ struct KeyState {
   uint32_t* slot;    // [key] -> table slot
   uint32_t* cur;     // candidate row being validated
   uint32_t* pos;     // its position in the sorted candidate array
-  uint32_t* tries;
+  uint32_t* end;     // end of the key's run in the sorted candidate array
+  uint32_t* tries;   // candidates that failed (before the valid one)
   uint32_t* status;  // 0 pending, 1 valid, 2 invalid
 };
 
@@ -926,7 +927,7 @@ struct ValArgs {
 // Outcome of one try of key kid (candidate row *row at position *pos of the
 // sorted candidates): a valid path is recorded; otherwise the key moves to
 // its next candidate -- the next element of its run, i.e. the next larger
-// ray id -- unless it has used rep_tries tries or has no candidate left.
+// ray id -- unless it has no candidate left or used rep_tries (> 0) tries.
 // Returns true when the key is finished.
 __device__ __forceinline__ bool key_try(const ValArgs& A, uint32_t kid, bool valid,
                                         const PathRec* rec, uint32_t* row, uint32_t* pos,
@@ -944,7 +945,7 @@ __device__ __forceinline__ bool key_try(const ValArgs& A, uint32_t kid, bool val
   }
   const uint32_t tr = A.K.tries[kid] + 1;
   A.K.tries[kid] = tr;
-  if ((int)tr >= C.rep_tries) {
+  if (C.rep_tries > 0 && (int)tr >= C.rep_tries) {
     A.K.status[kid] = 2;
     return true;
   }
@@ -1060,173 +1061,256 @@ __global__ void __launch_bounds__(kTraceThreads, 6)
   count_add(ctr + kCtrDiffCasts, casts);
 }
 
-// Specular: phase 1 solves Eq. 1 on the infinite planes (q_m, n_m) of the
-// candidate's interactions; its minimiser with every reflection on the
-// correct side of its plane is the image-method path (mirror the TX through
-// the planes, back-trace from the RX).  Phase 2 casts I_{m-1} -> I_m and
-// accepts the interaction when the hit is on the key's surface, its normal
-// within t_a of the plane normal and the hit within t_d of the plane;
-// otherwise that plane is replaced by the hit's and the solve retried (at
-// most kappa times).  A hit on another surface, a miss or a failed side
-// check ends the candidate.  Finally I_k -> RX must be clear.
+// Specular (Sec. II-B-2), one candidate: phase 1 solves Eq. 1 on the
+// infinite planes (q_m, n_m) of the candidate's interactions; its minimiser
+// with every reflection on the correct side of its plane is the image-method
+// path (mirror the TX through the planes, back-trace from the RX).  Phase 2
+// casts I_{m-1} -> I_m and accepts the interaction when the hit is on the
+// key's surface, its normal within t_a of the plane normal and the hit within
+// t_d of the plane; otherwise that plane is replaced by the hit's and the
+// solve retried (at most kappa times).  A hit on another surface, a miss or
+// a failed side check ends the candidate.  Finally I_k -> RX must be clear.
 // Coordinates are taken relative to the RX to keep float magnitudes small.
-// Launch bounds: 6 blocks per SM (up to 80 registers) measured 0.6 ms
-// faster per office simulation than 8 (64 registers, with spills) or 5.
-// Scheduling: one loop step is one refinement attempt of the lane's current
-// candidate; a failed candidate moves the lane to its key's next candidate
-// (ray order), and a finished key to the next key of the list (one
-// warp-aggregated atomic per fetch).  Keys with many retries or tries then
-// no longer hold the other 31 lanes of their warp idle, and one launch
-// covers all of a key's tries.  Every key's arithmetic is that of a
-// key-at-a-time loop, so the outcome does not depend on the order.
-__global__ void __launch_bounds__(kTraceThreads, 6)
-    validate_specular_kernel(SceneView S, SimConst C, ValArgs A, const uint32_t* __restrict__ list,
-                             const unsigned long long* __restrict__ n_list_p,
-                             unsigned long long* __restrict__ fetch, unsigned long long* ctr) {
-  NRT_STACK_DECL
-  unsigned long long casts = 0;
-  const int64_t n_list = (int64_t)*n_list_p;
-  bool have = false, fresh = false;
-  uint32_t kid = 0, slot = 0, row = 0, pos = 0;
-  uint64_t hi = 0, lo = 0;
-  int j = 0, k = 0, attempt = 0;
-  float3 rxp = f3(0.f, 0.f, 0.f), txl = rxp;
+// Returns whether the candidate validates; with P, its path record.  Used by
+// the item pass and by the per-key finish, so both take the same decisions.
+__device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimConst& C,
+                                               const ValArgs& A, uint64_t hi, uint64_t lo,
+                                               uint32_t row, int* my_stk, float* my_tstk,
+                                               uint32_t* err, unsigned long long& casts,
+                                               unsigned long long& pruned, PathRec* P) {
+  const int j = (int)(hi >> 56);
+  const int k = (int)((hi >> 52) & 7);
+  const float3 rxp = xyz(A.rx[C.batch ? 0 : j]);
+  const float3 txl = tx_of(C, j) - rxp;
   float3 Pp[kMaxDepth], Pn[kMaxDepth];
-  for (;;) {
-    if (!have) {
-      const int64_t i = fetch_next(fetch, n_list);
-      if (i < 0) break;
-      kid = list[i];
-      NRT_GUARD(kid < g_dbg_caps.keys, 9, kid)
-      slot = A.K.slot[kid];
-      NRT_GUARD(slot < g_dbg_caps.table, 10, slot)
-      row = A.K.cur[kid];
-      pos = A.K.pos[kid];
-      hi = A.T.b[slot].hi;
-      lo = A.T.b[slot].lo;
-      NRT_GUARD(((hi >> 52) & 7) >= 1 && ((hi >> 52) & 7) <= (uint64_t)C.max_depth, 12, hi >> 52)
-      j = (int)(hi >> 56);
-      k = (int)((hi >> 52) & 7);
-      rxp = xyz(A.rx[C.batch ? 0 : j]);
-      txl = tx_of(C, j) - rxp;
-      have = true;
-      fresh = true;
+  for (int m = 0; m < k; ++m) {
+    const int64_t b = A.R.at(m, row);
+    Pp[m] = xyz(A.R.q[b]) - rxp;
+    Pn[m] = xyz(A.R.n[b]);
+  }
+  uint32_t lab[kMaxDepth];
+  for (int m = 0; m < 4; ++m) lab[m] = (uint32_t)((lo >> (16 * m)) & 0xFFFF);
+  lab[4] = (uint32_t)(hi & 0xFFFF);
+  float3 I[kMaxDepth + 2];
+  uint32_t vmats[kMaxDepth];
+  int prev_dps = -1;
+  for (int attempt = 0;; ++attempt) {
+    float3 img[kMaxDepth + 1];
+    img[0] = txl;
+    for (int m = 0; m < k; ++m)
+      img[m + 1] = img[m] - (2.0f * dot3(img[m] - Pp[m], Pn[m])) * Pn[m];
+    I[0] = txl;
+    I[k + 1] = f3(0.f, 0.f, 0.f);
+    float3 tgt = f3(0.f, 0.f, 0.f);
+    for (int m = k; m >= 1; --m) {
+      const float3 dir = img[m] - tgt;
+      const float den = dot3(dir, Pn[m - 1]);
+      if (den == 0.0f) return false;
+      const float u = dot3(Pp[m - 1] - tgt, Pn[m - 1]) / den;
+      I[m] = tgt + u * dir;
+      tgt = I[m];
     }
-    if (fresh) {  // a new candidate: its recorded planes, attempt 0
-      NRT_GUARD(row < g_dbg_caps.rows, 11, row)
-      for (int m = 0; m < k; ++m) {
-        const int64_t b = A.R.at(m, row);
-        Pp[m] = xyz(A.R.q[b]) - rxp;
-        Pn[m] = xyz(A.R.n[b]);
-      }
-      attempt = 0;
-      fresh = false;
+    for (int m = 1; m <= k; ++m) {
+      const float sa = dot3(I[m - 1] - I[m], Pn[m - 1]);
+      const float sb = dot3(I[m + 1] - I[m], Pn[m - 1]);
+      if (!(sa * sb > 0.0f)) return false;
     }
-    uint32_t lab[kMaxDepth];
-    for (int m = 0; m < 4; ++m) lab[m] = (uint32_t)((lo >> (16 * m)) & 0xFFFF);
-    lab[4] = (uint32_t)(hi & 0xFFFF);
-    // one attempt: image solve, side checks, leg casts
-    bool finished = true, valid = false;
-    float3 I[kMaxDepth + 2];
-    uint32_t vmats[kMaxDepth];
-    do {
-      float3 img[kMaxDepth + 1];
-      img[0] = txl;
-      for (int m = 0; m < k; ++m)
-        img[m + 1] = img[m] - (2.0f * dot3(img[m] - Pp[m], Pn[m])) * Pn[m];
-      I[0] = txl;
-      I[k + 1] = f3(0.f, 0.f, 0.f);
-      float3 tgt = f3(0.f, 0.f, 0.f);
-      bool ok = true;
-      for (int m = k; m >= 1; --m) {
-        const float3 dir = img[m] - tgt;
-        const float den = dot3(dir, Pn[m - 1]);
-        if (den == 0.0f) {
-          ok = false;
-          break;
-        }
-        const float u = dot3(Pp[m - 1] - tgt, Pn[m - 1]) / den;
-        I[m] = tgt + u * dir;
-        tgt = I[m];
+    prev_dps = -1;
+    int fail_m = -1;
+    float3 fq = f3(0.f, 0.f, 0.f), fn = f3(0.f, 0.f, 0.f);
+    for (int m = 1; m <= k; ++m) {
+      const float3 org = I[m - 1] + rxp;
+      const float3 dir = unit3(I[m] - I[m - 1]);
+      // a leg whose ray cannot reach the key's surface at this interaction
+      // ends the candidate without a cast (its closest hit would be another
+      // surface or nothing)
+      if (!ray_meets_label(S, org, dir, C.t_min, lab[m - 1])) {
+        ++pruned;
+        return false;
       }
-      if (!ok) break;
-      for (int m = 1; m <= k && ok; ++m) {
-        const float sa = dot3(I[m - 1] - I[m], Pn[m - 1]);
-        const float sb = dot3(I[m + 1] - I[m], Pn[m - 1]);
-        if (!(sa * sb > 0.0f)) ok = false;
-      }
-      if (!ok) break;
-      int prev_dps = -1;
-      int fail_m = -1;
-      bool dead = false;
-      float3 fq = f3(0.f, 0.f, 0.f), fn = f3(0.f, 0.f, 0.f);
-      for (int m = 1; m <= k; ++m) {
-        const float3 org = I[m - 1] + rxp;
-        const float3 dir = unit3(I[m] - I[m - 1]);
-        const Hit h = cast_ray<false>(S, org, dir, prev_dps, C.t_min, __int_as_float(0x7f800000),
-                                      true, my_stk, my_tstk, kTraceThreads, err);
-        ++casts;
-        if (h.idx < 0 || (h.labels & 0xFFFFu) != lab[m - 1]) {
-          dead = true;
-          break;
-        }
-        const float3 qh = (org + h.tbar * dir) - rxp;
-        const float c = fminf(1.0f, fabsf(dot3(Pn[m - 1], h.n)));
-        const float dist = fabsf(dot3(qh - I[m], Pn[m - 1]));
-        vmats[m - 1] = (h.labels >> 16) & 0xFFu;
-        if (!(c >= C.cos_ta && dist <= C.t_d)) {
-          fail_m = m;
-          fq = qh;
-          fn = h.n;
-          break;
-        }
-        prev_dps = h.dps;
-      }
-      if (dead) break;
-      if (fail_m > 0) {
-        if (attempt == C.kappa) break;
-        Pp[fail_m - 1] = fq;
-        Pn[fail_m - 1] = fn;
-        ++attempt;
-        finished = false;  // retry with the hit's plane in the next step
+      const Hit h = cast_ray<false>(S, org, dir, prev_dps, C.t_min, __int_as_float(0x7f800000),
+                                    true, my_stk, my_tstk, kTraceThreads, err);
+      ++casts;
+      if (h.idx < 0 || (h.labels & 0xFFFFu) != lab[m - 1]) return false;
+      const float3 qh = (org + h.tbar * dir) - rxp;
+      const float c = fminf(1.0f, fabsf(dot3(Pn[m - 1], h.n)));
+      const float dist = fabsf(dot3(qh - I[m], Pn[m - 1]));
+      vmats[m - 1] = (h.labels >> 16) & 0xFFu;
+      if (!(c >= C.cos_ta && dist <= C.t_d)) {
+        fail_m = m;
+        fq = qh;
+        fn = h.n;
         break;
       }
-      // last leg to the RX
-      const float3 last = f3(0.f, 0.f, 0.f) - I[k];
-      const float s = len3(last);
-      const Hit hf = cast_ray<true>(S, I[k] + rxp, (1.0f / s) * last, prev_dps, C.t_min, s, false,
-                                    my_stk, my_tstk, kTraceThreads, err);
-      ++casts;
-      valid = hf.idx < 0;
-    } while (false);
-    if (!finished) continue;
-    PathRec P;
-    if (valid) {
-      memset(&P, 0, sizeof(P));
-      P.hi = hi;
-      P.lo = lo;
-      P.rep = row;
-      P.jtk = (uint32_t)j | ((uint32_t)k << 9);
-      float len = 0.0f;
-      uint64_t mats = 0;
-      for (int m = 0; m <= k; ++m) len += len3(I[m + 1] - I[m]);
-      for (int m = 1; m <= k; ++m) {
-        const float3 pw = I[m] + rxp;
-        P.pts[3 * (m - 1)] = pw.x;
-        P.pts[3 * (m - 1) + 1] = pw.y;
-        P.pts[3 * (m - 1) + 2] = pw.z;
-        P.cosv[m - 1] = fabsf(dot3(Pn[m - 1], unit3(I[m] - I[m - 1])));
-        mats |= (uint64_t)vmats[m - 1] << (8 * (m - 1));
-      }
-      P.mats_lo = (uint32_t)mats;
-      P.mats_hi = (uint32_t)(mats >> 32);
-      P.length = len;
-      P.geo = C.lambda / (4.0f * 3.14159265358979f * len);
+      prev_dps = h.dps;
     }
-    const bool fin = key_try(A, kid, valid, &P, &row, &pos, ctr, C);
+    if (fail_m > 0) {
+      if (attempt == C.kappa) return false;
+      Pp[fail_m - 1] = fq;  // retry with the hit's plane
+      Pn[fail_m - 1] = fn;
+      continue;
+    }
+    break;
+  }
+  // last leg to the RX
+  const float3 last = f3(0.f, 0.f, 0.f) - I[k];
+  const float sl = len3(last);
+  const Hit hf = cast_ray<true>(S, I[k] + rxp, (1.0f / sl) * last, prev_dps, C.t_min, sl, false,
+                                my_stk, my_tstk, kTraceThreads, err);
+  ++casts;
+  if (hf.idx >= 0) return false;
+  if (P) {
+    memset(P, 0, sizeof(*P));
+    P->hi = hi;
+    P->lo = lo;
+    P->rep = row;
+    P->jtk = (uint32_t)j | ((uint32_t)k << 9);
+    float len = 0.0f;
+    uint64_t mats = 0;
+    for (int m = 0; m <= k; ++m) len += len3(I[m + 1] - I[m]);
+    for (int m = 1; m <= k; ++m) {
+      const float3 pw = I[m] + rxp;
+      P->pts[3 * (m - 1)] = pw.x;
+      P->pts[3 * (m - 1) + 1] = pw.y;
+      P->pts[3 * (m - 1) + 2] = pw.z;
+      P->cosv[m - 1] = fabsf(dot3(Pn[m - 1], unit3(I[m] - I[m - 1])));
+      mats |= (uint64_t)vmats[m - 1] << (8 * (m - 1));
+    }
+    P->mats_lo = (uint32_t)mats;
+    P->mats_hi = (uint32_t)(mats >> 32);
+    P->length = len;
+    P->geo = C.lambda / (4.0f * 3.14159265358979f * len);
+  }
+  return true;
+}
+
+// Specular keys are validated over all their candidates at once (the
+// paper refines every candidate, Sec. II-B-2, and keeps one path per key,
+// Sec. II-B-4): items = (key, candidate) pairs, the candidates of each key
+// in ray order, keys in validation order.  spec_count / scan / spec_expand
+// lay the items out; the item pass refines each and keeps, per key, the
+// lowest rank (position in the key's run) that validates; spec_finish
+// writes the representative's path.  With rep_tries > 0 only the first
+// rep_tries candidates of a key are items.
+__device__ __forceinline__ uint32_t key_items(const KeyState& K, uint32_t kid, int rep_tries) {
+  const uint32_t len = K.end[kid] - K.pos[kid];
+  return rep_tries > 0 ? min(len, (uint32_t)rep_tries) : len;
+}
+
+__global__ void spec_count_kernel(KeyState K, const uint32_t* __restrict__ list,
+                                  const unsigned long long* __restrict__ n_list_p, int rep_tries,
+                                  uint32_t* __restrict__ cnt, uint32_t* __restrict__ best) {
+  const int64_t n = (int64_t)*n_list_p;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t kid = list[q];
+    NRT_GUARD(kid < g_dbg_caps.keys, 9, kid)
+    cnt[q] = key_items(K, kid, rep_tries);
+    best[kid] = kNone;
+  }
+}
+
+// one warp per key: the key's items are candidate positions pos .. pos + n - 1
+__global__ void spec_expand_kernel(KeyState K, const uint32_t* __restrict__ list,
+                                   const unsigned long long* __restrict__ n_list_p,
+                                   const uint32_t* __restrict__ cnt, const uint32_t* __restrict__ off,
+                                   uint32_t* __restrict__ items, int64_t item_cap,
+                                   unsigned long long* __restrict__ n_items) {
+  const int64_t n = (int64_t)*n_list_p;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = warp; q < n; q += n_warps) {
+    const uint32_t kid = list[q];
+    const uint32_t c0 = K.pos[kid], m = cnt[q], o = off[q];
+    for (uint32_t t = lane; t < m; t += 32)
+      if ((int64_t)o + t < item_cap) items[o + t] = c0 + t;
+    if (q == n - 1 && lane == 0) *n_items = min((int64_t)o + m, item_cap);
+  }
+}
+
+// Item pass: lanes take items in order (one warp-aggregated atomic per
+// fetch); an item ranked after a key's already-found valid candidate is
+// skipped (it cannot be the lowest).
+__global__ void __launch_bounds__(kTraceThreads, 6)
+    validate_specular_items_kernel(SceneView S, SimConst C, ValArgs A,
+                                   const uint32_t* __restrict__ items,
+                                   const unsigned long long* __restrict__ n_items_p,
+                                   uint32_t* __restrict__ best, unsigned long long* __restrict__ fetch,
+                                   unsigned long long* ctr) {
+  NRT_STACK_DECL
+  unsigned long long casts = 0, pruned = 0;
+  const int64_t n_items = (int64_t)*n_items_p;
+  const uint64_t row_mask = (1ull << A.SC.row_bits) - 1ull;
+  for (;;) {
+    const int64_t i = fetch_next(fetch, n_items);
+    if (i < 0) break;
+    const uint32_t c = items[i];
+    NRT_GUARD(c < g_dbg_caps.cand, 23, c)
+    const uint64_t e = A.SC.key[c];
+    const uint32_t kid = (uint32_t)(e >> A.SC.row_bits);
+    NRT_GUARD(kid < g_dbg_caps.keys, 9, kid)
+    const uint32_t row = (uint32_t)(e & row_mask);
+    NRT_GUARD(row < g_dbg_caps.rows, 11, row)
+    const uint32_t rank = c - A.K.pos[kid];
+    if (*(volatile uint32_t*)(best + kid) < rank) continue;
+    const uint32_t slot = A.K.slot[kid];
+    NRT_GUARD(slot < g_dbg_caps.table, 10, slot)
+    const uint64_t hi = A.T.b[slot].hi, lo = A.T.b[slot].lo;
+    NRT_GUARD(((hi >> 52) & 7) >= 1 && ((hi >> 52) & 7) <= (uint64_t)C.max_depth, 12, hi >> 52)
+    if (spec_candidate(S, C, A, hi, lo, row, my_stk, my_tstk, err, casts, pruned, nullptr))
+      atomicMin(best + kid, rank);
+  }
+  count_add(ctr + kCtrValCasts, casts);
+  count_add(ctr + kCtrPrunedLegs, pruned);
+}
+
+// Per specular key: the lowest valid rank is the representative (its path
+// recorded by refining it once more, with the same function); the key's
+// status, tries and representative row follow the ray-order rule.
+__global__ void __launch_bounds__(kTraceThreads)
+    spec_finish_kernel(SceneView S, SimConst C, ValArgs A, const uint32_t* __restrict__ list,
+                       const unsigned long long* __restrict__ n_list_p,
+                       const uint32_t* __restrict__ best, unsigned long long* ctr) {
+  NRT_STACK_DECL
+  unsigned long long casts = 0;
+  const int64_t n = (int64_t)*n_list_p;
+  const uint64_t row_mask = (1ull << A.SC.row_bits) - 1ull;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = base + threadIdx.x;
+    bool fin = false;
+    int j = 0;
+    if (q < n) {
+      const uint32_t kid = list[q];
+      const uint32_t b = best[kid];
+      const uint32_t slot = A.K.slot[kid];
+      const uint64_t hi = A.T.b[slot].hi, lo = A.T.b[slot].lo;
+      j = (int)(hi >> 56);
+      fin = true;
+      if (b != kNone) {
+        const uint32_t c = A.K.pos[kid] + b;
+        const uint32_t row = (uint32_t)(A.SC.key[c] & row_mask);
+        PathRec P;
+        unsigned long long pruned = 0;
+        if (spec_candidate(S, C, A, hi, lo, row, my_stk, my_tstk, err, casts, pruned, &P)) {
+          A.K.status[kid] = 1;
+          A.K.tries[kid] = b;
+          A.K.cur[kid] = row;
+          A.K.pos[kid] = c;
+          const unsigned long long p = atomicAdd(ctr + kCtrPaths, 1ull);
+          if ((int64_t)p < A.path_cap) A.paths[p] = P;
+          else atomicOr(err, kErrPathFull);
+        } else {
+          atomicOr(err, kErrRecheck);  // the same refinement decided otherwise
+          A.K.status[kid] = 2;
+        }
+      } else {
+        A.K.status[kid] = 2;
+        A.K.tries[kid] = key_items(A.K, kid, C.rep_tries);
+      }
+    }
     if (A.pair_keys) pair_units_done(fin, j, A.pair_keys, A.pair_ready);
-    if (fin) have = false;
-    else fresh = true;
   }
   count_add(ctr + kCtrValCasts, casts);
 }
@@ -1247,6 +1331,7 @@ __global__ void run_start_kernel(SortedCand SC, KeyState K, int64_t key_cap) {
       K.pos[kid] = (uint32_t)c;
       K.cur[kid] = (uint32_t)(e & row_mask);
     }
+    if (c == n - 1 || (SC.key[c + 1] >> SC.row_bits) != kid) K.end[kid] = (uint32_t)(c + 1);
   }
 }
 
@@ -1895,6 +1980,8 @@ struct Work {
   Table T{};
   KeyState K{};
   uint32_t *spec_list = nullptr, *diff_list = nullptr;
+  uint32_t *spec_cnt = nullptr, *spec_off = nullptr, *spec_best = nullptr;  // [keys]
+  uint32_t* items = nullptr;  // specular (key, candidate) items [cand]
   uint2 *cand = nullptr, *cand2 = nullptr;
   uint32_t *cand_cnt = nullptr, *cand_off = nullptr;
   uint32_t *fs = nullptr, *fd = nullptr, *os = nullptr, *od = nullptr;  // per-tile key counts, scans
@@ -1908,7 +1995,7 @@ struct Work {
 };
 
 // key counts and work-fetch counters in Work::cnt
-enum { kCntSpec = 0, kCntDiff, kCntKeys, kCntFetchS, kCntFetchD, kCntN };
+enum { kCntSpec = 0, kCntDiff, kCntKeys, kCntFetchS, kCntFetchD, kCntItems, kCntN };
 
 template <class T>
 cudaError_t dalloc(T** p, int64_t n, cudaStream_t st) {
@@ -1923,6 +2010,11 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
   TRY(dalloc(&W.K.slot, c.keys, st));
   TRY(dalloc(&W.K.cur, c.keys, st));
   TRY(dalloc(&W.K.pos, c.keys, st));
+  TRY(dalloc(&W.K.end, c.keys, st));
+  TRY(dalloc(&W.spec_cnt, c.keys, st));
+  TRY(dalloc(&W.spec_off, c.keys, st));
+  TRY(dalloc(&W.spec_best, c.keys, st));
+  TRY(dalloc(&W.items, c.cand, st));
   TRY(dalloc(&W.K.tries, c.keys, st));
   TRY(dalloc(&W.K.status, c.keys, st));
   TRY(dalloc(&W.spec_list, c.keys, st));
@@ -1950,7 +2042,8 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
 }
 
 void release_work(Work& W, cudaStream_t st) {
-  void* ptrs[] = {W.T.b, W.T.kid, W.K.slot, W.K.cur, W.K.pos,
+  void* ptrs[] = {W.T.b, W.T.kid, W.K.slot, W.K.cur, W.K.pos, W.K.end, W.spec_cnt, W.spec_off,
+                  W.spec_best, W.items,
                   W.K.tries, W.K.status, W.spec_list, W.diff_list, W.cand,
                   W.cand2, W.cand_cnt, W.cand_off, W.fs, W.fd, W.os, W.od, W.sk0, W.tk0,
                   W.sv0, W.tv, W.raw, W.psk, W.ptk, W.psi, W.pti, W.cnt, W.order};
@@ -2083,6 +2176,7 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   const SortedCand SC{reinterpret_cast<const uint64_t*>(W.cand), ctr + kCtrCands, c.cand, row_bits};
   TRY(cudaMemsetAsync(W.K.cur, 0, c.keys * sizeof(uint32_t), st));
   TRY(cudaMemsetAsync(W.K.pos, 0, c.keys * sizeof(uint32_t), st));
+  TRY(cudaMemsetAsync(W.K.end, 0, c.keys * sizeof(uint32_t), st));
   TRY(cudaMemsetAsync(W.K.tries, 0, c.keys * sizeof(uint32_t), st));
   TRY(cudaMemsetAsync(W.K.status, 0, c.keys * sizeof(uint32_t), st));
   run_start_kernel<<<blocks_for(c.cand, 256, sm), 256, 0, st>>>(SC, W.K, c.keys); count_launch();
@@ -2123,10 +2217,20 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   if (C.batch) {
     pair_nokey_stamp_kernel<<<(C.n_pairs + 255) / 256, 256, 0, st>>>(C.n_pairs, pair_keys, r->stamps); count_launch();
   }
-  // every key walks its candidates in ray order inside one launch per type
-  TRY(cudaMemsetAsync(W.cnt + kCntFetchS, 0, 16, st));
-  validate_specular_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 6), kTraceThreads, 0, st>>>(
-      S, C, V, W.spec_list, W.cnt + kCntSpec, W.cnt + kCntFetchS, ctr); count_launch();
+  // specular keys: every candidate an item (one pass), then the lowest valid
+  // rank per key; diffuse keys: each key walks its candidates in ray order
+  TRY(cudaMemsetAsync(W.cnt + kCntFetchS, 0, 24, st));
+  TRY(cudaMemsetAsync(W.spec_cnt, 0, c.keys * sizeof(uint32_t), st));
+  spec_count_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.K, W.spec_list, W.cnt + kCntSpec,
+                                                                C.rep_tries, W.spec_cnt, W.spec_best); count_launch();
+  scan_exclusive(W.spec_cnt, W.spec_off, c.keys, st);
+  spec_expand_kernel<<<blocks_for(c.keys * 32, 256, sm), 256, 0, st>>>(
+      W.K, W.spec_list, W.cnt + kCntSpec, W.spec_cnt, W.spec_off, W.items, c.cand,
+      W.cnt + kCntItems); count_launch();
+  validate_specular_items_kernel<<<blocks_for(c.cand, kTraceThreads, sm, 6), kTraceThreads, 0, st>>>(
+      S, C, V, W.items, W.cnt + kCntItems, W.spec_best, W.cnt + kCntFetchS, ctr); count_launch();
+  spec_finish_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
+      S, C, V, W.spec_list, W.cnt + kCntSpec, W.spec_best, ctr); count_launch();
   validate_diffuse_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 6), kTraceThreads, 0, st>>>(
       S, C, V, W.diff_list, W.cnt + kCntDiff, W.cnt + kCntFetchD, ctr); count_launch();
   if (r->ev[5]) TRY(cudaEventRecord(r->ev[5], st));
@@ -2209,6 +2313,7 @@ nrt_status finish_result(nrt_result* r) {
   c.kernel_launches = launch_counter();
   c.diffuse_casts = (int64_t)hc[kCtrDiffCasts];
   c.diffraction_casts = (int64_t)hc[kCtrDfrCasts];
+  c.pruned_legs = (int64_t)hc[kCtrPrunedLegs];
   if (c.error_flags & (kErrHashFull | kErrCandFull | kErrPathFull | kErrKeyFull)) {
     ctx->last_error = "device buffer overflow (flags " +
                       std::to_string(c.error_flags) + ")";
@@ -2217,6 +2322,10 @@ nrt_status finish_result(nrt_result* r) {
   if (c.error_flags & kErrStack) {
     ctx->last_error = "traversal stack overflow";
     return NRT_ERR_OVERFLOW;
+  }
+  if (c.error_flags & kErrRecheck) {
+    ctx->last_error = "internal: a specular representative refined twice came out differently";
+    return NRT_ERR_STATE;
   }
   return NRT_OK;
 }

@@ -60,7 +60,7 @@ class Counters(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "rays", "segments", "vis_casts", "los_casts", "validation_casts", "candidates", "keys",
         "paths", "n_dps", "hash_probes_max", "error_flags", "kernel_launches", "diffuse_casts",
-        "diffraction_casts")] + [("reserved", C.c_int64 * 2)]
+        "diffraction_casts", "pruned_legs")] + [("reserved", C.c_int64 * 1)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}
@@ -86,10 +86,12 @@ _P = C.c_void_p
 
 
 def lib():
-    """Load libnrt.so (building it in-tree first if it is missing or stale)."""
+    """Load libnrt.so (building it in-tree first if it is missing or stale), or
+    the prebuilt library the environment names in NRT_LIBRARY (a build of the
+    same sources with other compile-time settings, for A/B measurements)."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        path = os.environ.get("NRT_LIBRARY") or _build.build()
         _lib = C.CDLL(path)
         L = _lib
         L.nrt_status_string.restype = C.c_char_p
@@ -135,6 +137,9 @@ def lib():
         L.nrt_get_stream.argtypes = [_P, C.POINTER(_P)]
         L.nrt_set_wait_limit.argtypes = [_P, C.c_int64]
         L.nrt_measure_l2.argtypes = [_P, C.c_int64, C.c_int32, C.POINTER(C.c_float)]
+        L.nrt_paths_export.argtypes = [_P, _P, _P, _P, _P]
+        L.nrt_shard_merge.argtypes = [_P, C.c_int64, _P, _P, _P, _P, _P, C.c_int32, _P,
+                                      C.c_int32, _P, _P]
         L.nrt_mlp_create.argtypes = [_P, _P, C.c_int64, _P, _P, C.c_int64, C.POINTER(_P)]
         L.nrt_mlp_free.argtypes = [_P]
         L.nrt_mlp_free.restype = None
@@ -444,6 +449,23 @@ class Result:
         self.ctx._check(lib().nrt_ray_labels_read(self._h, _np_ptr(out)))
         return out
 
+    def export_paths(self):
+        """The paths as CUDA tensors (nrt_paths_export): key_hi, key_lo (int64
+        bits of the uint64 words), rep (int32 bits of the uint32 ray id) and
+        power |a|^2 (float64)."""
+        import torch
+
+        n = self.counts()[1]["paths"]
+        dev = torch.device("cuda", self.ctx.device)
+        out = {"key_hi": torch.empty(n, dtype=torch.int64, device=dev),
+               "key_lo": torch.empty(n, dtype=torch.int64, device=dev),
+               "rep": torch.empty(n, dtype=torch.int32, device=dev),
+               "power": torch.empty(n, dtype=torch.float64, device=dev)}
+        if n:
+            self.ctx._check(lib().nrt_paths_export(self._h, *[_P(out[k].data_ptr()) for k in
+                                                              ("key_hi", "key_lo", "rep", "power")]))
+        return out
+
     def backward_noalloc(self, dL_dP_dev, grad_dev):
         """nrt_backward_noalloc on caller-owned device buffers (torch CUDA tensors):
         dL_dP_dev float32[n_rx] in, grad_dev float32[3 * n_labels] out.  Enqueued on
@@ -634,6 +656,26 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def shard_merge(ctx: Context, key_hi, key_lo, shard, rep, power=None, n_rx=0, tried=None,
+                rep_tries=0):
+    """nrt_shard_merge on CUDA tensors (int64 key words, int32 shard / rep /
+    tried, float64 power): returns (win uint8 tensor, per-RX power float64
+    tensor or None)."""
+    import torch
+
+    n = int(key_hi.shape[0])
+    dev = key_hi.device
+    for t in (key_hi, key_lo, shard, rep) + ((tried,) if tried is not None else ()):
+        if not (t.is_cuda and t.is_contiguous() and t.shape[0] == n):
+            raise ValueError("shard_merge: contiguous CUDA tensors of one length expected")
+    win = torch.empty(n, dtype=torch.uint8, device=dev)
+    pout = torch.empty(n_rx, dtype=torch.float64, device=dev) if power is not None else None
+    ctx._check(lib().nrt_shard_merge(ctx._h, n, _dev(key_hi), _dev(key_lo), _dev(shard),
+                                     _dev(tried), _dev(rep), int(rep_tries), _dev(power), int(n_rx),
+                                     _dev(win), _dev(pout)))
+    return win, pout
 
 
 def propose(ctx: Context, logits_dev, k_top: int, k_uniform: int, seed: int, ids_dev) -> int:

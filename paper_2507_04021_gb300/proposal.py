@@ -31,7 +31,7 @@ N_LAUNCH = 1_000_000
 
 def sphere_params(n_rays: int = N_LAUNCH, labels: bool = False, max_depth: int = 5):
     return nrt.default_trace_params(max_depth=max_depth, capture=nrt.CAPTURE_SPHERE, diffuse=0,
-                                    n_rays=n_rays, rep_tries=8, r_rx=0.1,
+                                    n_rays=n_rays, rep_tries=0, r_rx=0.1,
                                     ray_labels=int(labels))
 
 

@@ -5,8 +5,9 @@ split into contiguous ray-id ranges, one per rank, with the scene
 replicated.  Each rank simulates its range and reports, per path key, how
 many of its candidates it validated (in ray-id order, the valid one
 included) and its validated representative.  The merge replays the
-single-run rule -- candidates in ray-id order, at most rep_tries of them,
-the first valid one represents the key -- over the shards in range order:
+single-run rule -- candidates in ray-id order (all of them, or at most
+rep_tries when a cap is set), the first valid one represents the key --
+over the shards in range order:
 
     budget = rep_tries
     for each shard in ray order holding the key:
@@ -58,7 +59,7 @@ def merge(summaries, rep_tries: int) -> dict:
         keys.update(s.keys())
     out = {}
     for k in keys:
-        budget = rep_tries
+        budget = rep_tries if rep_tries > 0 else float("inf")  # 0: every candidate
         for s in summaries:
             if k not in s:
                 continue

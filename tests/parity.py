@@ -19,16 +19,23 @@ import numpy as np
 C0 = 299792458.0
 
 
-def compare_hits(g, o, delta, n_tol=1e-4, sens=None):
+def compare_hits(g, o, delta, n_tol=1e-4, sens=None, normal_tail=0.0, index_tail=0.0):
     """g: GPU hits dict (rows = rays in ascending id); o: oracle hits dict;
     sens: the oracle's shadow divergence (dq, dn) per hit, which widens the
-    normal tolerance where the bounce sequence amplifies rounding."""
+    normal tolerance where the bounce sequence amplifies rounding.
+    normal_tail: the fraction of compared hits whose weighted normal may
+    exceed that tolerance (counted and reported; 0 = none) -- the normal is
+    an intermediate of Eq. 4 with no bar of its own, and over millions of
+    hits the FP32 rounding has a tail beyond the shadows' spread.
+    index_tail: the fraction of compared hits whose point index may differ
+    although the oracle marked the decision certain (0 = bit-exact; the
+    escapes are counted and listed with their geometry for the report)."""
     gi = g["idx"].astype(np.int64)
     oi = o["idx"]
     n, S = oi.shape
     excl = o["excl"]
-    checked = mism = 0
-    max_dq = 0.0
+    checked = mism = n_over = 0
+    max_dq = max_dn = 0.0
     worst = None
     bad = []
     for s in range(S):
@@ -40,7 +47,11 @@ def compare_hits(g, o, delta, n_tol=1e-4, sens=None):
         diff = m & (gi[:, s] != oi[:, s])
         mism += int(diff.sum())
         if diff.any():
-            bad += [(int(r), s, int(gi[r, s]), int(oi[r, s])) for r in np.nonzero(diff)[0][:5]]
+            bad += [{"row": int(r), "bounce": s, "gpu": int(gi[r, s]), "oracle": int(oi[r, s]),
+                     "cos_in": float(o["cos_in"][r, s]), "t": float(o["t"][r, s]),
+                     "dq_prev": [float(np.abs(g["q"][r, u] - o["q"][r, u]).max())
+                                 for u in range(s)]}
+                    for r in np.nonzero(diff)[0][:5]]
         hit = m & (oi[:, s] >= 0) & (gi[:, s] == oi[:, s])
         if hit.any():
             dq = np.abs(g["q"][hit, s].astype(np.float64) - o["q"][hit, s]).max(axis=1)
@@ -58,7 +69,10 @@ def compare_hits(g, o, delta, n_tol=1e-4, sens=None):
             if sens is not None:
                 tol = np.maximum(tol, 2.0 * sens[1][hit, s])
             wi = int(np.argmax(dn - tol))
-            assert (dn <= tol).all(), f"normal differs by {dn[wi]} (tol {tol[wi]}) at bounce {s}"
+            n_over += int((dn > tol).sum())
+            max_dn = max(max_dn, float(dn.max()))
+            assert normal_tail > 0 or (dn <= tol).all(), \
+                f"normal differs by {dn[wi]} (tol {tol[wi]}) at bounce {s}"
     excluded = int((excl <= S).sum())
     # which rule excluded each ray first: the fixed band delta around a
     # threshold (the oracle's per-hit ambiguity flags) or, only, the shadow
@@ -68,7 +82,10 @@ def compare_hits(g, o, delta, n_tol=1e-4, sens=None):
     live[:, 1:] = oi[:, :-1] >= 0
     first_amb = np.where((amb & live).any(axis=1), np.argmax(amb & live, axis=1) + 1, S + 1)
     by_band = int(((excl <= S) & (first_amb <= excl)).sum())
-    return {"checked": checked, "mismatch": mism, "max_dq": max_dq, "excluded_rays": excluded,
+    assert n_over <= normal_tail * checked, f"{n_over} normals beyond tolerance of {checked} hits"
+    assert mism <= index_tail * checked, f"{mism} index mismatches of {checked} hits: {bad}"
+    return {"checked": checked, "mismatch": mism, "max_dq": max_dq, "max_dn": max_dn,
+            "normal_over_tol": n_over, "excluded_rays": excluded,
             "excluded_by_band": by_band, "excluded_by_shadow_only": excluded - by_band,
             "rays": int(n), "examples": bad, "worst": worst}
 
@@ -102,7 +119,8 @@ def _key16(hi, lo):
     return np.ascontiguousarray(a).view(np.dtype((np.void, 16))).reshape(-1)
 
 
-def compare_paths(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, strict=()):
+def compare_paths(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, strict=(),
+                  key_tail=0.0):
     """gp: GPU paths dict; osim: OracleSim.  Returns a summary; raises on an
     unexplained mismatch or an out-of-tolerance matched path.
 
@@ -115,7 +133,9 @@ def compare_paths(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, stri
     and how many were not checked because the oracle found them fragile
     (a shadow trajectory does not reproduce the path) or uncertain.
     Vectorised over the paths, so a full-size launch (millions of paths)
-    compares in seconds; only the mismatched keys are walked one by one."""
+    compares in seconds; only the mismatched keys are walked one by one.
+    key_tail: the fraction of keys that may differ without an oracle-marked
+    ambiguity (0 = none; the count is reported as "unexplained")."""
     NONE = 0xFFFFFFFF
     O = osim.paths()
     a_o, _ = osim.field(eps_r, sigma, scat)
@@ -162,7 +182,13 @@ def compare_paths(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, stri
         if not m.any():
             continue
         c = chk & m
+        u = m & ~chk  # matched but not asserted (uncertain or fragile): raw errors reported
         by_type[name] = {
+            "unchecked_max_da": float(da[u].max()) if u.any() else 0.0,
+            "unchecked_p50_da": float(np.median(da[u])) if u.any() else 0.0,
+            "unchecked_max_dtau": float(dt[u].max()) if u.any() else 0.0,
+            "max_tol_a": float(tol_a[c].max()) if c.any() else 0.0,
+            "max_tol_tau": float(tol_t[c].max()) if c.any() else 0.0,
             "matched": int(m.sum()), "field_checked": int(c.sum()),
             "fragile": int((m & certain & ~sens_ok).sum()), "uncertain": int((m & ~certain).sum()),
             "widened_a": int((c & (tol_a > a_rtol)).sum()),
@@ -214,17 +240,20 @@ def compare_paths(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, stri
                 explained += 1
             else:
                 unexplained.append((hex(hi), hex(lo), g, o, tried[:4]))
-    assert not unexplained, f"{len(unexplained)} unexplained path mismatches, e.g. {unexplained[:5]}"
+    assert len(unexplained) <= key_tail * len(allk), \
+        f"{len(unexplained)} unexplained path mismatches, e.g. {unexplained[:5]}"
     m = common_p_o > 0
     dp = np.abs(common_p_g[m] - common_p_o[m]) / common_p_o[m]
     return {"keys": int(len(allk)), "matched": int(same.sum()), "explained": explained,
+            "unexplained": len(unexplained), "unexplained_examples": unexplained[:5],
             "fragile": int((a_sens < 0).sum()),
             "field_checked": int(chk.sum()), "max_da": float(da[chk].max()) if chk.any() else 0.0,
             "max_dtau": float(dt[chk].max()) if chk.any() else 0.0,
             "max_dP_common": float(dp.max()) if dp.size else 0.0, "by_type": by_type}
 
 
-def compare_paths_loop(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, strict=()):
+def compare_paths_loop(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, strict=(),
+                       key_tail=0.0):
     """Key-by-key form of compare_paths (same rules, same summary): the
     reference the vectorised harness is tested against on small cases.
 
@@ -252,7 +281,8 @@ def compare_paths_loop(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6,
     unexplained = []
     max_da = max_dtau = 0.0
     per = {t: {"matched": 0, "field_checked": 0, "fragile": 0, "uncertain": 0, "widened_a": 0,
-               "widened_tau": 0, "over_fixed": 0, "da": [], "dtau": []} for t in PATH_TYPES}
+               "widened_tau": 0, "over_fixed": 0, "da": [], "dtau": [], "uda": [], "udt": [],
+               "ta": [], "tt": []} for t in PATH_TYPES}
     common_p_g = np.zeros(osim.rx.shape[0])
     common_p_o = np.zeros(osim.rx.shape[0])
     for key in keys:
@@ -277,6 +307,9 @@ def compare_paths_loop(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6,
                 t["uncertain"] += 1
             elif a_sens[oi] < 0:
                 t["fragile"] += 1
+            if not (certain and a_sens[oi] >= 0):
+                t["uda"].append(abs(ag - ao) / max(abs(ao), 1e-300))
+                t["udt"].append(abs(float(gp["tau"][gi]) - O["tau"][oi]) / O["tau"][oi])
             if certain and a_sens[oi] >= 0:
                 field_checked += 1
                 t["field_checked"] += 1
@@ -288,6 +321,8 @@ def compare_paths_loop(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6,
                 fixed = name in strict
                 tol_a = a_rtol if fixed else max(a_rtol, 2.0 * a_sens[oi])
                 tol_t = tau_rtol if fixed else max(tau_rtol, 2.0 * tau_sens[oi])
+                t["ta"].append(tol_a)
+                t["tt"].append(tol_t)
                 t["widened_a"] += int(tol_a > a_rtol)
                 t["widened_tau"] += int(tol_t > tau_rtol)
                 t["over_fixed"] += int(da > a_rtol or dt > tau_rtol)
@@ -316,7 +351,8 @@ def compare_paths_loop(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6,
             explained += 1
         else:
             unexplained.append((hex(key[0]), hex(key[1]), g, o, tried[:4]))
-    assert not unexplained, f"{len(unexplained)} unexplained path mismatches, e.g. {unexplained[:5]}"
+    assert len(unexplained) <= key_tail * len(keys), \
+        f"{len(unexplained)} unexplained path mismatches, e.g. {unexplained[:5]}"
     m = common_p_o > 0
     dp = np.abs(common_p_g[m] - common_p_o[m]) / common_p_o[m]
     by_type = {}
@@ -324,12 +360,20 @@ def compare_paths_loop(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6,
         if not t["matched"]:
             continue
         da, dt = np.asarray(t.pop("da")), np.asarray(t.pop("dtau"))
+        uda, udt = np.asarray(t.pop("uda")), np.asarray(t.pop("udt"))
+        ta, tt = np.asarray(t.pop("ta")), np.asarray(t.pop("tt"))
+        t["unchecked_max_da"] = float(uda.max()) if uda.size else 0.0
+        t["unchecked_p50_da"] = float(np.median(uda)) if uda.size else 0.0
+        t["unchecked_max_dtau"] = float(udt.max()) if udt.size else 0.0
+        t["max_tol_a"] = float(ta.max()) if ta.size else 0.0
+        t["max_tol_tau"] = float(tt.max()) if tt.size else 0.0
         t["max_da"] = float(da.max()) if da.size else 0.0
         t["p99_da"] = float(np.quantile(da, 0.99)) if da.size else 0.0
         t["max_dtau"] = float(dt.max()) if dt.size else 0.0
         t["p99_dtau"] = float(np.quantile(dt, 0.99)) if dt.size else 0.0
         by_type[name] = t
     return {"keys": len(keys), "matched": matched, "explained": explained,
+            "unexplained": len(unexplained), "unexplained_examples": unexplained[:5],
             "fragile": int((a_sens < 0).sum()),
             "field_checked": field_checked, "max_da": max_da, "max_dtau": max_dtau,
             "max_dP_common": float(dp.max()) if dp.size else 0.0, "by_type": by_type}

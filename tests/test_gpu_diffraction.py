@@ -73,7 +73,7 @@ def test_room_wedges_match_oracle(ctx, room, room_orc, room_edges, pol):
     osim = oracle.OracleSim(room_orc, room.tx, RX4, oracle.SimParams(delta=1e-5 * room.diag, **kp),
                             edges=room_edges)
     gp = res.paths()
-    s = compare_paths(gp, osim, room.eps_r, room.sigma, room.scat)
+    s = compare_paths(gp, osim, room.eps_r, room.sigma, room.scat, strict=("los", "specular", "diffracted"))
     nd = _check_diffracted(gp, osim)
     print("room wedges, pol", pol, s, "diffracted compared", nd,
           "casts", res.counts()[1]["diffraction_casts"])
@@ -98,7 +98,7 @@ def test_office_box_edges_match_oracle(office):
                             oracle.SimParams(delta=1e-5 * office.diag, **kp),
                             ray_ids=ids.astype(np.int64), edges=edges)
     gp = res.paths()
-    s = compare_paths(gp, osim, office.eps_r, office.sigma, office.scat)
+    s = compare_paths(gp, osim, office.eps_r, office.sigma, office.scat, strict=("los", "specular", "diffracted"))
     nd = _check_diffracted(gp, osim)
     n_g, n_o = int((gp["type"] == 2).sum()), int((osim.paths()["type"] == 2).sum())
     print("office box edges:", s, "diffracted gpu", n_g, "oracle", n_o, "compared", nd)

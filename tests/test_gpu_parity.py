@@ -86,14 +86,15 @@ def test_room_sphere_capture(room, room_gpu, room_orc):
     assert h["mismatch"] == 0, h
     assert h["checked"] > 20000
     assert h["max_dq"] < delta
-    s = compare_paths(res.paths(), osim, room.eps_r, room.sigma, room.scat)
+    s = compare_paths(res.paths(), osim, room.eps_r, room.sigma, room.scat,
+                      strict=("los", "specular"))
     assert s["matched"] >= 1
 
 
 def test_room_visibility_capture(room, room_gpu, room_orc):
     """Room scene through the visibility-matrix capture with diffuse last
     interactions: exercises vis, dedup, diffuse validation and refinement."""
-    kp = _room_params(capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=4000)
+    kp = _room_params(capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=4000, rep_tries=0)
     res = room_gpu.trace(room.tx, room.rx, nrt.default_trace_params(**kp))
     delta = 1e-5 * room.diag
     osim = oracle.OracleSim(room_orc, room.tx, room.rx,
@@ -113,15 +114,22 @@ def test_room_visibility_capture(room, room_gpu, room_orc):
     sel = ~amb
     assert sel.sum() > 100
     assert np.array_equal(gvis[j[sel], g_of_o[d[sel]]], bit[sel])
-    s = compare_paths(res.paths(), osim, room.eps_r, room.sigma, room.scat)
+    s = compare_paths(res.paths(), osim, room.eps_r, room.sigma, room.scat,
+                      strict=("los", "specular"))
     assert s["matched"] > 100, s
 
 
-def test_office_subset_full_pipeline(office, office_gpu, office_orc):
+@pytest.mark.parametrize("rep_tries", [0, 8])
+def test_office_subset_full_pipeline(office, office_gpu, office_orc, rep_tries):
     """Office scene (2M points), 16 RX, 5 interactions, visibility capture,
-    diffuse on, on a 4,000-ray sample of the 1M Fibonacci launch."""
+    diffuse on, on a 4,000-ray sample of the 1M Fibonacci launch; every
+    candidate of a key refined (the paper's rule) and, for the cap, at most
+    8.  LOS and specular paths (refined on planes) are held to the fixed
+    tolerances; diffuse paths (their geometry is the traced trajectory's) to
+    the fixed ones widened by the oracle's shadow sensitivity."""
     ids = np.arange(0, 1_000_000, 250, dtype=np.uint32)
-    kp = dict(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1_000_000, rep_tries=8)
+    kp = dict(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1_000_000,
+              rep_tries=rep_tries)
     res = office_gpu.trace(office.tx, office.rx, nrt.default_trace_params(**kp), ray_subset=ids)
     delta = 1e-5 * office.diag
     osim = oracle.OracleSim(office_orc, office.tx, office.rx,
@@ -130,7 +138,8 @@ def test_office_subset_full_pipeline(office, office_gpu, office_orc):
     print("office subset hits:", h)
     assert h["mismatch"] == 0, h
     assert h["max_dq"] < delta, h
-    s = compare_paths(res.paths(), osim, office.eps_r, office.sigma, office.scat)
+    s = compare_paths(res.paths(), osim, office.eps_r, office.sigma, office.scat,
+                      strict=("los", "specular"))
     print("office subset:", h, s)
     assert s["matched"] > 0.8 * s["keys"], s
     assert s["max_dP_common"] < 1e-4
@@ -139,7 +148,7 @@ def test_office_subset_full_pipeline(office, office_gpu, office_orc):
 def test_office_full_launch_sampled_rays(office, office_gpu, office_orc):
     """The full 1M-ray launch (the benchmarked configuration): 1,000 sampled
     rays' hit records against the oracle, and a bit-identical re-run."""
-    kp = dict(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1_000_000, rep_tries=8)
+    kp = dict(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=1_000_000, rep_tries=0)
     p = nrt.default_trace_params(**kp)
     res = office_gpu.trace(office.tx, office.rx, p)
     rng = np.random.default_rng(7)
@@ -176,7 +185,8 @@ def test_room_dps_directed_launch(room, room_gpu, room_orc):
     h = compare_hits(res.hits(), osim.hits(), delta, sens=osim.hit_sens())
     print("room DPS launch hits:", h)
     assert h["mismatch"] == 0, h
-    s = compare_paths(res.paths(), osim, room.eps_r, room.sigma, room.scat)
+    s = compare_paths(res.paths(), osim, room.eps_r, room.sigma, room.scat,
+                      strict=("los", "specular"))
     print("room DPS launch paths:", s)
     assert s["matched"] > 100, s
 
@@ -196,6 +206,7 @@ def test_office_dps_directed_launch_subset(office, office_gpu, office_orc):
     h = compare_hits(res.hits(), osim.hits(), delta, sens=osim.hit_sens())
     print("office DPS launch hits:", h)
     assert h["mismatch"] == 0, h
-    s = compare_paths(res.paths(), osim, office.eps_r, office.sigma, office.scat)
+    s = compare_paths(res.paths(), osim, office.eps_r, office.sigma, office.scat,
+                      strict=("los", "specular"))
     print("office DPS launch paths:", s)
     assert s["matched"] > 0.8 * s["keys"], s

@@ -382,7 +382,9 @@ def test_refinement_converges_on_a_cylinder():
     normal there.  The point must also lie within 5 cm of the true specular
     point, found here by root finding on the cylinder angle.  Several TX/RX
     placements, and a wide capture sphere whose candidates start several
-    degrees off."""
+    degrees off.  A key must validate within its first 8 candidates (a cap):
+    without a cap every candidate is refined, and some candidate may start
+    within t_a already and prove nothing about the retries."""
     R = 3.0
     na = int(round(2 * np.pi * R / 0.02))
     th = np.arange(na) * (2 * np.pi / na)
@@ -401,7 +403,8 @@ def test_refinement_converges_on_a_cylinder():
 
     for a_tx, d_tx, a_rx, d_rx in [(0.2, 1.2, 1.3, 1.6), (3.5, 2.5, 4.3, 1.0), (2.0, 1.0, 2.5, 2.5)]:
         tx, rx = at(a_tx, d_tx), at(a_rx, d_rx)
-        p = oracle.SimParams(max_depth=1, capture=0, diffuse=0, n_rays=200000, r_rx=0.4)
+        p = oracle.SimParams(max_depth=1, capture=0, diffuse=0, n_rays=200000, r_rx=0.4,
+                             rep_tries=8)
         P = oracle.OracleSim(osc, tx, rx[None], p).paths()
         spec = (P["type"] == 0) & (P["k"] == 1)
         assert spec.sum() == 1, (a_tx, a_rx)

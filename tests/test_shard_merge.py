@@ -62,7 +62,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-@pytest.mark.parametrize("rep_tries", [2, 8])
+@pytest.mark.parametrize("rep_tries", [2, 0])
 def test_two_rank_merge_equals_single_run(rep_tries):
     n_rays = 30000
     ctx = mp.get_context("spawn")
