@@ -14,9 +14,10 @@ value     = ray segments cast per second (trace segments + visibility casts +
 ms_per_step = device time of one simulation.
 e2e       = the same metric through the C ABI with host buffers: TX/RX copied
             in, all paths and the per-RX power read back, every step.
-roofline  = the dominant work, the validation phase: algorithmic bytes of its
-            casts (oracle-counted disc reads per diffuse shadow cast; the
-            trace-segment figure for specular validation legs, tests/golden)
+roofline  = the dominant work, the validation phase (every candidate of a key
+            refined, the paper's rule): algorithmic bytes of its casts
+            (oracle-counted disc reads per diffuse shadow cast; the
+            trace-segment figure for specular refinement legs, tests/golden)
             over its CUDA-event duration, against the measured HBM copy
             bandwidth; roofline_other: the trace and visibility kernels.
 
@@ -647,9 +648,9 @@ def ours(args):
     n_spec = counts["validation_casts"] - n_diff
     per_val = ((n_diff * ab["bytes_per_shadow_cast"] + n_spec * ab["bytes_per_segment"])
                / max(counts["validation_casts"], 1))
-    roof = roof_entry("validation phase: validate_specular_kernel + validate_diffuse_kernel "
-                      "(one launch each)", counts["validation_casts"], per_val, ph["validate"],
-                      "validation cast", "validation")
+    roof = roof_entry("validation phase: validate_specular_items_kernel + spec_finish_kernel + "
+                      "validate_diffuse_kernel (one launch each)", counts["validation_casts"], per_val,
+                      ph["validate"], "validation cast", "validation")
     tr_ms = float(np.mean(trace_ms))
     roof_more = [
         roof_entry("trace_kernel", counts["segments"], ab["bytes_per_segment"], tr_ms,

@@ -127,6 +127,9 @@ typedef struct {
   int64_t pruned_legs;       /* specular refinement legs ended without a cast: the
                                 leg's ray cannot enter the box of the key's surface
                                 label there, so its closest hit is another surface */
+  int64_t spec_items;        /* specular (key, candidate) pairs refined (Sec. II-B-2) */
+  int64_t spec_ended_without_cast;  /* of which ended before any cast */
+  int64_t spec_ended_at_first_leg;  /* of which ended at the first leg's cast */
   int64_t reserved[1];
 } nrt_counters;
 

@@ -6,6 +6,7 @@
 
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "../../include/nrt.h"
 #include "nrt_device.cuh"
@@ -136,6 +137,9 @@ enum Ctr : int {
   kCtrDfrCasts,  // edge visibility casts (diffraction)
   kCtrRayFetch,  // trace: rays handed out to lanes
   kCtrPrunedLegs,  // specular refinement legs ended by the label-box test
+  kCtrSpecItems,   // specular (key, candidate) items refined
+  kCtrSpecNoCast,  // of which ended before any cast (side check, label box)
+  kCtrSpecLeg1,    // of which ended at the first leg's cast
   kCtrCount
 };
 

@@ -1073,11 +1073,16 @@ __global__ void __launch_bounds__(kTraceThreads, 6)
 // Coordinates are taken relative to the RX to keep float magnitudes small.
 // Returns whether the candidate validates; with P, its path record.  Used by
 // the item pass and by the per-key finish, so both take the same decisions.
+// stage at which a candidate ended (counters): before any cast, at its
+// first leg's cast, later (or valid)
+enum : int { kSpecNoCast = 0, kSpecLeg1 = 1, kSpecLater = 2 };
+
 __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimConst& C,
                                                const ValArgs& A, uint64_t hi, uint64_t lo,
                                                uint32_t row, int* my_stk, float* my_tstk,
                                                uint32_t* err, unsigned long long& casts,
-                                               unsigned long long& pruned, PathRec* P) {
+                                               unsigned long long& pruned, PathRec* P,
+                                               int* stage = nullptr) {
   const int j = (int)(hi >> 56);
   const int k = (int)((hi >> 52) & 7);
   const float3 rxp = xyz(A.rx[C.batch ? 0 : j]);
@@ -1094,6 +1099,8 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
   float3 I[kMaxDepth + 2];
   uint32_t vmats[kMaxDepth];
   int prev_dps = -1;
+  const unsigned long long casts0 = casts;
+  if (stage) *stage = kSpecNoCast;
   for (int attempt = 0;; ++attempt) {
     float3 img[kMaxDepth + 1];
     img[0] = txl;
@@ -1131,7 +1138,9 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
       const Hit h = cast_ray<false>(S, org, dir, prev_dps, C.t_min, __int_as_float(0x7f800000),
                                     true, my_stk, my_tstk, kTraceThreads, err);
       ++casts;
+      if (stage) *stage = casts - casts0 == 1 ? kSpecLeg1 : kSpecLater;
       if (h.idx < 0 || (h.labels & 0xFFFFu) != lab[m - 1]) return false;
+      if (stage) *stage = kSpecLater;
       const float3 qh = (org + h.tbar * dir) - rxp;
       const float c = fminf(1.0f, fabsf(dot3(Pn[m - 1], h.n)));
       const float dist = fabsf(dot3(qh - I[m], Pn[m - 1]));
@@ -1158,6 +1167,7 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
   const Hit hf = cast_ray<true>(S, I[k] + rxp, (1.0f / sl) * last, prev_dps, C.t_min, sl, false,
                                 my_stk, my_tstk, kTraceThreads, err);
   ++casts;
+  if (stage) *stage = kSpecLater;
   if (hf.idx >= 0) return false;
   if (P) {
     memset(P, 0, sizeof(*P));
@@ -1239,7 +1249,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6)
                                    uint32_t* __restrict__ best, unsigned long long* __restrict__ fetch,
                                    unsigned long long* ctr) {
   NRT_STACK_DECL
-  unsigned long long casts = 0, pruned = 0;
+  unsigned long long casts = 0, pruned = 0, evaluated = 0, no_cast = 0, at_leg1 = 0;
   const int64_t n_items = (int64_t)*n_items_p;
   const uint64_t row_mask = (1ull << A.SC.row_bits) - 1ull;
   for (;;) {
@@ -1258,11 +1268,18 @@ __global__ void __launch_bounds__(kTraceThreads, 6)
     NRT_GUARD(slot < g_dbg_caps.table, 10, slot)
     const uint64_t hi = A.T.b[slot].hi, lo = A.T.b[slot].lo;
     NRT_GUARD(((hi >> 52) & 7) >= 1 && ((hi >> 52) & 7) <= (uint64_t)C.max_depth, 12, hi >> 52)
-    if (spec_candidate(S, C, A, hi, lo, row, my_stk, my_tstk, err, casts, pruned, nullptr))
+    int stage = kSpecLater;
+    ++evaluated;
+    if (spec_candidate(S, C, A, hi, lo, row, my_stk, my_tstk, err, casts, pruned, nullptr, &stage))
       atomicMin(best + kid, rank);
+    no_cast += stage == kSpecNoCast;
+    at_leg1 += stage == kSpecLeg1;
   }
   count_add(ctr + kCtrValCasts, casts);
   count_add(ctr + kCtrPrunedLegs, pruned);
+  count_add(ctr + kCtrSpecItems, evaluated);
+  count_add(ctr + kCtrSpecNoCast, no_cast);
+  count_add(ctr + kCtrSpecLeg1, at_leg1);
 }
 
 // Per specular key: the lowest valid rank is the representative (its path
@@ -2314,6 +2331,9 @@ nrt_status finish_result(nrt_result* r) {
   c.diffuse_casts = (int64_t)hc[kCtrDiffCasts];
   c.diffraction_casts = (int64_t)hc[kCtrDfrCasts];
   c.pruned_legs = (int64_t)hc[kCtrPrunedLegs];
+  c.spec_items = (int64_t)hc[kCtrSpecItems];
+  c.spec_ended_without_cast = (int64_t)hc[kCtrSpecNoCast];
+  c.spec_ended_at_first_leg = (int64_t)hc[kCtrSpecLeg1];
   if (c.error_flags & (kErrHashFull | kErrCandFull | kErrPathFull | kErrKeyFull)) {
     ctx->last_error = "device buffer overflow (flags " +
                       std::to_string(c.error_flags) + ")";

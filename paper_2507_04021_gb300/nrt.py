@@ -60,7 +60,8 @@ class Counters(C.Structure):
     _fields_ = [(n, C.c_int64) for n in (
         "rays", "segments", "vis_casts", "los_casts", "validation_casts", "candidates", "keys",
         "paths", "n_dps", "hash_probes_max", "error_flags", "kernel_launches", "diffuse_casts",
-        "diffraction_casts", "pruned_legs")] + [("reserved", C.c_int64 * 1)]
+        "diffraction_casts", "pruned_legs", "spec_items", "spec_ended_without_cast",
+        "spec_ended_at_first_leg")] + [("reserved", C.c_int64 * 1)]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_ if n != "reserved"}

@@ -120,7 +120,7 @@ def _key16(hi, lo):
 
 
 def compare_paths(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, strict=(),
-                  key_tail=0.0):
+                  key_tail=0.0, path_tail=0.0):
     """gp: GPU paths dict; osim: OracleSim.  Returns a summary; raises on an
     unexplained mismatch or an out-of-tolerance matched path.
 
@@ -135,7 +135,11 @@ def compare_paths(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, stri
     Vectorised over the paths, so a full-size launch (millions of paths)
     compares in seconds; only the mismatched keys are walked one by one.
     key_tail: the fraction of keys that may differ without an oracle-marked
-    ambiguity (0 = none; the count is reported as "unexplained")."""
+    ambiguity (0 = none; the count is reported as "unexplained").
+    path_tail: for the types not held strict, the fraction of field-checked
+    paths that may exceed their (widened) tolerance -- counted per type as
+    "out_of_tol" with the largest error-to-tolerance ratios; strict types
+    may have none."""
     NONE = 0xFFFFFFFF
     O = osim.paths()
     a_o, _ = osim.field(eps_r, sigma, scat)
@@ -166,7 +170,12 @@ def compare_paths(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, stri
     strict_t = np.array([PATH_TYPES[t] in strict for t in types], bool)
     tol_a = np.where(strict_t, a_rtol, np.maximum(a_rtol, 2.0 * a_sens[om]))
     tol_t = np.where(strict_t, tau_rtol, np.maximum(tau_rtol, 2.0 * tau_sens[om]))
-    bad = chk & ((da > tol_a) | (dt > tol_t))
+    out = chk & ((da > tol_a) | (dt > tol_t))
+    bad = out & strict_t
+    for ti in range(len(PATH_TYPES)):
+        m_t = (types == ti) & ~strict_t
+        if (out & m_t).sum() > path_tail * max(int((chk & m_t).sum()), 1):
+            bad |= out & m_t
     if bad.any():
         w = int(np.nonzero(bad)[0][0])
         raise AssertionError(f"{PATH_TYPES[types[w]]} path ({hex(int(O['hi'][om[w]]))}, "
@@ -183,7 +192,12 @@ def compare_paths(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, stri
             continue
         c = chk & m
         u = m & ~chk  # matched but not asserted (uncertain or fragile): raw errors reported
+        ra = da[c] / tol_a[c] if c.any() else np.zeros(0)
+        rt = dt[c] / tol_t[c] if c.any() else np.zeros(0)
         by_type[name] = {
+            "out_of_tol": int((out & m).sum()),
+            "max_ratio_a": float(ra.max()) if ra.size else 0.0,
+            "max_ratio_tau": float(rt.max()) if rt.size else 0.0,
             "unchecked_max_da": float(da[u].max()) if u.any() else 0.0,
             "unchecked_p50_da": float(np.median(da[u])) if u.any() else 0.0,
             "unchecked_max_dtau": float(dt[u].max()) if u.any() else 0.0,
@@ -253,7 +267,7 @@ def compare_paths(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, stri
 
 
 def compare_paths_loop(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6, strict=(),
-                       key_tail=0.0):
+                       key_tail=0.0, path_tail=0.0):
     """Key-by-key form of compare_paths (same rules, same summary): the
     reference the vectorised harness is tested against on small cases.
 
@@ -282,7 +296,7 @@ def compare_paths_loop(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6,
     max_da = max_dtau = 0.0
     per = {t: {"matched": 0, "field_checked": 0, "fragile": 0, "uncertain": 0, "widened_a": 0,
                "widened_tau": 0, "over_fixed": 0, "da": [], "dtau": [], "uda": [], "udt": [],
-               "ta": [], "tt": []} for t in PATH_TYPES}
+               "ta": [], "tt": [], "out_of_tol": 0, "out": []} for t in PATH_TYPES}
     common_p_g = np.zeros(osim.rx.shape[0])
     common_p_o = np.zeros(osim.rx.shape[0])
     for key in keys:
@@ -328,8 +342,10 @@ def compare_paths_loop(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6,
                 t["over_fixed"] += int(da > a_rtol or dt > tau_rtol)
                 max_da = max(max_da, da)
                 max_dtau = max(max_dtau, dt)
-                assert da <= tol_a, f"{name} path {key}: a rel error {da} (tol {tol_a})"
-                assert dt <= tol_t, f"{name} path {key}: tau rel error {dt} (tol {tol_t})"
+                if da > tol_a or dt > tol_t:
+                    t["out_of_tol"] += 1
+                    t["out"].append((fixed, f"{name} path {key}: a rel error {da} (tol {tol_a}), "
+                                            f"tau rel error {dt} (tol {tol_t})"))
             continue
         info = omap.get(key)
         tried = info["tried"] if info else []
@@ -351,6 +367,11 @@ def compare_paths_loop(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6,
             explained += 1
         else:
             unexplained.append((hex(key[0]), hex(key[1]), g, o, tried[:4]))
+    for t in per.values():
+        outs = t.pop("out")
+        strict_out = [msg for fixed, msg in outs if fixed]
+        assert not strict_out, strict_out[0]
+        assert len(outs) <= path_tail * max(t["field_checked"], 1), outs[0][1]
     assert len(unexplained) <= key_tail * len(keys), \
         f"{len(unexplained)} unexplained path mismatches, e.g. {unexplained[:5]}"
     m = common_p_o > 0
@@ -367,6 +388,8 @@ def compare_paths_loop(gp, osim, eps_r, sigma, scat, a_rtol=1e-4, tau_rtol=1e-6,
         t["unchecked_max_dtau"] = float(udt.max()) if udt.size else 0.0
         t["max_tol_a"] = float(ta.max()) if ta.size else 0.0
         t["max_tol_tau"] = float(tt.max()) if tt.size else 0.0
+        t["max_ratio_a"] = float((da / ta).max()) if da.size else 0.0
+        t["max_ratio_tau"] = float((dt / tt).max()) if dt.size else 0.0
         t["max_da"] = float(da.max()) if da.size else 0.0
         t["p99_da"] = float(np.quantile(da, 0.99)) if da.size else 0.0
         t["max_dtau"] = float(dt.max()) if dt.size else 0.0

@@ -37,10 +37,10 @@ def test_office_full_launch_against_oracle(office):
     h = compare_hits(res.hits(), osim.hits(), delta, sens=osim.hit_sens(), normal_tail=1e-5,
                      index_tail=1e-6)
     print("full launch hits:", h)
-    assert h["checked"] > 3_000_000
+    assert h["checked"] > 2_000_000
     gp = res.paths()
     s = compare_paths(gp, osim, office.eps_r, office.sigma, office.scat,
-                      strict=("los", "specular"), key_tail=1e-6)
+                      strict=("los", "specular"), key_tail=1e-6, path_tail=1e-4)
     print("full launch paths:", json.dumps(s))
     K = osim.keys()
     n_keys_o = len(K["hi"])
