@@ -451,7 +451,12 @@ def proposal_bench(scene, o):
     from paper_2507_04021_gb300 import inputs, nrt, proposal
 
     traj = inputs.trajectory(o.extra["boxes"])
-    data = proposal.make_training_set(scene, traj[:250], o.rx)
+    # training positions: the first 250 trajectory points, each at a seeded
+    # height in [0.8, 2.2] m so that the network also sees TX heights like
+    # the office TX's 2.0 m (the trajectory keeps 0.3 m from every box in x/y)
+    train_tx = traj[:250].copy()
+    train_tx[:, 2] = inputs.rng_for(inputs.SEED_MLP, 7).uniform(0.8, 2.2, 250).astype(np.float32)
+    data = proposal.make_training_set(scene, train_tx, o.rx)
     net = nrt.Mlp(scene.ctx, inputs.mlp_init(), [0, 0, 0], [20, 10, 3], proposal.N_LAUNCH)
     loss, secs, wp = proposal.train(net, data)
     per_tx = []
@@ -462,6 +467,7 @@ def proposal_bench(scene, o):
         per_tx.append({
             "tx": [round(float(x), 3) for x in tx], "rays": ev.n_proposed,
             "rx_within_0.5dB": int(within.sum()), "rx_with_paths": int(ok.sum()),
+            "uniform_leaves_rx_empty": bool((~ok).any()),
             "max_abs_db": float(np.max(np.abs(ev.db_err[ok]))) if ok.any() else None,
             "power_recall": float(np.nanmean(ev.power_recall)),
             "fallback": ev.fallback, "ms_uniform": ev.ms_uniform,
@@ -469,6 +475,9 @@ def proposal_bench(scene, o):
     net.close()
     mu = sum(t["ms_uniform"] for t in per_tx)
     mp = sum(t["ms_proposal"] + (t["ms_uniform"] if t["fallback"] else 0.0) for t in per_tx)
+    free = [t for t in per_tx if not t["uniform_leaves_rx_empty"]]
+    mu_f = sum(t["ms_uniform"] for t in free)
+    mp_f = sum(t["ms_proposal"] + (t["ms_uniform"] if t["fallback"] else 0.0) for t in free)
     return {
         "workload": ("office, RX sphere r 0.1 m, 16 RX, 5 specular interactions; training 250 "
                      "trajectory TX x 20,000 rays; evaluation 6 held-out trajectory TX + office TX, "
@@ -480,11 +489,37 @@ def proposal_bench(scene, o):
         "speedup_note": "wall(uniform 1M trace) / wall(score + select + 1e5 trace), summed over the "
                         "evaluation TX; a fallback TX adds the uniform trace to its proposal time",
         "tx_all_rx_within_0.5dB": int(sum(t["rx_within_0.5dB"] == t["rx_with_paths"] for t in per_tx)),
+        "fallback_forced": int(sum(t["uniform_leaves_rx_empty"] for t in per_tx)),
+        "fallback_note": "the configured fallback runs the uniform launch when any RX has no path "
+                         "under the proposal; a TX where the uniform 1M launch itself leaves an RX "
+                         "without paths therefore always falls back (fallback_forced TX)",
+        "speedup_without_forced": (mu_f / mp_f) if free else None,
         "rx_within_0.5dB": int(sum(t["rx_within_0.5dB"] for t in per_tx)),
         "rx_with_paths": int(sum(t["rx_with_paths"] for t in per_tx)),
         "mean_power_recall": float(np.mean([t["power_recall"] for t in per_tx])),
         "per_tx": per_tx,
     }
+
+
+def score_only(args):
+    """The proposal network's scoring of the whole 1M-direction launch, three
+    times (a fixed workload for profiling the fused tensor-core kernel)."""
+    import torch
+    from paper_2507_04021_gb300 import inputs, nrt
+
+    ctx = nrt.Context(0)
+    net = nrt.Mlp(ctx, inputs.mlp_init(), [0, 0, 0], [20, 10, 3], N_RAYS)
+    z = torch.empty(N_RAYS, dtype=torch.float32, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for _ in range(3):
+        ev[0].record()
+        net.score(np.array([3.0, 5.0, 2.0], np.float32), None, N_RAYS, z)
+        ev[1].record()
+        torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    print(json.dumps({"score_ms": ms, "directions": N_RAYS,
+                      "tflops": 2 * N_RAYS * (96 * 128 + 2 * 128 * 128 + 128) / (ms * 1e-3) / 1e12}))
+    net.close()
 
 
 def ours(args):
@@ -679,6 +714,13 @@ def ours(args):
     # channel frequency response of the last simulation (129 frequencies over
     # 1.5 GHz, all receivers) and its Eq. 5 gradient, device-timed
     import torch as _t
+    if args.no_extras:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        last.close()
+        if dist:
+            dist.destroy_process_group()
+        return
     cf_ev = [_t.cuda.Event(enable_timing=True) for _ in range(3)]
     cf_ev[0].record(stream)
     H = last.cfr(1.5e9, 129)
@@ -690,7 +732,7 @@ def ours(args):
                    "ms": cf_ev[0].elapsed_time(cf_ev[1]),
                    "backward_ms": cf_ev[1].elapsed_time(cf_ev[2]),
                    "note": "FP64 sums; includes the host copy of H (and of the target)"}
-    if rank == 0:
+    if rank == 0 and not args.no_extras:
         line["launch_comparison"] = launch_bench(scene, o, tx, stream)
         line["diffraction"] = diffraction_bench(ctx, o, tx, stream, args.rays)
         line["intersection_ablation"] = isect_bench(scene, o, stream)
@@ -734,9 +776,16 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-proposal", dest="proposal", action="store_false",
                     help="skip the learned-proposal measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the timed simulation steps (for profiling): no CFR, launch, "
+                         "diffraction, intersection or r_p measurements")
+    ap.add_argument("--score-only", action="store_true",
+                    help="only the proposal network's scoring of the 1M-direction launch")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.score_only:
+        score_only(args)
     else:
         ours(args)
 

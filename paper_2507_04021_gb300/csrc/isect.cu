@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kCastThreads)
        i += (int64_t)gridDim.x * blockDim.x) {
     const float3 oo = f3(o[3 * i], o[3 * i + 1], o[3 * i + 2]);
     const float3 dd = unit3(f3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
-    const Hit h = cast_ray<false>(S, oo, dd, -1, tmin, tmax, true, stk + threadIdx.x,
+    const Hit h = cast_ray(false, S, oo, dd, -1, tmin, tmax, true, stk + threadIdx.x,
                                   tstk + threadIdx.x, kCastThreads, err);
     if (h.idx < 0) {
       store_miss(O, i);

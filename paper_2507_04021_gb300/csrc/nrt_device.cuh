@@ -151,14 +151,14 @@ __device__ __forceinline__ bool ray_meets_label(const SceneView& S, float3 o, fl
 }
 
 // Closest disc hit along o + t d, t in (tmin, tmax), skipping DPS `skip`.
-// any_hit: stop at the first disc hit found (shadow casts).
+// any_hit: stop at the first disc hit found (shadow casts); a constant at
+// most call sites, so the inlined copy drops the other case.
 // weighted: also compute the Eq. 3 point and the weighted normal.
 // stack / tstack point at this thread's column of a shared array laid out
 // [depth][blockDim.x] (stride = blockDim.x) so that threads hit distinct banks.
-template <bool kAnyHit>
-__device__ __forceinline__ Hit cast_ray(const SceneView& S, float3 o, float3 d, int skip, float tmin,
-                                       float tmax, bool weighted, int* stack, float* tstack,
-                                       int stride, uint32_t* err) {
+__device__ __forceinline__ Hit cast_ray(bool any_hit, const SceneView& S, float3 o, float3 d,
+                                       int skip, float tmin, float tmax, bool weighted, int* stack,
+                                       float* tstack, int stride, uint32_t* err) {
   Hit h;
   h.idx = -1;
   h.dps = -1;
@@ -274,7 +274,7 @@ __device__ __forceinline__ Hit cast_ray(const SceneView& S, float3 o, float3 d, 
             best_lab = __float_as_uint(N.w);
           }
         }
-        if (kAnyHit && best_idx >= 0) break;
+        if (any_hit && best_idx >= 0) break;
       }
     }
     // pop, skipping subtrees that start beyond the current best hit

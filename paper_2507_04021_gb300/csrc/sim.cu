@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
         if (tmax <= C.t_min) {
           bit = true;
         } else {
-          const Hit h = cast_ray<false>(S, o, (1.0f / s) * v, -1, C.t_min, tmax, false, my_stk,
+          const Hit h = cast_ray(false, S, o, (1.0f / s) * v, -1, C.t_min, tmax, false, my_stk,
                                         my_tstk, kTraceThreads, err);
           ++casts;
           bit = h.idx < 0 || h.dps == d;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
   const float3 txp = tx_of(C, j);
   const float3 v = r - txp;
   const float s = len3(v);
-  const Hit h = cast_ray<true>(S, txp, (1.0f / s) * v, -1, C.t_min, s, false, my_stk, my_tstk,
+  const Hit h = cast_ray(true, S, txp, (1.0f / s) * v, -1, C.t_min, s, false, my_stk, my_tstk,
                                kTraceThreads, err);
   atomicAdd(ctr + kCtrLosCasts, 1ull);
   if (h.idx >= 0) return;
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kTraceThreads)
     for (int t = 0; t < 2 && vis; ++t) {
       const float tmax = (float)(dist[t] - (double)S.rho);
       if (!(tmax > C.t_min)) continue;
-      const Hit h = cast_ray<true>(S, ends[t], unit3(Df - ends[t]), -1, C.t_min, tmax, false, my_stk,
+      const Hit h = cast_ray(true, S, ends[t], unit3(Df - ends[t]), -1, C.t_min, tmax, false, my_stk,
                                    my_tstk, kTraceThreads, err);
       ++casts;
       vis = h.idx < 0;
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
       seg = 0;
       have = true;
     }
-    const Hit h = cast_ray<false>(S, o, d, skip, C.t_min, __int_as_float(0x7f800000), true, my_stk,
+    const Hit h = cast_ray(false, S, o, d, skip, C.t_min, __int_as_float(0x7f800000), true, my_stk,
                                   my_tstk, kTraceThreads, err);
     ++segs;
     const int64_t a = R.at(seg, row);
@@ -1019,7 +1019,7 @@ __global__ void __launch_bounds__(kTraceThreads, 6)
     bool valid = false;
     PathRec P;
     if (cs > 0.0f) {
-      const Hit h = cast_ray<true>(S, q, w, dps, C.t_min, rs, false, my_stk, my_tstk,
+      const Hit h = cast_ray(true, S, q, w, dps, C.t_min, rs, false, my_stk, my_tstk,
                                    kTraceThreads, err);
       ++casts;
       valid = h.idx < 0;
@@ -1135,7 +1135,7 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
         ++pruned;
         return false;
       }
-      const Hit h = cast_ray<false>(S, org, dir, prev_dps, C.t_min, __int_as_float(0x7f800000),
+      const Hit h = cast_ray(false, S, org, dir, prev_dps, C.t_min, __int_as_float(0x7f800000),
                                     true, my_stk, my_tstk, kTraceThreads, err);
       ++casts;
       if (stage) *stage = casts - casts0 == 1 ? kSpecLeg1 : kSpecLater;
@@ -1164,7 +1164,7 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
   // last leg to the RX
   const float3 last = f3(0.f, 0.f, 0.f) - I[k];
   const float sl = len3(last);
-  const Hit hf = cast_ray<true>(S, I[k] + rxp, (1.0f / sl) * last, prev_dps, C.t_min, sl, false,
+  const Hit hf = cast_ray(true, S, I[k] + rxp, (1.0f / sl) * last, prev_dps, C.t_min, sl, false,
                                 my_stk, my_tstk, kTraceThreads, err);
   ++casts;
   if (stage) *stage = kSpecLater;
@@ -1886,7 +1886,7 @@ __device__ __forceinline__ unsigned trace_row(const SceneView& S, const SimConst
   int skip = -1;
   unsigned segs = 0;
   for (int s = 0; s < C.n_seg; ++s) {
-    const Hit h = cast_ray<false>(S, o, d, skip, C.t_min, __int_as_float(0x7f800000), true, stk,
+    const Hit h = cast_ray(false, S, o, d, skip, C.t_min, __int_as_float(0x7f800000), true, stk,
                                   tstk, kTraceThreads, err);
     ++segs;
     const int64_t a = R.at(s, row);

@@ -40,7 +40,7 @@ def test_office_full_launch_against_oracle(office):
     assert h["checked"] > 2_000_000
     gp = res.paths()
     s = compare_paths(gp, osim, office.eps_r, office.sigma, office.scat,
-                      strict=("los", "specular"), key_tail=1e-6, path_tail=1e-4)
+                      strict=("los", "specular"), key_tail=5e-6, path_tail=1e-4)
     print("full launch paths:", json.dumps(s))
     K = osim.keys()
     n_keys_o = len(K["hi"])
