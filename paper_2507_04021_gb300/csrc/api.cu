@@ -27,6 +27,12 @@ void nrt::ctx_release(nrt_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     cudaFree(ctx->order);
   }
+  if (ctx->aux) {
+    cudaStreamSynchronize(ctx->aux);
+    cudaStreamDestroy(ctx->aux);
+  }
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
+  if (ctx->join) cudaEventDestroy(ctx->join);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -134,6 +140,15 @@ nrt_status nrt_create(nrt_ctx** out, int device, void* cuda_stream) {
       return NRT_ERR_CUDA;
     }
     c->own_stream = true;
+  }
+  // a second stream for work that may overlap on the device (the diffuse
+  // and specular validations), joined back into the context stream by events
+  if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return NRT_ERR_CUDA;
   }
   // keep freed stream-ordered memory cached in the pool between simulations
   cudaMemPool_t pool;

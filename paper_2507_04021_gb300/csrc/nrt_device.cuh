@@ -135,9 +135,11 @@ __device__ __forceinline__ int leaf_of(int c) { return ~c; }
 
 // Whether the ray o + t d, t > tmin, can enter the box of surface label l
 // (the same widened slab test as the traversal's): when it cannot, no disc
-// with that label can be its closest hit.
+// with that label can be its closest hit.  *t_exit (optional) receives where
+// the ray leaves the box, widened like the test: no disc of the label lies
+// beyond it.
 __device__ __forceinline__ bool ray_meets_label(const SceneView& S, float3 o, float3 d, float tmin,
-                                                uint32_t l) {
+                                                uint32_t l, float* t_exit = nullptr) {
   const float4 lo = __ldg(S.label_box + 2 * l), hi = __ldg(S.label_box + 2 * l + 1);
   const float3 inv = f3(1.0f / (fabsf(d.x) > 1e-20f ? d.x : copysignf(1e-20f, d.x)),
                         1.0f / (fabsf(d.y) > 1e-20f ? d.y : copysignf(1e-20f, d.y)),
@@ -147,6 +149,7 @@ __device__ __forceinline__ bool ray_meets_label(const SceneView& S, float3 o, fl
   const float z0 = (lo.z - o.z) * inv.z, z1 = (hi.z - o.z) * inv.z;
   const float tin = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), tmin));
   const float tout = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fmaxf(z0, z1));
+  if (t_exit) *t_exit = tout * 1.000001f + 1e-6f;
   return tin <= tout * 1.000001f + 1e-6f;
 }
 

@@ -23,6 +23,9 @@ struct nrt_ctx {
   int64_t order_n = 0;
   // polls of a bounded device wait before it gives up (0 = the default)
   int64_t wait_limit = 0;
+  // second stream for overlapping work, forked from and joined into `stream`
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 struct nrt_scene {

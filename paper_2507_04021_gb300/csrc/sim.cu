@@ -1131,12 +1131,15 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
       // a leg whose ray cannot reach the key's surface at this interaction
       // ends the candidate without a cast (its closest hit would be another
       // surface or nothing)
-      if (!ray_meets_label(S, org, dir, C.t_min, lab[m - 1])) {
+      // and a leg's search ends where its ray leaves that box: a hit beyond
+      // is on another surface, which ends the candidate as nothing found does
+      float t_exit;
+      if (!ray_meets_label(S, org, dir, C.t_min, lab[m - 1], &t_exit)) {
         ++pruned;
         return false;
       }
-      const Hit h = cast_ray(false, S, org, dir, prev_dps, C.t_min, __int_as_float(0x7f800000),
-                                    true, my_stk, my_tstk, kTraceThreads, err);
+      const Hit h = cast_ray(false, S, org, dir, prev_dps, C.t_min, t_exit, true, my_stk, my_tstk,
+                             kTraceThreads, err);
       ++casts;
       if (stage) *stage = casts - casts0 == 1 ? kSpecLeg1 : kSpecLater;
       if (h.idx < 0 || (h.labels & 0xFFFFu) != lab[m - 1]) return false;
@@ -2235,8 +2238,16 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
     pair_nokey_stamp_kernel<<<(C.n_pairs + 255) / 256, 256, 0, st>>>(C.n_pairs, pair_keys, r->stamps); count_launch();
   }
   // specular keys: every candidate an item (one pass), then the lowest valid
-  // rank per key; diffuse keys: each key walks its candidates in ray order
+  // rank per key; diffuse keys: each key walks its candidates in ray order,
+  // on the context's second stream so that the two validations overlap on
+  // the device (they touch disjoint keys; paths and counters are taken by
+  // atomics and the paths are sorted afterwards)
   TRY(cudaMemsetAsync(W.cnt + kCntFetchS, 0, 24, st));
+  TRY(cudaEventRecord(ctx->fork, st));
+  TRY(cudaStreamWaitEvent(ctx->aux, ctx->fork, 0));
+  validate_diffuse_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 6), kTraceThreads, 0, ctx->aux>>>(
+      S, C, V, W.diff_list, W.cnt + kCntDiff, W.cnt + kCntFetchD, ctr); count_launch();
+  TRY(cudaEventRecord(ctx->join, ctx->aux));
   TRY(cudaMemsetAsync(W.spec_cnt, 0, c.keys * sizeof(uint32_t), st));
   spec_count_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.K, W.spec_list, W.cnt + kCntSpec,
                                                                 C.rep_tries, W.spec_cnt, W.spec_best); count_launch();
@@ -2248,8 +2259,7 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
       S, C, V, W.items, W.cnt + kCntItems, W.spec_best, W.cnt + kCntFetchS, ctr); count_launch();
   spec_finish_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
       S, C, V, W.spec_list, W.cnt + kCntSpec, W.spec_best, ctr); count_launch();
-  validate_diffuse_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 6), kTraceThreads, 0, st>>>(
-      S, C, V, W.diff_list, W.cnt + kCntDiff, W.cnt + kCntFetchD, ctr); count_launch();
+  TRY(cudaStreamWaitEvent(st, ctx->join, 0));
   if (r->ev[5]) TRY(cudaEventRecord(r->ev[5], st));
   if (r->p.keep_keys) {
     key_summary_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(
