@@ -235,6 +235,19 @@ nrt_status nrt_scene_dps_read(const nrt_scene* scene, int32_t* vox, int32_t* cou
 nrt_status nrt_set_materials(nrt_scene* scene, const float* eps_r, const float* sigma,
                              const float* scat, int n_labels);
 
+/* Same materials from DEVICE memory, for a learning loop whose parameters
+ * live on the GPU (Sec. III-B learns eps_r, sigma and S per label by gradient
+ * descent): mat is a device float[3][n_labels] -- eps_r, then sigma, then S,
+ * each n_labels (<= 256) long, read by a kernel enqueued on the context
+ * stream (the call does not synchronise; mat must stay valid until that
+ * kernel has run).  Values cannot be checked on the host without a copy, so
+ * the kernel brings each into its range instead: eps_r = max(eps_r, 1),
+ * sigma = max(sigma, 0), S clamped to [0, 1 - 2^-24]; NaN goes to the lower
+ * bound.  The call makes the context's device current for its launch and
+ * restores the caller's current device.  Errors: NRT_ERR_ARG for NULL mat or
+ * n_labels outside [1, 256]; NRT_ERR_CUDA. */
+nrt_status nrt_set_materials_device(nrt_scene* scene, const float* mat, int n_labels);
+
 /* Edges of the augmented point cloud (Sec. II, used by the diffraction of
  * Sec. II-B-3): host arrays of n_edges entries -- segment ends a, b
  * (float[3] each), the outward unit normals n0, n1 of the two faces meeting
@@ -316,9 +329,12 @@ void nrt_result_free(nrt_result* result);
 nrt_status nrt_result_counts(const nrt_result* result, int64_t* n_paths_per_rx,
                              nrt_counters* counters);
 
-/* Device times of the simulation phases in ms: [0] visibility, [1] LOS,
- * [2] trace, [3] candidates + dedup, [4] validation/refinement, [5] field,
- * [6] total.  Host float[8]. */
+/* Device times of the simulation phases in ms: [0] visibility (with the
+ * launch order and buffer set-up before it), [1] unused (0), [2] trace,
+ * [3] candidates + dedup + LOS, [4] validation/refinement, [5] field,
+ * [6] total, [7] the part of [3] the device spends waiting for the host to
+ * size the candidate and key buffers from the counted candidates (the one
+ * host round trip of a simulation).  Host float[8]. */
 nrt_status nrt_result_times(const nrt_result* result, float* ms);
 
 /* Read all paths into caller-allocated host arrays. */
@@ -346,6 +362,13 @@ nrt_status nrt_field(nrt_result* result);
  * reads the channel from the same per-path coefficients -- see nrt_cfr for
  * the coherent CFR).  Errors: NRT_ERR_STATE before the field was computed. */
 nrt_status nrt_field_read(const nrt_result* result, float* power_per_rx);
+
+/* Received power per RX into DEVICE memory: power is a device double[n_rx]
+ * (the FP64 sums of nrt_field_read before their rounding to float), copied
+ * on the context stream without synchronising, so that a learning loop
+ * (Sec. III-B) can form its loss on the GPU.  Errors: NRT_ERR_ARG for NULL;
+ * NRT_ERR_STATE before the field was computed; NRT_ERR_CUDA. */
+nrt_status nrt_field_read_device(const nrt_result* result, double* power);
 
 /* Adjoint of the received power (the differentiable electromagnetic
  * computation used to learn per-label relative permittivity, conductivity and

@@ -69,6 +69,24 @@ __global__ void subset_check_kernel(const uint64_t* __restrict__ ids, int64_t n,
   }
 }
 
+// Per-label materials from a device array [3][n_labels] into the scene's
+// [3][256] table, each value brought into its range (eps_r >= 1, sigma >= 0,
+// 0 <= S < 1; NaN goes to the lower bound); labels past n_labels get the
+// host setter's defaults.  One block of 256 threads.
+__global__ void materials_device_kernel(const float* __restrict__ in, int n_labels,
+                                        float* __restrict__ mat) {
+  const int l = threadIdx.x;
+  float e = 1.0f, g = 0.0f, c = 0.0f;
+  if (l < n_labels) {
+    e = fmaxf(in[l], 1.0f);
+    g = fmaxf(in[n_labels + l], 0.0f);
+    c = fminf(fmaxf(in[2 * n_labels + l], 0.0f), 0.99999994f);
+  }
+  mat[l] = e;
+  mat[256 + l] = g;
+  mat[512 + l] = c;
+}
+
 __global__ void widen_kernel(const uint32_t* __restrict__ in, int64_t n, uint64_t* __restrict__ k,
                              uint32_t* __restrict__ v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -299,6 +317,21 @@ nrt_status nrt_set_materials(nrt_scene* s, const float* eps_r, const float* sigm
   return NRT_OK;
 }
 
+nrt_status nrt_set_materials_device(nrt_scene* s, const float* mat, int n_labels) {
+  if (!s || !mat || n_labels <= 0 || n_labels > 256) return NRT_ERR_ARG;
+  nrt_ctx* ctx = s->ctx;
+  int cur = 0;
+  NRT_CUDA_TRY(ctx, cudaGetDevice(&cur));
+  NRT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  materials_device_kernel<<<1, 256, 0, ctx->stream>>>(mat, n_labels, s->mat);
+  const cudaError_t e = cudaGetLastError();
+  cudaSetDevice(cur);
+  NRT_CUDA_TRY(ctx, e);
+  s->n_labels = n_labels;
+  s->have_materials = true;
+  return NRT_OK;
+}
+
 nrt_status nrt_scene_set_edges(nrt_scene* s, int64_t n_edges, const float* a, const float* b,
                                const float* n0, const float* n1, const uint8_t* m0,
                                const uint8_t* m1) {
@@ -478,6 +511,8 @@ void nrt_result_free(nrt_result* r) {
     if (q) cudaFreeAsync(q, st);
   for (int e = 0; e < 8; ++e)
     if (r->ev[e]) cudaEventDestroy(r->ev[e]);
+  for (int e = 0; e < 2; ++e)
+    if (r->ev_gap[e]) cudaEventDestroy(r->ev_gap[e]);
   delete[] r->rx_count;
   delete[] r->rx_start;
   nrt_scene* s = r->scene;
@@ -515,6 +550,7 @@ nrt_status nrt_result_times(const nrt_result* r, float* ms) {
   ms[5] = el(5, 6);
   ms[6] = el(0, 7);
   ms[7] = 0.0f;
+  if (r->ev_gap[0] && r->ev_gap[1]) cudaEventElapsedTime(&ms[7], r->ev_gap[0], r->ev_gap[1]);
   return NRT_OK;
 }
 
@@ -879,6 +915,18 @@ nrt_status nrt_field_read(const nrt_result* r, float* power) {
                                     ctx->stream));
   NRT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   for (int j = 0; j < r->n_rx; ++j) power[j] = (float)h[j];
+  return NRT_OK;
+}
+
+nrt_status nrt_field_read_device(const nrt_result* r, double* power) {
+  if (!r || !power) return NRT_ERR_ARG;
+  nrt_ctx* ctx = r->scene->ctx;
+  if (!r->field_done) {
+    ctx->last_error = "field not computed (set materials, then nrt_field)";
+    return NRT_ERR_STATE;
+  }
+  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(power, r->power, (size_t)r->n_rx * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, ctx->stream));
   return NRT_OK;
 }
 

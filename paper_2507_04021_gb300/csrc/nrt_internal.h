@@ -110,6 +110,7 @@ struct nrt_result {
   unsigned long long* ctr = nullptr;  // device counters
   nrt_counters counters{};
   cudaEvent_t ev[8] = {};
+  cudaEvent_t ev_gap[2] = {};  // around the host sizing round trip
   bool field_done = false;
   // graph mode: pipeline buffers and the instantiated graph, kept for replays
   void* work = nullptr;

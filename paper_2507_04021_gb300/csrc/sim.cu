@@ -2436,6 +2436,9 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
   unsigned long long cnt2[2] = {0, 0};
   TRY(cudaMemcpyAsync(&cnt2[0], r->ctr + kCtrCands, 8, cudaMemcpyDeviceToHost, st));
   TRY(cudaMemcpyAsync(&cnt2[1], r->ctr + kCtrLeaders, 8, cudaMemcpyDeviceToHost, st));
+  for (int e = 0; e < 2; ++e)
+    if (!r->ev_gap[e]) TRY(cudaEventCreate(&r->ev_gap[e]));
+  TRY(cudaEventRecord(r->ev_gap[0], st));
   TRY(cudaStreamSynchronize(st));
   if (r->p.cand_capacity > 0 && (int64_t)cnt2[0] > r->p.cand_capacity) {
     ctx->last_error = "more path candidates than cand_capacity";
@@ -2465,6 +2468,7 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
   rc = alloc_result(r, c, true);
   if (rc == NRT_OK) rc = alloc_work(ctx, W, c, n, st);
   TRY(dbg_set_caps(c.table, c.keys, c.cand, c.paths, n, r->n_rx, st));
+  TRY(cudaEventRecord(r->ev_gap[1], st));
   if (rc == NRT_OK) rc = enqueue_rest(r, W, S, C, order);
   if (rc != NRT_OK) {
     release_work(W, st);

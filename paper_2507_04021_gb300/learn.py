@@ -71,6 +71,73 @@ class LibnrtBackend:
         return ge, gs, gc
 
 
+class DevicePowerFn(torch.autograd.Function):
+    """The same P[r, j] with every tensor on the GPU: the materials reach the
+    library through nrt_set_materials_device, the power comes back through
+    nrt_field_read_device and dL/dP goes to nrt_backward_noalloc, so a
+    learning step copies nothing through the host.  ``backend`` is a
+    LibnrtDeviceBackend."""
+
+    @staticmethod
+    def forward(ctx, eps, sig, sca, backend):
+        ctx.backend = backend
+        return backend.forward(eps, sig, sca)
+
+    @staticmethod
+    def backward(ctx, gP):
+        ge, gs, gc = ctx.backend.backward(gP)
+        return ge, gs, gc, None
+
+
+class LibnrtDeviceBackend:
+    """Field and adjoint of stored paths through libnrt with device buffers
+    (one scene, R results with the same receivers; scalar polarisation models
+    without diffraction, the cases nrt_backward_noalloc serves).  The
+    library's work runs on the context stream, ordered after the caller's
+    current stream and before its next work by stream waits."""
+
+    on_device = True
+
+    def __init__(self, scene, results):
+        self.scene = scene
+        self.results = list(results)
+        self.device = torch.device("cuda", scene.ctx.device)
+        self._stream = torch.cuda.ExternalStream(scene.ctx.stream_handle(), device=self.device)
+
+    def _enter(self):
+        cur = torch.cuda.current_stream(self.device)
+        if cur.cuda_stream != self._stream.cuda_stream:
+            self._stream.wait_stream(cur)
+        return cur
+
+    def _leave(self, cur):
+        if cur.cuda_stream != self._stream.cuda_stream:
+            cur.wait_stream(self._stream)
+
+    def forward(self, eps, sig, sca):
+        mat = torch.stack([eps.detach(), sig.detach(), sca.detach()]).to(torch.float32).contiguous()
+        P = torch.empty((len(self.results), self.results[0].n_rx), dtype=torch.float64,
+                        device=self.device)
+        cur = self._enter()
+        self.scene.set_materials_device(mat)
+        for i, r in enumerate(self.results):
+            r.field()
+            r.power_device(P[i])
+        self._leave(cur)
+        return P
+
+    def backward(self, gP):
+        L = self.scene.n_labels
+        g = gP.detach().to(torch.float32).contiguous()
+        grads = torch.empty((len(self.results), 3 * L), dtype=torch.float32, device=self.device)
+        cur = self._enter()
+        for i, r in enumerate(self.results):
+            r.backward_noalloc(g[i], grads[i])
+        self._leave(cur)
+        tot = grads.to(torch.float64).sum(0).view(3, L)
+        return tot[0], tot[1], tot[2]
+
+
 def to_params(eps, sig, sca):
     """Unconstrained parameters (u, v, w) for given materials."""
     eps = np.asarray(eps, np.float64)
@@ -102,14 +169,26 @@ def recover_materials(backend, target_db, init, steps=200, lr=0.05, checkpoint=N
     """Adam on the per-RX dB-gain MSE; target_db [R, M]; init = (eps, sigma, S).
     checkpoint / checkpoint_every: write the optimiser state to that path
     every so many steps (and after the last); resume: continue from such a
-    checkpoint (its steps count toward `steps`)."""
+    checkpoint (its steps count toward `steps`).  A backend with
+    ``on_device`` (LibnrtDeviceBackend) keeps the parameters, the optimiser
+    and the loss on its GPU; the loss history is read back only at
+    checkpoints and at the end."""
+    dev = backend.device if getattr(backend, "on_device", False) else None
+    fn = DevicePowerFn if dev is not None else PowerFn
     u0, v0, w0 = to_params(*init)
-    u = torch.tensor(u0, requires_grad=True)
-    v = torch.tensor(v0, requires_grad=True)
-    w = torch.tensor(w0, requires_grad=True)
-    tgt = torch.as_tensor(np.asarray(target_db, np.float64))
+    u = torch.tensor(u0, requires_grad=True, device=dev)
+    v = torch.tensor(v0, requires_grad=True, device=dev)
+    w = torch.tensor(w0, requires_grad=True, device=dev)
+    tgt = torch.as_tensor(np.asarray(target_db, np.float64), device=dev)
     opt = torch.optim.Adam([u, v, w], lr=lr)
     hist = []
+    pending = []
+
+    def flush():
+        if pending:
+            hist.extend(torch.stack(pending).cpu().tolist())
+            pending.clear()
+
     if resume is not None:
         st = torch.load(resume, weights_only=False)
         with torch.no_grad():
@@ -120,17 +199,19 @@ def recover_materials(backend, target_db, init, steps=200, lr=0.05, checkpoint=N
     for it in range(len(hist), steps):
         opt.zero_grad()
         eps, sig, sca = from_params(u, v, w)
-        P = PowerFn.apply(eps, sig, sca, backend)
+        P = fn.apply(eps, sig, sca, backend)
         G = 10.0 * torch.log10(P)
         loss = torch.mean((G - tgt) ** 2)
         loss.backward()
         opt.step()
-        hist.append(float(loss.detach()))
+        pending.append(loss.detach())
         if checkpoint and ((checkpoint_every and (it + 1) % checkpoint_every == 0) or it + 1 == steps):
+            flush()
             save_checkpoint(checkpoint, (u, v, w), opt, hist)
+    flush()
     with torch.no_grad():
         eps, sig, sca = from_params(u, v, w)
-    return Fit(eps.numpy(), sig.numpy(), sca.numpy(), hist)
+    return Fit(eps.cpu().numpy(), sig.cpu().numpy(), sca.cpu().numpy(), hist)
 
 
 # ---------------------------------------------------------------- Eq. 5 (CIR) loss

@@ -111,6 +111,7 @@ def lib():
         L.nrt_scene_info.argtypes = [_P, _P, _P, _P]
         L.nrt_scene_dps_read.argtypes = [_P, _P, _P, _P]
         L.nrt_set_materials.argtypes = [_P, _P, _P, _P, C.c_int]
+        L.nrt_set_materials_device.argtypes = [_P, _P, C.c_int]
         L.nrt_scene_set_edges.argtypes = [_P, C.c_int64, _P, _P, _P, _P, _P, _P]
         L.nrt_cast.argtypes = [_P, _P, _P, C.c_int64, C.POINTER(CastParams), _P, _P, _P, _P]
         L.nrt_trace.argtypes = [_P, _P, _P, C.c_int, C.POINTER(TraceParams), _P, C.c_int64,
@@ -124,6 +125,7 @@ def lib():
         L.nrt_vis_read.argtypes = [_P, _P]
         L.nrt_field.argtypes = [_P]
         L.nrt_field_read.argtypes = [_P, _P]
+        L.nrt_field_read_device.argtypes = [_P, _P]
         L.nrt_backward.argtypes = [_P, _P, _P, _P, _P]
         L.nrt_backward_noalloc.argtypes = [_P, _P, _P]
         L.nrt_trace_batch.argtypes = [_P, _P, _P, _P, C.c_int, C.POINTER(TraceParams),
@@ -276,6 +278,24 @@ class Scene:
                                                 int(e.shape[0])))
         self.n_labels = int(e.shape[0])
 
+    def set_materials_device(self, mat_dev):
+        """nrt_set_materials_device: mat_dev a contiguous float32 CUDA tensor
+        [3, n_labels] (eps_r, sigma, S rows) on the context's device, read on
+        the context stream; values are clamped into range there."""
+        import torch
+
+        if not (isinstance(mat_dev, torch.Tensor) and mat_dev.is_cuda):
+            raise ValueError("mat_dev must be a CUDA tensor")
+        if mat_dev.device.index != self.ctx.device:
+            raise ValueError(f"mat_dev is on cuda:{mat_dev.device.index}, the context on "
+                             f"cuda:{self.ctx.device}")
+        if mat_dev.dtype != torch.float32 or not mat_dev.is_contiguous() or mat_dev.dim() != 2 \
+                or mat_dev.shape[0] != 3:
+            raise ValueError("mat_dev must be a contiguous float32 [3, n_labels] tensor")
+        self.ctx._check(lib().nrt_set_materials_device(self._h, _P(mat_dev.data_ptr()),
+                                                       int(mat_dev.shape[1])))
+        self.n_labels = int(mat_dev.shape[1])
+
     def set_edges(self, edges):
         """Edges for the diffraction of Sec. II-B-3 (an object with arrays a, b,
         n0, n1 [n, 3] and m0, m1 [n], e.g. inputs.Edges); None clears them."""
@@ -364,7 +384,8 @@ class Result:
         t = np.zeros(8, np.float32)
         self.ctx._check(lib().nrt_result_times(self._h, _np_ptr(t)))
         return {"vis": float(t[0]), "trace": float(t[2]), "dedup": float(t[3]),
-                "validate": float(t[4]), "field": float(t[5]), "total": float(t[6])}
+                "validate": float(t[4]), "field": float(t[5]), "total": float(t[6]),
+                "sizing_wait": float(t[7])}
 
     def paths(self):
         per, c = self.counts()
@@ -403,6 +424,22 @@ class Result:
         p = np.zeros(self.n_rx, np.float32)
         self.ctx._check(lib().nrt_field_read(self._h, _np_ptr(p)))
         return p
+
+    def power_device(self, out_dev):
+        """nrt_field_read_device: per-RX power (float64) into out_dev, a
+        contiguous float64 CUDA tensor of at least n_rx elements on the
+        context's device, copied on the context stream."""
+        import torch
+
+        if not (isinstance(out_dev, torch.Tensor) and out_dev.is_cuda):
+            raise ValueError("out_dev must be a CUDA tensor")
+        if out_dev.device.index != self.ctx.device:
+            raise ValueError(f"out_dev is on cuda:{out_dev.device.index}, the context on "
+                             f"cuda:{self.ctx.device}")
+        if out_dev.dtype != torch.float64 or not out_dev.is_contiguous() \
+                or out_dev.numel() < self.n_rx:
+            raise ValueError(f"out_dev must be contiguous float64 with >= {self.n_rx} elements")
+        self.ctx._check(lib().nrt_field_read_device(self._h, _P(out_dev.data_ptr())))
 
     def backward(self, dL_dP):
         g = np.ascontiguousarray(dL_dP, np.float32)

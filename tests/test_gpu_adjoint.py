@@ -107,11 +107,57 @@ def test_backward_diffuse_office_subset(office, depth):
         assert rel.max() < 1e-3, (name, gi, wi)
 
 
-def test_recover_hidden_materials_on_gpu(office):
+def test_device_power_fn_matches_host_path(room_pair):
+    """The device-resident learning step (materials set from device memory,
+    power read into device memory, adjoint through nrt_backward_noalloc)
+    against the host path (nrt_set_materials, nrt_field_read, nrt_backward):
+    the same power (the host path rounds it to float32) and the same
+    gradient of a loss through torch.autograd."""
+    import torch
+
+    sc, res, _ = room_pair
+    host = learn.LibnrtBackend(sc, [res])
+    dev = learn.LibnrtDeviceBackend(sc, [res])
+    e0, s0, c0 = (torch.tensor(m, dtype=torch.float64) for m in MATS)
+    wts = torch.linspace(0.5, 1.5, len(RX4), dtype=torch.float64)
+
+    def run(fn, backend, device):
+        e, s, c = (t.clone().to(device).requires_grad_(True) for t in (e0, s0, c0))
+        P = fn.apply(e, s, c, backend)
+        (torch.log10(P) * wts.to(device)).sum().backward()
+        return P.detach().cpu().numpy(), [t.grad.cpu().numpy() for t in (e, s, c)]
+
+    Ph, gh = run(learn.PowerFn, host, "cpu")
+    Pd, gd = run(learn.DevicePowerFn, dev, dev.device)
+    print("power rel diff", float(np.max(np.abs(Pd - Ph) / Ph)))
+    assert np.all(Ph > 0)
+    assert np.max(np.abs(Pd - Ph) / Ph) < 1e-6
+    for name, a, b in zip(("eps", "sigma", "S"), gd, gh):
+        rel = np.abs(a - b) / np.maximum(np.abs(b), 1e-6 * np.abs(b).max())
+        print(name, "grad max rel diff", float(rel.max()))
+        assert rel.max() < 1e-4, (name, a, b)
+    # clamping on the device: out-of-range materials land on the bounds
+    mat = torch.tensor([[0.5, 2.0], [-1.0, 0.02], [1.5, -0.1]], dtype=torch.float32,
+                       device=dev.device)
+    sc.set_materials_device(mat)
+    res.field()
+    out = torch.empty(len(RX4), dtype=torch.float64, device=dev.device)
+    res.power_device(out)
+    sc.set_materials(np.array([1.0, 2.0], np.float32), np.array([0.0, 0.02], np.float32),
+                     np.array([0.99999994, 0.0], np.float32))
+    res.field()
+    np.testing.assert_allclose(out.cpu().numpy(), res.power(), rtol=1e-6)
+    sc.set_materials(*(m.astype(np.float32) for m in MATS))
+    res.field()
+
+
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_recover_hidden_materials_on_gpu(office, where):
     """Learning workload: office scene, 8 TX positions x 16 RX, hidden
     materials (seed 3), initial guess eps_r 4, sigma 0.01, S 0.3, 200 Adam
-    steps on the per-RX dB gain MSE.  eps_r and S are recovered within 5%;
-    sigma is weakly observable from power at 28 GHz and only reported."""
+    steps on the per-RX dB gain MSE, through the host path and through the
+    device-resident one.  eps_r and S are recovered within 5%; sigma is
+    weakly observable from power at 28 GHz and only reported."""
     ctx = nrt.Context(0)
     sc = nrt.Scene(ctx, office.pos, office.nrm, office.surf, office.mat, r_p=0.015)
     traj = inputs.trajectory(office.extra["boxes"])
@@ -122,6 +168,8 @@ def test_recover_hidden_materials_on_gpu(office):
     backend = learn.LibnrtBackend(sc, results)
     he, hs, hc = (a.astype(np.float64) for a in inputs.hidden_materials())
     target = 10 * np.log10(backend.forward(he, hs, hc))
+    if where == "device":
+        backend = learn.LibnrtDeviceBackend(sc, results)
     L = len(he)
     fit = learn.recover_materials(backend, target,
                                   (np.full(L, 4.0), np.full(L, 0.01), np.full(L, 0.3)),
