@@ -361,21 +361,34 @@ __global__ void features_kernel(SampleSrc S, int64_t B, int64_t n_rays, bf16* __
 
 // ---------------------------------------------------------------- fused scoring
 // One persistent CTA per SM scores 128-row tiles end to end on the tensor
-// cores: the tile's Fourier features are written straight into the MMA
-// operand layout in shared memory, the three hidden layers run as chained
-// tcgen05.mma into one tensor-memory accumulator (bias, ReLU and the BF16
-// rounding applied by the epilogue, which writes the next layer's operand
-// back to shared memory), and the output layer is folded into the last
-// epilogue: each thread owns one row, so the logit is a per-thread dot product.
-// W1, W2, W3 stay in shared memory for the whole launch.
-constexpr int kScoreThreads = 128;
+// cores: a tile's Fourier features are written straight into the MMA operand
+// layout in shared memory, the three hidden layers run as chained tcgen05.mma
+// into a tensor-memory accumulator (bias, ReLU and the BF16 rounding applied
+// by the epilogue, which writes the next layer's operand back to shared
+// memory), and the output layer is folded into the last epilogue: each thread
+// owns one row, so the logit is a per-thread dot product.  W1, W2, W3 stay in
+// shared memory for the whole launch.
+//
+// The CTA runs kScoreGroups independent groups of 128 threads, each with its
+// own tiles, activation tile, 128 accumulator columns, mbarrier and named
+// barrier; the first thread of a group issues that group's MMAs and commits
+// them to the group's mbarrier (a commit tracks the MMAs its own thread
+// issued).  One tile's feature and epilogue work on the CUDA cores thus
+// overlaps the other groups' MMAs on the tensor core.
+constexpr int kScoreGroups = 4;
+constexpr int kScoreThreads = 128 * kScoreGroups;
 constexpr int kSW1 = 0;                          // W1: 128 x 96 bf16
 constexpr int kSW2 = kSW1 + kH * kIn * 2;        // W2: 128 x 128 bf16
 constexpr int kSW3 = kSW2 + kH * kH * 2;         // W3
-constexpr int kSAct = kSW3 + kH * kH * 2;        // activations: 128 x 128 bf16
-constexpr int kSVec = kSAct + 128 * kH * 2;      // b1, b2, b3, w4 (fp32)
-constexpr int kSBar = kSVec + 4 * kH * 4;        // mbarrier + tensor-memory address
-constexpr size_t kScoreSmem = (size_t)kSBar + 16;
+constexpr int kSAct = kSW3 + kH * kH * 2;        // activations: one 128 x 128 bf16 tile per group
+constexpr int kSActBytes = 128 * kH * 2;
+constexpr int kSVec = kSAct + kScoreGroups * kSActBytes;  // b1, b2, b3, w4 (fp32)
+constexpr int kSBar = kSVec + 4 * kH * 4;        // one mbarrier per group, then the TMEM address
+constexpr size_t kScoreSmem = (size_t)kSBar + 8 * kScoreGroups + 8;
+constexpr uint32_t kScoreTmemCols = 128 * kScoreGroups;  // a power of two in [32, 512]
+static_assert(kScoreSmem <= 227 * 1024, "fused scoring shared memory");
+static_assert(kScoreTmemCols == 128 || kScoreTmemCols == 256 || kScoreTmemCols == 512,
+              "tensor-memory allocation");
 
 // byte offset of element (r, k) in the no-swizzle K-major core-matrix layout
 // of a tile with kdim columns: core (r / 8, k / 8) at ((r/8)(kdim/8) + k/8) 128 B
@@ -397,15 +410,32 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// bounded wait for the tile's MMAs, agreed by the whole block
-__device__ __forceinline__ bool block_wait(uint32_t bar, uint32_t phase, long long spin) {
-  const bool got = mbar_wait(bar, phase, spin);
-  return __syncthreads_and(got) != 0;
+// barrier of one 128-thread group (named barrier `id`, 1 + group)
+__device__ __forceinline__ void group_sync(uint32_t id) {
+  asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
 }
 
-__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a0, uint32_t b0, int kdim,
-                                            uint32_t bar) {
-  if (threadIdx.x == 0) {
+// the group's threads agree on v (AND) at named barrier `id`
+__device__ __forceinline__ bool group_and(bool v, uint32_t id) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, 128, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(out)
+      : "r"((uint32_t)v), "r"(id)
+      : "memory");
+  return out != 0;
+}
+
+// bounded wait for the group's MMAs, agreed by the whole group
+__device__ __forceinline__ bool group_wait(uint32_t bar, uint32_t phase, long long spin, uint32_t id) {
+  const bool got = mbar_wait(bar, phase, spin);
+  return group_and(got, id);
+}
+
+__device__ __forceinline__ void issue_layer(bool leader, uint32_t tmem, uint32_t a0, uint32_t b0,
+                                            int kdim, uint32_t bar) {
+  if (leader) {
     tc_fence_after();
     const uint32_t sbo = (uint32_t)(kdim / 8) * 128u;
     for (int kk = 0; kk < kdim / 16; ++kk)
@@ -415,13 +445,14 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a0, uint32_t
   }
 }
 
-// hidden-layer epilogue: row threadIdx.x of the accumulator + bias, ReLU,
-// BF16, into the activation tile (K = 128 layout)
-__device__ __forceinline__ void hidden_epilogue(uint32_t tmem, const float* bias, uint8_t* act) {
-  const int warp = threadIdx.x >> 5, r = threadIdx.x;
+// hidden-layer epilogue: row r of the group's accumulator (tensor-memory
+// lanes of warp quarter q = r / 32) + bias, ReLU, BF16, into the activation
+// tile (K = 128 layout)
+__device__ __forceinline__ void hidden_epilogue(uint32_t tmem, int r, const float* bias, uint8_t* act) {
+  const int q = r >> 5;
   for (int c0 = 0; c0 < kH; c0 += 16) {
     float v[16];
-    tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    tc_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
     uint32_t w[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
@@ -439,9 +470,12 @@ __global__ void __launch_bounds__(kScoreThreads, 1)
                            uint32_t* __restrict__ err, long long spin) {
   extern __shared__ __align__(1024) uint8_t smem[];
   float* vec = reinterpret_cast<float*>(smem + kSVec);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kSBar);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSBar + 8);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSBar + 8 * kScoreGroups);
   const int warp = threadIdx.x >> 5;
+  const int g = threadIdx.x >> 7;        // group
+  const int r = threadIdx.x & 127;       // the group's row of a tile
+  const uint32_t gbar_id = 1u + (uint32_t)g;
+  const bool leader = r == 0;
   stage_weights(smem + kSW1, W1, kIn);
   stage_weights(smem + kSW2, W2, kH);
   stage_weights(smem + kSW3, W3, kH);
@@ -455,23 +489,24 @@ __global__ void __launch_bounds__(kScoreThreads, 1)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(128));
+                 "r"(kScoreTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  if (threadIdx.x == 0) mbar_init(smem_u32(bar), 1);
+  if (leader) mbar_init(smem_u32(smem + kSBar + 8 * g), 1);
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-  const uint32_t sact = smem_u32(smem + kSAct), bar_a = smem_u32(bar);
-  uint8_t* act = smem + kSAct;
+  const uint32_t tmem = *tmem_slot + 128u * (uint32_t)g;  // the group's accumulator columns
+  uint8_t* act = smem + kSAct + g * kSActBytes;
+  const uint32_t sact = smem_u32(act), bar_a = smem_u32(smem + kSBar + 8 * g);
   uint32_t phase = 0;
   bool ok = true, issued = false;
   const int64_t n_tiles = (n + 127) / 128;
-  for (int64_t tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
-    // features of row threadIdx.x, eight columns per 16-byte store (K = 96 layout)
-    const int64_t row = tile * 128 + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * kScoreGroups;
+  for (int64_t tile = (int64_t)blockIdx.x * kScoreGroups + g; tile < n_tiles && ok; tile += stride) {
+    // features of row r, eight columns per 16-byte store (K = 96 layout)
+    const int64_t row = tile * 128 + r;
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (row < n) {
       const uint32_t ray = S.ray_id ? S.ray_id[row] : (uint32_t)row;
@@ -490,40 +525,40 @@ __global__ void __launch_bounds__(kScoreThreads, 1)
         w[k] = row < n ? pack_bf16x2(sn, cs) : 0u;
       }
       // columns (c * 8 + k) * 2 + {0, 1}: 16 columns per coordinate
-      *reinterpret_cast<uint4*>(act + cm_off(threadIdx.x, 16 * c, kIn)) = make_uint4(w[0], w[1], w[2], w[3]);
-      *reinterpret_cast<uint4*>(act + cm_off(threadIdx.x, 16 * c + 8, kIn)) = make_uint4(w[4], w[5], w[6], w[7]);
+      *reinterpret_cast<uint4*>(act + cm_off(r, 16 * c, kIn)) = make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(act + cm_off(r, 16 * c + 8, kIn)) = make_uint4(w[4], w[5], w[6], w[7]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
-    __syncthreads();
+    group_sync(gbar_id);
     // layer 1 (K = 96)
-    issue_layer(tmem, sact, smem_u32(smem + kSW1), kIn, bar_a);
+    issue_layer(leader, tmem, sact, smem_u32(smem + kSW1), kIn, bar_a);
     issued = true;
-    if (!(ok = block_wait(bar_a, phase, spin))) break;
+    if (!(ok = group_wait(bar_a, phase, spin, gbar_id))) break;
     phase ^= 1u;
     tc_fence_after();
-    hidden_epilogue(tmem, vec, act);
+    hidden_epilogue(tmem, r, vec, act);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
-    __syncthreads();
+    group_sync(gbar_id);
     // layer 2
-    issue_layer(tmem, sact, smem_u32(smem + kSW2), kH, bar_a);
-    if (!(ok = block_wait(bar_a, phase, spin))) break;
+    issue_layer(leader, tmem, sact, smem_u32(smem + kSW2), kH, bar_a);
+    if (!(ok = group_wait(bar_a, phase, spin, gbar_id))) break;
     phase ^= 1u;
     tc_fence_after();
-    hidden_epilogue(tmem, vec + kH, act);
+    hidden_epilogue(tmem, r, vec + kH, act);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
-    __syncthreads();
+    group_sync(gbar_id);
     // layer 3 and the output layer
-    issue_layer(tmem, sact, smem_u32(smem + kSW3), kH, bar_a);
-    if (!(ok = block_wait(bar_a, phase, spin))) break;
+    issue_layer(leader, tmem, sact, smem_u32(smem + kSW3), kH, bar_a);
+    if (!(ok = group_wait(bar_a, phase, spin, gbar_id))) break;
     phase ^= 1u;
     tc_fence_after();
     float z = 0.0f;
     for (int c0 = 0; c0 < kH; c0 += 16) {
       float a[16];
-      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, a);
+      tc_ld16(tmem + ((uint32_t)((r >> 5) * 32) << 16) + (uint32_t)c0, a);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const float h = __bfloat162float(__float2bfloat16_rn(fmaxf(a[i] + vec[2 * kH + c0 + i], 0.0f)));
@@ -532,16 +567,17 @@ __global__ void __launch_bounds__(kScoreThreads, 1)
     }
     if (row < n) logits[row] = z + b4;
     tc_fence_before();
-    __syncthreads();
+    group_sync(gbar_id);
   }
   if (!ok) {
-    if (threadIdx.x == 0) atomicOr(err, kErrMmaTimeout);
-    if (issued) mbar_wait(bar_a, phase);  // bounded: let our MMAs drain
+    if (r == 0) atomicOr(err, kErrMmaTimeout);
+    if (issued) mbar_wait(bar_a, phase);  // bounded: let the group's MMAs drain
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot),
+                 "r"(kScoreTmemCols));
 }
 
 // H = bf16(relu(Z + bias)) [B x 128], optionally also transposed [128 x ldt].
@@ -993,7 +1029,8 @@ nrt_status nrt_mlp_score(nrt_mlp* m, const float* tx, const uint32_t* ray_ids, i
     attr_set = true;
   }
   const int64_t tiles = (n + 127) / 128;
-  const unsigned grid = (unsigned)std::min<int64_t>(tiles, ctx->sm_count);
+  const unsigned grid = (unsigned)std::min<int64_t>((tiles + kScoreGroups - 1) / kScoreGroups,
+                                                    ctx->sm_count);
   mlp_score_fused_kernel<<<grid, kScoreThreads, kScoreSmem, st>>>(S, n, m->n_rays, m->W1, m->W2, m->W3,
                                                                  m->theta, logits, m->err,
                                                                  wait_limit(ctx));

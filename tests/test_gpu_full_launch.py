@@ -1,8 +1,9 @@
 """The benchmarked configuration in full against the FP64 oracle: the
 office (2M points, 16 RX), the whole 1M-ray Fibonacci launch, 5
 interactions, visibility capture with diffuse last interactions, every
-candidate of a key refined (the paper's rule) -- every step compared: hit records of every ray (bit-exact outside the
-oracle's ambiguity), the path set and each key's representative (the
+candidate of a key refined (the paper's rule) -- every step compared: hit
+records of every ray and the visibility bits the oracle evaluated
+(bit-exact outside the oracle's ambiguity), the path set and each key's representative (the
 lowest valid ray id of Sec. II-B-4), every matched path's coefficient and
 delay, and the per-RX received power.  The oracle traces all 1M rays with
 its shadow trajectories (a few minutes on the host's cores)."""
@@ -38,6 +39,28 @@ def test_office_full_launch_against_oracle(office):
                      index_tail=1e-6)
     print("full launch hits:", h)
     assert h["checked"] > 2_000_000
+    # visibility matrix: every (RX, DPS) bit the oracle evaluated, outside its
+    # ambiguity band, bit-exact (DPS matched by voxel)
+    gvis = res.vis()
+    gv, _, _ = sc.dps()
+    ov, _, _ = osc.dps()
+
+    def vkey(v):
+        v = np.asarray(v, np.int64)
+        return (v[:, 0] << 42) | (v[:, 1] << 21) | v[:, 2]
+
+    gk, ok = vkey(gv), vkey(ov)
+    gord = np.argsort(gk)
+    pos = np.searchsorted(gk[gord], ok)
+    assert np.array_equal(gk[gord][np.minimum(pos, len(gk) - 1)], ok)
+    g_of_o = gord[pos]
+    vj, vd, vbit, vamb = osim.vis()
+    sel = ~vamb
+    vis_mismatch = int(np.count_nonzero(gvis[vj[sel], g_of_o[vd[sel]]] != vbit[sel]))
+    vis_stats = {"pairs": int(len(vj)), "checked": int(sel.sum()), "ambiguous": int(vamb.sum()),
+                 "visible": int(vbit[sel].sum()), "mismatch": vis_mismatch}
+    print("full launch visibility:", vis_stats)
+    assert vis_stats["checked"] > 100_000 and vis_mismatch == 0
     gp = res.paths()
     s = compare_paths(gp, osim, office.eps_r, office.sigma, office.scat,
                       strict=("los", "specular"), key_tail=5e-6, path_tail=1e-4)
@@ -58,5 +81,6 @@ def test_office_full_launch_against_oracle(office):
     out = os.environ.get("NRT_PARITY_OUT")
     if out:
         with open(out, "w") as f:
-            json.dump({"hits": h, "paths": s, "keys_gpu": cg["keys"], "keys_oracle": n_keys_o,
+            json.dump({"hits": h, "visibility": vis_stats, "paths": s, "keys_gpu": cg["keys"],
+                       "keys_oracle": n_keys_o,
                        "power_rel_diff_all_paths": dP.tolist()}, f, indent=1)

@@ -74,9 +74,13 @@ def test_features_match_oracle(ctx):
     assert diff.mean() < 2e-3, diff.mean()
 
 
-def test_logits_match_oracle_forward(ctx):
+@pytest.mark.parametrize("n_ids", [1, 100, 7634, 142857])
+def test_logits_match_oracle_forward(ctx, n_ids):
+    """The fused scoring kernel (four 128-row tiles in flight per SM) against
+    the oracle's forward pass: one row, one partial tile, fewer tiles than
+    the grid's groups, and more tiles than groups with a ragged last tile."""
     net, theta = _net(ctx)
-    ids = np.arange(3, N_RAYS, 131, dtype=np.uint32)
+    ids = np.linspace(3, N_RAYS - 1, n_ids).astype(np.uint32)
     tx = np.array([12.5, 4.0, 1.0], np.float32)
     z = torch.zeros(ids.size, dtype=torch.float32, device="cuda")
     net.score(tx, torch.from_numpy(ids).cuda(), ids.size, z)
