@@ -578,7 +578,10 @@ nrt_status nrt_mlp_features(nrt_mlp* mlp, const float* tx, const uint32_t* ray_i
                             uint16_t* out);
 
 /* Logits of launch rays ray_ids (device uint32[n] or NULL) from TX tx (host
- * float[3]) into device float[n].  Asynchronous on the context stream. */
+ * float[3]) into device float[n].  Asynchronous on the context stream.  The
+ * first call allocates and fills a table of the launch's directions (16 B
+ * per ray, for launches of at most 2^26 rays; the network frees it), which
+ * later calls read instead of recomputing each direction. */
 nrt_status nrt_mlp_score(nrt_mlp* mlp, const float* tx, const uint32_t* ray_ids, int64_t n,
                          float* logits);
 

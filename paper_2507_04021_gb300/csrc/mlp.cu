@@ -359,6 +359,18 @@ __global__ void features_kernel(SampleSrc S, int64_t B, int64_t n_rays, bf16* __
   }
 }
 
+// launch directions of the N-ray Fibonacci launch, as fib_dir gives them
+// (scoring reads them instead of recomputing them per row); networks whose
+// launch is larger than kDirTableMax directions compute them per row
+constexpr int64_t kDirTableMax = 1ll << 26;
+__global__ void dir_table_kernel(int64_t n_rays, float4* __restrict__ dirs) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rays;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float3 d = fib_dir((uint32_t)i, n_rays);
+    dirs[i] = make_float4(d.x, d.y, d.z, 0.0f);
+  }
+}
+
 // ---------------------------------------------------------------- fused scoring
 // One persistent CTA per SM scores 128-row tiles end to end on the tensor
 // cores: a tile's Fourier features are written straight into the MMA operand
@@ -368,6 +380,11 @@ __global__ void features_kernel(SampleSrc S, int64_t B, int64_t n_rays, bf16* __
 // memory), and the output layer is folded into the last epilogue: each thread
 // owns one row, so the logit is a per-thread dot product.  W1, W2, W3 stay in
 // shared memory for the whole launch.
+//
+// The launch directions come from a table computed once per network (the
+// same float values fib_dir gives, without its FP64 arithmetic per row), and
+// the TX half of the features, equal for every row of a launch, is computed
+// once per CTA.
 //
 // The CTA runs kScoreGroups independent groups of 128 threads, each with its
 // own tiles, activation tile, 128 accumulator columns, mbarrier and named
@@ -383,7 +400,8 @@ constexpr int kSW3 = kSW2 + kH * kH * 2;         // W3
 constexpr int kSAct = kSW3 + kH * kH * 2;        // activations: one 128 x 128 bf16 tile per group
 constexpr int kSActBytes = 128 * kH * 2;
 constexpr int kSVec = kSAct + kScoreGroups * kSActBytes;  // b1, b2, b3, w4 (fp32)
-constexpr int kSBar = kSVec + 4 * kH * 4;        // one mbarrier per group, then the TMEM address
+constexpr int kSTx = kSVec + 4 * kH * 4;         // the TX's 48 features (24 packed BF16 pairs)
+constexpr int kSBar = kSTx + 24 * 4;             // one mbarrier per group, then the TMEM address
 constexpr size_t kScoreSmem = (size_t)kSBar + 8 * kScoreGroups + 8;
 constexpr uint32_t kScoreTmemCols = 128 * kScoreGroups;  // a power of two in [32, 512]
 static_assert(kScoreSmem <= 227 * 1024, "fused scoring shared memory");
@@ -464,12 +482,13 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t tmem, int r, const floa
 }
 
 __global__ void __launch_bounds__(kScoreThreads, 1)
-    mlp_score_fused_kernel(SampleSrc S, int64_t n, int64_t n_rays, const bf16* __restrict__ W1,
-                           const bf16* __restrict__ W2, const bf16* __restrict__ W3,
-                           const float* __restrict__ theta, float* __restrict__ logits,
-                           uint32_t* __restrict__ err, long long spin) {
+    mlp_score_fused_kernel(SampleSrc S, int64_t n, int64_t n_rays, const float4* __restrict__ dirs,
+                           const bf16* __restrict__ W1, const bf16* __restrict__ W2,
+                           const bf16* __restrict__ W3, const float* __restrict__ theta,
+                           float* __restrict__ logits, uint32_t* __restrict__ err, long long spin) {
   extern __shared__ __align__(1024) uint8_t smem[];
   float* vec = reinterpret_cast<float*>(smem + kSVec);
+  uint32_t* txw = reinterpret_cast<uint32_t*>(smem + kSTx);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kSBar + 8 * kScoreGroups);
   const int warp = threadIdx.x >> 5;
   const int g = threadIdx.x >> 7;        // group
@@ -484,6 +503,13 @@ __global__ void __launch_bounds__(kScoreThreads, 1)
     vec[kH + f] = theta[kOffB2 + f];
     vec[2 * kH + f] = theta[kOffB3 + f];
     vec[3 * kH + f] = __bfloat162float(__float2bfloat16_rn(theta[kOffW4 + f]));
+  }
+  if (threadIdx.x < 24) {  // feature (3 + c, octave k) of the TX
+    const int c = threadIdx.x >> 3, k = threadIdx.x & 7;
+    const float vt = __fdiv_rn(__fsub_rn(S.tx0[c], S.cen[c]), S.inv_half_num[c]);
+    float sn, cs;
+    sincospif(ldexpf(vt, k), &sn, &cs);
+    txw[threadIdx.x] = pack_bf16x2(sn, cs);
   }
   const float b4 = theta[kOffB4];
   if (warp == 0) {
@@ -507,22 +533,32 @@ __global__ void __launch_bounds__(kScoreThreads, 1)
   for (int64_t tile = (int64_t)blockIdx.x * kScoreGroups + g; tile < n_tiles && ok; tile += stride) {
     // features of row r, eight columns per 16-byte store (K = 96 layout)
     const int64_t row = tile * 128 + r;
-    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float v[3] = {0.f, 0.f, 0.f};
     if (row < n) {
       const uint32_t ray = S.ray_id ? S.ray_id[row] : (uint32_t)row;
-      const float3 d = fib_dir(ray, n_rays);
-      v[0] = d.x;
-      v[1] = d.y;
-      v[2] = d.z;
-      for (int c = 0; c < 3; ++c) v[3 + c] = __fdiv_rn(__fsub_rn(S.tx0[c], S.cen[c]), S.inv_half_num[c]);
+      if (dirs && (int64_t)ray < n_rays) {  // (an id past the launch: computed below)
+        const float4 d = __ldg(dirs + ray);
+        v[0] = d.x;
+        v[1] = d.y;
+        v[2] = d.z;
+      } else {
+        const float3 d = fib_dir(ray, n_rays);
+        v[0] = d.x;
+        v[1] = d.y;
+        v[2] = d.z;
+      }
     }
     for (int c = 0; c < 6; ++c) {
       uint32_t w[8];
 #pragma unroll
       for (int k = 0; k < kOct; ++k) {
-        float sn, cs;
-        sincospif(ldexpf(v[c], k), &sn, &cs);
-        w[k] = row < n ? pack_bf16x2(sn, cs) : 0u;
+        if (c < 3) {
+          float sn, cs;
+          sincospif(ldexpf(v[c], k), &sn, &cs);
+          w[k] = row < n ? pack_bf16x2(sn, cs) : 0u;
+        } else {
+          w[k] = row < n ? txw[(c - 3) * 8 + k] : 0u;
+        }
       }
       // columns (c * 8 + k) * 2 + {0, 1}: 16 columns per coordinate
       *reinterpret_cast<uint4*>(act + cm_off(r, 16 * c, kIn)) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -785,6 +821,7 @@ struct nrt_mlp {
   int64_t loss_cap = 0;
   uint32_t* idx = nullptr;
   uint32_t* err = nullptr;
+  float4* dirs = nullptr;  // launch directions [n_rays] for scoring (built at the first score)
   bool holds_ctx = false;
 };
 
@@ -939,7 +976,7 @@ void nrt_mlp_free(nrt_mlp* m) {
   cudaStreamSynchronize(m->ctx->stream);
   free_ws(m);
   void* p[] = {m->theta, m->grad, m->m, m->v, m->W1, m->W2, m->W3, m->W2T, m->W3T, m->w4, m->err,
-               m->loss};
+               m->loss, m->dirs};
   for (void* q : p)
     if (q) cudaFree(q);
   nrt_ctx* ctx = m->ctx;
@@ -1021,19 +1058,20 @@ nrt_status nrt_mlp_score(nrt_mlp* m, const float* tx, const uint32_t* ray_ids, i
   S.ray_id = ray_ids;
   S.n = n;
   cudaStream_t st = ctx->stream;
-  static bool attr_set = false;
-  if (!attr_set) {
-    NRT_CUDA_TRY(ctx, cudaFuncSetAttribute(mlp_score_fused_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)kScoreSmem));
-    attr_set = true;
+  NRT_CUDA_TRY(ctx, cudaFuncSetAttribute(mlp_score_fused_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kScoreSmem));
+  if (!m->dirs && m->n_rays <= kDirTableMax) {
+    NRT_CUDA_TRY(ctx, cudaMalloc(&m->dirs, (size_t)m->n_rays * sizeof(float4)));
+    dir_table_kernel<<<blocks_for_n(m->n_rays), 256, 0, st>>>(m->n_rays, m->dirs);
+    count_launch();
   }
   const int64_t tiles = (n + 127) / 128;
   const unsigned grid = (unsigned)std::min<int64_t>((tiles + kScoreGroups - 1) / kScoreGroups,
                                                     ctx->sm_count);
-  mlp_score_fused_kernel<<<grid, kScoreThreads, kScoreSmem, st>>>(S, n, m->n_rays, m->W1, m->W2, m->W3,
-                                                                 m->theta, logits, m->err,
-                                                                 wait_limit(ctx));
+  mlp_score_fused_kernel<<<grid, kScoreThreads, kScoreSmem, st>>>(S, n, m->n_rays, m->dirs, m->W1,
+                                                                 m->W2, m->W3, m->theta, logits,
+                                                                 m->err, wait_limit(ctx));
   count_launch();
   NRT_CUDA_TRY(ctx, cudaGetLastError());
   return NRT_OK;
