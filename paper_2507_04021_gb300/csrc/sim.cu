@@ -1245,7 +1245,7 @@ __global__ void spec_expand_kernel(KeyState K, const uint32_t* __restrict__ list
 // Item pass: lanes take items in order (one warp-aggregated atomic per
 // fetch); an item ranked after a key's already-found valid candidate is
 // skipped (it cannot be the lowest).
-__global__ void __launch_bounds__(kTraceThreads, 6)
+__global__ void __launch_bounds__(kTraceThreads, 5)
     validate_specular_items_kernel(SceneView S, SimConst C, ValArgs A,
                                    const uint32_t* __restrict__ items,
                                    const unsigned long long* __restrict__ n_items_p,
@@ -2255,7 +2255,7 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   spec_expand_kernel<<<blocks_for(c.keys * 32, 256, sm), 256, 0, st>>>(
       W.K, W.spec_list, W.cnt + kCntSpec, W.spec_cnt, W.spec_off, W.items, c.cand,
       W.cnt + kCntItems); count_launch();
-  validate_specular_items_kernel<<<blocks_for(c.cand, kTraceThreads, sm, 6), kTraceThreads, 0, st>>>(
+  validate_specular_items_kernel<<<blocks_for(c.cand, kTraceThreads, sm, 5), kTraceThreads, 0, st>>>(
       S, C, V, W.items, W.cnt + kCntItems, W.spec_best, W.cnt + kCntFetchS, ctr); count_launch();
   spec_finish_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
       S, C, V, W.spec_list, W.cnt + kCntSpec, W.spec_best, ctr); count_launch();
