@@ -88,7 +88,7 @@ typedef struct {
   float t_d;            /* refinement plane-distance threshold, m */
   float freq;           /* carrier frequency, Hz */
   int32_t keep_keys;    /* 1: keep per-key validation summaries, readable by nrt_keys_read */
-  int64_t key_capacity;   /* hash-table slots (power of two; 0 = automatic) */
+  int64_t key_capacity;   /* hash-table slots (power of two, at most 2^31; 0 = automatic) */
   int64_t cand_capacity;  /* candidate buffer entries (0 = automatic) */
   int32_t launch;       /* NRT_LAUNCH_FIB: Fibonacci sphere of n_rays rays;
                            NRT_LAUNCH_DPS: one ray per DPS toward its reception

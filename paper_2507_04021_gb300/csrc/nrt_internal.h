@@ -217,6 +217,8 @@ inline void count_launch_n(int64_t n = 1) { launch_counter() += n; }
 // debug builds: synchronise after every launch and report the first failing
 // launch site on stderr
 void debug_launch_check(const char* file, int line);
+// stream capture in progress on this thread: skip the per-launch synchronisation
+void debug_capture(bool on);
 #define count_launch(...) (count_launch_n(__VA_ARGS__), debug_launch_check(__FILE__, __LINE__))
 #else
 #define count_launch(...) count_launch_n(__VA_ARGS__)

@@ -56,8 +56,12 @@ int64_t& launch_counter() {
 }
 
 #ifdef NRT_CHECK_BOUNDS
+thread_local bool g_dbg_capturing = false;
+void debug_capture(bool on) { g_dbg_capturing = on; }
+
 void debug_launch_check(const char* file, int line) {
   static bool reported = false;
+  if (g_dbg_capturing) return;  // no synchronisation inside a stream capture
   const cudaError_t e = cudaDeviceSynchronize();
   const cudaError_t l = cudaPeekAtLastError();
   if (!reported && (e != cudaSuccess || l != cudaSuccess)) {

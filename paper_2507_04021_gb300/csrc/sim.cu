@@ -96,6 +96,10 @@ struct Table {
   uint32_t* kid;  // [slot] key id of an occupied slot
   uint64_t mask;
 };
+// candidate slot of a key the full table could not take (tables hold at most
+// 2^31 slots, so no slot index reaches it)
+constexpr uint32_t kNoSlot = 0xFFFFFFFFu;
+constexpr int64_t kMaxTable = 1ll << 31;
 
 struct KeyState {
   uint32_t* slot;    // [key] -> table slot
@@ -626,8 +630,11 @@ __device__ __forceinline__ void warp_emit(const EmitArgs& A, bool pred, uint64_t
   uint64_t slot = 0;
   if (lane == leader) slot = insert_key(A, hi, lo, f, ctr);
   slot = __shfl_sync(peers, slot, leader);
-  if (slot == ~0ull) return;
-  if (n_mine < A.cand_cap) A.cand[n_mine] = make_uint2((uint32_t)slot, row);
+  // a full table (flagged by insert_key) still fills the position the count
+  // pass reserved, with slot kNoSlot, so that no candidate entry below the
+  // count is left unwritten; cand_key_kernel gives it no key
+  const uint32_t s32 = slot == ~0ull ? kNoSlot : (uint32_t)slot;
+  if (n_mine < A.cand_cap) A.cand[n_mine] = make_uint2(s32, row);
   else atomicOr((uint32_t*)(ctr + kCtrErr), kErrCandFull);
   ++n_mine;
 }
@@ -900,11 +907,12 @@ __global__ void cand_key_kernel(Table T, uint2* cand, const unsigned long long* 
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cand;
        c += (int64_t)gridDim.x * blockDim.x) {
     const uint2 e = cand[c];
-    NRT_GUARD(e.x < g_dbg_caps.table, 21, e.x)
+    NRT_GUARD(e.x == kNoSlot || e.x < g_dbg_caps.table, 21, e.x)
     NRT_GUARD(e.y < g_dbg_caps.rows, 22, e.y)
-    const uint32_t kid = T.kid[e.x];
-    // a key over capacity gets all ones: its id field sorts after every id
-    // below key_cap (2^kid_bits > key_cap) and matches none of them
+    // a key over capacity (or a candidate the full table could not take)
+    // gets all ones: its id field sorts after every id below key_cap
+    // (2^kid_bits > key_cap) and matches none of them
+    const uint32_t kid = (uint64_t)e.x <= T.mask ? T.kid[e.x] : 0xFFFFFFFFu;
     reinterpret_cast<uint64_t*>(cand)[c] =
         (int64_t)kid < key_cap ? ((uint64_t)kid << row_bits) | (uint64_t)e.y : ~0ull;
   }
@@ -2242,7 +2250,7 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   // on the context's second stream so that the two validations overlap on
   // the device (they touch disjoint keys; paths and counters are taken by
   // atomics and the paths are sorted afterwards)
-  TRY(cudaMemsetAsync(W.cnt + kCntFetchS, 0, 24, st));
+  TRY(cudaMemsetAsync(W.cnt + kCntFetchS, 0, (kCntN - kCntFetchS) * sizeof(unsigned long long), st));
   TRY(cudaEventRecord(ctx->fork, st));
   TRY(cudaStreamWaitEvent(ctx->aux, ctx->fork, 0));
   validate_diffuse_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 6), kTraceThreads, 0, ctx->aux>>>(
@@ -2463,6 +2471,11 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
     release_work(W, st);
     return NRT_ERR_ARG;
   }
+  if (c.table > kMaxTable) {
+    ctx->last_error = "more path keys than a 2^31-slot hash table holds";
+    release_work(W, st);
+    return NRT_ERR_OVERFLOW;
+  }
   c.keys = std::min<int64_t>(c.keys, c.table);
   c.paths = c.keys + (C.batch ? r->n_pairs : r->n_rx_phys) + diffraction_slots(r);
   rc = alloc_result(r, c, true);
@@ -2518,6 +2531,10 @@ nrt_status batch_graph_build(nrt_result* r) {
   c.keys = std::max<int64_t>(m.keys + m.keys / 4 + 1024, 1);
   c.table = 1 << 12;
   while (c.table < 2 * c.keys) c.table <<= 1;
+  if (c.table > kMaxTable) {
+    ctx->last_error = "more path keys than a 2^31-slot hash table holds";
+    return NRT_ERR_OVERFLOW;
+  }
   c.paths = c.keys + r->n_pairs + diffraction_slots(r);
   // path buffers sized by the caps (the calibration run's paths are dropped)
   nrt_status rc = alloc_result(r, c, true);
@@ -2529,6 +2546,7 @@ nrt_status batch_graph_build(nrt_result* r) {
   if (rc != NRT_OK) return rc;
   rc = alloc_work(ctx, *W, c, r->n_traced, st);
   if (rc != NRT_OK) return rc;
+  TRY(dbg_set_caps(c.table, c.keys, c.cand, c.paths, r->n_traced, r->n_rx, st));
   TRY(cudaStreamSynchronize(st));
   for (int e = 0; e < 8; ++e) {
     if (r->ev[e]) cudaEventDestroy(r->ev[e]);
@@ -2537,6 +2555,9 @@ nrt_status batch_graph_build(nrt_result* r) {
   cudaGraph_t g;
   launch_counter() = 0;
   TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+#ifdef NRT_CHECK_BOUNDS
+  debug_capture(true);
+#endif
   rc = enqueue_trace(r, S, C, nullptr, order, false);
   Records R{r->rec_q, r->rec_n, r->rec_d, r->rec_i, r->n_traced};
   if (rc == NRT_OK) {
@@ -2547,6 +2568,9 @@ nrt_status batch_graph_build(nrt_result* r) {
     rc = enqueue_rest(r, *W, S, C, order);
   }
   cudaError_t e2 = cudaStreamEndCapture(st, &g);
+#ifdef NRT_CHECK_BOUNDS
+  debug_capture(false);
+#endif
   r->graph_launches = launch_counter();
   if (rc != NRT_OK) return rc;
   if (e2 != cudaSuccess) {
