@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -26,6 +28,8 @@ struct nrt_ctx {
   // second stream for overlapping work, forked from and joined into `stream`
   cudaStream_t aux = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  // capacity hints (candidates, keys, table slots, paths) per simulation shape
+  std::map<std::vector<int64_t>, std::array<int64_t, 4>> caps_hint;
 };
 
 struct nrt_scene {

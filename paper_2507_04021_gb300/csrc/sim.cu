@@ -2405,10 +2405,14 @@ nrt_status enqueue_trace(nrt_result* r, const SceneView& S, const SimConst& C,
 
 }  // namespace
 
-// One simulation into r (scene, params, receivers and rows set).  The only
-// host round trip sizes the candidate buffers and the hash table from an
-// exact count; everything after it is enqueued without synchronising.
-nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
+// One simulation into r (scene, params, receivers and rows set).  Without a
+// hint, the one host round trip sizes the candidate buffers and the hash
+// table from an exact count, and everything after it is enqueued without
+// synchronising.  With a hint (the capacities of an earlier run of the same
+// shape, with headroom) nothing waits for the host: every device write is
+// bounded by the capacities and an overflow is flagged, and run_trace redoes
+// a run that overflowed its hint with exact sizes.
+nrt_status run_trace_once(nrt_result* r, const uint32_t* subset_d, const Caps* hint) {
   nrt_scene* sc = r->scene;
   nrt_ctx* ctx = sc->ctx;
   cudaStream_t st = ctx->stream;
@@ -2441,11 +2445,16 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
   A.cand_cnt = W.cand_cnt;
   emit_kernel<kModeCount><<<blocks_for(n, 256, sm), 256, 0, st>>>(S, C, r->rx, R, r->vis, order, A, r->ctr); count_launch();
   scan_exclusive(W.cand_cnt, W.cand_off, n, st);
+  for (int e = 0; e < 2; ++e)
+    if (!r->ev_gap[e]) TRY(cudaEventCreate(&r->ev_gap[e]));
+  Caps c;
+  if (hint) {
+    c = *hint;
+    TRY(cudaEventRecord(r->ev_gap[0], st));
+  } else {
   unsigned long long cnt2[2] = {0, 0};
   TRY(cudaMemcpyAsync(&cnt2[0], r->ctr + kCtrCands, 8, cudaMemcpyDeviceToHost, st));
   TRY(cudaMemcpyAsync(&cnt2[1], r->ctr + kCtrLeaders, 8, cudaMemcpyDeviceToHost, st));
-  for (int e = 0; e < 2; ++e)
-    if (!r->ev_gap[e]) TRY(cudaEventCreate(&r->ev_gap[e]));
   TRY(cudaEventRecord(r->ev_gap[0], st));
   TRY(cudaStreamSynchronize(st));
   if (r->p.cand_capacity > 0 && (int64_t)cnt2[0] > r->p.cand_capacity) {
@@ -2458,7 +2467,6 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
     release_work(W, st);
     return NRT_ERR_OVERFLOW;
   }
-  Caps c;
   c.cand = std::max<int64_t>((int64_t)cnt2[0], 1);
   c.keys = std::max<int64_t>((int64_t)cnt2[1], 1);  // distinct keys <= per-warp distinct keys
   c.table = r->p.key_capacity;
@@ -2478,6 +2486,7 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
   }
   c.keys = std::min<int64_t>(c.keys, c.table);
   c.paths = c.keys + (C.batch ? r->n_pairs : r->n_rx_phys) + diffraction_slots(r);
+  }
   rc = alloc_result(r, c, true);
   if (rc == NRT_OK) rc = alloc_work(ctx, W, c, n, st);
   TRY(dbg_set_caps(c.table, c.keys, c.cand, c.paths, n, r->n_rx, st));
@@ -2490,7 +2499,53 @@ nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
   TRY(cudaEventRecord(r->ev[6], st));
   TRY(cudaEventRecord(r->ev[7], st));
   release_work(W, st);
-  return finish_result(r);
+  rc = finish_result(r);
+  if (rc == NRT_OK && hint && r->counters.candidates > c.cand) {
+    // (more candidates than the hint's capacity: flagged by the kernels too)
+    ctx->last_error = "device buffer overflow (candidates over the hint)";
+    rc = NRT_ERR_OVERFLOW;
+  }
+  return rc;
+}
+
+// Capacity hints per simulation shape (scene, rows, receivers, capture,
+// depth, diffuse, diffraction, launch): the last exact run's counts + 25%.
+std::vector<int64_t> hint_key(const nrt_result* r) {
+  return {(int64_t)(intptr_t)r->scene, r->n_traced, r->n_rx, (int64_t)r->p.capture,
+          (int64_t)r->p.max_depth, (int64_t)r->p.diffuse, (int64_t)r->p.diffraction,
+          (int64_t)r->p.launch};
+}
+
+nrt_status run_trace(nrt_result* r, const uint32_t* subset_d) {
+  nrt_ctx* ctx = r->scene->ctx;
+  const bool hinted = !r->n_pairs && r->p.cand_capacity <= 0 && r->p.key_capacity <= 0;
+  const std::vector<int64_t> key = hinted ? hint_key(r) : std::vector<int64_t>{};
+  if (hinted) {
+    auto it = ctx->caps_hint.find(key);
+    if (it != ctx->caps_hint.end()) {
+      Caps h;
+      h.cand = it->second[0];
+      h.keys = it->second[1];
+      h.table = it->second[2];
+      h.paths = it->second[3];
+      const nrt_status rc = run_trace_once(r, subset_d, &h);
+      if (rc != NRT_ERR_OVERFLOW) return rc;
+      ctx->caps_hint.erase(key);  // outgrown: size exactly once more
+    }
+  }
+  const nrt_status rc = run_trace_once(r, subset_d, nullptr);
+  if (rc == NRT_OK && hinted) {
+    const int64_t cand = r->counters.candidates + r->counters.candidates / 4 + 1024;
+    const int64_t keys = r->counters.keys + r->counters.keys / 4 + 1024;
+    int64_t table = 1 << 12;
+    while (table < keys + keys / 2) table <<= 1;
+    if (table <= kMaxTable && cand < 0xFFFFFFFFll) {
+      const int64_t k = std::min<int64_t>(keys, table);
+      const int64_t paths = k + r->n_rx_phys + diffraction_slots(r);
+      ctx->caps_hint[key] = {cand, k, table, paths};
+    }
+  }
+  return rc;
 }
 
 nrt_status run_field(nrt_result* r) {
