@@ -153,3 +153,39 @@ def test_trace_argument_checks(ctx, room):
         sc.trace(room.tx, room.rx, nrt.default_trace_params(key_capacity=3000, **ok))
     # a valid call still works afterwards on the same context
     sc.trace(room.tx, room.rx, nrt.default_trace_params(**ok)).close()
+
+
+def _same_paths(a, b):
+    for k in ("key_hi", "key_lo", "rep", "rx", "a", "tau"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_capacity_hints_give_the_exact_result(office):
+    """A context sizes the first simulation of a shape exactly (one host
+    round trip) and later ones from that run's counts + 25%, without waiting
+    for the host.  A hinted run, and a run that outgrows its hint (TX far
+    above the office first, so the hint is small) and is redone with exact
+    sizes, both equal a fresh context's exact run bit for bit."""
+    kp = dict(max_depth=5, capture=nrt.CAPTURE_VIS, diffuse=1, n_rays=60000, rep_tries=0)
+    p = nrt.default_trace_params(**kp)
+    ctx_a = nrt.Context(0)
+    sa = nrt.Scene(ctx_a, office.pos, office.nrm, office.surf, office.mat, r_p=0.015)
+    sa.set_materials(office.eps_r, office.sigma, office.scat)
+    far = sa.trace(np.array([10.0, 5.0, 200.0], np.float32), office.rx, p)
+    assert far.counts()[1]["candidates"] < 100
+    far.close()
+    grown = sa.trace(office.tx, office.rx, p)  # outgrows the hint: redone exactly
+    hinted = sa.trace(office.tx, office.rx, p)  # sized from the previous run
+    assert hinted.times()["sizing_wait"] < 0.05
+    ctx_b = nrt.Context(0)
+    sb = nrt.Scene(ctx_b, office.pos, office.nrm, office.surf, office.mat, r_p=0.015)
+    sb.set_materials(office.eps_r, office.sigma, office.scat)
+    ref = sb.trace(office.tx, office.rx, p)
+    R = ref.paths()
+    assert len(R["rep"]) > 1000
+    for r in (grown, hinted):
+        _same_paths(r.paths(), R)
+        np.testing.assert_array_equal(r.power(), ref.power())
+        c, cr = r.counts()[1], ref.counts()[1]
+        for k in ("candidates", "keys", "paths", "segments"):
+            assert c[k] == cr[k], k
