@@ -1081,6 +1081,9 @@ __global__ void __launch_bounds__(kTraceThreads, 6)
 // Coordinates are taken relative to the RX to keep float magnitudes small.
 // Returns whether the candidate validates; with P, its path record.  Used by
 // the item pass and by the per-key finish, so both take the same decisions.
+// best (the item pass): the key's lowest valid rank so far; once it drops
+// below this candidate's rank the candidate cannot be the key's path, so it
+// stops before its next cast (exact: only the lowest valid rank is kept).
 // stage at which a candidate ended (counters): before any cast, at its
 // first leg's cast, later (or valid)
 enum : int { kSpecNoCast = 0, kSpecLeg1 = 1, kSpecLater = 2 };
@@ -1090,7 +1093,8 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
                                                uint32_t row, int* my_stk, float* my_tstk,
                                                uint32_t* err, unsigned long long& casts,
                                                unsigned long long& pruned, PathRec* P,
-                                               int* stage = nullptr) {
+                                               int* stage = nullptr, const uint32_t* best = nullptr,
+                                               uint32_t kid = 0, uint32_t rank = 0) {
   const int j = (int)(hi >> 56);
   const int k = (int)((hi >> 52) & 7);
   const float3 rxp = xyz(A.rx[C.batch ? 0 : j]);
@@ -1110,6 +1114,7 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
   const unsigned long long casts0 = casts;
   if (stage) *stage = kSpecNoCast;
   for (int attempt = 0;; ++attempt) {
+    if (best && attempt > 0 && *(volatile const uint32_t*)(best + kid) < rank) return false;
     float3 img[kMaxDepth + 1];
     img[0] = txl;
     for (int m = 0; m < k; ++m)
@@ -1141,6 +1146,7 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
       // surface or nothing)
       // and a leg's search ends where its ray leaves that box: a hit beyond
       // is on another surface, which ends the candidate as nothing found does
+      if (best && m > 1 && *(volatile const uint32_t*)(best + kid) < rank) return false;
       float t_exit;
       if (!ray_meets_label(S, org, dir, C.t_min, lab[m - 1], &t_exit)) {
         ++pruned;
@@ -1172,6 +1178,7 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
     }
     break;
   }
+  if (best && *(volatile const uint32_t*)(best + kid) < rank) return false;
   // last leg to the RX
   const float3 last = f3(0.f, 0.f, 0.f) - I[k];
   const float sl = len3(last);
@@ -1281,7 +1288,8 @@ __global__ void __launch_bounds__(kTraceThreads, 5)
     NRT_GUARD(((hi >> 52) & 7) >= 1 && ((hi >> 52) & 7) <= (uint64_t)C.max_depth, 12, hi >> 52)
     int stage = kSpecLater;
     ++evaluated;
-    if (spec_candidate(S, C, A, hi, lo, row, my_stk, my_tstk, err, casts, pruned, nullptr, &stage))
+    if (spec_candidate(S, C, A, hi, lo, row, my_stk, my_tstk, err, casts, pruned, nullptr, &stage,
+                       best, kid, rank))
       atomicMin(best + kid, rank);
     no_cast += stage == kSpecNoCast;
     at_leg1 += stage == kSpecLeg1;
