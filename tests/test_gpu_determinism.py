@@ -3,7 +3,8 @@ keys, to lanes through atomic counters, so the order in which work is done
 differs between runs; the outputs must not.  Two traces of the same inputs
 give bit-identical paths (keys, representatives, points, coefficients,
 delays), counts and received power, with diffuse scattering, diffraction and
-the vector model on."""
+the vector model on (the validation cast count, a measure of work that the
+early stop of losing candidates makes timing-dependent, within 1%)."""
 import numpy as np
 import pytest
 
@@ -30,7 +31,11 @@ def test_office_trace_is_bit_identical_across_runs(office):
     for k in pa:
         assert np.array_equal(pa[k], pb[k]), k
     assert np.array_equal(na, nb)
-    for k in ("segments", "vis_casts", "validation_casts", "candidates", "keys", "paths",
-              "diffraction_casts"):
+    for k in ("segments", "vis_casts", "candidates", "keys", "paths", "diffraction_casts"):
         assert ca[k] == cb[k], k
+    # the number of validation casts is work, not output: a candidate ranked
+    # after its key's lowest valid one stops at its next cast, and when that
+    # happens depends on timing; it stays within the run's bounds
+    assert 0 < ca["validation_casts"] and 0 < cb["validation_casts"]
+    assert abs(ca["validation_casts"] - cb["validation_casts"]) <= 0.01 * ca["validation_casts"]
     assert np.array_equal(wa, wb)
