@@ -305,6 +305,7 @@ def batch_groups(args, scene, tx, rx, budgets, p, packet, schedule, stream, flus
     import torch
 
     n = len(budgets)
+    groups = max(1, min(groups, n))  # no empty group for small batches
     bounds = np.linspace(0, n, groups + 1).astype(int)
     plans = [scene.trace_batch(tx[a:b], rx, budgets[a:b], p, packet=packet, schedule=schedule,
                                use_graph=True) for a, b in zip(bounds[:-1], bounds[1:])]
