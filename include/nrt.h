@@ -366,7 +366,9 @@ nrt_status nrt_field_read(const nrt_result* result, float* power_per_rx);
 /* Received power per RX into DEVICE memory: power is a device double[n_rx]
  * (the FP64 sums of nrt_field_read before their rounding to float), copied
  * on the context stream without synchronising, so that a learning loop
- * (Sec. III-B) can form its loss on the GPU.  Errors: NRT_ERR_ARG for NULL;
+ * (Sec. III-B) can form its loss on the GPU.  The call makes the context's
+ * device current for the copy and restores the caller's current device.
+ * Errors: NRT_ERR_ARG for NULL;
  * NRT_ERR_STATE before the field was computed; NRT_ERR_CUDA. */
 nrt_status nrt_field_read_device(const nrt_result* result, double* power);
 

@@ -925,8 +925,13 @@ nrt_status nrt_field_read_device(const nrt_result* r, double* power) {
     ctx->last_error = "field not computed (set materials, then nrt_field)";
     return NRT_ERR_STATE;
   }
-  NRT_CUDA_TRY(ctx, cudaMemcpyAsync(power, r->power, (size_t)r->n_rx * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, ctx->stream));
+  int cur = 0;
+  NRT_CUDA_TRY(ctx, cudaGetDevice(&cur));
+  NRT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const cudaError_t e = cudaMemcpyAsync(power, r->power, (size_t)r->n_rx * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, ctx->stream);
+  cudaSetDevice(cur);
+  NRT_CUDA_TRY(ctx, e);
   return NRT_OK;
 }
 
