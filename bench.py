@@ -573,6 +573,22 @@ def score_only(args):
     net.close()
 
 
+def batch_only(args):
+    """Only the robot-trajectory batch measurement (one GPU): one JSON line
+    with the batch section (a fixed workload for profiling the batch)."""
+    import torch
+    from paper_2507_04021_gb300 import inputs, nrt
+
+    stream = torch.cuda.Stream()
+    ctx = nrt.Context(0, stream=stream.cuda_stream)
+    o = inputs.office_scene()
+    scene = nrt.Scene(ctx, o.pos, o.nrm, o.surf, o.mat, rho=0.0625, r_p=0.015, lambda_d=100.0)
+    scene.set_materials(o.eps_r, o.sigma, o.scat)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    print(json.dumps({"batch": batch_bench(args, scene, o, 0, stream, flush)}), flush=True)
+    scene.close()
+
+
 def ours(args):
     import torch
     from paper_2507_04021_gb300 import inputs, nrt
@@ -832,11 +848,15 @@ def main():
                          "diffraction, intersection or r_p measurements")
     ap.add_argument("--score-only", action="store_true",
                     help="only the proposal network's scoring of the 1M-direction launch")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="only the robot-trajectory batch measurement (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
     elif args.score_only:
         score_only(args)
+    elif args.batch_only:
+        batch_only(args)
     else:
         ours(args)
 
