@@ -777,6 +777,11 @@ def ours(args):
         "counts": {k: counts[k] for k in ("segments", "vis_casts", "validation_casts",
                                           "diffuse_casts", "candidates", "keys", "paths",
                                           "n_dps")},
+        # `value` counts every cast (trace, visibility, LOS, validation), so
+        # removing casts that cannot succeed lowers it; these count the
+        # simulations and the traced segments of the launched rays alone
+        "throughput": {"simulations_per_s": 1000.0 / (total_ms / args.steps),
+                       "traced_segments_per_s": counts["segments"] / (total_ms / args.steps / 1000.0)},
     }
     # channel frequency response of the last simulation (129 frequencies over
     # 1.5 GHz, all receivers) and its Eq. 5 gradient, device-timed
