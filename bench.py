@@ -667,11 +667,13 @@ def ours(args):
     sampler.start()
     torch.cuda.synchronize()
     evs, casts, trace_ms, launches, phases = [], 0, [], 0, []
+    traced = 0
     last = None
     for _ in range(args.steps):
         r, e0, e1 = step()
         _, c = r.counts()
         casts += c["segments"] + c["vis_casts"] + c["los_casts"] + c["validation_casts"]
+        traced += c["segments"]
         t = r.times()
         trace_ms.append(t["trace"])
         phases.append(t)
@@ -687,11 +689,11 @@ def ours(args):
     total_ms = float(sum(a.elapsed_time(b) for a, b in evs))
     counts = last.counts()[1]
     if dist:
-        t = torch.tensor([total_ms, float(casts)], device=dev, dtype=torch.float64)
+        t = torch.tensor([total_ms, float(casts), float(traced)], device=dev, dtype=torch.float64)
         tm = t.clone()
         dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
         dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, casts = float(tm[0]), float(t[1])
+        total_ms, casts, traced = float(tm[0]), float(t[1]), float(t[2])
     value = casts / (total_ms / 1000.0)
 
     # end to end through the C ABI with host buffers: TX/RX from host memory in,
@@ -781,7 +783,7 @@ def ours(args):
         # removing casts that cannot succeed lowers it; these count the
         # simulations and the traced segments of the launched rays alone
         "throughput": {"simulations_per_s": 1000.0 / (total_ms / args.steps),
-                       "traced_segments_per_s": counts["segments"] / (total_ms / args.steps / 1000.0)},
+                       "traced_segments_per_s": traced / (total_ms / 1000.0)},
     }
     # channel frequency response of the last simulation (129 frequencies over
     # 1.5 GHz, all receivers) and its Eq. 5 gradient, device-timed
