@@ -317,7 +317,14 @@ nrt_status nrt_cast(nrt_scene* scene, const float* o, const float* d, int64_t n,
  * x | y<<16 | z<<32 (each taken modulo 2^16); diffracted: hi = rx << 56 |
  * 1 << 52 | 1 << 51, lo = edge index.  The outputs do not depend on the order
  * in which the GPU hands rays and keys to its lanes: the same inputs give
- * bit-identical paths.
+ * bit-identical paths (the counter of validation casts, a measure of work,
+ * may differ slightly: a candidate stops once its key has a lower valid
+ * rank).  Buffer sizing: with key_capacity and cand_capacity at 0, the first
+ * simulation of a shape (scene, rays, receivers, capture, depth, diffuse,
+ * diffraction, launch) on a context sizes the candidate and key buffers from
+ * an exact count (one host round trip); later ones reuse that run's counts
+ * plus 25% and enqueue everything at once, and a run that outgrows them is
+ * redone with exact sizes inside the same call, with the same result.
  * Errors: NRT_ERR_ARG, NRT_ERR_OOM, NRT_ERR_OVERFLOW (hash table or candidate
  * buffer too small: raise key_capacity / cand_capacity), NRT_ERR_CUDA. */
 nrt_status nrt_trace(nrt_scene* scene, const float* tx, const float* rx, int n_rx,
