@@ -159,9 +159,14 @@ __device__ __forceinline__ bool ray_meets_label(const SceneView& S, float3 o, fl
 // weighted: also compute the Eq. 3 point and the weighted normal.
 // stack / tstack point at this thread's column of a shared array laid out
 // [depth][blockDim.x] (stride = blockDim.x) so that threads hit distinct banks.
+// kSmem: how many entries that array holds; deeper entries, up to
+// kStackDepth, go to a per-thread local array (a caller with register room
+// for more blocks keeps fewer in shared memory; the default keeps all).
+template <int kSmem = kStackDepth>
 __device__ __forceinline__ Hit cast_ray(bool any_hit, const SceneView& S, float3 o, float3 d,
                                        int skip, float tmin, float tmax, bool weighted, int* stack,
                                        float* tstack, int stride, uint32_t* err) {
+  constexpr bool kTwoLevel = kSmem < kStackDepth;
   Hit h;
   h.idx = -1;
   h.dps = -1;
@@ -169,6 +174,8 @@ __device__ __forceinline__ Hit cast_ray(bool any_hit, const SceneView& S, float3
   h.tbar = 0.0f;
   h.n = f3(0.f, 0.f, 0.f);
   h.labels = 0;
+  int lstk[kTwoLevel ? kStackDepth - kSmem : 1];
+  float ltstk[kTwoLevel ? kStackDepth - kSmem : 1];
   float best_t = tmax;
   int best_idx = -1;
   int best_leaf = -1;
@@ -232,8 +239,13 @@ __device__ __forceinline__ Hit cast_ray(bool any_hit, const SceneView& S, float3
             over = true;
             break;
           }
-          stack[sp * stride] = ce[c];
-          tstack[sp * stride] = te[c];
+          if (!kTwoLevel || sp < kSmem) {
+            stack[sp * stride] = ce[c];
+            tstack[sp * stride] = te[c];
+          } else {
+            lstk[sp - kSmem] = ce[c];
+            ltstk[sp - kSmem] = te[c];
+          }
           ++sp;
         }
         if (over) {
@@ -284,8 +296,9 @@ __device__ __forceinline__ Hit cast_ray(bool any_hit, const SceneView& S, float3
     bool found = false;
     while (sp > 0) {
       --sp;
-      if (tstack[sp * stride] <= best_t) {
-        node = stack[sp * stride];
+      const bool in_smem = !kTwoLevel || sp < kSmem;
+      if ((in_smem ? tstack[sp * stride] : ltstk[sp - kSmem]) <= best_t) {
+        node = in_smem ? stack[sp * stride] : lstk[sp - kSmem];
         found = true;
         break;
       }

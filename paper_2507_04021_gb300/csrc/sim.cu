@@ -220,7 +220,14 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
     vis_kernel(SceneView S, SimConst C, const float4* __restrict__ rx,
                const float4* __restrict__ recv, uint32_t* __restrict__ vis,
                unsigned long long* ctr, float margin) {
-  NRT_STACK_DECL
+  // 12 stack entries in shared memory (the rest in local memory): the
+  // kernel's registers allow more blocks per SM than 27 entries would
+  constexpr int kVisSmem = 12;
+  __shared__ int stk[kVisSmem * kTraceThreads];
+  __shared__ float tstk[kVisSmem * kTraceThreads];
+  int* my_stk = stk + threadIdx.x;
+  float* my_tstk = tstk + threadIdx.x;
+  uint32_t* err = (uint32_t*)(ctr + kCtrErr);
   const int64_t per_rx = C.vis_words * 32;
   const int64_t total = (int64_t)C.n_rx * per_rx;
   unsigned long long casts = 0;
@@ -239,8 +246,8 @@ __global__ void __launch_bounds__(kTraceThreads, 8)
         if (tmax <= C.t_min) {
           bit = true;
         } else {
-          const Hit h = cast_ray(false, S, o, (1.0f / s) * v, -1, C.t_min, tmax, false, my_stk,
-                                        my_tstk, kTraceThreads, err);
+          const Hit h = cast_ray<kVisSmem>(false, S, o, (1.0f / s) * v, -1, C.t_min, tmax, false,
+                                           my_stk, my_tstk, kTraceThreads, err);
           ++casts;
           bit = h.idx < 0 || h.dps == d;
         }
