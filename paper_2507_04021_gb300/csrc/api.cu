@@ -415,7 +415,7 @@ nrt_status nrt_trace(nrt_scene* s, const float* tx, const float* rx, int n_rx,
       p->n_rays > (int64_t)0xFFFFFFFE || p->rep_tries < 0 || p->kappa < 0 ||
       !(p->freq > 0.f) || !(p->t_min >= 0.f) || (p->capture != 0 && p->capture != 1) ||
       p->pol < NRT_POL_TE || p->pol > NRT_POL_VECTOR || (p->diffraction != 0 && p->diffraction != 1) ||
-      (p->capture == NRT_CAPTURE_SPHERE && p->diffuse)) {
+      p->spec_waves < 0 || p->spec_waves > 2 || (p->capture == NRT_CAPTURE_SPHERE && p->diffuse)) {
     ctx->last_error = "invalid trace parameters";
     return NRT_ERR_ARG;
   }
@@ -708,7 +708,7 @@ nrt_status nrt_trace_batch(nrt_scene* s, const float* tx, const float* rx, const
   if (p->capture != NRT_CAPTURE_VIS || p->max_depth < 1 || p->max_depth > kMaxDepth ||
       p->rep_tries < 0 || p->kappa < 0 || !(p->freq > 0.f) ||
       p->pol < NRT_POL_TE || p->pol > NRT_POL_VECTOR ||
-      (p->diffraction != 0 && p->diffraction != 1)) {
+      (p->diffraction != 0 && p->diffraction != 1) || p->spec_waves < 0 || p->spec_waves > 2) {
     ctx->last_error = "invalid batch trace parameters (visibility capture required)";
     return NRT_ERR_ARG;
   }

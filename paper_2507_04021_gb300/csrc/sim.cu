@@ -1095,6 +1095,79 @@ __global__ void __launch_bounds__(kTraceThreads, 6)
 // first leg's cast, later (or valid)
 enum : int { kSpecNoCast = 0, kSpecLeg1 = 1, kSpecLater = 2 };
 
+// Image-method points of one attempt (Eq. 1), relative to the RX: I[0] the
+// TX (txl), I[k + 1] the RX (the origin), I[1..k] on the planes (Pp, Pn)
+// found backwards from the RX through the mirrored TX images; false when a
+// leg is parallel to its plane or a point's neighbours lie on opposite
+// sides of its plane (no specular reflection there).  Shared by every
+// refinement path so that all take the same decisions.
+__device__ __forceinline__ bool spec_points(float3 txl, const float3* Pp, const float3* Pn, int k,
+                                            float3* I) {
+  float3 img[kMaxDepth + 1];
+  img[0] = txl;
+  for (int m = 0; m < k; ++m)
+    img[m + 1] = img[m] - (2.0f * dot3(img[m] - Pp[m], Pn[m])) * Pn[m];
+  I[0] = txl;
+  I[k + 1] = f3(0.f, 0.f, 0.f);
+  float3 tgt = f3(0.f, 0.f, 0.f);
+  for (int m = k; m >= 1; --m) {
+    const float3 dir = img[m] - tgt;
+    const float den = dot3(dir, Pn[m - 1]);
+    if (den == 0.0f) return false;
+    const float u = dot3(Pp[m - 1] - tgt, Pn[m - 1]) / den;
+    I[m] = tgt + u * dir;
+    tgt = I[m];
+  }
+  for (int m = 1; m <= k; ++m) {
+    const float sa = dot3(I[m - 1] - I[m], Pn[m - 1]);
+    const float sb = dot3(I[m + 1] - I[m], Pn[m - 1]);
+    if (!(sa * sb > 0.0f)) return false;
+  }
+  return true;
+}
+
+// Leg m of an attempt: from I[m - 1] towards I[m], in scene coordinates.
+__device__ __forceinline__ void spec_leg_ray(const float3* I, int m, float3 rxp, float3* org,
+                                             float3* dir) {
+  *org = I[m - 1] + rxp;
+  *dir = unit3(I[m] - I[m - 1]);
+}
+
+// Whether a leg's closest hit (on the key's surface) is the interaction the
+// plane predicts: its weighted normal within t_a of the plane's and its
+// Eq. 3 point within t_d of the plane (Table I thresholds).  *qh receives the
+// hit point relative to the RX, the plane point of a retry.
+__device__ __forceinline__ bool spec_hit_fits(const SimConst& C, float3 org, float3 dir, float3 rxp,
+                                              float tbar, float3 hn, float3 Im, float3 Pnm,
+                                              float3* qh) {
+  *qh = (org + tbar * dir) - rxp;
+  const float c = fminf(1.0f, fabsf(dot3(Pnm, hn)));
+  const float dist = fabsf(dot3(*qh - Im, Pnm));
+  return c >= C.cos_ta && dist <= C.t_d;
+}
+
+// The final leg: from I[k] to the RX (an any-hit cast over its length).
+__device__ __forceinline__ void spec_final_ray(const float3* I, int k, float3 rxp, float3* org,
+                                               float3* dir, float* len) {
+  const float3 last = f3(0.f, 0.f, 0.f) - I[k];
+  *len = len3(last);
+  *org = I[k] + rxp;
+  *dir = (1.0f / *len) * last;
+}
+
+// A candidate's starting planes (its own interaction points and weighted
+// normals, relative to the RX) and the key's surface label per interaction.
+__device__ __forceinline__ void spec_load(const ValArgs& A, uint64_t hi, uint64_t lo, uint32_t row,
+                                          int k, float3 rxp, float3* Pp, float3* Pn, uint32_t* lab) {
+  for (int m = 0; m < k; ++m) {
+    const int64_t b = A.R.at(m, row);
+    Pp[m] = xyz(A.R.q[b]) - rxp;
+    Pn[m] = xyz(A.R.n[b]);
+  }
+  for (int m = 0; m < 4; ++m) lab[m] = (uint32_t)((lo >> (16 * m)) & 0xFFFF);
+  lab[4] = (uint32_t)(hi & 0xFFFF);
+}
+
 __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimConst& C,
                                                const ValArgs& A, uint64_t hi, uint64_t lo,
                                                uint32_t row, int* my_stk, float* my_tstk,
@@ -1107,14 +1180,8 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
   const float3 rxp = xyz(A.rx[C.batch ? 0 : j]);
   const float3 txl = tx_of(C, j) - rxp;
   float3 Pp[kMaxDepth], Pn[kMaxDepth];
-  for (int m = 0; m < k; ++m) {
-    const int64_t b = A.R.at(m, row);
-    Pp[m] = xyz(A.R.q[b]) - rxp;
-    Pn[m] = xyz(A.R.n[b]);
-  }
   uint32_t lab[kMaxDepth];
-  for (int m = 0; m < 4; ++m) lab[m] = (uint32_t)((lo >> (16 * m)) & 0xFFFF);
-  lab[4] = (uint32_t)(hi & 0xFFFF);
+  spec_load(A, hi, lo, row, k, rxp, Pp, Pn, lab);
   float3 I[kMaxDepth + 2];
   uint32_t vmats[kMaxDepth];
   int prev_dps = -1;
@@ -1122,32 +1189,13 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
   if (stage) *stage = kSpecNoCast;
   for (int attempt = 0;; ++attempt) {
     if (best && attempt > 0 && *(volatile const uint32_t*)(best + kid) < rank) return false;
-    float3 img[kMaxDepth + 1];
-    img[0] = txl;
-    for (int m = 0; m < k; ++m)
-      img[m + 1] = img[m] - (2.0f * dot3(img[m] - Pp[m], Pn[m])) * Pn[m];
-    I[0] = txl;
-    I[k + 1] = f3(0.f, 0.f, 0.f);
-    float3 tgt = f3(0.f, 0.f, 0.f);
-    for (int m = k; m >= 1; --m) {
-      const float3 dir = img[m] - tgt;
-      const float den = dot3(dir, Pn[m - 1]);
-      if (den == 0.0f) return false;
-      const float u = dot3(Pp[m - 1] - tgt, Pn[m - 1]) / den;
-      I[m] = tgt + u * dir;
-      tgt = I[m];
-    }
-    for (int m = 1; m <= k; ++m) {
-      const float sa = dot3(I[m - 1] - I[m], Pn[m - 1]);
-      const float sb = dot3(I[m + 1] - I[m], Pn[m - 1]);
-      if (!(sa * sb > 0.0f)) return false;
-    }
+    if (!spec_points(txl, Pp, Pn, k, I)) return false;
     prev_dps = -1;
     int fail_m = -1;
     float3 fq = f3(0.f, 0.f, 0.f), fn = f3(0.f, 0.f, 0.f);
     for (int m = 1; m <= k; ++m) {
-      const float3 org = I[m - 1] + rxp;
-      const float3 dir = unit3(I[m] - I[m - 1]);
+      float3 org, dir;
+      spec_leg_ray(I, m, rxp, &org, &dir);
       // a leg whose ray cannot reach the key's surface at this interaction
       // ends the candidate without a cast (its closest hit would be another
       // surface or nothing)
@@ -1165,11 +1213,10 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
       if (stage) *stage = casts - casts0 == 1 ? kSpecLeg1 : kSpecLater;
       if (h.idx < 0 || (h.labels & 0xFFFFu) != lab[m - 1]) return false;
       if (stage) *stage = kSpecLater;
-      const float3 qh = (org + h.tbar * dir) - rxp;
-      const float c = fminf(1.0f, fabsf(dot3(Pn[m - 1], h.n)));
-      const float dist = fabsf(dot3(qh - I[m], Pn[m - 1]));
+      float3 qh;
+      const bool fits = spec_hit_fits(C, org, dir, rxp, h.tbar, h.n, I[m], Pn[m - 1], &qh);
       vmats[m - 1] = (h.labels >> 16) & 0xFFu;
-      if (!(c >= C.cos_ta && dist <= C.t_d)) {
+      if (!fits) {
         fail_m = m;
         fq = qh;
         fn = h.n;
@@ -1187,10 +1234,11 @@ __device__ __forceinline__ bool spec_candidate(const SceneView& S, const SimCons
   }
   if (best && *(volatile const uint32_t*)(best + kid) < rank) return false;
   // last leg to the RX
-  const float3 last = f3(0.f, 0.f, 0.f) - I[k];
-  const float sl = len3(last);
-  const Hit hf = cast_ray(true, S, I[k] + rxp, (1.0f / sl) * last, prev_dps, C.t_min, sl, false,
-                                my_stk, my_tstk, kTraceThreads, err);
+  float3 forg, fdir;
+  float sl;
+  spec_final_ray(I, k, rxp, &forg, &fdir, &sl);
+  const Hit hf = cast_ray(true, S, forg, fdir, prev_dps, C.t_min, sl, false, my_stk, my_tstk,
+                          kTraceThreads, err);
   ++casts;
   if (stage) *stage = kSpecLater;
   if (hf.idx >= 0) return false;
@@ -1242,7 +1290,7 @@ constexpr uint32_t kHeadItems = 2048;
 __global__ void spec_count_kernel(KeyState K, const uint32_t* __restrict__ list,
                                   const unsigned long long* __restrict__ n_list_p, int rep_tries,
                                   uint32_t* __restrict__ cnt_h, uint32_t* __restrict__ cnt_t,
-                                  uint32_t* __restrict__ best) {
+                                  uint32_t* __restrict__ best, uint32_t* __restrict__ hleft) {
   const int64_t n = (int64_t)*n_list_p;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
@@ -1252,6 +1300,7 @@ __global__ void spec_count_kernel(KeyState K, const uint32_t* __restrict__ list,
     cnt_h[q] = min(m, kHeadItems);
     cnt_t[q] = m - min(m, kHeadItems);
     best[kid] = kNone;
+    hleft[kid] = min(m, kHeadItems);
   }
 }
 
@@ -1323,6 +1372,433 @@ __global__ void __launch_bounds__(kTraceThreads, 5)
   count_add(ctr + kCtrSpecItems, evaluated);
   count_add(ctr + kCtrSpecNoCast, no_cast);
   count_add(ctr + kCtrSpecLeg1, at_leg1);
+}
+
+// Specular refinement as waves.  The item pass above runs each candidate's
+// whole retry chain in one lane: its refinement state (planes, image-method
+// points) stays in registers across every cast, so the pass runs at 96
+// registers and 5 blocks per SM, and lanes set up new items while their
+// neighbours traverse.  Here a candidate's state lives in one of up to
+// kSpecSlots slots in device memory, and each wave is three launches:
+//   spec_wave_advance_kernel: consumes the last wave's hit of every live slot
+//     and moves its candidate on -- to its next leg, a retry with the hit's
+//     plane, its final leg, or its end -- with the helpers spec_candidate
+//     uses and the same early stops (a candidate stops before its next cast
+//     once its key's lowest valid rank is below its own); a slot whose
+//     candidate ended takes the next items in item order until one needs a
+//     cast; the next leg of every live slot is queued;
+//   spec_wave_cast_kernel: the queued final legs (any hit; first, so that
+//     the long ones overlap the rest) and legs (closest hit, weighted), in a
+//     kernel that holds no refinement state (64 registers, 8 blocks per SM).
+// The decisions per candidate are those of spec_candidate, so the lowest
+// valid rank of every key -- the only thing kept -- is the same.
+// With millions of slots every head item is taken within the first waves,
+// before most keys have found their lowest valid rank; a tail item whose
+// key still has head candidates in slots is therefore deferred to a second
+// list, which opens once the first is exhausted and fewer than one slot in
+// 16 holds a head candidate.  Once every item is taken and a wave queues
+// fewer than kHandoffLegs casts, the waves stop (the later launches return
+// at once) and spec_resume_kernel runs the candidates still in slots to
+// their end, one lane each, without a kernel boundary per leg; the item
+// pass then takes whatever items the kSpecWaves waves left (none, unless
+// the work outgrew them).
+constexpr int64_t kSpecSlots = 1 << 22;
+constexpr int kSpecWaves = 32;
+// automatic schedule: waves from this candidate capacity on (below it the
+// fixed cost of the waves -- two launches each, a few hundred microseconds
+// of tail per wave -- outweighs the faster casts)
+constexpr int64_t kWaveMinCand = 1 << 21;
+constexpr unsigned long long kHandoffLegs = 1ull << 18;
+
+enum : int { kSlotEmpty = 0, kSlotLeg = 1, kSlotFinal = 2 };
+
+// wave counters (index + wave % 3): legs queued, final legs queued, their
+// fetch counters; the deferred list's count, fetch counter and open flag;
+// the stop flag; the resume pass's fetch counter; head candidates placed in
+// slots and ended there
+enum : int { kWcLegs = 0, kWcFinal = 3, kWcLegFetch = 6, kWcFinalFetch = 9, kWcDefer = 12,
+             kWcDeferFetch = 13, kWcDeferOpen = 14, kWcStop = 15, kWcResume = 16,
+             kWcHeadsIn = 17, kWcHeadsOut = 18, kWcN = 19 };
+
+struct SpecSlots {
+  uint32_t* kid;
+  uint32_t* rank;
+  ulonglong2* key;  // key words (hi, lo)
+  int4* ctl;        // attempt, leg m, DPS of the last hit (-1), phase
+  float* pl;        // [6 kMaxDepth][n]: plane t's point (3 floats), normal (3)
+  float* im;        // [3 kMaxDepth][n]: image-method points I[1..k]
+  float4* hq;       // last hit: tbar, weighted normal
+  int2* hd;         // last hit: DPS (-1: nothing hit), labels
+  float4* q;        // queued legs [2][n]: (origin, t_max), (direction, DPS skipped)
+  uint32_t* qs;     // their slots
+  float4* qa;       // queued final legs, same layout
+  uint32_t* qas;
+  uint32_t* defer;  // deferred tail items [cand]
+  uint32_t* hleft;  // per key: head candidates not yet finished
+  unsigned long long* wc;  // kWcN counters
+  int64_t n;
+};
+
+// component block b (3 floats) of slot s in a [3 b + c][n] array
+__device__ __forceinline__ float3 slot_f3(const float* a, int64_t n, int64_t s, int b) {
+  const float* p = a + (int64_t)(3 * b) * n + s;
+  return f3(p[0], p[n], p[2 * n]);
+}
+
+__device__ __forceinline__ void slot_put3(float* a, int64_t n, int64_t s, int b, float3 v) {
+  float* p = a + (int64_t)(3 * b) * n + s;
+  p[0] = v.x;
+  p[n] = v.y;
+  p[2 * n] = v.z;
+}
+
+// surface label of interaction t (0-based) of a specular key
+__device__ __forceinline__ uint32_t key_label(uint64_t hi, uint64_t lo, int t) {
+  return t < 4 ? (uint32_t)((lo >> (16 * t)) & 0xFFFF) : (uint32_t)(hi & 0xFFFF);
+}
+
+// one queue entry per live slot: warp-aggregated position in this wave's queue
+__device__ __forceinline__ void slot_queue(float4* q, uint32_t* qs, unsigned long long* count,
+                                           int64_t s, float3 org, float t_max, float3 dir,
+                                           int skip) {
+  const unsigned mask = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  const int64_t i = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+  q[2 * i] = make_float4(org.x, org.y, org.z, t_max);
+  q[2 * i + 1] = make_float4(dir.x, dir.y, dir.z, __int_as_float(skip));
+  qs[i] = (uint32_t)s;
+}
+
+// a leg or final leg to cast next
+struct SlotRay {
+  float3 org, dir;
+  float t_max;
+  int skip;
+};
+
+struct SpecCounts {
+  unsigned long long pruned = 0, evaluated = 0, no_cast = 0, at_leg1 = 0;
+  unsigned long long heads_in = 0, heads_out = 0;
+};
+
+// appends c to the deferred list (warp-aggregated)
+__device__ __forceinline__ void defer_push(const SpecSlots& Q, uint32_t c) {
+  const unsigned mask = __activemask();
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(Q.wc + kWcDefer, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  Q.defer[base + __popc(mask & ((1u << lane) - 1u))] = c;
+}
+
+// Consumes the hit of slot s's last cast and moves its candidate on, as
+// spec_candidate does after that cast; returns the phase of its next cast
+// (its ray in *ray), or kSlotEmpty when the candidate ended.  The slot's
+// phase is written either way; a head candidate that ended is counted off
+// its key's hleft.
+__device__ __forceinline__ int slot_advance(const SceneView& S, const SimConst& C,
+                                            const ValArgs& A, const SpecSlots& Q, int64_t s,
+                                            uint32_t* best, SlotRay* ray, SpecCounts& cnt) {
+  const int4 ctl = Q.ctl[s];
+  int attempt = ctl.x, m = ctl.y, prev = ctl.z;
+  const uint32_t kid = Q.kid[s], rank = Q.rank[s];
+  int next = kSlotEmpty;
+  if (ctl.w == kSlotFinal) {
+    if (Q.hd[s].x < 0) atomicMin(best + kid, rank);  // nothing in the way: valid
+  } else {
+    const ulonglong2 kw = Q.key[s];
+    const int j = (int)(kw.x >> 56);
+    const int k = (int)((kw.x >> 52) & 7);
+    const float3 rxp = xyz(A.rx[C.batch ? 0 : j]);
+    const float3 txl = tx_of(C, j) - rxp;
+    const int2 hd = Q.hd[s];
+    if (hd.x < 0 || ((uint32_t)hd.y & 0xFFFFu) != key_label(kw.x, kw.y, m - 1)) {
+      cnt.at_leg1 += attempt == 0 && m == 1;  // ended at its first cast
+    } else {
+      float3 J[2];  // I[m - 1], I[m]
+      J[0] = m == 1 ? txl : slot_f3(Q.im, Q.n, s, m - 2);
+      J[1] = slot_f3(Q.im, Q.n, s, m - 1);
+      const float4 hq = Q.hq[s];
+      const float3 hn = f3(hq.y, hq.z, hq.w);
+      float3 org, dir, qh;
+      spec_leg_ray(J, 1, rxp, &org, &dir);
+      if (!spec_hit_fits(C, org, dir, rxp, hq.x, hn, J[1], slot_f3(Q.pl, Q.n, s, 2 * m - 1), &qh)) {
+        if (attempt < C.kappa) {
+          ++attempt;  // retry with the hit's plane
+          if (!(*(volatile const uint32_t*)(best + kid) < rank)) {
+            float3 Pp[kMaxDepth], Pn[kMaxDepth], I[kMaxDepth + 2];
+            for (int t = 0; t < k; ++t) {
+              Pp[t] = slot_f3(Q.pl, Q.n, s, 2 * t);
+              Pn[t] = slot_f3(Q.pl, Q.n, s, 2 * t + 1);
+            }
+            Pp[m - 1] = qh;
+            Pn[m - 1] = hn;
+            if (spec_points(txl, Pp, Pn, k, I)) {
+              slot_put3(Q.pl, Q.n, s, 2 * m - 2, qh);
+              slot_put3(Q.pl, Q.n, s, 2 * m - 1, hn);
+              for (int t = 1; t <= k; ++t) slot_put3(Q.im, Q.n, s, t - 1, I[t]);
+              m = 1;
+              prev = -1;
+              spec_leg_ray(I, 1, rxp, &ray->org, &ray->dir);
+              next = kSlotLeg;
+            }
+          }
+        }
+      } else {
+        prev = hd.x;
+        ++m;
+        if (!(*(volatile const uint32_t*)(best + kid) < rank)) {
+          if (m <= k) {
+            J[0] = J[1];
+            J[1] = slot_f3(Q.im, Q.n, s, m - 1);
+            spec_leg_ray(J, 1, rxp, &ray->org, &ray->dir);
+            next = kSlotLeg;
+          } else {
+            spec_final_ray(J + 1, 0, rxp, &ray->org, &ray->dir, &ray->t_max);
+            next = kSlotFinal;
+          }
+        }
+      }
+      if (next == kSlotLeg && !ray_meets_label(S, ray->org, ray->dir, C.t_min,
+                                               key_label(kw.x, kw.y, m - 1), &ray->t_max)) {
+        ++cnt.pruned;
+        next = kSlotEmpty;
+      }
+    }
+  }
+  ray->skip = prev;
+  if (next == kSlotEmpty && rank < kHeadItems) {
+    atomicSub(Q.hleft + kid, 1u);
+    ++cnt.heads_out;
+  }
+  Q.ctl[s] = make_int4(attempt, m, prev, next);
+  return next;
+}
+
+// One item for the empty slot s, in item order: the next of the first list,
+// or, once that is exhausted and the deferred list is open (no deferral
+// can follow), of the deferred list.  Returns kTakePlaced (the item is in
+// the slot, its first leg in *ray), kTakeAgain (the item needed no cast,
+// was skipped or deferred) or kTakeNone (no item for now).  A tail item
+// whose key still has head candidates in slots is deferred.
+enum : int { kTakeNone = 0, kTakePlaced = 1, kTakeAgain = 2 };
+
+__device__ __forceinline__ int slot_take(const SceneView& S, const SimConst& C, const ValArgs& A,
+                                         const SpecSlots& Q, int64_t s,
+                                         const uint32_t* __restrict__ items, int64_t n_items,
+                                         unsigned long long* fetch, bool defer_open,
+                                         uint32_t* best, SlotRay* ray, SpecCounts& cnt) {
+  uint32_t c;
+  bool deferred = false;
+  if (*(volatile unsigned long long*)fetch < (unsigned long long)n_items) {
+    const int64_t i = fetch_next(fetch, n_items);
+    if (i < 0) return kTakeAgain;  // the last ones went to other lanes
+    c = items[i];
+  } else {
+    if (!defer_open) return kTakeNone;
+    const int64_t nd = (int64_t)*(volatile unsigned long long*)(Q.wc + kWcDefer);
+    if ((int64_t)*(volatile unsigned long long*)(Q.wc + kWcDeferFetch) >= nd) return kTakeNone;
+    const int64_t i = fetch_next(Q.wc + kWcDeferFetch, nd);
+    if (i < 0) return kTakeNone;
+    c = Q.defer[i];
+    deferred = true;
+  }
+  if (!NRT_OK_IDX(c < g_dbg_caps.cand, 31, c)) return kTakeAgain;
+  const uint64_t row_mask = (1ull << A.SC.row_bits) - 1ull;
+  const uint64_t e = A.SC.key[c];
+  const uint32_t kid = (uint32_t)(e >> A.SC.row_bits);
+  if (!NRT_OK_IDX(kid < g_dbg_caps.keys, 32, kid)) return kTakeAgain;
+  const uint32_t row = (uint32_t)(e & row_mask);
+  if (!NRT_OK_IDX(row < g_dbg_caps.rows, 33, row)) return kTakeAgain;
+  const uint32_t rank = c - A.K.pos[kid];
+  const bool head = rank < kHeadItems;
+  if (*(volatile const uint32_t*)(best + kid) < rank) {
+    if (head) atomicSub(Q.hleft + kid, 1u);
+    return kTakeAgain;
+  }
+  if (!head && !deferred && *(volatile const uint32_t*)(Q.hleft + kid) > 0) {
+    defer_push(Q, c);
+    return kTakeAgain;
+  }
+  const uint32_t slot = A.K.slot[kid];
+  if (!NRT_OK_IDX(slot < g_dbg_caps.table, 34, slot)) return kTakeAgain;
+  const uint64_t hi = A.T.b[slot].hi, lo = A.T.b[slot].lo;
+  const int k = (int)((hi >> 52) & 7);
+  if (!NRT_OK_IDX(k >= 1 && k <= C.max_depth, 35, k)) return kTakeAgain;
+  const int j = (int)(hi >> 56);
+  ++cnt.evaluated;
+  const float3 rxp = xyz(A.rx[C.batch ? 0 : j]);
+  const float3 txl = tx_of(C, j) - rxp;
+  float3 Pp[kMaxDepth], Pn[kMaxDepth], I[kMaxDepth + 2];
+  uint32_t lab[kMaxDepth];
+  spec_load(A, hi, lo, row, k, rxp, Pp, Pn, lab);
+  bool cast = spec_points(txl, Pp, Pn, k, I);
+  if (cast) {
+    spec_leg_ray(I, 1, rxp, &ray->org, &ray->dir);
+    cast = ray_meets_label(S, ray->org, ray->dir, C.t_min, lab[0], &ray->t_max);
+    cnt.pruned += !cast;
+  }
+  if (!cast) {
+    ++cnt.no_cast;
+    if (head) atomicSub(Q.hleft + kid, 1u);
+    return kTakeAgain;
+  }
+  Q.kid[s] = kid;
+  Q.rank[s] = rank;
+  Q.key[s] = make_ulonglong2(hi, lo);
+  for (int t = 0; t < k; ++t) {
+    slot_put3(Q.pl, Q.n, s, 2 * t, Pp[t]);
+    slot_put3(Q.pl, Q.n, s, 2 * t + 1, Pn[t]);
+    slot_put3(Q.im, Q.n, s, t, I[t + 1]);
+  }
+  ray->skip = -1;
+  Q.ctl[s] = make_int4(0, 1, -1, kSlotLeg);
+  cnt.heads_in += head;
+  return kTakePlaced;
+}
+
+__global__ void __launch_bounds__(kTraceThreads, 4)
+    spec_wave_advance_kernel(SceneView S, SimConst C, ValArgs A, SpecSlots Q,
+                             const uint32_t* __restrict__ items,
+                             const unsigned long long* __restrict__ n_items_p,
+                             uint32_t* __restrict__ best, unsigned long long* __restrict__ fetch,
+                             unsigned long long* ctr, int w) {
+  const int cur = w % 3, nxt = (w + 1) % 3;
+  // the next wave's counters (their last user was wave w - 2)
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Q.wc[kWcLegs + nxt] = 0;
+    Q.wc[kWcFinal + nxt] = 0;
+    Q.wc[kWcLegFetch + nxt] = 0;
+    Q.wc[kWcFinalFetch + nxt] = 0;
+  }
+  if (Q.wc[kWcStop]) return;  // set by the last wave's cast kernel
+  const bool defer_open = Q.wc[kWcDeferOpen] != 0;
+  const int64_t n_items = (int64_t)*n_items_p;
+  SpecCounts cnt;
+  // whole warps step through the slots together, so that the refill below
+  // takes items with one fetch per warp and round
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < Q.n;
+       base += stride) {
+    const int64_t s = base + (threadIdx.x & 31);
+    const bool valid = s < Q.n;
+    SlotRay ray;
+    int next = kSlotEmpty;
+    if (valid && Q.ctl[s].w != kSlotEmpty) next = slot_advance(S, C, A, Q, s, best, &ray, cnt);
+    bool need = valid && next == kSlotEmpty;
+    __syncwarp();
+    while (__any_sync(0xFFFFFFFFu, need)) {
+      if (need) {
+        const int r = slot_take(S, C, A, Q, s, items, n_items, fetch, defer_open, best, &ray, cnt);
+        if (r == kTakePlaced) next = kSlotLeg;
+        need = r == kTakeAgain;
+      }
+    }
+    if (next == kSlotLeg)
+      slot_queue(Q.q, Q.qs, Q.wc + kWcLegs + cur, s, ray.org, ray.t_max, ray.dir, ray.skip);
+    else if (next == kSlotFinal)
+      slot_queue(Q.qa, Q.qas, Q.wc + kWcFinal + cur, s, ray.org, ray.t_max, ray.dir, ray.skip);
+  }
+  count_add(ctr + kCtrPrunedLegs, cnt.pruned);
+  count_add(ctr + kCtrSpecItems, cnt.evaluated);
+  count_add(ctr + kCtrSpecNoCast, cnt.no_cast);
+  count_add(ctr + kCtrSpecLeg1, cnt.at_leg1);
+  count_add(Q.wc + kWcHeadsIn, cnt.heads_in);
+  count_add(Q.wc + kWcHeadsOut, cnt.heads_out);
+}
+
+// The wave's queued casts: the final legs first (any hit between I[k] and
+// the RX; some graze a surface for metres, and started first they overlap
+// the rest), then the legs (closest hit up to the exit of the key's surface
+// box, weighted: Eq. 3/4), as spec_candidate casts them.  Its first thread
+// also decides for the next wave: the deferred list opens once the first
+// list is exhausted and fewer than one slot in 16 holds a head candidate;
+// the waves stop once both lists are taken and this wave queued fewer than
+// kHandoffLegs casts.
+__global__ void __launch_bounds__(kTraceThreads, 8)
+    spec_wave_cast_kernel(SceneView S, SimConst C, SpecSlots Q,
+                          const unsigned long long* __restrict__ fetch,
+                          const unsigned long long* __restrict__ n_items_p, unsigned long long* ctr,
+                          int w) {
+  NRT_STACK_DECL
+  const int cur = w % 3;
+  const unsigned long long nl = Q.wc[kWcLegs + cur], nf = Q.wc[kWcFinal + cur];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !Q.wc[kWcStop] && *fetch >= *n_items_p) {
+    if (Q.wc[kWcDeferOpen] == 0) {
+      if (Q.wc[kWcHeadsIn] - Q.wc[kWcHeadsOut] <= (unsigned long long)(Q.n / 16))
+        Q.wc[kWcDeferOpen] = 1;
+    } else if (Q.wc[kWcDeferFetch] >= Q.wc[kWcDefer] && nl + nf < kHandoffLegs) {
+      Q.wc[kWcStop] = 1;
+    }
+  }
+  if (nl + nf == 0) return;
+  unsigned long long casts = 0;
+  bool finals = nf > 0;
+  for (;;) {
+    if (finals) {
+      const int64_t i = fetch_next(Q.wc + kWcFinalFetch + cur, (int64_t)nf);
+      if (i >= 0) {
+        const uint32_t s = Q.qas[i];
+        NRT_GUARD(s < Q.n, 37, s)
+        const float4 a = Q.qa[2 * i], b = Q.qa[2 * i + 1];
+        const Hit h = cast_ray(true, S, xyz(a), xyz(b), __float_as_int(b.w), C.t_min, a.w, false,
+                               my_stk, my_tstk, kTraceThreads, err);
+        ++casts;
+        Q.hd[s] = make_int2(h.dps, (int)h.labels);
+        continue;
+      }
+      finals = false;
+    }
+    const int64_t i = fetch_next(Q.wc + kWcLegFetch + cur, (int64_t)nl);
+    if (i < 0) break;
+    const uint32_t s = Q.qs[i];
+    NRT_GUARD(s < Q.n, 36, s)
+    const float4 a = Q.q[2 * i], b = Q.q[2 * i + 1];
+    const Hit h = cast_ray(false, S, xyz(a), xyz(b), __float_as_int(b.w), C.t_min, a.w, true, my_stk,
+                           my_tstk, kTraceThreads, err);
+    ++casts;
+    Q.hq[s] = make_float4(h.tbar, h.n.x, h.n.y, h.n.z);
+    Q.hd[s] = make_int2(h.dps, (int)h.labels);
+  }
+  count_add(ctr + kCtrValCasts, casts);
+}
+
+// After the waves: each candidate still in a slot runs to its end in one
+// lane (its pending hit first, then cast by cast).
+__global__ void __launch_bounds__(kTraceThreads, 5)
+    spec_resume_kernel(SceneView S, SimConst C, ValArgs A, SpecSlots Q, uint32_t* __restrict__ best,
+                       unsigned long long* ctr) {
+  NRT_STACK_DECL
+  SpecCounts cnt;
+  unsigned long long casts = 0;
+  for (;;) {
+    const int64_t s = fetch_next(Q.wc + kWcResume, Q.n);
+    if (s < 0) break;
+    if (Q.ctl[s].w == kSlotEmpty) continue;
+    for (;;) {
+      SlotRay ray;
+      const int next = slot_advance(S, C, A, Q, s, best, &ray, cnt);
+      if (next == kSlotEmpty) break;
+      Hit h;
+      if (next == kSlotLeg)
+        h = cast_ray(false, S, ray.org, ray.dir, ray.skip, C.t_min, ray.t_max, true, my_stk, my_tstk,
+                     kTraceThreads, err);
+      else
+        h = cast_ray(true, S, ray.org, ray.dir, ray.skip, C.t_min, ray.t_max, false, my_stk, my_tstk,
+                     kTraceThreads, err);
+      ++casts;
+      Q.hq[s] = make_float4(h.tbar, h.n.x, h.n.y, h.n.z);
+      Q.hd[s] = make_int2(h.dps, (int)h.labels);
+    }
+  }
+  count_add(ctr + kCtrValCasts, casts);
+  count_add(ctr + kCtrPrunedLegs, cnt.pruned);
+  count_add(ctr + kCtrSpecLeg1, cnt.at_leg1);
 }
 
 // Per specular key: the lowest valid rank is the representative (its path
@@ -2043,6 +2519,7 @@ struct Work {
   uint32_t *spec_cnt = nullptr, *spec_off = nullptr, *spec_best = nullptr;  // [keys]
   uint32_t *spec_cnt_t = nullptr, *spec_off_t = nullptr;  // tail item counts, offsets [keys]
   uint32_t* items = nullptr;  // specular (key, candidate) items [cand]
+  SpecSlots sw{};             // refinement state of the specular waves
   uint2 *cand = nullptr, *cand2 = nullptr;
   uint32_t *cand_cnt = nullptr, *cand_off = nullptr;
   uint32_t *fs = nullptr, *fd = nullptr, *os = nullptr, *od = nullptr;  // per-tile key counts, scans
@@ -2101,6 +2578,23 @@ nrt_status alloc_work(nrt_ctx* ctx, Work& W, const Caps& c, int64_t n_rows, cuda
   TRY(dalloc(&W.psi, c.paths, st));
   TRY(dalloc(&W.pti, c.paths, st));
   TRY(dalloc(&W.cnt, kCntN, st));
+  SpecSlots& Q = W.sw;
+  Q.n = std::min<int64_t>(c.cand, kSpecSlots);
+  TRY(dalloc(&Q.kid, Q.n, st));
+  TRY(dalloc(&Q.rank, Q.n, st));
+  TRY(dalloc(&Q.key, Q.n, st));
+  TRY(dalloc(&Q.ctl, Q.n, st));
+  TRY(dalloc(&Q.pl, 6 * kMaxDepth * Q.n, st));
+  TRY(dalloc(&Q.im, 3 * kMaxDepth * Q.n, st));
+  TRY(dalloc(&Q.hq, Q.n, st));
+  TRY(dalloc(&Q.hd, Q.n, st));
+  TRY(dalloc(&Q.q, 2 * Q.n, st));
+  TRY(dalloc(&Q.qs, Q.n, st));
+  TRY(dalloc(&Q.qa, 2 * Q.n, st));
+  TRY(dalloc(&Q.qas, Q.n, st));
+  TRY(dalloc(&Q.defer, c.cand, st));
+  TRY(dalloc(&Q.hleft, c.keys, st));
+  TRY(dalloc(&Q.wc, kWcN, st));
   return NRT_OK;
 }
 
@@ -2110,7 +2604,9 @@ void release_work(Work& W, cudaStream_t st) {
                   W.spec_best, W.items,
                   W.K.tries, W.K.status, W.spec_list, W.diff_list, W.cand,
                   W.cand2, W.cand_cnt, W.cand_off, W.fs, W.fd, W.os, W.od, W.sk0, W.tk0,
-                  W.sv0, W.tv, W.raw, W.psk, W.ptk, W.psi, W.pti, W.cnt, W.order};
+                  W.sv0, W.tv, W.raw, W.psk, W.ptk, W.psi, W.pti, W.cnt, W.order,
+                  W.sw.kid, W.sw.rank, W.sw.key, W.sw.ctl, W.sw.pl, W.sw.im, W.sw.hq, W.sw.hd,
+                  W.sw.q, W.sw.qs, W.sw.qa, W.sw.qas, W.sw.defer, W.sw.hleft, W.sw.wc};
   for (void* q : ptrs)
     if (q) cudaFreeAsync(q, st);
   W = Work();
@@ -2296,14 +2792,38 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   TRY(cudaMemsetAsync(W.spec_cnt_t, 0, c.keys * sizeof(uint32_t), st));
   spec_count_kernel<<<blocks_for(c.keys, 256, sm), 256, 0, st>>>(W.K, W.spec_list, W.cnt + kCntSpec,
                                                                 C.rep_tries, W.spec_cnt, W.spec_cnt_t,
-                                                                W.spec_best); count_launch();
+                                                                W.spec_best, W.sw.hleft); count_launch();
   scan_exclusive(W.spec_cnt, W.spec_off, c.keys, st);
   scan_exclusive(W.spec_cnt_t, W.spec_off_t, c.keys, st);
   spec_expand_kernel<<<blocks_for(c.keys * 32, 256, sm), 256, 0, st>>>(
       W.K, W.spec_list, W.cnt + kCntSpec, W.spec_cnt, W.spec_off, W.spec_cnt_t, W.spec_off_t,
       W.items, c.cand, W.cnt + kCntItems); count_launch();
-  validate_specular_items_kernel<<<blocks_for(c.cand, kTraceThreads, sm, 5), kTraceThreads, 0, st>>>(
-      S, C, V, W.items, W.cnt + kCntItems, W.spec_best, W.cnt + kCntFetchS, ctr); count_launch();
+  // the items in waves (spec_wave_*), the candidates still in slots to
+  // their end, then whatever items the waves left: the first list from its
+  // fetch counter on, then the deferred one; or the items in one persistent
+  // pass
+  if (r->p.spec_waves == 1 || (r->p.spec_waves == 0 && c.cand >= kWaveMinCand)) {
+    const SpecSlots& Q = W.sw;
+    TRY(cudaMemsetAsync(Q.ctl, 0, Q.n * sizeof(int4), st));
+    TRY(cudaMemsetAsync(Q.wc, 0, kWcN * sizeof(unsigned long long), st));
+    const int adv = blocks_for(Q.n, kTraceThreads, sm, 16);
+    for (int w = 0; w < kSpecWaves; ++w) {
+      spec_wave_advance_kernel<<<adv, kTraceThreads, 0, st>>>(S, C, V, Q, W.items, W.cnt + kCntItems,
+                                                              W.spec_best, W.cnt + kCntFetchS, ctr,
+                                                              w); count_launch();
+      spec_wave_cast_kernel<<<sm * 8, kTraceThreads, 0, st>>>(S, C, Q, W.cnt + kCntFetchS,
+                                                             W.cnt + kCntItems, ctr, w); count_launch();
+    }
+    spec_resume_kernel<<<blocks_for(Q.n, kTraceThreads, sm, 5), kTraceThreads, 0, st>>>(
+        S, C, V, Q, W.spec_best, ctr); count_launch();
+    validate_specular_items_kernel<<<blocks_for(c.cand, kTraceThreads, sm, 5), kTraceThreads, 0, st>>>(
+        S, C, V, W.items, W.cnt + kCntItems, W.spec_best, W.cnt + kCntFetchS, ctr); count_launch();
+    validate_specular_items_kernel<<<blocks_for(c.cand, kTraceThreads, sm, 5), kTraceThreads, 0, st>>>(
+        S, C, V, Q.defer, Q.wc + kWcDefer, W.spec_best, Q.wc + kWcDeferFetch, ctr); count_launch();
+  } else {
+    validate_specular_items_kernel<<<blocks_for(c.cand, kTraceThreads, sm, 5), kTraceThreads, 0, st>>>(
+        S, C, V, W.items, W.cnt + kCntItems, W.spec_best, W.cnt + kCntFetchS, ctr); count_launch();
+  }
   spec_finish_kernel<<<blocks_for(c.keys, kTraceThreads, sm, 8), kTraceThreads, 0, st>>>(
       S, C, V, W.spec_list, W.cnt + kCntSpec, W.spec_best, ctr); count_launch();
   TRY(cudaStreamWaitEvent(st, ctx->join, 0));

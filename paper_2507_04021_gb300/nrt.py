@@ -48,6 +48,7 @@ class TraceParams(C.Structure):
         ("r_rx", C.c_float), ("t_min", C.c_float), ("t_a_deg", C.c_float), ("t_d", C.c_float),
         ("freq", C.c_float), ("keep_keys", C.c_int32), ("key_capacity", C.c_int64),
         ("cand_capacity", C.c_int64), ("launch", C.c_int32), ("diffraction", C.c_int32),
+        ("spec_waves", C.c_int32),
     ]
 
 
