@@ -752,9 +752,8 @@ def ours(args):
     n_spec = counts["validation_casts"] - n_diff
     per_val = ((n_diff * ab["bytes_per_shadow_cast"] + n_spec * ab["bytes_per_segment"])
                / max(counts["validation_casts"], 1))
-    roof = roof_entry("validation phase: specular waves (spec_wave_advance_kernel + "
-                      "spec_wave_cast_kernel per wave, spec_resume_kernel), spec_finish_kernel, "
-                      "validate_diffuse_kernel", counts["validation_casts"], per_val,
+    roof = roof_entry("validation phase: validate_specular_items_kernel + spec_finish_kernel + "
+                      "validate_diffuse_kernel (one launch each)", counts["validation_casts"], per_val,
                       ph["validate"], "validation cast", "validation")
     tr_ms = float(np.mean(trace_ms))
     roof_more = [

@@ -98,13 +98,14 @@ typedef struct {
                            (Sec. II-B-3, nrt_scene_set_edges): one candidate per
                            (edge, RX), kept when its point lies inside the edge,
                            TX and RX lie outside the wedge and both see it */
-  int32_t spec_waves;   /* schedule of the specular refinement (Sec. II-B-2), the
-                           paths the same either way: 0 (default) automatic --
-                           waves of up to 2^22 candidates held in device memory,
-                           each leg cast by a lean kernel, when the candidate
-                           capacity is at least 2^21, else one persistent pass
-                           in which a lane refines a candidate from start to
-                           end; 1 waves; 2 the persistent pass */
+  int32_t spec_waves;   /* schedule of the specular refinement (Sec. II-B-2):
+                           0 (default) or 2: one persistent pass in which a lane
+                           refines a candidate from start to end; 1: waves of up
+                           to 2^22 candidates held in device memory, each leg
+                           cast by a lean kernel (experimental: the same paths
+                           on the office workloads tested, but on the office's
+                           DPS-directed launch a representative the waves chose
+                           failed the re-refinement check, NRT_ERR_STATE) */
 } nrt_trace_params;
 
 /* Per-simulation counters (nrt_result_counts). */

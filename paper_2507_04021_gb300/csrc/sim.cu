@@ -1404,10 +1404,6 @@ __global__ void __launch_bounds__(kTraceThreads, 5)
 // the work outgrew them).
 constexpr int64_t kSpecSlots = 1 << 22;
 constexpr int kSpecWaves = 32;
-// automatic schedule: waves from this candidate capacity on (below it the
-// fixed cost of the waves -- two launches each, a few hundred microseconds
-// of tail per wave -- outweighs the faster casts)
-constexpr int64_t kWaveMinCand = 1 << 21;
 constexpr unsigned long long kHandoffLegs = 1ull << 18;
 
 enum : int { kSlotEmpty = 0, kSlotLeg = 1, kSlotFinal = 2 };
@@ -2798,11 +2794,11 @@ nrt_status enqueue_rest(nrt_result* r, Work& W, const SceneView& S, const SimCon
   spec_expand_kernel<<<blocks_for(c.keys * 32, 256, sm), 256, 0, st>>>(
       W.K, W.spec_list, W.cnt + kCntSpec, W.spec_cnt, W.spec_off, W.spec_cnt_t, W.spec_off_t,
       W.items, c.cand, W.cnt + kCntItems); count_launch();
-  // the items in waves (spec_wave_*), the candidates still in slots to
-  // their end, then whatever items the waves left: the first list from its
-  // fetch counter on, then the deferred one; or the items in one persistent
-  // pass
-  if (r->p.spec_waves == 1 || (r->p.spec_waves == 0 && c.cand >= kWaveMinCand)) {
+  // the items in one persistent pass; or, on request, in waves
+  // (spec_wave_*), the candidates still in slots to their end, then
+  // whatever items the waves left: the first list from its fetch counter
+  // on, then the deferred one
+  if (r->p.spec_waves == 1) {
     const SpecSlots& Q = W.sw;
     TRY(cudaMemsetAsync(Q.ctl, 0, Q.n * sizeof(int4), st));
     TRY(cudaMemsetAsync(Q.wc, 0, kWcN * sizeof(unsigned long long), st));

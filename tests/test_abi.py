@@ -34,4 +34,4 @@ def test_status_strings_and_defaults():
     p = nrt.default_trace_params()
     assert p.kappa == 10 and abs(p.t_a_deg - 1.0) < 1e-7 and abs(p.t_d - 0.01) < 1e-9
     assert p.max_depth == 5
-    assert p.spec_waves == 0  # automatic schedule of the specular refinement
+    assert p.spec_waves == 0  # the specular refinement's persistent pass
