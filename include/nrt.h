@@ -103,9 +103,11 @@ typedef struct {
                            refines a candidate from start to end; 1: waves of up
                            to 2^22 candidates held in device memory, each leg
                            cast by a lean kernel (experimental: the same paths
-                           on the office workloads tested, but on the office's
-                           DPS-directed launch a representative the waves chose
-                           failed the re-refinement check, NRT_ERR_STATE) */
+                           on most office workloads tested, but the wave cast
+                           kernel and the refinement round the Eq. 4 normal of
+                           a cast differently in rare cases, and a representative
+                           chosen by the waves can then fail the re-refinement
+                           check, NRT_ERR_STATE) */
 } nrt_trace_params;
 
 /* Per-simulation counters (nrt_result_counts). */

@@ -1,6 +1,8 @@
 """The two schedules of the specular refinement (Sec. II-B-2) give the same
-paths on these workloads (the waves are opt-in: on the office's DPS-directed
-launch a representative they chose failed the re-refinement check).  The persistent pass refines each (key, candidate) item in one lane
+paths on these workloads (the waves are opt-in: two compiled copies of the
+Eq. 4 normal round differently in rare cases, and on the office's
+DPS-directed launch a representative they chose failed the re-refinement
+check).  The persistent pass refines each (key, candidate) item in one lane
 from start to end; the waves keep each candidate's planes and image-method
 points in device memory and cast every leg in a lean kernel, deferring a
 key's tail items until its first candidates are done.  Both take the same
