@@ -123,45 +123,56 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    once the kernel sources have changed since the capture."""
+# The ncu counters in profiles/office_sim_top_kernels.md hold while the
+# sources they were taken from are unchanged: the validation phase's against
+# the whole of csrc/sim.cu + csrc/nrt_device.cuh, the trace and visibility
+# kernels' against the part of sim.cu before the validation code (which
+# holds them and everything they call) + nrt_device.cuh.
+_VALIDATION_MARK = "// Diffuse: the candidate's own interaction points"
+
+
+def _source_hash(kernel):
     import hashlib
+    sim = open(os.path.join(ROOT, "paper_2507_04021_gb300", "csrc", "sim.cu"), "rb").read()
+    dev = open(os.path.join(ROOT, "paper_2507_04021_gb300", "csrc", "nrt_device.cuh"), "rb").read()
+    if kernel in ("trace_kernel", "vis_kernel"):
+        i = sim.find(_VALIDATION_MARK.encode())
+        if i < 0:
+            return None
+        sim = sim[:i]
+    return hashlib.sha256(sim + dev).hexdigest()
+
+
+def _profile_value(key, kernel):
+    """The committed summary's `key` figure for `kernel`, or None once the
+    kernel's sources have changed since the capture."""
     path = os.path.join(ROOT, "profiles", "office_sim_top_kernels.md")
     if not os.path.exists(path):
         return None
-    val = sha = None
+    val = None
+    sha = {}
     for ln in open(path):
         f = ln.split()
-        if len(f) == 3 and f[0] == "traffic_bytes_per_launch" and f[1] == kernel:
-            val = float(f[2])  # per launch (per simulation for a phase)
-        if len(f) == 2 and f[0] == "source_sha256":
-            sha = f[1]
-    h = hashlib.sha256()
-    for rel in ("csrc/sim.cu", "csrc/nrt_device.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2507_04021_gb300", rel), "rb").read())
-    return val if (val is not None and sha == h.hexdigest()) else None
+        if len(f) == 3 and f[0] == key and f[1] == kernel:
+            val = float(f[2])
+        if len(f) == 2 and f[0] in ("source_sha256", "source_sha256_traversal"):
+            sha[f[0]] = f[1]
+    want = sha.get("source_sha256_traversal" if kernel in ("trace_kernel", "vis_kernel")
+                   else "source_sha256")
+    return val if (val is not None and want is not None and want == _source_hash(kernel)) else None
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch of `kernel` (per simulation for the validation
+    phase) from the committed ncu summary, or None once its sources changed."""
+    return _profile_value("traffic_bytes_per_launch", kernel)
 
 
 def _l2_bytes(kernel):
     """L2 bytes per unit (lts__t_bytes per cast, from an ncu capture of the
-    small case) of `kernel` in the committed summary, or None once the
-    kernel sources have changed since the capture."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "office_sim_top_kernels.md")
-    if not os.path.exists(path):
-        return None
-    val = sha = None
-    for ln in open(path):
-        f = ln.split()
-        if len(f) == 3 and f[0] == "l2_bytes_per_unit" and f[1] == kernel:
-            val = float(f[2])
-        if len(f) == 2 and f[0] == "source_sha256":
-            sha = f[1]
-    h = hashlib.sha256()
-    for rel in ("csrc/sim.cu", "csrc/nrt_device.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2507_04021_gb300", rel), "rb").read())
-    return val if (val is not None and sha == h.hexdigest()) else None
+    small case) of `kernel` from the committed summary, or None once its
+    sources changed."""
+    return _profile_value("l2_bytes_per_unit", kernel)
 
 
 def _alg_bytes():
