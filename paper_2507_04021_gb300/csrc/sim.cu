@@ -1677,7 +1677,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4)
   const int64_t n_items = (int64_t)*n_items_p;
   SpecCounts cnt;
   // whole warps step through the slots together, so that the refill below
-  // takes items with one fetch per warp and round
+  // takes items with one fetch per warp and refill step
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < Q.n;
        base += stride) {
